@@ -1,0 +1,390 @@
+"""Plain, slow FP64 CPU oracle of the IBDL hot path.
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg may import this module; the library never does.
+It shares no code with the CUDA path: inputs come from ``workloads`` (point
+placement and boundary data only).
+
+Every function follows a passage of Leathers & Guy, "Immersed Boundary Double
+Layer method" (arXiv:2203.12126):
+
+* delta function          Sec. 5.2, eq. (delta eqn 1)-(delta eqn 2)
+* spread S                Sec. 5.2, eq. (spread operator again2)
+* interpolation S*        Sec. 5.2, eq. (interpolation again)
+* S~Q = div(S Q n)        Sec. 4.1 (ibdl), Sec. 5.2 eq. (Stilde): spread each
+                          component of Q n, then centred differences
+* 5/7-point Laplacian     Sec. 5.1 (five-point; its 3D analogue, Sec. 6.7)
+* Dirichlet system        Sec. 5.3, eq. (ibdl schur again)
+* Neumann system          Sec. 4.4, eq. (Neumann saddle point)
+* field evaluation        Sec. 4.1 step 2, eq. (ibdl 1 again); eq. (ib neumann 1)
+* GMRES                   Sec. 5.3 (unpreconditioned, relative residual)
+* interior indicator      App. D (Q = 1 with a Poisson-like large kappa)
+
+Conventions.  The paper writes the operator as L_p = Delta_h - k^2.  This
+oracle uses L' = I - kappa Delta_h with kappa = 1/k^2, so L_p = -(1/kappa) L'
+and L_p^{-1} = -kappa L'^{-1}; the Dirichlet operator of eq. (ibdl schur
+again), -S* L_p^{-1} S~ + I/2, becomes A_D = I/2 + kappa S* L'^{-1} S~ and
+the Neumann one becomes A_N = kappa S* L'^{-1} S~ - I/2.  Grid fields are
+numpy arrays of shape (n,)*d indexed [.., y, x] (x fastest in memory); grid
+node j sits at origin + j h.  Forcing g~ is given in the paper's convention
+Delta u - k^2 u = g.
+
+Parity pins live in tests/test_oracle_*.py; functions without a pin say so.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# ---------------------------------------------------------------------------
+# Regularised delta function, Sec. 5.2
+# ---------------------------------------------------------------------------
+
+
+def phi_peskin4(r):
+    """Peskin's 4-point kernel, eq. (delta eqn 2): two branches in |r|."""
+    a = np.abs(np.asarray(r, dtype=np.float64))
+    out = np.zeros_like(a)
+    inner = a <= 1.0
+    outer = (a > 1.0) & (a < 2.0)
+    ai = a[inner]
+    out[inner] = (3.0 - 2.0 * ai + np.sqrt(1.0 + 4.0 * ai - 4.0 * ai * ai)) / 8.0
+    ao = a[outer]
+    out[outer] = (5.0 - 2.0 * ao - np.sqrt(np.maximum(0.0, -7.0 + 12.0 * ao - 4.0 * ao * ao))) / 8.0
+    return out
+
+
+def phi_cos4(r):
+    """Cosine 4-point kernel (1 + cos(pi r / 2)) / 4 on |r| < 2."""
+    a = np.abs(np.asarray(r, dtype=np.float64))
+    return np.where(a < 2.0, 0.25 * (1.0 + np.cos(0.5 * np.pi * a)), 0.0)
+
+
+PHI = {"peskin4": phi_peskin4, "cos4": phi_cos4}
+
+
+class Box:
+    """Periodic box [origin, origin + L)^d with n nodes per axis."""
+
+    def __init__(self, dim, n, box_len, origin):
+        self.d = int(dim)
+        self.n = int(n)
+        self.L = float(box_len)
+        self.o = np.asarray(origin, dtype=np.float64)[: self.d]
+        self.h = self.L / self.n
+
+    @classmethod
+    def of(cls, geom):
+        return cls(geom.dim, geom.n, geom.box_len, geom.origin)
+
+    @property
+    def shape(self):
+        return (self.n,) * self.d
+
+    def axis(self, c):
+        """numpy array axis of spatial direction c (0 = x)."""
+        return self.d - 1 - c
+
+
+def _tap_table(box, X, delta):
+    """For every point and axis: the 4 node indices j whose |x_j - X| < 2h
+    (before periodic wrap) and phi((x_j - X)/h) there.
+
+    Nodes at origin + j h; with s = (X - origin)/h the support of phi(j - s)
+    is s-2 < j < s+2, i.e. j = floor(s)-1 .. floor(s)+2.
+    """
+    phi = PHI[delta]
+    s = (X - box.o[None, :]) / box.h                      # (M, d)
+    base = np.floor(s).astype(np.int64) - 1               # (M, d)
+    j = base[:, :, None] + np.arange(4)[None, None, :]    # (M, d, 4)
+    wt = phi(j - s[:, :, None])                           # (M, d, 4)
+    return j % box.n, wt
+
+
+def spread(box, X, F, w, delta="peskin4"):
+    """(S F)_j = sum_i F_i w_i delta_h(x_j - X_i), eq. (spread operator
+    again2), delta_h = h^{-d} prod_c phi((x_c - X_c)/h), eq. (delta eqn 1)."""
+    M = X.shape[0]
+    jj, wt = _tap_table(box, X, delta)
+    out = np.zeros(box.shape)
+    amp = F * w / box.h ** box.d
+    taps = np.indices((4,) * box.d).reshape(box.d, -1).T   # all 4^d tap tuples
+    for t in taps:
+        val = amp.copy()
+        idx = [None] * box.d
+        for c in range(box.d):
+            val = val * wt[:, c, t[c]]
+            idx[box.axis(c)] = jj[:, c, t[c]]
+        np.add.at(out, tuple(idx), val)
+    assert val.shape == (M,)
+    return out
+
+
+def interp(box, X, u, delta="peskin4"):
+    """(S* u)(X_i) = sum_j u_j delta_h(x_j - X_i) h^d, eq. (interpolation
+    again): the h^{-d} of delta_h cancels the h^d cell volume."""
+    jj, wt = _tap_table(box, X, delta)
+    out = np.zeros(X.shape[0])
+    taps = np.indices((4,) * box.d).reshape(box.d, -1).T
+    for t in taps:
+        val = np.ones(X.shape[0])
+        idx = [None] * box.d
+        for c in range(box.d):
+            val = val * wt[:, c, t[c]]
+            idx[box.axis(c)] = jj[:, c, t[c]]
+        out += val * u[tuple(idx)]
+    return out
+
+
+def central_diff(box, g, c):
+    """(D_c g)_j = (g_{j+e_c} - g_{j-e_c}) / (2h), periodic (Sec. 5.2)."""
+    a = box.axis(c)
+    return (np.roll(g, -1, axis=a) - np.roll(g, 1, axis=a)) / (2.0 * box.h)
+
+
+def spread_div(box, X, nrm, w, Q, delta="peskin4"):
+    """S~ Q = div_h (S (Q n)), eq. (Stilde): spread each component Q n_c,
+    then sum the centred differences."""
+    out = np.zeros(box.shape)
+    for c in range(box.d):
+        out += central_diff(box, spread(box, X, Q * nrm[:, c], w, delta), c)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Periodic Helmholtz solve, Sec. 5.1
+# ---------------------------------------------------------------------------
+
+
+def laplacian(box, u):
+    """Standard 5-point (2D) / 7-point (3D) Laplacian, periodic."""
+    out = -2.0 * box.d * u
+    for a in range(box.d):
+        out = out + np.roll(u, 1, axis=a) + np.roll(u, -1, axis=a)
+    return out / box.h ** 2
+
+
+def apply_Lprime(box, kappa, u):
+    """L' u = u - kappa Delta_h u (explicit stencil, used by pins)."""
+    return u - kappa * laplacian(box, u)
+
+
+def symbol(box, kappa):
+    """Eigenvalues of L' on the Fourier modes exp(2 pi i k.j / n):
+    sigma(k) = 1 + (4 kappa / h^2) sum_c sin^2(pi k_c / n)."""
+    k = np.arange(box.n)
+    s2 = np.sin(np.pi * k / box.n) ** 2
+    sig = np.ones(box.shape)
+    for a in range(box.d):
+        shp = [1] * box.d
+        shp[a] = box.n
+        sig = sig + (4.0 * kappa / box.h ** 2) * s2.reshape(shp)
+    return sig
+
+
+def helmholtz_solve(box, kappa, f):
+    """v = L'^{-1} f by diagonalising the periodic stencil with the FFT."""
+    F = np.fft.fftn(f)
+    return np.real(np.fft.ifftn(F / symbol(box, kappa)))
+
+
+def helmholtz_dense(box, kappa):
+    """Dense matrix of L' (tiny grids only): column j = L' e_j."""
+    n = box.n ** box.d
+    A = np.zeros((n, n))
+    e = np.zeros(box.shape)
+    for j in range(n):
+        e.reshape(-1)[j] = 1.0
+        A[:, j] = apply_Lprime(box, kappa, e).reshape(-1)
+        e.reshape(-1)[j] = 0.0
+    return A
+
+
+# ---------------------------------------------------------------------------
+# The boundary operators, Sec. 4.1, 4.4 and 5.3
+# ---------------------------------------------------------------------------
+
+DIRICHLET, NEUMANN = 0, 1
+
+
+class Operator:
+    """A_D Q = Q/2 + kappa S* L'^{-1} S~ Q         (eq. (ibdl schur again))
+    A_N U = kappa S* L'^{-1} S~ U - U/2          (eq. (Neumann saddle point))
+    """
+
+    def __init__(self, geom, bc, kappa=None, delta=None):
+        self.box = Box.of(geom)
+        self.X = np.asarray(geom.X, dtype=np.float64)
+        self.nrm = np.asarray(geom.normals, dtype=np.float64)
+        self.w = np.asarray(geom.weights, dtype=np.float64)
+        self.kappa = float(geom.kappa if kappa is None else kappa)
+        self.delta = geom.delta if delta is None else delta
+        self.bc = int(bc)
+        self.matvecs = 0
+
+    @property
+    def m(self):
+        return self.X.shape[0]
+
+    def layer(self, Q):
+        """v = L'^{-1} S~ Q on the grid."""
+        f = spread_div(self.box, self.X, self.nrm, self.w, Q, self.delta)
+        return helmholtz_solve(self.box, self.kappa, f)
+
+    def apply(self, Q):
+        self.matvecs += 1
+        Q = np.asarray(Q, dtype=np.float64)
+        y = self.kappa * interp(self.box, self.X, self.layer(Q), self.delta)
+        return y + 0.5 * Q if self.bc == DIRICHLET else y - 0.5 * Q
+
+    __call__ = apply
+
+    def rhs(self, bdata, g_grid=None):
+        """Right-hand side of the boundary system.
+
+        Dirichlet: U_b - S* L_p^{-1} g~ = U_b + kappa S* L'^{-1} g~.
+        Neumann:   S* L_p^{-1} S V_b - S* L_p^{-1} g~
+                   = kappa S* L'^{-1} (g~ - S V_b).
+        """
+        b = np.asarray(bdata, dtype=np.float64)
+        if self.bc == DIRICHLET:
+            out = b.copy()
+            if g_grid is not None:
+                out += self.kappa * interp(self.box, self.X,
+                                           helmholtz_solve(self.box, self.kappa, g_grid),
+                                           self.delta)
+            return out
+        src = -spread(self.box, self.X, b, self.w, self.delta)
+        if g_grid is not None:
+            src = src + g_grid
+        return self.kappa * interp(self.box, self.X,
+                                   helmholtz_solve(self.box, self.kappa, src),
+                                   self.delta)
+
+    def evaluate(self, Q, vb=None, g_grid=None):
+        """Grid solution, step 2 of Sec. 4.1: L_p u + S~Q = g~ gives
+        u = kappa L'^{-1}(S~Q - g~); Neumann (eq. (ib neumann 1)) adds S V_b."""
+        src = spread_div(self.box, self.X, self.nrm, self.w, Q, self.delta)
+        if self.bc == NEUMANN and vb is not None:
+            src = src + spread(self.box, self.X, vb, self.w, self.delta)
+        if g_grid is not None:
+            src = src - g_grid
+        return self.kappa * helmholtz_solve(self.box, self.kappa, src)
+
+    def dense(self):
+        """Assemble A column by column, A[:, i] = A e_i."""
+        M = self.m
+        A = np.zeros((M, M))
+        e = np.zeros(M)
+        for i in range(M):
+            e[i] = 1.0
+            A[:, i] = self.apply(e)
+            e[i] = 0.0
+        return A
+
+
+# ---------------------------------------------------------------------------
+# GMRES, Sec. 5.3 (textbook restarted GMRES(m), modified Gram-Schmidt)
+# ---------------------------------------------------------------------------
+
+
+class GmresResult:
+    def __init__(self, x, iters, rel_res, history, converged):
+        self.x, self.iters, self.rel_res = x, iters, rel_res
+        self.history, self.converged = history, converged
+
+
+def gmres(A, b, tol=1e-8, restart=30, maxiter=1000, x0=None):
+    """Solve A x = b until ||b - A x|| / ||b|| <= tol, x0 = 0 by default.
+
+    Arnoldi with modified Gram-Schmidt builds an orthonormal basis of the
+    Krylov space; Givens rotations keep the Hessenberg matrix triangular, so
+    |g_{j+1}| is the residual norm of the least-squares iterate.  ``iters``
+    counts inner iterations (matrix-vector products after the first
+    residual), as the paper's tables do.
+    """
+    b = np.asarray(b, dtype=np.float64)
+    M = b.shape[0]
+    x = np.zeros(M) if x0 is None else np.array(x0, dtype=np.float64)
+    bnorm = np.linalg.norm(b)
+    if bnorm == 0.0:
+        return GmresResult(np.zeros(M), 0, 0.0, [], True)
+    total = 0
+    history = []
+    while True:
+        r = b - A(x) if np.any(x) else b.copy()
+        beta = np.linalg.norm(r)
+        if beta / bnorm <= tol:
+            return GmresResult(x, total, beta / bnorm, history, True)
+        if total >= maxiter:
+            return GmresResult(x, total, beta / bnorm, history, False)
+        m = restart
+        V = np.zeros((m + 1, M))
+        H = np.zeros((m + 1, m))
+        cs = np.zeros(m)
+        sn = np.zeros(m)
+        g = np.zeros(m + 1)
+        V[0] = r / beta
+        g[0] = beta
+        k = 0
+        for j in range(m):
+            w = A(V[j])
+            total += 1
+            for i in range(j + 1):
+                H[i, j] = np.dot(w, V[i])
+                w = w - H[i, j] * V[i]
+            hnext = np.linalg.norm(w)
+            H[j + 1, j] = hnext
+            if hnext > 0.0:
+                V[j + 1] = w / hnext
+            for i in range(j):
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            den = np.hypot(H[j, j], H[j + 1, j])
+            cs[j], sn[j] = H[j, j] / den, H[j + 1, j] / den
+            H[j, j] = den
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            k = j + 1
+            history.append(abs(g[j + 1]) / bnorm)
+            if abs(g[j + 1]) / bnorm <= tol or total >= maxiter or hnext == 0.0:
+                break
+        y = np.linalg.solve(np.triu(H[:k, :k]), g[:k])
+        x = x + V[:k].T @ y
+
+
+def solve(geom, bc, bdata, tol=1e-10, restart=30, maxiter=1000, g_grid=None,
+          kappa=None):
+    """Step 1 of Sec. 4.1 (or Sec. 4.4): GMRES on the boundary system."""
+    op = Operator(geom, bc, kappa)
+    b = op.rhs(bdata, g_grid)
+    res = gmres(op, b, tol, restart, maxiter)
+    res.matvecs = op.matvecs
+    res.op = op
+    res.b = b
+    return res
+
+
+def solve_dense(geom, bc, bdata, g_grid=None, kappa=None):
+    """Exact discrete solution Q* = A^{-1} b by LU (small M only)."""
+    op = Operator(geom, bc, kappa)
+    b = op.rhs(bdata, g_grid)
+    return np.linalg.solve(op.dense(), b)
+
+
+# ---------------------------------------------------------------------------
+# Interior indicator, App. D
+# ---------------------------------------------------------------------------
+
+
+def indicator(geom, kappa_large=1e6):
+    """Regularised indicator chi_h: solve (I - kappa Delta_h) u = -kappa S~1
+    ... with kappa large (the Poisson limit -Delta u = div(delta n)), then
+    shift the value at the box corner to 0.  Parity unpinned beyond the
+    threshold-at-1/2 check against the exact shape."""
+    box = Box.of(geom)
+    f = spread_div(box, geom.X, geom.normals, geom.weights,
+                   np.ones(geom.m), geom.delta)
+    u = kappa_large * helmholtz_solve(box, kappa_large, f)
+    return u - u.reshape(-1)[0]

@@ -1,0 +1,373 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics
+(not against the oracle itself).  CPU only.
+
+Each test names what a plausible mistake in the oracle would break.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import ibdl_oracle as O
+from workloads import configs, geometry
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+# ---------------------------------------------------------------------------
+# delta function (Sec. 5.2, eq. (delta eqn 2); Peskin 2002 moment conditions)
+# ---------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("r", np.linspace(0.0, 1.0, 37)[:-1])
+def test_peskin4_moment_conditions(r):
+    """Peskin's kernel is built from: sum phi = 1, sum (r-j) phi = 0,
+    sum phi^2 = 3/8, and even/odd sums 1/2 each (a dropped sqrt term or a
+    wrong branch breaks these)."""
+    j = np.arange(-3, 5)
+    p = O.phi_peskin4(r - j)
+    assert abs(p.sum() - 1.0) < 1e-15
+    assert abs(((r - j) * p).sum()) < 1e-15
+    assert abs((p * p).sum() - 3.0 / 8.0) < 1e-15
+    assert abs(p[j % 2 == 0].sum() - 0.5) < 1e-15
+    assert abs(p[j % 2 == 1].sum() - 0.5) < 1e-15
+
+
+def test_peskin4_point_values():
+    """phi(0)=1/2, phi(1)=1/4 from both branches, phi(2)=0,
+    phi(1/2) = (2 + sqrt 2)/8."""
+    assert O.phi_peskin4(0.0) == 0.5
+    assert abs(O.phi_peskin4(1.0) - 0.25) < 1e-16
+    assert abs(O.phi_peskin4(1.0 + 1e-12) - 0.25) < 1e-10
+    assert O.phi_peskin4(2.0) == 0.0
+    assert abs(O.phi_peskin4(0.5) - (2 + math.sqrt(2)) / 8) < 1e-16
+    assert abs(O.phi_peskin4(-0.5) - O.phi_peskin4(0.5)) == 0.0
+
+
+@pytest.mark.parametrize("r", np.linspace(0.0, 1.0, 11)[:-1])
+def test_cos4_partition_of_unity(r):
+    j = np.arange(-3, 5)
+    assert abs(O.phi_cos4(r - j).sum() - 1.0) < 1e-15
+
+
+# ---------------------------------------------------------------------------
+# spread / interpolation (Sec. 5.2)
+# ---------------------------------------------------------------------------
+
+
+def _brute_delta(box, x, X, delta):
+    """delta_h(x - X) with the minimum periodic image, every axis."""
+    v = 1.0 / box.h ** box.d
+    for c in range(box.d):
+        dx = x[c] - X[c]
+        dx -= box.L * np.round(dx / box.L)
+        v *= O.PHI[delta](dx / box.h)
+    return float(v)
+
+
+def _node(box, idx):
+    """Coordinates of array index idx ([..,y,x]) as (x, y[, z])."""
+    return np.array([box.o[c] + box.h * idx[box.axis(c)] for c in range(box.d)])
+
+
+@pytest.mark.parametrize("dim,delta", [(2, "peskin4"), (2, "cos4"), (3, "peskin4")])
+def test_spread_matches_brute_force_over_all_nodes(dim, delta):
+    """Spread by the 4-tap table == a loop over every node of a tiny
+    periodic grid with minimum-image distances (points straddle the wrap)."""
+    rng = np.random.default_rng(5)
+    n = 8 if dim == 2 else 6
+    box = O.Box(dim, n, 1.0, (0.1,) * dim)
+    M = 5
+    X = box.o[None, :] + rng.uniform(0, 1, (M, dim))
+    X[0, 0] = box.o[0] + 0.01          # next to the lower wrap
+    X[1, -1] = box.o[-1] + 0.99        # next to the upper wrap
+    X[2] = box.o + 3 * box.h            # exactly on a node
+    F = rng.standard_normal(M)
+    w = rng.uniform(0.5, 1.5, M)
+    got = O.spread(box, X, F, w, delta)
+    ref = np.zeros(box.shape)
+    for idx in itertools.product(range(n), repeat=dim):
+        x = _node(box, idx)
+        ref[idx] = sum(F[i] * w[i] * _brute_delta(box, x, X[i], delta) for i in range(M))
+    assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
+    # interpolation from the same brute force
+    u = rng.standard_normal(box.shape)
+    gi = O.interp(box, X, u, delta)
+    for i in range(M):
+        s = sum(u[idx] * _brute_delta(box, _node(box, idx), X[i], delta) * box.h ** dim
+                for idx in itertools.product(range(n), repeat=dim))
+        assert abs(gi[i] - s) <= 1e-13 * max(1.0, abs(s))
+
+
+def test_spread_point_on_node_closed_form():
+    """A unit point source on node (3,5) spreads phi(-1),phi(0),phi(1) =
+    1/4,1/2,1/4 per axis: the centre value is (1/2)^2 / h^2."""
+    box = O.Box(2, 16, 1.0, (0.0, 0.0))
+    X = np.array([[3 * box.h, 5 * box.h]])
+    out = O.spread(box, X, np.array([1.0]), np.array([1.0]), "peskin4")
+    h2 = box.h ** 2
+    assert abs(out[5, 3] - 0.25 / h2) < 1e-12 / h2
+    assert abs(out[5, 4] - 0.125 / h2) < 1e-12 / h2
+    assert abs(out[6, 4] - 0.0625 / h2) < 1e-12 / h2
+    assert out[5, 5] == 0.0
+    assert abs(out.sum() * h2 - 1.0) < 1e-14
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_spread_interp_adjoint(dim):
+    """<S F, u>_grid h^d = sum_i w_i F_i (S* u)_i (eq. (operators), Sec. 2.1)."""
+    rng = np.random.default_rng(1)
+    n = 32 if dim == 2 else 16
+    box = O.Box(dim, n, 1.0, (0.0,) * dim)
+    M = 40
+    X = rng.uniform(0, 1, (M, dim))
+    F = rng.standard_normal(M)
+    w = rng.uniform(0.5, 2, M)
+    u = rng.standard_normal(box.shape)
+    for delta in ("peskin4", "cos4"):
+        lhs = np.sum(O.spread(box, X, F, w, delta) * u) * box.h ** dim
+        rhs = np.sum(w * F * O.interp(box, X, u, delta))
+        assert abs(lhs - rhs) <= 1e-13 * (abs(lhs) + 1)
+
+
+def test_spread_conserves_mass_and_interp_reproduces_linears():
+    """Zeroth moment: sum_j (SF)_j h^2 = sum_i F_i w_i; first moment:
+    interpolating a linear function is exact (Peskin kernel)."""
+    g = configs.c2(n=256).geom
+    box = O.Box.of(g)
+    F = np.cos(3 * g.param)
+    s = O.spread(box, g.X, F, g.weights, "peskin4")
+    assert abs(s.sum() * box.h ** 2 - np.sum(F * g.weights)) < 1e-12
+    P = configs.grid_nodes(g)
+    lin = (0.3 + 1.7 * P[:, 0] - 0.6 * P[:, 1]).reshape(box.shape)
+    ui = O.interp(box, g.X, lin, "peskin4")
+    assert np.max(np.abs(ui - (0.3 + 1.7 * g.X[:, 0] - 0.6 * g.X[:, 1]))) < 1e-13
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_spread_div_matches_fused_per_node_formula(dim):
+    """S~Q = div(S Q n) equals, node by node, sum_i Q_i w_i sum_c n_c
+    [delta_h(x_j + h e_c - X_i) - delta_h(x_j - h e_c - X_i)] / (2h), and its
+    grid sum vanishes (a discrete divergence)."""
+    rng = np.random.default_rng(2)
+    n = 8 if dim == 2 else 6
+    box = O.Box(dim, n, 1.0, (0.0,) * dim)
+    M = 4
+    X = rng.uniform(0, 1, (M, dim))
+    nr = rng.standard_normal((M, dim))
+    nr /= np.linalg.norm(nr, axis=1)[:, None]
+    w = rng.uniform(0.5, 1.5, M)
+    Q = rng.standard_normal(M)
+    got = O.spread_div(box, X, nr, w, Q, "peskin4")
+    ref = np.zeros(box.shape)
+    for idx in itertools.product(range(n), repeat=dim):
+        x = _node(box, idx)
+        acc = 0.0
+        for i in range(M):
+            for c in range(dim):
+                e = np.zeros(dim)
+                e[c] = box.h
+                acc += Q[i] * w[i] * nr[i, c] * (
+                    _brute_delta(box, x + e, X[i], "peskin4")
+                    - _brute_delta(box, x - e, X[i], "peskin4")) / (2 * box.h)
+        ref[idx] = acc
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+    assert abs(got.sum()) <= 1e-12 * np.abs(got).sum()
+
+
+# ---------------------------------------------------------------------------
+# periodic Helmholtz solve (Sec. 5.1)
+# ---------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("dim,n,kappa", [(2, 32, 1e-3), (2, 64, 1.0), (3, 16, 1e-2)])
+def test_helmholtz_solve_inverts_explicit_stencil(dim, n, kappa):
+    """The FFT solve is checked against the explicit 5/7-point stencil:
+    ||L' v - f|| / ||f|| <= 1e-13 (a wrong symbol sign or factor fails)."""
+    rng = np.random.default_rng(3)
+    box = O.Box(dim, n, 1.0, (0.0,) * dim)
+    f = rng.standard_normal(box.shape)
+    v = O.helmholtz_solve(box, kappa, f)
+    r = O.apply_Lprime(box, kappa, v) - f
+    assert np.linalg.norm(r) <= 1e-13 * np.linalg.norm(f)
+
+
+@pytest.mark.parametrize("dim,n", [(2, 8), (3, 4)])
+def test_helmholtz_solve_matches_dense_lu(dim, n):
+    rng = np.random.default_rng(4)
+    box = O.Box(dim, n, 1.0, (0.0,) * dim)
+    kappa = 0.01
+    f = rng.standard_normal(box.shape)
+    A = O.helmholtz_dense(box, kappa)
+    v_lu = np.linalg.solve(A, f.reshape(-1)).reshape(box.shape)
+    assert np.max(np.abs(O.helmholtz_solve(box, kappa, f) - v_lu)) < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# GMRES (Sec. 5.3)
+# ---------------------------------------------------------------------------
+
+
+def test_gmres_matches_lapack_on_a_random_nonsymmetric_matrix():
+    rng = np.random.default_rng(6)
+    M = 60
+    A = np.eye(M) * 3 + rng.standard_normal((M, M)) / np.sqrt(M)
+    b = rng.standard_normal(M)
+    res = O.gmres(lambda v: A @ v, b, tol=1e-13, restart=15, maxiter=500)
+    assert res.converged
+    assert np.linalg.norm(res.x - np.linalg.solve(A, b)) <= 1e-11 * np.linalg.norm(b)
+    # the residual estimate is the true residual
+    assert abs(np.linalg.norm(b - A @ res.x) / np.linalg.norm(b) - res.rel_res) < 1e-12
+
+
+@pytest.mark.parametrize("bc", [configs.DIRICHLET, configs.NEUMANN])
+def test_gmres_solve_matches_dense_lu_solution(bc):
+    """GMRES Q matches Q* = A^{-1} b from the assembled boundary matrix."""
+    g = geometry.circle(64, 0.3, kappa=1e-2, delta="cos4")
+    b = np.sin(2 * g.param) + 0.3 * np.cos(5 * g.param)
+    res = O.solve(g, bc, b, tol=1e-13)
+    q_star = O.solve_dense(g, bc, b)
+    assert np.linalg.norm(res.x - q_star) <= 1e-11 * np.linalg.norm(q_star)
+
+
+# ---------------------------------------------------------------------------
+# Method-level pins: the paper's iteration counts and closed forms
+# ---------------------------------------------------------------------------
+
+
+def _table1():
+    rows = {}
+    for line in open(os.path.join(GOLDEN, "table1_ibdl_iterations.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        v = [int(t) for t in line.split()]
+        rows[v[0]] = dict(zip((2.0, 1.5, 1.0, 0.75), v[1:]))
+    return rows
+
+
+@pytest.mark.parametrize("e", [6, 7, 8, 9])
+@pytest.mark.parametrize("c", [2.0, 1.5, 1.0, 0.75])
+def test_table1_iteration_counts(e, c):
+    """IBDL GMRES counts at tol 1e-8 are within +-1 of Table 1."""
+    expect = _table1()[e][c]
+    p = configs.table1(2 ** e, c)
+    res = O.solve(p.geom, p.bc, p.bdata, tol=1e-8)
+    assert res.converged
+    assert abs(res.iters - expect) <= 1, (e, c, res.iters, expect)
+
+
+def test_tol_1e10_needs_about_five_iterations():
+    """Sec. 6.1: tightening to 1e-10 costs about one iteration (5)."""
+    for c in (2.0, 0.75):
+        p = configs.table1(256, c)
+        res = O.solve(p.geom, p.bc, p.bdata, tol=1e-10)
+        assert 4 <= res.iters <= 6
+
+
+def _table3():
+    rows = []
+    for line in open(os.path.join(GOLDEN, "table3_ibdl_iterations.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        v = [int(t) for t in line.split()]
+        for c, (m, it) in zip((2.0, 1.5, 1.0), zip(v[1::2], v[2::2])):
+            if m > 0:
+                rows.append((v[0], c, m, it))
+    return rows
+
+
+@pytest.mark.parametrize("e,c,m,it", [r for r in _table3() if r[0] == 5])
+def test_table3_iteration_counts_3d(e, c, m, it):
+    """3D sphere (Table 3) with the paper's point counts on a Fibonacci
+    lattice standing in for the maximum-determinant sets: within +-2."""
+    g = geometry.sphere(2 ** e, 0.25, m=m, center=(0, 0, 0), origin=(-0.5,) * 3,
+                        kappa=1.0)
+    # boundary values of u = r^2 cos(theta) sin(2 phi) (the paper's exact
+    # solution of Sec. 6.7, used only as boundary data here)
+    x, y, z = (g.X - np.array(g.center)).T
+    # r^2 cos(theta) sin(2 phi) = r z 2xy / (x^2 + y^2), r = 0.25
+    ub = 0.25 * z * 2 * x * y / np.maximum(x * x + y * y, 1e-300)
+    res = O.solve(g, configs.DIRICHLET, ub, tol=1e-8)
+    assert res.converged and abs(res.iters - it) <= 2, (res.iters, it)
+
+
+def _interior_errors(p, res, margin_h):
+    g = p.geom
+    u = res.op.evaluate(res.x)
+    P = configs.grid_nodes(g)
+    R = g.extra["r"]
+    mask = configs.interior_mask_circle(g, R, margin_h * g.h)
+    e = np.abs(u.reshape(-1)[mask] - p.exact(P)[mask])
+    # discrete norms of Sec. 5.1 rescaled by |Omega| ~ (number of nodes) h^2
+    return np.mean(e), np.sqrt(np.mean(e * e))
+
+
+def _interior_l1(p, res, margin_h):
+    return _interior_errors(p, res, margin_h)[0]
+
+
+def test_first_order_convergence_in_l1_and_half_order_in_l2():
+    """Sec. 6.1: without near-boundary interpolation the error over Omega is
+    O(dx) in L1 and O(sqrt(dx)) in L2 (k=1 circle, U_b = sin 2 theta)."""
+    l1, l2 = [], []
+    for n in (128, 256, 512):
+        p = configs.table1(n, 1.0)
+        res = O.solve(p.geom, p.bc, p.bdata, tol=1e-10)
+        a, b = _interior_errors(p, res, 0)
+        l1.append(a)
+        l2.append(b)
+    r1 = [math.log2(l1[i] / l1[i + 1]) for i in range(2)]
+    r2 = [math.log2(l2[i] / l2[i + 1]) for i in range(2)]
+    assert all(0.8 < r < 1.3 for r in r1), (l1, r1)
+    assert all(0.3 < r < 0.8 for r in r2), (l2, r2)
+
+
+def test_c1_bessel_solution():
+    """Config C1 (kappa=1e-2, k=10): the field matches I_2(10 rho)sin(2
+    theta)/I_2(3) away from the boundary at the first-order level."""
+    p = configs.c1()
+    res = O.solve(p.geom, p.bc, p.bdata, tol=1e-10)
+    assert res.converged and res.iters <= 8
+    assert _interior_l1(p, res, 6) < 5e-3
+
+
+def test_neumann_boundary_values_converge():
+    """Neumann system (Sec. 4.4): the unknown U is the trace of u; for
+    u = exp(k d.(x-c)) it converges to the exact trace at first order."""
+    errs = []
+    for n in (64, 128, 256):
+        g = geometry.circle(n, 0.25, spacing=0.75, center=(0.0, 0.0), origin=(-0.5, -0.5),
+                            kappa=1.0)
+        p = configs.exp_problem(g, configs.NEUMANN, (0.6, 0.8))
+        res = O.solve(g, p.bc, p.bdata, tol=1e-10)
+        assert res.iters <= 8
+        exact = p.exact(g.X)
+        errs.append(np.max(np.abs(res.x - exact)))
+    assert errs[0] < 0.15 and errs[1] < errs[0] / 1.6 and errs[2] < errs[1] / 1.6, errs
+
+
+def test_dirichlet_constant_data_closed_form_density():
+    """Double-layer sign and jump (Sec. 4.1, Q = -gamma): in the near-Poisson
+    limit a constant density Q gives u = Q (chi_Omega - |Omega|/|C|) on the
+    periodic box (zero-mean solve), whose trace is Q (1/2 - |Omega|/|C|);
+    with U_b = 1 the system S*u + Q/2 = 1 gives Q = 1 / (1 - |Omega|/|C|).
+    The discrete Q converges to it at first order."""
+    exact = 1.0 / (1.0 - math.pi * 0.3 ** 2)
+    errs = []
+    for n in (64, 128, 256):
+        g = geometry.circle(n, 0.3, kappa=1e4)
+        res = O.solve(g, configs.DIRICHLET, np.ones(g.m), tol=1e-10)
+        errs.append(abs(np.mean(res.x) - exact))
+    assert errs[0] < 0.03 and errs[1] < errs[0] / 1.8 and errs[2] < errs[1] / 1.8, errs
+
+
+def test_indicator_thresholds_to_the_disk():
+    """App. D: Q = 1 gives a regularised indicator; threshold 1/2 flags the
+    nodes inside the circle (checked away from Gamma)."""
+    g = geometry.circle(128, 0.3, kappa=1.0)
+    chi = O.indicator(g).reshape(-1)
+    P = configs.grid_nodes(g)
+    rho = np.linalg.norm(P - np.array(g.center)[None, :], axis=1)
+    far = np.abs(rho - 0.3) > 3 * g.h
+    assert np.all((chi[far] > 0.5) == (rho[far] < 0.3))
