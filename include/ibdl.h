@@ -1,0 +1,223 @@
+/*
+ * ibdl.h -- C ABI of the GB300 (sm_103a) Immersed Boundary Double Layer
+ * (IBDL) library.
+ *
+ * The library solves the Helmholtz boundary value problems of Leathers & Guy,
+ * "Immersed Boundary Double Layer method" (arXiv:2203.12126):
+ *
+ *   Dirichlet (Sec. 2, eq. (pde)):           Delta u - k^2 u = g in Omega,
+ *                                             u = U_b on Gamma,
+ *   Neumann   (Sec. 4.4, eq. (pde neumann)):  Delta u - k^2 u = g in Omega,
+ *                                             du/dn = V_b on Gamma,
+ *
+ * by embedding Omega in a periodic box C = [origin, origin + L)^d (d = 2, 3)
+ * with n grid nodes per axis at origin + j h, h = L / n (Sec. 5.1), and
+ * solving the well-conditioned second-kind boundary system of Sec. 5.3 /
+ * Sec. 4.4 with unpreconditioned GMRES.  This library writes the operator as
+ * L' = I - kappa Delta_h with kappa = 1 / k^2, so the paper's
+ * L = Delta_h - k^2 = -(1/kappa) L'.  The boundary operators are then
+ *
+ *   A_D Q = Q/2 + kappa S* L'^{-1} S~ Q      (eq. (ibdl schur again))
+ *   A_N U = kappa S* L'^{-1} S~ U - U/2      (eq. (Neumann saddle point))
+ *
+ * where S is the spread (Sec. 5.2, eq. (spread operator again2)), S* the
+ * interpolation (eq. (interpolation again)), S~ Q = div_h(S (Q n)) (eq.
+ * (Stilde)) with centred differences, Delta_h the 5-point (2D) or 7-point
+ * (3D) Laplacian and delta_h the Peskin 4-point (eq. (delta eqn 2)) or the
+ * cosine 4-point kernel.
+ *
+ * Conventions for every entry point:
+ *   - Pointers to per-point arrays (length m) and grid arrays (n^d values,
+ *     x fastest, then y, then z) may be DEVICE or HOST memory; the library
+ *     tells them apart with cudaPointerGetAttributes.  Host arrays are
+ *     copied to/from library-owned device staging buffers on the call's
+ *     stream (pinned host memory makes those copies asynchronous).
+ *   - The caller owns every pointer it passes; it must stay valid until the
+ *     stream has finished the call.  The geometry handle owns its device
+ *     workspaces until ibdl_destroy_geometry.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls enqueue work asynchronously unless stated otherwise.
+ *   - A handle is not thread-safe: one host thread (and one stream at a
+ *     time) per handle.  Distinct handles are independent.
+ *   - Errors: every function returns an ibdl_status; on failure nothing is
+ *     written to the outputs unless stated otherwise, and
+ *     ibdl_last_error_message() returns a description (per host thread).
+ */
+#ifndef IBDL_H_
+#define IBDL_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IBDL_VERSION_MAJOR 0
+#define IBDL_VERSION_MINOR 1
+
+typedef enum {
+  IBDL_OK = 0,
+  IBDL_ERR_INVALID_ARG = 1,   /* bad size, pointer, kappa, bc, ... */
+  IBDL_ERR_OOM = 2,           /* device allocation failed */
+  IBDL_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+  IBDL_ERR_NOT_CONVERGED = 4, /* GMRES hit max_iters; best iterate returned */
+  IBDL_ERR_BREAKDOWN = 5,     /* Arnoldi produced a zero or non-finite norm */
+  IBDL_ERR_NONFINITE = 6,     /* NaN/Inf in inputs or in the residual */
+  IBDL_ERR_TIMEOUT = 7,       /* a bounded device wait gave up */
+  IBDL_ERR_UNSUPPORTED = 8    /* valid request this build does not support */
+} ibdl_status;
+
+typedef enum { IBDL_DIRICHLET = 0, IBDL_NEUMANN = 1 } ibdl_bc;
+
+/* Peskin's 4-point kernel, Sec. 5.2 eq. (delta eqn 2); or the cosine
+ * 4-point kernel phi(r) = (1 + cos(pi r / 2)) / 4 on |r| < 2. */
+typedef enum { IBDL_DELTA_PESKIN4 = 0, IBDL_DELTA_COS4 = 1 } ibdl_delta;
+
+/* IBDL_FP64: every step in float64.
+ * IBDL_FP32_REFINED: spread, FFT solve and interpolation in float32 inside
+ * the GMRES iterations; Arnoldi, Givens and an outer residual-refinement loop
+ * (residual b - A x with the float64 operator) in float64. */
+typedef enum { IBDL_FP64 = 0, IBDL_FP32_REFINED = 1 } ibdl_precision;
+
+typedef struct ibdl_geometry_s* ibdl_geometry; /* opaque, library-owned */
+
+/* Geometry of one IBDL problem (Sec. 5.1-5.2).  Copied at creation. */
+typedef struct {
+  int32_t dim;          /* 2 or 3 */
+  int32_t n;            /* grid nodes per axis: a power of two, 16..4096 in 2D,
+                           16..512 in 3D */
+  double box_len;       /* L > 0; h = L / n */
+  double origin[3];     /* lower box corner; nodes at origin + j h */
+  int64_t m;            /* number of boundary points, >= 1 */
+  const double* x;      /* point coordinates X_i, length m each; z only for */
+  const double* y;      /* dim == 3 (may be NULL in 2D)                      */
+  const double* z;
+  const double* nx;     /* unit normals n_i pointing OUT of Omega (Sec. 4.1) */
+  const double* ny;
+  const double* nz;
+  const double* w;      /* quadrature weights Delta s_i (arclength, Sec. 5.2)
+                           or dA_i (area, Sec. 6.7) */
+  double kappa;         /* > 0, finite: L' = I - kappa Delta_h, k^2 = 1/kappa */
+  int32_t delta;        /* ibdl_delta */
+  int32_t bc;           /* ibdl_bc: selects A_D or A_N */
+  int32_t precision;    /* ibdl_precision */
+  int32_t reserved;
+} ibdl_geometry_desc;
+
+typedef struct {
+  double tol;           /* stop when ||b - A x||_2 / ||b||_2 <= tol (the
+                           relative residual of Sec. 5.3); default 1e-8 */
+  int32_t restart;      /* GMRES(restart), 1..64; default 30 */
+  int32_t max_iters;    /* total inner iterations; default 500 */
+  int32_t max_refine;   /* outer refinement steps (FP32_REFINED); default 8 */
+  double inner_tol;     /* FP32_REFINED: relative tolerance of each inner
+                           solve; default 1e-5 */
+  const double* x0;     /* optional initial guess (length m), or NULL */
+} ibdl_solve_opts;
+
+typedef struct {
+  int32_t iters;             /* total GMRES inner iterations (all cycles) */
+  int32_t refine_steps;      /* outer refinement steps taken (0 for FP64) */
+  int32_t matvecs;           /* operator applications, all precisions */
+  int32_t n_history;         /* entries used in residual_history */
+  double rel_residual;       /* final ||b - A x|| / ||b|| (float64 operator) */
+  double residual_history[256]; /* relative residual after each iteration */
+} ibdl_solve_info;
+
+/* Sets every field of *opts to its default. */
+void ibdl_solve_opts_default(ibdl_solve_opts* opts);
+
+/* Create a geometry handle (Sec. 5.1-5.2 inputs; the paper's "minimal
+ * geometric information", Sec. 7): validates the description, copies points,
+ * normals and weights, bins the points by grid tile, precomputes the delta
+ * weights, the FFT twiddles and the Helmholtz symbol and allocates all
+ * workspaces (grid, spectrum, Krylov basis).  Synchronises `stream` before
+ * returning.  Errors: IBDL_ERR_INVALID_ARG (n not a power of two or out of
+ * range, m < 1, kappa <= 0 or non-finite, unknown enum, NULL pointer),
+ * IBDL_ERR_OOM, IBDL_ERR_CUDA.  *out is set only on success. */
+ibdl_status ibdl_create_geometry(const ibdl_geometry_desc* desc, void* stream,
+                                 ibdl_geometry* out);
+
+/* Release a handle and its device memory (NULL is ignored).  Synchronises
+ * the device first. */
+void ibdl_destroy_geometry(ibdl_geometry g);
+
+/* y = A q, one application of the boundary operator (A_D or A_N by the
+ * geometry's bc), the GMRES matrix-vector product of Sec. 5.3.  q and y have
+ * length m.  Computed in float64 for IBDL_FP64 geometries and in float32
+ * (spread, FFT solve, interpolation; the +-q/2 jump in float64) for
+ * IBDL_FP32_REFINED geometries.  q and y may alias. */
+ibdl_status ibdl_apply(ibdl_geometry g, const double* q, double* y, void* stream);
+
+/* Same as ibdl_apply with the precision chosen per call:
+ * ibdl_precision value 0 = float64 operator, 1 = float32 operator. */
+ibdl_status ibdl_apply_precision(ibdl_geometry g, const double* q, double* y,
+                                 int32_t precision, void* stream);
+
+/* Solve the boundary system for the density (Sec. 4.1 step 1):
+ *   Dirichlet: A_D Q = U_b - S* L^{-1} g~ = U_b + kappa S* L'^{-1} g~
+ *   Neumann:   A_N U = S* L^{-1} S V_b - S* L^{-1} g~
+ *                    = kappa S* L'^{-1} (g~ - S V_b)
+ * bdata: U_b (Dirichlet) or V_b (Neumann), length m.  g_grid: optional
+ * forcing g~ on the whole periodic grid (n^d values, paper convention
+ * Delta u - k^2 u = g), or NULL for g = 0.  q_out: Q (Dirichlet) or the
+ * unknown boundary values U (Neumann), length m.  opts/info may be NULL.
+ * Synchronises `stream` (the convergence test reads residuals on the host).
+ * Returns IBDL_ERR_NOT_CONVERGED with the last iterate in q_out and info
+ * filled when max_iters is reached; IBDL_ERR_NONFINITE / IBDL_ERR_BREAKDOWN
+ * likewise leave the last finite iterate. */
+ibdl_status ibdl_solve(ibdl_geometry g, const double* bdata, const double* g_grid,
+                       double* q_out, const ibdl_solve_opts* opts,
+                       ibdl_solve_info* info, void* stream);
+
+/* The grid solution (Sec. 4.1 step 2, eq. (ibdl 1 again); Neumann eq.
+ * (ib neumann 1)):
+ *   Dirichlet: u = kappa L'^{-1} (S~ q - g~)
+ *   Neumann:   u = kappa L'^{-1} (S~ q + S vb - g~)
+ * q: density from ibdl_solve (length m); vb: V_b (Neumann only, else NULL);
+ * g_grid: forcing or NULL.  u_out: n^d values, x fastest.  Always float64
+ * (also for FP32_REFINED geometries). */
+ibdl_status ibdl_evaluate(ibdl_geometry g, const double* q, const double* vb,
+                          const double* g_grid, double* u_out, void* stream);
+
+/* Component operators, exposed for testing and for callers that compose
+ * their own solvers.  All float64 unless `precision` = 1.
+ *   ibdl_spread_div: f = S~ q on the grid (Sec. 5.2, eq. (Stilde)).
+ *   ibdl_spread:     f = S v on the grid (eq. (spread operator again2)).
+ *   ibdl_helmholtz:  v = kappa L'^{-1} f (periodic FFT solve, Sec. 5.1);
+ *                    f and v are n^d grids and may alias.
+ *   ibdl_interp:     y = S* u at the points (eq. (interpolation again)). */
+ibdl_status ibdl_spread_div(ibdl_geometry g, const double* q, double* f_out,
+                            int32_t precision, void* stream);
+ibdl_status ibdl_spread(ibdl_geometry g, const double* v, double* f_out,
+                        int32_t precision, void* stream);
+ibdl_status ibdl_helmholtz(ibdl_geometry g, const double* f, double* v_out,
+                           int32_t precision, void* stream);
+ibdl_status ibdl_interp(ibdl_geometry g, const double* u, double* y_out,
+                        int32_t precision, void* stream);
+
+/* Read-only facts about a handle. */
+typedef struct {
+  int32_t dim, n;
+  int64_t m;
+  double h, kappa;
+  int32_t bc, delta, precision;
+  int64_t device_bytes;      /* device memory the handle owns */
+  int32_t fft_passes;        /* kernels per Helmholtz solve */
+  int32_t reserved;
+} ibdl_geometry_info;
+ibdl_status ibdl_get_geometry_info(ibdl_geometry g, ibdl_geometry_info* info);
+
+/* Number of this library's kernels launched so far in this process
+ * (all handles, all streams). */
+int64_t ibdl_kernel_launch_count(void);
+
+const char* ibdl_status_string(ibdl_status s);
+const char* ibdl_last_error_message(void);
+int32_t ibdl_version(void); /* 100 * MAJOR + MINOR */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IBDL_H_ */

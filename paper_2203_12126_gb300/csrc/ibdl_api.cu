@@ -1,0 +1,850 @@
+// C ABI of libibdl and the host-side orchestration of the IBDL hot path.
+//
+// Operators (Leathers & Guy, arXiv:2203.12126, with L' = I - kappa Delta_h):
+//   Dirichlet matvec  A_D q = q/2 + kappa S* L'^{-1} S~ q      (Sec. 5.3)
+//   Neumann matvec    A_N u = kappa S* L'^{-1} S~ u - u/2      (Sec. 4.4)
+//   Dirichlet rhs     b = U_b + kappa S* L'^{-1} g~
+//   Neumann rhs       b = kappa S* L'^{-1} (g~ - S V_b)
+//   field             u = kappa L'^{-1} (S~ q [+ S V_b] - g~)  (Sec. 4.1 step 2)
+// One matvec = rows_fwd (spread-divergence fused with the x FFT), the y (and
+// z) pencil passes with the symbol, rows_inv (x inverse FFT) and interp
+// (gather + jump term): 4 kernels in 2D, 6 in 3D.
+#include <math.h>
+#include <string.h>
+
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "ibdl_internal.cuh"
+
+namespace ibdl {
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+cudaError_t check_launch() { return cudaGetLastError(); }
+
+static thread_local std::string g_err;
+
+static ibdl_status fail(ibdl_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+static ibdl_status cuda_fail(cudaError_t e, const char* where) {
+  g_err = std::string(where) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? IBDL_ERR_OOM : IBDL_ERR_CUDA;
+}
+
+#define IBDL_CU(expr)                                  \
+  do {                                                 \
+    cudaError_t e_ = (expr);                           \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #expr); \
+  } while (0)
+
+#define IBDL_TRY(expr)                  \
+  do {                                  \
+    ibdl_status s_ = (expr);            \
+    if (s_ != IBDL_OK) return s_;       \
+  } while (0)
+
+static bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace ibdl
+
+using namespace ibdl;
+
+struct ibdl_geometry_s {
+  GridDesc grid;
+  int bc = 0, precision = 0, m = 0;
+  Bins bins;
+  PointData pd;
+  SpectralWs<double> ws64;
+  SpectralWs<float> ws32;
+  bool have32 = false;
+  KrylovWs kry;
+  double *vb = nullptr, *vx = nullptr, *vr = nullptr, *vt = nullptr, *vd = nullptr;
+  double *stage_a = nullptr, *stage_b = nullptr;
+  double* grid_stage = nullptr;   // n^d doubles, allocated on first host grid
+  double* host_scal = nullptr;    // pinned
+  int* d_flag = nullptr;
+  int64_t bytes = 0;
+  int64_t ncells = 0;
+  std::vector<void*> dev_allocs;
+
+  template <typename P>
+  ibdl_status alloc(P** out, size_t count) {
+    void* p = nullptr;
+    const size_t nbytes = count * sizeof(P);
+    cudaError_t e = cudaMalloc(&p, nbytes > 0 ? nbytes : 16);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    dev_allocs.push_back(p);
+    bytes += (int64_t)nbytes;
+    *out = static_cast<P*>(p);
+    return IBDL_OK;
+  }
+  ~ibdl_geometry_s() {
+    for (void* p : dev_allocs) cudaFree(p);
+    if (bins.pts) cudaFree((void*)bins.pts);
+    if (host_scal) cudaFreeHost(host_scal);
+  }
+};
+
+namespace {
+
+template <typename T>
+ibdl_status alloc_spectral(ibdl_geometry_s* g, SpectralWs<T>& ws, cudaStream_t st) {
+  const int n = g->grid.n;
+  const int64_t spec_count = (int64_t)(n / 2 + 1) * (g->ncells / n);
+  typename Cx<T>::type* spec;
+  T* grid;
+  typename Cx<T>::type* tw;
+  T* s2;
+  IBDL_TRY(g->alloc(&spec, (size_t)spec_count));
+  IBDL_TRY(g->alloc(&grid, (size_t)g->ncells));
+  IBDL_TRY(g->alloc(&tw, (size_t)n));
+  IBDL_TRY(g->alloc(&s2, (size_t)n));
+  std::vector<typename Cx<T>::type> htw(n);
+  std::vector<T> hs2(n);
+  for (int j = 0; j < n; ++j) {
+    // exp(-2 pi i j / n) and sin^2(pi j / n), from long double arithmetic
+    const long double a = 2.0L * 3.14159265358979323846264338327950288L * j / n;
+    htw[j].x = (T)cosl(a);
+    htw[j].y = (T)-sinl(a);
+    const long double s = sinl(0.5L * a);
+    hs2[j] = (T)(s * s);
+  }
+  IBDL_CU(cudaMemcpyAsync(tw, htw.data(), sizeof(htw[0]) * n, cudaMemcpyHostToDevice, st));
+  IBDL_CU(cudaMemcpyAsync(s2, hs2.data(), sizeof(T) * n, cudaMemcpyHostToDevice, st));
+  IBDL_CU(cudaStreamSynchronize(st));
+  ws.spec = spec;
+  ws.grid = grid;
+  ws.tw = tw;
+  ws.s2 = s2;
+  return IBDL_OK;
+}
+
+ibdl_status ensure32(ibdl_geometry_s* g, cudaStream_t st) {
+  if (g->have32) return IBDL_OK;
+  IBDL_TRY(alloc_spectral<float>(g, g->ws32, st));
+  g->have32 = true;
+  return IBDL_OK;
+}
+
+// Device view of a caller array of `count` doubles: the pointer itself when
+// it is device memory, else a copy in `stage`.
+ibdl_status dev_in(const double* p, size_t count, double* stage, const double** out,
+                   cudaStream_t st) {
+  if (is_device_ptr(p)) {
+    *out = p;
+    return IBDL_OK;
+  }
+  IBDL_CU(cudaMemcpyAsync(stage, p, count * sizeof(double), cudaMemcpyHostToDevice, st));
+  *out = stage;
+  return IBDL_OK;
+}
+
+ibdl_status grid_in(ibdl_geometry_s* g, const double* p, const double** out, cudaStream_t st) {
+  if (!p) {
+    *out = nullptr;
+    return IBDL_OK;
+  }
+  if (is_device_ptr(p)) {
+    *out = p;
+    return IBDL_OK;
+  }
+  if (!g->grid_stage) IBDL_TRY(g->alloc(&g->grid_stage, (size_t)g->ncells));
+  IBDL_CU(cudaMemcpyAsync(g->grid_stage, p, g->ncells * sizeof(double),
+                          cudaMemcpyHostToDevice, st));
+  *out = g->grid_stage;
+  return IBDL_OK;
+}
+
+template <typename T>
+SpectralWs<T>& wsof(ibdl_geometry_s* g);
+template <>
+SpectralWs<double>& wsof<double>(ibdl_geometry_s* g) {
+  return g->ws64;
+}
+template <>
+SpectralWs<float>& wsof<float>(ibdl_geometry_s* g) {
+  return g->ws32;
+}
+
+// grid = kappa L'^{-1} (sources), T-precision spectral passes, output OutT grid.
+template <typename T, typename OutT>
+ibdl_status field_solve(ibdl_geometry_s* g, const SpreadSrc& src, OutT* out, cudaStream_t st) {
+  SpectralWs<T>& ws = wsof<T>(g);
+  IBDL_CU(launch_rows_fwd<T>(g->grid, g->pd, g->bins, src, ws, nullptr, st));
+  IBDL_CU(launch_spectral_solve<T>(g->grid, ws, st));
+  IBDL_CU((launch_rows_inv<T, OutT>(g->grid, g->bins, ws, out, st)));
+  return IBDL_OK;
+}
+
+// y = A q with the T-precision spectral path.  q, y device, may alias.
+template <typename T>
+ibdl_status matvec(ibdl_geometry_s* g, const double* q, double* y, cudaStream_t st) {
+  SpreadSrc src;
+  src.q_div = q;
+  src.coef_div = 1.0;
+  SpectralWs<T>& ws = wsof<T>(g);
+  IBDL_TRY((field_solve<T, T>(g, src, ws.grid, st)));
+  const double jump = g->bc == IBDL_DIRICHLET ? 0.5 : -0.5;
+  IBDL_CU(launch_interp<T>(g->grid, g->pd, ws.grid, q, jump, y, st));
+  return IBDL_OK;
+}
+
+ibdl_status matvec_prec(ibdl_geometry_s* g, int prec, const double* q, double* y,
+                        cudaStream_t st) {
+  if (prec == IBDL_FP32_REFINED) {
+    IBDL_TRY(ensure32(g, st));
+    return matvec<float>(g, q, y, st);
+  }
+  return matvec<double>(g, q, y, st);
+}
+
+// b = right-hand side of the boundary system (float64).
+ibdl_status build_rhs(ibdl_geometry_s* g, const double* bdata, const double* ggrid, double* b,
+                      cudaStream_t st) {
+  if (g->bc == IBDL_DIRICHLET) {
+    if (!ggrid) {
+      IBDL_CU(cudaMemcpyAsync(b, bdata, sizeof(double) * g->m, cudaMemcpyDeviceToDevice, st));
+      return IBDL_OK;
+    }
+    SpreadSrc src;
+    src.f_grid = ggrid;
+    src.coef_grid = 1.0;
+    IBDL_TRY((field_solve<double, double>(g, src, g->ws64.grid, st)));
+    IBDL_CU(launch_interp<double>(g->grid, g->pd, g->ws64.grid, bdata, 1.0, b, st));
+    return IBDL_OK;
+  }
+  SpreadSrc src;
+  src.v_plain = bdata;
+  src.coef_plain = -1.0;
+  if (ggrid) {
+    src.f_grid = ggrid;
+    src.coef_grid = 1.0;
+  }
+  IBDL_TRY((field_solve<double, double>(g, src, g->ws64.grid, st)));
+  IBDL_CU(launch_interp<double>(g->grid, g->pd, g->ws64.grid, nullptr, 0.0, b, st));
+  return IBDL_OK;
+}
+
+double read_scalar(ibdl_geometry_s* g, const double* dptr, int slot, cudaStream_t st,
+                   cudaError_t* err) {
+  *err = cudaMemcpyAsync(g->host_scal + slot, dptr, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (*err == cudaSuccess) *err = cudaStreamSynchronize(st);
+  return g->host_scal[slot];
+}
+
+struct GmresRun {
+  int iters = 0;
+  int matvecs = 0;
+  double rel = 0;   // final relative residual (true, if checked)
+  std::vector<double> hist;
+};
+
+// Restarted GMRES on A_prec x = b (x in/out, device).  If true_check, a
+// converged estimate is confirmed with the true residual ||b - A x|| (the
+// same precision), as MATLAB's gmres does; otherwise the estimate is final.
+ibdl_status gmres(ibdl_geometry_s* g, int prec, const double* b, double* x, bool x_is_zero,
+                  double bnorm, double tol, int restart, int maxit, bool true_check,
+                  GmresRun* run, cudaStream_t st) {
+  KrylovWs& k = g->kry;
+  cudaError_t ce;
+  bool zero = x_is_zero;
+  bool est_converged = false;
+  for (;;) {
+    if (zero) {
+      IBDL_CU(cudaMemcpyAsync(g->vr, b, sizeof(double) * g->m, cudaMemcpyDeviceToDevice, st));
+    } else {
+      IBDL_TRY(matvec_prec(g, prec, x, g->vt, st));
+      run->matvecs++;
+      IBDL_CU(launch_axpby(g->m, 1.0, b, -1.0, g->vt, g->vr, st));
+    }
+    if (est_converged && !true_check) break;
+    IBDL_CU(krylov_start(k, g->vr, nullptr, st));
+    const double beta = read_scalar(g, k.scal + 2, 0, st, &ce);
+    if (ce) return cuda_fail(ce, "read residual");
+    run->rel = beta / bnorm;
+    if (!isfinite(beta)) return fail(IBDL_ERR_NONFINITE, "non-finite residual");
+    if (run->rel <= tol) return IBDL_OK;
+    if (run->iters >= maxit) return fail(IBDL_ERR_NOT_CONVERGED, "GMRES reached max_iters");
+    int kdim = 0;
+    bool breakdown = false;
+    est_converged = false;
+    for (int j = 0; j < restart; ++j) {
+      IBDL_TRY(matvec_prec(g, prec, k.V + (size_t)j * k.ld, k.V + (size_t)(j + 1) * k.ld, st));
+      run->matvecs++;
+      IBDL_CU(krylov_arnoldi(k, j, bnorm, st));
+      IBDL_CU(cudaMemcpyAsync(g->host_scal, k.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                              st));
+      IBDL_CU(cudaStreamSynchronize(st));
+      const double est = g->host_scal[0], hnext = g->host_scal[1];
+      run->iters++;
+      run->hist.push_back(est);
+      kdim = j + 1;
+      if (!isfinite(est) || !isfinite(hnext))
+        return fail(IBDL_ERR_NONFINITE, "non-finite value in the Arnoldi process");
+      if (est <= tol) {
+        est_converged = true;
+        break;
+      }
+      if (hnext == 0.0) {
+        breakdown = true;
+        break;
+      }
+      if (run->iters >= maxit) break;
+    }
+    IBDL_CU(krylov_finish(k, kdim, x, st));
+    zero = false;
+    if (breakdown) est_converged = true;
+    if (est_converged && !true_check) {
+      run->rel = g->host_scal[0];
+      return IBDL_OK;
+    }
+  }
+  return IBDL_OK;
+}
+
+ibdl_status vec_norm(ibdl_geometry_s* g, const double* v, double* out, cudaStream_t st) {
+  IBDL_CU(krylov_dot_norm(g->kry, v, g->kry.scal + 4, st));
+  cudaError_t ce;
+  *out = read_scalar(g, g->kry.scal + 4, 4, st, &ce);
+  if (ce) return cuda_fail(ce, "read norm");
+  return IBDL_OK;
+}
+
+ibdl_status check_handle(ibdl_geometry g) {
+  if (!g) return fail(IBDL_ERR_INVALID_ARG, "NULL geometry handle");
+  return IBDL_OK;
+}
+
+}  // namespace
+
+// =============================================================================
+// C ABI
+// =============================================================================
+
+extern "C" {
+
+void ibdl_solve_opts_default(ibdl_solve_opts* o) {
+  if (!o) return;
+  o->tol = 1e-8;
+  o->restart = 30;
+  o->max_iters = 500;
+  o->max_refine = 8;
+  o->inner_tol = 1e-5;
+  o->x0 = nullptr;
+}
+
+ibdl_status ibdl_create_geometry(const ibdl_geometry_desc* d, void* stream, ibdl_geometry* out) {
+  g_err.clear();
+  if (!d || !out) return fail(IBDL_ERR_INVALID_ARG, "NULL desc or out");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int dim = d->dim, n = d->n;
+  if (dim != 2 && dim != 3) return fail(IBDL_ERR_INVALID_ARG, "dim must be 2 or 3");
+  if (n < 16 || (n & (n - 1)) != 0 || n > (dim == 2 ? 4096 : 512))
+    return fail(IBDL_ERR_INVALID_ARG, "n must be a power of two in [16, 4096] (2D) / [16, 512] (3D)");
+  if (d->m < 1 || d->m > (1 << 26)) return fail(IBDL_ERR_INVALID_ARG, "m out of range");
+  if (!(d->box_len > 0) || !isfinite(d->box_len))
+    return fail(IBDL_ERR_INVALID_ARG, "box_len must be positive and finite");
+  if (!(d->kappa > 0) || !isfinite(d->kappa))
+    return fail(IBDL_ERR_INVALID_ARG, "kappa must be positive and finite");
+  if (d->delta != IBDL_DELTA_PESKIN4 && d->delta != IBDL_DELTA_COS4)
+    return fail(IBDL_ERR_INVALID_ARG, "unknown delta");
+  if (d->bc != IBDL_DIRICHLET && d->bc != IBDL_NEUMANN)
+    return fail(IBDL_ERR_INVALID_ARG, "unknown bc");
+  if (d->precision != IBDL_FP64 && d->precision != IBDL_FP32_REFINED)
+    return fail(IBDL_ERR_INVALID_ARG, "unknown precision");
+  for (int c = 0; c < 3; ++c)
+    if (!isfinite(d->origin[c])) return fail(IBDL_ERR_INVALID_ARG, "origin not finite");
+  if (!d->x || !d->y || !d->nx || !d->ny || !d->w || (dim == 3 && (!d->z || !d->nz)))
+    return fail(IBDL_ERR_INVALID_ARG, "NULL point, normal or weight array");
+
+  ibdl_geometry_s* g = new ibdl_geometry_s();
+  auto cleanup = [&](ibdl_status s) {
+    delete g;
+    return s;
+  };
+  const int m = (int)d->m;
+  g->m = m;
+  g->bc = d->bc;
+  g->precision = d->precision;
+  GridDesc& gd = g->grid;
+  gd.dim = dim;
+  gd.n = n;
+  gd.log2n = 0;
+  while ((1 << gd.log2n) < n) gd.log2n++;
+  gd.h = d->box_len / n;
+  gd.kappa = d->kappa;
+  gd.delta = d->delta;
+  for (int c = 0; c < 3; ++c) gd.origin[c] = c < dim ? d->origin[c] : 0.0;
+  g->ncells = (int64_t)n * n * (dim == 3 ? n : 1);
+
+  ibdl_status s;
+  double* pts;
+  if ((s = g->alloc(&pts, (size_t)7 * m))) return cleanup(s);
+  const double* src_arr[7] = {d->x, d->y, dim == 3 ? d->z : nullptr, d->nx, d->ny,
+                              dim == 3 ? d->nz : nullptr, d->w};
+  for (int a = 0; a < 7; ++a) {
+    if (!src_arr[a]) {
+      cudaMemsetAsync(pts + (size_t)a * m, 0, sizeof(double) * m, st);
+      continue;
+    }
+    cudaError_t e = cudaMemcpyAsync(pts + (size_t)a * m, src_arr[a], sizeof(double) * m,
+                                    cudaMemcpyDefault, st);
+    if (e) return cleanup(cuda_fail(e, "copy geometry"));
+  }
+  // weights scaled by h^-d on the host side of the device copy
+  {
+    std::vector<double> hw(m);
+    cudaError_t e = cudaMemcpyAsync(hw.data(), pts + (size_t)6 * m, sizeof(double) * m,
+                                    cudaMemcpyDeviceToHost, st);
+    if (!e) e = cudaStreamSynchronize(st);
+    if (e) return cleanup(cuda_fail(e, "read weights"));
+    std::vector<double> hx(m);
+    const double hd = dim == 3 ? gd.h * gd.h * gd.h : gd.h * gd.h;
+    for (int i = 0; i < m; ++i) {
+      if (!isfinite(hw[i])) return cleanup(fail(IBDL_ERR_INVALID_ARG, "non-finite weight"));
+      hw[i] /= hd;
+    }
+    for (int c = 0; c < dim; ++c) {
+      e = cudaMemcpyAsync(hx.data(), pts + (size_t)c * m, sizeof(double) * m,
+                          cudaMemcpyDeviceToHost, st);
+      if (!e) e = cudaStreamSynchronize(st);
+      if (e) return cleanup(cuda_fail(e, "read points"));
+      for (int i = 0; i < m; ++i)
+        if (!isfinite(hx[i])) return cleanup(fail(IBDL_ERR_INVALID_ARG, "non-finite point"));
+    }
+    e = cudaMemcpyAsync(pts + (size_t)6 * m, hw.data(), sizeof(double) * m,
+                        cudaMemcpyHostToDevice, st);
+    if (!e) e = cudaStreamSynchronize(st);
+    if (e) return cleanup(cuda_fail(e, "write weights"));
+  }
+  int* base;
+  double* W64;
+  float* W32;
+  if ((s = g->alloc(&base, (size_t)3 * m))) return cleanup(s);
+  if ((s = g->alloc(&W64, (size_t)12 * m))) return cleanup(s);
+  if ((s = g->alloc(&W32, (size_t)12 * m))) return cleanup(s);
+  PointData& pd = g->pd;
+  pd.m = m;
+  const double* X[3];
+  int* B[3];
+  double* WW[3];
+  float* VV[3];
+  for (int c = 0; c < 3; ++c) {
+    X[c] = pts + (size_t)c * m;
+    pd.X[c] = X[c];
+    pd.nrm[c] = pts + (size_t)(3 + c) * m;
+    B[c] = base + (size_t)c * m;
+    WW[c] = W64 + (size_t)4 * c * m;
+    VV[c] = W32 + (size_t)4 * c * m;
+    pd.base[c] = B[c];
+    pd.W64[c] = WW[c];
+    pd.W32[c] = VV[c];
+  }
+  pd.w = pts + (size_t)6 * m;
+  {
+    cudaError_t e = launch_point_prep(gd, m, X, B, WW, VV, st);
+    if (e) return cleanup(cuda_fail(e, "point prep"));
+  }
+  // bins
+  const int rows = n >= 4096 ? 2 : 4;
+  const int ntiles = (n / rows) * (dim == 3 ? n : 1);
+  int *start, *cursor;
+  if ((s = g->alloc(&start, (size_t)ntiles + 1))) return cleanup(s);
+  if ((s = g->alloc(&cursor, (size_t)ntiles + 1))) return cleanup(s);
+  int* bpts = nullptr;
+  int nnz = 0;
+  {
+    cudaError_t e = launch_bins(gd, pd, rows, ntiles, start, cursor, &bpts, &nnz, st);
+    if (e) return cleanup(cuda_fail(e, "binning"));
+  }
+  g->bytes += (int64_t)nnz * 4;
+  g->bins.rows = rows;
+  g->bins.ntiles = ntiles;
+  g->bins.start = start;
+  g->bins.pts = bpts;
+
+  {
+    cudaError_t e = configure_fft_kernels(n, rows);
+    if (e) return cleanup(cuda_fail(e, "configure kernels"));
+  }
+  if ((s = alloc_spectral<double>(g, g->ws64, st))) return cleanup(s);
+  if (d->precision == IBDL_FP32_REFINED) {
+    if ((s = ensure32(g, st))) return cleanup(s);
+  }
+
+  // Krylov workspace (float64, restart up to 64)
+  KrylovWs& k = g->kry;
+  k.m = m;
+  k.ld = (m + 31) / 32 * 32;
+  k.restart = 64;
+  k.nblk = (m + 2047) / 2048;
+  if (k.nblk > 148) k.nblk = 148;
+  if ((s = g->alloc(&k.V, (size_t)(k.restart + 1) * k.ld))) return cleanup(s);
+  if ((s = g->alloc(&k.H, (size_t)(k.restart + 1) * k.restart))) return cleanup(s);
+  if ((s = g->alloc(&k.cs, (size_t)k.restart))) return cleanup(s);
+  if ((s = g->alloc(&k.sn, (size_t)k.restart))) return cleanup(s);
+  if ((s = g->alloc(&k.gvec, (size_t)k.restart + 1))) return cleanup(s);
+  if ((s = g->alloc(&k.ysol, (size_t)k.restart))) return cleanup(s);
+  if ((s = g->alloc(&k.partial, (size_t)k.nblk * (k.restart + 2)))) return cleanup(s);
+  if ((s = g->alloc(&k.scal, (size_t)8))) return cleanup(s);
+  double* vecs;
+  if ((s = g->alloc(&vecs, (size_t)7 * k.ld))) return cleanup(s);
+  g->vb = vecs;
+  g->vx = vecs + k.ld;
+  g->vr = vecs + 2 * (size_t)k.ld;
+  g->vt = vecs + 3 * (size_t)k.ld;
+  g->vd = vecs + 4 * (size_t)k.ld;
+  g->stage_a = vecs + 5 * (size_t)k.ld;
+  g->stage_b = vecs + 6 * (size_t)k.ld;
+  if ((s = g->alloc(&g->d_flag, (size_t)4))) return cleanup(s);
+  {
+    cudaError_t e = cudaMallocHost((void**)&g->host_scal, 16 * sizeof(double));
+    if (e) return cleanup(cuda_fail(e, "cudaMallocHost"));
+    e = cudaStreamSynchronize(st);
+    if (e) return cleanup(cuda_fail(e, "create sync"));
+  }
+  *out = g;
+  return IBDL_OK;
+}
+
+void ibdl_destroy_geometry(ibdl_geometry g) {
+  if (!g) return;
+  cudaDeviceSynchronize();
+  delete g;
+}
+
+ibdl_status ibdl_apply_precision(ibdl_geometry g, const double* q, double* y, int32_t precision,
+                                 void* stream) {
+  g_err.clear();
+  IBDL_TRY(check_handle(g));
+  if (!q || !y) return fail(IBDL_ERR_INVALID_ARG, "NULL q or y");
+  if (precision != IBDL_FP64 && precision != IBDL_FP32_REFINED)
+    return fail(IBDL_ERR_INVALID_ARG, "unknown precision");
+  cudaStream_t st = (cudaStream_t)stream;
+  const double* qd;
+  IBDL_TRY(dev_in(q, g->m, g->stage_a, &qd, st));
+  const bool ydev = is_device_ptr(y);
+  double* yd = ydev ? y : g->stage_b;
+  IBDL_TRY(matvec_prec(g, precision, qd, yd, st));
+  if (!ydev) {
+    IBDL_CU(cudaMemcpyAsync(y, yd, sizeof(double) * g->m, cudaMemcpyDeviceToHost, st));
+    IBDL_CU(cudaStreamSynchronize(st));
+  }
+  return IBDL_OK;
+}
+
+ibdl_status ibdl_apply(ibdl_geometry g, const double* q, double* y, void* stream) {
+  IBDL_TRY(check_handle(g));
+  return ibdl_apply_precision(g, q, y, g->precision, stream);
+}
+
+ibdl_status ibdl_solve(ibdl_geometry g, const double* bdata, const double* g_grid, double* q_out,
+                       const ibdl_solve_opts* opts_in, ibdl_solve_info* info, void* stream) {
+  g_err.clear();
+  IBDL_TRY(check_handle(g));
+  if (!bdata || !q_out) return fail(IBDL_ERR_INVALID_ARG, "NULL bdata or q_out");
+  ibdl_solve_opts o;
+  ibdl_solve_opts_default(&o);
+  if (opts_in) o = *opts_in;
+  if (!(o.tol > 0) || !isfinite(o.tol)) return fail(IBDL_ERR_INVALID_ARG, "tol must be > 0");
+  if (o.restart < 1 || o.restart > 64) return fail(IBDL_ERR_INVALID_ARG, "restart in 1..64");
+  if (o.max_iters < 1) return fail(IBDL_ERR_INVALID_ARG, "max_iters >= 1");
+  if (o.max_refine < 1) o.max_refine = 1;
+  if (!(o.inner_tol > 0) || o.inner_tol >= 1) o.inner_tol = 1e-5;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int m = g->m;
+  // inputs
+  IBDL_CU(cudaMemcpyAsync(g->stage_a, bdata, sizeof(double) * m, cudaMemcpyDefault, st));
+  const double* gg = nullptr;
+  IBDL_TRY(grid_in(g, g_grid, &gg, st));
+  IBDL_CU(cudaMemsetAsync(g->d_flag, 0, sizeof(int), st));
+  IBDL_CU(launch_nonfinite_check(m, g->stage_a, g->d_flag, st));
+  IBDL_TRY(build_rhs(g, g->stage_a, gg, g->vb, st));
+  bool x_zero = true;
+  if (o.x0) {
+    IBDL_CU(cudaMemcpyAsync(g->vx, o.x0, sizeof(double) * m, cudaMemcpyDefault, st));
+    IBDL_CU(launch_nonfinite_check(m, g->vx, g->d_flag, st));
+    x_zero = false;
+  } else {
+    IBDL_CU(cudaMemsetAsync(g->vx, 0, sizeof(double) * m, st));
+  }
+  int flag = 0;
+  IBDL_CU(cudaMemcpyAsync(&flag, g->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  IBDL_CU(cudaStreamSynchronize(st));
+  if (flag) return fail(IBDL_ERR_NONFINITE, "non-finite boundary data or initial guess");
+  double bnorm = 0;
+  IBDL_TRY(vec_norm(g, g->vb, &bnorm, st));
+  if (!isfinite(bnorm)) return fail(IBDL_ERR_NONFINITE, "non-finite right-hand side");
+
+  GmresRun run;
+  int refine = 0;
+  ibdl_status status = IBDL_OK;
+  if (bnorm == 0.0) {
+    IBDL_CU(cudaMemsetAsync(g->vx, 0, sizeof(double) * m, st));
+    run.rel = 0;
+  } else if (g->precision == IBDL_FP64) {
+    status = gmres(g, IBDL_FP64, g->vb, g->vx, x_zero, bnorm, o.tol, o.restart, o.max_iters,
+                   true, &run, st);
+  } else {
+    // FP32 operator inside GMRES (float64 Arnoldi/Givens), float64 residuals
+    // outside: r = b - A64 x;  solve A32 d = r to inner_tol;  x += d.
+    if (x_zero) {
+      IBDL_CU(cudaMemcpyAsync(g->vr, g->vb, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
+    } else {
+      IBDL_TRY(matvec_prec(g, IBDL_FP64, g->vx, g->vt, st));
+      run.matvecs++;
+      IBDL_CU(launch_axpby(m, 1.0, g->vb, -1.0, g->vt, g->vr, st));
+    }
+    double rnorm = 0;
+    IBDL_TRY(vec_norm(g, g->vr, &rnorm, st));
+    run.rel = rnorm / bnorm;
+    status = IBDL_ERR_NOT_CONVERGED;
+    for (refine = 0; refine <= o.max_refine; ++refine) {
+      if (!isfinite(run.rel)) {
+        status = fail(IBDL_ERR_NONFINITE, "non-finite residual");
+        break;
+      }
+      if (run.rel <= o.tol) {
+        status = IBDL_OK;
+        break;
+      }
+      if (refine == o.max_refine || run.iters >= o.max_iters) {
+        status = fail(IBDL_ERR_NOT_CONVERGED, "refinement did not reach tol");
+        break;
+      }
+      // inner solve: the residual vector is moved to vd's right-hand side slot
+      IBDL_CU(cudaMemcpyAsync(g->vt, g->vr, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
+      IBDL_CU(cudaMemsetAsync(g->vd, 0, sizeof(double) * m, st));
+      GmresRun inner;
+      inner.iters = run.iters;
+      const double itol = fmax(o.inner_tol, 0.5 * o.tol * bnorm / rnorm);
+      double* rhs = g->stage_b;  // keep r intact while gmres reuses vr/vt
+      IBDL_CU(cudaMemcpyAsync(rhs, g->vr, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
+      ibdl_status si = gmres(g, IBDL_FP32_REFINED, rhs, g->vd, true, rnorm, itol, o.restart,
+                             o.max_iters, false, &inner, st);
+      run.iters = inner.iters;
+      run.matvecs += inner.matvecs;
+      if (si != IBDL_OK && si != IBDL_ERR_NOT_CONVERGED) {
+        status = si;
+        break;
+      }
+      IBDL_CU(launch_axpby(m, 1.0, g->vx, 1.0, g->vd, g->vx, st));
+      IBDL_TRY(matvec_prec(g, IBDL_FP64, g->vx, g->vt, st));
+      run.matvecs++;
+      IBDL_CU(launch_axpby(m, 1.0, g->vb, -1.0, g->vt, g->vr, st));
+      IBDL_TRY(vec_norm(g, g->vr, &rnorm, st));
+      run.rel = rnorm / bnorm;
+      run.hist.push_back(run.rel);
+    }
+  }
+  IBDL_CU(cudaMemcpyAsync(q_out, g->vx, sizeof(double) * m, cudaMemcpyDefault, st));
+  IBDL_CU(cudaStreamSynchronize(st));
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->iters = run.iters;
+    info->refine_steps = refine;
+    info->matvecs = run.matvecs;
+    info->rel_residual = run.rel;
+    const int nh = (int)run.hist.size() < 256 ? (int)run.hist.size() : 256;
+    info->n_history = nh;
+    for (int i = 0; i < nh; ++i) info->residual_history[i] = run.hist[i];
+  }
+  return status;
+}
+
+ibdl_status ibdl_evaluate(ibdl_geometry g, const double* q, const double* vb, const double* g_grid,
+                          double* u_out, void* stream) {
+  g_err.clear();
+  IBDL_TRY(check_handle(g));
+  if (!q || !u_out) return fail(IBDL_ERR_INVALID_ARG, "NULL q or u_out");
+  if (g->bc == IBDL_DIRICHLET && vb) return fail(IBDL_ERR_INVALID_ARG, "vb is Neumann-only");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int m = g->m;
+  IBDL_CU(cudaMemcpyAsync(g->stage_a, q, sizeof(double) * m, cudaMemcpyDefault, st));
+  if (vb) IBDL_CU(cudaMemcpyAsync(g->stage_b, vb, sizeof(double) * m, cudaMemcpyDefault, st));
+  const double* gg = nullptr;
+  IBDL_TRY(grid_in(g, g_grid, &gg, st));
+  SpreadSrc src;
+  src.q_div = g->stage_a;
+  src.coef_div = 1.0;
+  if (vb) {
+    src.v_plain = g->stage_b;
+    src.coef_plain = 1.0;
+  }
+  if (gg) {
+    src.f_grid = gg;
+    src.coef_grid = -1.0;
+  }
+  const bool udev = is_device_ptr(u_out);
+  double* ud = udev ? u_out : g->ws64.grid;
+  IBDL_TRY((field_solve<double, double>(g, src, ud, st)));
+  if (!udev) {
+    IBDL_CU(cudaMemcpyAsync(u_out, ud, sizeof(double) * g->ncells, cudaMemcpyDeviceToHost, st));
+    IBDL_CU(cudaStreamSynchronize(st));
+  }
+  return IBDL_OK;
+}
+
+static ibdl_status grid_out_begin(ibdl_geometry g, double* out, double** dev) {
+  if (is_device_ptr(out)) {
+    *dev = out;
+    return IBDL_OK;
+  }
+  if (!g->grid_stage) IBDL_TRY(g->alloc(&g->grid_stage, (size_t)g->ncells));
+  *dev = g->grid_stage;
+  return IBDL_OK;
+}
+
+static ibdl_status grid_out_end(ibdl_geometry g, double* out, double* dev, cudaStream_t st) {
+  if (dev == out) return IBDL_OK;
+  IBDL_CU(cudaMemcpyAsync(out, dev, sizeof(double) * g->ncells, cudaMemcpyDeviceToHost, st));
+  IBDL_CU(cudaStreamSynchronize(st));
+  return IBDL_OK;
+}
+
+static ibdl_status spread_common(ibdl_geometry g, const double* v, double* f_out, int precision,
+                                 bool div, void* stream) {
+  g_err.clear();
+  IBDL_TRY(check_handle(g));
+  if (!v || !f_out) return fail(IBDL_ERR_INVALID_ARG, "NULL input or output");
+  if (precision != 0 && precision != 1) return fail(IBDL_ERR_INVALID_ARG, "precision");
+  cudaStream_t st = (cudaStream_t)stream;
+  IBDL_CU(cudaMemcpyAsync(g->stage_a, v, sizeof(double) * g->m, cudaMemcpyDefault, st));
+  SpreadSrc src;
+  if (div) {
+    src.q_div = g->stage_a;
+    src.coef_div = 1.0;
+  } else {
+    src.v_plain = g->stage_a;
+    src.coef_plain = 1.0;
+  }
+  double* fd;
+  IBDL_TRY(grid_out_begin(g, f_out, &fd));
+  if (precision == 1) {
+    IBDL_TRY(ensure32(g, st));
+    IBDL_CU(launch_rows_fwd<float>(g->grid, g->pd, g->bins, src, g->ws32, fd, st));
+  } else {
+    IBDL_CU(launch_rows_fwd<double>(g->grid, g->pd, g->bins, src, g->ws64, fd, st));
+  }
+  return grid_out_end(g, f_out, fd, st);
+}
+
+ibdl_status ibdl_spread_div(ibdl_geometry g, const double* q, double* f_out, int32_t precision,
+                            void* stream) {
+  return spread_common(g, q, f_out, precision, true, stream);
+}
+
+ibdl_status ibdl_spread(ibdl_geometry g, const double* v, double* f_out, int32_t precision,
+                        void* stream) {
+  return spread_common(g, v, f_out, precision, false, stream);
+}
+
+ibdl_status ibdl_helmholtz(ibdl_geometry g, const double* f, double* v_out, int32_t precision,
+                           void* stream) {
+  g_err.clear();
+  IBDL_TRY(check_handle(g));
+  if (!f || !v_out) return fail(IBDL_ERR_INVALID_ARG, "NULL input or output");
+  if (precision != 0 && precision != 1) return fail(IBDL_ERR_INVALID_ARG, "precision");
+  cudaStream_t st = (cudaStream_t)stream;
+  const double* fd;
+  IBDL_TRY(grid_in(g, f, &fd, st));
+  double* vd;
+  if (is_device_ptr(v_out)) {
+    vd = v_out;
+  } else {
+    // the staging grid may hold f; the float64 workspace grid is free here
+    vd = g->ws64.grid;
+  }
+  SpreadSrc src;
+  src.f_grid = fd;
+  src.coef_grid = 1.0;
+  if (precision == 1) {
+    IBDL_TRY(ensure32(g, st));
+    IBDL_TRY((field_solve<float, double>(g, src, vd, st)));
+  } else {
+    IBDL_TRY((field_solve<double, double>(g, src, vd, st)));
+  }
+  if (vd != v_out) {
+    IBDL_CU(cudaMemcpyAsync(v_out, vd, sizeof(double) * g->ncells, cudaMemcpyDeviceToHost, st));
+    IBDL_CU(cudaStreamSynchronize(st));
+  }
+  return IBDL_OK;
+}
+
+ibdl_status ibdl_interp(ibdl_geometry g, const double* u, double* y_out, int32_t precision,
+                        void* stream) {
+  g_err.clear();
+  IBDL_TRY(check_handle(g));
+  if (!u || !y_out) return fail(IBDL_ERR_INVALID_ARG, "NULL input or output");
+  if (precision != 0 && precision != 1) return fail(IBDL_ERR_INVALID_ARG, "precision");
+  cudaStream_t st = (cudaStream_t)stream;
+  const double* ud;
+  IBDL_TRY(grid_in(g, u, &ud, st));
+  const bool ydev = is_device_ptr(y_out);
+  double* yd = ydev ? y_out : g->stage_b;
+  if (precision == 1) {
+    IBDL_TRY(ensure32(g, st));
+    IBDL_CU(launch_grid_to_float(ud, g->ws32.grid, g->ncells, st));
+    IBDL_CU(launch_interp<float>(g->grid, g->pd, g->ws32.grid, nullptr, 0.0, yd, st));
+  } else {
+    IBDL_CU(launch_interp<double>(g->grid, g->pd, ud, nullptr, 0.0, yd, st));
+  }
+  if (!ydev) {
+    IBDL_CU(cudaMemcpyAsync(y_out, yd, sizeof(double) * g->m, cudaMemcpyDeviceToHost, st));
+    IBDL_CU(cudaStreamSynchronize(st));
+  }
+  return IBDL_OK;
+}
+
+ibdl_status ibdl_get_geometry_info(ibdl_geometry g, ibdl_geometry_info* info) {
+  IBDL_TRY(check_handle(g));
+  if (!info) return fail(IBDL_ERR_INVALID_ARG, "NULL info");
+  memset(info, 0, sizeof(*info));
+  info->dim = g->grid.dim;
+  info->n = g->grid.n;
+  info->m = g->m;
+  info->h = g->grid.h;
+  info->kappa = g->grid.kappa;
+  info->bc = g->bc;
+  info->delta = g->grid.delta;
+  info->precision = g->precision;
+  info->device_bytes = g->bytes;
+  info->fft_passes = fft_kernels_per_solve<double>(g->grid.dim);
+  return IBDL_OK;
+}
+
+int64_t ibdl_kernel_launch_count(void) { return (int64_t)g_launches.load(); }
+
+const char* ibdl_status_string(ibdl_status s) {
+  switch (s) {
+    case IBDL_OK: return "ok";
+    case IBDL_ERR_INVALID_ARG: return "invalid argument";
+    case IBDL_ERR_OOM: return "out of device memory";
+    case IBDL_ERR_CUDA: return "CUDA error";
+    case IBDL_ERR_NOT_CONVERGED: return "not converged";
+    case IBDL_ERR_BREAKDOWN: return "GMRES breakdown";
+    case IBDL_ERR_NONFINITE: return "non-finite value";
+    case IBDL_ERR_TIMEOUT: return "device wait timed out";
+    case IBDL_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char* ibdl_last_error_message(void) { return g_err.c_str(); }
+
+int32_t ibdl_version(void) { return 100 * IBDL_VERSION_MAJOR + IBDL_VERSION_MINOR; }
+
+}  // extern "C"

@@ -1,0 +1,141 @@
+// Internal declarations shared by the translation units of libibdl.
+//
+// Data layout in device memory (one geometry handle):
+//   points   : SoA float64 x/y/z, normals, weights (length m)
+//   base[c]  : int32 floor((X_c - origin_c)/h) - 1, the first of the 4 nodes
+//              per axis where phi((x_j - X_c)/h) can be non-zero (Sec. 5.2)
+//   W[c][t]  : phi(base_c + t - s_c), t = 0..3, in float64 and float32
+//   bins     : CSR lists of the points whose 6-node support box touches each
+//              row tile (R consecutive y rows at one z), for the fused
+//              spread + forward x-FFT kernel
+//   grid     : real n^d field, x fastest
+//   spectrum : after the x real-to-complex transform, stored TRANSPOSED as
+//              (n/2 + 1) contiguous slabs, slab kx holding [z][y] (3D) or [y]
+//              (2D); the y/z pencils are then contiguous or uniformly strided
+//              and the Nyquist slab needs no special case.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ibdl.h"
+
+namespace ibdl {
+
+template <typename T> struct Cx;
+template <> struct Cx<double> { using type = double2; };
+template <> struct Cx<float> { using type = float2; };
+template <typename T> using cx_t = typename Cx<T>::type;
+
+// Row tile height of the fused spread + x-FFT and x-iFFT kernels.
+constexpr int kBoxSide = 6;   // nodes per axis touched by the centred
+                              // difference of a 4-point delta
+
+struct PointData {
+  int m = 0;
+  const double* X[3] = {nullptr, nullptr, nullptr};
+  const double* nrm[3] = {nullptr, nullptr, nullptr};
+  const double* w = nullptr;       // quadrature weight / h^d
+  const int* base[3] = {nullptr, nullptr, nullptr};
+  const double* W64[3] = {nullptr, nullptr, nullptr};  // [t*m + i]
+  const float* W32[3] = {nullptr, nullptr, nullptr};
+};
+
+struct Bins {
+  int rows = 4;              // R: y rows per tile (even)
+  int ntiles = 0;            // n^(d-2) * (n / R)
+  const int* start = nullptr;  // ntiles + 1
+  const int* pts = nullptr;
+};
+
+struct GridDesc {
+  int dim = 2;
+  int n = 0;
+  int log2n = 0;
+  double h = 0, kappa = 0;
+  double origin[3] = {0, 0, 0};
+  int delta = 0;
+};
+
+template <typename T>
+struct SpectralWs {
+  typename Cx<T>::type* spec = nullptr;  // (n/2+1) * n^(d-1) complex
+  T* grid = nullptr;                      // n^d real
+  const typename Cx<T>::type* tw = nullptr;  // tw[j] = exp(-2 pi i j / n)
+  const T* s2 = nullptr;                  // sin^2(pi k / n), k < n
+};
+
+// Sources of the fused spread kernel: out = coef_div * S~ q_div
+//   + coef_plain * S v_plain + coef_grid * f_grid (null pointers skip a term).
+struct SpreadSrc {
+  const double* q_div = nullptr;
+  double coef_div = 0;
+  const double* v_plain = nullptr;
+  double coef_plain = 0;
+  const double* f_grid = nullptr;
+  double coef_grid = 0;
+};
+
+// ---- launch bookkeeping -------------------------------------------------
+void count_launch();
+cudaError_t check_launch();
+
+// ---- point kernels (k_points.cu) -----------------------------------------
+cudaError_t launch_point_prep(const GridDesc& g, int m, const double* const X[3],
+                              int* const base[3], double* const W64[3],
+                              float* const W32[3], cudaStream_t st);
+// Bin building: counts, scan, fill.  tmp_counts has ntiles + 1 ints.
+cudaError_t launch_bins(const GridDesc& g, const PointData& p, int rows, int ntiles,
+                        int* start, int* cursor, int** pts_out, int* nnz_out,
+                        cudaStream_t st);
+template <typename T>
+cudaError_t launch_interp(const GridDesc& g, const PointData& p, const T* grid,
+                          const double* jvec, double jump, double* y, cudaStream_t st);
+cudaError_t launch_grid_to_float(const double* src, float* dst, int64_t count,
+                                 cudaStream_t st);
+
+// ---- FFT / Helmholtz kernels (k_fft.cu) ------------------------------------
+// Forward pass: spread sources into row tiles, x-FFT, write the transposed
+// half spectrum.  If write_grid != nullptr the tile rows are written to that
+// real grid instead (no FFT).
+template <typename T>
+cudaError_t launch_rows_fwd(const GridDesc& g, const PointData& p, const Bins& b,
+                            const SpreadSrc& src, SpectralWs<T>& ws, double* write_grid,
+                            cudaStream_t st);
+// y/z passes on the spectrum; solve multiplies by kappa / (sigma(k) n^d).
+template <typename T>
+cudaError_t launch_spectral_solve(const GridDesc& g, SpectralWs<T>& ws, cudaStream_t st);
+// Inverse x pass: transposed half spectrum -> real grid (T or double).
+template <typename T, typename OutT>
+cudaError_t launch_rows_inv(const GridDesc& g, const Bins& b, SpectralWs<T>& ws,
+                            OutT* out, cudaStream_t st);
+template <typename T>
+int fft_kernels_per_solve(int dim);
+cudaError_t configure_fft_kernels(int n, int rows);
+
+// ---- Krylov kernels (k_krylov.cu) -----------------------------------------
+struct KrylovWs {
+  int m = 0;            // vector length
+  int ld = 0;           // leading dimension of V (>= m, multiple of 32)
+  int restart = 0;
+  double* V = nullptr;  // (restart + 1) x ld
+  double* H = nullptr;  // column j at H[j * (restart + 1)]
+  double* cs = nullptr;
+  double* sn = nullptr;
+  double* gvec = nullptr;   // restart + 1
+  double* ysol = nullptr;   // restart
+  double* partial = nullptr;  // nblk * (restart + 2)
+  double* scal = nullptr;     // device scalars: [0] residual estimate, ...
+  int nblk = 0;
+};
+cudaError_t krylov_dot_norm(const KrylovWs& k, const double* x, double* out_sq,
+                            cudaStream_t st);   // out_sq[0] = ||x||^2 (device)
+cudaError_t krylov_start(const KrylovWs& k, const double* r, double* out_scal,
+                         cudaStream_t st);      // V0 = r/||r||, g = (||r||,0..)
+cudaError_t krylov_arnoldi(const KrylovWs& k, int j, double bnorm, cudaStream_t st);
+cudaError_t krylov_finish(const KrylovWs& k, int kdim, double* x, cudaStream_t st);
+cudaError_t launch_axpby(int m, double a, const double* x, double b, const double* y,
+                         double* out, cudaStream_t st);  // out = a x + b y
+cudaError_t launch_nonfinite_check(int m, const double* x, int* flag, cudaStream_t st);
+
+}  // namespace ibdl

@@ -1,0 +1,270 @@
+"""Thin ctypes binding of libibdl (argument marshalling only).
+
+Every computation happens in the CUDA library; this module converts torch
+tensors or numpy arrays to raw pointers, fills the C structs of
+``include/ibdl.h`` and turns error codes into exceptions.  The names follow
+the C entry points: ``create_geometry``, ``apply``, ``solve``, ``evaluate``,
+``spread_div``, ``spread``, ``helmholtz``, ``interp``.
+
+Arrays may live on the GPU (torch CUDA tensors) or on the host (numpy arrays
+or CPU tensors, pinned or not); the library copies host arrays itself.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libibdl.so")
+
+OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_NOT_CONVERGED = 0, 1, 2, 3, 4
+ERR_BREAKDOWN, ERR_NONFINITE, ERR_TIMEOUT, ERR_UNSUPPORTED = 5, 6, 7, 8
+DIRICHLET, NEUMANN = 0, 1
+DELTA = {"peskin4": 0, "cos4": 1}
+FP64, FP32_REFINED = 0, 1
+
+# Every function that include/ibdl.h declares (the ABI test checks this list
+# against the header and the library's exports).
+EXPORTS = [
+    "ibdl_solve_opts_default", "ibdl_create_geometry", "ibdl_destroy_geometry",
+    "ibdl_apply", "ibdl_apply_precision", "ibdl_solve", "ibdl_evaluate",
+    "ibdl_spread_div", "ibdl_spread", "ibdl_helmholtz", "ibdl_interp",
+    "ibdl_get_geometry_info", "ibdl_kernel_launch_count", "ibdl_status_string",
+    "ibdl_last_error_message", "ibdl_version",
+]
+
+
+class GeometryDesc(C.Structure):
+    _fields_ = [
+        ("dim", C.c_int32), ("n", C.c_int32), ("box_len", C.c_double),
+        ("origin", C.c_double * 3), ("m", C.c_int64),
+        ("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p),
+        ("nx", C.c_void_p), ("ny", C.c_void_p), ("nz", C.c_void_p),
+        ("w", C.c_void_p), ("kappa", C.c_double), ("delta", C.c_int32),
+        ("bc", C.c_int32), ("precision", C.c_int32), ("reserved", C.c_int32),
+    ]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [
+        ("tol", C.c_double), ("restart", C.c_int32), ("max_iters", C.c_int32),
+        ("max_refine", C.c_int32), ("inner_tol", C.c_double), ("x0", C.c_void_p),
+    ]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [
+        ("iters", C.c_int32), ("refine_steps", C.c_int32), ("matvecs", C.c_int32),
+        ("n_history", C.c_int32), ("rel_residual", C.c_double),
+        ("residual_history", C.c_double * 256),
+    ]
+
+    def as_dict(self):
+        return {"iters": self.iters, "refine_steps": self.refine_steps,
+                "matvecs": self.matvecs, "rel_residual": self.rel_residual,
+                "history": list(self.residual_history[: self.n_history])}
+
+
+class GeometryInfo(C.Structure):
+    _fields_ = [
+        ("dim", C.c_int32), ("n", C.c_int32), ("m", C.c_int64), ("h", C.c_double),
+        ("kappa", C.c_double), ("bc", C.c_int32), ("delta", C.c_int32),
+        ("precision", C.c_int32), ("device_bytes", C.c_int64),
+        ("fft_passes", C.c_int32), ("reserved", C.c_int32),
+    ]
+
+
+class IbdlError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"ibdl status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libibdl.so (built by ``build.py``); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libibdl.so not built ({path}); run __graft_entry__.build()")
+    lib = C.CDLL(path)
+    vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+    sig = {
+        "ibdl_solve_opts_default": (None, [C.POINTER(SolveOpts)]),
+        "ibdl_create_geometry": (C.c_int, [C.POINTER(GeometryDesc), vp, C.POINTER(vp)]),
+        "ibdl_destroy_geometry": (None, [vp]),
+        "ibdl_apply": (C.c_int, [vp, vp, vp, vp]),
+        "ibdl_apply_precision": (C.c_int, [vp, vp, vp, i32, vp]),
+        "ibdl_solve": (C.c_int, [vp, vp, vp, vp, C.POINTER(SolveOpts),
+                                 C.POINTER(SolveInfo), vp]),
+        "ibdl_evaluate": (C.c_int, [vp, vp, vp, vp, vp, vp]),
+        "ibdl_spread_div": (C.c_int, [vp, vp, vp, i32, vp]),
+        "ibdl_spread": (C.c_int, [vp, vp, vp, i32, vp]),
+        "ibdl_helmholtz": (C.c_int, [vp, vp, vp, i32, vp]),
+        "ibdl_interp": (C.c_int, [vp, vp, vp, i32, vp]),
+        "ibdl_get_geometry_info": (C.c_int, [vp, C.POINTER(GeometryInfo)]),
+        "ibdl_kernel_launch_count": (i64, []),
+        "ibdl_status_string": (C.c_char_p, [C.c_int]),
+        "ibdl_last_error_message": (C.c_char_p, []),
+        "ibdl_version": (i32, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != OK:
+        lib = load()
+        raise IbdlError(status, lib.ibdl_status_string(status).decode() + ": "
+                        + lib.ibdl_last_error_message().decode())
+
+
+def _ptr(a):
+    """Raw address of a contiguous float64 tensor / array (or None)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags.c_contiguous:
+            raise TypeError("numpy arrays must be contiguous float64")
+        return a.ctypes.data
+    # torch tensor
+    if str(a.dtype) != "torch.float64" or not a.is_contiguous():
+        raise TypeError("tensors must be contiguous float64")
+    return a.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+def kernel_launch_count() -> int:
+    return int(load().ibdl_kernel_launch_count())
+
+
+def version() -> int:
+    return int(load().ibdl_version())
+
+
+class Geometry:
+    """An IBDL problem's geometry handle (``ibdl_create_geometry``).
+
+    ``x, y, z, nx, ny, nz, w`` are float64 arrays of length m (host or
+    device); they are copied by the library.
+    """
+
+    def __init__(self, dim, n, box_len, origin, x, y, nx, ny, w, kappa, z=None,
+                 nz=None, delta="peskin4", bc=DIRICHLET, precision=FP64, stream=None):
+        lib = load()
+        d = GeometryDesc()
+        d.dim, d.n, d.box_len = int(dim), int(n), float(box_len)
+        org = list(origin) + [0.0] * (3 - len(origin))
+        d.origin = (C.c_double * 3)(*org[:3])
+        d.m = int(len(x))
+        d.x, d.y, d.z = _ptr(x), _ptr(y), _ptr(z)
+        d.nx, d.ny, d.nz = _ptr(nx), _ptr(ny), _ptr(nz)
+        d.w = _ptr(w)
+        d.kappa = float(kappa)
+        d.delta = DELTA[delta] if isinstance(delta, str) else int(delta)
+        d.bc, d.precision = int(bc), int(precision)
+        self._keep = (x, y, z, nx, ny, nz, w)
+        h = C.c_void_p()
+        _check(lib.ibdl_create_geometry(C.byref(d), _stream(stream), C.byref(h)))
+        self._h = h
+        self._keep = None
+        self.dim, self.n, self.m = d.dim, d.n, d.m
+        self.bc, self.precision = d.bc, d.precision
+
+    @classmethod
+    def from_workload(cls, geom, bc=DIRICHLET, precision=FP64, stream=None):
+        """Build from a ``workloads.geometry.Geometry`` (host float64)."""
+        X = np.ascontiguousarray(geom.X, dtype=np.float64)
+        N = np.ascontiguousarray(geom.normals, dtype=np.float64)
+        cols = [np.ascontiguousarray(X[:, c]) for c in range(geom.dim)]
+        ncols = [np.ascontiguousarray(N[:, c]) for c in range(geom.dim)]
+        return cls(geom.dim, geom.n, geom.box_len, geom.origin, cols[0], cols[1], ncols[0],
+                   ncols[1], np.ascontiguousarray(geom.weights, dtype=np.float64),
+                   geom.kappa, z=cols[2] if geom.dim == 3 else None,
+                   nz=ncols[2] if geom.dim == 3 else None, delta=geom.delta, bc=bc,
+                   precision=precision, stream=stream)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().ibdl_destroy_geometry(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        gi = GeometryInfo()
+        _check(load().ibdl_get_geometry_info(self._h, C.byref(gi)))
+        return {f: getattr(gi, f) for f, _ in GeometryInfo._fields_ if f != "reserved"}
+
+    def apply(self, q, y, precision=None, stream=None):
+        lib = load()
+        if precision is None:
+            _check(lib.ibdl_apply(self._h, _ptr(q), _ptr(y), _stream(stream)))
+        else:
+            _check(lib.ibdl_apply_precision(self._h, _ptr(q), _ptr(y), int(precision),
+                                            _stream(stream)))
+        return y
+
+    def solve(self, bdata, q_out, g_grid=None, tol=1e-8, restart=30, max_iters=500,
+              max_refine=8, inner_tol=1e-5, x0=None, stream=None, raise_on_error=True):
+        o = SolveOpts()
+        load().ibdl_solve_opts_default(C.byref(o))
+        o.tol, o.restart, o.max_iters = float(tol), int(restart), int(max_iters)
+        o.max_refine, o.inner_tol, o.x0 = int(max_refine), float(inner_tol), _ptr(x0)
+        info = SolveInfo()
+        st = load().ibdl_solve(self._h, _ptr(bdata), _ptr(g_grid), _ptr(q_out), C.byref(o),
+                               C.byref(info), _stream(stream))
+        if raise_on_error:
+            _check(st)
+        out = info.as_dict()
+        out["status"] = int(st)
+        return out
+
+    def evaluate(self, q, u_out, vb=None, g_grid=None, stream=None):
+        _check(load().ibdl_evaluate(self._h, _ptr(q), _ptr(vb), _ptr(g_grid), _ptr(u_out),
+                                    _stream(stream)))
+        return u_out
+
+    def spread_div(self, q, f_out, precision=FP64, stream=None):
+        _check(load().ibdl_spread_div(self._h, _ptr(q), _ptr(f_out), int(precision),
+                                      _stream(stream)))
+        return f_out
+
+    def spread(self, v, f_out, precision=FP64, stream=None):
+        _check(load().ibdl_spread(self._h, _ptr(v), _ptr(f_out), int(precision),
+                                  _stream(stream)))
+        return f_out
+
+    def helmholtz(self, f, v_out, precision=FP64, stream=None):
+        _check(load().ibdl_helmholtz(self._h, _ptr(f), _ptr(v_out), int(precision),
+                                     _stream(stream)))
+        return v_out
+
+    def interp(self, u, y_out, precision=FP64, stream=None):
+        _check(load().ibdl_interp(self._h, _ptr(u), _ptr(y_out), int(precision),
+                                  _stream(stream)))
+        return y_out
