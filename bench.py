@@ -1,0 +1,397 @@
+#!/usr/bin/env python3
+"""IBDL solve benchmark on one GB300 (or N independent replicas).
+
+Workload: the 2D star problem, periodic box [0,1)^2 with N=1024^2 nodes, star
+r(theta) = 0.3 (1 + 0.2 cos 5 theta), M = 3525 arclength-equispaced points,
+Peskin 4-point delta, kappa = 1e-3, seeded 10-mode Fourier boundary data.
+One step = one Dirichlet solve (seed 0) + one Neumann solve (seed 1) to a
+relative residual of 1e-8 (the whole hot path: spread-divergence, FFT
+Helmholtz solve, interpolation + jump, GMRES Arnoldi/Givens, the Neumann
+right-hand side).
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
+the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from workloads import configs  # noqa: E402
+
+METRIC = "IBDL solves/s at 1e-8 relative residual (2D star N=1024^2, M=3525, Dirichlet+Neumann)"
+WORKLOAD = "c2-star-n1024-m3525-kappa1e-3-dirichlet+neumann"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ibdl", choices=["ibdl", "reference"])
+    ap.add_argument("--precision", default="fp32-refined", choices=["fp32-refined", "fp64"])
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="CPU work budget of the oracle baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def problems():
+    return [configs.c2(bc=configs.DIRICHLET), configs.c2(bc=configs.NEUMANN)]
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# roofline bookkeeping: algorithmic bytes / flops per launch of each kernel
+# family on this workload (2D, n^2 grid, M points)
+# ---------------------------------------------------------------------------
+
+def kernel_model(name, n, m):
+    p = 8 if name.endswith("f64") else 4
+    spec = (n // 2 + 1) * n * 2 * p            # half spectrum, complex
+    grid = n * n * p
+    fft = 5.0 * n * math.log2(n)               # flops of one complex length-n FFT
+    pts = m * (8 * 4 + 4 * 2 + 8 * 8)          # q, w, normals, base, W per point
+    if name.startswith("rows_fwd"):
+        return {"bytes": spec + pts, "flops": (n // 2) * fft}
+    if name.startswith("pencils_solve"):
+        return {"bytes": 2 * spec, "flops": (n // 2 + 1) * (2 * fft + 6 * n)}
+    if name.startswith("rows_inv"):
+        return {"bytes": spec + grid, "flops": (n // 2) * fft}
+    if name.startswith("interp"):
+        return {"bytes": m * (16 * p + 8 * 3 + 4 * 2 + 8 * p), "flops": m * 40.0}
+    return None
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "src": "measured"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "src": "fallback"}
+
+
+# Nominal GB300 FP64 rate (the recipe's figure); the FP64 FFT passes are
+# bound by it, not by HBM.
+FP64_PEAK_TFLOPS = 1.25
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle as it stands
+# ---------------------------------------------------------------------------
+
+def oracle_sample(probs, tol, budget_s):
+    """Run oracle solves (alternating Dirichlet / Neumann) for ~budget_s."""
+    from oracle import ibdl_oracle as O
+    t0 = time.perf_counter()
+    done, iters = 0, []
+    sols = {}
+    while True:
+        p = probs[done % len(probs)]
+        r = O.solve(p.geom, p.bc, p.bdata, tol=tol)
+        iters.append(r.iters)
+        sols.setdefault(p.name, r.x)
+        done += 1
+        if time.perf_counter() - t0 >= budget_s and done % len(probs) == 0:
+            break
+    el = time.perf_counter() - t0
+    return done, el, iters, sols
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    probs = problems()
+    # each step is one bounded sample: a Dirichlet + Neumann oracle solve pair
+    for _ in range(args.warmup):
+        oracle_sample(probs, args.tol, 0.0)
+    t0 = time.perf_counter()
+    solves = 0
+    lat = []
+    for _ in range(args.steps):
+        s0 = time.perf_counter()
+        n, _, _, _ = oracle_sample(probs, args.tol, 0.0)
+        solves += n
+        lat.append((time.perf_counter() - s0) / n * 1e3)
+    el = time.perf_counter() - t0
+    value = solves / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": "fp64 (numpy oracle)",
+                   "tol": args.tol},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} steps x (1 Dirichlet + 1 Neumann oracle "
+                                   f"solve at tol {args.tol:g})"},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import paper_2203_12126_gb300 as pkg
+    from paper_2203_12126_gb300 import ibdl
+
+    assert torch.cuda.is_available(), "bench.py needs a GPU"
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    pkg.load()
+    stream = torch.cuda.current_stream()
+
+    prec = ibdl.FP32_REFINED if args.precision == "fp32-refined" else ibdl.FP64
+    probs = problems()
+    geoms, bs, qs = [], [], []
+    for p in probs:
+        geoms.append(pkg.Geometry.from_workload(p.geom, bc=p.bc, precision=prec))
+        bs.append(torch.tensor(p.bdata, dtype=torch.float64, device=dev))
+        qs.append(torch.zeros(p.geom.m, dtype=torch.float64, device=dev))
+    m, n = probs[0].geom.m, probs[0].geom.n
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def solve(i, b=None, q=None):
+        return geoms[i].solve(bs[i] if b is None else b, qs[i] if q is None else q,
+                              tol=args.tol)
+
+    for _ in range(args.warmup):
+        for i in range(len(probs)):
+            solve(i)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, per-solve CUDA events, L2 flushed between
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps * len(probs))]
+    infos = []
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = pkg.kernel_launch_count()
+    w0 = time.perf_counter()
+    k = 0
+    for _ in range(args.steps):
+        for i in range(len(probs)):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            infos.append(solve(i))
+            ev[k][1].record(stream)
+            k += 1
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - w0
+    launches = pkg.kernel_launch_count() - l0
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    lat = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(lat))
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    solves = args.steps * len(probs) * world
+    value = solves / (total_ms / 1e3)
+
+    # ---- accuracy of the timed path against a float64 GPU solve at 1e-12
+    errs = []
+    for i, p in enumerate(probs):
+        g64 = pkg.Geometry.from_workload(p.geom, bc=p.bc, precision=ibdl.FP64)
+        q64 = torch.zeros_like(qs[i])
+        g64.solve(bs[i], q64, tol=1e-12)
+        errs.append(float(torch.linalg.norm(qs[i] - q64) / torch.linalg.norm(q64)))
+        g64.close()
+
+    # ---- profiled pass: per-kernel event durations -> dominant kernel roofline
+    pkg.ibdl.profile_enable(True)
+    pkg.ibdl.profile_read(reset=True)
+    for _ in range(max(3, args.steps // 4)):
+        for i in range(len(probs)):
+            flush.fill_(1.0)
+            solve(i)
+    stats = pkg.ibdl.profile_read(reset=True)
+    pkg.ibdl.profile_enable(False)
+    peaks = load_peaks()
+    dom = max(stats.items(), key=lambda kv: kv[1][1]) if stats else None
+    roofline = None
+    kernels = {}
+    tot_prof = sum(v[1] for v in stats.values()) or 1.0
+    for name, (cnt, ms) in stats.items():
+        kernels[name] = {"launches": cnt, "avg_us": ms / cnt * 1e3, "share": ms / tot_prof}
+    if dom:
+        name, (cnt, ms) = dom
+        avg_s = ms / cnt / 1e3
+        model = kernel_model(name, n, m)
+        if model is not None:
+            if name.endswith("f64"):
+                ach = model["flops"] / avg_s / 1e12
+                roofline = {"kernel": name, "bound": "alu", "achieved": ach,
+                            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                            "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                            "peak_src": "nominal GB300 FP64 rate (no measured FP64 peak)",
+                            "algorithmic_flops": model["flops"],
+                            "avg_launch_us": avg_s * 1e6}
+            else:
+                ach = model["bytes"] / avg_s / 1e9
+                roofline = {"kernel": name, "bound": "hbm", "achieved": ach,
+                            "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                            "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                            "peak_src": peaks["src"], "algorithmic_bytes": model["bytes"],
+                            "avg_launch_us": avg_s * 1e6}
+
+    # ---- end to end through the C ABI with pinned host buffers
+    hb = [torch.tensor(p.bdata, dtype=torch.float64).pin_memory() for p in probs]
+    hq = [torch.zeros(p.geom.m, dtype=torch.float64).pin_memory() for p in probs]
+    e2e_steps = max(3, args.steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for i in range(len(probs)):
+            solve(i, hb[i], hq[i])
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": e2e_steps * len(probs) * world / e2e_s, "unit": "solves/s",
+           "h2d_bytes_per_step": int(sum(8 * p.geom.m for p in probs)),
+           "d2h_bytes_per_step": int(sum(8 * p.geom.m for p in probs)),
+           "note": "ibdl_solve with pinned host U_b/V_b in and host Q/U out; copies "
+                   "inside the call; host wall clock"}
+
+    out = None
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            done, el, citers, sols = oracle_sample(probs, args.tol, args.cpu_seconds)
+            cpu = {"value": done / el, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                   "sample": f"{done} oracle solves (Dirichlet/Neumann alternating, tol "
+                             f"{args.tol:g}) in {el:.1f} s, numpy single thread",
+                   "oracle_iters": citers[:2]}
+            qd = qs[0].cpu().numpy()
+            cpu["gpu_vs_oracle_rel_diff"] = float(
+                np.linalg.norm(qd - sols[probs[0].name]) / np.linalg.norm(sols[probs[0].name]))
+        iters = [f["iters"] for f in infos]
+        mv = [f["matvecs"] for f in infos]
+        out = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if prec == ibdl.FP32_REFINED else "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "m": m, "kappa": 1e-3,
+                       "tol": args.tol, "precision": args.precision,
+                       "l2": "flushed between solves (512 MiB write, outside the events)",
+                       "parallelism": f"replicas x{world}"},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)),
+                           "p99": float(np.percentile(lat, 99)),
+                           "mean": float(np.mean(lat))},
+            "iters_per_solve": {"min": min(iters), "max": max(iters)},
+            "matvecs_per_s": float(sum(mv)) * world / (total_ms / 1e3),
+            "rel_err_vs_fp64_1e-12": max(errs),
+            "roofline": roofline,
+            "kernels": kernels,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "wall_s_timed": wall,
+            "clocks": clocks,
+        }
+        print(json.dumps(out), flush=True)
+    for g in geoms:
+        g.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -213,6 +213,24 @@ ibdl_status ibdl_get_geometry_info(ibdl_geometry g, ibdl_geometry_info* info);
  * (all handles, all streams). */
 int64_t ibdl_kernel_launch_count(void);
 
+/* Kernel timing (off by default).  While on, every launch of this library is
+ * bracketed by a pair of CUDA events recorded on its own stream; the pairs
+ * are resolved by ibdl_profile_read.  The events add a few microseconds of
+ * host work per launch, so time end-to-end figures with profiling off. */
+void ibdl_profile_enable(int32_t on);
+
+typedef struct {
+  char name[48];       /* kernel family, e.g. "rows_fwd_f64", "pencils_solve_f32" */
+  int64_t launches;
+  double total_ms;     /* summed event-measured duration */
+} ibdl_kernel_stat;
+
+/* Synchronises the device, folds all pending event pairs into per-kernel
+ * totals and copies up to max_out entries (sorted by name) to out (may be
+ * NULL).  Returns the number of kernel families recorded; reset != 0 clears
+ * the totals afterwards. */
+int32_t ibdl_profile_read(ibdl_kernel_stat* out, int32_t max_out, int32_t reset);
+
 const char* ibdl_status_string(ibdl_status s);
 const char* ibdl_last_error_message(void);
 int32_t ibdl_version(void); /* 100 * MAJOR + MINOR */

@@ -13,6 +13,8 @@
 #include <string.h>
 
 #include <atomic>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -21,7 +23,52 @@
 namespace ibdl {
 
 static std::atomic<long long> g_launches{0};
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// Opt-in kernel timing: a CUDA event pair on the launching stream around
+// every launch, resolved when the statistics are read.
+struct ProfPending {
+  const char* name;
+  cudaEvent_t a, b;
+};
+static std::atomic<bool> g_prof{false};
+static std::mutex g_prof_mu;
+static std::vector<ProfPending> g_pending;
+static std::vector<cudaEvent_t> g_ev_pool;
+static std::map<std::string, std::pair<long long, double>> g_prof_stats;
+static thread_local cudaEvent_t t_begin = nullptr;
+
+static cudaEvent_t prof_event() {
+  if (!g_ev_pool.empty()) {
+    cudaEvent_t e = g_ev_pool.back();
+    g_ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+void prof_begin(cudaStream_t st) {
+  if (!g_prof.load(std::memory_order_relaxed)) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  t_begin = prof_event();
+  if (t_begin) cudaEventRecord(t_begin, st);
+}
+
+void count_launch(const char* name, cudaStream_t st) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  if (!g_prof.load(std::memory_order_relaxed) || !t_begin) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  cudaEvent_t e = prof_event();
+  if (!e) return;
+  cudaEventRecord(e, st);
+  g_pending.push_back({name, t_begin, e});
+  t_begin = nullptr;
+}
+
 cudaError_t check_launch() { return cudaGetLastError(); }
 
 static thread_local std::string g_err;
@@ -827,6 +874,38 @@ ibdl_status ibdl_get_geometry_info(ibdl_geometry g, ibdl_geometry_info* info) {
 }
 
 int64_t ibdl_kernel_launch_count(void) { return (int64_t)g_launches.load(); }
+
+void ibdl_profile_enable(int32_t on) { g_prof.store(on != 0); }
+
+int32_t ibdl_profile_read(ibdl_kernel_stat* out, int32_t max_out, int32_t reset) {
+  cudaDeviceSynchronize();
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (const ProfPending& p : g_pending) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      auto& st = g_prof_stats[p.name];
+      st.first += 1;
+      st.second += ms;
+    } else {
+      cudaGetLastError();
+    }
+    g_ev_pool.push_back(p.a);
+    g_ev_pool.push_back(p.b);
+  }
+  g_pending.clear();
+  int32_t k = 0;
+  for (const auto& kv : g_prof_stats) {
+    if (out && k < max_out) {
+      memset(&out[k], 0, sizeof(out[k]));
+      strncpy(out[k].name, kv.first.c_str(), sizeof(out[k].name) - 1);
+      out[k].launches = kv.second.first;
+      out[k].total_ms = kv.second.second;
+    }
+    ++k;
+  }
+  if (reset) g_prof_stats.clear();
+  return k;
+}
 
 const char* ibdl_status_string(ibdl_status s) {
   switch (s) {

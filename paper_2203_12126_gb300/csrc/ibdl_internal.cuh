@@ -77,7 +77,10 @@ struct SpreadSrc {
 };
 
 // ---- launch bookkeeping -------------------------------------------------
-void count_launch();
+// prof_begin records a start event when profiling is on; count_launch counts
+// the launch and records its end event (name must be a string literal).
+void prof_begin(cudaStream_t st);
+void count_launch(const char* name, cudaStream_t st);
 cudaError_t check_launch();
 
 // ---- point kernels (k_points.cu) -----------------------------------------

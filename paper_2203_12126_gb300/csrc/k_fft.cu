@@ -393,11 +393,12 @@ cudaError_t launch_rows_fwd(const GridDesc& g, const PointData& p, const Bins& b
   const int npen = b.rows / 2;
   const size_t smem = rows_smem<T>(g.n, b.rows);
   const int thr = rows_threads(g.n, npen);
+  prof_begin(st);
   if (g.dim == 2)
     k_rows_fwd<T, 2><<<b.ntiles, thr, smem, st>>>(g, p, b, src, ws.spec, ws.tw, write_grid);
   else
     k_rows_fwd<T, 3><<<b.ntiles, thr, smem, st>>>(g, p, b, src, ws.spec, ws.tw, write_grid);
-  count_launch();
+  count_launch(sizeof(T) == 8 ? "rows_fwd_f64" : "rows_fwd_f32", st);
   return check_launch();
 }
 
@@ -407,11 +408,12 @@ cudaError_t launch_rows_inv(const GridDesc& g, const Bins& b, SpectralWs<T>& ws,
   const int npen = b.rows / 2;
   const size_t smem = rows_smem<T>(g.n, b.rows);
   const int thr = rows_threads(g.n, npen);
+  prof_begin(st);
   if (g.dim == 2)
     k_rows_inv<T, 2, OutT><<<b.ntiles, thr, smem, st>>>(g, b, ws.spec, ws.tw, out);
   else
     k_rows_inv<T, 3, OutT><<<b.ntiles, thr, smem, st>>>(g, b, ws.spec, ws.tw, out);
-  count_launch();
+  count_launch(sizeof(T) == 8 ? "rows_inv_f64" : "rows_inv_f32", st);
   return check_launch();
 }
 
@@ -443,8 +445,11 @@ static cudaError_t run_pencils(const GridDesc& g, const PencilLayout& L, Spectra
   const double nd = g.dim == 3 ? (double)g.n * g.n * g.n : (double)g.n * g.n;
   const T cfac = (T)(4.0 * g.kappa / (g.h * g.h));
   const T scale0 = (T)(g.kappa / nd);
+  prof_begin(st);
   k_pencils<T, MODE><<<blocks, thr, smem, st>>>(g, L, ws.spec, ws.tw, ws.s2, cfac, scale0);
-  count_launch();
+  static const char* names[2][3] = {{"pencils_fwd_f32", "pencils_inv_f32", "pencils_solve_f32"},
+                                    {"pencils_fwd_f64", "pencils_inv_f64", "pencils_solve_f64"}};
+  count_launch(names[sizeof(T) == 8 ? 1 : 0][MODE], st);
   return check_launch();
 }
 

@@ -197,26 +197,30 @@ __global__ void k_nonfinite(int m, const double* x, int* flag) {
 cudaError_t krylov_dot_norm(const KrylovWs& k, const double* x, double* out_sq,
                             cudaStream_t st) {
   const int stride = k.restart + 2;
+  prof_begin(st);
   k_dots<<<k.nblk, kBs, 0, st>>>(x, 0, 1, x, k.m, k.partial, stride);
-  count_launch();
+  count_launch("dots", st);
   cudaError_t e = check_launch();
   if (e) return e;
   // reduce the block partials on one block into out_sq[0]
+  prof_begin(st);
   k_normalize<<<1, 32, 0, st>>>(nullptr, 0, k.partial, stride, k.nblk, 0, out_sq);
-  count_launch();
+  count_launch("normalize", st);
   return check_launch();
 }
 
 cudaError_t krylov_start(const KrylovWs& k, const double* r, double* /*unused*/,
                          cudaStream_t st) {
   const int stride = k.restart + 2;
+  prof_begin(st);
   k_dots<<<k.nblk, kBs, 0, st>>>(r, 0, 1, r, k.m, k.partial, stride);
-  count_launch();
+  count_launch("dots", st);
   cudaError_t e = check_launch();
   if (e) return e;
+  prof_begin(st);
   k_start<<<k.nblk, kBs, 0, st>>>(r, k.V, k.m, k.partial, stride, k.gvec, k.restart + 1,
                                   k.scal);
-  count_launch();
+  count_launch("start", st);
   return check_launch();
 }
 
@@ -227,30 +231,36 @@ cudaError_t krylov_arnoldi(const KrylovWs& k, int j, double bnorm, cudaStream_t 
   double* Hcol = k.H + (size_t)j * ldh;
   cudaError_t e;
   for (int pass = 0; pass < 2; ++pass) {
+    prof_begin(st);
     k_dots<<<k.nblk, kBs, 0, st>>>(k.V, k.ld, j + 1, w, k.m, k.partial, stride);
-    count_launch();
+    count_launch("dots", st);
     if ((e = check_launch())) return e;
+    prof_begin(st);
     k_orth_update<<<k.nblk, kBs, 0, st>>>(k.V, k.ld, j + 1, w, k.m, k.partial, stride, Hcol,
                                           pass);
-    count_launch();
+    count_launch("orth_update", st);
     if ((e = check_launch())) return e;
   }
+  prof_begin(st);
   k_normalize<<<k.nblk, kBs, 0, st>>>(w, k.m, k.partial, stride, k.nblk, j + 1, Hcol);
-  count_launch();
+  count_launch("normalize", st);
   if ((e = check_launch())) return e;
+  prof_begin(st);
   k_givens<<<1, 32, 0, st>>>(k.H, ldh, k.cs, k.sn, k.gvec, j, bnorm, k.scal);
-  count_launch();
+  count_launch("givens", st);
   return check_launch();
 }
 
 cudaError_t krylov_finish(const KrylovWs& k, int kdim, double* x, cudaStream_t st) {
   cudaError_t e;
+  prof_begin(st);
   k_backsolve<<<1, 32, 0, st>>>(k.H, k.restart + 1, k.gvec, kdim, k.ysol);
-  count_launch();
+  count_launch("backsolve", st);
   if ((e = check_launch())) return e;
   const int blocks = (k.m + kBs - 1) / kBs;
+  prof_begin(st);
   k_update_x<<<blocks < 1 ? 1 : blocks, kBs, 0, st>>>(k.V, k.ld, kdim, k.ysol, x, k.m);
-  count_launch();
+  count_launch("update_x", st);
   return check_launch();
 }
 
@@ -258,16 +268,18 @@ cudaError_t launch_axpby(int m, double a, const double* x, double b, const doubl
                          double* out, cudaStream_t st) {
   int blocks = (m + 255) / 256;
   if (blocks > 1216) blocks = 1216;
+  prof_begin(st);
   k_axpby<<<blocks < 1 ? 1 : blocks, 256, 0, st>>>(m, a, x, b, y, out);
-  count_launch();
+  count_launch("axpby", st);
   return check_launch();
 }
 
 cudaError_t launch_nonfinite_check(int m, const double* x, int* flag, cudaStream_t st) {
   int blocks = (m + 255) / 256;
   if (blocks > 1216) blocks = 1216;
+  prof_begin(st);
   k_nonfinite<<<blocks < 1 ? 1 : blocks, 256, 0, st>>>(m, x, flag);
-  count_launch();
+  count_launch("nonfinite", st);
   return check_launch();
 }
 

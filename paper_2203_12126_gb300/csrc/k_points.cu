@@ -50,10 +50,11 @@ cudaError_t launch_point_prep(const GridDesc& g, int m, const double* const X[3]
                               int* const base[3], double* const W64[3],
                               float* const W32[3], cudaStream_t st) {
   const int bs = 256;
+  prof_begin(st);
   k_point_prep<<<(m + bs - 1) / bs, bs, 0, st>>>(g, m, X[0], X[1], X[2], base[0], base[1],
                                                 base[2], W64[0], W64[1], W64[2], W32[0],
                                                 W32[1], W32[2]);
-  count_launch();
+  count_launch("point_prep", st);
   return check_launch();
 }
 
@@ -138,8 +139,9 @@ cudaError_t launch_bins(const GridDesc& g, const PointData& p, int rows, int nti
   const int bs = 256;
   const int gb = (p.m + bs - 1) / bs;
   if ((e = cudaMemsetAsync(cursor, 0, sizeof(int) * (ntiles + 1), st))) return e;
+  prof_begin(st);
   k_bins<false><<<gb, bs, 0, st>>>(g, p, rows, cursor, nullptr);
-  count_launch();
+  count_launch("bins", st);
   if ((e = check_launch())) return e;
   // counts live in cursor; scan them into start and re-seed cursor
   int* counts = nullptr;
@@ -147,8 +149,9 @@ cudaError_t launch_bins(const GridDesc& g, const PointData& p, int rows, int nti
   if ((e = cudaMemcpyAsync(counts, cursor, sizeof(int) * (ntiles + 1),
                            cudaMemcpyDeviceToDevice, st)))
     return e;
+  prof_begin(st);
   k_scan<<<1, 1024, 0, st>>>(counts, start, cursor, ntiles);
-  count_launch();
+  count_launch("scan", st);
   if ((e = check_launch())) return e;
   int nnz = 0;
   if ((e = cudaMemcpyAsync(&nnz, start + ntiles, sizeof(int), cudaMemcpyDeviceToHost, st)))
@@ -157,11 +160,13 @@ cudaError_t launch_bins(const GridDesc& g, const PointData& p, int rows, int nti
   cudaFreeAsync(counts, st);
   int* pts = nullptr;
   if ((e = cudaMalloc((void**)&pts, sizeof(int) * (nnz > 0 ? nnz : 1)))) return e;
+  prof_begin(st);
   k_bins<true><<<gb, bs, 0, st>>>(g, p, rows, cursor, pts);
-  count_launch();
+  count_launch("bins", st);
   if ((e = check_launch())) return e;
+  prof_begin(st);
   k_bins_sort<<<(ntiles + 127) / 128, 128, 0, st>>>(start, pts, ntiles);
-  count_launch();
+  count_launch("bins_sort", st);
   if ((e = check_launch())) return e;
   *pts_out = pts;
   *nnz_out = nnz;
@@ -238,11 +243,12 @@ cudaError_t launch_interp(const GridDesc& g, const PointData& p, const T* grid,
                           const double* jvec, double jump, double* y, cudaStream_t st) {
   const int bs = 128;
   const int gb = (p.m + bs - 1) / bs;
+  prof_begin(st);
   if (g.dim == 2)
     k_interp<T, 2><<<gb, bs, 0, st>>>(g, p, grid, jvec, jump, y);
   else
     k_interp<T, 3><<<gb, bs, 0, st>>>(g, p, grid, jvec, jump, y);
-  count_launch();
+  count_launch(sizeof(T) == 8 ? "interp_f64" : "interp_f32", st);
   return check_launch();
 }
 
@@ -259,8 +265,9 @@ __global__ void k_to_float(const double* __restrict__ s, float* __restrict__ d, 
 
 cudaError_t launch_grid_to_float(const double* src, float* dst, int64_t count,
                                  cudaStream_t st) {
+  prof_begin(st);
   k_to_float<<<608, 256, 0, st>>>(src, dst, count);
-  count_launch();
+  count_launch("to_float", st);
   return check_launch();
 }
 

@@ -31,7 +31,8 @@ EXPORTS = [
     "ibdl_solve_opts_default", "ibdl_create_geometry", "ibdl_destroy_geometry",
     "ibdl_apply", "ibdl_apply_precision", "ibdl_solve", "ibdl_evaluate",
     "ibdl_spread_div", "ibdl_spread", "ibdl_helmholtz", "ibdl_interp",
-    "ibdl_get_geometry_info", "ibdl_kernel_launch_count", "ibdl_status_string",
+    "ibdl_get_geometry_info", "ibdl_kernel_launch_count", "ibdl_profile_enable",
+    "ibdl_profile_read", "ibdl_status_string",
     "ibdl_last_error_message", "ibdl_version",
 ]
 
@@ -76,6 +77,10 @@ class GeometryInfo(C.Structure):
     ]
 
 
+class KernelStat(C.Structure):
+    _fields_ = [("name", C.c_char * 48), ("launches", C.c_int64), ("total_ms", C.c_double)]
+
+
 class IbdlError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"ibdl status {status}: {msg}")
@@ -109,6 +114,8 @@ def load(path: str = LIB_PATH):
         "ibdl_interp": (C.c_int, [vp, vp, vp, i32, vp]),
         "ibdl_get_geometry_info": (C.c_int, [vp, C.POINTER(GeometryInfo)]),
         "ibdl_kernel_launch_count": (i64, []),
+        "ibdl_profile_enable": (None, [i32]),
+        "ibdl_profile_read": (i32, [C.POINTER(KernelStat), i32, i32]),
         "ibdl_status_string": (C.c_char_p, [C.c_int]),
         "ibdl_last_error_message": (C.c_char_p, []),
         "ibdl_version": (i32, []),
@@ -156,6 +163,21 @@ def _stream(stream):
 
 def kernel_launch_count() -> int:
     return int(load().ibdl_kernel_launch_count())
+
+
+def profile_enable(on: bool = True) -> None:
+    """Bracket every library launch with CUDA events (see ibdl.h)."""
+    load().ibdl_profile_enable(1 if on else 0)
+
+
+def profile_read(reset: bool = True) -> dict:
+    """{kernel family: (launches, total_ms)} from the library's event pairs."""
+    lib = load()
+    k = lib.ibdl_profile_read(None, 0, 0)
+    arr = (KernelStat * max(k, 1))()
+    k = lib.ibdl_profile_read(arr, k, 1 if reset else 0)
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms))
+            for i in range(k)}
 
 
 def version() -> int:

@@ -178,11 +178,13 @@ def test_matvec_host_pointers_match_device_pointers():
     y_dev = torch.empty(g.m, dtype=torch.float64, device=DEV)
     G.apply(gpu(q), y_dev)
     torch.cuda.synchronize()
-    assert np.array_equal(y_host, host(y_dev))
+    # the spread accumulates with shared-memory atomics, so two applications
+    # agree to rounding, not bit for bit
+    assert rel(y_host, host(y_dev)) <= 1e-14
     pinned = torch.tensor(q).pin_memory()
     y_pin = torch.zeros(g.m, dtype=torch.float64).pin_memory()
     G.apply(pinned, y_pin)
-    assert np.array_equal(y_pin.numpy(), y_host)
+    assert rel(y_pin.numpy(), y_host) <= 1e-14
     G.close()
 
 
@@ -317,7 +319,8 @@ def test_c1_solve_against_closed_form():
     u = torch.empty((p.geom.n,) * 2, dtype=torch.float64, device=DEV)
     G.evaluate(q, u)
     P = configs.grid_nodes(p.geom)
-    mask = configs.interior_mask_circle(p.geom, 0.3, 0)
+    # L1 error over the nodes of Omega farther than 6h from Gamma
+    mask = configs.interior_mask_circle(p.geom, 0.3, 6 * p.geom.h)
     err = np.mean(np.abs(host(u).reshape(-1)[mask] - p.exact(P)[mask]))
     assert err < 5e-3
     G.close()
