@@ -231,6 +231,31 @@ typedef struct {
  * the totals afterwards. */
 int32_t ibdl_profile_read(ibdl_kernel_stat* out, int32_t max_out, int32_t reset);
 
+/* Allocation-free variant of ibdl_helmholtz for callers that cannot
+ * allocate device memory (for example code running inside a host callback
+ * or a plugin whose host application owns all device allocations, where a
+ * cudaMalloc is forbidden or would deadlock).  The paper has no counterpart:
+ * it is a deployment variant of the periodic solve of Sec. 5.1.
+ *
+ * Computes v_out = kappa L'^{-1} f on an n x n periodic grid of spacing
+ * h = box_len / n (L' = I - kappa Delta_h, 5-point stencil), float64, exactly
+ * as ibdl_helmholtz does, without a geometry handle.  f and v_out are n*n
+ * float64 values in DEVICE memory (x fastest) and may alias.  n must be a
+ * power of two in [16, 512]; larger n returns IBDL_ERR_INVALID_ARG.
+ *
+ * Scratch: one file-scope __device__ array of about 2.1 MB (a 512 x 512
+ * half spectrum, twiddle and symbol tables) that every GPU loading the
+ * library holds until the process exits.  The call allocates nothing and
+ * calls no allocating routine.  The first call on a device looks up the
+ * array's device address with cudaGetSymbolAddress (with that device
+ * current); make that first call before any stream capture.  Every call
+ * shares the array and rewrites the parts it reads (tables, tile lists,
+ * spectrum), so calls that overlap on the GPU -- on different streams or
+ * from different host threads -- race and must be serialised by the caller.
+ * Asynchronous on `stream`. */
+ibdl_status ibdl_helmholtz_2d_noalloc(int32_t n, double box_len, double kappa,
+                                      const double* f, double* v_out, void* stream);
+
 const char* ibdl_status_string(ibdl_status s);
 const char* ibdl_last_error_message(void);
 int32_t ibdl_version(void); /* 100 * MAJOR + MINOR */

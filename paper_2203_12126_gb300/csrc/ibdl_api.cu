@@ -78,6 +78,8 @@ static ibdl_status fail(ibdl_status s, const std::string& msg) {
   return s;
 }
 
+ibdl_status set_last_error(ibdl_status s, const char* msg) { return fail(s, msg); }
+
 static ibdl_status cuda_fail(cudaError_t e, const char* where) {
   g_err = std::string(where) + ": " + cudaGetErrorString(e);
   return e == cudaErrorMemoryAllocation ? IBDL_ERR_OOM : IBDL_ERR_CUDA;

@@ -82,6 +82,8 @@ struct SpreadSrc {
 void prof_begin(cudaStream_t st);
 void count_launch(const char* name, cudaStream_t st);
 cudaError_t check_launch();
+// Sets the per-thread message of ibdl_last_error_message and returns s.
+ibdl_status set_last_error(ibdl_status s, const char* msg);
 
 // ---- point kernels (k_points.cu) -----------------------------------------
 cudaError_t launch_point_prep(const GridDesc& g, int m, const double* const X[3],

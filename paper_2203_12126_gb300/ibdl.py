@@ -33,7 +33,7 @@ EXPORTS = [
     "ibdl_spread_div", "ibdl_spread", "ibdl_helmholtz", "ibdl_interp",
     "ibdl_get_geometry_info", "ibdl_kernel_launch_count", "ibdl_profile_enable",
     "ibdl_profile_read", "ibdl_status_string",
-    "ibdl_last_error_message", "ibdl_version",
+    "ibdl_last_error_message", "ibdl_version", "ibdl_helmholtz_2d_noalloc",
 ]
 
 
@@ -119,6 +119,7 @@ def load(path: str = LIB_PATH):
         "ibdl_status_string": (C.c_char_p, [C.c_int]),
         "ibdl_last_error_message": (C.c_char_p, []),
         "ibdl_version": (i32, []),
+        "ibdl_helmholtz_2d_noalloc": (C.c_int, [i32, C.c_double, C.c_double, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -178,6 +179,15 @@ def profile_read(reset: bool = True) -> dict:
     k = lib.ibdl_profile_read(arr, k, 1 if reset else 0)
     return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms))
             for i in range(k)}
+
+
+def helmholtz_2d_noalloc(n, box_len, kappa, f, v_out, stream=None):
+    """v_out = kappa L'^{-1} f on an n x n periodic grid without any device
+    allocation (for callers that cannot allocate; device arrays only, n <= 512;
+    overlapping calls race on the library's shared scratch)."""
+    _check(load().ibdl_helmholtz_2d_noalloc(int(n), float(box_len), float(kappa), _ptr(f),
+                                            _ptr(v_out), _stream(stream)))
+    return v_out
 
 
 def version() -> int:
