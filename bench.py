@@ -51,6 +51,19 @@ def parse():
     return ap.parse_args()
 
 
+def combine_ranks(local_ms, local_solves, dist=None, device=None):
+    """Whole-job aggregate over ranks: the slowest rank's timed duration and
+    the sum of all ranks' solves (independent replicas, no data exchange)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return local_ms, local_solves
+    import torch
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    s = torch.tensor([float(local_solves)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(s, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(s.item())
+
+
 def problems():
     return [configs.c2(bc=configs.DIRICHLET), configs.c2(bc=configs.NEUMANN)]
 
@@ -277,12 +290,7 @@ def main():
         dist.barrier()
     clocks = sampler.stop()
     lat = [a.elapsed_time(b) for a, b in ev]
-    total_ms = float(sum(lat))
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    solves = args.steps * len(probs) * world
+    total_ms, solves = combine_ranks(float(sum(lat)), args.steps * len(probs), dist, dev)
     value = solves / (total_ms / 1e3)
 
     # ---- accuracy of the timed path against a float64 GPU solve at 1e-12
