@@ -111,6 +111,10 @@ typedef struct {
   int32_t restart;      /* GMRES(restart), 1..64; default 30 */
   int32_t max_iters;    /* total inner iterations; default 500 */
   int32_t max_refine;   /* outer refinement steps (FP32_REFINED); default 8 */
+  int32_t engine;       /* 0 (default): the whole solve in one persistent
+                           cooperative kernel launch, no host round trip per
+                           iteration; 1: host-driven loop of per-pass kernels
+                           with a residual read-back per iteration */
   double inner_tol;     /* FP32_REFINED: relative tolerance of each inner
                            solve; default 1e-5 */
   const double* x0;     /* optional initial guess (length m), or NULL */
@@ -180,6 +184,28 @@ ibdl_status ibdl_solve(ibdl_geometry g, const double* bdata, const double* g_gri
  * (also for FP32_REFINED geometries). */
 ibdl_status ibdl_evaluate(ibdl_geometry g, const double* q, const double* vb,
                           const double* g_grid, double* u_out, void* stream);
+
+/* Batched solves (many independent problems in one launch).  A batch object
+ * owns the device descriptors of up to `capacity` (1..512) instances.
+ * ibdl_solve_batched solves geoms[k] with data bdata[k] (U_b or V_b, g = 0)
+ * into q_out[k] for k < count, all in ONE persistent cooperative kernel
+ * launch: every instance runs the same state machine as ibdl_solve (float64
+ * GMRES, or float32 GMRES cycles inside float64 residual refinement, by each
+ * geometry's precision), and each phase deals the work items of all active
+ * instances (grid tiles, pencils, vector chunks) to the resident blocks, so
+ * instances of different n, m, kappa, bc and precision advance together and
+ * finished ones drop out.  A geometry may appear once per call (its
+ * workspaces hold that instance's state).  Synchronises `stream`.
+ * statuses/infos (arrays of `count`, may be NULL) receive per-instance
+ * results; the return value is IBDL_OK when every instance converged, else
+ * the first failing instance's status. */
+typedef struct ibdl_batch_s* ibdl_batch;
+ibdl_status ibdl_batch_create(int32_t capacity, ibdl_batch* out);
+void ibdl_batch_destroy(ibdl_batch b);
+ibdl_status ibdl_solve_batched(ibdl_batch b, int32_t count, const ibdl_geometry* geoms,
+                               const double* const* bdata, double* const* q_out,
+                               const ibdl_solve_opts* opts, ibdl_solve_info* infos,
+                               ibdl_status* statuses, void* stream);
 
 /* Component operators, exposed for testing and for callers that compose
  * their own solvers.  All float64 unless `precision` = 1.

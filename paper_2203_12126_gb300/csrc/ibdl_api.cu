@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "ibdl_internal.cuh"
+#include "ibdl_solver.cuh"
 
 namespace ibdl {
 
@@ -125,6 +126,17 @@ struct ibdl_geometry_s {
   double* grid_stage = nullptr;   // n^d doubles, allocated on first host grid
   double* host_scal = nullptr;    // pinned
   int* d_flag = nullptr;
+  // persistent solver context
+  SolveInst* d_inst = nullptr;
+  SolveState* d_state = nullptr;
+  unsigned* d_bar = nullptr;
+  double* ppart = nullptr;
+  double* d_hist = nullptr;
+  int nchunk = 0;
+  int solver_smem = 0;
+  SolveInst* h_inst = nullptr;    // pinned
+  SolveState* h_state = nullptr;  // pinned
+  double* h_hist = nullptr;       // pinned
   int64_t bytes = 0;
   int64_t ncells = 0;
   std::vector<void*> dev_allocs;
@@ -144,6 +156,9 @@ struct ibdl_geometry_s {
     for (void* p : dev_allocs) cudaFree(p);
     if (bins.pts) cudaFree((void*)bins.pts);
     if (host_scal) cudaFreeHost(host_scal);
+    if (h_inst) cudaFreeHost(h_inst);
+    if (h_state) cudaFreeHost(h_state);
+    if (h_hist) cudaFreeHost(h_hist);
   }
 };
 
@@ -364,6 +379,62 @@ ibdl_status gmres(ibdl_geometry_s* g, int prec, const double* b, double* x, bool
   return IBDL_OK;
 }
 
+constexpr int kHistCap = 256;
+
+SolveInst make_inst(ibdl_geometry_s* g, const ibdl_solve_opts& o) {
+  SolveInst I;
+  memset(&I, 0, sizeof(I));
+  I.g = g->grid;
+  I.p = g->pd;
+  I.b = g->bins;
+  I.w64 = g->ws64;
+  I.w32 = g->ws32;
+  I.V = g->kry.V;
+  I.ld = g->kry.ld;
+  I.restart = o.restart;
+  I.H = g->kry.H;
+  I.cs = g->kry.cs;
+  I.sn = g->kry.sn;
+  I.gv = g->kry.gvec;
+  I.ysol = g->kry.ysol;
+  I.part = g->ppart;
+  I.nchunk = g->nchunk;
+  I.pstride = g->kry.restart + 2;
+  I.bvec = g->vb;
+  I.x = g->vx;
+  I.r = g->vr;
+  I.bc = g->bc;
+  I.refined = g->precision == IBDL_FP32_REFINED;
+  I.maxit = o.max_iters;
+  I.max_refine = o.max_refine;
+  I.tol = o.tol;
+  I.inner_tol = o.inner_tol;
+  I.hist = g->d_hist;
+  I.hist_cap = kHistCap;
+  return I;
+}
+
+SolveState initial_state(bool x_zero) {
+  SolveState s;
+  memset(&s, 0, sizeof(s));
+  s.action = x_zero ? ACT_RESID_ZERO : ACT_MV_RESIDUAL;
+  s.status = IBDL_ERR_NOT_CONVERGED;
+  s.bnorm = -1.0;
+  return s;
+}
+
+void info_from_state(const SolveState& st, const double* hist, ibdl_solve_info* info) {
+  if (!info) return;
+  memset(info, 0, sizeof(*info));
+  info->iters = st.iters;
+  info->refine_steps = st.outer;
+  info->matvecs = st.matvecs;
+  info->rel_residual = st.rel;
+  const int nh = st.nhist < 256 ? st.nhist : 256;
+  info->n_history = nh;
+  for (int i = 0; i < nh; ++i) info->residual_history[i] = hist[i];
+}
+
 ibdl_status vec_norm(ibdl_geometry_s* g, const double* v, double* out, cudaStream_t st) {
   IBDL_CU(krylov_dot_norm(g->kry, v, g->kry.scal + 4, st));
   cudaError_t ce;
@@ -391,6 +462,7 @@ void ibdl_solve_opts_default(ibdl_solve_opts* o) {
   o->restart = 30;
   o->max_iters = 500;
   o->max_refine = 8;
+  o->engine = 0;
   o->inner_tol = 1e-5;
   o->x0 = nullptr;
 }
@@ -559,6 +631,19 @@ ibdl_status ibdl_create_geometry(const ibdl_geometry_desc* d, void* stream, ibdl
   g->stage_a = vecs + 5 * (size_t)k.ld;
   g->stage_b = vecs + 6 * (size_t)k.ld;
   if ((s = g->alloc(&g->d_flag, (size_t)4))) return cleanup(s);
+  g->nchunk = (m + kSolverThreads - 1) / kSolverThreads;
+  if ((s = g->alloc(&g->ppart, (size_t)3 * g->nchunk * (k.restart + 2)))) return cleanup(s);
+  if ((s = g->alloc(&g->d_hist, (size_t)kHistCap))) return cleanup(s);
+  if ((s = g->alloc(&g->d_inst, (size_t)1))) return cleanup(s);
+  if ((s = g->alloc(&g->d_state, (size_t)1))) return cleanup(s);
+  if ((s = g->alloc(&g->d_bar, (size_t)4))) return cleanup(s);
+  {
+    cudaError_t e = cudaMallocHost((void**)&g->h_inst, sizeof(SolveInst));
+    if (!e) e = cudaMallocHost((void**)&g->h_state, sizeof(SolveState));
+    if (!e) e = cudaMallocHost((void**)&g->h_hist, kHistCap * sizeof(double));
+    if (e) return cleanup(cuda_fail(e, "cudaMallocHost"));
+  }
+  g->solver_smem = solver_smem_bytes(gd, 1);
   {
     cudaError_t e = cudaMallocHost((void**)&g->host_scal, 16 * sizeof(double));
     if (e) return cleanup(cuda_fail(e, "cudaMallocHost"));
@@ -613,6 +698,7 @@ ibdl_status ibdl_solve(ibdl_geometry g, const double* bdata, const double* g_gri
   if (o.max_iters < 1) return fail(IBDL_ERR_INVALID_ARG, "max_iters >= 1");
   if (o.max_refine < 1) o.max_refine = 1;
   if (!(o.inner_tol > 0) || o.inner_tol >= 1) o.inner_tol = 1e-5;
+  if (o.engine != 0 && o.engine != 1) return fail(IBDL_ERR_INVALID_ARG, "engine is 0 or 1");
   cudaStream_t st = (cudaStream_t)stream;
   const int m = g->m;
   // inputs
@@ -629,6 +715,32 @@ ibdl_status ibdl_solve(ibdl_geometry g, const double* bdata, const double* g_gri
     x_zero = false;
   } else {
     IBDL_CU(cudaMemsetAsync(g->vx, 0, sizeof(double) * m, st));
+  }
+  if (o.engine == 0) {
+    // one persistent launch runs the whole solve; the host waits once
+    *g->h_inst = make_inst(g, o);
+    *g->h_state = initial_state(x_zero);
+    IBDL_CU(cudaMemcpyAsync(g->d_inst, g->h_inst, sizeof(SolveInst), cudaMemcpyHostToDevice, st));
+    IBDL_CU(cudaMemcpyAsync(g->d_state, g->h_state, sizeof(SolveState), cudaMemcpyHostToDevice,
+                            st));
+    IBDL_CU(launch_persistent_solve(g->d_inst, g->d_state, 1, g->d_bar, g->solver_smem, st));
+    IBDL_CU(cudaMemcpyAsync(g->h_state, g->d_state, sizeof(SolveState), cudaMemcpyDeviceToHost,
+                            st));
+    IBDL_CU(cudaMemcpyAsync(g->h_hist, g->d_hist, kHistCap * sizeof(double),
+                            cudaMemcpyDeviceToHost, st));
+    unsigned* hb = reinterpret_cast<unsigned*>(g->host_scal + 8);
+    IBDL_CU(cudaMemcpyAsync(hb, g->d_bar, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    int* hflag = reinterpret_cast<int*>(g->host_scal + 10);
+    IBDL_CU(cudaMemcpyAsync(hflag, g->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    IBDL_CU(cudaMemcpyAsync(q_out, g->vx, sizeof(double) * m, cudaMemcpyDefault, st));
+    IBDL_CU(cudaStreamSynchronize(st));
+    info_from_state(*g->h_state, g->h_hist, info);
+    if (*hflag) return fail(IBDL_ERR_NONFINITE, "non-finite boundary data or initial guess");
+    if (hb[2]) return fail(IBDL_ERR_TIMEOUT, "persistent solver: a grid barrier timed out");
+    const int stt = g->h_state->status;
+    if (stt == IBDL_ERR_NOT_CONVERGED) return fail(IBDL_ERR_NOT_CONVERGED, "GMRES reached max_iters");
+    if (stt == IBDL_ERR_NONFINITE) return fail(IBDL_ERR_NONFINITE, "non-finite residual");
+    return (ibdl_status)stt;
   }
   int flag = 0;
   IBDL_CU(cudaMemcpyAsync(&flag, g->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -872,6 +984,111 @@ ibdl_status ibdl_get_geometry_info(ibdl_geometry g, ibdl_geometry_info* info) {
   info->precision = g->precision;
   info->device_bytes = g->bytes;
   info->fft_passes = fft_kernels_per_solve<double>(g->grid.dim);
+  return IBDL_OK;
+}
+
+
+struct ibdl_batch_s {
+  int cap = 0;
+  SolveInst* d_inst = nullptr;
+  SolveState* d_state = nullptr;
+  unsigned* d_bar = nullptr;
+  SolveInst* h_inst = nullptr;
+  SolveState* h_state = nullptr;
+  ~ibdl_batch_s() {
+    if (d_inst) cudaFree(d_inst);
+    if (d_state) cudaFree(d_state);
+    if (d_bar) cudaFree(d_bar);
+    if (h_inst) cudaFreeHost(h_inst);
+    if (h_state) cudaFreeHost(h_state);
+  }
+};
+
+ibdl_status ibdl_batch_create(int32_t capacity, ibdl_batch* out) {
+  g_err.clear();
+  if (!out) return fail(IBDL_ERR_INVALID_ARG, "NULL out");
+  if (capacity < 1 || capacity > kMaxBatch)
+    return fail(IBDL_ERR_INVALID_ARG, "capacity must be in [1, 512]");
+  ibdl_batch_s* b = new ibdl_batch_s();
+  b->cap = capacity;
+  cudaError_t e = cudaMalloc((void**)&b->d_inst, sizeof(SolveInst) * capacity);
+  if (!e) e = cudaMalloc((void**)&b->d_state, sizeof(SolveState) * capacity);
+  if (!e) e = cudaMalloc((void**)&b->d_bar, 4 * sizeof(unsigned));
+  if (!e) e = cudaMallocHost((void**)&b->h_inst, sizeof(SolveInst) * capacity);
+  if (!e) e = cudaMallocHost((void**)&b->h_state, sizeof(SolveState) * capacity);
+  if (e) {
+    delete b;
+    return cuda_fail(e, "ibdl_batch_create");
+  }
+  *out = b;
+  return IBDL_OK;
+}
+
+void ibdl_batch_destroy(ibdl_batch b) {
+  if (!b) return;
+  cudaDeviceSynchronize();
+  delete b;
+}
+
+ibdl_status ibdl_solve_batched(ibdl_batch b, int32_t count, const ibdl_geometry* geoms,
+                               const double* const* bdata, double* const* q_out,
+                               const ibdl_solve_opts* opts_in, ibdl_solve_info* infos,
+                               ibdl_status* statuses, void* stream) {
+  g_err.clear();
+  if (!b || !geoms || !bdata || !q_out) return fail(IBDL_ERR_INVALID_ARG, "NULL argument");
+  if (count < 1 || count > b->cap) return fail(IBDL_ERR_INVALID_ARG, "count out of range");
+  ibdl_solve_opts o;
+  ibdl_solve_opts_default(&o);
+  if (opts_in) o = *opts_in;
+  if (!(o.tol > 0) || !isfinite(o.tol)) return fail(IBDL_ERR_INVALID_ARG, "tol must be > 0");
+  if (o.restart < 1 || o.restart > 64) return fail(IBDL_ERR_INVALID_ARG, "restart in 1..64");
+  if (o.max_iters < 1) return fail(IBDL_ERR_INVALID_ARG, "max_iters >= 1");
+  if (o.max_refine < 1) o.max_refine = 1;
+  if (!(o.inner_tol > 0) || o.inner_tol >= 1) o.inner_tol = 1e-5;
+  for (int k = 0; k < count; ++k) {
+    if (!geoms[k] || !bdata[k] || !q_out[k])
+      return fail(IBDL_ERR_INVALID_ARG, "NULL geometry, bdata or q_out entry");
+    for (int l = 0; l < k; ++l)
+      if (geoms[l] == geoms[k])
+        return fail(IBDL_ERR_INVALID_ARG, "a geometry handle appears twice in one batch");
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  int smem = 0;
+  for (int k = 0; k < count; ++k) {
+    ibdl_geometry g = geoms[k];
+    IBDL_CU(cudaMemcpyAsync(g->stage_a, bdata[k], sizeof(double) * g->m, cudaMemcpyDefault, st));
+    IBDL_TRY(build_rhs(g, g->stage_a, nullptr, g->vb, st));
+    IBDL_CU(cudaMemsetAsync(g->vx, 0, sizeof(double) * g->m, st));
+    b->h_inst[k] = make_inst(g, o);
+    b->h_state[k] = initial_state(true);
+    if (g->solver_smem > smem) smem = g->solver_smem;
+  }
+  IBDL_CU(cudaMemcpyAsync(b->d_inst, b->h_inst, sizeof(SolveInst) * count,
+                          cudaMemcpyHostToDevice, st));
+  IBDL_CU(cudaMemcpyAsync(b->d_state, b->h_state, sizeof(SolveState) * count,
+                          cudaMemcpyHostToDevice, st));
+  IBDL_CU(launch_persistent_solve(b->d_inst, b->d_state, count, b->d_bar, smem, st));
+  IBDL_CU(cudaMemcpyAsync(b->h_state, b->d_state, sizeof(SolveState) * count,
+                          cudaMemcpyDeviceToHost, st));
+  for (int k = 0; k < count; ++k) {
+    ibdl_geometry g = geoms[k];
+    if (infos)
+      IBDL_CU(cudaMemcpyAsync(g->h_hist, g->d_hist, kHistCap * sizeof(double),
+                              cudaMemcpyDeviceToHost, st));
+    IBDL_CU(cudaMemcpyAsync(q_out[k], g->vx, sizeof(double) * g->m, cudaMemcpyDefault, st));
+  }
+  unsigned hb[4] = {0, 0, 0, 0};
+  IBDL_CU(cudaMemcpyAsync(hb, b->d_bar, sizeof(hb), cudaMemcpyDeviceToHost, st));
+  IBDL_CU(cudaStreamSynchronize(st));
+  if (hb[2]) return fail(IBDL_ERR_TIMEOUT, "persistent solver: a grid barrier timed out");
+  ibdl_status worst = IBDL_OK;
+  for (int k = 0; k < count; ++k) {
+    const ibdl_status sk = (ibdl_status)b->h_state[k].status;
+    if (statuses) statuses[k] = sk;
+    if (infos) info_from_state(b->h_state[k], geoms[k]->h_hist, &infos[k]);
+    if (sk != IBDL_OK && worst == IBDL_OK) worst = sk;
+  }
+  if (worst != IBDL_OK) return fail(worst, "at least one instance did not converge");
   return IBDL_OK;
 }
 

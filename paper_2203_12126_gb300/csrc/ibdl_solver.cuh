@@ -1,0 +1,63 @@
+// Descriptors of the persistent GMRES solver (k_solver.cu).
+#pragma once
+
+#include "ibdl_internal.cuh"
+
+namespace ibdl {
+
+constexpr int kSolverThreads = 512;  // threads per block; also the vector chunk
+constexpr int kMaxBatch = 512;       // instances per persistent launch
+
+enum SolveAction {
+  ACT_DONE = 0,
+  ACT_RESID_ZERO = 1,   // r = b (x = 0)
+  ACT_MV_RESIDUAL = 2,  // r = b - A64 x
+  ACT_MV_ARNOLDI = 3,   // Arnoldi step j
+  ACT_FINISH = 4        // back substitution, x += V y
+};
+
+// Read-only during a launch.
+struct SolveInst {
+  GridDesc g;
+  PointData p;
+  Bins b;
+  SpectralWs<double> w64;
+  SpectralWs<float> w32;
+  double* V;        // (restart + 1) x ld
+  int ld;
+  int restart;
+  double* H;        // column j at H + j * (restart + 1)
+  double* cs;
+  double* sn;
+  double* gv;       // restart + 1
+  double* ysol;     // restart
+  double* part;     // 3 sections x nchunk x pstride
+  int nchunk;
+  int pstride;
+  const double* bvec;
+  double* x;
+  double* r;
+  int bc;
+  int refined;
+  int maxit;
+  int max_refine;
+  double tol;
+  double inner_tol;
+  double* hist;
+  int hist_cap;
+  int pad;
+};
+
+// Mutable; written by the instance's control thread.
+struct SolveState {
+  int action, prec, j, kdim;
+  int iters, outer, status, matvecs;
+  int nhist, pad;
+  double beta, bnorm, tol_abs, rel;
+};
+
+int solver_smem_bytes(const GridDesc& g, int need32);
+cudaError_t launch_persistent_solve(const SolveInst* d_insts, SolveState* d_states, int ninst,
+                                    unsigned* d_bar, int smem, cudaStream_t st);
+
+}  // namespace ibdl

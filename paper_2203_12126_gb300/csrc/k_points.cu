@@ -6,7 +6,7 @@
 // point reads the 4^d nodes base_c + t (t = 0..3) with weights prod_c W[c][t].
 #include <math.h>
 
-#include "ibdl_internal.cuh"
+#include "ibdl_device.cuh"
 
 namespace ibdl {
 
@@ -175,65 +175,13 @@ cudaError_t launch_bins(const GridDesc& g, const PointData& p, int rows, int nti
 
 // ---- interpolation ------------------------------------------------------------
 
-template <typename T> __device__ __forceinline__ const T* wtab(const PointData& p, int c);
-template <> __device__ __forceinline__ const double* wtab<double>(const PointData& p, int c) {
-  return p.W64[c];
-}
-template <> __device__ __forceinline__ const float* wtab<float>(const PointData& p, int c) {
-  return p.W32[c];
-}
-
-// y_i = sum over the 4^d taps of grid * prod W  (+ jump * jvec_i).
+// y_i = S* grid at X_i (+ jump * jvec_i).
 template <typename T, int D>
-__global__ void __launch_bounds__(128) k_interp(GridDesc g, PointData p,
-                                                const T* __restrict__ grid,
-                                                const double* __restrict__ jvec,
-                                                double jump, double* __restrict__ y) {
+__global__ void __launch_bounds__(128) k_interp(GridDesc g, PointData p, const T* grid,
+                                                const double* jvec, double jump, double* y) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= p.m) return;
-  const int n = g.n, mask = n - 1, m = p.m;
-  T wx[4], wy[4], wz[4];
-  const T* Wx = wtab<T>(p, 0);
-  const T* Wy = wtab<T>(p, 1);
-#pragma unroll
-  for (int t = 0; t < 4; ++t) {
-    wx[t] = Wx[t * m + i];
-    wy[t] = Wy[t * m + i];
-  }
-  int col[4];
-  const int bx = p.base[0][i], by = p.base[1][i];
-#pragma unroll
-  for (int t = 0; t < 4; ++t) col[t] = (bx + t) & mask;
-  T acc = 0;
-  if (D == 2) {
-#pragma unroll
-    for (int ty = 0; ty < 4; ++ty) {
-      const T* row = grid + (size_t)((by + ty) & mask) * n;
-      T r = 0;
-#pragma unroll
-      for (int tx = 0; tx < 4; ++tx) r += row[col[tx]] * wx[tx];
-      acc += r * wy[ty];
-    }
-  } else {
-    const T* Wz = wtab<T>(p, 2);
-#pragma unroll
-    for (int t = 0; t < 4; ++t) wz[t] = Wz[t * m + i];
-    const int bz = p.base[2][i];
-    for (int tz = 0; tz < 4; ++tz) {
-      const T* plane = grid + (size_t)((bz + tz) & mask) * n * n;
-      T pz = 0;
-#pragma unroll
-      for (int ty = 0; ty < 4; ++ty) {
-        const T* row = plane + (size_t)((by + ty) & mask) * n;
-        T r = 0;
-#pragma unroll
-        for (int tx = 0; tx < 4; ++tx) r += row[col[tx]] * wx[tx];
-        pz += r * wy[ty];
-      }
-      acc += pz * wz[tz];
-    }
-  }
-  double out = (double)acc;
+  double out = (double)interp_point<T, D>(g, p, grid, i);
   if (jvec) out += jump * jvec[i];
   y[i] = out;
 }

@@ -34,6 +34,7 @@ EXPORTS = [
     "ibdl_get_geometry_info", "ibdl_kernel_launch_count", "ibdl_profile_enable",
     "ibdl_profile_read", "ibdl_status_string",
     "ibdl_last_error_message", "ibdl_version", "ibdl_helmholtz_2d_noalloc",
+    "ibdl_batch_create", "ibdl_batch_destroy", "ibdl_solve_batched",
 ]
 
 
@@ -51,7 +52,8 @@ class GeometryDesc(C.Structure):
 class SolveOpts(C.Structure):
     _fields_ = [
         ("tol", C.c_double), ("restart", C.c_int32), ("max_iters", C.c_int32),
-        ("max_refine", C.c_int32), ("inner_tol", C.c_double), ("x0", C.c_void_p),
+        ("max_refine", C.c_int32), ("engine", C.c_int32), ("inner_tol", C.c_double),
+        ("x0", C.c_void_p),
     ]
 
 
@@ -120,6 +122,11 @@ def load(path: str = LIB_PATH):
         "ibdl_last_error_message": (C.c_char_p, []),
         "ibdl_version": (i32, []),
         "ibdl_helmholtz_2d_noalloc": (C.c_int, [i32, C.c_double, C.c_double, vp, vp, vp]),
+        "ibdl_batch_create": (C.c_int, [i32, C.POINTER(vp)]),
+        "ibdl_batch_destroy": (None, [vp]),
+        "ibdl_solve_batched": (C.c_int, [vp, i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
+                                         C.POINTER(SolveOpts), C.POINTER(SolveInfo),
+                                         C.POINTER(C.c_int), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -262,11 +269,13 @@ class Geometry:
         return y
 
     def solve(self, bdata, q_out, g_grid=None, tol=1e-8, restart=30, max_iters=500,
-              max_refine=8, inner_tol=1e-5, x0=None, stream=None, raise_on_error=True):
+              max_refine=8, inner_tol=1e-5, x0=None, stream=None, raise_on_error=True,
+              engine=0):
         o = SolveOpts()
         load().ibdl_solve_opts_default(C.byref(o))
         o.tol, o.restart, o.max_iters = float(tol), int(restart), int(max_iters)
         o.max_refine, o.inner_tol, o.x0 = int(max_refine), float(inner_tol), _ptr(x0)
+        o.engine = int(engine)
         info = SolveInfo()
         st = load().ibdl_solve(self._h, _ptr(bdata), _ptr(g_grid), _ptr(q_out), C.byref(o),
                                C.byref(info), _stream(stream))
@@ -300,3 +309,47 @@ class Geometry:
         _check(load().ibdl_interp(self._h, _ptr(u), _ptr(y_out), int(precision),
                                   _stream(stream)))
         return y_out
+
+
+class Batch:
+    """Many IBDL solves in one persistent launch (``ibdl_solve_batched``)."""
+
+    def __init__(self, capacity):
+        h = C.c_void_p()
+        _check(load().ibdl_batch_create(int(capacity), C.byref(h)))
+        self._h = h
+        self.capacity = int(capacity)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().ibdl_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, geoms, bdata, q_out, tol=1e-8, restart=30, max_iters=500, max_refine=8,
+              inner_tol=1e-5, stream=None, raise_on_error=True):
+        n = len(geoms)
+        o = SolveOpts()
+        load().ibdl_solve_opts_default(C.byref(o))
+        o.tol, o.restart, o.max_iters = float(tol), int(restart), int(max_iters)
+        o.max_refine, o.inner_tol = int(max_refine), float(inner_tol)
+        G = (C.c_void_p * n)(*[g._h.value for g in geoms])
+        B = (C.c_void_p * n)(*[_ptr(b) for b in bdata])
+        Q = (C.c_void_p * n)(*[_ptr(q) for q in q_out])
+        infos = (SolveInfo * n)()
+        sts = (C.c_int * n)()
+        st = load().ibdl_solve_batched(self._h, n, G, B, Q, C.byref(o), infos, sts,
+                                       _stream(stream))
+        if raise_on_error:
+            _check(st)
+        out = []
+        for k in range(n):
+            d = infos[k].as_dict()
+            d["status"] = int(sts[k])
+            out.append(d)
+        return out

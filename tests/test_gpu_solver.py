@@ -1,0 +1,153 @@
+"""The persistent single-launch solver (default engine) and the batched
+solver against the host-driven loop, individual solves and the oracle."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import ibdl_oracle as O  # noqa: E402
+from workloads import configs, geometry  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    import paper_2203_12126_gb300 as pkg
+    from paper_2203_12126_gb300 import ibdl
+    DEV = torch.device("cuda:0")
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def gpu(x):
+    return torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device=DEV)
+
+
+def mixed_instances():
+    """Uneven 2D/3D instances: sizes, kappa, bc and precision all differ."""
+    out = []
+    rng = np.random.default_rng(40)
+    specs = [
+        (geometry.star(64, 0.3, 0.15, 4, kappa=1e-2), configs.DIRICHLET, 0),
+        (geometry.star(128, 0.25, 0.2, 6, kappa=3e-3), configs.NEUMANN, 0),
+        (geometry.star(256, 0.3, 0.1, 3, kappa=1e-3), configs.DIRICHLET, 1),
+        (geometry.circle(64, 0.35, center=(-0.25, 1.95), box_len=2.0, origin=(-0.3, 0.1),
+                         kappa=5e-2), configs.NEUMANN, 1),
+        (geometry.sphere(32, 0.3, kappa=1e-2), configs.DIRICHLET, 0),
+        (geometry.ellipsoid(32, (0.3, 0.22, 0.26), kappa=3e-2), configs.NEUMANN, 1),
+        (geometry.circle(16, 0.3, m=7, kappa=1e-1), configs.DIRICHLET, 0),
+    ]
+    for g, bc, prec in specs:
+        out.append((g, bc, prec, rng.standard_normal(g.m)))
+    return out
+
+
+@pytest.mark.parametrize("bc", [configs.DIRICHLET, configs.NEUMANN])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_persistent_engine_matches_host_loop(bc, prec):
+    g = geometry.star(256, 0.3, 0.2, 5, kappa=1e-3)
+    b = np.random.default_rng(1).standard_normal(g.m)
+    G = pkg.Geometry.from_workload(g, bc=bc, precision=prec)
+    q0 = torch.empty(g.m, dtype=torch.float64, device=DEV)
+    q1 = torch.empty_like(q0)
+    i0 = G.solve(gpu(b), q0, tol=1e-10, engine=0)
+    i1 = G.solve(gpu(b), q1, tol=1e-10, engine=1)
+    assert abs(i0["iters"] - i1["iters"]) <= 1
+    assert rel(q0.cpu(), q1.cpu()) <= 1e-8
+    assert i0["rel_residual"] <= 1e-10
+    ref = O.solve(g, bc, b, tol=1e-13).x
+    assert rel(q0.cpu(), ref) <= 1e-8
+    G.close()
+
+
+def test_persistent_solve_c1_tight():
+    p = configs.c1()
+    q_star = O.solve_dense(p.geom, p.bc, p.bdata)
+    G = pkg.Geometry.from_workload(p.geom, bc=p.bc)
+    q = torch.empty(p.geom.m, dtype=torch.float64, device=DEV)
+    info = G.solve(gpu(p.bdata), q, tol=1e-12)
+    assert rel(q.cpu(), q_star) <= 1e-10
+    assert 4 <= info["iters"] <= 8 and info["matvecs"] >= info["iters"]
+    assert len(info["history"]) == info["iters"]
+    G.close()
+
+
+def test_persistent_restarts_and_max_iters():
+    g = geometry.star(128, 0.3, 0.2, 5, kappa=1e-3)
+    b = np.random.default_rng(2).standard_normal(g.m)
+    G = pkg.Geometry.from_workload(g)
+    q = torch.empty(g.m, dtype=torch.float64, device=DEV)
+    info = G.solve(gpu(b), q, tol=1e-12, restart=2)       # many short cycles
+    ref = O.solve(g, configs.DIRICHLET, b, tol=1e-13).x
+    assert rel(q.cpu(), ref) <= 1e-10
+    info = G.solve(gpu(b), q, tol=1e-14, max_iters=3, raise_on_error=False)
+    assert info["status"] == ibdl.ERR_NOT_CONVERGED and info["iters"] == 3
+    G.close()
+
+
+def test_persistent_with_initial_guess():
+    g = geometry.star(128, 0.3, 0.2, 5, kappa=1e-3)
+    b = np.random.default_rng(3).standard_normal(g.m)
+    G = pkg.Geometry.from_workload(g)
+    q = torch.empty(g.m, dtype=torch.float64, device=DEV)
+    G.solve(gpu(b), q, tol=1e-12)
+    q2 = torch.empty_like(q)
+    info = G.solve(gpu(b), q2, tol=1e-10, x0=q.clone())
+    assert info["iters"] == 0 and rel(q2.cpu(), q.cpu()) <= 1e-14
+    G.close()
+
+
+def test_batched_matches_individual_and_oracle():
+    inst = mixed_instances()
+    geoms = [pkg.Geometry.from_workload(g, bc=bc, precision=prec) for g, bc, prec, _ in inst]
+    bs = [gpu(b) for *_, b in inst]
+    qs = [torch.empty(g.m, dtype=torch.float64, device=DEV) for g, *_ in inst]
+    batch = ibdl.Batch(16)
+    infos = batch.solve(geoms, bs, qs, tol=1e-10)
+    for k, (g, bc, prec, b) in enumerate(inst):
+        alone = torch.empty_like(qs[k])
+        ia = geoms[k].solve(bs[k], alone, tol=1e-10)
+        assert infos[k]["status"] == 0
+        # the spread's shared-memory atomics make rounding order vary between
+        # launches, so the two runs agree to the solve tolerance, not bitwise
+        assert abs(infos[k]["iters"] - ia["iters"]) <= 1
+        assert rel(qs[k].cpu(), alone.cpu()) <= (1e-8 if prec else 1e-10)
+        ref = O.solve(g, bc, b, tol=1e-13).x
+        assert rel(qs[k].cpu(), ref) <= (1e-8 if prec else 1e-9), (k, infos[k])
+    batch.close()
+    for G in geoms:
+        G.close()
+
+
+def test_batched_rejects_duplicates_and_overflow():
+    g = geometry.circle(32, 0.3, kappa=1e-2)
+    G = pkg.Geometry.from_workload(g)
+    b = gpu(np.ones(g.m))
+    q = torch.empty_like(b)
+    batch = ibdl.Batch(2)
+    with pytest.raises(ibdl.IbdlError):
+        batch.solve([G, G], [b, b], [q, q])
+    with pytest.raises(ibdl.IbdlError):
+        batch.solve([G, G, G], [b, b, b], [q, q, q])
+    batch.close()
+    G.close()
+
+
+def test_c4_style_batch_of_64():
+    """64 instances from the C4 generator (N in {128, 256}), FP32-refined to
+    1e-8, in one launch: each matches its own solve."""
+    probs = configs.c4_instances(64, seed=2, sizes=(128, 256))
+    geoms = [pkg.Geometry.from_workload(p.geom, precision=1) for p in probs]
+    bs = [gpu(p.bdata) for p in probs]
+    qs = [torch.empty(p.geom.m, dtype=torch.float64, device=DEV) for p in probs]
+    batch = ibdl.Batch(64)
+    infos = batch.solve(geoms, bs, qs, tol=1e-8)
+    for k in (0, 17, 42, 63):
+        ref = torch.empty_like(qs[k])
+        geoms[k].solve(bs[k], ref, tol=1e-12)
+        assert infos[k]["rel_residual"] <= 1e-8
+        assert rel(qs[k].cpu(), ref.cpu()) <= 1e-7
+    batch.close()
+    for G in geoms:
+        G.close()
