@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="CPU work budget of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--engine", type=int, default=0, choices=[0, 1],
+                    help="0: persistent single-launch solver, 1: host-driven loop")
     return ap.parse_args()
 
 
@@ -130,6 +132,10 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 
 def kernel_model(name, n, m):
+    """Algorithmic bytes and flops per launch of a kernel family or solver
+    phase on a 2D n^2 grid with M points (the same passes whether launched
+    alone or as a phase of the persistent solver)."""
+    name = name.replace("phase:", "")
     p = 8 if name.endswith("f64") else 4
     spec = (n // 2 + 1) * n * 2 * p            # half spectrum, complex
     grid = n * n * p
@@ -137,13 +143,24 @@ def kernel_model(name, n, m):
     pts = m * (8 * 4 + 4 * 2 + 8 * 8)          # q, w, normals, base, W per point
     if name.startswith("rows_fwd"):
         return {"bytes": spec + pts, "flops": (n // 2) * fft}
-    if name.startswith("pencils_solve"):
+    if name.startswith("pencils_solve") or name.startswith("solve"):
         return {"bytes": 2 * spec, "flops": (n // 2 + 1) * (2 * fft + 6 * n)}
     if name.startswith("rows_inv"):
         return {"bytes": spec + grid, "flops": (n // 2) * fft}
     if name.startswith("interp"):
         return {"bytes": m * (16 * p + 8 * 3 + 4 * 2 + 8 * p), "flops": m * 40.0}
     return None
+
+
+def matvec_flops(n, m, prec):
+    sfx = "_f64" if prec == 64 else "_f32"
+    return sum(kernel_model(k + sfx, n, m)["flops"] for k in ("rows_fwd", "solve", "rows_inv"))
+
+
+def matvec_bytes(n, m, prec):
+    sfx = "_f64" if prec == 64 else "_f32"
+    return sum(kernel_model(k + sfx, n, m)["bytes"]
+               for k in ("rows_fwd", "solve", "rows_inv", "interp"))
 
 
 def load_peaks():
@@ -256,7 +273,7 @@ def main():
 
     def solve(i, b=None, q=None):
         return geoms[i].solve(bs[i] if b is None else b, qs[i] if q is None else q,
-                              tol=args.tol)
+                              tol=args.tol, engine=args.engine)
 
     for _ in range(args.warmup):
         for i in range(len(probs)):
@@ -302,36 +319,75 @@ def main():
         errs.append(float(torch.linalg.norm(qs[i] - q64) / torch.linalg.norm(q64)))
         g64.close()
 
-    # ---- profiled pass: per-kernel event durations -> dominant kernel roofline
+    # ---- profiled pass: per-kernel CUDA-event durations (library event pairs
+    # on the launching stream) and, inside the persistent solver, per-phase
+    # wall times from the device's global timer -> dominant kernel roofline
     pkg.ibdl.profile_enable(True)
     pkg.ibdl.profile_read(reset=True)
+    pinfos = []
     for _ in range(max(3, args.steps // 4)):
         for i in range(len(probs)):
             flush.fill_(1.0)
-            solve(i)
+            pinfos.append(solve(i))
     stats = pkg.ibdl.profile_read(reset=True)
     pkg.ibdl.profile_enable(False)
     peaks = load_peaks()
-    dom = max(stats.items(), key=lambda kv: kv[1][1]) if stats else None
+    kstats = {k: v for k, v in stats.items() if not k.startswith("phase:")}
+    pstats = {k: v for k, v in stats.items() if k.startswith("phase:")}
+    dom = max(kstats.items(), key=lambda kv: kv[1][1]) if kstats else None
     roofline = None
     kernels = {}
-    tot_prof = sum(v[1] for v in stats.values()) or 1.0
-    for name, (cnt, ms) in stats.items():
+    tot_prof = sum(v[1] for v in kstats.values()) or 1.0
+    for name, (cnt, ms) in kstats.items():
         kernels[name] = {"launches": cnt, "avg_us": ms / cnt * 1e3, "share": ms / tot_prof}
+    phases = {}
+    tot_phase = sum(v[1] for v in pstats.values()) or 1.0
+    for name, (cnt, ms) in pstats.items():
+        e = {"count": cnt, "avg_us": ms / cnt * 1e3, "share_of_solver": ms / tot_phase}
+        model = kernel_model(name, n, m)
+        if model is not None:
+            avg_s = ms / cnt / 1e3
+            if name.endswith("f64"):
+                e.update(bound="alu", achieved=model["flops"] / avg_s / 1e12, unit="TFLOP/s",
+                         frac=model["flops"] / avg_s / 1e12 / FP64_PEAK_TFLOPS)
+            else:
+                e.update(bound="hbm", achieved=model["bytes"] / avg_s / 1e9, unit="GB/s",
+                         frac=model["bytes"] / avg_s / 1e9 / peaks["hbm_gbs"],
+                         note="working set L2-resident")
+        phases[name] = e
     if dom:
         name, (cnt, ms) = dom
         avg_s = ms / cnt / 1e3
-        model = kernel_model(name, n, m)
-        if model is not None:
-            if name.endswith("f64"):
+        if name == "persistent_solve":
+            # one launch = one whole solve: its binding resource is the FP64
+            # pipe of the float64 FFT passes (residuals / all matvecs)
+            mv = float(np.mean([f["matvecs"] for f in pinfos]))
+            it = float(np.mean([f["iters"] for f in pinfos]))
+            mv64 = (mv - it) if prec == ibdl.FP32_REFINED else mv
+            mv32 = it if prec == ibdl.FP32_REFINED else 0.0
+            fl = mv64 * matvec_flops(n, m, 64)
+            ach = fl / avg_s / 1e12
+            roofline = {"kernel": name, "bound": "alu", "achieved": ach,
+                        "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                        "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                        "peak_src": "nominal GB300 FP64 rate (measured FMA probe: 1.19)",
+                        "algorithmic_flops_per_launch": fl,
+                        "float64_matvecs_per_launch": mv64,
+                        "float32_matvecs_per_launch": mv32,
+                        "algorithmic_bytes_per_launch":
+                            mv64 * matvec_bytes(n, m, 64) + mv32 * matvec_bytes(n, m, 32),
+                        "avg_launch_us": avg_s * 1e6}
+        else:
+            model = kernel_model(name, n, m)
+            if model is not None and name.endswith("f64"):
                 ach = model["flops"] / avg_s / 1e12
                 roofline = {"kernel": name, "bound": "alu", "achieved": ach,
                             "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                             "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                            "peak_src": "nominal GB300 FP64 rate (no measured FP64 peak)",
+                            "peak_src": "nominal GB300 FP64 rate",
                             "algorithmic_flops": model["flops"],
                             "avg_launch_us": avg_s * 1e6}
-            else:
+            elif model is not None:
                 ach = model["bytes"] / avg_s / 1e9
                 roofline = {"kernel": name, "bound": "hbm", "achieved": ach,
                             "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -378,6 +434,7 @@ def main():
             "config": {"workload": WORKLOAD, "n": n, "m": m, "kappa": 1e-3,
                        "tol": args.tol, "precision": args.precision,
                        "l2": "flushed between solves (512 MiB write, outside the events)",
+                       "engine": "persistent" if args.engine == 0 else "host-loop",
                        "parallelism": f"replicas x{world}"},
             "latency_ms": {"p50": float(np.percentile(lat, 50)),
                            "p99": float(np.percentile(lat, 99)),
@@ -387,6 +444,7 @@ def main():
             "rel_err_vs_fp64_1e-12": max(errs),
             "roofline": roofline,
             "kernels": kernels,
+            "phases": phases,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(launches),

@@ -10,6 +10,7 @@
 // z) pencil passes with the symbol, rows_inv (x inverse FFT) and interp
 // (gather + jump term): 4 kernels in 2D, 6 in 3D.
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <atomic>
@@ -37,6 +38,7 @@ static std::vector<ProfPending> g_pending;
 static std::vector<cudaEvent_t> g_ev_pool;
 static std::map<std::string, std::pair<long long, double>> g_prof_stats;
 static thread_local cudaEvent_t t_begin = nullptr;
+static unsigned long long* g_phase_buf = nullptr;  // persistent-solver phase times
 
 static cudaEvent_t prof_event() {
   if (!g_ev_pool.empty()) {
@@ -50,6 +52,10 @@ static cudaEvent_t prof_event() {
     return nullptr;
   }
   return e;
+}
+
+unsigned long long* prof_phase_buffer() {
+  return g_prof.load(std::memory_order_relaxed) ? g_phase_buf : nullptr;
 }
 
 void prof_begin(cudaStream_t st) {
@@ -380,8 +386,17 @@ ibdl_status gmres(ibdl_geometry_s* g, int prec, const double* b, double* x, bool
 }
 
 constexpr int kHistCap = 256;
+// IBDL_SOLVER_MULTIBLOCK=1 forces the multi-block vector phases for every
+// instance (used by the tests to cover both code paths on small problems).
+const bool g_force_multi = [] {
+  const char* e = getenv("IBDL_SOLVER_MULTIBLOCK");
+  return e && e[0] == '1';
+}();
 
-SolveInst make_inst(ibdl_geometry_s* g, const ibdl_solve_opts& o) {
+// batch_size: instances in the launch.  One block per instance for the
+// vector work pays off only when many instances share the rounds; a lone
+// instance is faster with its vector work spread over many blocks.
+SolveInst make_inst(ibdl_geometry_s* g, const ibdl_solve_opts& o, int batch_size) {
   SolveInst I;
   memset(&I, 0, sizeof(I));
   I.g = g->grid;
@@ -411,6 +426,7 @@ SolveInst make_inst(ibdl_geometry_s* g, const ibdl_solve_opts& o) {
   I.inner_tol = o.inner_tol;
   I.hist = g->d_hist;
   I.hist_cap = kHistCap;
+  I.single = g->m <= kSingleMax && batch_size >= kSingleMinBatch && !g_force_multi;
   return I;
 }
 
@@ -718,7 +734,7 @@ ibdl_status ibdl_solve(ibdl_geometry g, const double* bdata, const double* g_gri
   }
   if (o.engine == 0) {
     // one persistent launch runs the whole solve; the host waits once
-    *g->h_inst = make_inst(g, o);
+    *g->h_inst = make_inst(g, o, 1);
     *g->h_state = initial_state(x_zero);
     IBDL_CU(cudaMemcpyAsync(g->d_inst, g->h_inst, sizeof(SolveInst), cudaMemcpyHostToDevice, st));
     IBDL_CU(cudaMemcpyAsync(g->d_state, g->h_state, sizeof(SolveState), cudaMemcpyHostToDevice,
@@ -1059,7 +1075,7 @@ ibdl_status ibdl_solve_batched(ibdl_batch b, int32_t count, const ibdl_geometry*
     IBDL_CU(cudaMemcpyAsync(g->stage_a, bdata[k], sizeof(double) * g->m, cudaMemcpyDefault, st));
     IBDL_TRY(build_rhs(g, g->stage_a, nullptr, g->vb, st));
     IBDL_CU(cudaMemsetAsync(g->vx, 0, sizeof(double) * g->m, st));
-    b->h_inst[k] = make_inst(g, o);
+    b->h_inst[k] = make_inst(g, o, count);
     b->h_state[k] = initial_state(true);
     if (g->solver_smem > smem) smem = g->solver_smem;
   }
@@ -1094,11 +1110,40 @@ ibdl_status ibdl_solve_batched(ibdl_batch b, int32_t count, const ibdl_geometry*
 
 int64_t ibdl_kernel_launch_count(void) { return (int64_t)g_launches.load(); }
 
-void ibdl_profile_enable(int32_t on) { g_prof.store(on != 0); }
+void ibdl_profile_enable(int32_t on) {
+  if (on && !g_phase_buf) {
+    // allocated when profiling is switched on, never on the solve path
+    if (cudaMalloc((void**)&g_phase_buf, 2 * kPhaseSlots * sizeof(unsigned long long)) ==
+        cudaSuccess)
+      cudaMemset(g_phase_buf, 0, 2 * kPhaseSlots * sizeof(unsigned long long));
+    else
+      g_phase_buf = nullptr;
+  }
+  g_prof.store(on != 0);
+}
 
 int32_t ibdl_profile_read(ibdl_kernel_stat* out, int32_t max_out, int32_t reset) {
   cudaDeviceSynchronize();
   std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (g_phase_buf) {
+    static const char* names[15] = {
+        "phase:rows_fwd_f64", "phase:y_fwd_f64", "phase:solve_f64", "phase:y_inv_f64",
+        "phase:rows_inv_f64", "phase:rows_fwd_f32", "phase:y_fwd_f32", "phase:solve_f32",
+        "phase:y_inv_f32", "phase:rows_inv_f32", "phase:D_interp_dots", "phase:E_cgs1",
+        "phase:F_cgs2", "phase:G_norm_givens", "phase:round"};
+    unsigned long long h[2 * kPhaseSlots];
+    if (cudaMemcpy(h, g_phase_buf, sizeof(h), cudaMemcpyDeviceToHost) == cudaSuccess) {
+      for (int id = 0; id < 15; ++id) {
+        if (!h[2 * id + 1]) continue;
+        auto& st = g_prof_stats[names[id]];
+        st.first += (long long)h[2 * id + 1];
+        st.second += (double)h[2 * id] * 1e-6;
+      }
+      cudaMemset(g_phase_buf, 0, sizeof(h));
+    } else {
+      cudaGetLastError();
+    }
+  }
   for (const ProfPending& p : g_pending) {
     float ms = 0;
     if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {

@@ -171,13 +171,17 @@ __device__ void phase_rows_fwd(const GridDesc& g, const PointData& p, const Bins
   }
   __syncthreads();
 
+  // One thread per (point, support row bb): the point's weights are loaded
+  // once and its (up to) 6 x nodes on that row are added from registers.
+  // With c = the plane offset (3D) and W[t] = 0 outside t = 0..3:
+  //   node a: W_x[a-1] * cA + (W_x[a] - W_x[a-2]) * cB,
+  //   cA = q w/h^d (ny dW_y[bb] W_z[c-1] + nz W_y[bb-1] dW_z[c]) + v w/h^d W_y[bb-1] W_z[c-1]
+  //   cB = q w/h^d nx W_y[bb-1] W_z[c-1] / (2h).
   const int lo = b.start[tile], hi = b.start[tile + 1];
-  const int total = (hi - lo) * (kBoxSide * kBoxSide);
+  const int units = (hi - lo) * kBoxSide;
   const T inv2h = (T)(0.5 / g.h);
-  for (int e = tid; e < total; e += nt) {
-    const int pi = e / (kBoxSide * kBoxSide);
-    const int l = e - pi * (kBoxSide * kBoxSide);
-    const int a = l % kBoxSide, bb = l / kBoxSide;
+  for (int e = tid; e < units; e += nt) {
+    const int pi = e / kBoxSide, bb = e - pi * kBoxSide;
     const int i = b.pts[lo + pi];
     const int ry = ((p.base[1][i] - 1 + bb) & mask) - y0;
     if ((unsigned)ry >= (unsigned)R) continue;
@@ -186,26 +190,39 @@ __device__ void phase_rows_fwd(const GridDesc& g, const PointData& p, const Bins
       cz = (z - (p.base[2][i] - 1)) & mask;
       if (cz >= kBoxSide) continue;
     }
-    const T wxa = wload<T>(p, 0, a - 1, i);
     const T wyb = wload<T>(p, 1, bb - 1, i);
-    const T wzc = (D == 3) ? wload<T>(p, 2, cz - 1, i) : (T)1;
-    T val = 0;
+    const T dyb = (wload<T>(p, 1, bb, i) - wload<T>(p, 1, bb - 2, i)) * inv2h;
+    T wzc = (T)1, dzc = (T)0;
+    if (D == 3) {
+      wzc = wload<T>(p, 2, cz - 1, i);
+      dzc = (wload<T>(p, 2, cz, i) - wload<T>(p, 2, cz - 2, i)) * inv2h;
+    }
+    T cA = 0, cB = 0;
     if (src.q_div) {
       const T amp = (T)(src.coef_div * __ldcg(src.q_div + i) * p.w[i]);
-      const T dx = (wload<T>(p, 0, a, i) - wload<T>(p, 0, a - 2, i)) * inv2h;
-      const T dy = (wload<T>(p, 1, bb, i) - wload<T>(p, 1, bb - 2, i)) * inv2h;
-      T s = (T)p.nrm[0][i] * dx * wyb * wzc + (T)p.nrm[1][i] * wxa * dy * wzc;
-      if (D == 3) {
-        const T dz = (wload<T>(p, 2, cz, i) - wload<T>(p, 2, cz - 2, i)) * inv2h;
-        s += (T)p.nrm[2][i] * wxa * wyb * dz;
-      }
-      val += amp * s;
+      T t = (T)p.nrm[1][i] * dyb * wzc;
+      if (D == 3) t += (T)p.nrm[2][i] * wyb * dzc;
+      cA = amp * t;
+      cB = amp * (T)p.nrm[0][i] * wyb * wzc * inv2h;
     }
     if (src.v_plain)
-      val += (T)(src.coef_plain * __ldcg(src.v_plain + i) * p.w[i]) * wxa * wyb * wzc;
-    if (val != (T)0) {
-      const int x = (p.base[0][i] - 1 + a) & mask;
-      atomicAdd(&rows[((size_t)(ry >> 1) * n + x) * 2 + (ry & 1)], val);
+      cA += (T)(src.coef_plain * __ldcg(src.v_plain + i) * p.w[i]) * wyb * wzc;
+    if (cA == (T)0 && cB == (T)0) continue;
+    T wx[6];
+    wx[0] = 0;
+    wx[5] = 0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) wx[t + 1] = wload<T>(p, 0, t, i);  // wx[k] = W_x[k-1]
+    T* rowp = rows + (size_t)(ry >> 1) * n * 2 + (ry & 1);
+    const int xb = p.base[0][i] - 1;
+#pragma unroll
+    for (int a = 0; a < kBoxSide; ++a) {
+      // W_x[a] - W_x[a-2] = wx[a+1] - wx[a-1]
+      const T wa1 = wx[a];
+      const T wa = (a + 1 < 6) ? wx[a + 1] : (T)0;
+      const T wam2 = (a >= 1) ? wx[a - 1] : (T)0;
+      const T val = wa1 * cA + (wa - wam2) * cB;
+      if (val != (T)0) atomicAdd(rowp + (size_t)((xb + a) & mask) * 2, val);
     }
   }
   __syncthreads();

@@ -82,6 +82,10 @@ struct SpreadSrc {
 void prof_begin(cudaStream_t st);
 void count_launch(const char* name, cudaStream_t st);
 cudaError_t check_launch();
+// Device buffer of per-phase times of the persistent solver while profiling
+// is on (nullptr otherwise); kPhaseSlots (id) pairs of (ns, count).
+constexpr int kPhaseSlots = 16;
+unsigned long long* prof_phase_buffer();
 // Sets the per-thread message of ibdl_last_error_message and returns s.
 ibdl_status set_last_error(ibdl_status s, const char* msg);
 

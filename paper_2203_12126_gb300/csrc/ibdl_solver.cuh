@@ -7,6 +7,8 @@ namespace ibdl {
 
 constexpr int kSolverThreads = 512;  // threads per block; also the vector chunk
 constexpr int kMaxBatch = 512;       // instances per persistent launch
+constexpr int kSingleMax = 4096;     // points up to which one block does the vector work
+constexpr int kSingleMinBatch = 8;   // ... when at least this many instances share a launch
 
 enum SolveAction {
   ACT_DONE = 0,
@@ -45,7 +47,7 @@ struct SolveInst {
   double inner_tol;
   double* hist;
   int hist_cap;
-  int pad;
+  int single;       // 1: all vector work of a round on one block (m <= kSingleMax)
 };
 
 // Mutable; written by the instance's control thread.

@@ -29,7 +29,7 @@
 
 namespace ibdl {
 
-constexpr unsigned kSpinLimit = 1u << 25;  // x ~100 ns sleeps: a few seconds
+constexpr unsigned kSpinLimit = 1u << 27;  // x >= 20 ns sleeps: a few seconds
 
 __device__ bool grid_barrier(unsigned* bar, unsigned nblocks) {
   __syncthreads();
@@ -49,7 +49,7 @@ __device__ bool grid_barrier(unsigned* bar, unsigned nblocks) {
           atomicExch(bar + 2, 1u);
           break;
         }
-        __nanosleep(100);
+        __nanosleep(20);
       }
     }
     __threadfence();
@@ -74,13 +74,23 @@ __device__ __forceinline__ double warp_sum(double v) {
 struct BlockRed {
   double red[kMaxCols][kSolverThreads / 32];
   double h[kMaxCols];
+  double col[kMaxCols];  // staged H column / Givens vectors for the control step
+  double cs[kMaxCols];
+  double sn[kMaxCols];
 };
 
-// Sum over chunks of the partial column c: part[ch * pstride + c].
-__device__ __forceinline__ double sum_parts(const double* part, int nchunk, int pstride, int c) {
-  double s = 0;
-  for (int ch = 0; ch < nchunk; ++ch) s += __ldcg(part + (size_t)ch * pstride + c);
-  return s;
+// out[c] = sum over chunks of part[ch * pstride + c0 + c], c < ncols: one
+// warp per column, lanes over chunks (one L2 round trip, then shuffles).
+__device__ void reduce_parts(const double* part, int nchunk, int pstride, int c0, int ncols,
+                             double* out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c = wid; c < ncols; c += nw) {
+    double s = 0;
+    for (int ch = lane; ch < nchunk; ch += 32) s += __ldcg(part + (size_t)ch * pstride + c0 + c);
+    s = warp_sum(s);
+    if (lane == 0) out[c] = s;
+  }
+  __syncthreads();
 }
 
 // Writes, for c < ncols, the block sum of x_i * V_c[i] over this chunk, and
@@ -183,6 +193,7 @@ __device__ int phase_items(const SolveInst& I, const RoundView& v, int phase) {
     return v.prec ? mv_items<float>(I, phase) : mv_items<double>(I, phase);
   }
   if (v.action == ACT_DONE) return 0;
+  if (I.single) return 0;  // handled by vec_single on its own block
   return I.nchunk;
 }
 
@@ -298,8 +309,7 @@ __device__ void cgs_pass(const SolveInst& I, const RoundView& v, int chunk, Bloc
                          const double* in, double* out, bool first) {
   const int ncols = v.j + 1;
   const int ldh = I.restart + 1;
-  for (int c = threadIdx.x; c < ncols; c += blockDim.x) R.h[c] = sum_parts(in, I.nchunk, I.pstride, c);
-  __syncthreads();
+  reduce_parts(in, I.nchunk, I.pstride, 0, ncols, R.h);
   if (chunk == 0) {
     double* Hcol = I.H + (size_t)v.j * ldh;
     for (int c = threadIdx.x; c < ncols; c += blockDim.x)
@@ -350,9 +360,8 @@ __device__ void phase_E(const SolveInst& I, const RoundView& v, int chunk, Block
     return;
   }
   // residual actions: V0 = r / ||r||
-  __shared__ double beta;
-  if (threadIdx.x == 0) beta = sqrt(sum_parts(part1, I.nchunk, I.pstride, 0));
-  __syncthreads();
+  reduce_parts(part1, I.nchunk, I.pstride, 0, 1, R.h);
+  const double beta = sqrt(R.h[0]);
   const double inv = (beta > 0 && isfinite(beta)) ? 1.0 / beta : 0.0;
   if (valid) I.V[i] = __ldcg(I.r + i) * inv;
   __syncthreads();
@@ -368,7 +377,7 @@ __device__ void phase_F(const SolveInst& I, const RoundView& v, int chunk, Block
 // Control of one instance (one thread).  hn: new subdiagonal, beta: residual
 // norm of a residual action, bnorm2: ||b||^2 partial sum.
 __device__ void control(const SolveInst& I, SolveState* S, const RoundView& v, double hn,
-                        double beta, double bnorm2) {
+                        double beta, double bnorm2, BlockRed& R) {
   const int ldh = I.restart + 1;
   SolveState s;
   {
@@ -392,11 +401,10 @@ __device__ void control(const SolveInst& I, SolveState* S, const RoundView& v, d
   if (v.action == ACT_MV_ARNOLDI) {
     const int j = v.j;
     double* col = I.H + (size_t)j * ldh;
-    double cj[kMaxCols];
-    for (int r = 0; r <= j; ++r) cj[r] = __ldcg(col + r);
+    double* cj = R.col;  // staged by the block: H[0..j, j], cs, sn, gv[j]
     cj[j + 1] = hn;
     for (int r = 0; r < j; ++r) {
-      const double cr = __ldcg(I.cs + r), sr = __ldcg(I.sn + r);
+      const double cr = R.cs[r], sr = R.sn[r];
       const double t = cr * cj[r] + sr * cj[r + 1];
       cj[r + 1] = -sr * cj[r] + cr * cj[r + 1];
       cj[r] = t;
@@ -413,7 +421,7 @@ __device__ void control(const SolveInst& I, SolveState* S, const RoundView& v, d
     for (int r = 0; r <= j + 1; ++r) col[r] = cj[r];
     I.cs[j] = c;
     I.sn[j] = sn;
-    const double gj = __ldcg(I.gv + j);
+    const double gj = R.h[0];
     I.gv[j + 1] = -sn * gj;
     I.gv[j] = c * gj;
     const double est = fabs(sn * gj);
@@ -470,51 +478,256 @@ __device__ void control(const SolveInst& I, SolveState* S, const RoundView& v, d
 
 __device__ void phase_G(const SolveInst& I, SolveState* S, const RoundView& v, int chunk,
                         BlockRed& R) {
-  __shared__ double hn_s;
   if (v.action == ACT_MV_ARNOLDI) {
     double* part3 = I.part + 2 * (size_t)I.nchunk * I.pstride;
-    if (threadIdx.x == 0) hn_s = sqrt(sum_parts(part3, I.nchunk, I.pstride, 0));
-    __syncthreads();
-    const double hn = hn_s;
+    reduce_parts(part3, I.nchunk, I.pstride, 0, 1, R.h);
+    const double hn = sqrt(R.h[0]);
     const double inv = (hn > 0 && isfinite(hn)) ? 1.0 / hn : 0.0;
     const int i = chunk * blockDim.x + threadIdx.x;
     if (i < I.p.m && inv != 0.0) {
       double* wp = I.V + (size_t)(v.j + 1) * I.ld;
       wp[i] = __ldcg(wp + i) * inv;
     }
-    if (chunk == 0 && threadIdx.x == 0) control(I, S, v, hn, 0, 0);
+    if (chunk == 0) {
+      const int j = v.j, ldh = I.restart + 1;
+      __syncthreads();
+      for (int r = threadIdx.x; r <= j; r += blockDim.x) {
+        R.col[r] = __ldcg(I.H + (size_t)j * ldh + r);
+        if (r < j) {
+          R.cs[r] = __ldcg(I.cs + r);
+          R.sn[r] = __ldcg(I.sn + r);
+        }
+      }
+      if (threadIdx.x == 0) R.h[0] = __ldcg(I.gv + j);
+      __syncthreads();
+      if (threadIdx.x == 0) control(I, S, v, hn, 0, 0, R);
+    }
     __syncthreads();
     return;
   }
   if (chunk != 0) return;
-  if (threadIdx.x == 0) {
-    double beta = 0, b2 = 0;
-    if (v.action != ACT_FINISH) {
-      beta = sqrt(sum_parts(I.part, I.nchunk, I.pstride, 0));
-      b2 = sum_parts(I.part, I.nchunk, I.pstride, 1);
-    }
-    control(I, S, v, 0, beta, b2);
+  double beta = 0, b2 = 0;
+  if (v.action != ACT_FINISH) {
+    reduce_parts(I.part, I.nchunk, I.pstride, 0, 2, R.h);
+    beta = sqrt(R.h[0]);
+    b2 = R.h[1];
   }
+  if (threadIdx.x == 0) control(I, S, v, 0, beta, b2, R);
+  __syncthreads();
+}
+
+// ---- single-block vector step (instances with few points) ------------------
+// For m <= kSingleMax the whole post-matvec work of an action (interpolation,
+// both CGS passes, norm, Givens, control) runs in one block with block-level
+// synchronisation: one grid barrier per round instead of four.  The block is
+// fixed per instance (instance k -> block k mod gridDim), so every Krylov
+// vector, x and r of the instance is produced and consumed on the same SM
+// and is read back with ordinary (L1-coherent) loads; only the grid, written
+// by other blocks, is read around L1.
+
+__device__ double block_sum_all(double v, BlockRed& R) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) R.red[0][wid] = v;
+  __syncthreads();
+  double s = 0;
+  for (int w = 0; w < nw; ++w) s += R.red[0][w];
+  __syncthreads();
+  return s;
+}
+
+template <int D>
+__device__ double interp_any(const SolveInst& I, int prec, int i) {
+  return prec ? (double)interp_point<float, D>(I.g, I.p, I.w32.grid, i)
+              : interp_point<double, D>(I.g, I.p, I.w64.grid, i);
+}
+
+constexpr int kSingleK = kSingleMax / kSolverThreads;  // elements per thread
+
+__device__ void vec_single(const SolveInst& I, SolveState* S, const RoundView& v, BlockRed& R) {
+  const int m = I.p.m, tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  const double jump = I.bc == IBDL_DIRICHLET ? 0.5 : -0.5;
+  const bool d3 = I.g.dim == 3;
+  // element k of this thread: i = tid + k * nt (m <= kSingleK * nt)
+  if (v.action == ACT_FINISH) {
+    if (tid == 0) {
+      const int k = v.kdim, ldh = I.restart + 1;
+      for (int r = k - 1; r >= 0; --r) {
+        double sacc = __ldcg(I.gv + r);
+        for (int l = r + 1; l < k; ++l) sacc -= __ldcg(I.H + (size_t)l * ldh + r) * R.h[l];
+        const double dgn = __ldcg(I.H + (size_t)r * ldh + r);
+        R.h[r] = dgn != 0.0 ? sacc / dgn : 0.0;
+      }
+    }
+    __syncthreads();
+    double xk[kSingleK];
+#pragma unroll
+    for (int k = 0; k < kSingleK; ++k) {
+      const int i = tid + k * nt;
+      xk[k] = i < m ? I.x[i] : 0.0;
+    }
+    for (int c = 0; c < v.kdim; ++c) {
+      const double yc = R.h[c];
+      const double* vc = I.V + (size_t)c * I.ld;
+#pragma unroll
+      for (int k = 0; k < kSingleK; ++k) {
+        const int i = tid + k * nt;
+        if (i < m) xk[k] += yc * vc[i];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kSingleK; ++k) {
+      const int i = tid + k * nt;
+      if (i < m) I.x[i] = xk[k];
+    }
+    __syncthreads();
+    if (tid == 0) control(I, S, v, 0, 0, 0, R);
+    __syncthreads();
+    return;
+  }
+  if (v.action == ACT_MV_ARNOLDI) {
+    const int j = v.j, ncols = j + 1;
+    double* w = I.V + (size_t)(j + 1) * I.ld;
+    const double* vin = I.V + (size_t)j * I.ld;
+    double wk[kSingleK];
+#pragma unroll
+    for (int k = 0; k < kSingleK; ++k) {
+      const int i = tid + k * nt;
+      wk[k] = 0.0;
+      if (i < m) {
+        const double acc = d3 ? interp_any<3>(I, v.prec, i) : interp_any<2>(I, v.prec, i);
+        wk[k] = acc + jump * vin[i];
+      }
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int c = 0; c < ncols; ++c) {
+        const double* vc = I.V + (size_t)c * I.ld;
+        double sacc = 0;
+#pragma unroll
+        for (int k = 0; k < kSingleK; ++k) {
+          const int i = tid + k * nt;
+          if (i < m) sacc += wk[k] * vc[i];
+        }
+        sacc = warp_sum(sacc);
+        if (lane == 0) R.red[c][wid] = sacc;
+      }
+      __syncthreads();
+      if (tid < ncols) {
+        double t = 0;
+        for (int q = 0; q < nw; ++q) t += R.red[tid][q];
+        R.h[tid] = t;
+        R.col[tid] = pass == 0 ? t : R.col[tid] + t;
+      }
+      __syncthreads();
+      for (int c = 0; c < ncols; ++c) {
+        const double hc = R.h[c];
+        const double* vc = I.V + (size_t)c * I.ld;
+#pragma unroll
+        for (int k = 0; k < kSingleK; ++k) {
+          const int i = tid + k * nt;
+          if (i < m) wk[k] -= hc * vc[i];
+        }
+      }
+      __syncthreads();
+    }
+    double nrm = 0;
+#pragma unroll
+    for (int k = 0; k < kSingleK; ++k) nrm += wk[k] * wk[k];
+    const double hn = sqrt(block_sum_all(nrm, R));
+    const double inv = (hn > 0 && isfinite(hn)) ? 1.0 / hn : 0.0;
+#pragma unroll
+    for (int k = 0; k < kSingleK; ++k) {
+      const int i = tid + k * nt;
+      if (i < m) w[i] = inv != 0.0 ? wk[k] * inv : wk[k];
+    }
+    for (int r = tid; r < j; r += nt) {
+      R.cs[r] = __ldcg(I.cs + r);
+      R.sn[r] = __ldcg(I.sn + r);
+    }
+    if (tid == 0) R.h[0] = __ldcg(I.gv + j);
+    __syncthreads();
+    if (tid == 0) control(I, S, v, hn, 0, 0, R);
+    __syncthreads();
+    return;
+  }
+  // residual actions: r = b - A x (or b); V0 = r / ||r||; control
+  double rk[kSingleK];
+  double rr = 0, bb = 0;
+#pragma unroll
+  for (int k = 0; k < kSingleK; ++k) {
+    const int i = tid + k * nt;
+    rk[k] = 0.0;
+    if (i < m) {
+      const double bi = I.bvec[i];
+      double r = bi;
+      if (v.action == ACT_MV_RESIDUAL) {
+        const double acc = d3 ? interp_point<double, 3>(I.g, I.p, I.w64.grid, i)
+                              : interp_point<double, 2>(I.g, I.p, I.w64.grid, i);
+        r = bi - (acc + jump * I.x[i]);
+      }
+      I.r[i] = r;
+      rk[k] = r;
+      rr += r * r;
+      bb += bi * bi;
+    }
+  }
+  rr = block_sum_all(rr, R);
+  bb = block_sum_all(bb, R);
+  const double beta = sqrt(rr);
+  const double inv = (beta > 0 && isfinite(beta)) ? 1.0 / beta : 0.0;
+#pragma unroll
+  for (int k = 0; k < kSingleK; ++k) {
+    const int i = tid + k * nt;
+    if (i < m) I.V[i] = rk[k] * inv;
+  }
+  __syncthreads();
+  if (tid == 0) control(I, S, v, 0, beta, bb, R);
   __syncthreads();
 }
 
 // ---- the persistent kernel ----------------------------------------------------
 
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Phase timing (optional): block 0, thread 0 adds the wall time between
+// consecutive grid-barrier exits to ptimes[2*id] and counts in ptimes[2*id+1].
+// Ids: 0..4 matvec phases in float64 (rows_fwd, y fwd, solve, y inv,
+// rows_inv), 5..9 the same in float32, 10..13 vector phases D..G, 14 round
+// bookkeeping.
+__device__ __forceinline__ void phase_tick(unsigned long long* ptimes, int id,
+                                           unsigned long long& t0) {
+  if (ptimes && blockIdx.x == 0 && threadIdx.x == 0) {
+    const unsigned long long t = global_ns();
+    ptimes[2 * id] += t - t0;
+    ptimes[2 * id + 1] += 1;
+    t0 = t;
+  }
+}
+
 __global__ void __launch_bounds__(kSolverThreads, 1)
     k_persistent_solve(const SolveInst* __restrict__ insts, SolveState* states, int ninst,
-                       unsigned* bar) {
+                       unsigned* bar, unsigned long long* ptimes) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ RoundView rv[kMaxBatch];
   __shared__ BlockRed R;
-  __shared__ int flags[3];
+  __shared__ int flags[4];
   const unsigned nblocks = gridDim.x;
   const int G = gridDim.x, bid = blockIdx.x;
+  unsigned long long t0 = 0;
+  if (ptimes && bid == 0 && threadIdx.x == 0) t0 = global_ns();
 
   for (int round = 0;; ++round) {
     if (threadIdx.x == 0) {
       flags[0] = 0;
       flags[1] = 0;
       flags[2] = 0;
+      flags[3] = 0;
     }
     __syncthreads();
     for (int k = threadIdx.x; k < ninst; k += blockDim.x) {
@@ -525,7 +738,10 @@ __global__ void __launch_bounds__(kSolverThreads, 1)
       v.j = s->j;
       v.kdim = s->kdim;
       rv[k] = v;
-      if (v.action != ACT_DONE) atomicOr(&flags[0], 1);
+      if (v.action != ACT_DONE) {
+        atomicOr(&flags[0], 1);
+        if (!insts[k].single) atomicOr(&flags[3], 1);
+      }
       if (is_mv(v.action)) {
         atomicOr(&flags[1], 1);
         if (insts[k].g.dim == 3) atomicOr(&flags[2], 1);
@@ -533,7 +749,9 @@ __global__ void __launch_bounds__(kSolverThreads, 1)
     }
     __syncthreads();
     if (!flags[0]) break;
-    const bool any_mv = flags[1] != 0, any3d = flags[2] != 0;
+    const bool any_mv = flags[1] != 0, any3d = flags[2] != 0, any_multi = flags[3] != 0;
+    phase_tick(ptimes, 14, t0);
+    const int prec0 = rv[0].prec;
 
     // matvec phases
     for (int phase = 0; phase < 5 && any_mv; ++phase) {
@@ -553,9 +771,17 @@ __global__ void __launch_bounds__(kSolverThreads, 1)
         base += cnt;
       }
       if (!grid_barrier(bar, nblocks)) return;
+      phase_tick(ptimes, phase + 5 * prec0, t0);
     }
-    // vector phases D..G
+    // vector phases D..G (single-block instances finish in D)
     for (int phase = 5; phase < 9; ++phase) {
+      if (phase > 5 && !any_multi) break;
+      if (phase == 5) {
+        for (int k = bid; k < ninst; k += G) {
+          const RoundView v = rv[k];
+          if (insts[k].single && v.action != ACT_DONE) vec_single(insts[k], states + k, v, R);
+        }
+      }
       int base = 0;
       for (int k = 0; k < ninst; ++k) {
         const RoundView v = rv[k];
@@ -580,6 +806,7 @@ __global__ void __launch_bounds__(kSolverThreads, 1)
         base += cnt;
       }
       if (!grid_barrier(bar, nblocks)) return;
+      phase_tick(ptimes, phase + 5, t0);
     }
   }
 }
@@ -602,6 +829,7 @@ int solver_smem_bytes(const GridDesc& g, int need32) {
 
 cudaError_t launch_persistent_solve(const SolveInst* d_insts, SolveState* d_states, int ninst,
                                     unsigned* d_bar, int smem, cudaStream_t st) {
+  unsigned long long* ptimes = prof_phase_buffer();
   static int sm_count = 0;
   static int configured_smem = -1;
   cudaError_t e;
@@ -624,7 +852,8 @@ cudaError_t launch_persistent_solve(const SolveInst* d_insts, SolveState* d_stat
   if (per_sm > 2) per_sm = 2;
   const int blocks = per_sm * sm_count;
   if ((e = cudaMemsetAsync(d_bar, 0, 4 * sizeof(unsigned), st))) return e;
-  void* args[] = {(void*)&d_insts, (void*)&d_states, (void*)&ninst, (void*)&d_bar};
+  void* args[] = {(void*)&d_insts, (void*)&d_states, (void*)&ninst, (void*)&d_bar,
+                  (void*)&ptimes};
   prof_begin(st);
   e = cudaLaunchCooperativeKernel((const void*)k_persistent_solve, dim3(blocks),
                                   dim3(kSolverThreads), args, (size_t)smem, st);

@@ -37,6 +37,10 @@ def mixed_instances():
         (geometry.sphere(32, 0.3, kappa=1e-2), configs.DIRICHLET, 0),
         (geometry.ellipsoid(32, (0.3, 0.22, 0.26), kappa=3e-2), configs.NEUMANN, 1),
         (geometry.circle(16, 0.3, m=7, kappa=1e-1), configs.DIRICHLET, 0),
+        (geometry.star(512, 0.28, 0.2, 7, kappa=2e-4), configs.DIRICHLET, 0),
+        # m > 4096: this one keeps the multi-block vector phases while the
+        # others (batch >= 8, m <= 4096) each run on one block
+        (geometry.sphere(64, 0.3, spacing=1.0, kappa=1e-2), configs.NEUMANN, 0),
     ]
     for g, bc, prec in specs:
         out.append((g, bc, prec, rng.standard_normal(g.m)))
@@ -151,3 +155,52 @@ def test_c4_style_batch_of_64():
     batch.close()
     for G in geoms:
         G.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_multiblock_vector_path_3d_large_m(prec):
+    """M > 4096 takes the multi-block vector phases (partials + grid barriers)."""
+    g = geometry.sphere(64, 0.3, spacing=1.0, kappa=1e-2)
+    assert g.m > 4096
+    b = np.random.default_rng(5).standard_normal(g.m)
+    G = pkg.Geometry.from_workload(g, bc=configs.NEUMANN, precision=prec)
+    q = torch.empty(g.m, dtype=torch.float64, device=DEV)
+    info = G.solve(gpu(b), q, tol=1e-10)
+    ref = O.solve(g, configs.NEUMANN, b, tol=1e-13).x
+    assert rel(q.cpu(), ref) <= (1e-8 if prec else 1e-9), info
+    G.close()
+
+
+def test_forced_multiblock_path_matches_single_block():
+    """The same small solves with the multi-block vector phases forced on
+    (environment switch read at library load, so in a child process)."""
+    import json
+    import os
+    import subprocess
+    import sys
+    code = r'''
+import json, sys, numpy as np, torch
+sys.path.insert(0, ".")
+import paper_2203_12126_gb300 as pkg
+from workloads import geometry, configs
+out = []
+for prec in (0, 1):
+    g = geometry.star(256, 0.3, 0.2, 5, kappa=1e-3)
+    b = np.random.default_rng(6).standard_normal(g.m)
+    G = pkg.Geometry.from_workload(g, bc=configs.NEUMANN, precision=prec)
+    q = torch.empty(g.m, dtype=torch.float64, device="cuda:0")
+    info = G.solve(torch.tensor(b, device="cuda:0"), q, tol=1e-10)
+    out.append([q.cpu().numpy().tolist(), info["iters"]])
+print(json.dumps(out))
+'''
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, IBDL_SOLVER_MULTIBLOCK="1")
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    forced = json.loads(r.stdout.strip().splitlines()[-1])
+    g = geometry.star(256, 0.3, 0.2, 5, kappa=1e-3)
+    b = np.random.default_rng(6).standard_normal(g.m)
+    ref = O.solve(g, configs.NEUMANN, b, tol=1e-13).x
+    for prec, (q, iters) in zip((0, 1), forced):
+        assert rel(q, ref) <= (1e-8 if prec else 1e-9)
