@@ -19,7 +19,7 @@
 #include <string>
 #include <vector>
 
-#include "ibdl_internal.cuh"
+#include "ibdl_device.cuh"
 #include "ibdl_solver.cuh"
 
 namespace ibdl {
@@ -180,19 +180,26 @@ ibdl_status alloc_spectral(ibdl_geometry_s* g, SpectralWs<T>& ws, cudaStream_t s
   T* s2;
   IBDL_TRY(g->alloc(&spec, (size_t)spec_count));
   IBDL_TRY(g->alloc(&grid, (size_t)g->ncells));
-  IBDL_TRY(g->alloc(&tw, (size_t)n));
+  const int ntw = fft_tw_count(n);
+  IBDL_TRY(g->alloc(&tw, (size_t)ntw));
   IBDL_TRY(g->alloc(&s2, (size_t)n));
-  std::vector<typename Cx<T>::type> htw(n);
+  std::vector<typename Cx<T>::type> htw(ntw);
   std::vector<T> hs2(n);
-  for (int j = 0; j < n; ++j) {
-    // exp(-2 pi i j / n) and sin^2(pi j / n), from long double arithmetic
-    const long double a = 2.0L * 3.14159265358979323846264338327950288L * j / n;
+  const long double two_pi = 2.0L * 3.14159265358979323846264338327950288L;
+  for (int j = 0; j < ntw; ++j) {
+    // the FFT pass twiddles exp(-2 pi i num / den), from long double arithmetic
+    int num, den;
+    fft_tw_angle(n, j, &num, &den);
+    const long double a = two_pi * (long double)(num % den) / den;
     htw[j].x = (T)cosl(a);
     htw[j].y = (T)-sinl(a);
-    const long double s = sinl(0.5L * a);
+  }
+  for (int j = 0; j < n; ++j) {
+    // sin^2(pi j / n)
+    const long double s = sinl(0.5L * two_pi * j / n);
     hs2[j] = (T)(s * s);
   }
-  IBDL_CU(cudaMemcpyAsync(tw, htw.data(), sizeof(htw[0]) * n, cudaMemcpyHostToDevice, st));
+  IBDL_CU(cudaMemcpyAsync(tw, htw.data(), sizeof(htw[0]) * ntw, cudaMemcpyHostToDevice, st));
   IBDL_CU(cudaMemcpyAsync(s2, hs2.data(), sizeof(T) * n, cudaMemcpyHostToDevice, st));
   IBDL_CU(cudaStreamSynchronize(st));
   ws.spec = spec;
@@ -596,7 +603,7 @@ ibdl_status ibdl_create_geometry(const ibdl_geometry_desc* d, void* stream, ibdl
     if (e) return cleanup(cuda_fail(e, "point prep"));
   }
   // bins
-  const int rows = n >= 4096 ? 2 : 4;
+  const int rows = rows_per_tile(dim, n);
   const int ntiles = (n / rows) * (dim == 3 ? n : 1);
   int *start, *cursor;
   if ((s = g->alloc(&start, (size_t)ntiles + 1))) return cleanup(s);

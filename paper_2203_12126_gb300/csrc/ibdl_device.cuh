@@ -1,7 +1,9 @@
 // Device-side building blocks of the IBDL matvec, shared by the one-kernel-
 // per-pass launchers (k_fft.cu, k_points.cu) and the persistent solver
 // (k_solver.cu).  Each "phase" function processes one work item (a row tile,
-// a group of pencils, a point) with all threads of the calling block.
+// a group of pencils, a point) with all threads of the calling block.  The FFT
+// cores are not inlined (their own register allocation; the persistent
+// solver also calls each phase through a non-inlined wrapper).
 //
 // Data produced by another block of the same launch (spectrum, grids, Krylov
 // vectors) is read with ld.global.cg (__ldcg), which bypasses L1: inside a
@@ -41,80 +43,284 @@ template <typename C> __device__ __forceinline__ C cconj(C a) {
   return a;
 }
 
-// Stockham FFT of `npen` pencils of length n held in src (pencil-major),
-// radix 4 with one radix-2 stage when log2 n is odd.  All threads of the
-// block take part; the caller synchronises before the call.  Returns the
-// buffer (src or dst) holding the result; the block is synchronised.
-template <typename T, bool INV>
-__device__ cx_t<T>* fft_pencils(cx_t<T>* src, cx_t<T>* dst, int n, int npen,
-                                const cx_t<T>* __restrict__ tw) {
-  using C = cx_t<T>;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  int Ns = 1;
-  while (Ns < n) {
-    if (((n / Ns) & 3) == 0) {
-      const int nb = n >> 2;
-      const int twstep = n / (Ns * 4);
-      for (int e = tid; e < npen * nb; e += nt) {
-        const int pen = e / nb;
-        const int j = e - pen * nb;
-        const int k = j & (Ns - 1);
-        const C* x = src + (size_t)pen * n;
-        C* y = dst + (size_t)pen * n;
-        C a0 = x[j], a1 = x[j + nb], a2 = x[j + 2 * nb], a3 = x[j + 3 * nb];
-        if (Ns > 1) {
-          const int m1 = k * twstep;
-          C w1 = tw[m1], w2 = tw[2 * m1], w3 = tw[3 * m1];
-          if (INV) {
-            w1 = cconj(w1);
-            w2 = cconj(w2);
-            w3 = cconj(w3);
-          }
-          a1 = cmul(a1, w1);
-          a2 = cmul(a2, w2);
-          a3 = cmul(a3, w3);
-        }
-        const C t0 = cadd(a0, a2), t1 = csub(a0, a2);
-        const C t2 = cadd(a1, a3), it3 = cmuli(csub(a1, a3));
-        const int o = (j - k) * 4 + k;
-        y[o] = cadd(t0, t2);
-        y[o + 2 * Ns] = csub(t0, t2);
-        if (INV) {
-          y[o + Ns] = cadd(t1, it3);
-          y[o + 3 * Ns] = csub(t1, it3);
-        } else {
-          y[o + Ns] = csub(t1, it3);
-          y[o + 3 * Ns] = cadd(t1, it3);
-        }
-      }
-      Ns *= 4;
-    } else {
-      const int nb = n >> 1;
-      const int twstep = n / (Ns * 2);
-      for (int e = tid; e < npen * nb; e += nt) {
-        const int pen = e / nb;
-        const int j = e - pen * nb;
-        const int k = j & (Ns - 1);
-        const C* x = src + (size_t)pen * n;
-        C* y = dst + (size_t)pen * n;
-        C a0 = x[j], a1 = x[j + nb];
-        if (Ns > 1) {
-          C w1 = tw[k * twstep];
-          if (INV) w1 = cconj(w1);
-          a1 = cmul(a1, w1);
-        }
-        const int o = (j - k) * 2 + k;
-        y[o] = cadd(a0, a1);
-        y[o + Ns] = csub(a0, a1);
-      }
-      Ns *= 2;
-    }
-    __syncthreads();
-    C* t = src;
-    src = dst;
-    dst = t;
+// ---- shared-memory FFT ---------------------------------------------------------
+//
+// Pencils of length n = 2^lg are transformed in shared memory by a Stockham
+// FFT whose passes have radix 16, 8, 4 or 2 (ceil(lg / 4) passes, radices as
+// even as possible, larger first).  A thread loads the R inputs of one
+// butterfly, multiplies them by the pass twiddles, does the R-point DFT in
+// registers and stores the R outputs; passes ping-pong between two buffers
+// with one block barrier each.
+//
+// Shared layout of a pencil: element t at padi(t) = t + t/16, pencils
+// pen_stride(n) = n + n/16 + 1 apart.  The spare slot after every 16
+// elements spreads the stride-R stores of the first pass and the stride-16
+// loads of later passes over distinct banks, for 8- and 16-byte complex.
+//
+// Twiddles: pass s (radix R, Ns = product of the earlier radices) multiplies
+// input q of butterfly j by w^(q k), w = exp(-2 pi i / (Ns R)), k = j mod Ns.
+// Its table holds w^(q k) at [q * Ns + k], so a warp reads consecutive
+// entries; the tables of all passes are concatenated (fft_tw_count entries).
+
+__host__ __device__ constexpr int padi(int t) { return t + (t >> 4); }
+__host__ __device__ constexpr int pen_stride(int n) { return n + (n >> 4) + 1; }
+
+// Pass plan of an n = 2^lg point FFT: a first pass of radix 16 (or n when
+// n < 16), then the remaining bits split as evenly as possible into passes
+// of radix <= 16, larger radices first.  After the first pass Ns >= 16, so
+// the padded shared offsets of every later pass are compile-time constants.
+__host__ __device__ constexpr int plan_npass(int lg) { return lg <= 4 ? 1 : 1 + (lg - 1) / 4; }
+__host__ __device__ constexpr int plan_lr(int lg, int s) {
+  return s == 0 ? (lg < 4 ? lg : 4)
+                : (lg - 4) / (plan_npass(lg) - 1) +
+                      (s - 1 < (lg - 4) % (plan_npass(lg) - 1) ? 1 : 0);
+}
+__host__ __device__ constexpr int plan_lgns(int lg, int s) {
+  return s == 0 ? 0 : plan_lgns(lg, s - 1) + plan_lr(lg, s - 1);
+}
+__host__ __device__ constexpr int plan_off(int lg, int s) {
+  return s == 0 ? 0 : plan_off(lg, s - 1) + (1 << (plan_lgns(lg, s - 1) + plan_lr(lg, s - 1)));
+}
+__host__ __device__ constexpr int plan_tw_total(int lg) { return plan_off(lg, plan_npass(lg)); }
+
+__host__ __device__ inline int ilog2(int n) {
+  int lg = 0;
+  while ((1 << lg) < n) ++lg;
+  return lg;
+}
+
+__host__ __device__ inline int fft_tw_count(int n) {
+  switch (ilog2(n)) {
+    case 4: return plan_tw_total(4);
+    case 5: return plan_tw_total(5);
+    case 6: return plan_tw_total(6);
+    case 7: return plan_tw_total(7);
+    case 8: return plan_tw_total(8);
+    case 9: return plan_tw_total(9);
+    case 10: return plan_tw_total(10);
+    case 11: return plan_tw_total(11);
+    default: return plan_tw_total(12);
   }
-  return src;
+}
+
+// Table entry idx of an n-point FFT is exp(-2 pi i num / den) (the passes'
+// tables walked without recursion, for run-time n).
+__host__ __device__ inline void fft_tw_angle(int n, int idx, int* num, int* den) {
+  const int lg = ilog2(n), np = plan_npass(lg);
+  int off = 0, lgns = 0;
+  for (int s = 0; s < np; ++s) {
+    const int lr = s == 0 ? (lg < 4 ? lg : 4)
+                          : (lg - 4) / (np - 1) + (s - 1 < (lg - 4) % (np - 1) ? 1 : 0);
+    const int size = 1 << (lgns + lr);
+    if (idx < off + size || s == np - 1) {
+      const int local = idx - off;
+      *num = (local >> lgns) * (local & ((1 << lgns) - 1));
+      *den = size;
+      return;
+    }
+    off += size;
+    lgns += lr;
+  }
+}
+
+// -i * a (forward) or +i * a (inverse)
+template <bool INV, typename C> __device__ __forceinline__ C rot90(C a) {
+  C r;
+  if (INV) {
+    r.x = -a.y;
+    r.y = a.x;
+  } else {
+    r.x = a.y;
+    r.y = -a.x;
+  }
+  return r;
+}
+
+template <typename C> __device__ __forceinline__ C cmulc(C a, double wr, double wi) {
+  using T = decltype(a.x);
+  const T cr = (T)wr, ci = (T)wi;
+  C r;
+  r.x = a.x * cr - a.y * ci;
+  r.y = a.x * ci + a.y * cr;
+  return r;
+}
+
+// In-register DFTs, natural order in and out; sign -1 (forward) or +1.
+template <bool INV, typename C> __device__ __forceinline__ void dft2(C* a) {
+  const C t = a[0];
+  a[0] = cadd(t, a[1]);
+  a[1] = csub(t, a[1]);
+}
+
+template <bool INV, typename C> __device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
+  const C t0 = cadd(a0, a2), t1 = csub(a0, a2);
+  const C t2 = cadd(a1, a3), t3 = rot90<INV>(csub(a1, a3));
+  a0 = cadd(t0, t2);
+  a2 = csub(t0, t2);
+  a1 = cadd(t1, t3);
+  a3 = csub(t1, t3);
+}
+template <bool INV, typename C> __device__ __forceinline__ void dft4(C* a) {
+  dft4<INV>(a[0], a[1], a[2], a[3]);
+}
+
+constexpr double kR2 = 0.70710678118654752440;   // cos(pi/4)
+constexpr double kC8 = 0.92387953251128675613;   // cos(pi/8)
+constexpr double kS8 = 0.38268343236508977173;   // sin(pi/8)
+
+// X[p] = E[p] + w8^p O[p], X[p+4] = E[p] - w8^p O[p] (radix-2 split of 8)
+template <bool INV, typename C> __device__ __forceinline__ void dft8(C* a) {
+  C e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
+  C o0 = a[1], o1 = a[3], o2 = a[5], o3 = a[7];
+  dft4<INV>(e0, e1, e2, e3);
+  dft4<INV>(o0, o1, o2, o3);
+  const double sg = INV ? 1.0 : -1.0;
+  o1 = cmulc(o1, kR2, sg * kR2);
+  o2 = rot90<INV>(o2);
+  o3 = cmulc(o3, -kR2, sg * kR2);
+  a[0] = cadd(e0, o0);
+  a[4] = csub(e0, o0);
+  a[1] = cadd(e1, o1);
+  a[5] = csub(e1, o1);
+  a[2] = cadd(e2, o2);
+  a[6] = csub(e2, o2);
+  a[3] = cadd(e3, o3);
+  a[7] = csub(e3, o3);
+}
+
+// 16 = 4 x 4: DFT-4 over q1 of a[q2 + 4 q1], twiddle w16^(p1 q2), DFT-4 over
+// q2; output index p1 + 4 p2.
+template <bool INV, typename C> __device__ __forceinline__ void dft16(C* a) {
+#pragma unroll
+  for (int q2 = 0; q2 < 4; ++q2) dft4<INV>(a[q2], a[q2 + 4], a[q2 + 8], a[q2 + 12]);
+  // a[q2 + 4 p1] now holds B[q2][p1]
+  const double sg = INV ? 1.0 : -1.0;
+  a[5] = cmulc(a[5], kC8, sg * kS8);      // w^1
+  a[9] = cmulc(a[9], kR2, sg * kR2);      // w^2
+  a[13] = cmulc(a[13], kS8, sg * kC8);    // w^3
+  a[6] = cmulc(a[6], kR2, sg * kR2);      // w^2
+  a[10] = rot90<INV>(a[10]);              // w^4
+  a[14] = cmulc(a[14], -kR2, sg * kR2);   // w^6
+  a[7] = cmulc(a[7], kS8, sg * kC8);      // w^3
+  a[11] = cmulc(a[11], -kR2, sg * kR2);   // w^6
+  a[15] = cmulc(a[15], -kC8, -sg * kS8);  // w^9
+#pragma unroll
+  for (int p1 = 0; p1 < 4; ++p1) dft4<INV>(a[4 * p1], a[4 * p1 + 1], a[4 * p1 + 2], a[4 * p1 + 3]);
+  // a[4 p1 + p2] holds X[p1 + 4 p2]: transpose the 4 x 4 index
+  C t;
+  t = a[1]; a[1] = a[4]; a[4] = t;
+  t = a[2]; a[2] = a[8]; a[8] = t;
+  t = a[3]; a[3] = a[12]; a[12] = t;
+  t = a[6]; a[6] = a[9]; a[9] = t;
+  t = a[7]; a[7] = a[13]; a[13] = t;
+  t = a[11]; a[11] = a[14]; a[14] = t;
+}
+
+template <int LR, bool INV, typename C> __device__ __forceinline__ void dft_reg(C* a) {
+  if (LR == 1) dft2<INV>(a);
+  if (LR == 2) dft4<INV>(a);
+  if (LR == 3) dft8<INV>(a);
+  if (LR == 4) dft16<INV>(a);
+}
+
+template <typename T, int LG, int S, bool INV>
+__device__ __forceinline__ void fft_pass(const cx_t<T>* __restrict__ src,
+                                         cx_t<T>* __restrict__ dst, int npen,
+                                         const cx_t<T>* __restrict__ tws) {
+  using C = cx_t<T>;
+  constexpr int LR = plan_lr(LG, S), LGNS = plan_lgns(LG, S), OFF = plan_off(LG, S);
+  constexpr int R = 1 << LR, LGNB = LG - LR, NB = 1 << LGNB, NS = 1 << LGNS;
+  constexpr int PS = pen_stride(1 << LG);
+  const int total = npen << LGNB;
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    const int pen = e >> LGNB, j = e & (NB - 1);
+    const int k = j & (NS - 1);
+    const C* x = src + pen * PS;
+    C a[R];
+    if (NB % 16 == 0) {
+      // padi(j + q NB) = padi(j) + q (NB + NB/16)
+      const C* xb = x + padi(j);
+#pragma unroll
+      for (int q = 0; q < R; ++q) a[q] = xb[q * (NB + NB / 16)];
+    } else {
+#pragma unroll
+      for (int q = 0; q < R; ++q) a[q] = x[padi(j + q * NB)];
+    }
+    if (NS > 1) {
+      const C* tw = tws + OFF + k;
+#pragma unroll
+      for (int q = 1; q < R; ++q) {
+        C w = tw[q * NS];
+        if (INV) w.y = -w.y;
+        a[q] = cmul(a[q], w);
+      }
+    }
+    dft_reg<LR, INV>(a);
+    C* y = dst + pen * PS;
+    const int o = ((j - k) << LR) + k;
+    C* yb = y + padi(o);
+    if (NS % 16 == 0) {
+      // padi(o + p NS) = padi(o) + p (NS + NS/16)
+#pragma unroll
+      for (int p = 0; p < R; ++p) yb[p * (NS + NS / 16)] = a[p];
+    } else {
+      // NS == 1: o = R j, and o mod 16 + p < 16, so padi(o + p) = padi(o) + p
+#pragma unroll
+      for (int p = 0; p < R; ++p) yb[p] = a[p];
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T, int LG, bool INV>
+__device__ __noinline__ cx_t<T>* fft_run_lg(cx_t<T>* src, cx_t<T>* dst, int npen,
+                                            const cx_t<T>* __restrict__ tws) {
+  constexpr int NP = plan_npass(LG);
+  static_assert(NP <= 3, "n <= 4096");
+  fft_pass<T, LG, 0, INV>(src, dst, npen, tws);
+  if (NP == 1) return dst;
+  fft_pass<T, LG, (NP > 1 ? 1 : 0), INV>(dst, src, npen, tws);
+  if (NP == 2) return src;
+  fft_pass<T, LG, (NP > 2 ? 2 : 0), INV>(src, dst, npen, tws);
+  return dst;
+}
+
+// Transforms npen pencils held in src (shared, padded layout); tws is the
+// concatenated twiddle table in shared memory.  The caller synchronises
+// before the call.  Returns the buffer (src or dst) holding the result.
+template <typename T, bool INV>
+__device__ __forceinline__ cx_t<T>* fft_run(cx_t<T>* src, cx_t<T>* dst, int lg, int npen,
+                                            const cx_t<T>* __restrict__ tws) {
+  switch (lg) {
+    case 4: return fft_run_lg<T, 4, INV>(src, dst, npen, tws);
+    case 5: return fft_run_lg<T, 5, INV>(src, dst, npen, tws);
+    case 6: return fft_run_lg<T, 6, INV>(src, dst, npen, tws);
+    case 7: return fft_run_lg<T, 7, INV>(src, dst, npen, tws);
+    case 8: return fft_run_lg<T, 8, INV>(src, dst, npen, tws);
+    case 9: return fft_run_lg<T, 9, INV>(src, dst, npen, tws);
+    case 10: return fft_run_lg<T, 10, INV>(src, dst, npen, tws);
+    case 11: return fft_run_lg<T, 11, INV>(src, dst, npen, tws);
+    default: return fft_run_lg<T, 12, INV>(src, dst, npen, tws);
+  }
+}
+
+// Copies `count` values from global (around L1) to shared memory.
+template <typename V>
+__device__ __forceinline__ void copy_to_shared(V* dst, const V* __restrict__ src, int count) {
+  constexpr int U = 4;
+  for (int e0 = threadIdx.x; e0 < count; e0 += U * blockDim.x) {
+    V v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e < count) v[u] = __ldcg(src + e);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e < count) dst[e] = v[u];
+    }
+  }
 }
 
 template <typename T> __device__ __forceinline__ T wload(const PointData& p, int c, int t, int i);
@@ -127,9 +333,18 @@ template <> __device__ __forceinline__ float wload<float>(const PointData& p, in
   return (t >= 0 && t < 4) ? p.W32[c][t * p.m + i] : 0.0f;
 }
 
+// Rows per tile of the x passes: 2D keeps 4 (2 for n = 4096) so that even a
+// 1024^2 grid has 256 tiles; 3D takes 8, so each kx of a tile is a 64-byte
+// (float) or 128-byte (double) segment of the transposed spectrum.
+__host__ __device__ inline int rows_per_tile(int dim, int n) {
+  if (dim == 3) return 8;
+  return n >= 4096 ? 2 : 4;
+}
+
+// Shared memory of a row tile: two pencil buffers and the twiddle table.
 template <typename T>
 __host__ __device__ __forceinline__ size_t rows_smem_bytes(int n, int rows) {
-  return 2 * (size_t)(rows / 2) * n * sizeof(cx_t<T>);
+  return (2 * (size_t)(rows / 2) * pen_stride(n) + fft_tw_count(n)) * sizeof(cx_t<T>);
 }
 
 // ---- fused spread + forward x pass ------------------------------------------
@@ -148,104 +363,149 @@ __host__ __device__ __forceinline__ size_t rows_smem_bytes(int n, int rows) {
 // (A_k = (Z_k + conj Z_{n-k})/2, B_k = (Z_k - conj Z_{n-k})/(2i)) and written
 // to the transposed half spectrum spec[k][z][y], k = 0..n/2.
 template <typename T, int D>
-__device__ void phase_rows_fwd(const GridDesc& g, const PointData& p, const Bins& b,
+__device__ __forceinline__ void phase_rows_fwd(const GridDesc& g, const PointData& p, const Bins& b,
                                const SpreadSrc& src, cx_t<T>* spec,
                                const cx_t<T>* __restrict__ tw, double* write_grid, int tile,
                                unsigned char* smem) {
   using C = cx_t<T>;
-  const int n = g.n, mask = n - 1, R = b.rows, npen = R >> 1;
+  const int n = g.n, lg = g.log2n, mask = n - 1, R = b.rows, npen = R >> 1;
+  const int PS = pen_stride(n);
   C* bufA = reinterpret_cast<C*>(smem);
-  C* bufB = bufA + (size_t)npen * n;
-  T* rows = reinterpret_cast<T*>(bufA);  // row r, column x at [((r>>1)*n + x)*2 + (r&1)]
+  C* bufB = bufA + (size_t)npen * PS;
+  C* tws = bufB + (size_t)npen * PS;
+  T* rows = reinterpret_cast<T*>(bufA);  // row r, column x at [((r>>1)*PS + padi(x))*2 + (r&1)]
   const int ngroups = n / R;
   const int z = (D == 3) ? tile / ngroups : 0;
   const int y0 = (tile % ngroups) * R;
   const int tid = threadIdx.x, nt = blockDim.x;
   const size_t row0 = ((size_t)z * n + y0) * n;
+  const int lo = b.start[tile], hi = b.start[tile + 1];
+  const int half = n >> 1;
+  const size_t slab = (D == 3) ? (size_t)n * n : (size_t)n;
+  const size_t pos0 = (size_t)z * n + y0;
+
+  if (lo == hi && !src.f_grid) {
+    // no source touches the tile: its rows, and so their spectrum, are zero
+    if (write_grid) {
+      for (int e = tid; e < R * n; e += nt) write_grid[row0 + e] = 0.0;
+    } else {
+      C zero;
+      zero.x = 0;
+      zero.y = 0;
+      for (int e = tid; e < (half + 1) * R; e += nt) {
+        const int k = e / R, a = e - k * R;
+        spec[(size_t)k * slab + pos0 + a] = zero;
+      }
+    }
+    return;
+  }
 
   for (int e = tid; e < R * n; e += nt) {
-    const int r = e / n, x = e - r * n;
+    const int r = e >> lg, x = e & mask;
     T v = 0;
     if (src.f_grid) v = (T)(src.coef_grid * src.f_grid[row0 + (size_t)r * n + x]);
-    rows[((size_t)(r >> 1) * n + x) * 2 + (r & 1)] = v;
+    rows[((r >> 1) * PS + padi(x)) * 2 + (r & 1)] = v;
   }
+  if (!write_grid) copy_to_shared(tws, tw, fft_tw_count(n));
   __syncthreads();
 
-  // One thread per (point, support row bb): the point's weights are loaded
-  // once and its (up to) 6 x nodes on that row are added from registers.
-  // With c = the plane offset (3D) and W[t] = 0 outside t = 0..3:
+  // The tile's points are taken in chunks of KP.  Stage A (one thread per
+  // point) gathers each point's data with independent loads and folds it
+  // into per-point coefficients, staged in bufB (unused until the FFT);
+  // stage B (one thread per (point, support row bb)) adds the 6 x nodes of
+  // that row.  With c = the plane offset (3D) and W[t] = 0 outside t = 0..3:
   //   node a: W_x[a-1] * cA + (W_x[a] - W_x[a-2]) * cB,
   //   cA = q w/h^d (ny dW_y[bb] W_z[c-1] + nz W_y[bb-1] dW_z[c]) + v w/h^d W_y[bb-1] W_z[c-1]
-  //   cB = q w/h^d nx W_y[bb-1] W_z[c-1] / (2h).
-  const int lo = b.start[tile], hi = b.start[tile + 1];
-  const int units = (hi - lo) * kBoxSide;
+  //   cB = q w/h^d nx W_y[bb-1] W_z[c-1] / (2h),
+  // staged as  cA = P dW_y[bb] + Q W_y[bb-1],  cB = X W_y[bb-1].
   const T inv2h = (T)(0.5 / g.h);
-  for (int e = tid; e < units; e += nt) {
-    const int pi = e / kBoxSide, bb = e - pi * kBoxSide;
-    const int i = b.pts[lo + pi];
-    const int ry = ((p.base[1][i] - 1 + bb) & mask) - y0;
-    if ((unsigned)ry >= (unsigned)R) continue;
-    int cz = 1;
-    if (D == 3) {
-      cz = (z - (p.base[2][i] - 1)) & mask;
-      if (cz >= kBoxSide) continue;
-    }
-    const T wyb = wload<T>(p, 1, bb - 1, i);
-    const T dyb = (wload<T>(p, 1, bb, i) - wload<T>(p, 1, bb - 2, i)) * inv2h;
-    T wzc = (T)1, dzc = (T)0;
-    if (D == 3) {
-      wzc = wload<T>(p, 2, cz - 1, i);
-      dzc = (wload<T>(p, 2, cz, i) - wload<T>(p, 2, cz - 2, i)) * inv2h;
-    }
-    T cA = 0, cB = 0;
-    if (src.q_div) {
-      const T amp = (T)(src.coef_div * __ldcg(src.q_div + i) * p.w[i]);
-      T t = (T)p.nrm[1][i] * dyb * wzc;
-      if (D == 3) t += (T)p.nrm[2][i] * wyb * dzc;
-      cA = amp * t;
-      cB = amp * (T)p.nrm[0][i] * wyb * wzc * inv2h;
-    }
-    if (src.v_plain)
-      cA += (T)(src.coef_plain * __ldcg(src.v_plain + i) * p.w[i]) * wyb * wzc;
-    if (cA == (T)0 && cB == (T)0) continue;
-    T wx[6];
-    wx[0] = 0;
-    wx[5] = 0;
+  constexpr int kWords = 11;  // wx[4], wy[4], P, Q, X
+  const int per_pt = kWords * (int)sizeof(T) + 2 * (int)sizeof(int);
+  int KP = (int)((size_t)npen * PS * sizeof(C) / per_pt);
+  if (KP > 256) KP = 256;
+  T* sv = reinterpret_cast<T*>(bufB);         // [kWords][KP]
+  int* sxb = reinterpret_cast<int*>(sv + kWords * KP);
+  int* syb = sxb + KP;
+  for (int c0 = lo; c0 < hi; c0 += KP) {
+    const int np = min(KP, hi - c0);
+    for (int t = tid; t < np; t += nt) {
+      const int i = __ldg(b.pts + c0 + t);
+      int ok = 1;
+      T wz = (T)1, dz = (T)0;
+      if (D == 3) {
+        const int cz = (z - (__ldg(p.base[2] + i) - 1)) & mask;
+        ok = cz < kBoxSide;
+        wz = wload<T>(p, 2, cz - 1, i);
+        dz = (wload<T>(p, 2, cz, i) - wload<T>(p, 2, cz - 2, i)) * inv2h;
+      }
+      T P = 0, Q = 0, X = 0;
+      const double wi = p.w[i];
+      if (src.q_div) {
+        const T amp = (T)(src.coef_div * __ldcg(src.q_div + i) * wi);
+        P = amp * (T)p.nrm[1][i] * wz;
+        if (D == 3) Q = amp * (T)p.nrm[2][i] * dz;
+        X = amp * (T)p.nrm[0][i] * wz * inv2h;
+      }
+      if (src.v_plain) Q += (T)(src.coef_plain * __ldcg(src.v_plain + i) * wi) * wz;
+      if (!ok) P = Q = X = 0;
 #pragma unroll
-    for (int t = 0; t < 4; ++t) wx[t + 1] = wload<T>(p, 0, t, i);  // wx[k] = W_x[k-1]
-    T* rowp = rows + (size_t)(ry >> 1) * n * 2 + (ry & 1);
-    const int xb = p.base[0][i] - 1;
-#pragma unroll
-    for (int a = 0; a < kBoxSide; ++a) {
-      // W_x[a] - W_x[a-2] = wx[a+1] - wx[a-1]
-      const T wa1 = wx[a];
-      const T wa = (a + 1 < 6) ? wx[a + 1] : (T)0;
-      const T wam2 = (a >= 1) ? wx[a - 1] : (T)0;
-      const T val = wa1 * cA + (wa - wam2) * cB;
-      if (val != (T)0) atomicAdd(rowp + (size_t)((xb + a) & mask) * 2, val);
+      for (int u = 0; u < 4; ++u) {
+        sv[u * KP + t] = wload<T>(p, 0, u, i);
+        sv[(4 + u) * KP + t] = wload<T>(p, 1, u, i);
+      }
+      sv[8 * KP + t] = P;
+      sv[9 * KP + t] = Q;
+      sv[10 * KP + t] = X;
+      sxb[t] = __ldg(p.base[0] + i) - 1;
+      syb[t] = __ldg(p.base[1] + i) - 1;
     }
+    __syncthreads();
+    for (int e = tid; e < np * kBoxSide; e += nt) {
+      const int t = e / kBoxSide, bb = e - t * kBoxSide;
+      const int ry = ((syb[t] + bb) & mask) - y0;
+      if ((unsigned)ry >= (unsigned)R) continue;
+      const T P = sv[8 * KP + t], Q = sv[9 * KP + t], X = sv[10 * KP + t];
+      const T wyb = (bb >= 1 && bb <= 4) ? sv[(4 + bb - 1) * KP + t] : (T)0;
+      const T wy0 = bb <= 3 ? sv[(4 + bb) * KP + t] : (T)0;
+      const T wy2 = bb >= 2 ? sv[(4 + bb - 2) * KP + t] : (T)0;
+      const T cA = P * (wy0 - wy2) * inv2h + Q * wyb;
+      const T cB = X * wyb;
+      if (cA == (T)0 && cB == (T)0) continue;
+      T wx[6];
+      wx[0] = 0;
+      wx[5] = 0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) wx[u + 1] = sv[u * KP + t];  // wx[k] = W_x[k-1]
+      T* rowp = rows + (size_t)(ry >> 1) * PS * 2 + (ry & 1);
+      const int xb = sxb[t];
+#pragma unroll
+      for (int a = 0; a < kBoxSide; ++a) {
+        // W_x[a] - W_x[a-2] = wx[a+1] - wx[a-1]
+        const T wa1 = wx[a];
+        const T wa = (a + 1 < 6) ? wx[a + 1] : (T)0;
+        const T wam2 = (a >= 1) ? wx[a - 1] : (T)0;
+        const T val = wa1 * cA + (wa - wam2) * cB;
+        if (val != (T)0) atomicAdd(rowp + (size_t)padi((xb + a) & mask) * 2, val);
+      }
+    }
+    __syncthreads();
   }
-  __syncthreads();
 
   if (write_grid) {
     for (int e = tid; e < R * n; e += nt) {
-      const int r = e / n, x = e - r * n;
-      write_grid[row0 + (size_t)r * n + x] =
-          (double)rows[((size_t)(r >> 1) * n + x) * 2 + (r & 1)];
+      const int r = e >> lg, x = e & mask;
+      write_grid[row0 + (size_t)r * n + x] = (double)rows[((r >> 1) * PS + padi(x)) * 2 + (r & 1)];
     }
     __syncthreads();
     return;
   }
 
-  C* res = fft_pencils<T, false>(bufA, bufB, n, npen, tw);
+  C* res = fft_run<T, false>(bufA, bufB, lg, npen, tws);
 
-  const int half = n >> 1;
-  const size_t slab = (D == 3) ? (size_t)n * n : (size_t)n;
-  const size_t pos0 = (size_t)z * n + y0;
   for (int e = tid; e < (half + 1) * npen; e += nt) {
     const int k = e / npen, a = e - k * npen;
-    const C zk = res[(size_t)a * n + k];
-    const C zm = res[(size_t)a * n + ((n - k) & mask)];
+    const C zk = res[a * PS + padi(k)];
+    const C zm = res[a * PS + padi((n - k) & mask)];
     C A, B;
     A.x = (T)0.5 * (zk.x + zm.x);
     A.y = (T)0.5 * (zk.y - zm.y);
@@ -261,10 +521,22 @@ __device__ void phase_rows_fwd(const GridDesc& g, const PointData& p, const Bins
 // ---- pencil passes on the transposed half spectrum -----------------------
 struct PencilLayout {
   int64_t gstride, bstride, estride;
-  int pg;        // pencils per group
+  int pg;        // pencils per group (a power of two)
   int npencils;  // total pencils
-  int c;         // pencils per block
+  int c;         // pencils per block (a power of two)
+  int lgc, lgpg;
 };
+
+// c: pencils per work item (a power of two <= 16): at most pg when the
+// pencils are strided, shared memory (pencil buffers + tables) within 90 KB
+// so that two 512-thread blocks of the persistent solver fit on an SM, and
+// small enough that a pass over contiguous pencils has >= 256 items when it
+// can.
+template <typename T>
+__host__ __device__ inline size_t pencil_smem_for(int n, int c) {
+  return (2 * (size_t)c * pen_stride(n) + fft_tw_count(n)) * sizeof(cx_t<T>) +
+         (size_t)n * sizeof(T);
+}
 
 template <typename T>
 __host__ __device__ inline PencilLayout pencil_layout(int n, int64_t gstride, int64_t bstride,
@@ -275,11 +547,15 @@ __host__ __device__ inline PencilLayout pencil_layout(int n, int64_t gstride, in
   L.estride = estride;
   L.pg = pg;
   L.npencils = npencils;
-  int c = (int)(65536 / (2 * (size_t)n * sizeof(cx_t<T>)));
-  if (c < 1) c = 1;
-  if (c > 16) c = 16;
+  int c = 16;
   if (estride != 1 && c > pg) c = pg;
+  while (c > 1 && pencil_smem_for<T>(n, c) > 90 * 1024) c >>= 1;
+  while (c > 1 && npencils / c < 256 && estride == 1) c >>= 1;
   L.c = c;
+  L.lgc = 0;
+  while ((1 << L.lgc) < c) ++L.lgc;
+  L.lgpg = 0;
+  while ((1 << L.lgpg) < pg) ++L.lgpg;
   return L;
 }
 
@@ -295,79 +571,99 @@ __host__ __device__ inline PencilLayout solve_layout(int dim, int n, int which) 
   return pencil_layout<T>(n, n2, n, 1, n, (half + 1) * n);
 }
 
+// pencil buffers, twiddles, sin^2 table
 template <typename T>
 __host__ __device__ inline size_t pencil_smem_bytes(const PencilLayout& L, int n) {
-  return 2 * (size_t)L.c * n * sizeof(cx_t<T>);
+  return pencil_smem_for<T>(n, L.c);
 }
 
 // MODE 0: forward, 1: inverse, 2: forward, multiply by
 // scale0 / (1 + cfac * sum_c sin^2(pi k_c / n)), inverse.
 template <typename T, int MODE>
-__device__ void phase_pencils(const GridDesc& g, const PencilLayout& L, cx_t<T>* data,
+__device__ __forceinline__ void phase_pencils(const GridDesc& g, const PencilLayout& L, cx_t<T>* data,
                               const cx_t<T>* __restrict__ tw, const T* __restrict__ s2,
                               T cfac, T scale0, int blk, unsigned char* smem) {
   using C = cx_t<T>;
-  const int n = g.n, c = L.c;
+  const int n = g.n, lg = g.log2n, c = L.c, lgc = L.lgc, PS = pen_stride(n);
+  const int ntw = fft_tw_count(n);
   C* bufA = reinterpret_cast<C*>(smem);
-  C* bufB = bufA + (size_t)c * n;
+  C* bufB = bufA + (size_t)c * PS;
+  C* tws = bufB + (size_t)c * PS;
+  T* s2s = reinterpret_cast<T*>(tws + ntw);
   const int tid = threadIdx.x, nt = blockDim.x;
   const int p0 = blk * c;
   const bool tfast = (L.estride == 1);
+  const int total = c << lg;
 
-  for (int e = tid; e < c * n; e += nt) {
-    int pl, t;
-    if (tfast) {
-      pl = e / n;
-      t = e - pl * n;
-    } else {
-      t = e / c;
-      pl = e - t * c;
+  // element e of the item: (pencil pl, position t); t fastest when the
+  // pencils are contiguous, pl fastest when they are strided
+  constexpr int U = sizeof(T) == 4 ? 8 : 4;
+  for (int e0 = tid; e0 < total; e0 += U * nt) {
+    C v[U];
+    int at[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * nt;
+      at[u] = -1;
+      v[u].x = 0;
+      v[u].y = 0;
+      if (e < total) {
+        int pl, t;
+        if (tfast) {
+          pl = e >> lg;
+          t = e & (n - 1);
+        } else {
+          t = e >> lgc;
+          pl = e & (c - 1);
+        }
+        const int p = p0 + pl;
+        if (p < L.npencils) {
+          const int gi = p >> L.lgpg, q = p & (L.pg - 1);
+          v[u] = __ldcg(data + gi * L.gstride + q * L.bstride + t * L.estride);
+        }
+        at[u] = pl * PS + padi(t);
+      }
     }
-    const int p = p0 + pl;
-    C v;
-    v.x = 0;
-    v.y = 0;
-    if (p < L.npencils) {
-      const int gi = p / L.pg, q = p - gi * L.pg;
-      v = __ldcg(data + gi * L.gstride + q * L.bstride + t * L.estride);
-    }
-    bufA[(size_t)pl * n + t] = v;
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (at[u] >= 0) bufA[at[u]] = v[u];
   }
+  copy_to_shared(tws, tw, ntw);
+  if (MODE == 2) copy_to_shared(s2s, s2, n);
   __syncthreads();
 
-  C* res = fft_pencils<T, MODE == 1>(bufA, bufB, n, c, tw);
+  C* res = fft_run<T, MODE == 1>(bufA, bufB, lg, c, tws);
   if (MODE == 2) {
-    for (int e = tid; e < c * n; e += nt) {
-      const int pl = e / n, t = e - pl * n;
+    for (int e = tid; e < total; e += nt) {
+      const int pl = e >> lg, t = e & (n - 1);
       const int p = p0 + pl;
       if (p >= L.npencils) continue;
-      const int gi = p / L.pg, q = p - gi * L.pg;
-      T ssum = s2[gi] + s2[t];
-      if (g.dim == 3) ssum += s2[q];
+      const int gi = p >> L.lgpg, q = p & (L.pg - 1);
+      T ssum = s2s[gi] + s2s[t];
+      if (g.dim == 3) ssum += s2s[q];
       const T f = scale0 / ((T)1 + cfac * ssum);
-      C v = res[(size_t)pl * n + t];
+      C& v = res[pl * PS + padi(t)];
       v.x *= f;
       v.y *= f;
-      res[(size_t)pl * n + t] = v;
     }
     __syncthreads();
     C* other = (res == bufA) ? bufB : bufA;
-    res = fft_pencils<T, true>(res, other, n, c, tw);
+    res = fft_run<T, true>(res, other, lg, c, tws);
   }
 
-  for (int e = tid; e < c * n; e += nt) {
+  for (int e = tid; e < total; e += nt) {
     int pl, t;
     if (tfast) {
-      pl = e / n;
-      t = e - pl * n;
+      pl = e >> lg;
+      t = e & (n - 1);
     } else {
-      t = e / c;
-      pl = e - t * c;
+      t = e >> lgc;
+      pl = e & (c - 1);
     }
     const int p = p0 + pl;
     if (p < L.npencils) {
-      const int gi = p / L.pg, q = p - gi * L.pg;
-      data[gi * L.gstride + q * L.bstride + t * L.estride] = res[(size_t)pl * n + t];
+      const int gi = p >> L.lgpg, q = p & (L.pg - 1);
+      data[gi * L.gstride + q * L.bstride + t * L.estride] = res[pl * PS + padi(t)];
     }
   }
   __syncthreads();
@@ -377,13 +673,15 @@ __device__ void phase_pencils(const GridDesc& g, const PencilLayout& L, cx_t<T>*
 // Rebuild the full spectrum of the packed pair a + i b from the half spectra
 // A, B (Hermitian): Z_k = A_k + i B_k, Z_{n-k} = conj A_k + i conj B_k.
 template <typename T, int D, typename OutT>
-__device__ void phase_rows_inv(const GridDesc& g, const Bins& b, const cx_t<T>* spec,
+__device__ __forceinline__ void phase_rows_inv(const GridDesc& g, const Bins& b, const cx_t<T>* spec,
                                const cx_t<T>* __restrict__ tw, OutT* out, int tile,
                                unsigned char* smem) {
   using C = cx_t<T>;
-  const int n = g.n, R = b.rows, npen = R >> 1;
+  const int n = g.n, lg = g.log2n, R = b.rows, npen = R >> 1;
+  const int PS = pen_stride(n);
   C* bufA = reinterpret_cast<C*>(smem);
-  C* bufB = bufA + (size_t)npen * n;
+  C* bufB = bufA + (size_t)npen * PS;
+  C* tws = bufB + (size_t)npen * PS;
   const int ngroups = n / R;
   const int z = (D == 3) ? tile / ngroups : 0;
   const int y0 = (tile % ngroups) * R;
@@ -392,30 +690,49 @@ __device__ void phase_rows_inv(const GridDesc& g, const Bins& b, const cx_t<T>* 
   const size_t slab = (D == 3) ? (size_t)n * n : (size_t)n;
   const size_t pos0 = (size_t)z * n + y0;
 
-  for (int e = tid; e < (half + 1) * npen; e += nt) {
-    const int k = e / npen, a = e - k * npen;
-    const C* in = spec + (size_t)k * slab + pos0 + 2 * a;
-    C A = __ldcg(in), B = __ldcg(in + 1);
-    if (k == 0 || k == half) {
-      A.y = 0;
-      B.y = 0;
+  constexpr int U = sizeof(T) == 4 ? 4 : 2;
+  const int total = (half + 1) * npen;
+  for (int e0 = tid; e0 < total; e0 += U * nt) {
+    C A[U], B[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * nt;
+      if (e < total) {
+        const int k = e / npen, a = e - k * npen;
+        const C* in = spec + (size_t)k * slab + pos0 + 2 * a;
+        A[u] = __ldcg(in);
+        B[u] = __ldcg(in + 1);
+      }
     }
-    C zk, zm;
-    zk.x = A.x - B.y;
-    zk.y = A.y + B.x;
-    bufA[(size_t)a * n + k] = zk;
-    if (k > 0 && k < half) {
-      zm.x = A.x + B.y;
-      zm.y = B.x - A.y;
-      bufA[(size_t)a * n + (n - k)] = zm;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * nt;
+      if (e < total) {
+        const int k = e / npen, a = e - k * npen;
+        C Au = A[u], Bu = B[u];
+        if (k == 0 || k == half) {
+          Au.y = 0;
+          Bu.y = 0;
+        }
+        C zk, zm;
+        zk.x = Au.x - Bu.y;
+        zk.y = Au.y + Bu.x;
+        bufA[a * PS + padi(k)] = zk;
+        if (k > 0 && k < half) {
+          zm.x = Au.x + Bu.y;
+          zm.y = Bu.x - Au.y;
+          bufA[a * PS + padi(n - k)] = zm;
+        }
+      }
     }
   }
+  copy_to_shared(tws, tw, fft_tw_count(n));
   __syncthreads();
-  C* res = fft_pencils<T, true>(bufA, bufB, n, npen, tw);
+  C* res = fft_run<T, true>(bufA, bufB, lg, npen, tws);
   const size_t row0 = ((size_t)z * n + y0) * n;
   for (int e = tid; e < R * n; e += nt) {
-    const int r = e / n, x = e - r * n;
-    const C v = res[(size_t)(r >> 1) * n + x];
+    const int r = e >> lg, x = e & (n - 1);
+    const C v = res[(r >> 1) * PS + padi(x)];
     out[row0 + (size_t)r * n + x] = (OutT)((r & 1) ? v.y : v.x);
   }
   __syncthreads();

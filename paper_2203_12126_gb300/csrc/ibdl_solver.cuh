@@ -5,7 +5,7 @@
 
 namespace ibdl {
 
-constexpr int kSolverThreads = 512;  // threads per block; also the vector chunk
+constexpr int kSolverThreads = 256;  // threads per block; also the vector chunk
 constexpr int kMaxBatch = 512;       // instances per persistent launch
 constexpr int kSingleMax = 4096;     // points up to which one block does the vector work
 constexpr int kSingleMinBatch = 8;   // ... when at least this many instances share a launch

@@ -22,7 +22,7 @@
 namespace ibdl {
 
 template <typename T, int D>
-__global__ void __launch_bounds__(1024) k_rows_fwd(GridDesc g, PointData p, Bins b,
+__global__ void __launch_bounds__(512) k_rows_fwd(GridDesc g, PointData p, Bins b,
                                                    SpreadSrc src, cx_t<T>* spec,
                                                    const cx_t<T>* __restrict__ tw,
                                                    double* write_grid) {
@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(512) k_pencils(GridDesc g, PencilLayout L, cx_
 }
 
 template <typename T, int D, typename OutT>
-__global__ void __launch_bounds__(1024) k_rows_inv(GridDesc g, Bins b, const cx_t<T>* spec,
+__global__ void __launch_bounds__(512) k_rows_inv(GridDesc g, Bins b, const cx_t<T>* spec,
                                                    const cx_t<T>* __restrict__ tw,
                                                    OutT* out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -49,9 +49,9 @@ __global__ void __launch_bounds__(1024) k_rows_inv(GridDesc g, Bins b, const cx_
 // ---- launchers ----------------------------------------------------------------
 
 static int rows_threads(int n, int npen) {
-  int t = npen * n / 4;
+  int t = npen * n / 8;
   if (t < 64) t = 64;
-  if (t > 1024) t = 1024;
+  if (t > 512) t = 512;
   return t;
 }
 
@@ -90,10 +90,10 @@ template <typename T, int MODE>
 static cudaError_t run_pencils(const GridDesc& g, const PencilLayout& L, SpectralWs<T>& ws,
                                cudaStream_t st) {
   const int blocks = (L.npencils + L.c - 1) / L.c;
-  int thr = L.c * g.n / 4;
+  int thr = L.c * g.n / 8;
   if (thr < 64) thr = 64;
   if (thr > 512) thr = 512;
-  const size_t smem = 2 * (size_t)L.c * g.n * sizeof(cx_t<T>);
+  const size_t smem = pencil_smem_bytes<T>(L, g.n);
   const double nd = g.dim == 3 ? (double)g.n * g.n * g.n : (double)g.n * g.n;
   const T cfac = (T)(4.0 * g.kappa / (g.h * g.h));
   const T scale0 = (T)(g.kappa / nd);

@@ -148,42 +148,58 @@ __device__ int mv_items(const SolveInst& I, int phase) {
   return (L.npencils + L.c - 1) / L.c;
 }
 
+// Each matvec phase is called through a non-inlined wrapper, so that every
+// phase gets its own register allocation inside this one large kernel.  The
+// wrappers take the instance by reference to its global-memory descriptor.
+template <typename T, int D>
+__device__ __noinline__ void solver_rows_fwd(const SolveInst& I, const double* q, int item,
+                                             unsigned char* smem) {
+  SpreadSrc src;
+  src.q_div = q;
+  src.coef_div = 1.0;
+  const SpectralWs<T> ws = ws_of<T>(I);
+  phase_rows_fwd<T, D>(I.g, I.p, I.b, src, ws.spec, ws.tw, nullptr, item, smem);
+}
+
+template <typename T, int D>
+__device__ __noinline__ void solver_rows_inv(const SolveInst& I, int item, unsigned char* smem) {
+  const SpectralWs<T> ws = ws_of<T>(I);
+  phase_rows_inv<T, D, T>(I.g, I.b, ws.spec, ws.tw, ws.grid, item, smem);
+}
+
+template <typename T, int MODE>
+__device__ __noinline__ void solver_pencils(const SolveInst& I, int which, int item,
+                                            unsigned char* smem) {
+  const SpectralWs<T> ws = ws_of<T>(I);
+  const GridDesc& g = I.g;
+  const double nd = g.dim == 3 ? (double)g.n * g.n * g.n : (double)g.n * g.n;
+  const T cfac = (T)(4.0 * g.kappa / (g.h * g.h));
+  const T scale0 = (T)(g.kappa / nd);
+  phase_pencils<T, MODE>(g, solve_layout<T>(g.dim, g.n, which), ws.spec, ws.tw, ws.s2, cfac,
+                         scale0, item, smem);
+}
+
 // phase: 0 rows_fwd, 1 y forward (3D), 2 solve pass, 3 y inverse (3D), 4 rows_inv
 template <typename T>
 __device__ void mv_item(const SolveInst& I, const RoundView& v, int phase, int item,
                         unsigned char* smem) {
-  SpectralWs<T> ws = ws_of<T>(I);
-  const GridDesc& g = I.g;
+  const int d = I.g.dim;
   if (phase == 0) {
-    SpreadSrc src;
-    src.q_div = mv_input(I, v);
-    src.coef_div = 1.0;
-    if (g.dim == 2)
-      phase_rows_fwd<T, 2>(g, I.p, I.b, src, ws.spec, ws.tw, nullptr, item, smem);
+    if (d == 2)
+      solver_rows_fwd<T, 2>(I, mv_input(I, v), item, smem);
     else
-      phase_rows_fwd<T, 3>(g, I.p, I.b, src, ws.spec, ws.tw, nullptr, item, smem);
+      solver_rows_fwd<T, 3>(I, mv_input(I, v), item, smem);
   } else if (phase == 4) {
-    if (g.dim == 2)
-      phase_rows_inv<T, 2, T>(g, I.b, ws.spec, ws.tw, ws.grid, item, smem);
+    if (d == 2)
+      solver_rows_inv<T, 2>(I, item, smem);
     else
-      phase_rows_inv<T, 3, T>(g, I.b, ws.spec, ws.tw, ws.grid, item, smem);
+      solver_rows_inv<T, 3>(I, item, smem);
+  } else if (d == 2 || phase == 2) {
+    solver_pencils<T, 2>(I, 1, item, smem);
+  } else if (phase == 1) {
+    solver_pencils<T, 0>(I, 0, item, smem);
   } else {
-    const double nd = g.dim == 3 ? (double)g.n * g.n * g.n : (double)g.n * g.n;
-    const T cfac = (T)(4.0 * g.kappa / (g.h * g.h));
-    const T scale0 = (T)(g.kappa / nd);
-    if (g.dim == 2) {
-      phase_pencils<T, 2>(g, solve_layout<T>(2, g.n, 1), ws.spec, ws.tw, ws.s2, cfac, scale0,
-                          item, smem);
-    } else if (phase == 1) {
-      phase_pencils<T, 0>(g, solve_layout<T>(3, g.n, 0), ws.spec, ws.tw, ws.s2, cfac, scale0,
-                          item, smem);
-    } else if (phase == 2) {
-      phase_pencils<T, 2>(g, solve_layout<T>(3, g.n, 1), ws.spec, ws.tw, ws.s2, cfac, scale0,
-                          item, smem);
-    } else {
-      phase_pencils<T, 1>(g, solve_layout<T>(3, g.n, 0), ws.spec, ws.tw, ws.s2, cfac, scale0,
-                          item, smem);
-    }
+    solver_pencils<T, 1>(I, 0, item, smem);
   }
 }
 
@@ -710,7 +726,7 @@ __device__ __forceinline__ void phase_tick(unsigned long long* ptimes, int id,
   }
 }
 
-__global__ void __launch_bounds__(kSolverThreads, 1)
+__global__ void __launch_bounds__(kSolverThreads, 2)
     k_persistent_solve(const SolveInst* __restrict__ insts, SolveState* states, int ninst,
                        unsigned* bar, unsigned long long* ptimes) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -812,7 +828,7 @@ __global__ void __launch_bounds__(kSolverThreads, 1)
 }
 
 int solver_smem_bytes(const GridDesc& g, int need32) {
-  size_t s = rows_smem_bytes<double>(g.n, g.n >= 4096 ? 2 : 4);
+  size_t s = rows_smem_bytes<double>(g.n, rows_per_tile(g.dim, g.n));
   const int nl = g.dim == 2 ? 1 : 2;
   for (int w = 0; w < nl; ++w) {
     const PencilLayout L = solve_layout<double>(g.dim, g.n, w == 0 ? 1 : 0);

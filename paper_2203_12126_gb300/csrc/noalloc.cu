@@ -10,13 +10,13 @@
 
 #include <mutex>
 
-#include "ibdl_internal.cuh"
+#include "ibdl_device.cuh"
 
 namespace ibdl {
 
 constexpr int kNoAllocMaxN = 512;  // largest grid: 512 x 512
 constexpr size_t kSpecBytes = (size_t)(kNoAllocMaxN / 2 + 1) * kNoAllocMaxN * sizeof(double2);
-constexpr size_t kTwBytes = (size_t)kNoAllocMaxN * sizeof(double2);
+constexpr size_t kTwBytes = 2 * (size_t)kNoAllocMaxN * sizeof(double2);  // >= fft_tw_count(n)
 constexpr size_t kS2Bytes = (size_t)kNoAllocMaxN * sizeof(double);
 constexpr size_t kStartBytes = 256 * 4;  // >= (n/4 + 1) ints for n <= 512
 constexpr size_t kScratchBytes = kSpecBytes + kTwBytes + kS2Bytes + kStartBytes;
@@ -25,15 +25,21 @@ constexpr size_t kScratchBytes = kSpecBytes + kTwBytes + kS2Bytes + kStartBytes;
 // device address; it takes the address from cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-// exp(-2 pi i j / n) and sin^2(pi j / n) for j < n, rewritten by every call.
-__global__ void k_noalloc_tables(int n, double2* tw, double* s2) {
+// FFT pass twiddles (fft_tw_count(n) entries) and sin^2(pi j / n), j < n,
+// rewritten by every call.
+__global__ void k_noalloc_tables(int n, int ntw, double2* tw, double* s2) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  double s, c;
-  sincospi(2.0 * j / n, &s, &c);
-  tw[j] = make_double2(c, -s);
-  const double h = sinpi((double)j / n);
-  s2[j] = h * h;
+  if (j < ntw) {
+    int num, den;
+    fft_tw_angle(n, j, &num, &den);
+    double s, c;
+    sincospi(2.0 * (double)(num % den) / den, &s, &c);
+    tw[j] = make_double2(c, -s);
+  }
+  if (j < n) {
+    const double h = sinpi((double)j / n);
+    s2[j] = h * h;
+  }
 }
 
 namespace {
@@ -99,7 +105,8 @@ extern "C" ibdl_status ibdl_helmholtz_2d_noalloc(int32_t n, double box_len, doub
   if ((e = cudaMemsetAsync(start, 0, kStartBytes, st)) != cudaSuccess)
     return set_last_error(IBDL_ERR_CUDA, "ibdl_helmholtz_2d_noalloc: clearing scratch");
   prof_begin(st);
-  k_noalloc_tables<<<(n + 127) / 128, 128, 0, st>>>(n, tw, s2);
+  const int ntw = fft_tw_count(n);
+  k_noalloc_tables<<<(2 * n + 127) / 128, 128, 0, st>>>(n, ntw, tw, s2);
   count_launch("noalloc_tables", st);
   if ((e = check_launch()) != cudaSuccess)
     return set_last_error(IBDL_ERR_CUDA, "ibdl_helmholtz_2d_noalloc: table kernel");
