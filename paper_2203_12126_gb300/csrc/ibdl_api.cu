@@ -437,10 +437,14 @@ SolveInst make_inst(ibdl_geometry_s* g, const ibdl_solve_opts& o, int batch_size
   return I;
 }
 
-SolveState initial_state(bool x_zero) {
+// rhs_in_kernel: the Neumann right-hand side is built by the solver's first
+// action (ACT_RHS) from V_b in inst.vdata.
+SolveState initial_state(bool x_zero, bool rhs_in_kernel = false) {
   SolveState s;
   memset(&s, 0, sizeof(s));
   s.action = x_zero ? ACT_RESID_ZERO : ACT_MV_RESIDUAL;
+  if (rhs_in_kernel) s.action = ACT_RHS;
+  s.xinit = x_zero ? 0 : 1;
   s.status = IBDL_ERR_NOT_CONVERGED;
   s.bnorm = -1.0;
   return s;
@@ -659,7 +663,7 @@ ibdl_status ibdl_create_geometry(const ibdl_geometry_desc* d, void* stream, ibdl
   if ((s = g->alloc(&g->d_hist, (size_t)kHistCap))) return cleanup(s);
   if ((s = g->alloc(&g->d_inst, (size_t)1))) return cleanup(s);
   if ((s = g->alloc(&g->d_state, (size_t)1))) return cleanup(s);
-  if ((s = g->alloc(&g->d_bar, (size_t)4))) return cleanup(s);
+  if ((s = g->alloc(&g->d_bar, (size_t)8))) return cleanup(s);
   {
     cudaError_t e = cudaMallocHost((void**)&g->h_inst, sizeof(SolveInst));
     if (!e) e = cudaMallocHost((void**)&g->h_state, sizeof(SolveState));
@@ -730,7 +734,9 @@ ibdl_status ibdl_solve(ibdl_geometry g, const double* bdata, const double* g_gri
   IBDL_TRY(grid_in(g, g_grid, &gg, st));
   IBDL_CU(cudaMemsetAsync(g->d_flag, 0, sizeof(int), st));
   IBDL_CU(launch_nonfinite_check(m, g->stage_a, g->d_flag, st));
-  IBDL_TRY(build_rhs(g, g->stage_a, gg, g->vb, st));
+  // the persistent engine builds an unforced Neumann right-hand side itself
+  const bool rhs_in_kernel = o.engine == 0 && g->bc == IBDL_NEUMANN && !gg;
+  if (!rhs_in_kernel) IBDL_TRY(build_rhs(g, g->stage_a, gg, g->vb, st));
   bool x_zero = true;
   if (o.x0) {
     IBDL_CU(cudaMemcpyAsync(g->vx, o.x0, sizeof(double) * m, cudaMemcpyDefault, st));
@@ -742,7 +748,8 @@ ibdl_status ibdl_solve(ibdl_geometry g, const double* bdata, const double* g_gri
   if (o.engine == 0) {
     // one persistent launch runs the whole solve; the host waits once
     *g->h_inst = make_inst(g, o, 1);
-    *g->h_state = initial_state(x_zero);
+    g->h_inst->vdata = g->stage_a;
+    *g->h_state = initial_state(x_zero, rhs_in_kernel);
     IBDL_CU(cudaMemcpyAsync(g->d_inst, g->h_inst, sizeof(SolveInst), cudaMemcpyHostToDevice, st));
     IBDL_CU(cudaMemcpyAsync(g->d_state, g->h_state, sizeof(SolveState), cudaMemcpyHostToDevice,
                             st));
@@ -1036,7 +1043,7 @@ ibdl_status ibdl_batch_create(int32_t capacity, ibdl_batch* out) {
   b->cap = capacity;
   cudaError_t e = cudaMalloc((void**)&b->d_inst, sizeof(SolveInst) * capacity);
   if (!e) e = cudaMalloc((void**)&b->d_state, sizeof(SolveState) * capacity);
-  if (!e) e = cudaMalloc((void**)&b->d_bar, 4 * sizeof(unsigned));
+  if (!e) e = cudaMalloc((void**)&b->d_bar, (4 + 4 * (size_t)capacity) * sizeof(unsigned));
   if (!e) e = cudaMallocHost((void**)&b->h_inst, sizeof(SolveInst) * capacity);
   if (!e) e = cudaMallocHost((void**)&b->h_state, sizeof(SolveState) * capacity);
   if (e) {
@@ -1080,10 +1087,12 @@ ibdl_status ibdl_solve_batched(ibdl_batch b, int32_t count, const ibdl_geometry*
   for (int k = 0; k < count; ++k) {
     ibdl_geometry g = geoms[k];
     IBDL_CU(cudaMemcpyAsync(g->stage_a, bdata[k], sizeof(double) * g->m, cudaMemcpyDefault, st));
-    IBDL_TRY(build_rhs(g, g->stage_a, nullptr, g->vb, st));
+    const bool rhs_in_kernel = g->bc == IBDL_NEUMANN;
+    if (!rhs_in_kernel) IBDL_TRY(build_rhs(g, g->stage_a, nullptr, g->vb, st));
     IBDL_CU(cudaMemsetAsync(g->vx, 0, sizeof(double) * g->m, st));
     b->h_inst[k] = make_inst(g, o, count);
-    b->h_state[k] = initial_state(true);
+    b->h_inst[k].vdata = g->stage_a;
+    b->h_state[k] = initial_state(true, rhs_in_kernel);
     if (g->solver_smem > smem) smem = g->solver_smem;
   }
   IBDL_CU(cudaMemcpyAsync(b->d_inst, b->h_inst, sizeof(SolveInst) * count,
@@ -1136,8 +1145,8 @@ int32_t ibdl_profile_read(ibdl_kernel_stat* out, int32_t max_out, int32_t reset)
     static const char* names[15] = {
         "phase:rows_fwd_f64", "phase:y_fwd_f64", "phase:solve_f64", "phase:y_inv_f64",
         "phase:rows_inv_f64", "phase:rows_fwd_f32", "phase:y_fwd_f32", "phase:solve_f32",
-        "phase:y_inv_f32", "phase:rows_inv_f32", "phase:D_interp_dots", "phase:E_cgs1",
-        "phase:F_cgs2", "phase:G_norm_givens", "phase:round"};
+        "phase:y_inv_f32", "phase:rows_inv_f32", "phase:vector_D_to_G", "phase:unused11",
+        "phase:unused12", "phase:unused13", "phase:round"};
     unsigned long long h[2 * kPhaseSlots];
     if (cudaMemcpy(h, g_phase_buf, sizeof(h), cudaMemcpyDeviceToHost) == cudaSuccess) {
       for (int id = 0; id < 15; ++id) {

@@ -15,7 +15,8 @@ enum SolveAction {
   ACT_RESID_ZERO = 1,   // r = b (x = 0)
   ACT_MV_RESIDUAL = 2,  // r = b - A64 x
   ACT_MV_ARNOLDI = 3,   // Arnoldi step j
-  ACT_FINISH = 4        // back substitution, x += V y
+  ACT_FINISH = 4,       // back substitution, x += V y
+  ACT_RHS = 5           // Neumann right-hand side b = -kappa S* L'^{-1} S V_b (float64)
 };
 
 // Read-only during a launch.
@@ -36,7 +37,8 @@ struct SolveInst {
   double* part;     // 3 sections x nchunk x pstride
   int nchunk;
   int pstride;
-  const double* bvec;
+  double* bvec;         // right-hand side (written by ACT_RHS)
+  const double* vdata;  // V_b for ACT_RHS
   double* x;
   double* r;
   int bc;
@@ -54,7 +56,7 @@ struct SolveInst {
 struct SolveState {
   int action, prec, j, kdim;
   int iters, outer, status, matvecs;
-  int nhist, pad;
+  int nhist, xinit;  // xinit: the solve starts from a caller-given x
   double beta, bnorm, tol_abs, rel;
 };
 

@@ -31,31 +31,41 @@ namespace ibdl {
 
 constexpr unsigned kSpinLimit = 1u << 27;  // x >= 20 ns sleeps: a few seconds
 
-__device__ bool grid_barrier(unsigned* bar, unsigned nblocks) {
+// Counting barrier among `parties` blocks on ctr[0] (arrivals) and ctr[1]
+// (generation).  The spin is bounded: on timeout it raises *err, which every
+// later barrier sees, and all blocks leave the kernel.
+__device__ bool counted_barrier(unsigned* ctr, unsigned parties, unsigned* err) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* vgen = bar + 1;
+    volatile unsigned* vgen = ctr + 1;
     const unsigned gen = *vgen;
     __threadfence();
-    const unsigned arrived = atomicAdd(bar, 1u);
-    if (arrived == nblocks - 1) {
-      atomicExch(bar, 0u);
+    const unsigned arrived = atomicAdd(ctr, 1u);
+    if (arrived == parties - 1) {
+      atomicExch(ctr, 0u);
       __threadfence();
-      atomicAdd(bar + 1, 1u);
+      atomicAdd(ctr + 1, 1u);
     } else {
       unsigned spins = 0;
       while (*vgen == gen) {
         if (++spins > kSpinLimit) {
-          atomicExch(bar + 2, 1u);
+          atomicExch(err, 1u);
           break;
         }
+        if (*(volatile unsigned*)err) break;
         __nanosleep(20);
       }
     }
     __threadfence();
   }
   __syncthreads();
-  return *(volatile unsigned*)(bar + 2) == 0u;
+  return *(volatile unsigned*)err == 0u;
+}
+
+// bar[0..1]: grid barrier, bar[2]: error flag, bar[4 + 4k ..]: barrier of the
+// blocks that hold instance k's vector chunks.
+__device__ bool grid_barrier(unsigned* bar, unsigned nblocks) {
+  return counted_barrier(bar, nblocks, bar + 2);
 }
 
 struct RoundView {
@@ -117,6 +127,13 @@ __device__ void chunk_dots(const SolveInst& I, double xi, bool valid, int i, int
   __syncthreads();
 }
 
+// w - sum_{c < ncols} h[c] V_c[i]
+__device__ __forceinline__ double sub_projection(const SolveInst& I, double w, int i, int ncols,
+                                                 const double* h) {
+  for (int c = 0; c < ncols; ++c) w -= h[c] * __ldcg(I.V + (size_t)c * I.ld + i);
+  return w;
+}
+
 template <typename T>
 __device__ __forceinline__ SpectralWs<T> ws_of(const SolveInst& I);
 template <>
@@ -128,9 +145,12 @@ __device__ __forceinline__ SpectralWs<float> ws_of<float>(const SolveInst& I) {
   return I.w32;
 }
 
-__device__ __forceinline__ bool is_mv(int a) { return a == ACT_MV_ARNOLDI || a == ACT_MV_RESIDUAL; }
+__device__ __forceinline__ bool is_mv(int a) {
+  return a == ACT_MV_ARNOLDI || a == ACT_MV_RESIDUAL || a == ACT_RHS;
+}
 
 __device__ __forceinline__ const double* mv_input(const SolveInst& I, const RoundView& v) {
+  if (v.action == ACT_RHS) return nullptr;
   return v.action == ACT_MV_ARNOLDI ? I.V + (size_t)v.j * I.ld : I.x;
 }
 
@@ -155,8 +175,13 @@ template <typename T, int D>
 __device__ __noinline__ void solver_rows_fwd(const SolveInst& I, const double* q, int item,
                                              unsigned char* smem) {
   SpreadSrc src;
-  src.q_div = q;
-  src.coef_div = 1.0;
+  if (q) {
+    src.q_div = q;
+    src.coef_div = 1.0;
+  } else {
+    src.v_plain = I.vdata;  // right-hand side: -S V_b
+    src.coef_plain = -1.0;
+  }
   const SpectralWs<T> ws = ws_of<T>(I);
   phase_rows_fwd<T, D>(I.g, I.p, I.b, src, ws.spec, ws.tw, nullptr, item, smem);
 }
@@ -215,6 +240,7 @@ __device__ int phase_items(const SolveInst& I, const RoundView& v, int phase) {
 
 // ---- vector phases ------------------------------------------------------------
 
+template <int D>
 __device__ void phase_D(const SolveInst& I, const RoundView& v, int chunk, BlockRed& R) {
   const int i = chunk * blockDim.x + threadIdx.x;
   const bool valid = i < I.p.m;
@@ -232,13 +258,18 @@ __device__ void phase_D(const SolveInst& I, const RoundView& v, int chunk, Block
     }
     return;
   }
+  if (v.action == ACT_RHS) {
+    // b = S* grid, grid = -kappa L'^{-1} S V_b (the Neumann right-hand side)
+    if (valid) I.bvec[i] = interp_point<double, D>(I.g, I.p, I.w64.grid, i);
+    return;
+  }
   const double jump = I.bc == IBDL_DIRICHLET ? 0.5 : -0.5;
   if (v.action == ACT_MV_ARNOLDI) {
     double w = 0;
     if (valid) {
       const double* vin = I.V + (size_t)v.j * I.ld;
-      const double acc = v.prec ? (double)interp_point<float, 2>(I.g, I.p, I.w32.grid, i)
-                                : interp_point<double, 2>(I.g, I.p, I.w64.grid, i);
+      const double acc = v.prec ? (double)interp_point<float, D>(I.g, I.p, I.w32.grid, i)
+                                : interp_point<double, D>(I.g, I.p, I.w64.grid, i);
       w = acc + jump * __ldcg(vin + i);
       I.V[(size_t)(v.j + 1) * I.ld + i] = w;
     }
@@ -248,55 +279,9 @@ __device__ void phase_D(const SolveInst& I, const RoundView& v, int chunk, Block
   // residual actions: r = b - A x (or r = b), partial ||r||^2 and ||b||^2
   double r = 0, bi = 0;
   if (valid) {
-    bi = I.bvec[i];
+    bi = __ldcg(I.bvec + i);
     if (v.action == ACT_MV_RESIDUAL) {
-      const double t = interp_point<double, 2>(I.g, I.p, I.w64.grid, i) + jump * __ldcg(I.x + i);
-      r = bi - t;
-    } else {
-      r = bi;
-    }
-    I.r[i] = r;
-  }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const double s0 = warp_sum(valid ? r * r : 0.0);
-  const double s1 = warp_sum(valid ? bi * bi : 0.0);
-  if (lane == 0) {
-    R.red[0][wid] = s0;
-    R.red[1][wid] = s1;
-  }
-  __syncthreads();
-  if (threadIdx.x < 2) {
-    double s = 0;
-    for (int w = 0; w < nw; ++w) s += R.red[threadIdx.x][w];
-    part1[(size_t)chunk * I.pstride + threadIdx.x] = s;
-  }
-  __syncthreads();
-}
-
-// 3D instances interpolate with the 3D kernel
-__device__ void phase_D3(const SolveInst& I, const RoundView& v, int chunk, BlockRed& R) {
-  // identical to phase_D apart from the interpolation template
-  const int i = chunk * blockDim.x + threadIdx.x;
-  const bool valid = i < I.p.m;
-  double* part1 = I.part;
-  const double jump = I.bc == IBDL_DIRICHLET ? 0.5 : -0.5;
-  if (v.action == ACT_MV_ARNOLDI) {
-    double w = 0;
-    if (valid) {
-      const double* vin = I.V + (size_t)v.j * I.ld;
-      const double acc = v.prec ? (double)interp_point<float, 3>(I.g, I.p, I.w32.grid, i)
-                                : interp_point<double, 3>(I.g, I.p, I.w64.grid, i);
-      w = acc + jump * __ldcg(vin + i);
-      I.V[(size_t)(v.j + 1) * I.ld + i] = w;
-    }
-    chunk_dots(I, w, valid, i, v.j + 1, false, part1, chunk, R);
-    return;
-  }
-  double r = 0, bi = 0;
-  if (valid) {
-    bi = I.bvec[i];
-    if (v.action == ACT_MV_RESIDUAL) {
-      const double t = interp_point<double, 3>(I.g, I.p, I.w64.grid, i) + jump * __ldcg(I.x + i);
+      const double t = interp_point<double, D>(I.g, I.p, I.w64.grid, i) + jump * __ldcg(I.x + i);
       r = bi - t;
     } else {
       r = bi;
@@ -336,8 +321,7 @@ __device__ void cgs_pass(const SolveInst& I, const RoundView& v, int chunk, Bloc
   double w = 0;
   double* wp = I.V + (size_t)(v.j + 1) * I.ld;
   if (valid) {
-    w = __ldcg(wp + i);
-    for (int c = 0; c < ncols; ++c) w -= R.h[c] * __ldcg(I.V + (size_t)c * I.ld + i);
+    w = sub_projection(I, __ldcg(wp + i), i, ncols, R.h);
     wp[i] = w;
   }
   __syncthreads();
@@ -364,15 +348,15 @@ __device__ void phase_E(const SolveInst& I, const RoundView& v, int chunk, Block
     cgs_pass(I, v, chunk, R, part1, part2, true);
     return;
   }
+  if (v.action == ACT_RHS) return;
   const int i = chunk * blockDim.x + threadIdx.x;
   const bool valid = i < I.p.m;
   if (v.action == ACT_FINISH) {
-    if (valid) {
-      double x = __ldcg(I.x + i);
-      for (int c = 0; c < v.kdim; ++c)
-        x += __ldcg(I.ysol + c) * __ldcg(I.V + (size_t)c * I.ld + i);
-      I.x[i] = x;
-    }
+    // x += V y: stage -y in shared memory, then one batched pass over V
+    for (int c = threadIdx.x; c < v.kdim; c += blockDim.x) R.h[c] = -__ldcg(I.ysol + c);
+    __syncthreads();
+    if (valid) I.x[i] = sub_projection(I, __ldcg(I.x + i), i, v.kdim, R.h);
+    __syncthreads();
     return;
   }
   // residual actions: V0 = r / ||r||
@@ -408,7 +392,7 @@ __device__ void control(const SolveInst& I, SolveState* S, const RoundView& v, d
     s.status = vs->status;
     s.matvecs = vs->matvecs;
     s.nhist = vs->nhist;
-    s.pad = vs->pad;
+    s.xinit = vs->xinit;
     s.beta = vs->beta;
     s.bnorm = vs->bnorm;
     s.tol_abs = vs->tol_abs;
@@ -455,6 +439,9 @@ __device__ void control(const SolveInst& I, SolveState* S, const RoundView& v, d
     }
   } else if (v.action == ACT_FINISH) {
     s.action = ACT_MV_RESIDUAL;
+    s.prec = 0;
+  } else if (v.action == ACT_RHS) {
+    s.action = s.xinit ? ACT_MV_RESIDUAL : ACT_RESID_ZERO;
     s.prec = 0;
   } else {
     if (v.action == ACT_MV_RESIDUAL) s.matvecs++;
@@ -523,7 +510,7 @@ __device__ void phase_G(const SolveInst& I, SolveState* S, const RoundView& v, i
   }
   if (chunk != 0) return;
   double beta = 0, b2 = 0;
-  if (v.action != ACT_FINISH) {
+  if (v.action != ACT_FINISH && v.action != ACT_RHS) {
     reduce_parts(I.part, I.nchunk, I.pstride, 0, 2, R.h);
     beta = sqrt(R.h[0]);
     b2 = R.h[1];
@@ -567,6 +554,19 @@ __device__ void vec_single(const SolveInst& I, SolveState* S, const RoundView& v
   const double jump = I.bc == IBDL_DIRICHLET ? 0.5 : -0.5;
   const bool d3 = I.g.dim == 3;
   // element k of this thread: i = tid + k * nt (m <= kSingleK * nt)
+  if (v.action == ACT_RHS) {
+#pragma unroll
+    for (int k = 0; k < kSingleK; ++k) {
+      const int i = tid + k * nt;
+      if (i < m)
+        I.bvec[i] = d3 ? interp_point<double, 3>(I.g, I.p, I.w64.grid, i)
+                       : interp_point<double, 2>(I.g, I.p, I.w64.grid, i);
+    }
+    __syncthreads();
+    if (tid == 0) control(I, S, v, 0, 0, 0, R);
+    __syncthreads();
+    return;
+  }
   if (v.action == ACT_FINISH) {
     if (tid == 0) {
       const int k = v.kdim, ldh = I.restart + 1;
@@ -676,7 +676,7 @@ __device__ void vec_single(const SolveInst& I, SolveState* S, const RoundView& v
     const int i = tid + k * nt;
     rk[k] = 0.0;
     if (i < m) {
-      const double bi = I.bvec[i];
+      const double bi = __ldcg(I.bvec + i);
       double r = bi;
       if (v.action == ACT_MV_RESIDUAL) {
         const double acc = d3 ? interp_point<double, 3>(I.g, I.p, I.w64.grid, i)
@@ -714,7 +714,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // Phase timing (optional): block 0, thread 0 adds the wall time between
 // consecutive grid-barrier exits to ptimes[2*id] and counts in ptimes[2*id+1].
 // Ids: 0..4 matvec phases in float64 (rows_fwd, y fwd, solve, y inv,
-// rows_inv), 5..9 the same in float32, 10..13 vector phases D..G, 14 round
+// rows_inv), 5..9 the same in float32, 10 the vector phases D..G, 14 round
 // bookkeeping.
 __device__ __forceinline__ void phase_tick(unsigned long long* ptimes, int id,
                                            unsigned long long& t0) {
@@ -789,41 +789,42 @@ __global__ void __launch_bounds__(kSolverThreads, 2)
       if (!grid_barrier(bar, nblocks)) return;
       phase_tick(ptimes, phase + 5 * prec0, t0);
     }
-    // vector phases D..G (single-block instances finish in D)
-    for (int phase = 5; phase < 9; ++phase) {
-      if (phase > 5 && !any_multi) break;
-      if (phase == 5) {
-        for (int k = bid; k < ninst; k += G) {
-          const RoundView v = rv[k];
-          if (insts[k].single && v.action != ACT_DONE) vec_single(insts[k], states + k, v, R);
-        }
-      }
+    // vector phases D..G.  Single-block instances finish in one block; the
+    // others run D, E, F, G on the blocks that hold their chunks, separated
+    // by a barrier among those blocks only, and one grid barrier closes the
+    // round.
+    for (int k = bid; k < ninst; k += G) {
+      const RoundView v = rv[k];
+      if (insts[k].single && v.action != ACT_DONE) vec_single(insts[k], states + k, v, R);
+    }
+    if (any_multi) {
       int base = 0;
       for (int k = 0; k < ninst; ++k) {
         const RoundView v = rv[k];
-        const int cnt = phase_items(insts[k], v, phase);
+        const SolveInst& I = insts[k];
+        const int cnt = phase_items(I, v, 5);
         if (cnt == 0) continue;
         const int first = ((bid - base) % G + G) % G;
-        for (int it = first; it < cnt; it += G) {
-          const SolveInst& I = insts[k];
-          if (phase == 5) {
-            if (I.g.dim == 2 || v.action == ACT_FINISH)
-              phase_D(I, v, it, R);
-            else
-              phase_D3(I, v, it, R);
-          } else if (phase == 6) {
-            phase_E(I, v, it, R);
-          } else if (phase == 7) {
-            phase_F(I, v, it, R);
-          } else {
-            phase_G(I, states + k, v, it, R);
-          }
-        }
         base += cnt;
+        if (first >= cnt) continue;
+        const unsigned parties = cnt < G ? (unsigned)cnt : (unsigned)G;
+        unsigned* ib = bar + 4 + 4 * k;
+        for (int it = first; it < cnt; it += G) {
+          if (I.g.dim == 2)
+            phase_D<2>(I, v, it, R);
+          else
+            phase_D<3>(I, v, it, R);
+        }
+        if (!counted_barrier(ib, parties, bar + 2)) return;
+        for (int it = first; it < cnt; it += G) phase_E(I, v, it, R);
+        if (!counted_barrier(ib, parties, bar + 2)) return;
+        for (int it = first; it < cnt; it += G) phase_F(I, v, it, R);
+        if (!counted_barrier(ib, parties, bar + 2)) return;
+        for (int it = first; it < cnt; it += G) phase_G(I, states + k, v, it, R);
       }
-      if (!grid_barrier(bar, nblocks)) return;
-      phase_tick(ptimes, phase + 5, t0);
     }
+    if (!grid_barrier(bar, nblocks)) return;
+    phase_tick(ptimes, 10, t0);
   }
 }
 
@@ -867,7 +868,8 @@ cudaError_t launch_persistent_solve(const SolveInst* d_insts, SolveState* d_stat
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   if (per_sm > 2) per_sm = 2;
   const int blocks = per_sm * sm_count;
-  if ((e = cudaMemsetAsync(d_bar, 0, 4 * sizeof(unsigned), st))) return e;
+  if ((e = cudaMemsetAsync(d_bar, 0, (4 + 4 * (size_t)ninst) * sizeof(unsigned), st)))
+    return e;
   void* args[] = {(void*)&d_insts, (void*)&d_states, (void*)&ninst, (void*)&d_bar,
                   (void*)&ptimes};
   prof_begin(st);
