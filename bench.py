@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--engine", type=int, default=0, choices=[0, 1],
                     help="0: persistent single-launch solver, 1: host-driven loop")
+    ap.add_argument("--serve-requests", type=int, default=200,
+                    help="requests of the mixed serving stream (0: skip it)")
     return ap.parse_args()
 
 
@@ -64,6 +66,64 @@ def combine_ranks(local_ms, local_solves, dist=None, device=None):
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     dist.all_reduce(s, op=dist.ReduceOp.SUM)
     return float(t.item()), int(s.item())
+
+
+def run_serving(pkg, nreq, seed=3, rate=2000.0, budget=120 << 30):
+    """Replay the seeded mixed serving stream (Poisson arrivals) in real time
+    through the continuous-batching server; latency = arrival -> result."""
+    import torch
+    from paper_2203_12126_gb300 import ibdl
+    reqs = configs.c5_requests(nreq, seed=seed, rate=rate)
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(min(budget, 0.8 * free))
+    srv = pkg.Server(memory_budget=budget, max_active=64, rounds_per_step=4, reserve_sms=8,
+                     tol=1e-8)
+    t0 = srv.clock() + 0.02
+    nxt = 0
+    outstanding = {}
+    recs = []
+    while nxt < len(reqs) or outstanding:
+        now = srv.clock()
+        while nxt < len(reqs) and t0 + reqs[nxt].t <= now:
+            r = reqs[nxt]
+            rid = srv.submit(r.problem.geom, r.problem.bdata, bc=r.problem.bc,
+                             precision=ibdl.FP32_REFINED, t_arrival=t0 + r.t)
+            outstanding[rid] = r
+            nxt += 1
+        st = srv.stats()
+        if st["active"] == 0 and st["queued"] == 0 and nxt < len(reqs):
+            time.sleep(max(0.0, t0 + reqs[nxt].t - srv.clock()))
+            continue
+        for rid in srv.step():
+            r = outstanding.pop(rid)
+            _, rec = srv.take(rid, r.problem.geom.m)
+            rec["kind"] = r.kind
+            recs.append(rec)
+    stats = srv.stats()
+    srv.close()
+    lat = np.array([(x["t_done"] - x["t_arrival"]) * 1e3 for x in recs])
+    span = max(x["t_done"] for x in recs) - t0
+    ok = [x for x in recs if x["status"] == 0]
+    kinds = {}
+    for x in recs:
+        k = x["kind"].rsplit("-", 1)[0]
+        kinds.setdefault(k, []).append((x["t_done"] - x["t_arrival"]) * 1e3)
+    return {
+        "workload": f"mixed stream, {nreq} requests, Poisson {rate:g}/s (seed {seed}): 80% 2D "
+                    "stars N in {256,512,1024}^2, 20% 3D spheres/ellipsoids N in "
+                    "{64,128,256}^3, kappa log-U[1e-4,1e-1], Dirichlet/Neumann 50/50, "
+                    "float32-refined, tol 1e-8",
+        "requests": nreq, "completed_ok": len(ok),
+        "solves_per_s": len(ok) / span,
+        "latency_ms": {"p50": float(np.percentile(lat, 50)),
+                       "p99": float(np.percentile(lat, 99)),
+                       "max": float(lat.max())},
+        "latency_p50_ms_by_kind": {k: float(np.median(v)) for k, v in sorted(kinds.items())},
+        "max_rel_residual": float(max(x["rel_residual"] for x in ok)) if ok else None,
+        "memory_budget_bytes": budget, "peak_device_bytes": int(stats["peak_bytes"]),
+        "slices": int(stats["launches"]),
+        "offered_span_s": float(reqs[-1].t), "makespan_s": float(span),
+    }
 
 
 def problems():
@@ -410,6 +470,10 @@ def main():
            "note": "ibdl_solve with pinned host U_b/V_b in and host Q/U out; copies "
                    "inside the call; host wall clock"}
 
+    serving = None
+    if args.serve_requests > 0:
+        serving = run_serving(pkg, args.serve_requests)
+
     out = None
     if rank == 0:
         cpu = None
@@ -447,6 +511,7 @@ def main():
             "phases": phases,
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "serving": serving,
             "gpu_launches": int(launches),
             "wall_s_timed": wall,
             "clocks": clocks,

@@ -207,6 +207,95 @@ ibdl_status ibdl_solve_batched(ibdl_batch b, int32_t count, const ibdl_geometry*
                                const ibdl_solve_opts* opts, ibdl_solve_info* infos,
                                ibdl_status* statuses, void* stream);
 
+/* Serving engine: continuous batching of independent IBDL solves.
+ *
+ * A server owns a table of `max_active` solver slots and a FIFO queue.
+ * Requests (a geometry description with its boundary data, g = 0) are
+ * submitted at any time; ibdl_server_step then
+ *   1. launches one slice of the persistent solver (ibdl_solve_batched's
+ *      kernel, stopped after `rounds_per_step` GMRES rounds) over every
+ *      active slot -- requests of different dim, n, m, kappa, bc and
+ *      precision advance together and keep their grids, spectra, FFT
+ *      tables and Krylov bases resident in device memory between slices;
+ *   2. while that slice runs, admits queued requests in arrival order as long
+ *      as a slot is free and the device bytes of all admitted requests stay
+ *      within `memory_budget`: each one's geometry is built on a second
+ *      stream, on the `reserve_sms` SMs the solver leaves free, and it joins
+ *      the next slice;
+ *   3. waits for the slice and retires the requests whose solve finished,
+ *      releasing their slot and memory.
+ * Every request is solved exactly as ibdl_solve would solve it alone (the
+ * same state machine, tolerances and precision); only the scheduling is
+ * shared.  This is the method's solve (Sec. 5.3) per request in serving
+ * form; the paper itself has no serving counterpart.
+ *
+ * Thread safety: calls on one server are serialised by an internal lock.
+ * Each step synchronises the server's streams. */
+typedef struct ibdl_server_s* ibdl_server;
+
+typedef struct {
+  int64_t memory_budget;    /* bytes of device memory admitted requests may
+                               hold; 0 = 80% of the free memory at creation */
+  int32_t max_active;       /* solver slots, 1..512; default 64 */
+  int32_t rounds_per_step;  /* solver rounds per slice, >= 1; default 8 */
+  int32_t reserve_sms;      /* SMs left free for request set-up while a slice
+                               runs, 0..(SM count - 1); default 8 */
+  int32_t reserved;
+  ibdl_solve_opts opts;     /* tolerances of every request (x0 is ignored) */
+} ibdl_server_config;
+
+typedef struct {
+  int64_t id;
+  int32_t status;           /* ibdl_status of the solve */
+  int32_t slot;
+  double t_arrival;         /* seconds on ibdl_server_clock(): as submitted */
+  double t_admit;           /* geometry built, slot taken */
+  double t_done;            /* retired after its last slice */
+  int64_t device_bytes;     /* device memory the request held */
+  ibdl_solve_info info;
+} ibdl_request_result;
+
+typedef struct {
+  int32_t queued, active, finished;  /* finished = completed, not yet taken */
+  int32_t reserved;
+  int64_t bytes_in_use, peak_bytes, memory_budget;
+  int64_t steps, launches, submitted;
+} ibdl_server_stats;
+
+void ibdl_server_config_default(ibdl_server_config* cfg);
+/* Errors: IBDL_ERR_INVALID_ARG (bad config), IBDL_ERR_CUDA. */
+ibdl_status ibdl_server_create(const ibdl_server_config* cfg, ibdl_server* out);
+/* Waits for the server's streams, releases every request still held. */
+void ibdl_server_destroy(ibdl_server s);
+/* Monotonic clock (seconds) on which request times are measured. */
+double ibdl_server_clock(void);
+/* Queue a request.  desc pointers (points, normals, weights) and bdata
+ * (U_b for Dirichlet, V_b for Neumann, length desc->m) may be host or device
+ * memory; they are copied before the call returns.  t_arrival: the request's
+ * arrival time on ibdl_server_clock() (latency is t_done - t_arrival), or a
+ * negative value for "now".  Errors: IBDL_ERR_INVALID_ARG (size and pointer
+ * checks of ibdl_create_geometry; the rest are made at admission, where a
+ * failure finishes the request with that status), IBDL_ERR_NONFINITE
+ * (bdata not finite). */
+ibdl_status ibdl_server_submit(ibdl_server s, const ibdl_geometry_desc* desc,
+                               const double* bdata, double t_arrival, int64_t* id_out);
+/* One scheduling step (see above).  Writes up to max_ids ids of requests
+ * finished in this step to done_ids (may be NULL) and their count to
+ * *n_done.  Returns IBDL_OK, or IBDL_ERR_TIMEOUT / IBDL_ERR_CUDA when the
+ * slice failed (the active requests are then finished with that status).
+ * A request whose own solve fails, or that alone exceeds the memory budget
+ * (IBDL_ERR_OOM), is finished with its status; the step still returns
+ * IBDL_OK. */
+ibdl_status ibdl_server_step(ibdl_server s, int64_t* done_ids, int32_t max_ids,
+                             int32_t* n_done);
+/* Hand over a finished request: q_out (host or device, length m, may be
+ * NULL) receives its density Q (Dirichlet) or boundary values U (Neumann),
+ * *res its record; the server forgets it.  IBDL_ERR_INVALID_ARG if the id
+ * is unknown or not finished yet. */
+ibdl_status ibdl_server_take(ibdl_server s, int64_t id, double* q_out,
+                             ibdl_request_result* res);
+ibdl_status ibdl_server_get_stats(ibdl_server s, ibdl_server_stats* out);
+
 /* Component operators, exposed for testing and for callers that compose
  * their own solvers.  All float64 unless `precision` = 1.
  *   ibdl_spread_div: f = S~ q on the grid (Sec. 5.2, eq. (Stilde)).

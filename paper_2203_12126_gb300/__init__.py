@@ -7,4 +7,4 @@ fallback: loading fails loudly if the library has not been built.
 """
 from . import ibdl  # noqa: F401
 from .ibdl import (DIRICHLET, FP32_REFINED, FP64, NEUMANN, Geometry,  # noqa: F401
-                   IbdlError, kernel_launch_count, load)
+                   IbdlError, Server, kernel_launch_count, load)

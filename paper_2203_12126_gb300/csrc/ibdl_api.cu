@@ -13,7 +13,10 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
+#include <chrono>
+#include <deque>
 #include <map>
 #include <mutex>
 #include <string>
@@ -1207,3 +1210,428 @@ const char* ibdl_last_error_message(void) { return g_err.c_str(); }
 int32_t ibdl_version(void) { return 100 * IBDL_VERSION_MAJOR + IBDL_VERSION_MINOR; }
 
 }  // extern "C"
+
+// =============================================================================
+// Serving engine (continuous batching over the persistent solver)
+// =============================================================================
+
+namespace {
+
+double server_now() {
+  using namespace std::chrono;
+  return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+// Device bytes a request will hold, from the sizes ibdl_create_geometry
+// allocates (tile lists at their largest: 3 tiles per point in 2D, 18 in 3D).
+int64_t estimate_request_bytes(const ibdl_geometry_desc& d) {
+  const int64_t n = d.n, m = d.m;
+  const int64_t ncells = d.dim == 3 ? n * n * n : n * n;
+  const int64_t spec = (n / 2 + 1) * (ncells / n);
+  const int64_t ntw = fft_tw_count((int)n);
+  const int64_t rows = rows_per_tile(d.dim, (int)n);
+  const int64_t ntiles = (n / rows) * (d.dim == 3 ? n : 1);
+  const int64_t ld = (m + 31) / 32 * 32;
+  int64_t b = 7 * m * 8 + 3 * m * 4 + 12 * m * 8 + 12 * m * 4;      // points, delta weights
+  b += 2 * (ntiles + 1) * 4 + (d.dim == 3 ? 18 : 3) * m * 4;        // tile lists
+  b += spec * 16 + ncells * 8 + ntw * 16 + n * 8;                   // float64 spectral
+  if (d.precision == IBDL_FP32_REFINED) b += spec * 8 + ncells * 4 + ntw * 8 + n * 4;
+  b += (65 * ld + 65 * 64 + 3 * 64 + 65 + 8 + 7 * ld) * 8;          // Krylov, vectors
+  b += 3 * ((m + kSolverThreads - 1) / kSolverThreads) * 66 * 8 + kHistCap * 8;
+  return b + (1 << 16);
+}
+
+}  // namespace
+
+struct SrvReq {
+  int64_t id = 0;
+  ibdl_geometry_desc desc;
+  std::vector<double> arr[7];  // x, y, z, nx, ny, nz, w
+  std::vector<double> bdata;
+  double t_arrival = 0, t_admit = 0, t_done = 0;
+  int64_t est = 0, held = 0;
+  ibdl_geometry g = nullptr;
+  int slot = -1;
+  ibdl_status status = IBDL_ERR_NOT_CONVERGED;
+  ibdl_solve_info info;
+  std::vector<double> q;
+};
+
+struct ibdl_server_s {
+  ibdl_server_config cfg;
+  int cap = 0;
+  cudaStream_t solve_st = nullptr, setup_st = nullptr;
+  SolveInst* d_inst = nullptr;
+  SolveState* d_state = nullptr;
+  unsigned* d_bar = nullptr;
+  SolveInst* h_inst = nullptr;         // pinned: descriptors of fresh slots
+  SolveState* h_state_in = nullptr;    // pinned: initial states of fresh slots
+  SolveState* h_state_out = nullptr;   // pinned: states after a slice
+  unsigned* h_bar = nullptr;           // pinned
+  std::vector<SrvReq*> slot;
+  std::vector<char> fresh;             // admitted since the last launch
+  std::deque<SrvReq*> queue;
+  std::map<int64_t, SrvReq*> done;
+  std::vector<int64_t> just_done;      // finished during the current step
+  int64_t next_id = 1, bytes = 0, peak = 0, steps = 0, launches = 0;
+  std::mutex mu;
+  ~ibdl_server_s() {
+    if (solve_st) cudaStreamSynchronize(solve_st);
+    if (setup_st) cudaStreamSynchronize(setup_st);
+    for (SrvReq* r : slot)
+      if (r) {
+        ibdl_destroy_geometry(r->g);
+        delete r;
+      }
+    for (SrvReq* r : queue) delete r;
+    for (auto& kv : done) delete kv.second;
+    if (d_inst) cudaFree(d_inst);
+    if (d_state) cudaFree(d_state);
+    if (d_bar) cudaFree(d_bar);
+    if (h_inst) cudaFreeHost(h_inst);
+    if (h_state_in) cudaFreeHost(h_state_in);
+    if (h_state_out) cudaFreeHost(h_state_out);
+    if (h_bar) cudaFreeHost(h_bar);
+    if (solve_st) cudaStreamDestroy(solve_st);
+    if (setup_st) cudaStreamDestroy(setup_st);
+  }
+};
+
+namespace {
+
+ibdl_status sanitize_opts(ibdl_solve_opts* o) {
+  if (!(o->tol > 0) || !isfinite(o->tol)) return fail(IBDL_ERR_INVALID_ARG, "tol must be > 0");
+  if (o->restart < 1 || o->restart > 64) return fail(IBDL_ERR_INVALID_ARG, "restart in 1..64");
+  if (o->max_iters < 1) return fail(IBDL_ERR_INVALID_ARG, "max_iters >= 1");
+  if (o->max_refine < 1) o->max_refine = 1;
+  if (!(o->inner_tol > 0) || o->inner_tol >= 1) o->inner_tol = 1e-5;
+  o->x0 = nullptr;
+  o->engine = 0;
+  return IBDL_OK;
+}
+
+void finish_request(ibdl_server_s* s, SrvReq* r, ibdl_status st) {
+  r->status = st;
+  r->t_done = server_now();
+  s->done[r->id] = r;
+  s->just_done.push_back(r->id);
+}
+
+// Builds the request's geometry on the set-up stream and stages its data;
+// the slot's descriptor and initial state wait in the pinned tables until
+// the next launch.
+ibdl_status admit_one(ibdl_server_s* s, SrvReq* r, int k) {
+  ibdl_geometry g = nullptr;
+  IBDL_TRY(ibdl_create_geometry(&r->desc, s->setup_st, &g));
+  const size_t mb = sizeof(double) * (size_t)g->m;
+  // Dirichlet: b = U_b; Neumann: V_b, from which the solver's first action
+  // builds b
+  double* target = g->bc == IBDL_NEUMANN ? g->stage_a : g->vb;
+  cudaError_t e = cudaMemcpyAsync(target, r->bdata.data(), mb, cudaMemcpyHostToDevice,
+                                  s->setup_st);
+  if (!e) e = cudaMemsetAsync(g->vx, 0, mb, s->setup_st);
+  if (!e) e = cudaStreamSynchronize(s->setup_st);
+  if (e) {
+    ibdl_destroy_geometry(g);
+    return cuda_fail(e, "server: staging request data");
+  }
+  r->g = g;
+  r->slot = k;
+  r->held = g->bytes;
+  r->t_admit = server_now();
+  s->h_inst[k] = make_inst(g, s->cfg.opts, s->cap);
+  s->h_inst[k].vdata = g->stage_a;
+  s->h_state_in[k] = initial_state(true, g->bc == IBDL_NEUMANN);
+  s->slot[k] = r;
+  s->fresh[k] = 1;
+  s->bytes += r->held;
+  if (s->bytes > s->peak) s->peak = s->bytes;
+  return IBDL_OK;
+}
+
+// Admits queued requests in arrival order while a slot is free and the
+// budget allows; a request larger than the whole budget fails with OOM.
+void admit_queued(ibdl_server_s* s) {
+  while (!s->queue.empty()) {
+    SrvReq* r = s->queue.front();
+    if (r->est > s->cfg.memory_budget) {
+      s->queue.pop_front();
+      finish_request(s, r, IBDL_ERR_OOM);
+      continue;
+    }
+    int k = -1;
+    for (int j = 0; j < s->cap; ++j)
+      if (!s->slot[j]) {
+        k = j;
+        break;
+      }
+    if (k < 0) return;
+    if (s->bytes + r->est > s->cfg.memory_budget) return;
+    s->queue.pop_front();
+    const ibdl_status st = admit_one(s, r, k);
+    if (st != IBDL_OK) finish_request(s, r, st);
+  }
+}
+
+// Retires slot k: result to the host, geometry released.
+void retire(ibdl_server_s* s, int k, ibdl_status st, const SolveState* state) {
+  SrvReq* r = s->slot[k];
+  ibdl_geometry g = r->g;
+  r->q.resize(g->m);
+  cudaMemcpy(r->q.data(), g->vx, sizeof(double) * g->m, cudaMemcpyDeviceToHost);
+  std::vector<double> hist(kHistCap);
+  cudaMemcpy(hist.data(), g->d_hist, sizeof(double) * kHistCap, cudaMemcpyDeviceToHost);
+  memset(&r->info, 0, sizeof(r->info));
+  if (state) info_from_state(*state, hist.data(), &r->info);
+  ibdl_destroy_geometry(g);
+  r->g = nullptr;
+  s->bytes -= r->held;
+  s->slot[k] = nullptr;
+  s->fresh[k] = 0;
+  finish_request(s, r, st);
+}
+
+}  // namespace
+
+void ibdl_server_config_default(ibdl_server_config* cfg) {
+  if (!cfg) return;
+  memset(cfg, 0, sizeof(*cfg));
+  cfg->memory_budget = 0;
+  cfg->max_active = 64;
+  cfg->rounds_per_step = 8;
+  cfg->reserve_sms = 8;
+  ibdl_solve_opts_default(&cfg->opts);
+}
+
+double ibdl_server_clock(void) { return server_now(); }
+
+ibdl_status ibdl_server_create(const ibdl_server_config* cfg_in, ibdl_server* out) {
+  g_err.clear();
+  if (!out) return fail(IBDL_ERR_INVALID_ARG, "NULL out");
+  ibdl_server_config cfg;
+  ibdl_server_config_default(&cfg);
+  if (cfg_in) cfg = *cfg_in;
+  if (cfg.max_active < 1 || cfg.max_active > kMaxBatch)
+    return fail(IBDL_ERR_INVALID_ARG, "max_active must be in [1, 512]");
+  if (cfg.rounds_per_step < 1) return fail(IBDL_ERR_INVALID_ARG, "rounds_per_step >= 1");
+  if (cfg.memory_budget < 0) return fail(IBDL_ERR_INVALID_ARG, "memory_budget >= 0");
+  IBDL_TRY(sanitize_opts(&cfg.opts));
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (!e) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e) return cuda_fail(e, "server: device query");
+  if (cfg.reserve_sms < 0 || cfg.reserve_sms >= sms)
+    return fail(IBDL_ERR_INVALID_ARG, "reserve_sms must leave at least one SM to the solver");
+  if (cfg.memory_budget == 0) {
+    size_t fr = 0, tot = 0;
+    if ((e = cudaMemGetInfo(&fr, &tot))) return cuda_fail(e, "server: cudaMemGetInfo");
+    cfg.memory_budget = (int64_t)(0.8 * (double)fr);
+  }
+  ibdl_server_s* s = new ibdl_server_s();
+  s->cfg = cfg;
+  s->cap = cfg.max_active;
+  const size_t nb = 4 + 4 * (size_t)s->cap;
+  e = cudaStreamCreateWithFlags(&s->solve_st, cudaStreamNonBlocking);
+  if (!e) e = cudaStreamCreateWithFlags(&s->setup_st, cudaStreamNonBlocking);
+  if (!e) e = cudaMalloc((void**)&s->d_inst, sizeof(SolveInst) * s->cap);
+  if (!e) e = cudaMalloc((void**)&s->d_state, sizeof(SolveState) * s->cap);
+  if (!e) e = cudaMalloc((void**)&s->d_bar, sizeof(unsigned) * nb);
+  if (!e) e = cudaMallocHost((void**)&s->h_inst, sizeof(SolveInst) * s->cap);
+  if (!e) e = cudaMallocHost((void**)&s->h_state_in, sizeof(SolveState) * s->cap);
+  if (!e) e = cudaMallocHost((void**)&s->h_state_out, sizeof(SolveState) * s->cap);
+  if (!e) e = cudaMallocHost((void**)&s->h_bar, sizeof(unsigned) * 4);
+  if (e) {
+    delete s;
+    return cuda_fail(e, "ibdl_server_create");
+  }
+  // every slot starts empty: zero descriptors, DONE states
+  memset(s->h_inst, 0, sizeof(SolveInst) * s->cap);
+  for (int k = 0; k < s->cap; ++k) {
+    memset(&s->h_state_out[k], 0, sizeof(SolveState));
+    s->h_state_out[k].action = ACT_DONE;
+  }
+  e = cudaMemcpy(s->d_inst, s->h_inst, sizeof(SolveInst) * s->cap, cudaMemcpyHostToDevice);
+  if (!e)
+    e = cudaMemcpy(s->d_state, s->h_state_out, sizeof(SolveState) * s->cap,
+                   cudaMemcpyHostToDevice);
+  if (e) {
+    delete s;
+    return cuda_fail(e, "ibdl_server_create");
+  }
+  s->slot.assign(s->cap, nullptr);
+  s->fresh.assign(s->cap, 0);
+  *out = s;
+  return IBDL_OK;
+}
+
+void ibdl_server_destroy(ibdl_server s) { delete s; }
+
+ibdl_status ibdl_server_submit(ibdl_server s, const ibdl_geometry_desc* d, const double* bdata,
+                               double t_arrival, int64_t* id_out) {
+  g_err.clear();
+  if (!s || !d || !bdata) return fail(IBDL_ERR_INVALID_ARG, "NULL server, desc or bdata");
+  if (d->dim != 2 && d->dim != 3) return fail(IBDL_ERR_INVALID_ARG, "dim must be 2 or 3");
+  if (d->n < 16 || (d->n & (d->n - 1)) != 0 || d->n > (d->dim == 2 ? 4096 : 512))
+    return fail(IBDL_ERR_INVALID_ARG,
+                "n must be a power of two in [16, 4096] (2D) / [16, 512] (3D)");
+  if (d->m < 1 || d->m > (1 << 26)) return fail(IBDL_ERR_INVALID_ARG, "m out of range");
+  if (!d->x || !d->y || !d->nx || !d->ny || !d->w || (d->dim == 3 && (!d->z || !d->nz)))
+    return fail(IBDL_ERR_INVALID_ARG, "NULL point, normal or weight array");
+  SrvReq* r = new SrvReq();
+  const size_t m = (size_t)d->m;
+  const double* src[7] = {d->x, d->y, d->dim == 3 ? d->z : nullptr, d->nx, d->ny,
+                          d->dim == 3 ? d->nz : nullptr, d->w};
+  for (int a = 0; a < 7; ++a) {
+    if (!src[a]) continue;
+    r->arr[a].resize(m);
+    if (cudaMemcpy(r->arr[a].data(), src[a], sizeof(double) * m, cudaMemcpyDefault)) {
+      cudaGetLastError();
+      delete r;
+      return fail(IBDL_ERR_INVALID_ARG, "server: unreadable point array");
+    }
+  }
+  r->bdata.resize(m);
+  if (cudaMemcpy(r->bdata.data(), bdata, sizeof(double) * m, cudaMemcpyDefault)) {
+    cudaGetLastError();
+    delete r;
+    return fail(IBDL_ERR_INVALID_ARG, "server: unreadable bdata");
+  }
+  for (double v : r->bdata)
+    if (!isfinite(v)) {
+      delete r;
+      return fail(IBDL_ERR_NONFINITE, "non-finite boundary data");
+    }
+  r->desc = *d;
+  double* dst[7];
+  for (int a = 0; a < 7; ++a) dst[a] = r->arr[a].empty() ? nullptr : r->arr[a].data();
+  r->desc.x = dst[0];
+  r->desc.y = dst[1];
+  r->desc.z = dst[2];
+  r->desc.nx = dst[3];
+  r->desc.ny = dst[4];
+  r->desc.nz = dst[5];
+  r->desc.w = dst[6];
+  r->est = estimate_request_bytes(*d);
+  r->t_arrival = t_arrival >= 0 ? t_arrival : server_now();
+  std::lock_guard<std::mutex> lk(s->mu);
+  r->id = s->next_id++;
+  s->queue.push_back(r);
+  if (id_out) *id_out = r->id;
+  return IBDL_OK;
+}
+
+ibdl_status ibdl_server_step(ibdl_server s, int64_t* done_ids, int32_t max_ids,
+                             int32_t* n_done) {
+  g_err.clear();
+  if (!s) return fail(IBDL_ERR_INVALID_ARG, "NULL server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->steps++;
+  s->just_done.clear();
+  // 1. one slice over the active slots, fresh slots uploaded first
+  int hi = -1, smem = 0;
+  for (int k = 0; k < s->cap; ++k)
+    if (s->slot[k]) {
+      hi = k;
+      if (s->slot[k]->g->solver_smem > smem) smem = s->slot[k]->g->solver_smem;
+    }
+  ibdl_status slice_err = IBDL_OK;
+  bool launched = false;
+  if (hi >= 0) {
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k <= hi && !e; ++k) {
+      if (!s->fresh[k]) continue;
+      e = cudaMemcpyAsync(s->d_inst + k, s->h_inst + k, sizeof(SolveInst),
+                          cudaMemcpyHostToDevice, s->solve_st);
+      if (!e)
+        e = cudaMemcpyAsync(s->d_state + k, s->h_state_in + k, sizeof(SolveState),
+                            cudaMemcpyHostToDevice, s->solve_st);
+      s->fresh[k] = 0;
+    }
+    if (!e)
+      e = launch_persistent_solve(s->d_inst, s->d_state, hi + 1, s->d_bar, smem, s->solve_st,
+                                  s->cfg.rounds_per_step, s->cfg.reserve_sms);
+    if (!e)
+      e = cudaMemcpyAsync(s->h_state_out, s->d_state, sizeof(SolveState) * (hi + 1),
+                          cudaMemcpyDeviceToHost, s->solve_st);
+    if (!e)
+      e = cudaMemcpyAsync(s->h_bar, s->d_bar, sizeof(unsigned) * 4, cudaMemcpyDeviceToHost,
+                          s->solve_st);
+    if (e) {
+      slice_err = cuda_fail(e, "server: slice launch");
+    } else {
+      launched = true;
+      s->launches++;
+    }
+  }
+  // 2. admit while the slice runs (set-up kernels use the reserved SMs)
+  admit_queued(s);
+  // 3. wait, then retire finished solves
+  if (launched) {
+    const cudaError_t e = cudaStreamSynchronize(s->solve_st);
+    if (e)
+      slice_err = cuda_fail(e, "server: slice");
+    else if (s->h_bar[2])
+      slice_err = fail(IBDL_ERR_TIMEOUT, "server: a solver barrier timed out");
+  }
+  for (int k = 0; k <= hi; ++k) {
+    SrvReq* r = s->slot[k];
+    if (!r || s->fresh[k]) continue;  // empty, or admitted during this slice
+    if (slice_err != IBDL_OK) {
+      retire(s, k, slice_err, nullptr);
+      continue;
+    }
+    const SolveState& st = s->h_state_out[k];
+    if (st.action != ACT_DONE) continue;
+    retire(s, k, (ibdl_status)st.status, &st);
+  }
+  const int32_t cnt = (int32_t)s->just_done.size();
+  for (int32_t i = 0; done_ids && i < cnt && i < max_ids; ++i) done_ids[i] = s->just_done[i];
+  if (n_done) *n_done = cnt;
+  return slice_err;
+}
+
+ibdl_status ibdl_server_take(ibdl_server s, int64_t id, double* q_out,
+                             ibdl_request_result* res) {
+  g_err.clear();
+  if (!s) return fail(IBDL_ERR_INVALID_ARG, "NULL server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->done.find(id);
+  if (it == s->done.end()) return fail(IBDL_ERR_INVALID_ARG, "unknown or unfinished request");
+  SrvReq* r = it->second;
+  if (q_out && !r->q.empty()) {
+    const cudaError_t e = cudaMemcpy(q_out, r->q.data(), sizeof(double) * r->q.size(),
+                                     cudaMemcpyDefault);
+    if (e) return cuda_fail(e, "server: copying the result");
+  }
+  if (res) {
+    memset(res, 0, sizeof(*res));
+    res->id = r->id;
+    res->status = r->status;
+    res->slot = r->slot;
+    res->t_arrival = r->t_arrival;
+    res->t_admit = r->t_admit;
+    res->t_done = r->t_done;
+    res->device_bytes = r->held;
+    res->info = r->info;
+  }
+  s->done.erase(it);
+  delete r;
+  return IBDL_OK;
+}
+
+ibdl_status ibdl_server_get_stats(ibdl_server s, ibdl_server_stats* out) {
+  if (!s || !out) return fail(IBDL_ERR_INVALID_ARG, "NULL server or out");
+  std::lock_guard<std::mutex> lk(s->mu);
+  memset(out, 0, sizeof(*out));
+  out->queued = (int32_t)s->queue.size();
+  for (SrvReq* r : s->slot)
+    if (r) out->active++;
+  out->finished = (int32_t)s->done.size();
+  out->bytes_in_use = s->bytes;
+  out->peak_bytes = s->peak;
+  out->memory_budget = s->cfg.memory_budget;
+  out->steps = s->steps;
+  out->launches = s->launches;
+  out->submitted = s->next_id - 1;
+  return IBDL_OK;
+}

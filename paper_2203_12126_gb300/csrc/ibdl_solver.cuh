@@ -61,7 +61,10 @@ struct SolveState {
 };
 
 int solver_smem_bytes(const GridDesc& g, int need32);
+// max_rounds > 0 stops the launch after that many rounds (states persist for
+// the next launch); reserve_sms SMs are left without solver blocks.
 cudaError_t launch_persistent_solve(const SolveInst* d_insts, SolveState* d_states, int ninst,
-                                    unsigned* d_bar, int smem, cudaStream_t st);
+                                    unsigned* d_bar, int smem, cudaStream_t st,
+                                    int max_rounds = 0, int reserve_sms = 0);
 
 }  // namespace ibdl

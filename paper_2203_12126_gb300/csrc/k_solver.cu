@@ -728,7 +728,7 @@ __device__ __forceinline__ void phase_tick(unsigned long long* ptimes, int id,
 
 __global__ void __launch_bounds__(kSolverThreads, 2)
     k_persistent_solve(const SolveInst* __restrict__ insts, SolveState* states, int ninst,
-                       unsigned* bar, unsigned long long* ptimes) {
+                       unsigned* bar, unsigned long long* ptimes, int max_rounds) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ RoundView rv[kMaxBatch];
   __shared__ BlockRed R;
@@ -739,6 +739,9 @@ __global__ void __launch_bounds__(kSolverThreads, 2)
   if (ptimes && bid == 0 && threadIdx.x == 0) t0 = global_ns();
 
   for (int round = 0;; ++round) {
+    // a bounded slice stops between rounds; the states stay in global memory
+    // and the next launch resumes them
+    if (max_rounds > 0 && round >= max_rounds) break;
     if (threadIdx.x == 0) {
       flags[0] = 0;
       flags[1] = 0;
@@ -845,7 +848,8 @@ int solver_smem_bytes(const GridDesc& g, int need32) {
 }
 
 cudaError_t launch_persistent_solve(const SolveInst* d_insts, SolveState* d_states, int ninst,
-                                    unsigned* d_bar, int smem, cudaStream_t st) {
+                                    unsigned* d_bar, int smem, cudaStream_t st, int max_rounds,
+                                    int reserve_sms) {
   unsigned long long* ptimes = prof_phase_buffer();
   static int sm_count = 0;
   static int configured_smem = -1;
@@ -867,11 +871,13 @@ cudaError_t launch_persistent_solve(const SolveInst* d_insts, SolveState* d_stat
     return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   if (per_sm > 2) per_sm = 2;
-  const int blocks = per_sm * sm_count;
+  int sms = sm_count - (reserve_sms > 0 ? reserve_sms : 0);
+  if (sms < 1) sms = 1;
+  const int blocks = per_sm * sms;
   if ((e = cudaMemsetAsync(d_bar, 0, (4 + 4 * (size_t)ninst) * sizeof(unsigned), st)))
     return e;
   void* args[] = {(void*)&d_insts, (void*)&d_states, (void*)&ninst, (void*)&d_bar,
-                  (void*)&ptimes};
+                  (void*)&ptimes, (void*)&max_rounds};
   prof_begin(st);
   e = cudaLaunchCooperativeKernel((const void*)k_persistent_solve, dim3(blocks),
                                   dim3(kSolverThreads), args, (size_t)smem, st);

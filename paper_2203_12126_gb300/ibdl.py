@@ -35,6 +35,9 @@ EXPORTS = [
     "ibdl_profile_read", "ibdl_status_string",
     "ibdl_last_error_message", "ibdl_version", "ibdl_helmholtz_2d_noalloc",
     "ibdl_batch_create", "ibdl_batch_destroy", "ibdl_solve_batched",
+    "ibdl_server_config_default", "ibdl_server_create", "ibdl_server_destroy",
+    "ibdl_server_clock", "ibdl_server_submit", "ibdl_server_step", "ibdl_server_take",
+    "ibdl_server_get_stats",
 ]
 
 
@@ -76,6 +79,31 @@ class GeometryInfo(C.Structure):
         ("kappa", C.c_double), ("bc", C.c_int32), ("delta", C.c_int32),
         ("precision", C.c_int32), ("device_bytes", C.c_int64),
         ("fft_passes", C.c_int32), ("reserved", C.c_int32),
+    ]
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [
+        ("memory_budget", C.c_int64), ("max_active", C.c_int32),
+        ("rounds_per_step", C.c_int32), ("reserve_sms", C.c_int32), ("reserved", C.c_int32),
+        ("opts", SolveOpts),
+    ]
+
+
+class RequestResult(C.Structure):
+    _fields_ = [
+        ("id", C.c_int64), ("status", C.c_int32), ("slot", C.c_int32),
+        ("t_arrival", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
+        ("device_bytes", C.c_int64), ("info", SolveInfo),
+    ]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [
+        ("queued", C.c_int32), ("active", C.c_int32), ("finished", C.c_int32),
+        ("reserved", C.c_int32), ("bytes_in_use", C.c_int64), ("peak_bytes", C.c_int64),
+        ("memory_budget", C.c_int64), ("steps", C.c_int64), ("launches", C.c_int64),
+        ("submitted", C.c_int64),
     ]
 
 
@@ -127,6 +155,15 @@ def load(path: str = LIB_PATH):
         "ibdl_solve_batched": (C.c_int, [vp, i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
                                          C.POINTER(SolveOpts), C.POINTER(SolveInfo),
                                          C.POINTER(C.c_int), vp]),
+        "ibdl_server_config_default": (None, [C.POINTER(ServerConfig)]),
+        "ibdl_server_create": (C.c_int, [C.POINTER(ServerConfig), C.POINTER(vp)]),
+        "ibdl_server_destroy": (None, [vp]),
+        "ibdl_server_clock": (C.c_double, []),
+        "ibdl_server_submit": (C.c_int, [vp, C.POINTER(GeometryDesc), vp, C.c_double,
+                                         C.POINTER(i64)]),
+        "ibdl_server_step": (C.c_int, [vp, C.POINTER(i64), i32, C.POINTER(i32)]),
+        "ibdl_server_take": (C.c_int, [vp, i64, vp, C.POINTER(RequestResult)]),
+        "ibdl_server_get_stats": (C.c_int, [vp, C.POINTER(ServerStats)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -199,6 +236,101 @@ def helmholtz_2d_noalloc(n, box_len, kappa, f, v_out, stream=None):
 
 def version() -> int:
     return int(load().ibdl_version())
+
+
+def make_desc(dim, n, box_len, origin, x, y, nx, ny, w, kappa, z=None, nz=None,
+              delta="peskin4", bc=DIRICHLET, precision=FP64):
+    """Fill an ``ibdl_geometry_desc`` (the arrays must outlive its use)."""
+    d = GeometryDesc()
+    d.dim, d.n, d.box_len = int(dim), int(n), float(box_len)
+    org = list(origin) + [0.0] * (3 - len(origin))
+    d.origin = (C.c_double * 3)(*org[:3])
+    d.m = int(len(x))
+    d.x, d.y, d.z = _ptr(x), _ptr(y), _ptr(z)
+    d.nx, d.ny, d.nz = _ptr(nx), _ptr(ny), _ptr(nz)
+    d.w = _ptr(w)
+    d.kappa = float(kappa)
+    d.delta = DELTA[delta] if isinstance(delta, str) else int(delta)
+    d.bc, d.precision = int(bc), int(precision)
+    return d
+
+
+def workload_arrays(geom):
+    """Contiguous float64 columns (x, y, z, nx, ny, nz, w) of a workload geometry."""
+    X = np.ascontiguousarray(geom.X, dtype=np.float64)
+    N = np.ascontiguousarray(geom.normals, dtype=np.float64)
+    cols = [np.ascontiguousarray(X[:, c]) for c in range(geom.dim)]
+    ncols = [np.ascontiguousarray(N[:, c]) for c in range(geom.dim)]
+    z = cols[2] if geom.dim == 3 else None
+    nz = ncols[2] if geom.dim == 3 else None
+    return (cols[0], cols[1], z, ncols[0], ncols[1], nz,
+            np.ascontiguousarray(geom.weights, dtype=np.float64))
+
+
+class Server:
+    """Continuous-batching solve server (``ibdl_server_*``)."""
+
+    def __init__(self, memory_budget=0, max_active=64, rounds_per_step=8, reserve_sms=8,
+                 tol=1e-8, restart=30, max_iters=500, max_refine=8, inner_tol=1e-5):
+        lib = load()
+        cfg = ServerConfig()
+        lib.ibdl_server_config_default(C.byref(cfg))
+        cfg.memory_budget, cfg.max_active = int(memory_budget), int(max_active)
+        cfg.rounds_per_step, cfg.reserve_sms = int(rounds_per_step), int(reserve_sms)
+        cfg.opts.tol, cfg.opts.restart = float(tol), int(restart)
+        cfg.opts.max_iters, cfg.opts.max_refine = int(max_iters), int(max_refine)
+        cfg.opts.inner_tol = float(inner_tol)
+        h = C.c_void_p()
+        _check(lib.ibdl_server_create(C.byref(cfg), C.byref(h)))
+        self._h = h
+
+    @staticmethod
+    def clock():
+        return float(load().ibdl_server_clock())
+
+    def submit(self, geom, bdata, bc=DIRICHLET, precision=FP32_REFINED, t_arrival=-1.0):
+        """Queue a workload geometry with its boundary data; returns the request id."""
+        x, y, z, nx, ny, nz, w = workload_arrays(geom)
+        d = make_desc(geom.dim, geom.n, geom.box_len, geom.origin, x, y, nx, ny, w,
+                      geom.kappa, z=z, nz=nz, delta=geom.delta, bc=bc, precision=precision)
+        b = np.ascontiguousarray(bdata, dtype=np.float64)
+        rid = C.c_int64()
+        _check(load().ibdl_server_submit(self._h, C.byref(d), _ptr(b), float(t_arrival),
+                                         C.byref(rid)))
+        return int(rid.value)
+
+    def step(self, max_ids=4096):
+        """One scheduling step; returns the ids finished in it."""
+        ids = (C.c_int64 * max_ids)()
+        nd = C.c_int32()
+        _check(load().ibdl_server_step(self._h, ids, int(max_ids), C.byref(nd)))
+        return [int(ids[i]) for i in range(min(nd.value, max_ids))]
+
+    def take(self, rid, m):
+        """(q, record) of a finished request."""
+        q = np.empty(int(m), dtype=np.float64)
+        r = RequestResult()
+        _check(load().ibdl_server_take(self._h, int(rid), _ptr(q), C.byref(r)))
+        rec = {"id": r.id, "status": r.status, "slot": r.slot, "t_arrival": r.t_arrival,
+               "t_admit": r.t_admit, "t_done": r.t_done, "device_bytes": r.device_bytes}
+        rec.update(r.info.as_dict())
+        return q, rec
+
+    def stats(self):
+        s = ServerStats()
+        _check(load().ibdl_server_get_stats(self._h, C.byref(s)))
+        return {f: getattr(s, f) for f, _ in ServerStats._fields_ if f != "reserved"}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().ibdl_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Geometry:

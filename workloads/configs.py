@@ -100,6 +100,53 @@ def c4_instances(count=256, seed=2, sizes=(128, 256, 512)):
     return out
 
 
+@dataclass
+class Request:
+    t: float                # arrival offset in seconds
+    problem: Problem
+    kind: str
+
+
+def c5_requests(count=300, seed=3, rate=2000.0, sizes2d=(256, 512, 1024),
+                sizes3d=(64, 128, 256), frac3d=0.2):
+    """The mixed serving stream: Poisson arrivals (mean ``rate`` per second);
+    80% 2D stars (N ~ U{sizes2d}, lobes 3-8, amplitude U[0,0.25], r0
+    U[0.15,0.35]) and 20% 3D spheres (r ~ U[0.2,0.35]) or ellipsoids (axes ~
+    U[0.2,0.35]), 50/50; log10 kappa ~ U[-4,-1]; Dirichlet/Neumann 50/50 with
+    the closed-form data u = exp(k d.(x - c)), d a random unit vector."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for i in range(count):
+        t += float(rng.exponential(1.0 / rate))
+        kappa = float(10.0 ** rng.uniform(-4.0, -1.0))
+        bc = DIRICHLET if rng.uniform() < 0.5 else NEUMANN
+        if rng.uniform() < frac3d:
+            n = int(rng.choice(sizes3d))
+            if rng.uniform() < 0.5:
+                r = float(rng.uniform(0.2, 0.35))
+                g = geometry.sphere(n, r, kappa=kappa, name=f"c5-{i}-sphere")
+                kind = f"3d-sphere-n{n}"
+            else:
+                axes = tuple(float(a) for a in rng.uniform(0.2, 0.35, size=3))
+                g = geometry.ellipsoid(n, axes, kappa=kappa, name=f"c5-{i}-ellipsoid")
+                kind = f"3d-ellipsoid-n{n}"
+        else:
+            n = int(rng.choice(sizes2d))
+            lobes = int(rng.integers(3, 9))
+            amp = float(rng.uniform(0.0, 0.25))
+            r0 = float(rng.uniform(0.15, 0.35))
+            g = geometry.star(n, r0, amp, lobes, spacing=1.0 / 1.5, kappa=kappa,
+                              name=f"c5-{i}-star")
+            kind = f"2d-star-n{n}"
+        d = data.random_direction(rng, g.dim)
+        p = exp_problem(g, bc, d)
+        p.tol = 1e-8
+        p.name = f"c5-{i}"
+        out.append(Request(t, p, kind + ("-dirichlet" if bc == DIRICHLET else "-neumann")))
+    return out
+
+
 def grid_nodes(geom):
     """(n^d, d) coordinates of all grid nodes in memory order (x fastest)."""
     h = geom.h

@@ -84,7 +84,9 @@ class StarCurve:
         # accurate and the arclength integrates term by term.
         t = 2.0 * np.pi * np.arange(n_modes) / n_modes
         c = np.fft.fft(self.speed(t)) / n_modes
-        keep = max(8, int(np.max(np.nonzero(np.abs(c[: n_modes // 2]) > 1e-18 * abs(c[0]))[0])) + 1)
+        # modes below 1e-15 |c_0| are FFT rounding noise: the real harmonics
+        # of the speed decay geometrically well before that
+        keep = max(8, int(np.max(np.nonzero(np.abs(c[: n_modes // 2]) > 1e-15 * abs(c[0]))[0])) + 1)
         self._c0 = c[0].real
         self._cm = c[1:keep]
         self._mm = np.arange(1, keep)
@@ -118,7 +120,9 @@ class StarCurve:
         for _ in range(60):
             dt = (self.arclength(t) - target) / self.speed(t)
             t = t - dt
-            if np.max(np.abs(dt)) < 1e-15:
+            # Newton converges quadratically; below 1e-13 the next step only
+            # moves t by rounding noise
+            if np.max(np.abs(dt)) < 1e-13:
                 break
         r, dr = self.radius(t), self.dradius(t)
         c, s = np.cos(t), np.sin(t)
