@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--engine", type=int, default=0, choices=[0, 1],
                     help="0: persistent single-launch solver, 1: host-driven loop")
+    ap.add_argument("--no-matvec", action="store_true",
+                    help="skip the matvec HBM-roofline measurement")
     ap.add_argument("--serve-requests", type=int, default=200,
                     help="requests of the mixed serving stream (0: skip it)")
     return ap.parse_args()
@@ -221,6 +223,50 @@ def matvec_bytes(n, m, prec):
     sfx = "_f64" if prec == 64 else "_f32"
     return sum(kernel_model(k + sfx, n, m)["bytes"]
                for k in ("rows_fwd", "solve", "rows_inv", "interp"))
+
+
+def survey_matvec_bytes(dim, n, m, p):
+    """Algorithmic bytes of one matvec, the fixed model
+    B = 9 p N^d + p M (4^d + 2d + 4): one grid write by the spread, two
+    read+write passes per transform, the taps and point I/O."""
+    return 9 * p * n ** dim + p * m * (4 ** dim + 2 * dim + 4)
+
+
+def run_matvec_roofline(pkg, peaks, reps=30):
+    """Event-timed matvecs (float32 and float64) on the 3D 256^3 sphere (the
+    HBM-bound case) and the 2D 1024^2 star, L2 flushed between launches."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    out = {}
+    for name, prob in (("c3-sphere-n256-m38039", configs.c3()),
+                       ("c2-star-n1024-m3525", configs.c2())):
+        g = pkg.Geometry.from_workload(prob.geom, bc=prob.bc, precision=1)
+        q = torch.tensor(np.random.default_rng(0).standard_normal(prob.geom.m),
+                         dtype=torch.float64, device=dev)
+        y = torch.empty_like(q)
+        for prec, tag, p in ((1, "f32", 4), (0, "f64", 8)):
+            for _ in range(3):
+                g.apply(q, y, precision=prec)
+            ev = []
+            for _ in range(reps):
+                flush.fill_(2.0)
+                a = torch.cuda.Event(enable_timing=True)
+                c = torch.cuda.Event(enable_timing=True)
+                a.record()
+                g.apply(q, y, precision=prec)
+                c.record()
+                ev.append((a, c))
+            torch.cuda.synchronize()
+            us = float(np.median([a.elapsed_time(c) for a, c in ev])) * 1e3
+            B = survey_matvec_bytes(prob.geom.dim, prob.geom.n, prob.geom.m, p)
+            gbs = B / (us * 1e-6) / 1e9
+            out[f"{name}-{tag}"] = {"us_median": us, "algorithmic_bytes": B,
+                                    "achieved_gbs": gbs, "peak_gbs": peaks["hbm_gbs"],
+                                    "frac_of_hbm": gbs / peaks["hbm_gbs"],
+                                    "peak_src": peaks["src"]}
+        g.close()
+    return out
 
 
 def load_peaks():
@@ -470,6 +516,8 @@ def main():
            "note": "ibdl_solve with pinned host U_b/V_b in and host Q/U out; copies "
                    "inside the call; host wall clock"}
 
+    matvec = run_matvec_roofline(pkg, peaks) if not args.no_matvec else None
+
     serving = None
     if args.serve_requests > 0:
         serving = run_serving(pkg, args.serve_requests)
@@ -511,6 +559,7 @@ def main():
             "phases": phases,
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "matvec": matvec,
             "serving": serving,
             "gpu_launches": int(launches),
             "wall_s_timed": wall,

@@ -323,6 +323,32 @@ __device__ __forceinline__ void copy_to_shared(V* dst, const V* __restrict__ src
   }
 }
 
+// Two consecutive complex values as one 16-byte access (float) or two
+// (double).  Even element indices keep the float pair 16-byte aligned.
+template <typename T> struct Pair;
+template <> struct Pair<float> {
+  float2 a, b;
+  __device__ __forceinline__ void load(const float2* p) {
+    const float4 v = __ldcg(reinterpret_cast<const float4*>(p));
+    a = make_float2(v.x, v.y);
+    b = make_float2(v.z, v.w);
+  }
+  __device__ __forceinline__ void store(float2* p) const {
+    *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+  }
+};
+template <> struct Pair<double> {
+  double2 a, b;
+  __device__ __forceinline__ void load(const double2* p) {
+    a = __ldcg(p);
+    b = __ldcg(p + 1);
+  }
+  __device__ __forceinline__ void store(double2* p) const {
+    p[0] = a;
+    p[1] = b;
+  }
+};
+
 template <typename T> __device__ __forceinline__ T wload(const PointData& p, int c, int t, int i);
 template <> __device__ __forceinline__ double wload<double>(const PointData& p, int c, int t,
                                                             int i) {
@@ -511,9 +537,10 @@ __device__ __forceinline__ void phase_rows_fwd(const GridDesc& g, const PointDat
     A.y = (T)0.5 * (zk.y - zm.y);
     B.x = (T)0.5 * (zk.y + zm.y);
     B.y = (T)-0.5 * (zk.x - zm.x);
-    C* out = spec + (size_t)k * slab + pos0 + 2 * a;
-    out[0] = A;
-    out[1] = B;
+    Pair<T> pr;
+    pr.a = A;
+    pr.b = B;
+    pr.store(spec + (size_t)k * slab + pos0 + 2 * a);
   }
   __syncthreads();  // the block's shared buffers are reused by the next item
 }
@@ -551,6 +578,7 @@ __host__ __device__ inline PencilLayout pencil_layout(int n, int64_t gstride, in
   if (estride != 1 && c > pg) c = pg;
   while (c > 1 && pencil_smem_for<T>(n, c) > 90 * 1024) c >>= 1;
   while (c > 1 && npencils / c < 256 && estride == 1) c >>= 1;
+  if (estride != 1 && c < 2) c = 2;  // strided items move pencils in pairs
   L.c = c;
   L.lgc = 0;
   while ((1 << L.lgc) < c) ++L.lgc;
@@ -579,10 +607,16 @@ __host__ __device__ inline size_t pencil_smem_bytes(const PencilLayout& L, int n
 
 // MODE 0: forward, 1: inverse, 2: forward, multiply by
 // scale0 / (1 + cfac * sum_c sin^2(pi k_c / n)), inverse.
+//
+// An item's pencils are either contiguous (pencil p at data + p n: the 2D
+// kx slabs and the 3D y pencils) or strided (3D z pencils: the item's c
+// pencils are c consecutive y of one kx slab, element t at t n + pl), so one
+// base pointer per item addresses everything; elements move in pairs.
 template <typename T, int MODE>
-__device__ __forceinline__ void phase_pencils(const GridDesc& g, const PencilLayout& L, cx_t<T>* data,
-                              const cx_t<T>* __restrict__ tw, const T* __restrict__ s2,
-                              T cfac, T scale0, int blk, unsigned char* smem) {
+__device__ __forceinline__ void phase_pencils(const GridDesc& g, const PencilLayout& L,
+                                              cx_t<T>* data, const cx_t<T>* __restrict__ tw,
+                                              const T* __restrict__ s2, T cfac, T scale0,
+                                              int blk, unsigned char* smem) {
   using C = cx_t<T>;
   const int n = g.n, lg = g.log2n, c = L.c, lgc = L.lgc, PS = pen_stride(n);
   const int ntw = fft_tw_count(n);
@@ -592,41 +626,47 @@ __device__ __forceinline__ void phase_pencils(const GridDesc& g, const PencilLay
   T* s2s = reinterpret_cast<T*>(tws + ntw);
   const int tid = threadIdx.x, nt = blockDim.x;
   const int p0 = blk * c;
+  const int npl = min(c, L.npencils - p0);
   const bool tfast = (L.estride == 1);
-  const int total = c << lg;
+  const int gi0 = p0 >> L.lgpg, q0 = p0 & (L.pg - 1);
+  C* base = tfast ? data + (size_t)p0 * n : data + (size_t)gi0 * L.gstride + q0;
+  const int npairs = (npl << lg) >> 1;
 
-  // element e of the item: (pencil pl, position t); t fastest when the
-  // pencils are contiguous, pl fastest when they are strided
-  constexpr int U = sizeof(T) == 4 ? 8 : 4;
-  for (int e0 = tid; e0 < total; e0 += U * nt) {
-    C v[U];
-    int at[U];
+  // pair k: contiguous -> elements 2k, 2k+1 of the item (one pencil, t even);
+  // strided -> pencils pl, pl+1 (pl even) at position t.  npl is even or 1
+  // in the strided case (c | pg, pg a power of two), so pairs never straddle.
+  constexpr int U = sizeof(T) == 4 ? 4 : 2;
+  for (int k0 = tid; k0 < npairs; k0 += U * nt) {
+    Pair<T> v[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int e = e0 + u * nt;
-      at[u] = -1;
-      v[u].x = 0;
-      v[u].y = 0;
-      if (e < total) {
-        int pl, t;
+      const int k = k0 + u * nt;
+      if (k < npairs) {
         if (tfast) {
-          pl = e >> lg;
-          t = e & (n - 1);
+          v[u].load(base + 2 * k);
         } else {
-          t = e >> lgc;
-          pl = e & (c - 1);
+          const int e = 2 * k, t = e >> lgc, pl = e & (c - 1);
+          v[u].load(base + (size_t)t * n + pl);
         }
-        const int p = p0 + pl;
-        if (p < L.npencils) {
-          const int gi = p >> L.lgpg, q = p & (L.pg - 1);
-          v[u] = __ldcg(data + gi * L.gstride + q * L.bstride + t * L.estride);
-        }
-        at[u] = pl * PS + padi(t);
       }
     }
 #pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (at[u] >= 0) bufA[at[u]] = v[u];
+    for (int u = 0; u < U; ++u) {
+      const int k = k0 + u * nt;
+      if (k < npairs) {
+        const int e = 2 * k;
+        if (tfast) {
+          const int pl = e >> lg, t = e & (n - 1);
+          C* d = bufA + pl * PS + padi(t);  // padi(t + 1) = padi(t) + 1, t even
+          d[0] = v[u].a;
+          d[1] = v[u].b;
+        } else {
+          const int t = e >> lgc, pl = e & (c - 1);
+          bufA[pl * PS + padi(t)] = v[u].a;
+          bufA[(pl + 1) * PS + padi(t)] = v[u].b;
+        }
+      }
+    }
   }
   copy_to_shared(tws, tw, ntw);
   if (MODE == 2) copy_to_shared(s2s, s2, n);
@@ -634,13 +674,11 @@ __device__ __forceinline__ void phase_pencils(const GridDesc& g, const PencilLay
 
   C* res = fft_run<T, MODE == 1>(bufA, bufB, lg, c, tws);
   if (MODE == 2) {
-    for (int e = tid; e < total; e += nt) {
+    // 2D: pencil kx = p0 + pl, position ky = t; 3D: kx = gi0, ky = q0 + pl, kz = t
+    const T sfix = g.dim == 3 ? s2s[gi0] : (T)0;
+    for (int e = tid; e < (npl << lg); e += nt) {
       const int pl = e >> lg, t = e & (n - 1);
-      const int p = p0 + pl;
-      if (p >= L.npencils) continue;
-      const int gi = p >> L.lgpg, q = p & (L.pg - 1);
-      T ssum = s2s[gi] + s2s[t];
-      if (g.dim == 3) ssum += s2s[q];
+      const T ssum = g.dim == 3 ? sfix + s2s[q0 + pl] + s2s[t] : s2s[p0 + pl] + s2s[t];
       const T f = scale0 / ((T)1 + cfac * ssum);
       C& v = res[pl * PS + padi(t)];
       v.x *= f;
@@ -651,19 +689,20 @@ __device__ __forceinline__ void phase_pencils(const GridDesc& g, const PencilLay
     res = fft_run<T, true>(res, other, lg, c, tws);
   }
 
-  for (int e = tid; e < total; e += nt) {
-    int pl, t;
+  for (int k = tid; k < npairs; k += nt) {
+    const int e = 2 * k;
+    Pair<T> v;
     if (tfast) {
-      pl = e >> lg;
-      t = e & (n - 1);
+      const int pl = e >> lg, t = e & (n - 1);
+      const C* sp = res + pl * PS + padi(t);
+      v.a = sp[0];
+      v.b = sp[1];
+      v.store(base + 2 * k);
     } else {
-      t = e >> lgc;
-      pl = e & (c - 1);
-    }
-    const int p = p0 + pl;
-    if (p < L.npencils) {
-      const int gi = p >> L.lgpg, q = p & (L.pg - 1);
-      data[gi * L.gstride + q * L.bstride + t * L.estride] = res[pl * PS + padi(t)];
+      const int t = e >> lgc, pl = e & (c - 1);
+      v.a = res[pl * PS + padi(t)];
+      v.b = res[(pl + 1) * PS + padi(t)];
+      v.store(base + (size_t)t * n + pl);
     }
   }
   __syncthreads();
@@ -699,9 +738,10 @@ __device__ __forceinline__ void phase_rows_inv(const GridDesc& g, const Bins& b,
       const int e = e0 + u * nt;
       if (e < total) {
         const int k = e / npen, a = e - k * npen;
-        const C* in = spec + (size_t)k * slab + pos0 + 2 * a;
-        A[u] = __ldcg(in);
-        B[u] = __ldcg(in + 1);
+        Pair<T> pr;
+        pr.load(spec + (size_t)k * slab + pos0 + 2 * a);
+        A[u] = pr.a;
+        B[u] = pr.b;
       }
     }
 #pragma unroll
