@@ -1,0 +1,60 @@
+"""Small fixed workloads for profilers (ncu) and quick timing.
+
+    python -m paper_2203_12126_gb300.probe matvec c3 f32 [reps]
+    python -m paper_2203_12126_gb300.probe solve c2 [reps]
+
+``matvec`` applies the boundary operator of the 3D sphere (c3: N=256^3,
+M=38039) or the 2D star (c2: N=1024^2, M=3525) ``reps`` times (default 5)
+in float32 (f32) or float64 (f64); ``solve`` runs ``reps`` (default 2)
+float32-refined Dirichlet solves of c2 at tolerance 1e-8 through the
+persistent solver.  Everything runs in the CUDA library; the script only
+builds the inputs.
+"""
+from __future__ import annotations
+
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main(argv):
+    import numpy as np
+    import torch
+
+    import paper_2203_12126_gb300 as pkg
+    from workloads import configs
+
+    pkg.load()
+    what, case = argv[0], argv[1]
+    prob = configs.c3() if case == "c3" else configs.c2()
+    dev = torch.device("cuda:0")
+    if what == "matvec":
+        prec = 1 if (len(argv) < 3 or argv[2] == "f32") else 0
+        reps = int(argv[3]) if len(argv) > 3 else 5
+        g = pkg.Geometry.from_workload(prob.geom, bc=prob.bc, precision=prec)
+        q = torch.tensor(np.random.default_rng(0).standard_normal(prob.geom.m), device=dev)
+        y = torch.empty_like(q)
+        for _ in range(reps):
+            g.apply(q, y, precision=prec)
+        torch.cuda.synchronize()
+        print(f"matvec {case} {'f32' if prec else 'f64'} x{reps}: |y| = {float(y.norm()):.6e}")
+    elif what == "solve":
+        reps = int(argv[2]) if len(argv) > 2 else 2
+        g = pkg.Geometry.from_workload(prob.geom, bc=prob.bc, precision=pkg.FP32_REFINED)
+        b = torch.tensor(prob.bdata, device=dev)
+        q = torch.empty_like(b)
+        for _ in range(reps):
+            info = g.solve(b, q, tol=1e-8)
+        torch.cuda.synchronize()
+        print(f"solve {case} x{reps}: iters {info['iters']} rel_res {info['rel_residual']:.2e}")
+    else:
+        raise SystemExit(__doc__)
+    g.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main(sys.argv[1:]))
