@@ -5,7 +5,8 @@ Workload: the 2D star problem, periodic box [0,1)^2 with N=1024^2 nodes, star
 r(theta) = 0.3 (1 + 0.2 cos 5 theta), M = 3525 arclength-equispaced points,
 Peskin 4-point delta, kappa = 1e-3, seeded 10-mode Fourier boundary data.
 One step = one Dirichlet solve (seed 0) + one Neumann solve (seed 1) to a
-relative residual of 1e-8 (the whole hot path: spread-divergence, FFT
+relative residual of 1e-8, solved together in one batched persistent launch
+(``--mode solo``: one launch each) (the whole hot path: spread-divergence, FFT
 Helmholtz solve, interpolation + jump, GMRES Arnoldi/Givens, the Neumann
 right-hand side).
 
@@ -48,6 +49,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="CPU work budget of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="batched", choices=["batched", "solo"],
+                    help="batched: each step solves the Dirichlet + Neumann pair in one "
+                         "persistent launch; solo: one launch per solve")
     ap.add_argument("--engine", type=int, default=0, choices=[0, 1],
                     help="0: persistent single-launch solver, 1: host-driven loop")
     ap.add_argument("--no-matvec", action="store_true",
@@ -381,14 +385,24 @@ def main():
         return geoms[i].solve(bs[i] if b is None else b, qs[i] if q is None else q,
                               tol=args.tol, engine=args.engine)
 
+    batch = ibdl.Batch(len(probs))
+
+    def step_batched(gs=None, qq=None):
+        # the Dirichlet + Neumann pair advances together in one persistent launch
+        return batch.solve(gs or geoms, bs, qq or qs, tol=args.tol)
+
+    def step_solo():
+        return [solve(i) for i in range(len(probs))]
+
+    run_step = step_batched if args.mode == "batched" else step_solo
+
     for _ in range(args.warmup):
-        for i in range(len(probs)):
-            solve(i)
+        run_step()
     torch.cuda.synchronize()
 
-    # ---- timed region: K steps, per-solve CUDA events, L2 flushed between
+    # ---- timed region: K steps, per-step CUDA events, L2 flushed between
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps * len(probs))]
+          for _ in range(args.steps)]
     infos = []
     sampler = ClockSampler(local)
     sampler.start()
@@ -398,14 +412,11 @@ def main():
     torch.cuda.synchronize()
     l0 = pkg.kernel_launch_count()
     w0 = time.perf_counter()
-    k = 0
-    for _ in range(args.steps):
-        for i in range(len(probs)):
-            flush.fill_(float(k))
-            ev[k][0].record(stream)
-            infos.append(solve(i))
-            ev[k][1].record(stream)
-            k += 1
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        infos.extend(run_step())
+        ev[k][1].record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - w0
     launches = pkg.kernel_launch_count() - l0
@@ -416,6 +427,36 @@ def main():
     total_ms, solves = combine_ranks(float(sum(lat)), args.steps * len(probs), dist, dev)
     value = solves / (total_ms / 1e3)
 
+    # ---- the same pair solved one at a time (single-solve latency) and the
+    # plain float64 path at the same tolerance (batched), for comparison
+    def timed(fn, reps):
+        evs = []
+        for _ in range(reps):
+            flush.fill_(3.0)
+            a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            c.record(stream)
+            evs.append((a, c))
+        torch.cuda.synchronize()
+        return [a.elapsed_time(c) for a, c in evs]
+
+    solo_lat = []
+    for _ in range(max(5, args.steps // 2)):
+        for i in range(len(probs)):
+            solo_lat.extend(timed(lambda: solve(i), 1))
+    solo = {"solves_per_s": len(solo_lat) / (sum(solo_lat) / 1e3),
+            "latency_ms": {"p50": float(np.percentile(solo_lat, 50)),
+                           "p99": float(np.percentile(solo_lat, 99))},
+            "note": "each solve alone through ibdl_solve (one persistent launch)"}
+    g64s = [pkg.Geometry.from_workload(p.geom, bc=p.bc, precision=ibdl.FP64) for p in probs]
+    q64s = [torch.zeros_like(q) for q in qs]
+    step_batched(g64s, q64s)
+    f64_lat = timed(lambda: step_batched(g64s, q64s), max(5, args.steps // 2))
+    fp64 = {"solves_per_s": len(probs) * len(f64_lat) / (sum(f64_lat) / 1e3),
+            "latency_ms_per_pair": {"p50": float(np.percentile(f64_lat, 50))},
+            "note": "plain float64 GMRES, same pair, same tolerance, batched launch"}
+
     # ---- accuracy of the timed path against a float64 GPU solve at 1e-12
     errs = []
     for i, p in enumerate(probs):
@@ -423,7 +464,12 @@ def main():
         q64 = torch.zeros_like(qs[i])
         g64.solve(bs[i], q64, tol=1e-12)
         errs.append(float(torch.linalg.norm(qs[i] - q64) / torch.linalg.norm(q64)))
+        fp64.setdefault("rel_err_vs_fp64_1e-12", 0.0)
+        fp64["rel_err_vs_fp64_1e-12"] = max(fp64["rel_err_vs_fp64_1e-12"], float(
+            torch.linalg.norm(q64s[i] - q64) / torch.linalg.norm(q64)))
         g64.close()
+    for g in g64s:
+        g.close()
 
     # ---- profiled pass: per-kernel CUDA-event durations (library event pairs
     # on the launching stream) and, inside the persistent solver, per-phase
@@ -432,9 +478,9 @@ def main():
     pkg.ibdl.profile_read(reset=True)
     pinfos = []
     for _ in range(max(3, args.steps // 4)):
-        for i in range(len(probs)):
-            flush.fill_(1.0)
-            pinfos.append(solve(i))
+        flush.fill_(1.0)
+        pinfos.extend(run_step())
+    per_launch = len(probs) if args.mode == "batched" else 1
     stats = pkg.ibdl.profile_read(reset=True)
     pkg.ibdl.profile_enable(False)
     peaks = load_peaks()
@@ -465,10 +511,10 @@ def main():
         name, (cnt, ms) = dom
         avg_s = ms / cnt / 1e3
         if name == "persistent_solve":
-            # one launch = one whole solve: its binding resource is the FP64
-            # pipe of the float64 FFT passes (residuals / all matvecs)
-            mv = float(np.mean([f["matvecs"] for f in pinfos]))
-            it = float(np.mean([f["iters"] for f in pinfos]))
+            # one launch = whole solves (per_launch of them): its binding
+            # resource is the FP64 pipe of the float64 FFT passes
+            mv = float(np.mean([f["matvecs"] for f in pinfos])) * per_launch
+            it = float(np.mean([f["iters"] for f in pinfos])) * per_launch
             mv64 = (mv - it) if prec == ibdl.FP32_REFINED else mv
             mv32 = it if prec == ibdl.FP32_REFINED else 0.0
             fl = mv64 * matvec_flops(n, m, 64)
@@ -507,14 +553,18 @@ def main():
     e2e_steps = max(3, args.steps // 2)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        for i in range(len(probs)):
-            solve(i, hb[i], hq[i])
+        if args.mode == "batched":
+            batch.solve(geoms, hb, hq, tol=args.tol)
+        else:
+            for i in range(len(probs)):
+                solve(i, hb[i], hq[i])
     e2e_s = time.perf_counter() - t0
     e2e = {"value": e2e_steps * len(probs) * world / e2e_s, "unit": "solves/s",
            "h2d_bytes_per_step": int(sum(8 * p.geom.m for p in probs)),
            "d2h_bytes_per_step": int(sum(8 * p.geom.m for p in probs)),
-           "note": "ibdl_solve with pinned host U_b/V_b in and host Q/U out; copies "
-                   "inside the call; host wall clock"}
+           "note": ("ibdl_solve_batched" if args.mode == "batched" else "ibdl_solve") +
+                   " with pinned host U_b/V_b in and host Q/U out; copies inside the "
+                   "call; host wall clock"}
 
     matvec = run_matvec_roofline(pkg, peaks) if not args.no_matvec else None
 
@@ -547,10 +597,15 @@ def main():
                        "tol": args.tol, "precision": args.precision,
                        "l2": "flushed between solves (512 MiB write, outside the events)",
                        "engine": "persistent" if args.engine == 0 else "host-loop",
+                       "mode": args.mode,
                        "parallelism": f"replicas x{world}"},
             "latency_ms": {"p50": float(np.percentile(lat, 50)),
                            "p99": float(np.percentile(lat, 99)),
-                           "mean": float(np.mean(lat))},
+                           "mean": float(np.mean(lat)),
+                           "per": "step (the Dirichlet + Neumann pair)" if args.mode == "batched"
+                                  else "step (two solves in sequence)"},
+            "solo": solo,
+            "fp64": fp64,
             "iters_per_solve": {"min": min(iters), "max": max(iters)},
             "matvecs_per_s": float(sum(mv)) * world / (total_ms / 1e3),
             "rel_err_vs_fp64_1e-12": max(errs),

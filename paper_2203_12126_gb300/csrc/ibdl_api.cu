@@ -260,12 +260,16 @@ SpectralWs<float>& wsof<float>(ibdl_geometry_s* g) {
 }
 
 // grid = kappa L'^{-1} (sources), T-precision spectral passes, output OutT grid.
+// band_only: the grid feeds only the interpolation (matvec, right-hand
+// side), so tiles and planes without points are not produced.
 template <typename T, typename OutT>
-ibdl_status field_solve(ibdl_geometry_s* g, const SpreadSrc& src, OutT* out, cudaStream_t st) {
+ibdl_status field_solve(ibdl_geometry_s* g, const SpreadSrc& src, OutT* out, cudaStream_t st,
+                        bool band_only = false) {
   SpectralWs<T>& ws = wsof<T>(g);
   IBDL_CU(launch_rows_fwd<T>(g->grid, g->pd, g->bins, src, ws, nullptr, st));
-  IBDL_CU(launch_spectral_solve<T>(g->grid, ws, st));
-  IBDL_CU((launch_rows_inv<T, OutT>(g->grid, g->bins, ws, out, st)));
+  IBDL_CU(launch_spectral_solve<T>(g->grid, ws, st, band_only ? &g->bins : nullptr,
+                                   band_only && !src.f_grid));
+  IBDL_CU((launch_rows_inv<T, OutT>(g->grid, g->bins, ws, out, st, band_only)));
   return IBDL_OK;
 }
 
@@ -276,7 +280,7 @@ ibdl_status matvec(ibdl_geometry_s* g, const double* q, double* y, cudaStream_t 
   src.q_div = q;
   src.coef_div = 1.0;
   SpectralWs<T>& ws = wsof<T>(g);
-  IBDL_TRY((field_solve<T, T>(g, src, ws.grid, st)));
+  IBDL_TRY((field_solve<T, T>(g, src, ws.grid, st, true)));
   const double jump = g->bc == IBDL_DIRICHLET ? 0.5 : -0.5;
   IBDL_CU(launch_interp<T>(g->grid, g->pd, ws.grid, q, jump, y, st));
   return IBDL_OK;
@@ -302,7 +306,7 @@ ibdl_status build_rhs(ibdl_geometry_s* g, const double* bdata, const double* ggr
     SpreadSrc src;
     src.f_grid = ggrid;
     src.coef_grid = 1.0;
-    IBDL_TRY((field_solve<double, double>(g, src, g->ws64.grid, st)));
+    IBDL_TRY((field_solve<double, double>(g, src, g->ws64.grid, st, true)));
     IBDL_CU(launch_interp<double>(g->grid, g->pd, g->ws64.grid, bdata, 1.0, b, st));
     return IBDL_OK;
   }
@@ -313,7 +317,7 @@ ibdl_status build_rhs(ibdl_geometry_s* g, const double* bdata, const double* ggr
     src.f_grid = ggrid;
     src.coef_grid = 1.0;
   }
-  IBDL_TRY((field_solve<double, double>(g, src, g->ws64.grid, st)));
+  IBDL_TRY((field_solve<double, double>(g, src, g->ws64.grid, st, true)));
   IBDL_CU(launch_interp<double>(g->grid, g->pd, g->ws64.grid, nullptr, 0.0, b, st));
   return IBDL_OK;
 }

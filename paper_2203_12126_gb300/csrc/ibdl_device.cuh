@@ -616,7 +616,8 @@ template <typename T, int MODE>
 __device__ __forceinline__ void phase_pencils(const GridDesc& g, const PencilLayout& L,
                                               cx_t<T>* data, const cx_t<T>* __restrict__ tw,
                                               const T* __restrict__ s2, T cfac, T scale0,
-                                              int blk, unsigned char* smem) {
+                                              int blk, unsigned char* smem,
+                                              const int* zskip = nullptr, int ngroups = 0) {
   using C = cx_t<T>;
   const int n = g.n, lg = g.log2n, c = L.c, lgc = L.lgc, PS = pen_stride(n);
   const int ntw = fft_tw_count(n);
@@ -631,6 +632,11 @@ __device__ __forceinline__ void phase_pencils(const GridDesc& g, const PencilLay
   const int gi0 = p0 >> L.lgpg, q0 = p0 & (L.pg - 1);
   C* base = tfast ? data + (size_t)p0 * n : data + (size_t)gi0 * L.gstride + q0;
   const int npairs = (npl << lg) >> 1;
+  // 3D y passes (pencils (kx, z), items of consecutive z): zskip = the tile
+  // starts of the bins; an item whose planes hold no point is skipped -- a
+  // forward pass would map zeros to zeros, and an inverse pass feeds only
+  // the interpolation, which reads planes that hold points
+  if (zskip && zskip[(q0 + npl) * ngroups] == zskip[q0 * ngroups]) return;
 
   // pair k: contiguous -> elements 2k, 2k+1 of the item (one pencil, t even);
   // strided -> pencils pl, pl+1 (pl even) at position t.  npl is even or 1
@@ -714,7 +720,10 @@ __device__ __forceinline__ void phase_pencils(const GridDesc& g, const PencilLay
 template <typename T, int D, typename OutT>
 __device__ __forceinline__ void phase_rows_inv(const GridDesc& g, const Bins& b, const cx_t<T>* spec,
                                const cx_t<T>* __restrict__ tw, OutT* out, int tile,
-                               unsigned char* smem) {
+                               unsigned char* smem, bool band_only = false) {
+  // band_only: the grid feeds only the interpolation, whose stencil rows lie
+  // in tiles that hold the point in their bin; other tiles are not produced
+  if (band_only && b.start[tile] == b.start[tile + 1]) return;
   using C = cx_t<T>;
   const int n = g.n, lg = g.log2n, R = b.rows, npen = R >> 1;
   const int PS = pen_stride(n);

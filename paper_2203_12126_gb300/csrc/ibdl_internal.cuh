@@ -112,12 +112,18 @@ cudaError_t launch_rows_fwd(const GridDesc& g, const PointData& p, const Bins& b
                             const SpreadSrc& src, SpectralWs<T>& ws, double* write_grid,
                             cudaStream_t st);
 // y/z passes on the spectrum; solve multiplies by kappa / (sigma(k) n^d).
+// skip (3D, may be null): the bins, to skip y-pass items of planes without
+// points -- in the inverse pass always, in the forward pass when skip_fwd
+// (the forward input of such planes is zero: no grid source).
 template <typename T>
-cudaError_t launch_spectral_solve(const GridDesc& g, SpectralWs<T>& ws, cudaStream_t st);
+cudaError_t launch_spectral_solve(const GridDesc& g, SpectralWs<T>& ws, cudaStream_t st,
+                                  const Bins* skip = nullptr, bool skip_fwd = false);
 // Inverse x pass: transposed half spectrum -> real grid (T or double).
+// band_only: produce only the tiles that hold points (the grid then feeds
+// the interpolation alone).
 template <typename T, typename OutT>
 cudaError_t launch_rows_inv(const GridDesc& g, const Bins& b, SpectralWs<T>& ws,
-                            OutT* out, cudaStream_t st);
+                            OutT* out, cudaStream_t st, bool band_only = false);
 template <typename T>
 int fft_kernels_per_solve(int dim);
 cudaError_t configure_fft_kernels(int n, int rows);

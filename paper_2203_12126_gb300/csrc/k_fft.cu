@@ -33,17 +33,19 @@ __global__ void __launch_bounds__(512) k_rows_fwd(GridDesc g, PointData p, Bins 
 template <typename T, int MODE>
 __global__ void __launch_bounds__(512) k_pencils(GridDesc g, PencilLayout L, cx_t<T>* data,
                                                  const cx_t<T>* __restrict__ tw,
-                                                 const T* __restrict__ s2, T cfac, T scale0) {
+                                                 const T* __restrict__ s2, T cfac, T scale0,
+                                                 const int* zskip, int ngroups) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  phase_pencils<T, MODE>(g, L, data, tw, s2, cfac, scale0, blockIdx.x, smem_raw);
+  phase_pencils<T, MODE>(g, L, data, tw, s2, cfac, scale0, blockIdx.x, smem_raw, zskip,
+                         ngroups);
 }
 
 template <typename T, int D, typename OutT>
 __global__ void __launch_bounds__(512) k_rows_inv(GridDesc g, Bins b, const cx_t<T>* spec,
                                                    const cx_t<T>* __restrict__ tw,
-                                                   OutT* out) {
+                                                   OutT* out, bool band_only) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  phase_rows_inv<T, D, OutT>(g, b, spec, tw, out, blockIdx.x, smem_raw);
+  phase_rows_inv<T, D, OutT>(g, b, spec, tw, out, blockIdx.x, smem_raw, band_only);
 }
 
 // ---- launchers ----------------------------------------------------------------
@@ -73,22 +75,22 @@ cudaError_t launch_rows_fwd(const GridDesc& g, const PointData& p, const Bins& b
 
 template <typename T, typename OutT>
 cudaError_t launch_rows_inv(const GridDesc& g, const Bins& b, SpectralWs<T>& ws, OutT* out,
-                            cudaStream_t st) {
+                            cudaStream_t st, bool band_only) {
   const int npen = b.rows / 2;
   const size_t smem = rows_smem_bytes<T>(g.n, b.rows);
   const int thr = rows_threads(g.n, npen);
   prof_begin(st);
   if (g.dim == 2)
-    k_rows_inv<T, 2, OutT><<<b.ntiles, thr, smem, st>>>(g, b, ws.spec, ws.tw, out);
+    k_rows_inv<T, 2, OutT><<<b.ntiles, thr, smem, st>>>(g, b, ws.spec, ws.tw, out, band_only);
   else
-    k_rows_inv<T, 3, OutT><<<b.ntiles, thr, smem, st>>>(g, b, ws.spec, ws.tw, out);
+    k_rows_inv<T, 3, OutT><<<b.ntiles, thr, smem, st>>>(g, b, ws.spec, ws.tw, out, band_only);
   count_launch(sizeof(T) == 8 ? "rows_inv_f64" : "rows_inv_f32", st);
   return check_launch();
 }
 
 template <typename T, int MODE>
 static cudaError_t run_pencils(const GridDesc& g, const PencilLayout& L, SpectralWs<T>& ws,
-                               cudaStream_t st) {
+                               cudaStream_t st, const int* zskip = nullptr, int ngroups = 0) {
   const int blocks = (L.npencils + L.c - 1) / L.c;
   int thr = L.c * g.n / 8;
   if (thr < 64) thr = 64;
@@ -98,7 +100,8 @@ static cudaError_t run_pencils(const GridDesc& g, const PencilLayout& L, Spectra
   const T cfac = (T)(4.0 * g.kappa / (g.h * g.h));
   const T scale0 = (T)(g.kappa / nd);
   prof_begin(st);
-  k_pencils<T, MODE><<<blocks, thr, smem, st>>>(g, L, ws.spec, ws.tw, ws.s2, cfac, scale0);
+  k_pencils<T, MODE><<<blocks, thr, smem, st>>>(g, L, ws.spec, ws.tw, ws.s2, cfac, scale0,
+                                                 zskip, ngroups);
   static const char* names[2][3] = {{"pencils_fwd_f32", "pencils_inv_f32", "pencils_solve_f32"},
                                     {"pencils_fwd_f64", "pencils_inv_f64", "pencils_solve_f64"}};
   count_launch(names[sizeof(T) == 8 ? 1 : 0][MODE], st);
@@ -106,17 +109,18 @@ static cudaError_t run_pencils(const GridDesc& g, const PencilLayout& L, Spectra
 }
 
 template <typename T>
-cudaError_t launch_spectral_solve(const GridDesc& g, SpectralWs<T>& ws, cudaStream_t st) {
-  const int n = g.n, half = n / 2;
+cudaError_t launch_spectral_solve(const GridDesc& g, SpectralWs<T>& ws, cudaStream_t st,
+                                  const Bins* skip, bool skip_fwd) {
   cudaError_t e;
-  (void)n;
-  (void)half;
   if (g.dim == 2) return run_pencils<T, 2>(g, solve_layout<T>(2, g.n, 1), ws, st);
   PencilLayout Ly = solve_layout<T>(3, g.n, 0);   // (kx, z) -> y
   PencilLayout Lz = solve_layout<T>(3, g.n, 1);   // (kx, y) -> z
-  if ((e = run_pencils<T, 0>(g, Ly, ws, st))) return e;
+  const int ngroups = g.n / (skip ? skip->rows : 1);
+  if ((e = run_pencils<T, 0>(g, Ly, ws, st, (skip && skip_fwd) ? skip->start : nullptr,
+                             ngroups)))
+    return e;
   if ((e = run_pencils<T, 2>(g, Lz, ws, st))) return e;
-  return run_pencils<T, 1>(g, Ly, ws, st);
+  return run_pencils<T, 1>(g, Ly, ws, st, skip ? skip->start : nullptr, ngroups);
 }
 
 template <typename T>
@@ -160,15 +164,18 @@ template cudaError_t launch_rows_fwd<float>(const GridDesc&, const PointData&, c
                                             const SpreadSrc&, SpectralWs<float>&, double*,
                                             cudaStream_t);
 template cudaError_t launch_rows_inv<double, double>(const GridDesc&, const Bins&,
-                                                     SpectralWs<double>&, double*, cudaStream_t);
+                                                     SpectralWs<double>&, double*, cudaStream_t,
+                                                     bool);
 template cudaError_t launch_rows_inv<float, float>(const GridDesc&, const Bins&,
-                                                   SpectralWs<float>&, float*, cudaStream_t);
+                                                   SpectralWs<float>&, float*, cudaStream_t,
+                                                   bool);
 template cudaError_t launch_rows_inv<float, double>(const GridDesc&, const Bins&,
-                                                    SpectralWs<float>&, double*, cudaStream_t);
+                                                    SpectralWs<float>&, double*, cudaStream_t,
+                                                    bool);
 template cudaError_t launch_spectral_solve<double>(const GridDesc&, SpectralWs<double>&,
-                                                   cudaStream_t);
+                                                   cudaStream_t, const Bins*, bool);
 template cudaError_t launch_spectral_solve<float>(const GridDesc&, SpectralWs<float>&,
-                                                  cudaStream_t);
+                                                  cudaStream_t, const Bins*, bool);
 template int fft_kernels_per_solve<double>(int);
 template int fft_kernels_per_solve<float>(int);
 

@@ -189,7 +189,7 @@ __device__ __noinline__ void solver_rows_fwd(const SolveInst& I, const double* q
 template <typename T, int D>
 __device__ __noinline__ void solver_rows_inv(const SolveInst& I, int item, unsigned char* smem) {
   const SpectralWs<T> ws = ws_of<T>(I);
-  phase_rows_inv<T, D, T>(I.g, I.b, ws.spec, ws.tw, ws.grid, item, smem);
+  phase_rows_inv<T, D, T>(I.g, I.b, ws.spec, ws.tw, ws.grid, item, smem, true);
 }
 
 template <typename T, int MODE>
@@ -200,8 +200,11 @@ __device__ __noinline__ void solver_pencils(const SolveInst& I, int which, int i
   const double nd = g.dim == 3 ? (double)g.n * g.n * g.n : (double)g.n * g.n;
   const T cfac = (T)(4.0 * g.kappa / (g.h * g.h));
   const T scale0 = (T)(g.kappa / nd);
+  // the matvec's grid feeds only the interpolation and has no grid source:
+  // 3D y-pass items of planes without points are skipped (both directions)
+  const int* zskip = (g.dim == 3 && MODE != 2) ? I.b.start : nullptr;
   phase_pencils<T, MODE>(g, solve_layout<T>(g.dim, g.n, which), ws.spec, ws.tw, ws.s2, cfac,
-                         scale0, item, smem);
+                         scale0, item, smem, zskip, g.n / I.b.rows);
 }
 
 // phase: 0 rows_fwd, 1 y forward (3D), 2 solve pass, 3 y inverse (3D), 4 rows_inv
