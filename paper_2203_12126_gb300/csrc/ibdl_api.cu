@@ -266,7 +266,9 @@ template <typename T, typename OutT>
 ibdl_status field_solve(ibdl_geometry_s* g, const SpreadSrc& src, OutT* out, cudaStream_t st,
                         bool band_only = false) {
   SpectralWs<T>& ws = wsof<T>(g);
-  IBDL_CU(launch_rows_fwd<T>(g->grid, g->pd, g->bins, src, ws, nullptr, st));
+  SpreadSrc s = src;
+  s.skip_empty_planes = band_only && !src.f_grid;
+  IBDL_CU(launch_rows_fwd<T>(g->grid, g->pd, g->bins, s, ws, nullptr, st));
   IBDL_CU(launch_spectral_solve<T>(g->grid, ws, st, band_only ? &g->bins : nullptr,
                                    band_only && !src.f_grid));
   IBDL_CU((launch_rows_inv<T, OutT>(g->grid, g->bins, ws, out, st, band_only)));
@@ -630,6 +632,24 @@ ibdl_status ibdl_create_geometry(const ibdl_geometry_desc* d, void* stream, ibdl
   g->bins.ntiles = ntiles;
   g->bins.start = start;
   g->bins.pts = bpts;
+  if (dim == 3) {
+    // planes no point touches: their spectrum stays zero through the x and
+    // y passes of a matvec
+    std::vector<int> hs(ntiles + 1);
+    std::vector<unsigned char> hz(n);
+    unsigned char* dz = nullptr;
+    cudaError_t e = cudaMemcpyAsync(hs.data(), start, sizeof(int) * (ntiles + 1),
+                                    cudaMemcpyDeviceToHost, st);
+    if (!e) e = cudaStreamSynchronize(st);
+    if (e) return cleanup(cuda_fail(e, "plane flags"));
+    const int ng = n / rows;
+    for (int z = 0; z < n; ++z) hz[z] = hs[(size_t)(z + 1) * ng] == hs[(size_t)z * ng] ? 1 : 0;
+    if ((s = g->alloc(&dz, (size_t)n))) return cleanup(s);
+    e = cudaMemcpyAsync(dz, hz.data(), n, cudaMemcpyHostToDevice, st);
+    if (!e) e = cudaStreamSynchronize(st);
+    if (e) return cleanup(cuda_fail(e, "plane flags"));
+    g->bins.zempty = dz;
+  }
 
   {
     cudaError_t e = configure_fft_kernels(n, rows);

@@ -410,6 +410,9 @@ __device__ __forceinline__ void phase_rows_fwd(const GridDesc& g, const PointDat
   const size_t slab = (D == 3) ? (size_t)n * n : (size_t)n;
   const size_t pos0 = (size_t)z * n + y0;
 
+  if (D == 3 && src.skip_empty_planes && !src.f_grid && !write_grid && b.zempty &&
+      b.zempty[z])
+    return;  // a plane without points: zero, and read as zero by the z pass
   if (lo == hi && !src.f_grid) {
     // no source touches the tile: its rows, and so their spectrum, are zero
     if (write_grid) {
@@ -617,7 +620,8 @@ __device__ __forceinline__ void phase_pencils(const GridDesc& g, const PencilLay
                                               cx_t<T>* data, const cx_t<T>* __restrict__ tw,
                                               const T* __restrict__ s2, T cfac, T scale0,
                                               int blk, unsigned char* smem,
-                                              const int* zskip = nullptr, int ngroups = 0) {
+                                              const int* zskip = nullptr, int ngroups = 0,
+                                              const unsigned char* zempty = nullptr) {
   using C = cx_t<T>;
   const int n = g.n, lg = g.log2n, c = L.c, lgc = L.lgc, PS = pen_stride(n);
   const int ntw = fft_tw_count(n);
@@ -651,8 +655,13 @@ __device__ __forceinline__ void phase_pencils(const GridDesc& g, const PencilLay
         if (tfast) {
           v[u].load(base + 2 * k);
         } else {
+          // z pass: planes without points hold zeros (not written by the x pass)
           const int e = 2 * k, t = e >> lgc, pl = e & (c - 1);
-          v[u].load(base + (size_t)t * n + pl);
+          if (zempty && zempty[t]) {
+            v[u].a.x = v[u].a.y = v[u].b.x = v[u].b.y = 0;
+          } else {
+            v[u].load(base + (size_t)t * n + pl);
+          }
         }
       }
     }
@@ -706,6 +715,7 @@ __device__ __forceinline__ void phase_pencils(const GridDesc& g, const PencilLay
       v.store(base + 2 * k);
     } else {
       const int t = e >> lgc, pl = e & (c - 1);
+      if (zempty && zempty[t]) continue;  // never read by the y inverse pass
       v.a = res[pl * PS + padi(t)];
       v.b = res[(pl + 1) * PS + padi(t)];
       v.store(base + (size_t)t * n + pl);

@@ -46,6 +46,7 @@ struct Bins {
   int ntiles = 0;            // n^(d-2) * (n / R)
   const int* start = nullptr;  // ntiles + 1
   const int* pts = nullptr;
+  const unsigned char* zempty = nullptr;  // 3D: 1 for z planes no point touches
 };
 
 struct GridDesc {
@@ -74,6 +75,9 @@ struct SpreadSrc {
   double coef_plain = 0;
   const double* f_grid = nullptr;
   double coef_grid = 0;
+  // 3D, no grid source, grid feeding only the interpolation: tiles of
+  // planes without points are not written (the z pass reads them as zero)
+  bool skip_empty_planes = false;
 };
 
 // ---- launch bookkeeping -------------------------------------------------

@@ -34,10 +34,11 @@ template <typename T, int MODE>
 __global__ void __launch_bounds__(512) k_pencils(GridDesc g, PencilLayout L, cx_t<T>* data,
                                                  const cx_t<T>* __restrict__ tw,
                                                  const T* __restrict__ s2, T cfac, T scale0,
-                                                 const int* zskip, int ngroups) {
+                                                 const int* zskip, int ngroups,
+                                                 const unsigned char* zempty) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   phase_pencils<T, MODE>(g, L, data, tw, s2, cfac, scale0, blockIdx.x, smem_raw, zskip,
-                         ngroups);
+                         ngroups, zempty);
 }
 
 template <typename T, int D, typename OutT>
@@ -90,7 +91,8 @@ cudaError_t launch_rows_inv(const GridDesc& g, const Bins& b, SpectralWs<T>& ws,
 
 template <typename T, int MODE>
 static cudaError_t run_pencils(const GridDesc& g, const PencilLayout& L, SpectralWs<T>& ws,
-                               cudaStream_t st, const int* zskip = nullptr, int ngroups = 0) {
+                               cudaStream_t st, const int* zskip = nullptr, int ngroups = 0,
+                               const unsigned char* zempty = nullptr) {
   const int blocks = (L.npencils + L.c - 1) / L.c;
   int thr = L.c * g.n / 8;
   if (thr < 64) thr = 64;
@@ -101,7 +103,7 @@ static cudaError_t run_pencils(const GridDesc& g, const PencilLayout& L, Spectra
   const T scale0 = (T)(g.kappa / nd);
   prof_begin(st);
   k_pencils<T, MODE><<<blocks, thr, smem, st>>>(g, L, ws.spec, ws.tw, ws.s2, cfac, scale0,
-                                                 zskip, ngroups);
+                                                 zskip, ngroups, zempty);
   static const char* names[2][3] = {{"pencils_fwd_f32", "pencils_inv_f32", "pencils_solve_f32"},
                                     {"pencils_fwd_f64", "pencils_inv_f64", "pencils_solve_f64"}};
   count_launch(names[sizeof(T) == 8 ? 1 : 0][MODE], st);
@@ -119,7 +121,9 @@ cudaError_t launch_spectral_solve(const GridDesc& g, SpectralWs<T>& ws, cudaStre
   if ((e = run_pencils<T, 0>(g, Ly, ws, st, (skip && skip_fwd) ? skip->start : nullptr,
                              ngroups)))
     return e;
-  if ((e = run_pencils<T, 2>(g, Lz, ws, st))) return e;
+  if ((e = run_pencils<T, 2>(g, Lz, ws, st, nullptr, 0,
+                             (skip && skip_fwd) ? skip->zempty : nullptr)))
+    return e;
   return run_pencils<T, 1>(g, Ly, ws, st, skip ? skip->start : nullptr, ngroups);
 }
 

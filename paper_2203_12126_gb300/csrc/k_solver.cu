@@ -175,6 +175,7 @@ template <typename T, int D>
 __device__ __noinline__ void solver_rows_fwd(const SolveInst& I, const double* q, int item,
                                              unsigned char* smem) {
   SpreadSrc src;
+  src.skip_empty_planes = true;  // the grid feeds only the interpolation
   if (q) {
     src.q_div = q;
     src.coef_div = 1.0;
@@ -204,7 +205,8 @@ __device__ __noinline__ void solver_pencils(const SolveInst& I, int which, int i
   // 3D y-pass items of planes without points are skipped (both directions)
   const int* zskip = (g.dim == 3 && MODE != 2) ? I.b.start : nullptr;
   phase_pencils<T, MODE>(g, solve_layout<T>(g.dim, g.n, which), ws.spec, ws.tw, ws.s2, cfac,
-                         scale0, item, smem, zskip, g.n / I.b.rows);
+                         scale0, item, smem, zskip, g.n / I.b.rows,
+                         (g.dim == 3 && MODE == 2) ? I.b.zempty : nullptr);
 }
 
 // phase: 0 rows_fwd, 1 y forward (3D), 2 solve pass, 3 y inverse (3D), 4 rows_inv
