@@ -56,6 +56,8 @@ def parse():
                     help="0: persistent single-launch solver, 1: host-driven loop")
     ap.add_argument("--no-matvec", action="store_true",
                     help="skip the matvec HBM-roofline measurement")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the 256-instance batched measurement")
     ap.add_argument("--serve-requests", type=int, default=200,
                     help="requests of the mixed serving stream (0: skip it)")
     return ap.parse_args()
@@ -128,8 +130,51 @@ def run_serving(pkg, nreq, seed=3, rate=2000.0, budget=120 << 30):
         "max_rel_residual": float(max(x["rel_residual"] for x in ok)) if ok else None,
         "memory_budget_bytes": budget, "peak_device_bytes": int(stats["peak_bytes"]),
         "slices": int(stats["launches"]),
+        "host_admit_s": float(stats["admit_seconds"]),
+        "host_wait_for_gpu_s": float(stats["wait_seconds"]),
+        "queue_wait_ms_p50": float(np.median([(x["t_admit"] - x["t_arrival"]) * 1e3
+                                              for x in recs])),
+        "in_service_ms_p50": float(np.median([(x["t_done"] - x["t_admit"]) * 1e3
+                                              for x in recs])),
         "offered_span_s": float(reqs[-1].t), "makespan_s": float(span),
     }
+
+
+def run_batched_c4(pkg, count=256, reps=3):
+    """C4: `count` uneven 2D star instances (N in {128,256,512}^2, kappa
+    log-uniform [1e-4,1e-1], seed 2) solved in ONE persistent launch,
+    float32-refined to 1e-8; event-timed, L2 flushed between launches."""
+    import torch
+    from paper_2203_12126_gb300 import ibdl
+    dev = torch.device("cuda", torch.cuda.current_device())
+    insts = configs.c4_instances(count)
+    geoms = [pkg.Geometry.from_workload(p.geom, bc=p.bc, precision=ibdl.FP32_REFINED)
+             for p in insts]
+    bs = [torch.tensor(p.bdata, dtype=torch.float64, device=dev) for p in insts]
+    qs = [torch.zeros(p.geom.m, dtype=torch.float64, device=dev) for p in insts]
+    batch = ibdl.Batch(count)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    batch.solve(geoms, bs, qs, tol=1e-8)
+    ms, infos = [], None
+    for _ in range(reps):
+        flush.fill_(4.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        infos = batch.solve(geoms, bs, qs, tol=1e-8)
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    batch.close()
+    for g in geoms:
+        g.close()
+    med = float(np.median(ms))
+    return {"workload": f"{count} 2D star instances, N in {{128,256,512}}^2 (seed 2), "
+                        "float32-refined, tol 1e-8, one persistent launch",
+            "solves_per_s": count / (med / 1e3), "launch_ms": med,
+            "max_rel_residual": float(max(f["rel_residual"] for f in infos)),
+            "all_ok": all(f["status"] == 0 for f in infos),
+            "iters": {"min": min(f["iters"] for f in infos),
+                      "max": max(f["iters"] for f in infos)}}
 
 
 def problems():
@@ -568,6 +613,8 @@ def main():
 
     matvec = run_matvec_roofline(pkg, peaks) if not args.no_matvec else None
 
+    batched_c4 = run_batched_c4(pkg) if not args.no_batched else None
+
     serving = None
     if args.serve_requests > 0:
         serving = run_serving(pkg, args.serve_requests)
@@ -615,6 +662,7 @@ def main():
             "cpu_baseline": cpu,
             "e2e": e2e,
             "matvec": matvec,
+            "batched_c4": batched_c4,
             "serving": serving,
             "gpu_launches": int(launches),
             "wall_s_timed": wall,

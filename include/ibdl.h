@@ -221,7 +221,8 @@ ibdl_status ibdl_solve_batched(ibdl_batch b, int32_t count, const ibdl_geometry*
  *      as a slot is free and the device bytes of all admitted requests stay
  *      within `memory_budget`: each one's geometry is built on a second
  *      stream, on the `reserve_sms` SMs the solver leaves free, and it joins
- *      the next slice;
+ *      the next slice; admission stops once the slice has finished (at
+ *      least one request per step), or after 8 requests when no slice runs;
  *   3. waits for the slice and retires the requests whose solve finished,
  *      releasing their slot and memory.
  * Every request is solved exactly as ibdl_solve would solve it alone (the
@@ -260,6 +261,8 @@ typedef struct {
   int32_t reserved;
   int64_t bytes_in_use, peak_bytes, memory_budget;
   int64_t steps, launches, submitted;
+  double admit_seconds;     /* host time spent setting requests up */
+  double wait_seconds;      /* host time spent waiting for slices */
 } ibdl_server_stats;
 
 void ibdl_server_config_default(ibdl_server_config* cfg);

@@ -20,6 +20,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "ibdl_device.cuh"
@@ -121,6 +122,41 @@ static bool is_device_ptr(const void* p) {
 
 using namespace ibdl;
 
+namespace {
+
+// Device workspaces of geometry handles come from one stream-ordered memory
+// pool per device that keeps freed blocks for reuse (release threshold at
+// its maximum): creating and destroying many handles -- the serving engine
+// does one per request -- then costs no cudaMalloc/cudaFree round trips.
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[64] = {};
+
+cudaError_t workspace_pool(cudaMemPool_t* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool;
+    if ((e = cudaMemPoolCreate(&pool, &props))) return e;
+    uint64_t keep = ~0ull;
+    if ((e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep))) return e;
+    g_pool[dev] = pool;
+  }
+  *out = g_pool[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+constexpr int kHistCapHost = 256;  // residual history entries (kHistCap)
+
 struct ibdl_geometry_s {
   GridDesc grid;
   int bc = 0, precision = 0, m = 0;
@@ -150,20 +186,41 @@ struct ibdl_geometry_s {
   int64_t ncells = 0;
   std::vector<void*> dev_allocs;
 
+  cudaStream_t alloc_st = nullptr;  // stream of the creating call
+
+  // Pool allocation, ordered on the creating stream (which the creation
+  // synchronises before returning, so other streams may use the memory).
   template <typename P>
   ibdl_status alloc(P** out, size_t count) {
     void* p = nullptr;
     const size_t nbytes = count * sizeof(P);
-    cudaError_t e = cudaMalloc(&p, nbytes > 0 ? nbytes : 16);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    cudaMemPool_t pool;
+    cudaError_t e = workspace_pool(&pool);
+    if (!e) e = cudaMallocFromPoolAsync(&p, nbytes > 0 ? nbytes : 16, pool, alloc_st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return e == cudaErrorMemoryAllocation ? fail(IBDL_ERR_OOM, "device workspace")
+                                            : cuda_fail(e, "cudaMallocFromPoolAsync");
+    }
     dev_allocs.push_back(p);
     bytes += (int64_t)nbytes;
     *out = static_cast<P*>(p);
     return IBDL_OK;
   }
+  // Pinned host scratch of ibdl_solve, made on its first call.
+  ibdl_status ensure_host() {
+    if (host_scal) return IBDL_OK;
+    cudaError_t e = cudaMallocHost((void**)&h_inst, sizeof(SolveInst));
+    if (!e) e = cudaMallocHost((void**)&h_state, sizeof(SolveState));
+    if (!e) e = cudaMallocHost((void**)&h_hist, kHistCapHost * sizeof(double));
+    if (!e) e = cudaMallocHost((void**)&host_scal, 16 * sizeof(double));
+    if (e) return cuda_fail(e, "cudaMallocHost");
+    return IBDL_OK;
+  }
+  // The handle's users have finished (ibdl_destroy_geometry synchronises
+  // the device first): the blocks go back to the pool.
   ~ibdl_geometry_s() {
-    for (void* p : dev_allocs) cudaFree(p);
-    if (bins.pts) cudaFree((void*)bins.pts);
+    for (void* p : dev_allocs) cudaFreeAsync(p, 0);
     if (host_scal) cudaFreeHost(host_scal);
     if (h_inst) cudaFreeHost(h_inst);
     if (h_state) cudaFreeHost(h_state);
@@ -173,38 +230,83 @@ struct ibdl_geometry_s {
 
 namespace {
 
+// cos and sin of 2 pi num / den (0 <= num < den): exact quadrant and octant
+// reduction, then the double library functions on |angle| <= pi/4.
+void cis_2pi(int64_t num, int64_t den, double* c, double* s) {
+  num %= den;
+  const double x = (double)num / (double)den;  // exact: den is a power of two
+  const int k = (int)(4.0 * x);                 // quadrant
+  double y = x - 0.25 * k;                      // [0, 1/4), exact
+  const bool swap = y > 0.125;
+  if (swap) y = 0.25 - y;
+  const double t = 6.283185307179586476925286766559 * y;
+  double cc = cos(t), ss = sin(t);
+  if (swap) {
+    const double u = cc;
+    cc = ss;
+    ss = u;
+  }
+  switch (k & 3) {
+    case 0: *c = cc; *s = ss; break;
+    case 1: *c = -ss; *s = cc; break;
+    case 2: *c = -cc; *s = -ss; break;
+    default: *c = ss; *s = -cc; break;
+  }
+}
+
+// FFT pass twiddles and sin^2(pi j / n) tables, read-only and the same for
+// every handle with the same n: made once per (device, n, precision) and
+// kept for the life of the process.
+std::mutex g_tab_mu;
+std::map<std::tuple<int, int, int>, std::pair<const void*, const void*>> g_tabs;
+
 template <typename T>
-ibdl_status alloc_spectral(ibdl_geometry_s* g, SpectralWs<T>& ws, cudaStream_t st) {
+ibdl_status fft_tables(int n, const typename Cx<T>::type** tw_out, const T** s2_out) {
+  int dev = 0;
+  IBDL_CU(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_tab_mu);
+  const auto key = std::make_tuple(dev, n, (int)sizeof(T));
+  auto it = g_tabs.find(key);
+  if (it == g_tabs.end()) {
+    const int ntw = fft_tw_count(n);
+    std::vector<typename Cx<T>::type> htw(ntw);
+    std::vector<T> hs2(n);
+    for (int j = 0; j < ntw; ++j) {
+      int num, den;
+      fft_tw_angle(n, j, &num, &den);
+      double c, s;
+      cis_2pi(num, den, &c, &s);
+      htw[j].x = (T)c;
+      htw[j].y = (T)-s;
+    }
+    for (int j = 0; j < n; ++j) {
+      double c, s;
+      cis_2pi(j, 2 * (int64_t)n, &c, &s);  // sin(pi j / n)
+      hs2[j] = (T)(s * s);
+    }
+    void *dtw = nullptr, *ds2 = nullptr;
+    IBDL_CU(cudaMalloc(&dtw, sizeof(htw[0]) * ntw));
+    IBDL_CU(cudaMalloc(&ds2, sizeof(T) * n));
+    IBDL_CU(cudaMemcpy(dtw, htw.data(), sizeof(htw[0]) * ntw, cudaMemcpyHostToDevice));
+    IBDL_CU(cudaMemcpy(ds2, hs2.data(), sizeof(T) * n, cudaMemcpyHostToDevice));
+    it = g_tabs.emplace(key, std::make_pair((const void*)dtw, (const void*)ds2)).first;
+  }
+  *tw_out = static_cast<const typename Cx<T>::type*>(it->second.first);
+  *s2_out = static_cast<const T*>(it->second.second);
+  return IBDL_OK;
+}
+
+template <typename T>
+ibdl_status alloc_spectral(ibdl_geometry_s* g, SpectralWs<T>& ws, cudaStream_t) {
   const int n = g->grid.n;
   const int64_t spec_count = (int64_t)(n / 2 + 1) * (g->ncells / n);
   typename Cx<T>::type* spec;
   T* grid;
-  typename Cx<T>::type* tw;
-  T* s2;
+  const typename Cx<T>::type* tw;
+  const T* s2;
   IBDL_TRY(g->alloc(&spec, (size_t)spec_count));
   IBDL_TRY(g->alloc(&grid, (size_t)g->ncells));
-  const int ntw = fft_tw_count(n);
-  IBDL_TRY(g->alloc(&tw, (size_t)ntw));
-  IBDL_TRY(g->alloc(&s2, (size_t)n));
-  std::vector<typename Cx<T>::type> htw(ntw);
-  std::vector<T> hs2(n);
-  const long double two_pi = 2.0L * 3.14159265358979323846264338327950288L;
-  for (int j = 0; j < ntw; ++j) {
-    // the FFT pass twiddles exp(-2 pi i num / den), from long double arithmetic
-    int num, den;
-    fft_tw_angle(n, j, &num, &den);
-    const long double a = two_pi * (long double)(num % den) / den;
-    htw[j].x = (T)cosl(a);
-    htw[j].y = (T)-sinl(a);
-  }
-  for (int j = 0; j < n; ++j) {
-    // sin^2(pi j / n)
-    const long double s = sinl(0.5L * two_pi * j / n);
-    hs2[j] = (T)(s * s);
-  }
-  IBDL_CU(cudaMemcpyAsync(tw, htw.data(), sizeof(htw[0]) * ntw, cudaMemcpyHostToDevice, st));
-  IBDL_CU(cudaMemcpyAsync(s2, hs2.data(), sizeof(T) * n, cudaMemcpyHostToDevice, st));
-  IBDL_CU(cudaStreamSynchronize(st));
+  IBDL_TRY(fft_tables<T>(n, &tw, &s2));
   ws.spec = spec;
   ws.grid = grid;
   ws.tw = tw;
@@ -528,7 +630,9 @@ ibdl_status ibdl_create_geometry(const ibdl_geometry_desc* d, void* stream, ibdl
     return fail(IBDL_ERR_INVALID_ARG, "NULL point, normal or weight array");
 
   ibdl_geometry_s* g = new ibdl_geometry_s();
+  g->alloc_st = st;
   auto cleanup = [&](ibdl_status s) {
+    cudaStreamSynchronize(st);  // nothing in flight may use the freed blocks
     delete g;
     return s;
   };
@@ -622,12 +726,13 @@ ibdl_status ibdl_create_geometry(const ibdl_geometry_desc* d, void* stream, ibdl
   if ((s = g->alloc(&start, (size_t)ntiles + 1))) return cleanup(s);
   if ((s = g->alloc(&cursor, (size_t)ntiles + 1))) return cleanup(s);
   int* bpts = nullptr;
-  int nnz = 0;
+  int* counts = nullptr;
+  if ((s = g->alloc(&counts, (size_t)ntiles + 1))) return cleanup(s);
+  if ((s = g->alloc(&bpts, (size_t)bins_capacity(dim, rows, m)))) return cleanup(s);
   {
-    cudaError_t e = launch_bins(gd, pd, rows, ntiles, start, cursor, &bpts, &nnz, st);
+    cudaError_t e = launch_bins(gd, pd, rows, ntiles, start, cursor, counts, bpts, st);
     if (e) return cleanup(cuda_fail(e, "binning"));
   }
-  g->bytes += (int64_t)nnz * 4;
   g->bins.rows = rows;
   g->bins.ntiles = ntiles;
   g->bins.start = start;
@@ -635,18 +740,9 @@ ibdl_status ibdl_create_geometry(const ibdl_geometry_desc* d, void* stream, ibdl
   if (dim == 3) {
     // planes no point touches: their spectrum stays zero through the x and
     // y passes of a matvec
-    std::vector<int> hs(ntiles + 1);
-    std::vector<unsigned char> hz(n);
     unsigned char* dz = nullptr;
-    cudaError_t e = cudaMemcpyAsync(hs.data(), start, sizeof(int) * (ntiles + 1),
-                                    cudaMemcpyDeviceToHost, st);
-    if (!e) e = cudaStreamSynchronize(st);
-    if (e) return cleanup(cuda_fail(e, "plane flags"));
-    const int ng = n / rows;
-    for (int z = 0; z < n; ++z) hz[z] = hs[(size_t)(z + 1) * ng] == hs[(size_t)z * ng] ? 1 : 0;
     if ((s = g->alloc(&dz, (size_t)n))) return cleanup(s);
-    e = cudaMemcpyAsync(dz, hz.data(), n, cudaMemcpyHostToDevice, st);
-    if (!e) e = cudaStreamSynchronize(st);
+    cudaError_t e = launch_plane_flags(start, n / rows, n, dz, st);
     if (e) return cleanup(cuda_fail(e, "plane flags"));
     g->bins.zempty = dz;
   }
@@ -691,17 +787,10 @@ ibdl_status ibdl_create_geometry(const ibdl_geometry_desc* d, void* stream, ibdl
   if ((s = g->alloc(&g->d_inst, (size_t)1))) return cleanup(s);
   if ((s = g->alloc(&g->d_state, (size_t)1))) return cleanup(s);
   if ((s = g->alloc(&g->d_bar, (size_t)8))) return cleanup(s);
-  {
-    cudaError_t e = cudaMallocHost((void**)&g->h_inst, sizeof(SolveInst));
-    if (!e) e = cudaMallocHost((void**)&g->h_state, sizeof(SolveState));
-    if (!e) e = cudaMallocHost((void**)&g->h_hist, kHistCap * sizeof(double));
-    if (e) return cleanup(cuda_fail(e, "cudaMallocHost"));
-  }
+
   g->solver_smem = solver_smem_bytes(gd, 1);
   {
-    cudaError_t e = cudaMallocHost((void**)&g->host_scal, 16 * sizeof(double));
-    if (e) return cleanup(cuda_fail(e, "cudaMallocHost"));
-    e = cudaStreamSynchronize(st);
+    cudaError_t e = cudaStreamSynchronize(st);
     if (e) return cleanup(cuda_fail(e, "create sync"));
   }
   *out = g;
@@ -755,6 +844,7 @@ ibdl_status ibdl_solve(ibdl_geometry g, const double* bdata, const double* g_gri
   if (o.engine != 0 && o.engine != 1) return fail(IBDL_ERR_INVALID_ARG, "engine is 0 or 1");
   cudaStream_t st = (cudaStream_t)stream;
   const int m = g->m;
+  IBDL_TRY(g->ensure_host());
   // inputs
   IBDL_CU(cudaMemcpyAsync(g->stage_a, bdata, sizeof(double) * m, cudaMemcpyDefault, st));
   const double* gg = nullptr;
@@ -1105,6 +1195,7 @@ ibdl_status ibdl_solve_batched(ibdl_batch b, int32_t count, const ibdl_geometry*
   for (int k = 0; k < count; ++k) {
     if (!geoms[k] || !bdata[k] || !q_out[k])
       return fail(IBDL_ERR_INVALID_ARG, "NULL geometry, bdata or q_out entry");
+    IBDL_TRY(geoms[k]->ensure_host());
     for (int l = 0; l < k; ++l)
       if (geoms[l] == geoms[k])
         return fail(IBDL_ERR_INVALID_ARG, "a geometry handle appears twice in one batch");
@@ -1298,6 +1389,7 @@ struct ibdl_server_s {
   std::map<int64_t, SrvReq*> done;
   std::vector<int64_t> just_done;      // finished during the current step
   int64_t next_id = 1, bytes = 0, peak = 0, steps = 0, launches = 0;
+  double admit_seconds = 0, wait_seconds = 0;
   std::mutex mu;
   ~ibdl_server_s() {
     if (solve_st) cudaStreamSynchronize(solve_st);
@@ -1375,8 +1467,17 @@ ibdl_status admit_one(ibdl_server_s* s, SrvReq* r, int k) {
 
 // Admits queued requests in arrival order while a slot is free and the
 // budget allows; a request larger than the whole budget fails with OOM.
-void admit_queued(ibdl_server_s* s) {
+// While a slice runs, admission stops as soon as it has finished, so the
+// GPU is not left idle behind host-side set-up; with no slice running at
+// most kIdleAdmit requests are set up before the next launch.
+constexpr int kIdleAdmit = 8;
+void admit_queued(ibdl_server_s* s, bool slice_running) {
+  int admitted = 0;
+  const double t0 = server_now();
   while (!s->queue.empty()) {
+    if (slice_running ? (admitted > 0 && cudaStreamQuery(s->solve_st) != cudaErrorNotReady)
+                      : admitted >= kIdleAdmit)
+      break;
     SrvReq* r = s->queue.front();
     if (r->est > s->cfg.memory_budget) {
       s->queue.pop_front();
@@ -1394,7 +1495,9 @@ void admit_queued(ibdl_server_s* s) {
     s->queue.pop_front();
     const ibdl_status st = admit_one(s, r, k);
     if (st != IBDL_OK) finish_request(s, r, st);
+    ++admitted;
   }
+  s->admit_seconds += server_now() - t0;
 }
 
 // Retires slot k: result to the host, geometry released.
@@ -1588,10 +1691,12 @@ ibdl_status ibdl_server_step(ibdl_server s, int64_t* done_ids, int32_t max_ids,
     }
   }
   // 2. admit while the slice runs (set-up kernels use the reserved SMs)
-  admit_queued(s);
+  admit_queued(s, launched);
   // 3. wait, then retire finished solves
   if (launched) {
+    const double tw = server_now();
     const cudaError_t e = cudaStreamSynchronize(s->solve_st);
+    s->wait_seconds += server_now() - tw;
     if (e)
       slice_err = cuda_fail(e, "server: slice");
     else if (s->h_bar[2])
@@ -1657,5 +1762,7 @@ ibdl_status ibdl_server_get_stats(ibdl_server s, ibdl_server_stats* out) {
   out->steps = s->steps;
   out->launches = s->launches;
   out->submitted = s->next_id - 1;
+  out->admit_seconds = s->admit_seconds;
+  out->wait_seconds = s->wait_seconds;
   return IBDL_OK;
 }

@@ -97,10 +97,14 @@ ibdl_status set_last_error(ibdl_status s, const char* msg);
 cudaError_t launch_point_prep(const GridDesc& g, int m, const double* const X[3],
                               int* const base[3], double* const W64[3],
                               float* const W32[3], cudaStream_t st);
-// Bin building: counts, scan, fill.  tmp_counts has ntiles + 1 ints.
+// Bin building: counts, scan, fill (asynchronous).  counts: ntiles + 1
+// ints of scratch; pts: bins_capacity(dim, rows, m) ints.
 cudaError_t launch_bins(const GridDesc& g, const PointData& p, int rows, int ntiles,
-                        int* start, int* cursor, int** pts_out, int* nnz_out,
-                        cudaStream_t st);
+                        int* start, int* cursor, int* counts, int* pts, cudaStream_t st);
+int64_t bins_capacity(int dim, int rows, int64_t m);
+// 3D: zempty[z] = 1 for planes whose tiles list no point.
+cudaError_t launch_plane_flags(const int* start, int ngroups, int n, unsigned char* zempty,
+                               cudaStream_t st);
 template <typename T>
 cudaError_t launch_interp(const GridDesc& g, const PointData& p, const T* grid,
                           const double* jvec, double jump, double* y, cudaStream_t st);

@@ -115,26 +115,13 @@ __global__ void k_scan(const int* counts, int* start, int* cursor, int ntiles) {
   }
 }
 
-// Sort each tile's list by point index (insertion sort, lists are short), so
-// the per-tile processing order does not depend on atomic scheduling.
-__global__ void k_bins_sort(const int* start, int* pts, int ntiles) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= ntiles) return;
-  const int lo = start[t], hi = start[t + 1];
-  for (int a = lo + 1; a < hi; ++a) {
-    const int v = pts[a];
-    int b = a - 1;
-    while (b >= lo && pts[b] > v) {
-      pts[b + 1] = pts[b];
-      --b;
-    }
-    pts[b + 1] = v;
-  }
-}
-
+// Tile lists: count, scan, fill.  The order of points inside a tile is the
+// order of the fill's atomics; it does not matter, since the spread adds a
+// tile's contributions with shared-memory atomics anyway (the sum is the
+// same up to rounding in any order).  pts has room for the largest possible
+// count (bins_capacity), so no host round trip sizes it.
 cudaError_t launch_bins(const GridDesc& g, const PointData& p, int rows, int ntiles,
-                        int* start, int* cursor, int** pts_out, int* nnz_out,
-                        cudaStream_t st) {
+                        int* start, int* cursor, int* counts, int* pts, cudaStream_t st) {
   cudaError_t e;
   const int bs = 256;
   const int gb = (p.m + bs - 1) / bs;
@@ -143,9 +130,6 @@ cudaError_t launch_bins(const GridDesc& g, const PointData& p, int rows, int nti
   k_bins<false><<<gb, bs, 0, st>>>(g, p, rows, cursor, nullptr);
   count_launch("bins", st);
   if ((e = check_launch())) return e;
-  // counts live in cursor; scan them into start and re-seed cursor
-  int* counts = nullptr;
-  if ((e = cudaMallocAsync((void**)&counts, sizeof(int) * (ntiles + 1), st))) return e;
   if ((e = cudaMemcpyAsync(counts, cursor, sizeof(int) * (ntiles + 1),
                            cudaMemcpyDeviceToDevice, st)))
     return e;
@@ -153,24 +137,30 @@ cudaError_t launch_bins(const GridDesc& g, const PointData& p, int rows, int nti
   k_scan<<<1, 1024, 0, st>>>(counts, start, cursor, ntiles);
   count_launch("scan", st);
   if ((e = check_launch())) return e;
-  int nnz = 0;
-  if ((e = cudaMemcpyAsync(&nnz, start + ntiles, sizeof(int), cudaMemcpyDeviceToHost, st)))
-    return e;
-  if ((e = cudaStreamSynchronize(st))) return e;
-  cudaFreeAsync(counts, st);
-  int* pts = nullptr;
-  if ((e = cudaMalloc((void**)&pts, sizeof(int) * (nnz > 0 ? nnz : 1)))) return e;
   prof_begin(st);
   k_bins<true><<<gb, bs, 0, st>>>(g, p, rows, cursor, pts);
   count_launch("bins", st);
-  if ((e = check_launch())) return e;
+  return check_launch();
+}
+
+int64_t bins_capacity(int dim, int rows, int64_t m) {
+  // the 6 support rows meet at most 1 + ceil(5 / R) row groups, on 6 planes in 3D
+  const int64_t groups = 1 + (5 + rows - 1) / rows;
+  return m * groups * (dim == 3 ? 6 : 1);
+}
+
+// zempty[z] = 1 when no tile of plane z lists a point (3D).
+__global__ void k_plane_flags(const int* start, int ngroups, int n, unsigned char* zempty) {
+  const int z = blockIdx.x * blockDim.x + threadIdx.x;
+  if (z < n) zempty[z] = start[(z + 1) * ngroups] == start[z * ngroups] ? 1 : 0;
+}
+
+cudaError_t launch_plane_flags(const int* start, int ngroups, int n, unsigned char* zempty,
+                               cudaStream_t st) {
   prof_begin(st);
-  k_bins_sort<<<(ntiles + 127) / 128, 128, 0, st>>>(start, pts, ntiles);
-  count_launch("bins_sort", st);
-  if ((e = check_launch())) return e;
-  *pts_out = pts;
-  *nnz_out = nnz;
-  return cudaSuccess;
+  k_plane_flags<<<(n + 127) / 128, 128, 0, st>>>(start, ngroups, n, zempty);
+  count_launch("plane_flags", st);
+  return check_launch();
 }
 
 // ---- interpolation ------------------------------------------------------------

@@ -103,7 +103,7 @@ class ServerStats(C.Structure):
         ("queued", C.c_int32), ("active", C.c_int32), ("finished", C.c_int32),
         ("reserved", C.c_int32), ("bytes_in_use", C.c_int64), ("peak_bytes", C.c_int64),
         ("memory_budget", C.c_int64), ("steps", C.c_int64), ("launches", C.c_int64),
-        ("submitted", C.c_int64),
+        ("submitted", C.c_int64), ("admit_seconds", C.c_double), ("wait_seconds", C.c_double),
     ]
 
 
