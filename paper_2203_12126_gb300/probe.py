@@ -2,13 +2,15 @@
 
     python -m paper_2203_12126_gb300.probe matvec c3 f32 [reps]
     python -m paper_2203_12126_gb300.probe solve c2 [reps]
+    python -m paper_2203_12126_gb300.probe pair c2 [reps]
 
 ``matvec`` applies the boundary operator of the 3D sphere (c3: N=256^3,
 M=38039) or the 2D star (c2: N=1024^2, M=3525) ``reps`` times (default 5)
 in float32 (f32) or float64 (f64); ``solve`` runs ``reps`` (default 2)
 float32-refined Dirichlet solves of c2 at tolerance 1e-8 through the
-persistent solver.  Everything runs in the CUDA library; the script only
-builds the inputs.
+persistent solver; ``pair`` runs ``reps`` (default 2) batched launches of the
+benchmark's step, the c2 Dirichlet + Neumann pair in one persistent launch.
+Everything runs in the CUDA library; the script only builds the inputs.
 """
 from __future__ import annotations
 
@@ -50,6 +52,23 @@ def main(argv):
             info = g.solve(b, q, tol=1e-8)
         torch.cuda.synchronize()
         print(f"solve {case} x{reps}: iters {info['iters']} rel_res {info['rel_residual']:.2e}")
+    elif what == "pair":
+        reps = int(argv[2]) if len(argv) > 2 else 2
+        from paper_2203_12126_gb300 import ibdl
+        probs = [configs.c2(bc=configs.DIRICHLET), configs.c2(bc=configs.NEUMANN)]
+        gs = [pkg.Geometry.from_workload(p.geom, bc=p.bc, precision=pkg.FP32_REFINED)
+              for p in probs]
+        bs = [torch.tensor(p.bdata, device=dev) for p in probs]
+        qs = [torch.empty_like(b) for b in bs]
+        batch = ibdl.Batch(2)
+        for _ in range(reps):
+            infos = batch.solve(gs, bs, qs, tol=1e-8)
+        torch.cuda.synchronize()
+        print(f"pair {case} x{reps}: iters {[f['iters'] for f in infos]}")
+        batch.close()
+        for gg in gs:
+            gg.close()
+        return 0
     else:
         raise SystemExit(__doc__)
     g.close()
