@@ -537,21 +537,14 @@ def main():
     tot_prof = sum(v[1] for v in kstats.values()) or 1.0
     for name, (cnt, ms) in kstats.items():
         kernels[name] = {"launches": cnt, "avg_us": ms / cnt * 1e3, "share": ms / tot_prof}
+    # solver items: per phase, the summed duration of its work items (blocks
+    # run items of different phases and instances at the same time)
     phases = {}
-    tot_phase = sum(v[1] for v in pstats.values()) or 1.0
+    tot_phase = sum(v[1] for k, v in pstats.items() if "idle" not in k) or 1.0
     for name, (cnt, ms) in pstats.items():
-        e = {"count": cnt, "avg_us": ms / cnt * 1e3, "share_of_solver": ms / tot_phase}
-        model = kernel_model(name, n, m)
-        if model is not None:
-            avg_s = ms / cnt / 1e3
-            if name.endswith("f64"):
-                e.update(bound="alu", achieved=model["flops"] / avg_s / 1e12, unit="TFLOP/s",
-                         frac=model["flops"] / avg_s / 1e12 / FP64_PEAK_TFLOPS)
-            else:
-                e.update(bound="hbm", achieved=model["bytes"] / avg_s / 1e9, unit="GB/s",
-                         frac=model["bytes"] / avg_s / 1e9 / peaks["hbm_gbs"],
-                         note="working set L2-resident")
-        phases[name] = e
+        phases[name] = {"items": cnt, "avg_item_us": ms / cnt * 1e3, "item_ms": ms,
+                        "share_of_busy_item_time": (ms / tot_phase) if "idle" not in name
+                        else None}
     if dom:
         name, (cnt, ms) = dom
         avg_s = ms / cnt / 1e3

@@ -89,7 +89,7 @@ typedef struct {
                            16..512 in 3D */
   double box_len;       /* L > 0; h = L / n */
   double origin[3];     /* lower box corner; nodes at origin + j h */
-  int64_t m;            /* number of boundary points, >= 1 */
+  int64_t m;            /* number of boundary points, 1..16776960 */
   const double* x;      /* point coordinates X_i, length m each; z only for */
   const double* y;      /* dim == 3 (may be NULL in 2D)                      */
   const double* z;

@@ -156,6 +156,9 @@ cudaError_t workspace_pool(cudaMemPool_t* out) {
 }  // namespace
 
 constexpr int kHistCapHost = 256;  // residual history entries (kHistCap)
+// the solver's work items per phase are counted in 16 bits: at most 65535
+// vector chunks of kSolverThreads points
+constexpr int64_t kMaxPoints = 65535LL * kSolverThreads;
 
 struct ibdl_geometry_s {
   GridDesc grid;
@@ -613,7 +616,8 @@ ibdl_status ibdl_create_geometry(const ibdl_geometry_desc* d, void* stream, ibdl
   if (dim != 2 && dim != 3) return fail(IBDL_ERR_INVALID_ARG, "dim must be 2 or 3");
   if (n < 16 || (n & (n - 1)) != 0 || n > (dim == 2 ? 4096 : 512))
     return fail(IBDL_ERR_INVALID_ARG, "n must be a power of two in [16, 4096] (2D) / [16, 512] (3D)");
-  if (d->m < 1 || d->m > (1 << 26)) return fail(IBDL_ERR_INVALID_ARG, "m out of range");
+  if (d->m < 1 || d->m > kMaxPoints)
+    return fail(IBDL_ERR_INVALID_ARG, "m out of range (1 .. 16776960)");
   if (!(d->box_len > 0) || !isfinite(d->box_len))
     return fail(IBDL_ERR_INVALID_ARG, "box_len must be positive and finite");
   if (!(d->kappa > 0) || !isfinite(d->kappa))
@@ -786,7 +790,7 @@ ibdl_status ibdl_create_geometry(const ibdl_geometry_desc* d, void* stream, ibdl
   if ((s = g->alloc(&g->d_hist, (size_t)kHistCap))) return cleanup(s);
   if ((s = g->alloc(&g->d_inst, (size_t)1))) return cleanup(s);
   if ((s = g->alloc(&g->d_state, (size_t)1))) return cleanup(s);
-  if ((s = g->alloc(&g->d_bar, (size_t)8))) return cleanup(s);
+  if ((s = g->alloc(&g->d_bar, (size_t)(4 + kSchedWords)))) return cleanup(s);
 
   g->solver_smem = solver_smem_bytes(gd, 1);
   {
@@ -1160,7 +1164,7 @@ ibdl_status ibdl_batch_create(int32_t capacity, ibdl_batch* out) {
   b->cap = capacity;
   cudaError_t e = cudaMalloc((void**)&b->d_inst, sizeof(SolveInst) * capacity);
   if (!e) e = cudaMalloc((void**)&b->d_state, sizeof(SolveState) * capacity);
-  if (!e) e = cudaMalloc((void**)&b->d_bar, (4 + 4 * (size_t)capacity) * sizeof(unsigned));
+  if (!e) e = cudaMalloc((void**)&b->d_bar, (4 + kSchedWords * (size_t)capacity) * sizeof(unsigned));
   if (!e) e = cudaMallocHost((void**)&b->h_inst, sizeof(SolveInst) * capacity);
   if (!e) e = cudaMallocHost((void**)&b->h_state, sizeof(SolveState) * capacity);
   if (e) {
@@ -1264,7 +1268,7 @@ int32_t ibdl_profile_read(ibdl_kernel_stat* out, int32_t max_out, int32_t reset)
         "phase:rows_fwd_f64", "phase:y_fwd_f64", "phase:solve_f64", "phase:y_inv_f64",
         "phase:rows_inv_f64", "phase:rows_fwd_f32", "phase:y_fwd_f32", "phase:solve_f32",
         "phase:y_inv_f32", "phase:rows_inv_f32", "phase:vector_D_to_G", "phase:unused11",
-        "phase:unused12", "phase:unused13", "phase:round"};
+        "phase:unused12", "phase:unused13", "phase:idle_blocks"};
     unsigned long long h[2 * kPhaseSlots];
     if (cudaMemcpy(h, g_phase_buf, sizeof(h), cudaMemcpyDeviceToHost) == cudaSuccess) {
       for (int id = 0; id < 15; ++id) {
@@ -1557,7 +1561,7 @@ ibdl_status ibdl_server_create(const ibdl_server_config* cfg_in, ibdl_server* ou
   ibdl_server_s* s = new ibdl_server_s();
   s->cfg = cfg;
   s->cap = cfg.max_active;
-  const size_t nb = 4 + 4 * (size_t)s->cap;
+  const size_t nb = 4 + kSchedWords * (size_t)s->cap;
   e = cudaStreamCreateWithFlags(&s->solve_st, cudaStreamNonBlocking);
   if (!e) e = cudaStreamCreateWithFlags(&s->setup_st, cudaStreamNonBlocking);
   if (!e) e = cudaMalloc((void**)&s->d_inst, sizeof(SolveInst) * s->cap);
@@ -1601,7 +1605,8 @@ ibdl_status ibdl_server_submit(ibdl_server s, const ibdl_geometry_desc* d, const
   if (d->n < 16 || (d->n & (d->n - 1)) != 0 || d->n > (d->dim == 2 ? 4096 : 512))
     return fail(IBDL_ERR_INVALID_ARG,
                 "n must be a power of two in [16, 4096] (2D) / [16, 512] (3D)");
-  if (d->m < 1 || d->m > (1 << 26)) return fail(IBDL_ERR_INVALID_ARG, "m out of range");
+  if (d->m < 1 || d->m > kMaxPoints)
+    return fail(IBDL_ERR_INVALID_ARG, "m out of range (1 .. 16776960)");
   if (!d->x || !d->y || !d->nx || !d->ny || !d->w || (d->dim == 3 && (!d->z || !d->nz)))
     return fail(IBDL_ERR_INVALID_ARG, "NULL point, normal or weight array");
   SrvReq* r = new SrvReq();

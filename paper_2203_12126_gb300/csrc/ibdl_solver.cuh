@@ -9,6 +9,9 @@ constexpr int kSolverThreads = 256;  // threads per block; also the vector chunk
 constexpr int kMaxBatch = 512;       // instances per persistent launch
 constexpr int kSingleMax = 4096;     // points up to which one block does the vector work
 constexpr int kSingleMinBatch = 8;   // ... when at least this many instances share a launch
+// Scheduler words per instance in the solver's barrier buffer (4 + this many
+// per instance, 32-bit words): claim counter, done counter, phase descriptor.
+constexpr int kSchedWords = 12;
 
 enum SolveAction {
   ACT_DONE = 0,

@@ -2,8 +2,8 @@
 // (Sec. 5.3: unpreconditioned GMRES on the second-kind boundary system) for
 // one or many instances, with no host round trip between iterations.
 //
-// Every block loops over "rounds".  In a round each active instance does one
-// action of its state machine, split into phases separated by grid barriers:
+// Each instance runs rounds; in a round it does one action of its state
+// machine as a sequence of phases, each a set of independent work items:
 //
 //   A   rows_fwd   spread-divergence of the matvec input + x FFT   (matvec)
 //   B   pencils    y (and z) FFT passes with the symbol            (matvec)
@@ -13,15 +13,18 @@
 //   F   reduce, w -= V h (CGS pass 2), norm partial / x update
 //   G   normalise w; Givens rotation; control (next action)
 //
-// Actions: RESID_ZERO (r = b at x = 0), MV_RESIDUAL (r = b - A64 x),
-// MV_ARNOLDI (Arnoldi step j with the float64 or float32 operator),
-// FINISH (back substitution, x += V y), DONE.  The float64 mode restarts with
-// the true residual after every cycle; the float32-refined mode runs one
-// float32 GMRES cycle per refinement step between float64 residuals.
+// (small instances in large batches do D..G as one item on one block).
+// Actions: RHS (Neumann right-hand side), RESID_ZERO (r = b at x = 0),
+// MV_RESIDUAL (r = b - A64 x), MV_ARNOLDI (Arnoldi step j with the float64
+// or float32 operator), FINISH (back substitution, x += V y), DONE.  The
+// float64 mode restarts with the true residual after every cycle; the
+// float32-refined mode runs one float32 GMRES cycle per refinement step
+// between float64 residuals.
 //
-// Work items of all instances are concatenated per phase and dealt to blocks
-// round-robin.  The grid barrier spins a bounded number of times; on timeout
-// it sets an error flag and every block leaves the kernel.
+// Blocks take items of any instance dynamically (see "dynamic scheduling"),
+// so instances of different sizes and precisions overlap instead of moving
+// in lock step.  Every wait is bounded; on timeout an error flag is raised
+// and every block leaves the kernel.
 #include <math.h>
 
 #include "ibdl_device.cuh"
@@ -233,15 +236,6 @@ __device__ void mv_item(const SolveInst& I, const RoundView& v, int phase, int i
   }
 }
 
-__device__ int phase_items(const SolveInst& I, const RoundView& v, int phase) {
-  if (phase < 5) {
-    if (!is_mv(v.action)) return 0;
-    return v.prec ? mv_items<float>(I, phase) : mv_items<double>(I, phase);
-  }
-  if (v.action == ACT_DONE) return 0;
-  if (I.single) return 0;  // handled by vec_single on its own block
-  return I.nchunk;
-}
 
 // ---- vector phases ------------------------------------------------------------
 
@@ -525,13 +519,11 @@ __device__ void phase_G(const SolveInst& I, SolveState* S, const RoundView& v, i
 }
 
 // ---- single-block vector step (instances with few points) ------------------
-// For m <= kSingleMax the whole post-matvec work of an action (interpolation,
-// both CGS passes, norm, Givens, control) runs in one block with block-level
-// synchronisation: one grid barrier per round instead of four.  The block is
-// fixed per instance (instance k -> block k mod gridDim), so every Krylov
-// vector, x and r of the instance is produced and consumed on the same SM
-// and is read back with ordinary (L1-coherent) loads; only the grid, written
-// by other blocks, is read around L1.
+// For m <= kSingleMax in batches of >= kSingleMinBatch the whole post-matvec
+// work of an action (interpolation, both CGS passes, norm, Givens, control)
+// is one work item run by one block with block-level synchronisation.  The
+// block that takes it may differ from round to round, so everything another
+// round wrote is read around L1 (ld.global.cg).
 
 __device__ double block_sum_all(double v, BlockRed& R) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -587,7 +579,7 @@ __device__ void vec_single(const SolveInst& I, SolveState* S, const RoundView& v
 #pragma unroll
     for (int k = 0; k < kSingleK; ++k) {
       const int i = tid + k * nt;
-      xk[k] = i < m ? I.x[i] : 0.0;
+      xk[k] = i < m ? __ldcg(I.x + i) : 0.0;
     }
     for (int c = 0; c < v.kdim; ++c) {
       const double yc = R.h[c];
@@ -595,7 +587,7 @@ __device__ void vec_single(const SolveInst& I, SolveState* S, const RoundView& v
 #pragma unroll
       for (int k = 0; k < kSingleK; ++k) {
         const int i = tid + k * nt;
-        if (i < m) xk[k] += yc * vc[i];
+        if (i < m) xk[k] += yc * __ldcg(vc + i);
       }
     }
 #pragma unroll
@@ -619,7 +611,7 @@ __device__ void vec_single(const SolveInst& I, SolveState* S, const RoundView& v
       wk[k] = 0.0;
       if (i < m) {
         const double acc = d3 ? interp_any<3>(I, v.prec, i) : interp_any<2>(I, v.prec, i);
-        wk[k] = acc + jump * vin[i];
+        wk[k] = acc + jump * __ldcg(vin + i);
       }
     }
     for (int pass = 0; pass < 2; ++pass) {
@@ -629,7 +621,7 @@ __device__ void vec_single(const SolveInst& I, SolveState* S, const RoundView& v
 #pragma unroll
         for (int k = 0; k < kSingleK; ++k) {
           const int i = tid + k * nt;
-          if (i < m) sacc += wk[k] * vc[i];
+          if (i < m) sacc += wk[k] * __ldcg(vc + i);
         }
         sacc = warp_sum(sacc);
         if (lane == 0) R.red[c][wid] = sacc;
@@ -648,7 +640,7 @@ __device__ void vec_single(const SolveInst& I, SolveState* S, const RoundView& v
 #pragma unroll
         for (int k = 0; k < kSingleK; ++k) {
           const int i = tid + k * nt;
-          if (i < m) wk[k] -= hc * vc[i];
+          if (i < m) wk[k] -= hc * __ldcg(vc + i);
         }
       }
       __syncthreads();
@@ -686,7 +678,7 @@ __device__ void vec_single(const SolveInst& I, SolveState* S, const RoundView& v
       if (v.action == ACT_MV_RESIDUAL) {
         const double acc = d3 ? interp_point<double, 3>(I.g, I.p, I.w64.grid, i)
                               : interp_point<double, 2>(I.g, I.p, I.w64.grid, i);
-        r = bi - (acc + jump * I.x[i]);
+        r = bi - (acc + jump * __ldcg(I.x + i));
       }
       I.r[i] = r;
       rk[k] = r;
@@ -716,123 +708,299 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Phase timing (optional): block 0, thread 0 adds the wall time between
-// consecutive grid-barrier exits to ptimes[2*id] and counts in ptimes[2*id+1].
-// Ids: 0..4 matvec phases in float64 (rows_fwd, y fwd, solve, y inv,
-// rows_inv), 5..9 the same in float32, 10 the vector phases D..G, 14 round
-// bookkeeping.
-__device__ __forceinline__ void phase_tick(unsigned long long* ptimes, int id,
-                                           unsigned long long& t0) {
-  if (ptimes && blockIdx.x == 0 && threadIdx.x == 0) {
-    const unsigned long long t = global_ns();
-    ptimes[2 * id] += t - t0;
-    ptimes[2 * id + 1] += 1;
-    t0 = t;
+// ---- dynamic scheduling -------------------------------------------------------
+//
+// Each instance walks its own phase sequence; no phase of one instance waits
+// for another instance.  Per instance (scheduler words in `bar`):
+//   claim : 64-bit  (epoch << 32) | next item index, taken with atomicAdd
+//   done  : items finished in the current epoch
+//   desc  : the current phase, its item count and the round's view of the
+//           solver state, written before the epoch is published
+// A block looking for work takes an item of any instance whose current phase
+// has items left; the block that finishes an instance's last item advances
+// that instance to its next phase (or, after the vector phases, to the next
+// round from the state its control step wrote).  Items of one phase are
+// independent, so no block ever waits for another block's item: an idle
+// block only spins (bounded) until new items are published.
+
+struct PhaseDesc {
+  int epoch, phase, nitems, round;
+  int action, prec, j, kdim;
+};
+
+constexpr int kPhaseD = 5, kPhaseE = 6, kPhaseF = 7, kPhaseG = 8, kPhaseSingle = 9;
+
+// claim word: bits 63..48 the phase epoch (mod 2^16), 47..32 the phase's
+// item count, 31..0 the next item index.  A claim is valid exactly when the
+// index it took is below the count it carries, so neither the scan nor the
+// claim needs the descriptor; a valid claim then reads the descriptor, which
+// was written before the claim word was published and cannot change until
+// the claimed item is done.
+__device__ __forceinline__ unsigned long long claim_value(int epoch, int nitems) {
+  return ((unsigned long long)(epoch & 0xffff) << 48) |
+         ((unsigned long long)(nitems & 0xffff) << 32);
+}
+__device__ __forceinline__ bool claim_open(unsigned long long w) {
+  return (unsigned)(w & 0xffffffffu) < (unsigned)((w >> 32) & 0xffffu);
+}
+
+__device__ __forceinline__ unsigned long long* claim_word(unsigned* bar, int k) {
+  return reinterpret_cast<unsigned long long*>(bar + 4 + kSchedWords * k);
+}
+__device__ __forceinline__ unsigned* done_word(unsigned* bar, int k) {
+  return bar + 4 + kSchedWords * k + 2;
+}
+__device__ __forceinline__ PhaseDesc* desc_of(unsigned* bar, int k) {
+  return reinterpret_cast<PhaseDesc*>(bar + 4 + kSchedWords * k + 4);
+}
+
+// Descriptor reads go around L1 in two 16-byte loads.
+__device__ PhaseDesc load_desc(const PhaseDesc* p) {
+  const int4 a = __ldcg(reinterpret_cast<const int4*>(p));
+  const int4 b = __ldcg(reinterpret_cast<const int4*>(p) + 1);
+  PhaseDesc d;
+  d.epoch = a.x;
+  d.phase = a.y;
+  d.nitems = a.z;
+  d.round = a.w;
+  d.action = b.x;
+  d.prec = b.y;
+  d.j = b.z;
+  d.kdim = b.w;
+  return d;
+}
+
+__device__ void store_desc(PhaseDesc* p, const PhaseDesc& d) {
+  int4* q = reinterpret_cast<int4*>(p);
+  __stcg(q, make_int4(d.epoch, d.phase, d.nitems, d.round));
+  __stcg(q + 1, make_int4(d.action, d.prec, d.j, d.kdim));
+}
+
+__device__ int first_phase(const SolveInst& I, int action) {
+  if (is_mv(action)) return 0;
+  return I.single ? kPhaseSingle : kPhaseD;
+}
+
+// -1: the round ends after `phase`
+__device__ int next_phase(const SolveInst& I, int phase) {
+  const bool d3 = I.g.dim == 3;
+  switch (phase) {
+    case 0: return d3 ? 1 : 2;
+    case 1: return 2;
+    case 2: return d3 ? 3 : 4;
+    case 3: return 4;
+    case 4: return I.single ? kPhaseSingle : kPhaseD;
+    case kPhaseD: return kPhaseE;
+    case kPhaseE: return kPhaseF;
+    case kPhaseF: return kPhaseG;
+    default: return -1;
   }
 }
+
+__device__ int items_of(const SolveInst& I, const PhaseDesc& d) {
+  if (d.phase < 5) return d.prec ? mv_items<float>(I, d.phase) : mv_items<double>(I, d.phase);
+  if (d.phase == kPhaseSingle) return 1;
+  return I.nchunk;
+}
+
+// The round view of the state; `active` is false when the instance is done.
+__device__ bool view_from_state(const SolveState* S, PhaseDesc& d) {
+  const volatile SolveState* vs = S;
+  d.action = vs->action;
+  d.prec = vs->prec;
+  d.j = vs->j;
+  d.kdim = vs->kdim;
+  return d.action != ACT_DONE;
+}
+
+// Publishes instance k's next phase (one thread).  `finished` counts
+// instances that are done or have used their rounds for this launch.
+__device__ void advance(const SolveInst& I, const SolveState* S, unsigned* bar, int k,
+                        int max_rounds) {
+  PhaseDesc d = load_desc(desc_of(bar, k));
+  int np = next_phase(I, d.phase);
+  if (np < 0) {
+    d.round++;
+    const bool active = view_from_state(S, d);
+    if (!active || (max_rounds > 0 && d.round >= max_rounds)) {
+      d.nitems = 0;
+      d.epoch++;
+      store_desc(desc_of(bar, k), d);
+      __threadfence();
+      atomicExch(claim_word(bar, k), claim_value(d.epoch, 0));
+      atomicAdd(bar + 3, 1u);
+      return;
+    }
+    np = first_phase(I, d.action);
+  }
+  d.phase = np;
+  d.nitems = items_of(I, d);
+  d.epoch++;
+  store_desc(desc_of(bar, k), d);
+  *(volatile unsigned*)done_word(bar, k) = 0u;
+  __threadfence();
+  atomicExch(claim_word(bar, k), claim_value(d.epoch, d.nitems));
+}
+
+__device__ void run_item(const SolveInst& I, SolveState* S, const PhaseDesc& d, int item,
+                         unsigned char* smem, BlockRed& R) {
+  RoundView v;
+  v.action = d.action;
+  v.prec = d.prec;
+  v.j = d.j;
+  v.kdim = d.kdim;
+  if (d.phase < 5) {
+    if (v.prec)
+      mv_item<float>(I, v, d.phase, item, smem);
+    else
+      mv_item<double>(I, v, d.phase, item, smem);
+  } else if (d.phase == kPhaseD) {
+    if (I.g.dim == 2)
+      phase_D<2>(I, v, item, R);
+    else
+      phase_D<3>(I, v, item, R);
+  } else if (d.phase == kPhaseE) {
+    phase_E(I, v, item, R);
+  } else if (d.phase == kPhaseF) {
+    phase_F(I, v, item, R);
+  } else if (d.phase == kPhaseG) {
+    phase_G(I, S, v, item, R);
+  } else {
+    vec_single(I, S, v, R);
+  }
+}
+
+// Item timing (optional): the executing block's thread 0 adds each item's
+// duration to ptimes[2*id] and counts it in ptimes[2*id+1].  Ids: 0..4
+// matvec phases in float64 (rows_fwd, y fwd, solve, y inv, rows_inv), 5..9
+// the same in float32, 10 the vector phases D..G (and the one-block step),
+// 14 idle block time spent looking for work.
+__device__ __forceinline__ void add_time(unsigned long long* ptimes, int id,
+                                         unsigned long long dt) {
+  atomicAdd(ptimes + 2 * id, dt);
+  atomicAdd(ptimes + 2 * id + 1, 1ull);
+}
+
+struct ItemSlot {
+  int k, item, have;
+  PhaseDesc d;
+};
 
 __global__ void __launch_bounds__(kSolverThreads, 2)
     k_persistent_solve(const SolveInst* __restrict__ insts, SolveState* states, int ninst,
                        unsigned* bar, unsigned long long* ptimes, int max_rounds) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ RoundView rv[kMaxBatch];
   __shared__ BlockRed R;
-  __shared__ int flags[4];
+  __shared__ ItemSlot slot;
   const unsigned nblocks = gridDim.x;
-  const int G = gridDim.x, bid = blockIdx.x;
-  unsigned long long t0 = 0;
-  if (ptimes && bid == 0 && threadIdx.x == 0) t0 = global_ns();
+  const int bid = blockIdx.x;
 
-  for (int round = 0;; ++round) {
-    // a bounded slice stops between rounds; the states stay in global memory
-    // and the next launch resumes them
-    if (max_rounds > 0 && round >= max_rounds) break;
-    if (threadIdx.x == 0) {
-      flags[0] = 0;
-      flags[1] = 0;
-      flags[2] = 0;
-      flags[3] = 0;
-    }
-    __syncthreads();
+  // block 0 publishes every instance's first phase
+  if (bid == 0) {
     for (int k = threadIdx.x; k < ninst; k += blockDim.x) {
-      volatile SolveState* s = states + k;
-      RoundView v;
-      v.action = s->action;
-      v.prec = s->prec;
-      v.j = s->j;
-      v.kdim = s->kdim;
-      rv[k] = v;
-      if (v.action != ACT_DONE) {
-        atomicOr(&flags[0], 1);
-        if (!insts[k].single) atomicOr(&flags[3], 1);
+      PhaseDesc d;
+      d.round = 0;
+      d.epoch = 1;
+      if (view_from_state(states + k, d)) {
+        d.phase = first_phase(insts[k], d.action);
+        d.nitems = items_of(insts[k], d);
+      } else {
+        d.phase = 0;
+        d.nitems = 0;
+        atomicAdd(bar + 3, 1u);
       }
-      if (is_mv(v.action)) {
-        atomicOr(&flags[1], 1);
-        if (insts[k].g.dim == 3) atomicOr(&flags[2], 1);
+      store_desc(desc_of(bar, k), d);
+      *(volatile unsigned*)done_word(bar, k) = 0u;
+      __threadfence();
+      atomicExch(claim_word(bar, k), claim_value(d.epoch, d.nitems));
+    }
+  }
+  if (!grid_barrier(bar, nblocks)) return;
+
+  unsigned spins = 0;
+  unsigned long long idle0 = 0;
+  int rot = bid % (ninst > 0 ? ninst : 1);
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    // warp 0 looks for an item: its lanes probe 32 instances at a time (the
+    // descriptor's epoch and item count and the claim word, read around L1)
+    if (threadIdx.x < 32) {
+      int have = 0;
+      if (lane == 0 && *(volatile unsigned*)(bar + 2) != 0u) have = -1;  // error: leave
+      have = __shfl_sync(0xffffffffu, have, 0);
+      for (int base = 0; base < ninst && have == 0; base += 32) {
+        const int t = base + lane;
+        const int k = (rot + t) % ninst;
+        const bool avail = t < ninst && claim_open(__ldcg(claim_word(bar, k)));
+        unsigned cand = __ballot_sync(0xffffffffu, avail);
+        while (cand && have == 0) {
+          const int l = __ffs(cand) - 1;
+          cand &= cand - 1;
+          const int kk = __shfl_sync(0xffffffffu, k, l);
+          int got = 0;
+          if (lane == 0) {
+            const unsigned long long w = atomicAdd(claim_word(bar, kk), 1ull);
+            if (claim_open(w)) {
+              __threadfence();
+              slot.k = kk;
+              slot.item = (int)(w & 0xffffffffu);
+              slot.d = load_desc(desc_of(bar, kk));
+              got = 1;
+            }
+          }
+          got = __shfl_sync(0xffffffffu, got, 0);
+          if (got) {
+            have = 1;
+            rot = kk;  // stay on this instance while it has items
+          }
+        }
       }
+      if (lane == 0) {
+        if (have == 0) {
+          if (*(volatile unsigned*)(bar + 3) >= (unsigned)ninst) {
+            have = -1;  // every instance is done (or paused)
+          } else {
+            if (ptimes && spins == 0) idle0 = global_ns();
+            if (++spins > kSpinLimit) {
+              atomicExch(bar + 2, 1u);
+              have = -1;
+            } else {
+              __nanosleep(20);
+            }
+          }
+        } else if (have > 0 && spins) {
+          if (ptimes) add_time(ptimes, 14, global_ns() - idle0);
+          spins = 0;
+        }
+        slot.have = have;
+      }
+      rot = __shfl_sync(0xffffffffu, rot, 0);
     }
     __syncthreads();
-    if (!flags[0]) break;
-    const bool any_mv = flags[1] != 0, any3d = flags[2] != 0, any_multi = flags[3] != 0;
-    phase_tick(ptimes, 14, t0);
-    const int prec0 = rv[0].prec;
-
-    // matvec phases
-    for (int phase = 0; phase < 5 && any_mv; ++phase) {
-      if ((phase == 1 || phase == 3) && !any3d) continue;
-      int base = 0;
-      for (int k = 0; k < ninst; ++k) {
-        const RoundView v = rv[k];
-        const int cnt = phase_items(insts[k], v, phase);
-        if (cnt == 0) continue;
-        const int first = ((bid - base) % G + G) % G;
-        for (int it = first; it < cnt; it += G) {
-          if (v.prec)
-            mv_item<float>(insts[k], v, phase, it, smem);
-          else
-            mv_item<double>(insts[k], v, phase, it, smem);
-        }
-        base += cnt;
-      }
-      if (!grid_barrier(bar, nblocks)) return;
-      phase_tick(ptimes, phase + 5 * prec0, t0);
+    const int have = slot.have;
+    if (have < 0) break;
+    if (have == 0) {
+      __syncthreads();
+      continue;
     }
-    // vector phases D..G.  Single-block instances finish in one block; the
-    // others run D, E, F, G on the blocks that hold their chunks, separated
-    // by a barrier among those blocks only, and one grid barrier closes the
-    // round.
-    for (int k = bid; k < ninst; k += G) {
-      const RoundView v = rv[k];
-      if (insts[k].single && v.action != ACT_DONE) vec_single(insts[k], states + k, v, R);
-    }
-    if (any_multi) {
-      int base = 0;
-      for (int k = 0; k < ninst; ++k) {
-        const RoundView v = rv[k];
-        const SolveInst& I = insts[k];
-        const int cnt = phase_items(I, v, 5);
-        if (cnt == 0) continue;
-        const int first = ((bid - base) % G + G) % G;
-        base += cnt;
-        if (first >= cnt) continue;
-        const unsigned parties = cnt < G ? (unsigned)cnt : (unsigned)G;
-        unsigned* ib = bar + 4 + 4 * k;
-        for (int it = first; it < cnt; it += G) {
-          if (I.g.dim == 2)
-            phase_D<2>(I, v, it, R);
-          else
-            phase_D<3>(I, v, it, R);
-        }
-        if (!counted_barrier(ib, parties, bar + 2)) return;
-        for (int it = first; it < cnt; it += G) phase_E(I, v, it, R);
-        if (!counted_barrier(ib, parties, bar + 2)) return;
-        for (int it = first; it < cnt; it += G) phase_F(I, v, it, R);
-        if (!counted_barrier(ib, parties, bar + 2)) return;
-        for (int it = first; it < cnt; it += G) phase_G(I, states + k, v, it, R);
+    const int k = slot.k, item = slot.item;
+    const PhaseDesc d = slot.d;
+    __syncthreads();  // slot is rewritten by thread 0 in the next iteration
+    unsigned long long ta = 0;
+    if (ptimes && threadIdx.x == 0) ta = global_ns();
+    run_item(insts[k], states + k, d, item, smem, R);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (ptimes) add_time(ptimes, d.phase < 5 ? d.phase + 5 * d.prec : 10, global_ns() - ta);
+      __threadfence();
+      const unsigned prior = atomicAdd(done_word(bar, k), 1u);
+      if ((int)prior == d.nitems - 1) {
+        // every item of the phase is done: see their writes (the state of
+        // the control step included) before choosing the next phase
+        __threadfence();
+        advance(insts[k], states + k, bar, k, max_rounds);
       }
     }
-    if (!grid_barrier(bar, nblocks)) return;
-    phase_tick(ptimes, 10, t0);
   }
 }
 
@@ -879,7 +1047,8 @@ cudaError_t launch_persistent_solve(const SolveInst* d_insts, SolveState* d_stat
   int sms = sm_count - (reserve_sms > 0 ? reserve_sms : 0);
   if (sms < 1) sms = 1;
   const int blocks = per_sm * sms;
-  if ((e = cudaMemsetAsync(d_bar, 0, (4 + 4 * (size_t)ninst) * sizeof(unsigned), st)))
+  if ((e = cudaMemsetAsync(d_bar, 0, (4 + kSchedWords * (size_t)ninst) * sizeof(unsigned),
+                           st)))
     return e;
   void* args[] = {(void*)&d_insts, (void*)&d_states, (void*)&ninst, (void*)&d_bar,
                   (void*)&ptimes, (void*)&max_rounds};

@@ -204,3 +204,34 @@ print(json.dumps(out))
     ref = O.solve(g, configs.NEUMANN, b, tol=1e-13).x
     for prec, (q, iters) in zip((0, 1), forced):
         assert rel(q, ref) <= (1e-8 if prec else 1e-9)
+
+
+def test_scheduler_stress_many_tiny_instances():
+    """128 tiny instances (phases of one to a few items, so the dynamic
+    scheduler publishes new phases constantly and idle blocks race for
+    them), solved five times: every run converges and equals the solo
+    solves."""
+    rng = np.random.default_rng(77)
+    specs = []
+    for k in range(128):
+        n = 16 if k % 2 else 32
+        g = geometry.circle(n, 0.25 + 0.05 * (k % 3), m=12 + k % 17,
+                            kappa=float(10.0 ** rng.uniform(-2, -1)))
+        specs.append((g, configs.DIRICHLET if k % 3 else configs.NEUMANN, k % 2))
+    geoms = [pkg.Geometry.from_workload(g, bc=bc, precision=prec) for g, bc, prec in specs]
+    bs = [gpu(rng.standard_normal(g.m)) for g, _, _ in specs]
+    solo = []
+    for G, b in zip(geoms, bs):
+        q = torch.empty_like(b)
+        G.solve(b, q, tol=1e-10)
+        solo.append(q.cpu().numpy())
+    batch = ibdl.Batch(len(specs))
+    for _ in range(5):
+        qs = [torch.full_like(b, float("nan")) for b in bs]
+        infos = batch.solve(geoms, bs, qs, tol=1e-10)
+        for k, info in enumerate(infos):
+            assert info["status"] == 0 and info["rel_residual"] <= 1e-10, (k, info)
+            assert rel(qs[k].cpu(), solo[k]) <= 1e-8, k
+    batch.close()
+    for G in geoms:
+        G.close()
