@@ -332,6 +332,10 @@ def load_peaks():
 # bound by it, not by HBM.
 FP64_PEAK_TFLOPS = 1.25
 
+# DRAM bytes (read + write) of one batched-pair launch of the persistent
+# solver, from one ncu capture of that launch (profiles/c2_persistent_solve.md)
+PAIR_LAUNCH_DRAM_BYTES = (49.879296 + 265.82784) * 1e6
+
 
 # ---------------------------------------------------------------------------
 # reference arm: the CPU oracle as it stands
@@ -559,7 +563,10 @@ def main():
             ach = fl / avg_s / 1e12
             roofline = {"kernel": name, "bound": "alu", "achieved": ach,
                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                        "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                        "frac": ach / FP64_PEAK_TFLOPS,
+                        "traffic": PAIR_LAUNCH_DRAM_BYTES if args.mode == "batched" else None,
+                        "traffic_src": "ncu dram__bytes_read.sum + dram__bytes_write.sum of "
+                                       "one pair launch (profiles/c2_persistent_solve.md)",
                         "peak_src": "nominal GB300 FP64 rate (measured FMA probe: 1.19)",
                         "algorithmic_flops_per_launch": fl,
                         "float64_matvecs_per_launch": mv64,
