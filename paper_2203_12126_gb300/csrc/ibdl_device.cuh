@@ -558,10 +558,10 @@ struct PencilLayout {
 };
 
 // c: pencils per work item (a power of two <= 16): at most pg when the
-// pencils are strided, shared memory (pencil buffers + tables) within 90 KB
-// so that two 512-thread blocks of the persistent solver fit on an SM, and
-// small enough that a pass over contiguous pencils has >= 256 items when it
-// can.
+// pencils are strided, shared memory (pencil buffers + tables) within 100 KB
+// so that two blocks of the persistent solver fit on an SM (with its ~7 KB
+// of static shared memory), and small enough that a pass over contiguous
+// pencils has >= 256 items when it can.
 template <typename T>
 __host__ __device__ inline size_t pencil_smem_for(int n, int c) {
   return (2 * (size_t)c * pen_stride(n) + fft_tw_count(n)) * sizeof(cx_t<T>) +
@@ -579,7 +579,7 @@ __host__ __device__ inline PencilLayout pencil_layout(int n, int64_t gstride, in
   L.npencils = npencils;
   int c = 16;
   if (estride != 1 && c > pg) c = pg;
-  while (c > 1 && pencil_smem_for<T>(n, c) > 90 * 1024) c >>= 1;
+  while (c > 1 && pencil_smem_for<T>(n, c) > 100 * 1024) c >>= 1;
   while (c > 1 && npencils / c < 256 && estride == 1) c >>= 1;
   if (estride != 1 && c < 2) c = 2;  // strided items move pencils in pairs
   L.c = c;
