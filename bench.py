@@ -642,7 +642,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": n, "m": m, "kappa": 1e-3,
                        "tol": args.tol, "precision": args.precision,
-                       "l2": "flushed between solves (512 MiB write, outside the events)",
+                       "l2": "flushed between steps (512 MiB write, outside the events)",
                        "engine": "persistent" if args.engine == 0 else "host-loop",
                        "mode": args.mode,
                        "parallelism": f"replicas x{world}"},
