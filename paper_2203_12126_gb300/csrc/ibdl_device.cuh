@@ -807,8 +807,16 @@ template <> __device__ __forceinline__ const float* wtab<float>(const PointData&
   return p.W32[c];
 }
 
+// Grid load of the interpolation: around L1 (ld.global.cg) where another
+// block of the same launch wrote the grid, through the read-only cache when
+// an earlier launch did (neighbouring points then share cached lines).
+template <typename T, bool CACHED>
+__device__ __forceinline__ T grid_load(const T* p) {
+  return CACHED ? __ldg(p) : __ldcg(p);
+}
+
 // sum over the 4^d taps of grid * prod_c W[c][t]  (S* u at X_i, Sec. 5.2)
-template <typename T, int D>
+template <typename T, int D, bool CACHED = false>
 __device__ __forceinline__ T interp_point(const GridDesc& g, const PointData& p, const T* grid,
                                           int i) {
   const int n = g.n, mask = n - 1, m = p.m;
@@ -831,7 +839,7 @@ __device__ __forceinline__ T interp_point(const GridDesc& g, const PointData& p,
       const T* row = grid + (size_t)((by + ty) & mask) * n;
       T r = 0;
 #pragma unroll
-      for (int tx = 0; tx < 4; ++tx) r += __ldcg(row + col[tx]) * wx[tx];
+      for (int tx = 0; tx < 4; ++tx) r += grid_load<T, CACHED>(row + col[tx]) * wx[tx];
       acc += r * wy[ty];
     }
   } else {
@@ -846,7 +854,7 @@ __device__ __forceinline__ T interp_point(const GridDesc& g, const PointData& p,
         const T* row = plane + (size_t)((by + ty) & mask) * n;
         T r = 0;
 #pragma unroll
-        for (int tx = 0; tx < 4; ++tx) r += __ldcg(row + col[tx]) * wx[tx];
+        for (int tx = 0; tx < 4; ++tx) r += grid_load<T, CACHED>(row + col[tx]) * wx[tx];
         pz += r * wy[ty];
       }
       acc += pz * wz;

@@ -51,12 +51,22 @@ __global__ void __launch_bounds__(512) k_rows_inv(GridDesc g, Bins b, const cx_t
 
 // ---- launchers ----------------------------------------------------------------
 
-static int rows_threads(int n, int npen) {
-  int t = npen * n / 8;
-  if (t < 64) t = 64;
-  if (t > 512) t = 512;
-  return t;
+// Threads per block.  Pencil items: one per butterfly of the FFT pass with
+// the most butterflies (n over the smallest radix of the plan, per pencil)
+// -- more would idle in the FFT passes and thin the per-thread work over
+// which an item's fixed cost is spread.  Row tiles take n/8 per pencil:
+// their spread stage wants the extra threads.
+static int clamp_threads(int t) { return t < 64 ? 64 : (t > 512 ? 512 : t); }
+
+static int pencil_threads(int n, int c) {
+  const int lg = ilog2(n);
+  int min_lr = 4;
+  for (int s = 0; s < plan_npass(lg); ++s)
+    if (plan_lr(lg, s) < min_lr) min_lr = plan_lr(lg, s);
+  return clamp_threads(c * (n >> min_lr));
 }
+
+static int rows_threads(int n, int npen) { return clamp_threads(npen * n / 8); }
 
 template <typename T>
 cudaError_t launch_rows_fwd(const GridDesc& g, const PointData& p, const Bins& b,
@@ -94,9 +104,7 @@ static cudaError_t run_pencils(const GridDesc& g, const PencilLayout& L, Spectra
                                cudaStream_t st, const int* zskip = nullptr, int ngroups = 0,
                                const unsigned char* zempty = nullptr) {
   const int blocks = (L.npencils + L.c - 1) / L.c;
-  int thr = L.c * g.n / 8;
-  if (thr < 64) thr = 64;
-  if (thr > 512) thr = 512;
+  const int thr = pencil_threads(g.n, L.c);
   const size_t smem = pencil_smem_bytes<T>(L, g.n);
   const double nd = g.dim == 3 ? (double)g.n * g.n * g.n : (double)g.n * g.n;
   const T cfac = (T)(4.0 * g.kappa / (g.h * g.h));

@@ -171,7 +171,8 @@ __global__ void __launch_bounds__(128) k_interp(GridDesc g, PointData p, const T
                                                 const double* jvec, double jump, double* y) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= p.m) return;
-  double out = (double)interp_point<T, D>(g, p, grid, i);
+  // the grid comes from an earlier launch: cached loads are coherent here
+  double out = (double)interp_point<T, D, true>(g, p, grid, i);
   if (jvec) out += jump * jvec[i];
   y[i] = out;
 }
