@@ -323,6 +323,22 @@ __device__ __forceinline__ void copy_to_shared(V* dst, const V* __restrict__ src
   }
 }
 
+// 1/x for the Helmholtz symbol (x >= 1).  float: the correctly rounded
+// reciprocal.  double: Newton-Raphson for 1/x, r <- r + r (1 - x r), from a
+// float first guess; each step doubles the number of correct bits (24 ->
+// 48 -> beyond 53), at four FMAs instead of a full double division.
+template <typename T> __device__ __forceinline__ T recip_symbol(T x);
+template <> __device__ __forceinline__ float recip_symbol<float>(float x) {
+  return __frcp_rn(x);
+}
+template <> __device__ __forceinline__ double recip_symbol<double>(double x) {
+  double r = (double)__frcp_rn((float)x);
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+
 // Two consecutive complex values as one 16-byte access (float) or two
 // (double).  Even element indices keep the float pair 16-byte aligned.
 template <typename T> struct Pair;
@@ -694,7 +710,7 @@ __device__ __forceinline__ void phase_pencils(const GridDesc& g, const PencilLay
     for (int e = tid; e < (npl << lg); e += nt) {
       const int pl = e >> lg, t = e & (n - 1);
       const T ssum = g.dim == 3 ? sfix + s2s[q0 + pl] + s2s[t] : s2s[p0 + pl] + s2s[t];
-      const T f = scale0 / ((T)1 + cfac * ssum);
+      const T f = scale0 * recip_symbol<T>((T)1 + cfac * ssum);
       C& v = res[pl * PS + padi(t)];
       v.x *= f;
       v.y *= f;
