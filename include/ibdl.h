@@ -191,9 +191,10 @@ ibdl_status ibdl_evaluate(ibdl_geometry g, const double* q, const double* vb,
  * into q_out[k] for k < count, all in ONE persistent cooperative kernel
  * launch: every instance runs the same state machine as ibdl_solve (float64
  * GMRES, or float32 GMRES cycles inside float64 residual refinement, by each
- * geometry's precision), and each phase deals the work items of all active
- * instances (grid tiles, pencils, vector chunks) to the resident blocks, so
- * instances of different n, m, kappa, bc and precision advance together and
+ * geometry's precision), and the resident blocks take work items (grid
+ * tiles, pencils, vector chunks) of whichever instance has some, each
+ * instance moving through its own phases: instances of different n, m,
+ * kappa, bc and precision overlap instead of waiting for one another, and
  * finished ones drop out.  A geometry may appear once per call (its
  * workspaces hold that instance's state).  Synchronises `stream`.
  * statuses/infos (arrays of `count`, may be NULL) receive per-instance
@@ -213,8 +214,8 @@ ibdl_status ibdl_solve_batched(ibdl_batch b, int32_t count, const ibdl_geometry*
  * Requests (a geometry description with its boundary data, g = 0) are
  * submitted at any time; ibdl_server_step then
  *   1. launches one slice of the persistent solver (ibdl_solve_batched's
- *      kernel, stopped after `rounds_per_step` GMRES rounds) over every
- *      active slot -- requests of different dim, n, m, kappa, bc and
+ *      kernel; each request runs at most `rounds_per_step` GMRES rounds in
+ *      it) over every active slot -- requests of different dim, n, m, kappa, bc and
  *      precision advance together and keep their grids, spectra, FFT
  *      tables and Krylov bases resident in device memory between slices;
  *   2. while that slice runs, admits queued requests in arrival order as long
@@ -238,7 +239,8 @@ typedef struct {
   int64_t memory_budget;    /* bytes of device memory admitted requests may
                                hold; 0 = 80% of the free memory at creation */
   int32_t max_active;       /* solver slots, 1..512; default 64 */
-  int32_t rounds_per_step;  /* solver rounds per slice, >= 1; default 8 */
+  int32_t rounds_per_step;  /* solver rounds per request per slice, >= 1;
+                               default 8 */
   int32_t reserve_sms;      /* SMs left free for request set-up while a slice
                                runs, 0..(SM count - 1); default 8 */
   int32_t reserved;

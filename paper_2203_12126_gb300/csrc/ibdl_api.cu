@@ -887,7 +887,7 @@ ibdl_status ibdl_solve(ibdl_geometry g, const double* bdata, const double* g_gri
     IBDL_CU(cudaStreamSynchronize(st));
     info_from_state(*g->h_state, g->h_hist, info);
     if (*hflag) return fail(IBDL_ERR_NONFINITE, "non-finite boundary data or initial guess");
-    if (hb[2]) return fail(IBDL_ERR_TIMEOUT, "persistent solver: a grid barrier timed out");
+    if (hb[2]) return fail(IBDL_ERR_TIMEOUT, "persistent solver: a bounded device wait timed out");
     const int stt = g->h_state->status;
     if (stt == IBDL_ERR_NOT_CONVERGED) return fail(IBDL_ERR_NOT_CONVERGED, "GMRES reached max_iters");
     if (stt == IBDL_ERR_NONFINITE) return fail(IBDL_ERR_NONFINITE, "non-finite residual");
@@ -1234,7 +1234,7 @@ ibdl_status ibdl_solve_batched(ibdl_batch b, int32_t count, const ibdl_geometry*
   unsigned hb[4] = {0, 0, 0, 0};
   IBDL_CU(cudaMemcpyAsync(hb, b->d_bar, sizeof(hb), cudaMemcpyDeviceToHost, st));
   IBDL_CU(cudaStreamSynchronize(st));
-  if (hb[2]) return fail(IBDL_ERR_TIMEOUT, "persistent solver: a grid barrier timed out");
+  if (hb[2]) return fail(IBDL_ERR_TIMEOUT, "persistent solver: a bounded device wait timed out");
   ibdl_status worst = IBDL_OK;
   for (int k = 0; k < count; ++k) {
     const ibdl_status sk = (ibdl_status)b->h_state[k].status;

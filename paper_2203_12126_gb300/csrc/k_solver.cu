@@ -65,8 +65,9 @@ __device__ bool counted_barrier(unsigned* ctr, unsigned parties, unsigned* err) 
   return *(volatile unsigned*)err == 0u;
 }
 
-// bar[0..1]: grid barrier, bar[2]: error flag, bar[4 + 4k ..]: barrier of the
-// blocks that hold instance k's vector chunks.
+// bar[0..1]: the start-up grid barrier, bar[2]: error flag, bar[3]: count of
+// instances done (or paused) in this launch, bar[4 + kSchedWords k ..]:
+// instance k's scheduler words.
 __device__ bool grid_barrier(unsigned* bar, unsigned nblocks) {
   return counted_barrier(bar, nblocks, bar + 2);
 }
