@@ -140,6 +140,46 @@ def run_serving(pkg, nreq, seed=3, rate=2000.0, budget=120 << 30):
     }
 
 
+def run_c3_solve(pkg, reps=3):
+    """C3: the 3D sphere (N=256^3, M=38039) Neumann solve, float32-refined to
+    1e-8 through the persistent solver; event-timed; error against a float64
+    GPU solve at 1e-12."""
+    import torch
+    from paper_2203_12126_gb300 import ibdl
+    dev = torch.device("cuda", torch.cuda.current_device())
+    p = configs.c3()
+    b = torch.tensor(p.bdata, dtype=torch.float64, device=dev)
+    g = pkg.Geometry.from_workload(p.geom, bc=p.bc, precision=ibdl.FP32_REFINED)
+    q = torch.zeros_like(b)
+    info = g.solve(b, q, tol=1e-8)
+    ms = []
+    for _ in range(reps):
+        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        info = g.solve(b, q, tol=1e-8)
+        c.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(c))
+    g.close()
+    g64 = pkg.Geometry.from_workload(p.geom, bc=p.bc, precision=ibdl.FP64)
+    q64 = torch.zeros_like(b)
+    a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    i64 = g64.solve(b, q64, tol=1e-8)
+    c.record()
+    torch.cuda.synchronize()
+    fp64_ms = a.elapsed_time(c)
+    g64.solve(b, q64, tol=1e-12)
+    g64.close()
+    return {"workload": "3D sphere r=0.3, N=256^3, M=38039, kappa=1e-3, Neumann, "
+                        "float32-refined to 1e-8",
+            "solve_ms": float(np.median(ms)), "solves_per_s": 1e3 / float(np.median(ms)),
+            "iters": info["iters"], "matvecs": info["matvecs"],
+            "refine_steps": info["refine_steps"], "rel_residual": info["rel_residual"],
+            "rel_err_vs_fp64_1e-12": float(torch.linalg.norm(q - q64) / torch.linalg.norm(q64)),
+            "fp64_solve_ms": fp64_ms, "fp64_iters": i64["iters"]}
+
+
 def run_batched_c4(pkg, count=256, reps=3):
     """C4: `count` uneven 2D star instances (N in {128,256,512}^2, kappa
     log-uniform [1e-4,1e-1], seed 2) solved in ONE persistent launch,
@@ -614,6 +654,7 @@ def main():
     matvec = run_matvec_roofline(pkg, peaks) if not args.no_matvec else None
 
     batched_c4 = run_batched_c4(pkg) if not args.no_batched else None
+    c3_solve = run_c3_solve(pkg) if not args.no_matvec else None
 
     serving = None
     if args.serve_requests > 0:
@@ -663,6 +704,7 @@ def main():
             "e2e": e2e,
             "matvec": matvec,
             "batched_c4": batched_c4,
+            "c3_solve": c3_solve,
             "serving": serving,
             "gpu_launches": int(launches),
             "wall_s_timed": wall,

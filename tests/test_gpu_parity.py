@@ -368,3 +368,20 @@ def test_launch_counter_counts_library_kernels():
     G.apply(q, y)
     assert pkg.kernel_launch_count() - n0 == 4   # rows_fwd, pencils, rows_inv, interp
     G.close()
+
+
+def test_c3_refined_solve_matches_fp64_solve():
+    """C3 at full size (3D sphere N=256^3, M=38039, Neumann): the
+    float32-refined solve to 1e-10 equals the float64 solve to 1e-12 within
+    the refined path's 1e-8."""
+    p = configs.c3()
+    b = gpu(p.bdata)
+    out = {}
+    for prec, tol in ((1, 1e-10), (0, 1e-12)):
+        G = make(p.geom, bc=p.bc, precision=prec)
+        q = torch.empty(p.geom.m, dtype=torch.float64, device=DEV)
+        info = G.solve(b, q, tol=tol)
+        assert info["rel_residual"] <= tol, info
+        out[prec] = host(q)
+        G.close()
+    assert rel(out[1], out[0]) <= 1e-8
