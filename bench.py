@@ -152,6 +152,7 @@ def run_c3_solve(pkg, reps=3):
     g = pkg.Geometry.from_workload(p.geom, bc=p.bc, precision=ibdl.FP32_REFINED)
     q = torch.zeros_like(b)
     info = g.solve(b, q, tol=1e-8)
+    rows = g.info()["rows_per_tile"]
     ms = []
     for _ in range(reps):
         a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -177,7 +178,7 @@ def run_c3_solve(pkg, reps=3):
             "iters": info["iters"], "matvecs": info["matvecs"],
             "refine_steps": info["refine_steps"], "rel_residual": info["rel_residual"],
             "rel_err_vs_fp64_1e-12": float(torch.linalg.norm(q - q64) / torch.linalg.norm(q64)),
-            "fp64_solve_ms": fp64_ms, "fp64_iters": i64["iters"]}
+            "fp64_solve_ms": fp64_ms, "fp64_iters": i64["iters"], "rows_per_tile": rows}
 
 
 def run_batched_c4(pkg, count=256, reps=3):
@@ -353,7 +354,8 @@ def run_matvec_roofline(pkg, peaks, reps=30):
             out[f"{name}-{tag}"] = {"us_median": us, "algorithmic_bytes": B,
                                     "achieved_gbs": gbs, "peak_gbs": peaks["hbm_gbs"],
                                     "frac_of_hbm": gbs / peaks["hbm_gbs"],
-                                    "peak_src": peaks["src"]}
+                                    "peak_src": peaks["src"],
+                                    "rows_per_tile": g.info()["rows_per_tile"]}
         g.close()
     return out
 

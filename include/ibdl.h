@@ -325,9 +325,20 @@ typedef struct {
   int32_t bc, delta, precision;
   int64_t device_bytes;      /* device memory the handle owns */
   int32_t fft_passes;        /* kernels per Helmholtz solve */
-  int32_t reserved;
+  int32_t rows_per_tile;     /* grid rows per x-pass tile (spread bin size) */
 } ibdl_geometry_info;
 ibdl_status ibdl_get_geometry_info(ibdl_geometry g, ibdl_geometry_info* info);
+
+/* Autotuner of the x-pass tiling (on by default).  The first geometry of
+ * each (device, dim, n, precision) times one matvec for every admissible
+ * number of grid rows per tile -- an even R with n/R >= 4, R <= n - 5 and
+ * float64 row buffers within 100 KB of shared memory -- and the fastest is
+ * used by every later geometry of that kind in the process (a few matvecs
+ * once, inside that first ibdl_create_geometry).  Geometries built by the
+ * server use a tiling already chosen, else the fixed rule (4 rows in 2D, 2
+ * for n = 4096; 8 in 3D).  Off: the fixed rule always.  Results of the two
+ * tilings agree to rounding. */
+void ibdl_tuning_enable(int32_t on);
 
 /* Number of this library's kernels launched so far in this process
  * (all handles, all streams). */

@@ -584,6 +584,138 @@ ibdl_status vec_norm(ibdl_geometry_s* g, const double* v, double* out, cudaStrea
   return IBDL_OK;
 }
 
+// Tile lists of `rows` rows per tile into `out` (3D: with the empty-plane
+// flags in dz), from caller-provided buffers; asynchronous on st.
+cudaError_t build_tiles(ibdl_geometry_s* g, int rows, int* start, int* cursor, int* counts,
+                        int* pts, unsigned char* dz, Bins* out, cudaStream_t st) {
+  const GridDesc& gd = g->grid;
+  const int n = gd.n;
+  const int ntiles = (n / rows) * (gd.dim == 3 ? n : 1);
+  cudaError_t e = launch_bins(gd, g->pd, rows, ntiles, start, cursor, counts, pts, st);
+  if (e) return e;
+  out->rows = rows;
+  out->ntiles = ntiles;
+  out->start = start;
+  out->pts = pts;
+  out->zempty = nullptr;
+  if (gd.dim == 3) {
+    // planes no point touches: their spectrum stays zero through the x and
+    // y passes of a matvec
+    if ((e = launch_plane_flags(start, n / rows, n, dz, st))) return e;
+    out->zempty = dz;
+  }
+  return cudaSuccess;
+}
+
+// ---- autotuner ---------------------------------------------------------------
+// Rows per tile of the x passes (the spread bin size, and how many pencils a
+// row tile transforms together) for each (device, dim, n, precision): the
+// first geometry of a kind times a matvec (band-only field solve and
+// interpolation, in its inner precision) for every admissible tiling -- an
+// even R with n/R >= 4 tiles per plane, R <= n - 5 (the tile-list rule) and
+// float64 row buffers within the persistent solver's 100 KB -- and the
+// fastest is kept for the process.  Off (ibdl_tuning_enable(0)), the fixed
+// rule rows_per_tile applies.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, int> g_tuned;
+std::atomic<int> g_tuning_on{1};
+// set while the server builds a request's geometry: it takes a cached
+// tiling or the rule, never times candidates beside a running slice
+thread_local bool tl_no_tune = false;
+
+ibdl_status tuned_rows(ibdl_geometry_s* g, int* rows_out, cudaStream_t st) {
+  const GridDesc& gd = g->grid;
+  const int n = gd.n, dim = gd.dim;
+  if (!g_tuning_on.load()) return IBDL_OK;
+  int dev = 0;
+  IBDL_CU(cudaGetDevice(&dev));
+  const auto key = std::make_tuple(dev, dim, n, g->precision);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) {
+      *rows_out = it->second;
+      return IBDL_OK;
+    }
+  }
+  if (tl_no_tune) return IBDL_OK;
+  std::vector<int> cand;
+  for (int R = 2; R <= 32; R *= 2)
+    if (n / R >= 4 && R <= n - 5 && rows_smem_bytes<double>(n, R) <= 100 * 1024)
+      cand.push_back(R);
+  if (cand.size() < 2) return IBDL_OK;
+  cudaMemPool_t pool;
+  IBDL_CU(workspace_pool(&pool));
+  const int m = g->m;
+  double *q = nullptr, *y = nullptr;
+  IBDL_CU(cudaMallocFromPoolAsync((void**)&q, sizeof(double) * m, pool, st));
+  IBDL_CU(cudaMallocFromPoolAsync((void**)&y, sizeof(double) * m, pool, st));
+  {
+    std::vector<double> hq(m);
+    uint64_t r = 0x9e3779b97f4a7c15ull;
+    for (int i = 0; i < m; ++i) {
+      r ^= r << 13;
+      r ^= r >> 7;
+      r ^= r << 17;
+      hq[i] = (double)(r >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+    }
+    IBDL_CU(cudaMemcpyAsync(q, hq.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st));
+  }
+  cudaEvent_t e0, e1;
+  IBDL_CU(cudaEventCreate(&e0));
+  IBDL_CU(cudaEventCreate(&e1));
+  const Bins saved = g->bins;
+  const int prec = g->precision;
+  int best = cand[0];
+  float best_ms = 1e30f;
+  ibdl_status status = IBDL_OK;
+  for (int R : cand) {
+    const int ntiles = (n / R) * (dim == 3 ? n : 1);
+    void* buf = nullptr;
+    const size_t ni = 3 * ((size_t)ntiles + 1) + (size_t)bins_capacity(dim, R, m);
+    cudaError_t e = cudaMallocFromPoolAsync(&buf, ni * sizeof(int) + n, pool, st);
+    if (e) {
+      status = cuda_fail(e, "autotuner buffers");
+      break;
+    }
+    int* start = static_cast<int*>(buf);
+    int* cursor = start + ntiles + 1;
+    int* counts = cursor + ntiles + 1;
+    int* pts = counts + ntiles + 1;
+    unsigned char* dz = reinterpret_cast<unsigned char*>(pts + bins_capacity(dim, R, m));
+    e = build_tiles(g, R, start, cursor, counts, pts, dz, &g->bins, st);
+    float ms = 0;
+    for (int rep = 0; rep < 4 && !e && status == IBDL_OK; ++rep) {
+      if (rep == 1) e = cudaEventRecord(e0, st);
+      if (e) break;
+      status = matvec_prec(g, prec, q, y, st);
+    }
+    if (!e && status == IBDL_OK) e = cudaEventRecord(e1, st);
+    if (!e && status == IBDL_OK) e = cudaEventSynchronize(e1);
+    if (!e && status == IBDL_OK) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaFreeAsync(buf, st);
+    if (e) status = cuda_fail(e, "autotuner timing");
+    if (status != IBDL_OK) break;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = R;
+    }
+  }
+  g->bins = saved;
+  cudaFreeAsync(q, st);
+  cudaFreeAsync(y, st);
+  cudaStreamSynchronize(st);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (status != IBDL_OK) return status;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[key] = best;
+  }
+  *rows_out = best;
+  return IBDL_OK;
+}
+
 ibdl_status check_handle(ibdl_geometry g) {
   if (!g) return fail(IBDL_ERR_INVALID_ARG, "NULL geometry handle");
   return IBDL_OK;
@@ -723,41 +855,29 @@ ibdl_status ibdl_create_geometry(const ibdl_geometry_desc* d, void* stream, ibdl
     cudaError_t e = launch_point_prep(gd, m, X, B, WW, VV, st);
     if (e) return cleanup(cuda_fail(e, "point prep"));
   }
-  // bins
-  const int rows = rows_per_tile(dim, n);
-  const int ntiles = (n / rows) * (dim == 3 ? n : 1);
-  int *start, *cursor;
-  if ((s = g->alloc(&start, (size_t)ntiles + 1))) return cleanup(s);
-  if ((s = g->alloc(&cursor, (size_t)ntiles + 1))) return cleanup(s);
-  int* bpts = nullptr;
-  int* counts = nullptr;
-  if ((s = g->alloc(&counts, (size_t)ntiles + 1))) return cleanup(s);
-  if ((s = g->alloc(&bpts, (size_t)bins_capacity(dim, rows, m)))) return cleanup(s);
   {
-    cudaError_t e = launch_bins(gd, pd, rows, ntiles, start, cursor, counts, bpts, st);
-    if (e) return cleanup(cuda_fail(e, "binning"));
-  }
-  g->bins.rows = rows;
-  g->bins.ntiles = ntiles;
-  g->bins.start = start;
-  g->bins.pts = bpts;
-  if (dim == 3) {
-    // planes no point touches: their spectrum stays zero through the x and
-    // y passes of a matvec
-    unsigned char* dz = nullptr;
-    if ((s = g->alloc(&dz, (size_t)n))) return cleanup(s);
-    cudaError_t e = launch_plane_flags(start, n / rows, n, dz, st);
-    if (e) return cleanup(cuda_fail(e, "plane flags"));
-    g->bins.zempty = dz;
-  }
-
-  {
-    cudaError_t e = configure_fft_kernels(n, rows);
+    cudaError_t e = configure_fft_kernels(n, 0);
     if (e) return cleanup(cuda_fail(e, "configure kernels"));
   }
   if ((s = alloc_spectral<double>(g, g->ws64, st))) return cleanup(s);
   if (d->precision == IBDL_FP32_REFINED) {
     if ((s = ensure32(g, st))) return cleanup(s);
+  }
+
+  // tile lists, with the rows per tile chosen by the autotuner
+  int rows = rows_per_tile(dim, n);
+  if ((s = tuned_rows(g, &rows, st))) return cleanup(s);
+  {
+    const int ntiles = (n / rows) * (dim == 3 ? n : 1);
+    int *start, *cursor, *counts, *bpts;
+    unsigned char* dz = nullptr;
+    if ((s = g->alloc(&start, (size_t)ntiles + 1))) return cleanup(s);
+    if ((s = g->alloc(&cursor, (size_t)ntiles + 1))) return cleanup(s);
+    if ((s = g->alloc(&counts, (size_t)ntiles + 1))) return cleanup(s);
+    if ((s = g->alloc(&bpts, (size_t)bins_capacity(dim, rows, m)))) return cleanup(s);
+    if (dim == 3 && (s = g->alloc(&dz, (size_t)n))) return cleanup(s);
+    cudaError_t e = build_tiles(g, rows, start, cursor, counts, bpts, dz, &g->bins, st);
+    if (e) return cleanup(cuda_fail(e, "binning"));
   }
 
   // Krylov workspace (float64, restart up to 64)
@@ -792,7 +912,7 @@ ibdl_status ibdl_create_geometry(const ibdl_geometry_desc* d, void* stream, ibdl
   if ((s = g->alloc(&g->d_state, (size_t)1))) return cleanup(s);
   if ((s = g->alloc(&g->d_bar, (size_t)(4 + kSchedWords)))) return cleanup(s);
 
-  g->solver_smem = solver_smem_bytes(gd, 1);
+  g->solver_smem = solver_smem_bytes(gd, g->bins.rows, 1);
   {
     cudaError_t e = cudaStreamSynchronize(st);
     if (e) return cleanup(cuda_fail(e, "create sync"));
@@ -1135,6 +1255,7 @@ ibdl_status ibdl_get_geometry_info(ibdl_geometry g, ibdl_geometry_info* info) {
   info->precision = g->precision;
   info->device_bytes = g->bytes;
   info->fft_passes = fft_kernels_per_solve<double>(g->grid.dim);
+  info->rows_per_tile = g->bins.rows;
   return IBDL_OK;
 }
 
@@ -1247,6 +1368,8 @@ ibdl_status ibdl_solve_batched(ibdl_batch b, int32_t count, const ibdl_geometry*
 }
 
 int64_t ibdl_kernel_launch_count(void) { return (int64_t)g_launches.load(); }
+
+void ibdl_tuning_enable(int32_t on) { g_tuning_on.store(on != 0); }
 
 void ibdl_profile_enable(int32_t on) {
   if (on && !g_phase_buf) {
@@ -1442,7 +1565,10 @@ void finish_request(ibdl_server_s* s, SrvReq* r, ibdl_status st) {
 // the next launch.
 ibdl_status admit_one(ibdl_server_s* s, SrvReq* r, int k) {
   ibdl_geometry g = nullptr;
-  IBDL_TRY(ibdl_create_geometry(&r->desc, s->setup_st, &g));
+  tl_no_tune = true;
+  const ibdl_status cs = ibdl_create_geometry(&r->desc, s->setup_st, &g);
+  tl_no_tune = false;
+  IBDL_TRY(cs);
   const size_t mb = sizeof(double) * (size_t)g->m;
   // Dirichlet: b = U_b; Neumann: V_b, from which the solver's first action
   // builds b

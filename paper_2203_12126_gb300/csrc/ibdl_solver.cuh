@@ -63,7 +63,7 @@ struct SolveState {
   double beta, bnorm, tol_abs, rel;
 };
 
-int solver_smem_bytes(const GridDesc& g, int need32);
+int solver_smem_bytes(const GridDesc& g, int rows, int need32);
 // max_rounds > 0 stops the launch after that many rounds (states persist for
 // the next launch); reserve_sms SMs are left without solver blocks.
 cudaError_t launch_persistent_solve(const SolveInst* d_insts, SolveState* d_states, int ninst,

@@ -1005,8 +1005,8 @@ __global__ void __launch_bounds__(kSolverThreads, 2)
   }
 }
 
-int solver_smem_bytes(const GridDesc& g, int need32) {
-  size_t s = rows_smem_bytes<double>(g.n, rows_per_tile(g.dim, g.n));
+int solver_smem_bytes(const GridDesc& g, int rows, int need32) {
+  size_t s = rows_smem_bytes<double>(g.n, rows);
   const int nl = g.dim == 2 ? 1 : 2;
   for (int w = 0; w < nl; ++w) {
     const PencilLayout L = solve_layout<double>(g.dim, g.n, w == 0 ? 1 : 0);

@@ -37,7 +37,7 @@ EXPORTS = [
     "ibdl_batch_create", "ibdl_batch_destroy", "ibdl_solve_batched",
     "ibdl_server_config_default", "ibdl_server_create", "ibdl_server_destroy",
     "ibdl_server_clock", "ibdl_server_submit", "ibdl_server_step", "ibdl_server_take",
-    "ibdl_server_get_stats",
+    "ibdl_server_get_stats", "ibdl_tuning_enable",
 ]
 
 
@@ -78,7 +78,7 @@ class GeometryInfo(C.Structure):
         ("dim", C.c_int32), ("n", C.c_int32), ("m", C.c_int64), ("h", C.c_double),
         ("kappa", C.c_double), ("bc", C.c_int32), ("delta", C.c_int32),
         ("precision", C.c_int32), ("device_bytes", C.c_int64),
-        ("fft_passes", C.c_int32), ("reserved", C.c_int32),
+        ("fft_passes", C.c_int32), ("rows_per_tile", C.c_int32),
     ]
 
 
@@ -164,6 +164,7 @@ def load(path: str = LIB_PATH):
         "ibdl_server_step": (C.c_int, [vp, C.POINTER(i64), i32, C.POINTER(i32)]),
         "ibdl_server_take": (C.c_int, [vp, i64, vp, C.POINTER(RequestResult)]),
         "ibdl_server_get_stats": (C.c_int, [vp, C.POINTER(ServerStats)]),
+        "ibdl_tuning_enable": (None, [i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -232,6 +233,10 @@ def helmholtz_2d_noalloc(n, box_len, kappa, f, v_out, stream=None):
     _check(load().ibdl_helmholtz_2d_noalloc(int(n), float(box_len), float(kappa), _ptr(f),
                                             _ptr(v_out), _stream(stream)))
     return v_out
+
+
+def tuning_enable(on: bool = True) -> None:
+    load().ibdl_tuning_enable(1 if on else 0)
 
 
 def version() -> int:

@@ -1,0 +1,45 @@
+"""The x-pass tiling autotuner: whatever tiling it picks, the operator is
+the fixed rule's to rounding (float64 1e-12, float32 1e-6 relative)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from workloads import configs, geometry  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    import paper_2203_12126_gb300 as pkg
+    from paper_2203_12126_gb300 import ibdl
+    DEV = torch.device("cuda:0")
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-6)])
+@pytest.mark.parametrize("which", ["star256", "ellipsoid32"])
+def test_tuned_tiling_matches_fixed_rule(which, prec, tol):
+    if which == "star256":
+        g = geometry.star(256, 0.3, 0.2, 5, kappa=1e-3)
+        rule, admissible = 4, {2, 4, 8, 16, 32}
+    else:
+        g = geometry.ellipsoid(32, (0.3, 0.22, 0.26), kappa=1e-2)
+        rule, admissible = 8, {2, 4, 8}
+    q = torch.tensor(np.random.default_rng(5).standard_normal(g.m), device=DEV)
+    out = {}
+    try:
+        for on in (False, True):
+            ibdl.tuning_enable(on)
+            G = pkg.Geometry.from_workload(g, bc=configs.NEUMANN, precision=prec)
+            rows = G.info()["rows_per_tile"]
+            assert rows == rule if not on else rows in admissible
+            y = torch.empty_like(q)
+            G.apply(q, y, precision=prec)
+            out[on] = y.cpu().numpy()
+            G.close()
+    finally:
+        ibdl.tuning_enable(True)
+    assert rel(out[True], out[False]) <= tol
