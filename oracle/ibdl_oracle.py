@@ -18,7 +18,14 @@ Layer method" (arXiv:2203.12126):
 * Neumann system          Sec. 4.4, eq. (Neumann saddle point)
 * field evaluation        Sec. 4.1 step 2, eq. (ibdl 1 again); eq. (ib neumann 1)
 * GMRES                   Sec. 5.3 (unpreconditioned, relative residual)
-* interior indicator      App. D (Q = 1 with a Poisson-like large kappa)
+* Poisson limit           Sec. 5.4, App. C: kappa = inf (k = 0); the mean-zero
+                          inverse Delta_0^{-1} replaces -kappa L'^{-1}
+* completed IBDL          Sec. 5.4 eq. (ibdl completed), App. C: unknowns
+                          (Q, u_bar), single layer eta S Q added
+* interior indicator      App. D: Delta u + S~ 1 = 0, mean-zero solve, shift by
+                          the box-corner value, threshold at 1/2
+* near-boundary values    Sec. 5.5, App. A (2D): linear interpolation between
+                          the chord point x_A and a point x_B m2 h inside
 
 Conventions.  The paper writes the operator as L_p = Delta_h - k^2.  This
 oracle uses L' = I - kappa Delta_h with kappa = 1/k^2, so L_p = -(1/kappa) L'
@@ -32,6 +39,8 @@ Delta u - k^2 u = g.
 Parity pins live in tests/test_oracle_*.py; functions without a pin say so.
 """
 from __future__ import annotations
+
+import math
 
 import numpy as np
 
@@ -187,6 +196,38 @@ def helmholtz_solve(box, kappa, f):
     return np.real(np.fft.ifftn(F / symbol(box, kappa)))
 
 
+def laplace_symbol(box):
+    """Eigenvalues of -Delta_h on the Fourier modes:
+    lambda(k) = (4 / h^2) sum_c sin^2(pi k_c / n); zero only at k = 0."""
+    k = np.arange(box.n)
+    s2 = np.sin(np.pi * k / box.n) ** 2
+    lam = np.zeros(box.shape)
+    for a in range(box.d):
+        shp = [1] * box.d
+        shp[a] = box.n
+        lam = lam + (4.0 / box.h ** 2) * s2.reshape(shp)
+    return lam
+
+
+def laplace_inverse0(box, f):
+    """Delta_0^{-1} f of Sec. 5.4 / App. C: the mean-zero u with
+    Delta_h u = f - mean(f) (the k = 0 mode of f is dropped)."""
+    lam = laplace_symbol(box)
+    F = np.fft.fftn(f)
+    F.reshape(-1)[0] = 0.0
+    lam.reshape(-1)[0] = 1.0
+    return np.real(np.fft.ifftn(-F / lam))
+
+
+def green(box, kappa, f):
+    """The grid solve every operator below uses: kappa L'^{-1} f for finite
+    kappa (= -L_p^{-1} f with L_p = Delta_h - k^2), and its k = 0 limit
+    -Delta_0^{-1} f for kappa = inf (the Poisson equation, Sec. 5.4)."""
+    if np.isinf(kappa):
+        return -laplace_inverse0(box, f)
+    return kappa * helmholtz_solve(box, kappa, f)
+
+
 def helmholtz_dense(box, kappa):
     """Dense matrix of L' (tiny grids only): column j = L' e_j."""
     n = box.n ** box.d
@@ -209,6 +250,9 @@ DIRICHLET, NEUMANN = 0, 1
 class Operator:
     """A_D Q = Q/2 + kappa S* L'^{-1} S~ Q         (eq. (ibdl schur again))
     A_N U = kappa S* L'^{-1} S~ U - U/2          (eq. (Neumann saddle point))
+
+    kappa = inf is the Poisson equation (Sec. 5.4, App. C with eta = 0):
+    A_D Q = Q/2 - S* Delta_0^{-1} S~ Q (Dirichlet only).
     """
 
     def __init__(self, geom, bc, kappa=None, delta=None):
@@ -220,20 +264,22 @@ class Operator:
         self.delta = geom.delta if delta is None else delta
         self.bc = int(bc)
         self.matvecs = 0
+        if np.isinf(self.kappa) and self.bc != DIRICHLET:
+            raise ValueError("the Poisson limit is defined for the Dirichlet problem only")
 
     @property
     def m(self):
         return self.X.shape[0]
 
     def layer(self, Q):
-        """v = L'^{-1} S~ Q on the grid."""
+        """v = kappa L'^{-1} S~ Q on the grid (-Delta_0^{-1} S~ Q if kappa = inf)."""
         f = spread_div(self.box, self.X, self.nrm, self.w, Q, self.delta)
-        return helmholtz_solve(self.box, self.kappa, f)
+        return green(self.box, self.kappa, f)
 
     def apply(self, Q):
         self.matvecs += 1
         Q = np.asarray(Q, dtype=np.float64)
-        y = self.kappa * interp(self.box, self.X, self.layer(Q), self.delta)
+        y = interp(self.box, self.X, self.layer(Q), self.delta)
         return y + 0.5 * Q if self.bc == DIRICHLET else y - 0.5 * Q
 
     __call__ = apply
@@ -249,16 +295,13 @@ class Operator:
         if self.bc == DIRICHLET:
             out = b.copy()
             if g_grid is not None:
-                out += self.kappa * interp(self.box, self.X,
-                                           helmholtz_solve(self.box, self.kappa, g_grid),
-                                           self.delta)
+                out += interp(self.box, self.X, green(self.box, self.kappa, g_grid),
+                              self.delta)
             return out
         src = -spread(self.box, self.X, b, self.w, self.delta)
         if g_grid is not None:
             src = src + g_grid
-        return self.kappa * interp(self.box, self.X,
-                                   helmholtz_solve(self.box, self.kappa, src),
-                                   self.delta)
+        return interp(self.box, self.X, green(self.box, self.kappa, src), self.delta)
 
     def evaluate(self, Q, vb=None, g_grid=None):
         """Grid solution, step 2 of Sec. 4.1: L_p u + S~Q = g~ gives
@@ -268,7 +311,7 @@ class Operator:
             src = src + spread(self.box, self.X, vb, self.w, self.delta)
         if g_grid is not None:
             src = src - g_grid
-        return self.kappa * helmholtz_solve(self.box, self.kappa, src)
+        return green(self.box, self.kappa, src)
 
     def dense(self):
         """Assemble A column by column, A[:, i] = A e_i."""
@@ -374,17 +417,173 @@ def solve_dense(geom, bc, bdata, g_grid=None, kappa=None):
 
 
 # ---------------------------------------------------------------------------
+# Completed IBDL for the Poisson equation, Sec. 5.4 and App. C
+# ---------------------------------------------------------------------------
+
+
+class CompletedOperator:
+    """The completed system of App. C on z = (Q, u_bar), length M + 1:
+
+      Q/2 - S* Delta_0^{-1} (S~ + eta S) Q + u_bar 1 = U_b - S* Delta_0^{-1} g~
+      eta sum_i w_i Q_i                               = h^d sum_j g~_j
+
+    The second row is the solvability condition eta int_Gamma Q ds =
+    int_C g~; with per-point weights w_i it reads sum_i w_i Q_i (the paper's
+    Delta s 1^T Q for uniform spacing).  Dirichlet only.
+    """
+
+    def __init__(self, geom, eta, delta=None):
+        self.box = Box.of(geom)
+        self.X = np.asarray(geom.X, dtype=np.float64)
+        self.nrm = np.asarray(geom.normals, dtype=np.float64)
+        self.w = np.asarray(geom.weights, dtype=np.float64)
+        self.delta = geom.delta if delta is None else delta
+        self.eta = float(eta)
+        self.matvecs = 0
+
+    @property
+    def m(self):
+        return self.X.shape[0]
+
+    def source(self, Q):
+        """(S~ + eta S) Q on the grid."""
+        return (spread_div(self.box, self.X, self.nrm, self.w, Q, self.delta)
+                + self.eta * spread(self.box, self.X, Q, self.w, self.delta))
+
+    def apply(self, z):
+        self.matvecs += 1
+        z = np.asarray(z, dtype=np.float64)
+        Q, ubar = z[:self.m], z[self.m]
+        top = (0.5 * Q - interp(self.box, self.X, laplace_inverse0(self.box, self.source(Q)),
+                                self.delta) + ubar)
+        return np.concatenate([top, [self.eta * np.dot(self.w, Q)]])
+
+    __call__ = apply
+
+    def rhs(self, ub, g_grid=None):
+        top = np.array(ub, dtype=np.float64)
+        last = 0.0
+        if g_grid is not None:
+            top -= interp(self.box, self.X, laplace_inverse0(self.box, g_grid), self.delta)
+            last = self.box.h ** self.box.d * float(np.sum(g_grid))
+        return np.concatenate([top, [last]])
+
+    def evaluate(self, z, g_grid=None):
+        """u = -Delta_0^{-1} (S~ + eta S) Q + Delta_0^{-1} g~ + u_bar."""
+        Q, ubar = np.asarray(z[:self.m]), float(z[self.m])
+        u = -laplace_inverse0(self.box, self.source(Q)) + ubar
+        if g_grid is not None:
+            u = u + laplace_inverse0(self.box, g_grid)
+        return u
+
+
+def solve_completed(geom, eta, ub, g_grid=None, tol=1e-10, restart=30, maxiter=1000):
+    """GMRES on the completed system; returns the result with x = (Q, u_bar)."""
+    op = CompletedOperator(geom, eta)
+    b = op.rhs(ub, g_grid)
+    res = gmres(op, b, tol, restart, maxiter)
+    res.matvecs = op.matvecs
+    res.op = op
+    res.b = b
+    return res
+
+
+# ---------------------------------------------------------------------------
 # Interior indicator, App. D
 # ---------------------------------------------------------------------------
 
 
-def indicator(geom, kappa_large=1e6):
-    """Regularised indicator chi_h: solve (I - kappa Delta_h) u = -kappa S~1
-    ... with kappa large (the Poisson limit -Delta u = div(delta n)), then
-    shift the value at the box corner to 0.  Parity unpinned beyond the
-    threshold-at-1/2 check against the exact shape."""
+def indicator(geom):
+    """App. D: Delta u + S~ 1 = 0 solved for the mean-zero u, i.e.
+    u = -Delta_0^{-1} S~ 1; chi_h = u - u(box corner node); the indicator is
+    chi = 1 where chi_h > 1/2, else 0.  Returns (chi_h, chi as uint8)."""
     box = Box.of(geom)
-    f = spread_div(box, geom.X, geom.normals, geom.weights,
-                   np.ones(geom.m), geom.delta)
-    u = kappa_large * helmholtz_solve(box, kappa_large, f)
-    return u - u.reshape(-1)[0]
+    f = spread_div(box, geom.X, geom.normals, geom.weights, np.ones(geom.m), geom.delta)
+    u = -laplace_inverse0(box, f)
+    chi_h = u - u.reshape(-1)[0]
+    return chi_h, (chi_h > 0.5).astype(np.uint8)
+
+
+# ---------------------------------------------------------------------------
+# Near-boundary values, Sec. 5.5 and App. A (2D)
+# ---------------------------------------------------------------------------
+
+
+def near_boundary_values(geom, u, ub, inside, m1, m2):
+    """Replace u at the nodes of Omega within m1 meshwidths of Gamma (App. A).
+
+    For a node x_p with inside = 1 whose nearest boundary point is closer than
+    m1 h:
+      1. x_1, x_2 = the two nearest boundary points (ties: lower index first);
+      2. x_A = the orthogonal projection of x_p on the line x_2 + t (x_1 - x_2);
+         if t is outside [0, 1], take the third nearest point and use the two
+         of the three that lie farthest apart, with t clamped to [0, 1];
+      3. u(x_A) = U_b(x_1)|x_A - x_2| / |x_2 - x_1| + U_b(x_2)|x_A - x_1| / |x_2 - x_1|;
+      4. x_B = x_A + m2 h (x_p - x_A) / |x_p - x_A|;
+      5. u(x_B) = the bilinear interpolation of u on the cell holding x_B;
+      6. u(x_p) = u(x_A)|x_B - x_p| / |x_B - x_A| + u(x_B)|x_A - x_p| / |x_B - x_A|.
+    A node on the chord (|x_p - x_A| = 0) takes u(x_A).  Other nodes keep
+    their value.  u: grid (n, n); ub: boundary values (the data U_b for
+    Dirichlet, the solved U for Neumann); inside: (n, n) 0/1."""
+    box = Box.of(geom)
+    assert box.d == 2
+    n, h = box.n, box.h
+    X = np.asarray(geom.X, dtype=np.float64)
+    ub = np.asarray(ub, dtype=np.float64)
+    uin = np.asarray(u, dtype=np.float64).reshape(n, n)
+    out = uin.copy()
+    ins = np.asarray(inside).reshape(n, n)
+    thresh = (m1 * h) * (m1 * h)
+    ox, oy = float(box.o[0]), float(box.o[1])
+    for iy in range(n):
+        py = oy + iy * h
+        dy = py - X[:, 1]
+        for ix in range(n):
+            if not ins[iy, ix]:
+                continue
+            px = ox + ix * h
+            dx = px - X[:, 0]
+            d2 = dx * dx + dy * dy
+            order = np.argsort(d2, kind="stable")
+            if not d2[order[0]] < thresh:
+                continue
+            a, b = int(order[0]), int(order[1])
+            p = np.array([px, py])
+            t = _chord_t(p, X[a], X[b])
+            if not (0.0 <= t <= 1.0):
+                c = int(order[2])
+                best = -1.0
+                for i, j in ((a, b), (a, c), (b, c)):
+                    e = X[i] - X[j]
+                    s = e[0] * e[0] + e[1] * e[1]
+                    if s > best:
+                        best, pa, pb = s, i, j
+                a, b = pa, pb
+                t = min(max(_chord_t(p, X[a], X[b]), 0.0), 1.0)
+            x1, x2 = X[a], X[b]
+            xA = x2 + t * (x1 - x2)
+            L12 = np.linalg.norm(x2 - x1)
+            uA = ub[a] * np.linalg.norm(xA - x2) / L12 + ub[b] * np.linalg.norm(xA - x1) / L12
+            dA = np.linalg.norm(p - xA)
+            if dA == 0.0:
+                out[iy, ix] = uA
+                continue
+            xB = xA + (p - xA) / dA * (m2 * h)
+            rx, ry = (xB[0] - ox) / h, (xB[1] - oy) / h
+            jx, jy = math.floor(rx), math.floor(ry)
+            fx, fy = rx - jx, ry - jy
+            u00 = uin[jy % n, jx % n]
+            u10 = uin[jy % n, (jx + 1) % n]
+            u01 = uin[(jy + 1) % n, jx % n]
+            u11 = uin[(jy + 1) % n, (jx + 1) % n]
+            uB = (fx * fy * u11 + fy * (1.0 - fx) * u01 + fx * (1.0 - fy) * u10
+                  + (1.0 - fx - fy + fx * fy) * u00)
+            LAB = np.linalg.norm(xB - xA)
+            out[iy, ix] = uA * np.linalg.norm(xB - p) / LAB + uB * dA / LAB
+    return out
+
+
+def _chord_t(p, x1, x2):
+    """Parameter t of the orthogonal projection of p on x_2 + t (x_1 - x_2)."""
+    e = x1 - x2
+    return float(((p[0] - x2[0]) * e[0] + (p[1] - x2[1]) * e[1]) / (e[0] * e[0] + e[1] * e[1]))

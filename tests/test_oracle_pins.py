@@ -363,11 +363,176 @@ def test_dirichlet_constant_data_closed_form_density():
 
 
 def test_indicator_thresholds_to_the_disk():
-    """App. D: Q = 1 gives a regularised indicator; threshold 1/2 flags the
-    nodes inside the circle (checked away from Gamma)."""
+    """App. D: Delta u + S~ 1 = 0, shifted by the corner value, is a
+    regularised indicator that is 1/2 on Gamma; threshold 1/2 flags the nodes
+    inside the circle (checked away from Gamma).  A flipped sign of S~ or of
+    the solve gives chi_h near -1/2 and an empty indicator."""
     g = geometry.circle(128, 0.3, kappa=1.0)
-    chi = O.indicator(g).reshape(-1)
+    chi_h, chi = O.indicator(g)
+    chi = chi.reshape(-1)
     P = configs.grid_nodes(g)
     rho = np.linalg.norm(P - np.array(g.center)[None, :], axis=1)
     far = np.abs(rho - 0.3) > 3 * g.h
-    assert np.all((chi[far] > 0.5) == (rho[far] < 0.3))
+    assert np.all((chi[far] == 1) == (rho[far] < 0.3))
+    on_gamma = O.interp(O.Box.of(g), g.X, chi_h, g.delta)
+    assert np.max(np.abs(on_gamma - 0.5)) < 0.01
+    assert abs(chi_h.reshape(-1)[0]) == 0.0
+
+
+def test_indicator_of_a_star():
+    g = geometry.star(256, 0.3, 0.2, 5, kappa=1e-3)
+    _, chi = O.indicator(g)
+    rho, rad = configs.star_radius_at(g, configs.grid_nodes(g))
+    far = np.abs(rho - rad) > 3 * g.h
+    assert np.all((chi.reshape(-1)[far] == 1) == (rho[far] < rad[far]))
+
+
+# ---------------------------------------------------------------------------
+# Poisson limit and the completed system (Sec. 5.4, App. C)
+# ---------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("dim,n", [(2, 32), (3, 16)])
+def test_laplace_inverse0_inverts_explicit_stencil(dim, n):
+    """Delta_0^{-1} f is the mean-zero u with Delta_h u = f - mean(f),
+    checked with the explicit 5/7-point stencil."""
+    box = O.Box(dim, n, 1.3, (0.0,) * dim)
+    f = np.random.default_rng(dim).standard_normal(box.shape) + 0.7
+    u = O.laplace_inverse0(box, f)
+    assert np.max(np.abs(O.laplacian(box, u) - (f - f.mean()))) < 1e-12 * np.max(np.abs(f))
+    assert abs(u.mean()) < 1e-15
+
+
+def test_poisson_operator_is_the_large_kappa_limit():
+    """kappa L'^{-1} -> -Delta_0^{-1} on mean-zero sources as kappa grows
+    (S~ Q has zero mean: a discrete divergence)."""
+    g = geometry.circle(64, 0.3, kappa=1.0)
+    Q = np.random.default_rng(1).standard_normal(g.m)
+    a = O.Operator(g, configs.DIRICHLET, kappa=np.inf).apply(Q)
+    d = [np.linalg.norm(a - O.Operator(g, configs.DIRICHLET, kappa=k).apply(Q))
+         / np.linalg.norm(a) for k in (1e2, 1e6)]
+    assert d[1] < 1e-8 and d[0] > 100 * d[1], d
+
+
+def test_poisson_dirichlet_harmonic_polynomial():
+    """Laplace's equation inside a circle with U_b = x^2 - y^2: the Poisson
+    IBDL field converges to the harmonic polynomial away from Gamma."""
+    errs = []
+    for n in (64, 128, 256):
+        g = geometry.circle(n, 0.3, kappa=np.inf, spacing=0.75)
+        Xc = g.X - np.array(g.center)
+        res = O.solve(g, configs.DIRICHLET, Xc[:, 0] ** 2 - Xc[:, 1] ** 2, tol=1e-10)
+        u = res.op.evaluate(res.x).reshape(-1)
+        P = configs.grid_nodes(g) - np.array(g.center)
+        m = np.linalg.norm(P, axis=1) < 0.3 - 6 * g.h
+        errs.append(np.max(np.abs(u[m] - (P[m, 0] ** 2 - P[m, 1] ** 2))))
+    assert errs[0] < 2e-3 and errs[1] < errs[0] / 1.3 and errs[2] < errs[1] / 1.3, errs
+
+
+def _exp_exterior(n, L):
+    """Sec. 6.3: Delta u = g outside a circle of radius 0.25 in the periodic
+    box [-L/2, L/2)^2, u = exp(sin 2 pi x); g_e = 0 inside the circle."""
+    g = geometry.exterior(geometry.circle(n, 0.25, spacing=0.75, center=(0.0, 0.0),
+                                          origin=(-L / 2, -L / 2), box_len=L, kappa=np.inf))
+    P = configs.grid_nodes(g)
+    s, c = np.sin(2 * np.pi * P[:, 0]), np.cos(2 * np.pi * P[:, 0])
+    rho = np.linalg.norm(P, axis=1)
+    lap = np.exp(s) * ((2 * np.pi * c) ** 2 - 4 * np.pi ** 2 * s)
+    gt = np.where(rho > 0.25, lap, 0.0).reshape(n, n)
+    ub = np.exp(np.sin(2 * np.pi * g.X[:, 0]))
+    far = rho > 0.25 + 6 * g.h
+    return g, gt, ub, np.exp(s), far
+
+
+def test_completed_ibdl_converges_on_the_large_exterior_box():
+    """Sec. 6.3 (L = 8): the completed method with eta = 10 converges at
+    first order away from Gamma; the plain IBDL (g_e chosen so the
+    solvability condition of App. C holds) does not converge there."""
+    ec, ep = [], []
+    for n in (256, 512):
+        g, gt, ub, uex, far = _exp_exterior(n, 8.0)
+        res = O.solve_completed(g, 10.0, ub, gt, tol=1e-10)
+        u = res.op.evaluate(res.x, gt).reshape(-1)
+        ec.append(np.max(np.abs(u[far] - uex[far])))
+        inside = ~(np.linalg.norm(configs.grid_nodes(g), axis=1) > 0.25)
+        g2 = gt.reshape(-1).copy()
+        g2[inside] = -np.sum(gt) / inside.sum()
+        g2 = g2.reshape(gt.shape)
+        r2 = O.solve(g, configs.DIRICHLET, ub, tol=1e-10, g_grid=g2)
+        u2 = r2.op.evaluate(r2.x, g_grid=g2).reshape(-1)
+        ep.append(np.max(np.abs(u2[far] - uex[far])))
+    assert ec[0] < 0.03 and ec[1] < ec[0] / 1.8, ec
+    assert min(ep) > 0.5, ep
+
+
+def test_completed_ibdl_on_the_unit_box():
+    """Sec. 6.3 (L = 1): first order with the completed method; the
+    solvability row eta sum w Q = h^2 sum g~ holds at the solution."""
+    errs = []
+    for n in (64, 128):
+        g, gt, ub, uex, far = _exp_exterior(n, 1.0)
+        res = O.solve_completed(g, 10.0, ub, gt, tol=1e-12)
+        u = res.op.evaluate(res.x, gt).reshape(-1)
+        errs.append(np.max(np.abs(u[far] - uex[far])))
+        lhs = 10.0 * np.dot(g.weights, res.x[:g.m])
+        assert abs(lhs - g.h ** 2 * gt.sum()) < 1e-9 * abs(g.h ** 2 * gt.sum())
+    assert errs[0] < 0.02 and errs[1] < errs[0] / 1.7, errs
+
+
+# ---------------------------------------------------------------------------
+# Near-boundary values (Sec. 5.5, App. A)
+# ---------------------------------------------------------------------------
+
+
+def test_chord_projection_is_the_orthogonal_foot():
+    """x_A is the point of the chord closest to x_p: p = x2 + 0.3 (x1 - x2)
+    + an orthogonal offset gives t = 0.3 (the printed formula's sign would
+    give -0.3)."""
+    x1, x2 = np.array([0.4, 0.1]), np.array([0.1, 0.5])
+    e = x1 - x2
+    perp = np.array([-e[1], e[0]])
+    p = x2 + 0.3 * e + 0.7 * perp
+    assert abs(O._chord_t(p, x1, x2) - 0.3) < 1e-15
+
+
+def _nearest_dist(g):
+    P = configs.grid_nodes(g)
+    d2 = ((P[:, None, :] - g.X[None, :, :]) ** 2).sum(-1)
+    return np.sqrt(d2.min(axis=1)).reshape(g.n, g.n)
+
+
+def test_near_boundary_values_exact_for_linear_fields():
+    """Every step of App. A is a linear interpolation, so a linear u with
+    U_b = u on Gamma is reproduced.  Offsetting the grid field by 1 (not U_b)
+    changes exactly the inside nodes nearer than m1 h to a boundary point."""
+    g = geometry.star(128, 0.3, 0.2, 5, kappa=1e-2)
+    lin = lambda Z: 0.3 + 1.7 * Z[:, 0] - 0.9 * Z[:, 1]
+    u = lin(configs.grid_nodes(g)).reshape(g.n, g.n)
+    _, chi = O.indicator(g)
+    near = (chi == 1) & (_nearest_dist(g) < 6 * g.h)
+    out = O.near_boundary_values(g, u, lin(g.X), chi, 6, 8.0)
+    assert np.max(np.abs(out - u)) < 1e-13
+    off = O.near_boundary_values(g, u + 1.0, lin(g.X), chi, 6, 8.0)
+    assert np.all(off[~near] == u[~near] + 1.0)
+    assert np.all(np.abs(off[near] - (u[near] + 1.0)) > 1e-3)
+
+
+def test_near_boundary_values_restore_pointwise_convergence():
+    """Sec. 4.2 / 6.2: without the replacement the max error over Omega does
+    not converge (the solution jumps across Gamma); with m1 = 6, m2 = 8 it
+    converges at first order up to the boundary."""
+    raw, cor = [], []
+    for n in (64, 128, 256):
+        g = geometry.circle(n, 0.3, kappa=np.inf, spacing=0.75)
+        Xc = g.X - np.array(g.center)
+        ub = Xc[:, 0] ** 2 - Xc[:, 1] ** 2
+        res = O.solve(g, configs.DIRICHLET, ub, tol=1e-10)
+        u = res.op.evaluate(res.x).reshape(g.n, g.n)
+        _, chi = O.indicator(g)
+        P = configs.grid_nodes(g) - np.array(g.center)
+        ex = (P[:, 0] ** 2 - P[:, 1] ** 2).reshape(g.n, g.n)
+        ins = chi == 1
+        raw.append(np.max(np.abs(u - ex)[ins]))
+        cor.append(np.max(np.abs(O.near_boundary_values(g, u, ub, chi, 6, 8.0) - ex)[ins]))
+    assert min(raw) > 0.05, raw
+    assert cor[0] < 0.01 and cor[1] < cor[0] / 1.8 and cor[2] < cor[1] / 1.8, cor

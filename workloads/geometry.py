@@ -216,3 +216,11 @@ def ellipsoid(n, axes, m=None, spacing=1.5, center=(0.5, 0.5, 0.5),
     polar = np.arccos(np.clip(u[:, 2], -1.0, 1.0))
     return Geometry(3, n, box_len, tuple(origin), X, nrm, w, kappa, delta,
                     polar, tuple(center), name, {"axes": (a, b, c)})
+
+
+def exterior(geom):
+    """The same points for the exterior domain: normals negated (they point
+    out of Omega, i.e. into the curve)."""
+    import dataclasses
+    return dataclasses.replace(geom, normals=-geom.normals, name=geom.name + "-exterior",
+                               extra=dict(geom.extra, exterior=True))
