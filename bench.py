@@ -218,6 +218,93 @@ def run_batched_c4(pkg, count=256, reps=3):
                       "max": max(f["iters"] for f in infos)}}
 
 
+def _event_ms(fn, reps, flush):
+    import torch
+    fn()
+    ms = []
+    for _ in range(reps):
+        flush.fill_(3.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    return float(np.median(ms))
+
+
+def run_poisson_rows(pkg, peaks, reps=10):
+    """The Poisson-limit rows, event-timed with L2 flushed between calls:
+    the interior indicator (App. D) and the near-boundary values (App. A,
+    m1 = 6, m2 = 8) on the C2 star (N = 1024^2, M = 3525); a Dirichlet
+    Poisson solve on the same star (kappa = inf, float32-refined, tol 1e-8);
+    the completed solve of Sec. 6.3 (exterior of r = 0.25 in [-4, 4)^2,
+    N = 1024^2, eta = 10, u = exp(sin 2 pi x)), with its error against the
+    closed form away from Gamma."""
+    import dataclasses
+    import torch
+    from paper_2203_12126_gb300 import ibdl
+    dev = torch.device("cuda", torch.cuda.current_device())
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    p = configs.c2()
+    g = p.geom
+    nn = g.n * g.n
+    out = {}
+    G = pkg.Geometry.from_workload(g)
+    chi = torch.empty(nn, dtype=torch.uint8, device=dev)
+    ind_ms = _event_ms(lambda: G.indicator(None, chi), reps, flush)
+    P = configs.grid_nodes(g)
+    uin = torch.tensor(np.sin(3 * P[:, 0]) * np.cos(2 * P[:, 1]), dtype=torch.float64,
+                       device=dev)
+    ub = torch.tensor(p.bdata, dtype=torch.float64, device=dev)
+    uout = torch.empty_like(uin)
+    near_ms = _event_ms(lambda: G.near_boundary(uin, ub, chi, 6, 8.0, uout), reps, flush)
+    fixed = int((uout != uin).sum().item())
+    out["indicator_c2"] = {"us": ind_ms * 1e3, "inside_nodes": int(chi.sum().item()),
+                           "note": "spread-divergence of Q = 1, float64 Poisson solve, "
+                                   "threshold; n = 1024^2"}
+    out["near_boundary_c2"] = {"us": near_ms * 1e3, "replaced_nodes": fixed,
+                               "ns_per_replaced_node": near_ms * 1e6 / max(fixed, 1),
+                               "note": "m1 = 6, m2 = 8; the three nearest boundary points "
+                                       "of each node from a cell list (3 x 3 cells of 8 h)"}
+    G.close()
+    gp = dataclasses.replace(g, kappa=float("inf"))
+    Gp = pkg.Geometry.from_workload(gp, bc=configs.DIRICHLET, precision=ibdl.FP32_REFINED)
+    q = torch.zeros(g.m, dtype=torch.float64, device=dev)
+    info = {}
+
+    def psolve():
+        info.update(Gp.solve(ub, q, tol=1e-8))
+    ps_ms = _event_ms(psolve, 3, flush)
+    out["poisson_solve_c2"] = {"ms": ps_ms, "iters": info["iters"],
+                               "rel_residual": info["rel_residual"],
+                               "note": "Dirichlet, kappa = inf, float32-refined, tol 1e-8, "
+                                       "persistent launch"}
+    Gp.close()
+    ge, gt, ube, uex = configs.poisson_exterior(1024, 8.0)
+    Gc = pkg.Geometry.from_workload(ge, bc=configs.DIRICHLET, precision=ibdl.FP32_REFINED,
+                                    eta=10.0)
+    z = torch.zeros(ge.m + 1, dtype=torch.float64, device=dev)
+    ubt = torch.tensor(ube, dtype=torch.float64, device=dev)
+    gtt = torch.tensor(gt.reshape(-1), dtype=torch.float64, device=dev)
+    cinfo = {}
+
+    def csolve():
+        cinfo.update(Gc.solve(ubt, z, g_grid=gtt, tol=1e-8))
+    cs_ms = _event_ms(csolve, 3, flush)
+    u = torch.empty(ge.n * ge.n, dtype=torch.float64, device=dev)
+    Gc.evaluate(z, u, g_grid=gtt)
+    Pe = configs.grid_nodes(ge)
+    far = np.linalg.norm(Pe, axis=1) > 0.25 + 6 * ge.h
+    err = float(np.max(np.abs(u.cpu().numpy()[far] - uex[far])))
+    out["completed_solve_sec6_3"] = {"ms": cs_ms, "iters": cinfo["iters"], "m": ge.m,
+                                     "max_err_away_from_gamma": err,
+                                     "note": "L = 8, N = 1024^2, eta = 10, float32-refined, "
+                                             "tol 1e-8, launch-based engine"}
+    Gc.close()
+    return out
+
+
 def problems():
     return [configs.c2(bc=configs.DIRICHLET), configs.c2(bc=configs.NEUMANN)]
 
@@ -657,6 +744,7 @@ def main():
 
     batched_c4 = run_batched_c4(pkg) if not args.no_batched else None
     c3_solve = run_c3_solve(pkg) if not args.no_matvec else None
+    poisson_rows = run_poisson_rows(pkg, peaks) if not args.no_matvec else None
 
     serving = None
     if args.serve_requests > 0:
@@ -707,6 +795,7 @@ def main():
             "matvec": matvec,
             "batched_c4": batched_c4,
             "c3_solve": c3_solve,
+            "poisson_rows": poisson_rows,
             "serving": serving,
             "gpu_launches": int(launches),
             "wall_s_timed": wall,

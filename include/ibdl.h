@@ -98,11 +98,32 @@ typedef struct {
   const double* nz;
   const double* w;      /* quadrature weights Delta s_i (arclength, Sec. 5.2)
                            or dA_i (area, Sec. 6.7) */
-  double kappa;         /* > 0, finite: L' = I - kappa Delta_h, k^2 = 1/kappa */
+  double kappa;         /* > 0: L' = I - kappa Delta_h, k^2 = 1/kappa.
+                           +INFINITY selects the Poisson equation (k = 0,
+                           Sec. 5.4): kappa L'^{-1} becomes -Delta_0^{-1}, the
+                           inverse of Delta_h returning the mean-zero field
+                           (the k = 0 mode of every source is dropped, so a
+                           forcing g~ must satisfy the solvability condition
+                           of App. C, e.g. through the choice of g_e).
+                           Dirichlet only. */
   int32_t delta;        /* ibdl_delta */
   int32_t bc;           /* ibdl_bc: selects A_D or A_N */
   int32_t precision;    /* ibdl_precision */
-  int32_t reserved;
+  int32_t reserved;     /* 0 */
+  double eta;           /* completed IBDL (Sec. 5.4 eq. (ibdl completed),
+                           App. C): weight of the single layer eta S Q added
+                           to S~ Q.  0 = the plain method.  eta > 0 needs
+                           kappa = +INFINITY.  The unknown is then
+                           z = (Q, u_bar), length m + 1 (z[m] = u_bar, the
+                           field's mean), and the system is
+                             Q/2 - S* Delta_0^{-1} (S~ + eta S) Q + u_bar
+                                 = U_b - S* Delta_0^{-1} g~
+                             eta sum_i w_i Q_i = h^d sum_j g~_j.
+                           ibdl_apply, ibdl_solve (q_out, x0) and
+                           ibdl_evaluate (q) then take length m + 1 vectors;
+                           such geometries solve on the launch-based engine
+                           and are not accepted by ibdl_solve_batched or the
+                           server. */
 } ibdl_geometry_desc;
 
 typedef struct {
@@ -138,7 +159,9 @@ void ibdl_solve_opts_default(ibdl_solve_opts* opts);
  * weights, the FFT twiddles and the Helmholtz symbol and allocates all
  * workspaces (grid, spectrum, Krylov basis).  Synchronises `stream` before
  * returning.  Errors: IBDL_ERR_INVALID_ARG (n not a power of two or out of
- * range, m < 1, kappa <= 0 or non-finite, unknown enum, NULL pointer),
+ * range, m < 1, kappa <= 0 or NaN, eta < 0 or non-finite, eta > 0 with
+ * finite kappa, unknown enum, NULL pointer), IBDL_ERR_UNSUPPORTED (kappa = inf
+ * with the Neumann condition),
  * IBDL_ERR_OOM, IBDL_ERR_CUDA.  *out is set only on success. */
 ibdl_status ibdl_create_geometry(const ibdl_geometry_desc* desc, void* stream,
                                  ibdl_geometry* out);
@@ -316,6 +339,38 @@ ibdl_status ibdl_helmholtz(ibdl_geometry g, const double* f, double* v_out,
                            int32_t precision, void* stream);
 ibdl_status ibdl_interp(ibdl_geometry g, const double* u, double* y_out,
                         int32_t precision, void* stream);
+
+/* Interior indicator of the discretised boundary (App. D), float64.  Solves
+ * Delta_h u + S~ 1 = 0 for the mean-zero u (Q = 1, the Poisson solve
+ * whatever the geometry's kappa), then
+ *   chi_h = u - u(node 0)     (the box corner: far from Gamma, about 0)
+ *   chi   = 1 where chi_h > 1/2, else 0
+ * chi_h is about 1/2 on Gamma and about 1 inside a closed curve whose normals
+ * point out of it.  chi_h_out: n^d doubles, chi_out: n^d bytes (x fastest),
+ * host or device, either may be NULL (not both).  Errors:
+ * IBDL_ERR_INVALID_ARG (no output), IBDL_ERR_CUDA. */
+ibdl_status ibdl_indicator(ibdl_geometry g, double* chi_h_out, uint8_t* chi_out,
+                           void* stream);
+
+/* Near-boundary values (Sec. 5.5, App. A), 2D, float64.  u_out = u_in,
+ * except at the nodes x_p with inside = 1 whose nearest boundary point is
+ * closer than m1 h.  Those take the linear interpolation between
+ *   x_A: the orthogonal foot of x_p on the chord of its two nearest
+ *        boundary points (the two of the three nearest that lie farthest
+ *        apart when the foot falls outside the chord, clamped to it), with
+ *        the value interpolated from ub at those two points;
+ *   x_B = x_A + m2 h (x_p - x_A) / |x_p - x_A|, with the bilinear
+ *        interpolation of u_in in its grid cell.
+ * Ties in distance go to the lower point index.  ub: the boundary values
+ * (U_b for Dirichlet, the solved U for Neumann), length m.  inside: n^2
+ * bytes, 1 = node of Omega (e.g. ibdl_indicator's chi, or 1 - chi for an
+ * exterior domain).  u_in, u_out: n^2 doubles, must not overlap.  All
+ * host or device.  m1 in 1..n/2 (the paper uses 6), m2 > 0 (the paper uses
+ * m1 + 2).  Errors: IBDL_ERR_UNSUPPORTED (3D), IBDL_ERR_INVALID_ARG (m < 3,
+ * m1 or m2 out of range, NULL or overlapping arrays), IBDL_ERR_CUDA. */
+ibdl_status ibdl_near_boundary(ibdl_geometry g, const double* u_in, const double* ub,
+                               const uint8_t* inside, int32_t m1, double m2, double* u_out,
+                               void* stream);
 
 /* Read-only facts about a handle. */
 typedef struct {

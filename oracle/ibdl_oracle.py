@@ -509,7 +509,7 @@ def indicator(geom):
 # ---------------------------------------------------------------------------
 
 
-def near_boundary_values(geom, u, ub, inside, m1, m2):
+def near_boundary_values(geom, u, ub, inside, m1, m2, nodes=None):
     """Replace u at the nodes of Omega within m1 meshwidths of Gamma (App. A).
 
     For a node x_p with inside = 1 whose nearest boundary point is closer than
@@ -524,7 +524,9 @@ def near_boundary_values(geom, u, ub, inside, m1, m2):
       6. u(x_p) = u(x_A)|x_B - x_p| / |x_B - x_A| + u(x_B)|x_A - x_p| / |x_B - x_A|.
     A node on the chord (|x_p - x_A| = 0) takes u(x_A).  Other nodes keep
     their value.  u: grid (n, n); ub: boundary values (the data U_b for
-    Dirichlet, the solved U for Neumann); inside: (n, n) 0/1."""
+    Dirichlet, the solved U for Neumann); inside: (n, n) 0/1.  ``nodes``
+    (flat indices iy * n + ix) restricts the work to a sample of nodes; the
+    others are returned unchanged."""
     box = Box.of(geom)
     assert box.d == 2
     n, h = box.n, box.h
@@ -535,51 +537,52 @@ def near_boundary_values(geom, u, ub, inside, m1, m2):
     ins = np.asarray(inside).reshape(n, n)
     thresh = (m1 * h) * (m1 * h)
     ox, oy = float(box.o[0]), float(box.o[1])
-    for iy in range(n):
+    todo = range(n * n) if nodes is None else sorted(int(j) for j in nodes)
+    for j in todo:
+        iy, ix = divmod(j, n)
+        if not ins[iy, ix]:
+            continue
         py = oy + iy * h
         dy = py - X[:, 1]
-        for ix in range(n):
-            if not ins[iy, ix]:
-                continue
-            px = ox + ix * h
-            dx = px - X[:, 0]
-            d2 = dx * dx + dy * dy
-            order = np.argsort(d2, kind="stable")
-            if not d2[order[0]] < thresh:
-                continue
-            a, b = int(order[0]), int(order[1])
-            p = np.array([px, py])
-            t = _chord_t(p, X[a], X[b])
-            if not (0.0 <= t <= 1.0):
-                c = int(order[2])
-                best = -1.0
-                for i, j in ((a, b), (a, c), (b, c)):
-                    e = X[i] - X[j]
-                    s = e[0] * e[0] + e[1] * e[1]
-                    if s > best:
-                        best, pa, pb = s, i, j
-                a, b = pa, pb
-                t = min(max(_chord_t(p, X[a], X[b]), 0.0), 1.0)
-            x1, x2 = X[a], X[b]
-            xA = x2 + t * (x1 - x2)
-            L12 = np.linalg.norm(x2 - x1)
-            uA = ub[a] * np.linalg.norm(xA - x2) / L12 + ub[b] * np.linalg.norm(xA - x1) / L12
-            dA = np.linalg.norm(p - xA)
-            if dA == 0.0:
-                out[iy, ix] = uA
-                continue
-            xB = xA + (p - xA) / dA * (m2 * h)
-            rx, ry = (xB[0] - ox) / h, (xB[1] - oy) / h
-            jx, jy = math.floor(rx), math.floor(ry)
-            fx, fy = rx - jx, ry - jy
-            u00 = uin[jy % n, jx % n]
-            u10 = uin[jy % n, (jx + 1) % n]
-            u01 = uin[(jy + 1) % n, jx % n]
-            u11 = uin[(jy + 1) % n, (jx + 1) % n]
-            uB = (fx * fy * u11 + fy * (1.0 - fx) * u01 + fx * (1.0 - fy) * u10
-                  + (1.0 - fx - fy + fx * fy) * u00)
-            LAB = np.linalg.norm(xB - xA)
-            out[iy, ix] = uA * np.linalg.norm(xB - p) / LAB + uB * dA / LAB
+        px = ox + ix * h
+        dx = px - X[:, 0]
+        d2 = dx * dx + dy * dy
+        order = np.argsort(d2, kind="stable")
+        if not d2[order[0]] < thresh:
+            continue
+        a, b = int(order[0]), int(order[1])
+        p = np.array([px, py])
+        t = _chord_t(p, X[a], X[b])
+        if not (0.0 <= t <= 1.0):
+            c = int(order[2])
+            best = -1.0
+            for ia, ib in ((a, b), (a, c), (b, c)):
+                e = X[ia] - X[ib]
+                sep = e[0] * e[0] + e[1] * e[1]
+                if sep > best:
+                    best, pa, pb = sep, ia, ib
+            a, b = pa, pb
+            t = min(max(_chord_t(p, X[a], X[b]), 0.0), 1.0)
+        x1, x2 = X[a], X[b]
+        xA = x2 + t * (x1 - x2)
+        L12 = np.linalg.norm(x2 - x1)
+        uA = ub[a] * np.linalg.norm(xA - x2) / L12 + ub[b] * np.linalg.norm(xA - x1) / L12
+        dA = np.linalg.norm(p - xA)
+        if dA == 0.0:
+            out[iy, ix] = uA
+            continue
+        xB = xA + (p - xA) / dA * (m2 * h)
+        rx, ry = (xB[0] - ox) / h, (xB[1] - oy) / h
+        jx, jy = math.floor(rx), math.floor(ry)
+        fx, fy = rx - jx, ry - jy
+        u00 = uin[jy % n, jx % n]
+        u10 = uin[jy % n, (jx + 1) % n]
+        u01 = uin[(jy + 1) % n, jx % n]
+        u11 = uin[(jy + 1) % n, (jx + 1) % n]
+        uB = (fx * fy * u11 + fy * (1.0 - fx) * u01 + fx * (1.0 - fy) * u10
+              + (1.0 - fx - fy + fx * fy) * u00)
+        LAB = np.linalg.norm(xB - xA)
+        out[iy, ix] = uA * np.linalg.norm(xB - p) / LAB + uB * dA / LAB
     return out
 
 

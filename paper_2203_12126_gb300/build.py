@@ -18,6 +18,9 @@ LIB = os.path.join(HERE, "libibdl.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
          "--expt-relaxed-constexpr"]
+# Per-file flags: the near-boundary kernel rounds each operation on its own
+# (no fused multiply-add), so its decisions match a plain IEEE evaluation.
+FILE_FLAGS = {"k_near.cu": ["-fmad=false"]}
 
 
 def nvcc() -> str:
@@ -49,7 +52,8 @@ def build(verbose: bool = False, force: bool = False, ptxas_info: bool = False) 
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if force or not _newer(obj, [src] + headers):
-            cmd = [cc, *ARCH, *FLAGS, "-c", src, "-o", obj]
+            cmd = [cc, *ARCH, *FLAGS, *FILE_FLAGS.get(os.path.basename(src), []),
+                   "-c", src, "-o", obj]
             if ptxas_info:
                 cmd.insert(1, "-Xptxas=-v")
             jobs.append(cmd)

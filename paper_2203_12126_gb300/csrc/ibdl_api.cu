@@ -163,6 +163,11 @@ constexpr int64_t kMaxPoints = 65535LL * kSolverThreads;
 struct ibdl_geometry_s {
   GridDesc grid;
   int bc = 0, precision = 0, m = 0;
+  // completed IBDL (eta > 0, Poisson limit): the system unknown is
+  // (Q, u_bar), nsys = m + 1; otherwise nsys = m
+  int nsys = 0;
+  double eta = 0;
+  double* cpart = nullptr;  // kRedBlocks + 1 reduction partials
   Bins bins;
   PointData pd;
   SpectralWs<double> ws64;
@@ -402,10 +407,52 @@ ibdl_status matvec_prec(ibdl_geometry_s* g, int prec, const double* q, double* y
   return matvec<double>(g, q, y, st);
 }
 
+double cell_volume(const GridDesc& g) {
+  return g.dim == 3 ? g.h * g.h * g.h : g.h * g.h;
+}
+
+// Completed IBDL (Sec. 5.4, App. C), z = (Q, u_bar):
+//   y[0:m] = Q/2 + S* (-Delta_0^{-1}) (S~ + eta S) Q + u_bar,  y[m] = eta sum w_i Q_i.
+// The weight sum and u_bar are read before the interpolation writes y.
+template <typename T>
+ibdl_status completed_matvec(ibdl_geometry_s* g, const double* q, double* y, cudaStream_t st) {
+  IBDL_CU(launch_completed_head(g->m, g->pd.w, q, g->cpart, st));
+  SpreadSrc src;
+  src.q_div = q;
+  src.coef_div = 1.0;
+  src.v_plain = q;
+  src.coef_plain = g->eta;
+  SpectralWs<T>& ws = wsof<T>(g);
+  IBDL_TRY((field_solve<T, T>(g, src, ws.grid, st, true)));
+  IBDL_CU(launch_interp<T>(g->grid, g->pd, ws.grid, q, 0.5, y, st));
+  // pd.w holds w_i / h^d
+  IBDL_CU(launch_completed_tail(g->m, y, g->cpart, g->eta * cell_volume(g->grid), st));
+  return IBDL_OK;
+}
+
+// The operator of the geometry's boundary system (length nsys).
+ibdl_status sys_matvec(ibdl_geometry_s* g, int prec, const double* q, double* y,
+                       cudaStream_t st) {
+  if (g->eta <= 0) return matvec_prec(g, prec, q, y, st);
+  if (prec == IBDL_FP32_REFINED) {
+    IBDL_TRY(ensure32(g, st));
+    return completed_matvec<float>(g, q, y, st);
+  }
+  return completed_matvec<double>(g, q, y, st);
+}
+
 // b = right-hand side of the boundary system (float64).
 ibdl_status build_rhs(ibdl_geometry_s* g, const double* bdata, const double* ggrid, double* b,
                       cudaStream_t st) {
   if (g->bc == IBDL_DIRICHLET) {
+    if (g->eta > 0) {
+      // completed system: last row h^d sum g~ (App. C solvability condition)
+      if (ggrid)
+        IBDL_CU(launch_scaled_sum(g->ncells, ggrid, cell_volume(g->grid), g->cpart, b + g->m,
+                                  st));
+      else
+        IBDL_CU(cudaMemsetAsync(b + g->m, 0, sizeof(double), st));
+    }
     if (!ggrid) {
       IBDL_CU(cudaMemcpyAsync(b, bdata, sizeof(double) * g->m, cudaMemcpyDeviceToDevice, st));
       return IBDL_OK;
@@ -455,11 +502,11 @@ ibdl_status gmres(ibdl_geometry_s* g, int prec, const double* b, double* x, bool
   bool est_converged = false;
   for (;;) {
     if (zero) {
-      IBDL_CU(cudaMemcpyAsync(g->vr, b, sizeof(double) * g->m, cudaMemcpyDeviceToDevice, st));
+      IBDL_CU(cudaMemcpyAsync(g->vr, b, sizeof(double) * g->nsys, cudaMemcpyDeviceToDevice, st));
     } else {
-      IBDL_TRY(matvec_prec(g, prec, x, g->vt, st));
+      IBDL_TRY(sys_matvec(g, prec, x, g->vt, st));
       run->matvecs++;
-      IBDL_CU(launch_axpby(g->m, 1.0, b, -1.0, g->vt, g->vr, st));
+      IBDL_CU(launch_axpby(g->nsys, 1.0, b, -1.0, g->vt, g->vr, st));
     }
     if (est_converged && !true_check) break;
     IBDL_CU(krylov_start(k, g->vr, nullptr, st));
@@ -473,7 +520,7 @@ ibdl_status gmres(ibdl_geometry_s* g, int prec, const double* b, double* x, bool
     bool breakdown = false;
     est_converged = false;
     for (int j = 0; j < restart; ++j) {
-      IBDL_TRY(matvec_prec(g, prec, k.V + (size_t)j * k.ld, k.V + (size_t)(j + 1) * k.ld, st));
+      IBDL_TRY(sys_matvec(g, prec, k.V + (size_t)j * k.ld, k.V + (size_t)(j + 1) * k.ld, st));
       run->matvecs++;
       IBDL_CU(krylov_arnoldi(k, j, bnorm, st));
       IBDL_CU(cudaMemcpyAsync(g->host_scal, k.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost,
@@ -752,8 +799,14 @@ ibdl_status ibdl_create_geometry(const ibdl_geometry_desc* d, void* stream, ibdl
     return fail(IBDL_ERR_INVALID_ARG, "m out of range (1 .. 16776960)");
   if (!(d->box_len > 0) || !isfinite(d->box_len))
     return fail(IBDL_ERR_INVALID_ARG, "box_len must be positive and finite");
-  if (!(d->kappa > 0) || !isfinite(d->kappa))
-    return fail(IBDL_ERR_INVALID_ARG, "kappa must be positive and finite");
+  if (!(d->kappa > 0))
+    return fail(IBDL_ERR_INVALID_ARG, "kappa must be positive (or +inf for Poisson)");
+  if (isinf(d->kappa) && d->bc != IBDL_DIRICHLET)
+    return fail(IBDL_ERR_UNSUPPORTED, "the Poisson limit (kappa = inf) is Dirichlet only");
+  if (!(d->eta >= 0) || !isfinite(d->eta))
+    return fail(IBDL_ERR_INVALID_ARG, "eta must be finite and >= 0");
+  if (d->eta > 0 && !isinf(d->kappa))
+    return fail(IBDL_ERR_INVALID_ARG, "eta > 0 (completed IBDL) needs kappa = inf");
   if (d->delta != IBDL_DELTA_PESKIN4 && d->delta != IBDL_DELTA_COS4)
     return fail(IBDL_ERR_INVALID_ARG, "unknown delta");
   if (d->bc != IBDL_DIRICHLET && d->bc != IBDL_NEUMANN)
@@ -774,6 +827,8 @@ ibdl_status ibdl_create_geometry(const ibdl_geometry_desc* d, void* stream, ibdl
   };
   const int m = (int)d->m;
   g->m = m;
+  g->eta = d->eta;
+  g->nsys = d->eta > 0 ? m + 1 : m;
   g->bc = d->bc;
   g->precision = d->precision;
   GridDesc& gd = g->grid;
@@ -783,6 +838,7 @@ ibdl_status ibdl_create_geometry(const ibdl_geometry_desc* d, void* stream, ibdl
   while ((1 << gd.log2n) < n) gd.log2n++;
   gd.h = d->box_len / n;
   gd.kappa = d->kappa;
+  gd.poisson = isinf(d->kappa) ? 1 : 0;
   gd.delta = d->delta;
   for (int c = 0; c < 3; ++c) gd.origin[c] = c < dim ? d->origin[c] : 0.0;
   g->ncells = (int64_t)n * n * (dim == 3 ? n : 1);
@@ -882,8 +938,8 @@ ibdl_status ibdl_create_geometry(const ibdl_geometry_desc* d, void* stream, ibdl
 
   // Krylov workspace (float64, restart up to 64)
   KrylovWs& k = g->kry;
-  k.m = m;
-  k.ld = (m + 31) / 32 * 32;
+  k.m = g->nsys;
+  k.ld = (g->nsys + 31) / 32 * 32;
   k.restart = 64;
   k.nblk = (m + 2047) / 2048;
   if (k.nblk > 148) k.nblk = 148;
@@ -905,6 +961,7 @@ ibdl_status ibdl_create_geometry(const ibdl_geometry_desc* d, void* stream, ibdl
   g->stage_a = vecs + 5 * (size_t)k.ld;
   g->stage_b = vecs + 6 * (size_t)k.ld;
   if ((s = g->alloc(&g->d_flag, (size_t)4))) return cleanup(s);
+  if ((s = g->alloc(&g->cpart, (size_t)kRedBlocks + 1))) return cleanup(s);
   g->nchunk = (m + kSolverThreads - 1) / kSolverThreads;
   if ((s = g->alloc(&g->ppart, (size_t)3 * g->nchunk * (k.restart + 2)))) return cleanup(s);
   if ((s = g->alloc(&g->d_hist, (size_t)kHistCap))) return cleanup(s);
@@ -936,12 +993,12 @@ ibdl_status ibdl_apply_precision(ibdl_geometry g, const double* q, double* y, in
     return fail(IBDL_ERR_INVALID_ARG, "unknown precision");
   cudaStream_t st = (cudaStream_t)stream;
   const double* qd;
-  IBDL_TRY(dev_in(q, g->m, g->stage_a, &qd, st));
+  IBDL_TRY(dev_in(q, g->nsys, g->stage_a, &qd, st));
   const bool ydev = is_device_ptr(y);
   double* yd = ydev ? y : g->stage_b;
-  IBDL_TRY(matvec_prec(g, precision, qd, yd, st));
+  IBDL_TRY(sys_matvec(g, precision, qd, yd, st));
   if (!ydev) {
-    IBDL_CU(cudaMemcpyAsync(y, yd, sizeof(double) * g->m, cudaMemcpyDeviceToHost, st));
+    IBDL_CU(cudaMemcpyAsync(y, yd, sizeof(double) * g->nsys, cudaMemcpyDeviceToHost, st));
     IBDL_CU(cudaStreamSynchronize(st));
   }
   return IBDL_OK;
@@ -966,8 +1023,11 @@ ibdl_status ibdl_solve(ibdl_geometry g, const double* bdata, const double* g_gri
   if (o.max_refine < 1) o.max_refine = 1;
   if (!(o.inner_tol > 0) || o.inner_tol >= 1) o.inner_tol = 1e-5;
   if (o.engine != 0 && o.engine != 1) return fail(IBDL_ERR_INVALID_ARG, "engine is 0 or 1");
+  // the completed system (length m + 1) runs on the launch-based engine
+  if (g->eta > 0) o.engine = 1;
   cudaStream_t st = (cudaStream_t)stream;
   const int m = g->m;
+  const int ns = g->nsys;
   IBDL_TRY(g->ensure_host());
   // inputs
   IBDL_CU(cudaMemcpyAsync(g->stage_a, bdata, sizeof(double) * m, cudaMemcpyDefault, st));
@@ -980,11 +1040,11 @@ ibdl_status ibdl_solve(ibdl_geometry g, const double* bdata, const double* g_gri
   if (!rhs_in_kernel) IBDL_TRY(build_rhs(g, g->stage_a, gg, g->vb, st));
   bool x_zero = true;
   if (o.x0) {
-    IBDL_CU(cudaMemcpyAsync(g->vx, o.x0, sizeof(double) * m, cudaMemcpyDefault, st));
-    IBDL_CU(launch_nonfinite_check(m, g->vx, g->d_flag, st));
+    IBDL_CU(cudaMemcpyAsync(g->vx, o.x0, sizeof(double) * ns, cudaMemcpyDefault, st));
+    IBDL_CU(launch_nonfinite_check(ns, g->vx, g->d_flag, st));
     x_zero = false;
   } else {
-    IBDL_CU(cudaMemsetAsync(g->vx, 0, sizeof(double) * m, st));
+    IBDL_CU(cudaMemsetAsync(g->vx, 0, sizeof(double) * ns, st));
   }
   if (o.engine == 0) {
     // one persistent launch runs the whole solve; the host waits once
@@ -1025,7 +1085,7 @@ ibdl_status ibdl_solve(ibdl_geometry g, const double* bdata, const double* g_gri
   int refine = 0;
   ibdl_status status = IBDL_OK;
   if (bnorm == 0.0) {
-    IBDL_CU(cudaMemsetAsync(g->vx, 0, sizeof(double) * m, st));
+    IBDL_CU(cudaMemsetAsync(g->vx, 0, sizeof(double) * ns, st));
     run.rel = 0;
   } else if (g->precision == IBDL_FP64) {
     status = gmres(g, IBDL_FP64, g->vb, g->vx, x_zero, bnorm, o.tol, o.restart, o.max_iters,
@@ -1034,11 +1094,11 @@ ibdl_status ibdl_solve(ibdl_geometry g, const double* bdata, const double* g_gri
     // FP32 operator inside GMRES (float64 Arnoldi/Givens), float64 residuals
     // outside: r = b - A64 x;  solve A32 d = r to inner_tol;  x += d.
     if (x_zero) {
-      IBDL_CU(cudaMemcpyAsync(g->vr, g->vb, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
+      IBDL_CU(cudaMemcpyAsync(g->vr, g->vb, sizeof(double) * ns, cudaMemcpyDeviceToDevice, st));
     } else {
-      IBDL_TRY(matvec_prec(g, IBDL_FP64, g->vx, g->vt, st));
+      IBDL_TRY(sys_matvec(g, IBDL_FP64, g->vx, g->vt, st));
       run.matvecs++;
-      IBDL_CU(launch_axpby(m, 1.0, g->vb, -1.0, g->vt, g->vr, st));
+      IBDL_CU(launch_axpby(ns, 1.0, g->vb, -1.0, g->vt, g->vr, st));
     }
     double rnorm = 0;
     IBDL_TRY(vec_norm(g, g->vr, &rnorm, st));
@@ -1058,13 +1118,13 @@ ibdl_status ibdl_solve(ibdl_geometry g, const double* bdata, const double* g_gri
         break;
       }
       // inner solve: the residual vector is moved to vd's right-hand side slot
-      IBDL_CU(cudaMemcpyAsync(g->vt, g->vr, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
-      IBDL_CU(cudaMemsetAsync(g->vd, 0, sizeof(double) * m, st));
+      IBDL_CU(cudaMemcpyAsync(g->vt, g->vr, sizeof(double) * ns, cudaMemcpyDeviceToDevice, st));
+      IBDL_CU(cudaMemsetAsync(g->vd, 0, sizeof(double) * ns, st));
       GmresRun inner;
       inner.iters = run.iters;
       const double itol = fmax(o.inner_tol, 0.5 * o.tol * bnorm / rnorm);
       double* rhs = g->stage_b;  // keep r intact while gmres reuses vr/vt
-      IBDL_CU(cudaMemcpyAsync(rhs, g->vr, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
+      IBDL_CU(cudaMemcpyAsync(rhs, g->vr, sizeof(double) * ns, cudaMemcpyDeviceToDevice, st));
       ibdl_status si = gmres(g, IBDL_FP32_REFINED, rhs, g->vd, true, rnorm, itol, o.restart,
                              o.max_iters, false, &inner, st);
       run.iters = inner.iters;
@@ -1073,16 +1133,16 @@ ibdl_status ibdl_solve(ibdl_geometry g, const double* bdata, const double* g_gri
         status = si;
         break;
       }
-      IBDL_CU(launch_axpby(m, 1.0, g->vx, 1.0, g->vd, g->vx, st));
-      IBDL_TRY(matvec_prec(g, IBDL_FP64, g->vx, g->vt, st));
+      IBDL_CU(launch_axpby(ns, 1.0, g->vx, 1.0, g->vd, g->vx, st));
+      IBDL_TRY(sys_matvec(g, IBDL_FP64, g->vx, g->vt, st));
       run.matvecs++;
-      IBDL_CU(launch_axpby(m, 1.0, g->vb, -1.0, g->vt, g->vr, st));
+      IBDL_CU(launch_axpby(ns, 1.0, g->vb, -1.0, g->vt, g->vr, st));
       IBDL_TRY(vec_norm(g, g->vr, &rnorm, st));
       run.rel = rnorm / bnorm;
       run.hist.push_back(run.rel);
     }
   }
-  IBDL_CU(cudaMemcpyAsync(q_out, g->vx, sizeof(double) * m, cudaMemcpyDefault, st));
+  IBDL_CU(cudaMemcpyAsync(q_out, g->vx, sizeof(double) * ns, cudaMemcpyDefault, st));
   IBDL_CU(cudaStreamSynchronize(st));
   if (info) {
     memset(info, 0, sizeof(*info));
@@ -1105,7 +1165,7 @@ ibdl_status ibdl_evaluate(ibdl_geometry g, const double* q, const double* vb, co
   if (g->bc == IBDL_DIRICHLET && vb) return fail(IBDL_ERR_INVALID_ARG, "vb is Neumann-only");
   cudaStream_t st = (cudaStream_t)stream;
   const int m = g->m;
-  IBDL_CU(cudaMemcpyAsync(g->stage_a, q, sizeof(double) * m, cudaMemcpyDefault, st));
+  IBDL_CU(cudaMemcpyAsync(g->stage_a, q, sizeof(double) * g->nsys, cudaMemcpyDefault, st));
   if (vb) IBDL_CU(cudaMemcpyAsync(g->stage_b, vb, sizeof(double) * m, cudaMemcpyDefault, st));
   const double* gg = nullptr;
   IBDL_TRY(grid_in(g, g_grid, &gg, st));
@@ -1116,6 +1176,11 @@ ibdl_status ibdl_evaluate(ibdl_geometry g, const double* q, const double* vb, co
     src.v_plain = g->stage_b;
     src.coef_plain = 1.0;
   }
+  if (g->eta > 0) {
+    // completed: u = -Delta_0^{-1} ((S~ + eta S) Q - g~) + u_bar
+    src.v_plain = g->stage_a;
+    src.coef_plain = g->eta;
+  }
   if (gg) {
     src.f_grid = gg;
     src.coef_grid = -1.0;
@@ -1123,6 +1188,7 @@ ibdl_status ibdl_evaluate(ibdl_geometry g, const double* q, const double* vb, co
   const bool udev = is_device_ptr(u_out);
   double* ud = udev ? u_out : g->ws64.grid;
   IBDL_TRY((field_solve<double, double>(g, src, ud, st)));
+  if (g->eta > 0) IBDL_CU(launch_add_scalar(g->ncells, ud, g->stage_a + m, st));
   if (!udev) {
     IBDL_CU(cudaMemcpyAsync(u_out, ud, sizeof(double) * g->ncells, cudaMemcpyDeviceToHost, st));
     IBDL_CU(cudaStreamSynchronize(st));
@@ -1241,6 +1307,87 @@ ibdl_status ibdl_interp(ibdl_geometry g, const double* u, double* y_out, int32_t
   return IBDL_OK;
 }
 
+ibdl_status ibdl_indicator(ibdl_geometry g, double* chi_h_out, uint8_t* chi_out, void* stream) {
+  g_err.clear();
+  IBDL_TRY(check_handle(g));
+  if (!chi_h_out && !chi_out) return fail(IBDL_ERR_INVALID_ARG, "no output requested");
+  cudaStream_t st = (cudaStream_t)stream;
+  // Delta u = -S~ 1: spread-divergence of Q = 1, then the mean-zero Poisson
+  // solve whatever the geometry's kappa
+  IBDL_CU(launch_fill(g->m, g->stage_a, 1.0, st));
+  SpreadSrc src;
+  src.q_div = g->stage_a;
+  src.coef_div = 1.0;
+  const GridDesc saved = g->grid;
+  g->grid.poisson = 1;
+  const ibdl_status fs = field_solve<double, double>(g, src, g->ws64.grid, st);
+  g->grid = saved;
+  IBDL_TRY(fs);
+  double* hd = nullptr;
+  if (chi_h_out) IBDL_TRY(grid_out_begin(g, chi_h_out, &hd));
+  unsigned char* cd = nullptr;
+  const bool cdev = chi_out && is_device_ptr(chi_out);
+  cudaMemPool_t pool;
+  if (chi_out && !cdev) {
+    IBDL_CU(workspace_pool(&pool));
+    IBDL_CU(cudaMallocFromPoolAsync((void**)&cd, (size_t)g->ncells, pool, st));
+  } else {
+    cd = reinterpret_cast<unsigned char*>(chi_out);
+  }
+  cudaError_t e = launch_indicator(g->ncells, g->ws64.grid, hd, cd, st);
+  if (!e && chi_out && !cdev) {
+    e = cudaMemcpyAsync(chi_out, cd, (size_t)g->ncells, cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(cd, st);
+    if (!e) e = cudaStreamSynchronize(st);
+  }
+  if (e) return cuda_fail(e, "indicator");
+  if (chi_h_out) IBDL_TRY(grid_out_end(g, chi_h_out, hd, st));
+  return IBDL_OK;
+}
+
+ibdl_status ibdl_near_boundary(ibdl_geometry g, const double* u_in, const double* ub,
+                               const uint8_t* inside, int32_t m1, double m2, double* u_out,
+                               void* stream) {
+  g_err.clear();
+  IBDL_TRY(check_handle(g));
+  if (!u_in || !ub || !inside || !u_out) return fail(IBDL_ERR_INVALID_ARG, "NULL argument");
+  if (g->grid.dim != 2) return fail(IBDL_ERR_UNSUPPORTED, "near-boundary values are 2D");
+  if (g->m < 3) return fail(IBDL_ERR_INVALID_ARG, "at least three boundary points are needed");
+  if (m1 < 1 || m1 > g->grid.n / 2) return fail(IBDL_ERR_INVALID_ARG, "m1 in 1 .. n/2");
+  if (!(m2 > 0) || !isfinite(m2)) return fail(IBDL_ERR_INVALID_ARG, "m2 must be > 0");
+  const int64_t nn = g->ncells;
+  if (u_out < u_in + nn && u_in < u_out + nn)
+    return fail(IBDL_ERR_INVALID_ARG, "u_in and u_out overlap");
+  cudaStream_t st = (cudaStream_t)stream;
+  const double* ubd;
+  IBDL_TRY(dev_in(ub, g->m, g->stage_a, &ubd, st));
+  const double* uind;
+  IBDL_TRY(grid_in(g, u_in, &uind, st));
+  const bool udev = is_device_ptr(u_out);
+  double* uoutd = udev ? u_out : g->ws64.grid;
+  const bool idev = is_device_ptr(inside);
+  // scratch: the kernels' buffers, then a copy of a host mask
+  const size_t kb = (near_scratch_bytes(g->grid.n, g->m, m1) + 15) / 16 * 16;
+  const size_t bytes = kb + (idev ? 0 : (size_t)nn);
+  cudaMemPool_t pool;
+  IBDL_CU(workspace_pool(&pool));
+  unsigned char* scratch = nullptr;
+  IBDL_CU(cudaMallocFromPoolAsync((void**)&scratch, bytes, pool, st));
+  const unsigned char* insd = inside;
+  cudaError_t e = cudaSuccess;
+  if (!idev) {
+    e = cudaMemcpyAsync(scratch + kb, inside, (size_t)nn, cudaMemcpyHostToDevice, st);
+    insd = scratch + kb;
+  }
+  if (!e) e = launch_near_boundary(g->grid, g->pd, ubd, uind, insd, m1, m2, uoutd, scratch, st);
+  if (!e && !udev)
+    e = cudaMemcpyAsync(u_out, uoutd, sizeof(double) * nn, cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(scratch, st);
+  if (!e && (!udev || !idev)) e = cudaStreamSynchronize(st);
+  if (e) return cuda_fail(e, "near-boundary values");
+  return IBDL_OK;
+}
+
 ibdl_status ibdl_get_geometry_info(ibdl_geometry g, ibdl_geometry_info* info) {
   IBDL_TRY(check_handle(g));
   if (!info) return fail(IBDL_ERR_INVALID_ARG, "NULL info");
@@ -1320,6 +1467,8 @@ ibdl_status ibdl_solve_batched(ibdl_batch b, int32_t count, const ibdl_geometry*
   for (int k = 0; k < count; ++k) {
     if (!geoms[k] || !bdata[k] || !q_out[k])
       return fail(IBDL_ERR_INVALID_ARG, "NULL geometry, bdata or q_out entry");
+    if (geoms[k]->eta > 0)
+      return fail(IBDL_ERR_UNSUPPORTED, "completed IBDL geometries solve with ibdl_solve");
     IBDL_TRY(geoms[k]->ensure_host());
     for (int l = 0; l < k; ++l)
       if (geoms[l] == geoms[k])
@@ -1735,6 +1884,8 @@ ibdl_status ibdl_server_submit(ibdl_server s, const ibdl_geometry_desc* d, const
     return fail(IBDL_ERR_INVALID_ARG, "m out of range (1 .. 16776960)");
   if (!d->x || !d->y || !d->nx || !d->ny || !d->w || (d->dim == 3 && (!d->z || !d->nz)))
     return fail(IBDL_ERR_INVALID_ARG, "NULL point, normal or weight array");
+  if (d->eta != 0)
+    return fail(IBDL_ERR_UNSUPPORTED, "completed IBDL requests solve with ibdl_solve");
   SrvReq* r = new SrvReq();
   const size_t m = (size_t)d->m;
   const double* src[7] = {d->x, d->y, d->dim == 3 ? d->z : nullptr, d->nx, d->ny,

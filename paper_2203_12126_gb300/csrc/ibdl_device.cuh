@@ -625,7 +625,8 @@ __host__ __device__ inline size_t pencil_smem_bytes(const PencilLayout& L, int n
 }
 
 // MODE 0: forward, 1: inverse, 2: forward, multiply by
-// scale0 / (1 + cfac * sum_c sin^2(pi k_c / n)), inverse.
+// scale0 / (c0 + cfac * sum_c sin^2(pi k_c / n)) (c0 = 1; c0 = 0 and the
+// k = 0 mode zeroed in the Poisson limit), inverse.
 //
 // An item's pencils are either contiguous (pencil p at data + p n: the 2D
 // kx slabs and the 3D y pencils) or strided (3D z pencils: the item's c
@@ -707,10 +708,12 @@ __device__ __forceinline__ void phase_pencils(const GridDesc& g, const PencilLay
   if (MODE == 2) {
     // 2D: pencil kx = p0 + pl, position ky = t; 3D: kx = gi0, ky = q0 + pl, kz = t
     const T sfix = g.dim == 3 ? s2s[gi0] : (T)0;
+    const T c0 = g.poisson ? (T)0 : (T)1;
     for (int e = tid; e < (npl << lg); e += nt) {
       const int pl = e >> lg, t = e & (n - 1);
       const T ssum = g.dim == 3 ? sfix + s2s[q0 + pl] + s2s[t] : s2s[p0 + pl] + s2s[t];
-      const T f = scale0 * recip_symbol<T>((T)1 + cfac * ssum);
+      const T den = c0 + cfac * ssum;
+      const T f = den > (T)0 ? scale0 * recip_symbol<T>(den) : (T)0;
       C& v = res[pl * PS + padi(t)];
       v.x *= f;
       v.y *= f;

@@ -56,7 +56,23 @@ struct GridDesc {
   double h = 0, kappa = 0;
   double origin[3] = {0, 0, 0};
   int delta = 0;
+  // 1: the Poisson limit kappa = inf (Sec. 5.4): the solve applies the
+  // mean-zero -Delta_0^{-1} (symbol 1 / lambda(k), the k = 0 mode dropped)
+  // in place of kappa L'^{-1}.
+  int poisson = 0;
 };
+
+// Host constants of the symbol multiply: the solve scales mode k by
+// scale0 / (c0 + cfac * sum_c sin^2(pi k_c / n)), and by 0 where that
+// denominator is 0 (only k = 0 in the Poisson limit).
+__host__ __device__ inline double symbol_cfac(const GridDesc& g) {
+  return 4.0 * (g.poisson ? 1.0 : g.kappa) / (g.h * g.h);
+}
+__host__ __device__ inline double symbol_scale0(const GridDesc& g) {
+  double nd = 1.0;
+  for (int c = 0; c < g.dim; ++c) nd *= g.n;
+  return (g.poisson ? 1.0 : g.kappa) / nd;
+}
 
 template <typename T>
 struct SpectralWs {
@@ -160,5 +176,29 @@ cudaError_t krylov_finish(const KrylovWs& k, int kdim, double* x, cudaStream_t s
 cudaError_t launch_axpby(int m, double a, const double* x, double b, const double* y,
                          double* out, cudaStream_t st);  // out = a x + b y
 cudaError_t launch_nonfinite_check(int m, const double* x, int* flag, cudaStream_t st);
+
+// Poisson limit (k_poisson.cu).  Reduction buffers hold kRedBlocks + 1 doubles.
+constexpr int kRedBlocks = 152;
+// part = block partials of w^T q and part[kRedBlocks] = q[m] (u_bar)
+cudaError_t launch_completed_head(int m, const double* w, const double* q, double* part,
+                                  cudaStream_t st);
+// y[i] += u_bar (i < m), y[m] = scale * w^T q
+cudaError_t launch_completed_tail(int m, double* y, const double* part, double scale,
+                                  cudaStream_t st);
+// out[0] = scale * sum a
+cudaError_t launch_scaled_sum(int64_t n, const double* a, double scale, double* part,
+                              double* out, cudaStream_t st);
+cudaError_t launch_add_scalar(int64_t n, double* u, const double* s, cudaStream_t st);
+cudaError_t launch_fill(int64_t n, double* x, double v, cudaStream_t st);
+// chi_h = u - u[0], chi = chi_h > 1/2 (either output may be null)
+cudaError_t launch_indicator(int64_t n, const double* u, double* chi_h, unsigned char* chi,
+                             cudaStream_t st);
+
+// Near-boundary values, 2D (k_near.cu); scratch: near_scratch_bytes, 16-byte aligned.
+int64_t near_list_capacity(int n, int m, int m1);
+size_t near_scratch_bytes(int n, int m, int m1);
+cudaError_t launch_near_boundary(const GridDesc& g, const PointData& p, const double* ub,
+                                 const double* uin, const unsigned char* inside, int m1,
+                                 double m2, double* uout, void* scratch, cudaStream_t st);
 
 }  // namespace ibdl

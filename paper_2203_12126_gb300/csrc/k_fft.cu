@@ -106,9 +106,8 @@ static cudaError_t run_pencils(const GridDesc& g, const PencilLayout& L, Spectra
   const int blocks = (L.npencils + L.c - 1) / L.c;
   const int thr = pencil_threads(g.n, L.c);
   const size_t smem = pencil_smem_bytes<T>(L, g.n);
-  const double nd = g.dim == 3 ? (double)g.n * g.n * g.n : (double)g.n * g.n;
-  const T cfac = (T)(4.0 * g.kappa / (g.h * g.h));
-  const T scale0 = (T)(g.kappa / nd);
+  const T cfac = (T)symbol_cfac(g);
+  const T scale0 = (T)symbol_scale0(g);
   prof_begin(st);
   k_pencils<T, MODE><<<blocks, thr, smem, st>>>(g, L, ws.spec, ws.tw, ws.s2, cfac, scale0,
                                                  zskip, ngroups, zempty);

@@ -202,9 +202,8 @@ __device__ __noinline__ void solver_pencils(const SolveInst& I, int which, int i
                                             unsigned char* smem) {
   const SpectralWs<T> ws = ws_of<T>(I);
   const GridDesc& g = I.g;
-  const double nd = g.dim == 3 ? (double)g.n * g.n * g.n : (double)g.n * g.n;
-  const T cfac = (T)(4.0 * g.kappa / (g.h * g.h));
-  const T scale0 = (T)(g.kappa / nd);
+  const T cfac = (T)symbol_cfac(g);
+  const T scale0 = (T)symbol_scale0(g);
   // the matvec's grid feeds only the interpolation and has no grid source:
   // 3D y-pass items of planes without points are skipped (both directions)
   const int* zskip = (g.dim == 3 && MODE != 2) ? I.b.start : nullptr;

@@ -37,7 +37,7 @@ EXPORTS = [
     "ibdl_batch_create", "ibdl_batch_destroy", "ibdl_solve_batched",
     "ibdl_server_config_default", "ibdl_server_create", "ibdl_server_destroy",
     "ibdl_server_clock", "ibdl_server_submit", "ibdl_server_step", "ibdl_server_take",
-    "ibdl_server_get_stats", "ibdl_tuning_enable",
+    "ibdl_server_get_stats", "ibdl_tuning_enable", "ibdl_indicator", "ibdl_near_boundary",
 ]
 
 
@@ -49,6 +49,7 @@ class GeometryDesc(C.Structure):
         ("nx", C.c_void_p), ("ny", C.c_void_p), ("nz", C.c_void_p),
         ("w", C.c_void_p), ("kappa", C.c_double), ("delta", C.c_int32),
         ("bc", C.c_int32), ("precision", C.c_int32), ("reserved", C.c_int32),
+        ("eta", C.c_double),
     ]
 
 
@@ -165,6 +166,8 @@ def load(path: str = LIB_PATH):
         "ibdl_server_take": (C.c_int, [vp, i64, vp, C.POINTER(RequestResult)]),
         "ibdl_server_get_stats": (C.c_int, [vp, C.POINTER(ServerStats)]),
         "ibdl_tuning_enable": (None, [i32]),
+        "ibdl_indicator": (C.c_int, [vp, vp, vp, vp]),
+        "ibdl_near_boundary": (C.c_int, [vp, vp, vp, vp, i32, C.c_double, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -192,6 +195,19 @@ def _ptr(a):
     # torch tensor
     if str(a.dtype) != "torch.float64" or not a.is_contiguous():
         raise TypeError("tensors must be contiguous float64")
+    return a.data_ptr()
+
+
+def _ptr_u8(a):
+    """Raw address of a contiguous uint8 tensor / array (or None)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.uint8 or not a.flags.c_contiguous:
+            raise TypeError("masks must be contiguous uint8 arrays")
+        return a.ctypes.data
+    if str(a.dtype) != "torch.uint8" or not a.is_contiguous():
+        raise TypeError("masks must be contiguous uint8 tensors")
     return a.data_ptr()
 
 
@@ -244,7 +260,7 @@ def version() -> int:
 
 
 def make_desc(dim, n, box_len, origin, x, y, nx, ny, w, kappa, z=None, nz=None,
-              delta="peskin4", bc=DIRICHLET, precision=FP64):
+              delta="peskin4", bc=DIRICHLET, precision=FP64, eta=0.0):
     """Fill an ``ibdl_geometry_desc`` (the arrays must outlive its use)."""
     d = GeometryDesc()
     d.dim, d.n, d.box_len = int(dim), int(n), float(box_len)
@@ -257,6 +273,7 @@ def make_desc(dim, n, box_len, origin, x, y, nx, ny, w, kappa, z=None, nz=None,
     d.kappa = float(kappa)
     d.delta = DELTA[delta] if isinstance(delta, str) else int(delta)
     d.bc, d.precision = int(bc), int(precision)
+    d.eta = float(eta)
     return d
 
 
@@ -346,7 +363,8 @@ class Geometry:
     """
 
     def __init__(self, dim, n, box_len, origin, x, y, nx, ny, w, kappa, z=None,
-                 nz=None, delta="peskin4", bc=DIRICHLET, precision=FP64, stream=None):
+                 nz=None, delta="peskin4", bc=DIRICHLET, precision=FP64, stream=None,
+                 eta=0.0):
         lib = load()
         d = GeometryDesc()
         d.dim, d.n, d.box_len = int(dim), int(n), float(box_len)
@@ -359,6 +377,7 @@ class Geometry:
         d.kappa = float(kappa)
         d.delta = DELTA[delta] if isinstance(delta, str) else int(delta)
         d.bc, d.precision = int(bc), int(precision)
+        d.eta = float(eta)
         self._keep = (x, y, z, nx, ny, nz, w)
         h = C.c_void_p()
         _check(lib.ibdl_create_geometry(C.byref(d), _stream(stream), C.byref(h)))
@@ -366,9 +385,11 @@ class Geometry:
         self._keep = None
         self.dim, self.n, self.m = d.dim, d.n, d.m
         self.bc, self.precision = d.bc, d.precision
+        self.eta = d.eta
+        self.nsys = d.m + 1 if d.eta > 0 else d.m
 
     @classmethod
-    def from_workload(cls, geom, bc=DIRICHLET, precision=FP64, stream=None):
+    def from_workload(cls, geom, bc=DIRICHLET, precision=FP64, stream=None, eta=0.0):
         """Build from a ``workloads.geometry.Geometry`` (host float64)."""
         X = np.ascontiguousarray(geom.X, dtype=np.float64)
         N = np.ascontiguousarray(geom.normals, dtype=np.float64)
@@ -378,7 +399,7 @@ class Geometry:
                    ncols[1], np.ascontiguousarray(geom.weights, dtype=np.float64),
                    geom.kappa, z=cols[2] if geom.dim == 3 else None,
                    nz=ncols[2] if geom.dim == 3 else None, delta=geom.delta, bc=bc,
-                   precision=precision, stream=stream)
+                   precision=precision, stream=stream, eta=eta)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -425,6 +446,18 @@ class Geometry:
     def evaluate(self, q, u_out, vb=None, g_grid=None, stream=None):
         _check(load().ibdl_evaluate(self._h, _ptr(q), _ptr(vb), _ptr(g_grid), _ptr(u_out),
                                     _stream(stream)))
+        return u_out
+
+    def indicator(self, chi_h_out=None, chi_out=None, stream=None):
+        """App. D indicator: chi_h (float64 grid) and chi (uint8 grid)."""
+        _check(load().ibdl_indicator(self._h, _ptr(chi_h_out), _ptr_u8(chi_out),
+                                     _stream(stream)))
+        return chi_h_out, chi_out
+
+    def near_boundary(self, u_in, ub, inside, m1, m2, u_out, stream=None):
+        """App. A near-boundary values (2D): u_out from u_in."""
+        _check(load().ibdl_near_boundary(self._h, _ptr(u_in), _ptr(ub), _ptr_u8(inside),
+                                         int(m1), float(m2), _ptr(u_out), _stream(stream)))
         return u_out
 
     def spread_div(self, q, f_out, precision=FP64, stream=None):

@@ -432,16 +432,9 @@ def test_poisson_dirichlet_harmonic_polynomial():
 def _exp_exterior(n, L):
     """Sec. 6.3: Delta u = g outside a circle of radius 0.25 in the periodic
     box [-L/2, L/2)^2, u = exp(sin 2 pi x); g_e = 0 inside the circle."""
-    g = geometry.exterior(geometry.circle(n, 0.25, spacing=0.75, center=(0.0, 0.0),
-                                          origin=(-L / 2, -L / 2), box_len=L, kappa=np.inf))
-    P = configs.grid_nodes(g)
-    s, c = np.sin(2 * np.pi * P[:, 0]), np.cos(2 * np.pi * P[:, 0])
-    rho = np.linalg.norm(P, axis=1)
-    lap = np.exp(s) * ((2 * np.pi * c) ** 2 - 4 * np.pi ** 2 * s)
-    gt = np.where(rho > 0.25, lap, 0.0).reshape(n, n)
-    ub = np.exp(np.sin(2 * np.pi * g.X[:, 0]))
-    far = rho > 0.25 + 6 * g.h
-    return g, gt, ub, np.exp(s), far
+    g, gt, ub, uex = configs.poisson_exterior(n, L)
+    far = np.linalg.norm(configs.grid_nodes(g), axis=1) > 0.25 + 6 * g.h
+    return g, gt, ub, uex, far
 
 
 def test_completed_ibdl_converges_on_the_large_exterior_box():

@@ -147,6 +147,22 @@ def c5_requests(count=300, seed=3, rate=2000.0, sizes2d=(256, 512, 1024),
     return out
 
 
+def poisson_exterior(n, L, spacing=0.75):
+    """Sec. 6.3: Delta u = g outside a circle of radius 0.25 centred in the
+    periodic box [-L/2, L/2)^2, exact u = exp(sin 2 pi x).  Returns the
+    exterior geometry (kappa = inf, normals into the circle), the forcing g~
+    on the grid (g = Delta u outside, g_e = 0 inside), U_b at the points and
+    the exact u at the grid nodes."""
+    g = geometry.exterior(geometry.circle(n, 0.25, spacing=spacing, center=(0.0, 0.0),
+                                          origin=(-L / 2, -L / 2), box_len=L,
+                                          kappa=float("inf")))
+    P = grid_nodes(g)
+    s, c = np.sin(2 * np.pi * P[:, 0]), np.cos(2 * np.pi * P[:, 0])
+    lap = np.exp(s) * ((2 * np.pi * c) ** 2 - 4 * np.pi ** 2 * s)
+    gt = np.where(np.linalg.norm(P, axis=1) > 0.25, lap, 0.0).reshape(n, n)
+    return g, gt, np.exp(np.sin(2 * np.pi * g.X[:, 0])), np.exp(s)
+
+
 def grid_nodes(geom):
     """(n^d, d) coordinates of all grid nodes in memory order (x fastest)."""
     h = geom.h
