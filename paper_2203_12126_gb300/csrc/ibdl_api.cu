@@ -837,6 +837,7 @@ ibdl_status ibdl_create_geometry(const ibdl_geometry_desc* d, void* stream, ibdl
   gd.log2n = 0;
   while ((1 << gd.log2n) < n) gd.log2n++;
   gd.h = d->box_len / n;
+  gd.inv2h = 0.5 / gd.h;
   gd.kappa = d->kappa;
   gd.poisson = isinf(d->kappa) ? 1 : 0;
   gd.delta = d->delta;
@@ -907,6 +908,16 @@ ibdl_status ibdl_create_geometry(const ibdl_geometry_desc* d, void* stream, ibdl
     pd.W32[c] = VV[c];
   }
   pd.w = pts + (size_t)6 * m;
+  {
+    // float copies of the normals and scaled weights for the float32 spread
+    float* p32;
+    if ((s = g->alloc(&p32, (size_t)4 * m))) return cleanup(s);
+    cudaError_t e = launch_grid_to_float(pts + (size_t)3 * m, p32, (int64_t)3 * m, st);
+    if (!e) e = launch_grid_to_float(pts + (size_t)6 * m, p32 + (size_t)3 * m, m, st);
+    if (e) return cleanup(cuda_fail(e, "float copies"));
+    for (int c = 0; c < 3; ++c) pd.nrm32[c] = p32 + (size_t)c * m;
+    pd.w32 = p32 + (size_t)3 * m;
+  }
   {
     cudaError_t e = launch_point_prep(gd, m, X, B, WW, VV, st);
     if (e) return cleanup(cuda_fail(e, "point prep"));

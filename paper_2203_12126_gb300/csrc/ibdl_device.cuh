@@ -375,6 +375,22 @@ template <> __device__ __forceinline__ float wload<float>(const PointData& p, in
   return (t >= 0 && t < 4) ? p.W32[c][t * p.m + i] : 0.0f;
 }
 
+// Point normal component c and weight / h^d in the spread's precision.
+template <typename T> __device__ __forceinline__ T pt_nrm(const PointData& p, int c, int i);
+template <> __device__ __forceinline__ double pt_nrm<double>(const PointData& p, int c, int i) {
+  return p.nrm[c][i];
+}
+template <> __device__ __forceinline__ float pt_nrm<float>(const PointData& p, int c, int i) {
+  return p.nrm32[c][i];
+}
+template <typename T> __device__ __forceinline__ T pt_w(const PointData& p, int i);
+template <> __device__ __forceinline__ double pt_w<double>(const PointData& p, int i) {
+  return p.w[i];
+}
+template <> __device__ __forceinline__ float pt_w<float>(const PointData& p, int i) {
+  return p.w32[i];
+}
+
 // Rows per tile of the x passes: 2D keeps 4 (2 for n = 4096) so that even a
 // 1024^2 grid has 256 tiles; 3D takes 8, so each kx of a tile is a 64-byte
 // (float) or 128-byte (double) segment of the transposed spectrum.
@@ -463,7 +479,7 @@ __device__ __forceinline__ void phase_rows_fwd(const GridDesc& g, const PointDat
   //   cA = q w/h^d (ny dW_y[bb] W_z[c-1] + nz W_y[bb-1] dW_z[c]) + v w/h^d W_y[bb-1] W_z[c-1]
   //   cB = q w/h^d nx W_y[bb-1] W_z[c-1] / (2h),
   // staged as  cA = P dW_y[bb] + Q W_y[bb-1],  cB = X W_y[bb-1].
-  const T inv2h = (T)(0.5 / g.h);
+  const T inv2h = (T)g.inv2h;
   constexpr int kWords = 11;  // wx[4], wy[4], P, Q, X
   const int per_pt = kWords * (int)sizeof(T) + 2 * (int)sizeof(int);
   int KP = (int)((size_t)npen * PS * sizeof(C) / per_pt);
@@ -484,14 +500,16 @@ __device__ __forceinline__ void phase_rows_fwd(const GridDesc& g, const PointDat
         dz = (wload<T>(p, 2, cz, i) - wload<T>(p, 2, cz - 2, i)) * inv2h;
       }
       T P = 0, Q = 0, X = 0;
-      const double wi = p.w[i];
+      // float32: one conversion (q) per staged point; the normals and
+      // weights have float copies (float64 work is slow on GB300)
+      const T wi = pt_w<T>(p, i);
       if (src.q_div) {
-        const T amp = (T)(src.coef_div * __ldcg(src.q_div + i) * wi);
-        P = amp * (T)p.nrm[1][i] * wz;
-        if (D == 3) Q = amp * (T)p.nrm[2][i] * dz;
-        X = amp * (T)p.nrm[0][i] * wz * inv2h;
+        const T amp = (T)src.coef_div * (T)__ldcg(src.q_div + i) * wi;
+        P = amp * pt_nrm<T>(p, 1, i) * wz;
+        if (D == 3) Q = amp * pt_nrm<T>(p, 2, i) * dz;
+        X = amp * pt_nrm<T>(p, 0, i) * wz * inv2h;
       }
-      if (src.v_plain) Q += (T)(src.coef_plain * __ldcg(src.v_plain + i) * wi) * wz;
+      if (src.v_plain) Q += (T)src.coef_plain * (T)__ldcg(src.v_plain + i) * wi * wz;
       if (!ok) P = Q = X = 0;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {

@@ -36,6 +36,8 @@ struct PointData {
   const double* X[3] = {nullptr, nullptr, nullptr};
   const double* nrm[3] = {nullptr, nullptr, nullptr};
   const double* w = nullptr;       // quadrature weight / h^d
+  const float* nrm32[3] = {nullptr, nullptr, nullptr};  // float copies for the
+  const float* w32 = nullptr;                            // float32 spread
   const int* base[3] = {nullptr, nullptr, nullptr};
   const double* W64[3] = {nullptr, nullptr, nullptr};  // [t*m + i]
   const float* W32[3] = {nullptr, nullptr, nullptr};
@@ -54,6 +56,8 @@ struct GridDesc {
   int n = 0;
   int log2n = 0;
   double h = 0, kappa = 0;
+  double inv2h = 0;  // 1 / (2h) of the centred difference, set with h (a
+                     // float64 divide per thread is slow on GB300's FP64 pipe)
   double origin[3] = {0, 0, 0};
   int delta = 0;
   // 1: the Poisson limit kappa = inf (Sec. 5.4): the solve applies the

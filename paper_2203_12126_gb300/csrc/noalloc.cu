@@ -116,6 +116,7 @@ extern "C" ibdl_status ibdl_helmholtz_2d_noalloc(int32_t n, double box_len, doub
   g.n = n;
   while ((1 << g.log2n) < n) g.log2n++;
   g.h = box_len / n;
+  g.inv2h = 0.5 / g.h;
   g.kappa = kappa;
   PointData p;  // m = 0
   Bins b;
