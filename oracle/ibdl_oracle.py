@@ -26,6 +26,8 @@ Layer method" (arXiv:2203.12126):
                           the box-corner value, threshold at 1/2
 * near-boundary values    Sec. 5.5, App. A (2D): linear interpolation between
                           the chord point x_A and a point x_B m2 h inside
+* Fourier-spectral        Sec. 5.1-5.2, Sec. 6.2.1, Sec. 6.7: spectral Laplacian
+  discretisation          and (matching it, Sec. 5.2) spectral divergence in S~
 
 Conventions.  The paper writes the operator as L_p = Delta_h - k^2.  This
 oracle uses L' = I - kappa Delta_h with kappa = 1/k^2, so L_p = -(1/kappa) L'
@@ -219,13 +221,68 @@ def laplace_inverse0(box, f):
     return np.real(np.fft.ifftn(-F / lam))
 
 
-def green(box, kappa, f):
+def green(box, kappa, f, disc="fd"):
     """The grid solve every operator below uses: kappa L'^{-1} f for finite
     kappa (= -L_p^{-1} f with L_p = Delta_h - k^2), and its k = 0 limit
-    -Delta_0^{-1} f for kappa = inf (the Poisson equation, Sec. 5.4)."""
+    -Delta_0^{-1} f for kappa = inf (the Poisson equation, Sec. 5.4).
+    disc = "spectral" uses the Fourier-spectral Laplacian instead of the
+    5/7-point stencil."""
+    if disc == "spectral":
+        lam = spectral_laplace_symbol(box)
+        F = np.fft.fftn(f)
+        if np.isinf(kappa):
+            F.reshape(-1)[0] = 0.0
+            lam.reshape(-1)[0] = 1.0
+            return np.real(np.fft.ifftn(F / lam))
+        return np.real(np.fft.ifftn(kappa * F / (1.0 + kappa * lam)))
     if np.isinf(kappa):
         return -laplace_inverse0(box, f)
     return kappa * helmholtz_solve(box, kappa, f)
+
+
+# ---------------------------------------------------------------------------
+# Fourier-spectral discretisation (Sec. 5.1, Sec. 6.2.1, Sec. 6.7)
+# ---------------------------------------------------------------------------
+
+
+def wavenumbers(box):
+    """Signed integer wavenumbers of the n-point grid in FFT order:
+    0, 1, ..., n/2 - 1, -n/2, ..., -1."""
+    return np.fft.fftfreq(box.n, d=1.0 / box.n)
+
+
+def spectral_derivative(box, g, c):
+    """d/dx_c of the trigonometric interpolant: mode k times i 2 pi k / L;
+    the Nyquist mode (k = -n/2) is set to zero so real data stays real."""
+    a = box.axis(c)
+    k = wavenumbers(box)
+    fac = 2j * np.pi * k / box.L
+    fac[box.n // 2] = 0.0
+    shp = [1] * box.d
+    shp[a] = box.n
+    return np.real(np.fft.ifft(np.fft.fft(g, axis=a) * fac.reshape(shp), axis=a))
+
+
+def spectral_laplace_symbol(box):
+    """Eigenvalues of the spectral -Delta: sum_c (2 pi k_c / L)^2 (the
+    Nyquist mode keeps (pi n / L)^2)."""
+    k = wavenumbers(box)
+    k2 = (2.0 * np.pi * k / box.L) ** 2
+    lam = np.zeros(box.shape)
+    for a in range(box.d):
+        shp = [1] * box.d
+        shp[a] = box.n
+        lam = lam + k2.reshape(shp)
+    return lam
+
+
+def spread_div_spectral(box, X, nrm, w, Q, delta="peskin4"):
+    """S~ Q with the spectral divergence: sum_c D_c S(Q n_c) (Sec. 5.2: the
+    divergence matches the PDE's discretisation)."""
+    out = np.zeros(box.shape)
+    for c in range(box.d):
+        out += spectral_derivative(box, spread(box, X, Q * nrm[:, c], w, delta), c)
+    return out
 
 
 def helmholtz_dense(box, kappa):
@@ -255,8 +312,9 @@ class Operator:
     A_D Q = Q/2 - S* Delta_0^{-1} S~ Q (Dirichlet only).
     """
 
-    def __init__(self, geom, bc, kappa=None, delta=None):
+    def __init__(self, geom, bc, kappa=None, delta=None, disc="fd"):
         self.box = Box.of(geom)
+        self.disc = disc
         self.X = np.asarray(geom.X, dtype=np.float64)
         self.nrm = np.asarray(geom.normals, dtype=np.float64)
         self.w = np.asarray(geom.weights, dtype=np.float64)
@@ -271,10 +329,14 @@ class Operator:
     def m(self):
         return self.X.shape[0]
 
+    def div(self, Q):
+        """S~ Q with the divergence of the chosen discretisation."""
+        sd = spread_div_spectral if self.disc == "spectral" else spread_div
+        return sd(self.box, self.X, self.nrm, self.w, Q, self.delta)
+
     def layer(self, Q):
         """v = kappa L'^{-1} S~ Q on the grid (-Delta_0^{-1} S~ Q if kappa = inf)."""
-        f = spread_div(self.box, self.X, self.nrm, self.w, Q, self.delta)
-        return green(self.box, self.kappa, f)
+        return green(self.box, self.kappa, self.div(Q), self.disc)
 
     def apply(self, Q):
         self.matvecs += 1
@@ -295,23 +357,23 @@ class Operator:
         if self.bc == DIRICHLET:
             out = b.copy()
             if g_grid is not None:
-                out += interp(self.box, self.X, green(self.box, self.kappa, g_grid),
+                out += interp(self.box, self.X, green(self.box, self.kappa, g_grid, self.disc),
                               self.delta)
             return out
         src = -spread(self.box, self.X, b, self.w, self.delta)
         if g_grid is not None:
             src = src + g_grid
-        return interp(self.box, self.X, green(self.box, self.kappa, src), self.delta)
+        return interp(self.box, self.X, green(self.box, self.kappa, src, self.disc), self.delta)
 
     def evaluate(self, Q, vb=None, g_grid=None):
         """Grid solution, step 2 of Sec. 4.1: L_p u + S~Q = g~ gives
         u = kappa L'^{-1}(S~Q - g~); Neumann (eq. (ib neumann 1)) adds S V_b."""
-        src = spread_div(self.box, self.X, self.nrm, self.w, Q, self.delta)
+        src = self.div(Q)
         if self.bc == NEUMANN and vb is not None:
             src = src + spread(self.box, self.X, vb, self.w, self.delta)
         if g_grid is not None:
             src = src - g_grid
-        return green(self.box, self.kappa, src)
+        return green(self.box, self.kappa, src, self.disc)
 
     def dense(self):
         """Assemble A column by column, A[:, i] = A e_i."""
@@ -398,9 +460,9 @@ def gmres(A, b, tol=1e-8, restart=30, maxiter=1000, x0=None):
 
 
 def solve(geom, bc, bdata, tol=1e-10, restart=30, maxiter=1000, g_grid=None,
-          kappa=None):
+          kappa=None, disc="fd"):
     """Step 1 of Sec. 4.1 (or Sec. 4.4): GMRES on the boundary system."""
-    op = Operator(geom, bc, kappa)
+    op = Operator(geom, bc, kappa, disc=disc)
     b = op.rhs(bdata, g_grid)
     res = gmres(op, b, tol, restart, maxiter)
     res.matvecs = op.matvecs
@@ -409,9 +471,9 @@ def solve(geom, bc, bdata, tol=1e-10, restart=30, maxiter=1000, g_grid=None,
     return res
 
 
-def solve_dense(geom, bc, bdata, g_grid=None, kappa=None):
+def solve_dense(geom, bc, bdata, g_grid=None, kappa=None, disc="fd"):
     """Exact discrete solution Q* = A^{-1} b by LU (small M only)."""
-    op = Operator(geom, bc, kappa)
+    op = Operator(geom, bc, kappa, disc=disc)
     b = op.rhs(bdata, g_grid)
     return np.linalg.solve(op.dense(), b)
 

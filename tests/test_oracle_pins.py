@@ -529,3 +529,70 @@ def test_near_boundary_values_restore_pointwise_convergence():
         cor.append(np.max(np.abs(O.near_boundary_values(g, u, ub, chi, 6, 8.0) - ex)[ins]))
     assert min(raw) > 0.05, raw
     assert cor[0] < 0.01 and cor[1] < cor[0] / 1.8 and cor[2] < cor[1] / 1.8, cor
+
+
+# ---------------------------------------------------------------------------
+# Fourier-spectral discretisation (Sec. 5.1, Sec. 6.2.1, Sec. 6.7)
+# ---------------------------------------------------------------------------
+
+
+def _trig(box, m, p, phase):
+    x = box.o[0] + box.h * np.arange(box.n)
+    y = box.o[1] + box.h * np.arange(box.n)
+    Y, X = np.meshgrid(y, x, indexing="ij")
+    arg = 2 * np.pi * (m * X + p * Y) / box.L + phase
+    return np.sin(arg), np.cos(arg)
+
+
+@pytest.mark.parametrize("m,p", [(5, 3), (0, 15), (-7, 1)])
+def test_spectral_derivative_is_exact_on_trigonometric_polynomials(m, p):
+    """d/dx sin(2 pi (m x + p y)/L + c) = (2 pi m / L) cos(...) exactly for
+    |m|, |p| < n/2; a swapped axis or a dropped 2 pi / L fails at O(1)."""
+    box = O.Box(2, 32, 1.3, (0.1, -0.2))
+    s, c = _trig(box, m, p, 0.4)
+    assert np.max(np.abs(O.spectral_derivative(box, s, 0) - 2 * np.pi * m / box.L * c)) < 1e-11
+    assert np.max(np.abs(O.spectral_derivative(box, s, 1) - 2 * np.pi * p / box.L * c)) < 1e-11
+
+
+def test_spectral_derivative_of_the_nyquist_mode_is_zero():
+    box = O.Box(2, 16, 1.0, (0.0, 0.0))
+    g = np.cos(np.pi * np.arange(16))[None, :] * np.ones((16, 1))
+    assert np.max(np.abs(O.spectral_derivative(box, g, 0))) == 0.0
+
+
+@pytest.mark.parametrize("kappa", [1e-2, np.inf])
+def test_spectral_solve_closed_form(kappa):
+    """kappa L'^{-1} of a Fourier mode: kappa / (1 + kappa |2 pi k / L|^2)
+    times it; the Poisson limit gives 1 / |2 pi k / L|^2."""
+    box = O.Box(2, 32, 1.3, (0.0, 0.0))
+    s, _ = _trig(box, 5, -3, 0.2)
+    k2 = (2 * np.pi / box.L) ** 2 * 34
+    want = s / k2 if np.isinf(kappa) else kappa * s / (1 + kappa * k2)
+    assert np.max(np.abs(O.green(box, kappa, s, "spectral") - want)) < 1e-15 * 1e3
+
+
+@pytest.mark.parametrize("e,c,m,it", [r for r in _table3() if r[0] == 5])
+def test_table3_iteration_counts_3d_spectral(e, c, m, it):
+    """Sec. 6.7 discretises with the Fourier-spectral method: Table 3's
+    counts within +-1 on the Fibonacci stand-in for the point sets."""
+    g = geometry.sphere(2 ** e, 0.25, m=m, center=(0, 0, 0), origin=(-0.5,) * 3,
+                        kappa=1.0)
+    x, y, z = (g.X - np.array(g.center)).T
+    ub = 0.25 * z * 2 * x * y / np.maximum(x * x + y * y, 1e-300)
+    res = O.solve(g, configs.DIRICHLET, ub, tol=1e-8, disc="spectral")
+    assert res.converged and abs(res.iters - it) <= 1, (res.iters, it)
+
+
+def test_spectral_first_order_convergence_in_l1():
+    """Sec. 6.2.1: with the spectral discretisation the error away from the
+    boundary still converges at first order in L1 (k = 1 circle)."""
+    l1 = []
+    for n in (128, 256, 512):
+        p = configs.table1(n, 1.0)
+        res = O.solve(p.geom, p.bc, p.bdata, tol=1e-10, disc="spectral")
+        u = res.op.evaluate(res.x)
+        P = configs.grid_nodes(p.geom)
+        mask = configs.interior_mask_circle(p.geom, p.geom.extra["r"], 0)
+        l1.append(np.mean(np.abs(u.reshape(-1)[mask] - p.exact(P)[mask])))
+    r = [math.log2(l1[i] / l1[i + 1]) for i in range(2)]
+    assert all(0.85 < x < 1.2 for x in r), (l1, r)
