@@ -31,7 +31,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-from workloads import configs  # noqa: E402
+from workloads import configs, geometry  # noqa: E402
 
 METRIC = "IBDL solves/s at 1e-8 relative residual (2D star N=1024^2, M=3525, Dirichlet+Neumann)"
 WORKLOAD = "c2-star-n1024-m3525-kappa1e-3-dirichlet+neumann"
@@ -233,8 +233,9 @@ def _event_ms(fn, reps, flush):
     return float(np.median(ms))
 
 
-def run_poisson_rows(pkg, peaks, reps=10):
-    """The Poisson-limit rows, event-timed with L2 flushed between calls:
+def run_method_rows(pkg, peaks, reps=10):
+    """The method rows beyond the Helmholtz hot path, event-timed with L2
+    flushed between calls.  Poisson limit:
     the interior indicator (App. D) and the near-boundary values (App. A,
     m1 = 6, m2 = 8) on the C2 star (N = 1024^2, M = 3525); a Dirichlet
     Poisson solve on the same star (kappa = inf, float32-refined, tol 1e-8);
@@ -302,6 +303,34 @@ def run_poisson_rows(pkg, peaks, reps=10):
                                      "note": "L = 8, N = 1024^2, eta = 10, float32-refined, "
                                              "tol 1e-8, launch-based engine"}
     Gc.close()
+    # Fourier-spectral discretisation (Sec. 6.2.1): matvecs on C2 and C3
+    for name, prob in (("c2", configs.c2()), ("c3", configs.c3())):
+        Gs = pkg.Geometry.from_workload(prob.geom, bc=prob.bc, precision=ibdl.FP32_REFINED,
+                                        disc="spectral")
+        qv = torch.tensor(np.random.default_rng(0).standard_normal(prob.geom.m),
+                          dtype=torch.float64, device=dev)
+        yv = torch.empty_like(qv)
+        for prec, tag in ((1, "f32"), (0, "f64")):
+            us = _event_ms(lambda: Gs.apply(qv, yv, precision=prec), reps, flush) * 1e3
+            out[f"spectral_matvec_{name}_{tag}"] = {"us": us}
+        Gs.close()
+    # Sec. 6.7: the 3D Dirichlet problem (spectral), dx = 2^-8, 14400 points
+    g3 = geometry.sphere(256, 0.25, m=14400, center=(0, 0, 0), origin=(-0.5,) * 3, kappa=1.0)
+    x, y, z = (g3.X - np.array(g3.center)).T
+    ub3 = torch.tensor(0.25 * z * 2 * x * y / np.maximum(x * x + y * y, 1e-300),
+                       dtype=torch.float64, device=dev)
+    G3 = pkg.Geometry.from_workload(g3, precision=ibdl.FP32_REFINED, disc="spectral")
+    q3 = torch.zeros(g3.m, dtype=torch.float64, device=dev)
+    i3 = {}
+
+    def s3():
+        i3.update(G3.solve(ub3, q3, tol=1e-8))
+    s3_ms = _event_ms(s3, 3, flush)
+    out["spectral_solve_sec6_7"] = {"ms": s3_ms, "iters": i3["iters"],
+                                    "note": "sphere r = 0.25, N = 256^3, M = 14400 (Fibonacci), "
+                                            "k = 1, Dirichlet, float32-refined, tol 1e-8 "
+                                            "(Table 3 lists 5 iterations at dx = 2^-8)"}
+    G3.close()
     return out
 
 
@@ -744,7 +773,7 @@ def main():
 
     batched_c4 = run_batched_c4(pkg) if not args.no_batched else None
     c3_solve = run_c3_solve(pkg) if not args.no_matvec else None
-    poisson_rows = run_poisson_rows(pkg, peaks) if not args.no_matvec else None
+    method_rows = run_method_rows(pkg, peaks) if not args.no_matvec else None
 
     serving = None
     if args.serve_requests > 0:
@@ -795,7 +824,7 @@ def main():
             "matvec": matvec,
             "batched_c4": batched_c4,
             "c3_solve": c3_solve,
-            "poisson_rows": poisson_rows,
+            "method_rows": method_rows,
             "serving": serving,
             "gpu_launches": int(launches),
             "wall_s_timed": wall,

@@ -80,6 +80,16 @@ typedef enum { IBDL_DELTA_PESKIN4 = 0, IBDL_DELTA_COS4 = 1 } ibdl_delta;
  * (residual b - A x with the float64 operator) in float64. */
 typedef enum { IBDL_FP64 = 0, IBDL_FP32_REFINED = 1 } ibdl_precision;
 
+/* Discretisation of the PDE operator (Sec. 5.1, Sec. 6.2.1).  The divergence
+ * inside S~ follows it (Sec. 5.2).
+ * IBDL_DISC_FD: the 5/7-point Laplacian and centred differences.
+ * IBDL_DISC_SPECTRAL: the Fourier-spectral Laplacian, symbol
+ *   sum_c (2 pi k_c / L)^2, and spectral derivatives i 2 pi k_c / L, zero at
+ *   the Nyquist mode.  Solves use the launch-based engine.  Batched solves,
+ *   the server, ibdl_spread_div and ibdl_helmholtz (finite-difference
+ *   operators) and the completed system return IBDL_ERR_UNSUPPORTED. */
+typedef enum { IBDL_DISC_FD = 0, IBDL_DISC_SPECTRAL = 1 } ibdl_disc;
+
 typedef struct ibdl_geometry_s* ibdl_geometry; /* opaque, library-owned */
 
 /* Geometry of one IBDL problem (Sec. 5.1-5.2).  Copied at creation. */
@@ -109,7 +119,7 @@ typedef struct {
   int32_t delta;        /* ibdl_delta */
   int32_t bc;           /* ibdl_bc: selects A_D or A_N */
   int32_t precision;    /* ibdl_precision */
-  int32_t reserved;     /* 0 */
+  int32_t disc;         /* ibdl_disc (0: finite difference) */
   double eta;           /* completed IBDL (Sec. 5.4 eq. (ibdl completed),
                            App. C): weight of the single layer eta S Q added
                            to S~ Q.  0 = the plain method.  eta > 0 needs

@@ -315,6 +315,7 @@ ibdl_status alloc_spectral(ibdl_geometry_s* g, SpectralWs<T>& ws, cudaStream_t) 
   IBDL_TRY(g->alloc(&spec, (size_t)spec_count));
   IBDL_TRY(g->alloc(&grid, (size_t)g->ncells));
   IBDL_TRY(fft_tables<T>(n, &tw, &s2));
+  if (g->grid.spectral) IBDL_TRY(g->alloc(&ws.acc, (size_t)spec_count));
   ws.spec = spec;
   ws.grid = grid;
   ws.tw = tw;
@@ -369,12 +370,57 @@ SpectralWs<float>& wsof<float>(ibdl_geometry_s* g) {
   return g->ws32;
 }
 
+// Fourier-spectral discretisation (Sec. 5.1, Sec. 6.2.1): the divergence in
+// S~ is spectral too (Sec. 5.2), so each component S(q n_c) is transformed
+// on its own and combined as i 2 pi k_c / L times its transform; the
+// scalar sources (plain spread, grid) are added as they are; the last
+// combination applies kappa / sigma(k) and the inverse passes follow.
+template <typename T, typename OutT>
+ibdl_status spectral_field_solve(ibdl_geometry_s* g, const SpreadSrc& src, OutT* out,
+                                 cudaStream_t st) {
+  SpectralWs<T>& ws = wsof<T>(g);
+  const GridDesc& gd = g->grid;
+  struct Term {
+    SpreadSrc s;
+    int deriv;
+  };
+  Term terms[4];
+  int nt = 0;
+  if (src.q_div)
+    for (int c = 0; c < gd.dim; ++c) {
+      SpreadSrc t;
+      t.v_plain = src.q_div;
+      t.coef_plain = src.coef_div;
+      t.plain_nrm = c;
+      terms[nt++] = {t, c};
+    }
+  if (src.v_plain || src.f_grid) {
+    SpreadSrc t;
+    t.v_plain = src.v_plain;
+    t.coef_plain = src.coef_plain;
+    t.plain_nrm = src.plain_nrm;
+    t.f_grid = src.f_grid;
+    t.coef_grid = src.coef_grid;
+    terms[nt++] = {t, -1};
+  }
+  if (nt == 0) return fail(IBDL_ERR_INVALID_ARG, "no source");
+  for (int k = 0; k < nt; ++k) {
+    IBDL_CU(launch_rows_fwd<T>(gd, g->pd, g->bins, terms[k].s, ws, nullptr, st));
+    IBDL_CU(launch_pencils_forward<T>(gd, ws, st));
+    IBDL_CU(launch_spec_combine<T>(gd, ws, terms[k].deriv, k > 0, k == nt - 1, st));
+  }
+  IBDL_CU(launch_pencils_inverse<T>(gd, ws, st));
+  IBDL_CU((launch_rows_inv<T, OutT>(gd, g->bins, ws, out, st, false)));
+  return IBDL_OK;
+}
+
 // grid = kappa L'^{-1} (sources), T-precision spectral passes, output OutT grid.
 // band_only: the grid feeds only the interpolation (matvec, right-hand
 // side), so tiles and planes without points are not produced.
 template <typename T, typename OutT>
 ibdl_status field_solve(ibdl_geometry_s* g, const SpreadSrc& src, OutT* out, cudaStream_t st,
                         bool band_only = false) {
+  if (g->grid.spectral) return spectral_field_solve<T, OutT>(g, src, out, st);
   SpectralWs<T>& ws = wsof<T>(g);
   SpreadSrc s = src;
   s.skip_empty_planes = band_only && !src.f_grid;
@@ -685,7 +731,7 @@ ibdl_status tuned_rows(ibdl_geometry_s* g, int* rows_out, cudaStream_t st) {
       return IBDL_OK;
     }
   }
-  if (tl_no_tune) return IBDL_OK;
+  if (tl_no_tune || g->grid.spectral) return IBDL_OK;
   std::vector<int> cand;
   for (int R = 2; R <= 32; R *= 2)
     if (n / R >= 4 && R <= n - 5 && rows_smem_bytes<double>(n, R) <= 100 * 1024)
@@ -807,6 +853,11 @@ ibdl_status ibdl_create_geometry(const ibdl_geometry_desc* d, void* stream, ibdl
     return fail(IBDL_ERR_INVALID_ARG, "eta must be finite and >= 0");
   if (d->eta > 0 && !isinf(d->kappa))
     return fail(IBDL_ERR_INVALID_ARG, "eta > 0 (completed IBDL) needs kappa = inf");
+  if (d->disc != IBDL_DISC_FD && d->disc != IBDL_DISC_SPECTRAL)
+    return fail(IBDL_ERR_INVALID_ARG, "unknown discretisation");
+  if (d->disc == IBDL_DISC_SPECTRAL && d->eta > 0)
+    return fail(IBDL_ERR_UNSUPPORTED, "the completed system uses the finite-difference "
+                                      "discretisation");
   if (d->delta != IBDL_DELTA_PESKIN4 && d->delta != IBDL_DELTA_COS4)
     return fail(IBDL_ERR_INVALID_ARG, "unknown delta");
   if (d->bc != IBDL_DIRICHLET && d->bc != IBDL_NEUMANN)
@@ -840,6 +891,7 @@ ibdl_status ibdl_create_geometry(const ibdl_geometry_desc* d, void* stream, ibdl
   gd.inv2h = 0.5 / gd.h;
   gd.kappa = d->kappa;
   gd.poisson = isinf(d->kappa) ? 1 : 0;
+  gd.spectral = d->disc == IBDL_DISC_SPECTRAL ? 1 : 0;
   gd.delta = d->delta;
   for (int c = 0; c < 3; ++c) gd.origin[c] = c < dim ? d->origin[c] : 0.0;
   g->ncells = (int64_t)n * n * (dim == 3 ? n : 1);
@@ -1034,8 +1086,9 @@ ibdl_status ibdl_solve(ibdl_geometry g, const double* bdata, const double* g_gri
   if (o.max_refine < 1) o.max_refine = 1;
   if (!(o.inner_tol > 0) || o.inner_tol >= 1) o.inner_tol = 1e-5;
   if (o.engine != 0 && o.engine != 1) return fail(IBDL_ERR_INVALID_ARG, "engine is 0 or 1");
-  // the completed system (length m + 1) runs on the launch-based engine
-  if (g->eta > 0) o.engine = 1;
+  // the completed system (length m + 1) and the spectral discretisation run
+  // on the launch-based engine
+  if (g->eta > 0 || g->grid.spectral) o.engine = 1;
   cudaStream_t st = (cudaStream_t)stream;
   const int m = g->m;
   const int ns = g->nsys;
@@ -1228,6 +1281,8 @@ static ibdl_status spread_common(ibdl_geometry g, const double* v, double* f_out
                                  bool div, void* stream) {
   g_err.clear();
   IBDL_TRY(check_handle(g));
+  if (div && g->grid.spectral)
+    return fail(IBDL_ERR_UNSUPPORTED, "ibdl_spread_div is the finite-difference S~");
   if (!v || !f_out) return fail(IBDL_ERR_INVALID_ARG, "NULL input or output");
   if (precision != 0 && precision != 1) return fail(IBDL_ERR_INVALID_ARG, "precision");
   cudaStream_t st = (cudaStream_t)stream;
@@ -1265,6 +1320,8 @@ ibdl_status ibdl_helmholtz(ibdl_geometry g, const double* f, double* v_out, int3
                            void* stream) {
   g_err.clear();
   IBDL_TRY(check_handle(g));
+  if (g->grid.spectral)
+    return fail(IBDL_ERR_UNSUPPORTED, "ibdl_helmholtz is the finite-difference solve");
   if (!f || !v_out) return fail(IBDL_ERR_INVALID_ARG, "NULL input or output");
   if (precision != 0 && precision != 1) return fail(IBDL_ERR_INVALID_ARG, "precision");
   cudaStream_t st = (cudaStream_t)stream;
@@ -1478,8 +1535,9 @@ ibdl_status ibdl_solve_batched(ibdl_batch b, int32_t count, const ibdl_geometry*
   for (int k = 0; k < count; ++k) {
     if (!geoms[k] || !bdata[k] || !q_out[k])
       return fail(IBDL_ERR_INVALID_ARG, "NULL geometry, bdata or q_out entry");
-    if (geoms[k]->eta > 0)
-      return fail(IBDL_ERR_UNSUPPORTED, "completed IBDL geometries solve with ibdl_solve");
+    if (geoms[k]->eta > 0 || geoms[k]->grid.spectral)
+      return fail(IBDL_ERR_UNSUPPORTED,
+                  "completed or spectral geometries solve with ibdl_solve");
     IBDL_TRY(geoms[k]->ensure_host());
     for (int l = 0; l < k; ++l)
       if (geoms[l] == geoms[k])
@@ -1895,8 +1953,9 @@ ibdl_status ibdl_server_submit(ibdl_server s, const ibdl_geometry_desc* d, const
     return fail(IBDL_ERR_INVALID_ARG, "m out of range (1 .. 16776960)");
   if (!d->x || !d->y || !d->nx || !d->ny || !d->w || (d->dim == 3 && (!d->z || !d->nz)))
     return fail(IBDL_ERR_INVALID_ARG, "NULL point, normal or weight array");
-  if (d->eta != 0)
-    return fail(IBDL_ERR_UNSUPPORTED, "completed IBDL requests solve with ibdl_solve");
+  if (d->eta != 0 || d->disc != IBDL_DISC_FD)
+    return fail(IBDL_ERR_UNSUPPORTED,
+                "completed or spectral requests solve with ibdl_solve");
   SrvReq* r = new SrvReq();
   const size_t m = (size_t)d->m;
   const double* src[7] = {d->x, d->y, d->dim == 3 ? d->z : nullptr, d->nx, d->ny,

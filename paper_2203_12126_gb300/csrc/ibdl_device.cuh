@@ -509,7 +509,11 @@ __device__ __forceinline__ void phase_rows_fwd(const GridDesc& g, const PointDat
         if (D == 3) Q = amp * pt_nrm<T>(p, 2, i) * dz;
         X = amp * pt_nrm<T>(p, 0, i) * wz * inv2h;
       }
-      if (src.v_plain) Q += (T)src.coef_plain * (T)__ldcg(src.v_plain + i) * wi * wz;
+      if (src.v_plain) {
+        T v = (T)src.coef_plain * (T)__ldcg(src.v_plain + i) * wi * wz;
+        if (src.plain_nrm >= 0) v *= pt_nrm<T>(p, src.plain_nrm, i);
+        Q += v;
+      }
       if (!ok) P = Q = X = 0;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {

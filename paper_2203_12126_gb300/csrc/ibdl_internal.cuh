@@ -64,6 +64,9 @@ struct GridDesc {
   // mean-zero -Delta_0^{-1} (symbol 1 / lambda(k), the k = 0 mode dropped)
   // in place of kappa L'^{-1}.
   int poisson = 0;
+  // 1: the Fourier-spectral discretisation (Sec. 5.1, Sec. 6.2.1): spectral
+  // Laplacian in the solve, spectral divergence in S~ (Sec. 5.2)
+  int spectral = 0;
 };
 
 // Host constants of the symbol multiply: the solve scales mode k by
@@ -84,6 +87,7 @@ struct SpectralWs {
   T* grid = nullptr;                      // n^d real
   const typename Cx<T>::type* tw = nullptr;  // tw[j] = exp(-2 pi i j / n)
   const T* s2 = nullptr;                  // sin^2(pi k / n), k < n
+  typename Cx<T>::type* acc = nullptr;    // spectral discretisation: source accumulator
 };
 
 // Sources of the fused spread kernel: out = coef_div * S~ q_div
@@ -93,6 +97,7 @@ struct SpreadSrc {
   double coef_div = 0;
   const double* v_plain = nullptr;
   double coef_plain = 0;
+  int plain_nrm = -1;  // >= 0: the plain term spreads v_plain * n_c, c = plain_nrm
   const double* f_grid = nullptr;
   double coef_grid = 0;
   // 3D, no grid source, grid feeding only the interpolation: tiles of
@@ -180,6 +185,20 @@ cudaError_t krylov_finish(const KrylovWs& k, int kdim, double* x, cudaStream_t s
 cudaError_t launch_axpby(int m, double a, const double* x, double b, const double* y,
                          double* out, cudaStream_t st);  // out = a x + b y
 cudaError_t launch_nonfinite_check(int m, const double* x, int* flag, cudaStream_t st);
+
+// Fourier-spectral discretisation (k_fft.cu).  The forward passes after the
+// x pass (y; 3D y then z) and the inverse passes before the x inverse, in
+// place on ws.spec.  combine: term = spec, times i 2 pi k_c / L when
+// deriv_c >= 0 (0 at the Nyquist mode); accumulate adds ws.acc; final
+// writes (term) * scale0 / (c0 + cfac sum_c (pi k_c / n)^2) into ws.spec
+// (0 where the denominator is 0), else stores term into ws.acc.
+template <typename T>
+cudaError_t launch_pencils_forward(const GridDesc& g, SpectralWs<T>& ws, cudaStream_t st);
+template <typename T>
+cudaError_t launch_pencils_inverse(const GridDesc& g, SpectralWs<T>& ws, cudaStream_t st);
+template <typename T>
+cudaError_t launch_spec_combine(const GridDesc& g, SpectralWs<T>& ws, int deriv_c,
+                                bool accumulate, bool final, cudaStream_t st);
 
 // Poisson limit (k_poisson.cu).  Reduction buffers hold kRedBlocks + 1 doubles.
 constexpr int kRedBlocks = 152;

@@ -135,6 +135,104 @@ cudaError_t launch_spectral_solve(const GridDesc& g, SpectralWs<T>& ws, cudaStre
 }
 
 template <typename T>
+cudaError_t launch_pencils_forward(const GridDesc& g, SpectralWs<T>& ws, cudaStream_t st) {
+  if (g.dim == 2) return run_pencils<T, 0>(g, solve_layout<T>(2, g.n, 1), ws, st);
+  cudaError_t e = run_pencils<T, 0>(g, solve_layout<T>(3, g.n, 0), ws, st);
+  if (e) return e;
+  return run_pencils<T, 0>(g, solve_layout<T>(3, g.n, 1), ws, st);
+}
+
+template <typename T>
+cudaError_t launch_pencils_inverse(const GridDesc& g, SpectralWs<T>& ws, cudaStream_t st) {
+  if (g.dim == 2) return run_pencils<T, 1>(g, solve_layout<T>(2, g.n, 1), ws, st);
+  cudaError_t e = run_pencils<T, 1>(g, solve_layout<T>(3, g.n, 1), ws, st);
+  if (e) return e;
+  return run_pencils<T, 1>(g, solve_layout<T>(3, g.n, 0), ws, st);
+}
+
+// Combination of spectral source terms on the transposed half spectrum
+// ([kx][y] in 2D, [kx][z][y] in 3D; kx = 0..n/2).  Signed wavenumber of
+// index k: k (k < n/2), k - n (k > n/2); the Nyquist index n/2 gets a zero
+// first derivative and (pi/2)^2 in the Laplacian.
+template <typename T>
+__global__ void __launch_bounds__(256) k_spec_combine(int dim, int n, cx_t<T>* __restrict__ spec,
+                                                      cx_t<T>* __restrict__ acc, int64_t count,
+                                                      int deriv_c, int accumulate, int final,
+                                                      T two_pi_over_L, T c0, T cfac, T scale0) {
+  const int lg = 31 - __clz(n);
+  const int half = n >> 1;
+  const T pin = (T)3.14159265358979323846 / (T)n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int k[3];
+    k[1] = (int)(e & (n - 1));  // y
+    if (dim == 2) {
+      k[0] = (int)(e >> lg);
+      k[2] = 0;
+    } else {
+      k[2] = (int)((e >> lg) & (n - 1));  // z
+      k[0] = (int)(e >> (2 * lg));
+    }
+    cx_t<T> t = spec[e];
+    if (deriv_c >= 0) {
+      const int kc = k[deriv_c];
+      const T f = kc == half ? (T)0 : two_pi_over_L * (T)(kc < half ? kc : kc - n);
+      const T re = -f * t.y, im = f * t.x;
+      t.x = re;
+      t.y = im;
+    }
+    if (accumulate) {
+      const cx_t<T> a = acc[e];
+      t.x += a.x;
+      t.y += a.y;
+    }
+    if (final) {
+      T ssum = 0;
+      for (int c = 0; c < dim; ++c) {
+        const T kt = (T)(k[c] <= half ? k[c] : k[c] - n) * pin;
+        ssum += kt * kt;
+      }
+      const T den = c0 + cfac * ssum;
+      const T f = den > (T)0 ? scale0 / den : (T)0;
+      t.x *= f;
+      t.y *= f;
+      spec[e] = t;
+    } else {
+      acc[e] = t;
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_spec_combine(const GridDesc& g, SpectralWs<T>& ws, int deriv_c,
+                                bool accumulate, bool final, cudaStream_t st) {
+  const int64_t count = (int64_t)(g.n / 2 + 1) * g.n * (g.dim == 3 ? g.n : 1);
+  int64_t blocks = (count + 255) / 256;
+  if (blocks > 8 * 152) blocks = 8 * 152;
+  const double L = g.h * g.n;
+  prof_begin(st);
+  k_spec_combine<T><<<(int)blocks, 256, 0, st>>>(
+      g.dim, g.n, ws.spec, ws.acc, count, deriv_c, accumulate ? 1 : 0, final ? 1 : 0,
+      (T)(6.283185307179586476925 / L), (T)(g.poisson ? 0.0 : 1.0), (T)symbol_cfac(g),
+      (T)symbol_scale0(g));
+  count_launch(sizeof(T) == 4 ? "spec_combine_f32" : "spec_combine_f64", st);
+  return check_launch();
+}
+
+template cudaError_t launch_pencils_forward<double>(const GridDesc&, SpectralWs<double>&,
+                                                    cudaStream_t);
+template cudaError_t launch_pencils_forward<float>(const GridDesc&, SpectralWs<float>&,
+                                                   cudaStream_t);
+template cudaError_t launch_pencils_inverse<double>(const GridDesc&, SpectralWs<double>&,
+                                                    cudaStream_t);
+template cudaError_t launch_pencils_inverse<float>(const GridDesc&, SpectralWs<float>&,
+                                                   cudaStream_t);
+template cudaError_t launch_spec_combine<double>(const GridDesc&, SpectralWs<double>&, int, bool,
+                                                 bool, cudaStream_t);
+template cudaError_t launch_spec_combine<float>(const GridDesc&, SpectralWs<float>&, int, bool,
+                                                bool, cudaStream_t);
+
+template <typename T>
 int fft_kernels_per_solve(int dim) {
   return dim == 2 ? 3 : 5;
 }

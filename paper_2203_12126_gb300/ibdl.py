@@ -24,6 +24,7 @@ ERR_BREAKDOWN, ERR_NONFINITE, ERR_TIMEOUT, ERR_UNSUPPORTED = 5, 6, 7, 8
 DIRICHLET, NEUMANN = 0, 1
 DELTA = {"peskin4": 0, "cos4": 1}
 FP64, FP32_REFINED = 0, 1
+DISC = {"fd": 0, "spectral": 1}
 
 # Every function that include/ibdl.h declares (the ABI test checks this list
 # against the header and the library's exports).
@@ -48,7 +49,7 @@ class GeometryDesc(C.Structure):
         ("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p),
         ("nx", C.c_void_p), ("ny", C.c_void_p), ("nz", C.c_void_p),
         ("w", C.c_void_p), ("kappa", C.c_double), ("delta", C.c_int32),
-        ("bc", C.c_int32), ("precision", C.c_int32), ("reserved", C.c_int32),
+        ("bc", C.c_int32), ("precision", C.c_int32), ("disc", C.c_int32),
         ("eta", C.c_double),
     ]
 
@@ -260,7 +261,7 @@ def version() -> int:
 
 
 def make_desc(dim, n, box_len, origin, x, y, nx, ny, w, kappa, z=None, nz=None,
-              delta="peskin4", bc=DIRICHLET, precision=FP64, eta=0.0):
+              delta="peskin4", bc=DIRICHLET, precision=FP64, eta=0.0, disc=0):
     """Fill an ``ibdl_geometry_desc`` (the arrays must outlive its use)."""
     d = GeometryDesc()
     d.dim, d.n, d.box_len = int(dim), int(n), float(box_len)
@@ -274,6 +275,7 @@ def make_desc(dim, n, box_len, origin, x, y, nx, ny, w, kappa, z=None, nz=None,
     d.delta = DELTA[delta] if isinstance(delta, str) else int(delta)
     d.bc, d.precision = int(bc), int(precision)
     d.eta = float(eta)
+    d.disc = DISC[disc] if isinstance(disc, str) else int(disc)
     return d
 
 
@@ -364,7 +366,7 @@ class Geometry:
 
     def __init__(self, dim, n, box_len, origin, x, y, nx, ny, w, kappa, z=None,
                  nz=None, delta="peskin4", bc=DIRICHLET, precision=FP64, stream=None,
-                 eta=0.0):
+                 eta=0.0, disc=0):
         lib = load()
         d = GeometryDesc()
         d.dim, d.n, d.box_len = int(dim), int(n), float(box_len)
@@ -378,6 +380,7 @@ class Geometry:
         d.delta = DELTA[delta] if isinstance(delta, str) else int(delta)
         d.bc, d.precision = int(bc), int(precision)
         d.eta = float(eta)
+        d.disc = DISC[disc] if isinstance(disc, str) else int(disc)
         self._keep = (x, y, z, nx, ny, nz, w)
         h = C.c_void_p()
         _check(lib.ibdl_create_geometry(C.byref(d), _stream(stream), C.byref(h)))
@@ -389,7 +392,8 @@ class Geometry:
         self.nsys = d.m + 1 if d.eta > 0 else d.m
 
     @classmethod
-    def from_workload(cls, geom, bc=DIRICHLET, precision=FP64, stream=None, eta=0.0):
+    def from_workload(cls, geom, bc=DIRICHLET, precision=FP64, stream=None, eta=0.0,
+                      disc=0):
         """Build from a ``workloads.geometry.Geometry`` (host float64)."""
         X = np.ascontiguousarray(geom.X, dtype=np.float64)
         N = np.ascontiguousarray(geom.normals, dtype=np.float64)
@@ -399,7 +403,7 @@ class Geometry:
                    ncols[1], np.ascontiguousarray(geom.weights, dtype=np.float64),
                    geom.kappa, z=cols[2] if geom.dim == 3 else None,
                    nz=ncols[2] if geom.dim == 3 else None, delta=geom.delta, bc=bc,
-                   precision=precision, stream=stream, eta=eta)
+                   precision=precision, stream=stream, eta=eta, disc=disc)
 
     def close(self):
         if getattr(self, "_h", None):
