@@ -172,6 +172,7 @@ struct ibdl_geometry_s {
   PointData pd;
   SpectralWs<double> ws64;
   SpectralWs<float> ws32;
+  SpectralWs<dd> wsdd;  // double-float view of the float64 buffers (own tables)
   bool have32 = false;
   KrylovWs kry;
   double *vb = nullptr, *vx = nullptr, *vr = nullptr, *vt = nullptr, *vd = nullptr;
@@ -273,7 +274,8 @@ ibdl_status fft_tables(int n, const typename Cx<T>::type** tw_out, const T** s2_
   int dev = 0;
   IBDL_CU(cudaGetDevice(&dev));
   std::lock_guard<std::mutex> lk(g_tab_mu);
-  const auto key = std::make_tuple(dev, n, (int)sizeof(T));
+  const int tag = std::is_same<T, dd>::value ? 2 : (sizeof(T) == 8 ? 1 : 0);
+  const auto key = std::make_tuple(dev, n, tag);
   auto it = g_tabs.find(key);
   if (it == g_tabs.end()) {
     const int ntw = fft_tw_count(n);
@@ -369,6 +371,20 @@ template <>
 SpectralWs<float>& wsof<float>(ibdl_geometry_s* g) {
   return g->ws32;
 }
+template <>
+SpectralWs<dd>& wsof<dd>(ibdl_geometry_s* g) {
+  return g->wsdd;
+}
+
+// Precision of the float64-grade matvecs of a solve (residuals, right-hand
+// side): a float32-refined geometry takes double-float transforms (float64
+// spread and interpolation); IBDL_FP64 geometries, the spectral
+// discretisation and the completed system stay in native float64.
+int resid_prec(const ibdl_geometry_s* g) {
+  return g->precision == IBDL_FP32_REFINED && !g->grid.spectral && g->eta <= 0
+             ? IBDL_FP64_DF
+             : IBDL_FP64;
+}
 
 // Fourier-spectral discretisation (Sec. 5.1, Sec. 6.2.1): the divergence in
 // S~ is spectral too (Sec. 5.2), so each component S(q n_c) is transformed
@@ -420,7 +436,9 @@ ibdl_status spectral_field_solve(ibdl_geometry_s* g, const SpreadSrc& src, OutT*
 template <typename T, typename OutT>
 ibdl_status field_solve(ibdl_geometry_s* g, const SpreadSrc& src, OutT* out, cudaStream_t st,
                         bool band_only = false) {
-  if (g->grid.spectral) return spectral_field_solve<T, OutT>(g, src, out, st);
+  if constexpr (!std::is_same<T, dd>::value) {
+    if (g->grid.spectral) return spectral_field_solve<T, OutT>(g, src, out, st);
+  }
   SpectralWs<T>& ws = wsof<T>(g);
   SpreadSrc s = src;
   s.skip_empty_planes = band_only && !src.f_grid;
@@ -444,8 +462,20 @@ ibdl_status matvec(ibdl_geometry_s* g, const double* q, double* y, cudaStream_t 
   return IBDL_OK;
 }
 
+// y = A q with float64 spread / interpolation and double-float transforms.
+ibdl_status matvec_dd(ibdl_geometry_s* g, const double* q, double* y, cudaStream_t st) {
+  SpreadSrc src;
+  src.q_div = q;
+  src.coef_div = 1.0;
+  IBDL_TRY((field_solve<dd, double>(g, src, g->ws64.grid, st, true)));
+  const double jump = g->bc == IBDL_DIRICHLET ? 0.5 : -0.5;
+  IBDL_CU(launch_interp<double>(g->grid, g->pd, g->ws64.grid, q, jump, y, st));
+  return IBDL_OK;
+}
+
 ibdl_status matvec_prec(ibdl_geometry_s* g, int prec, const double* q, double* y,
                         cudaStream_t st) {
+  if (prec == IBDL_FP64_DF) return matvec_dd(g, q, y, st);
   if (prec == IBDL_FP32_REFINED) {
     IBDL_TRY(ensure32(g, st));
     return matvec<float>(g, q, y, st);
@@ -479,6 +509,9 @@ ibdl_status completed_matvec(ibdl_geometry_s* g, const double* q, double* y, cud
 // The operator of the geometry's boundary system (length nsys).
 ibdl_status sys_matvec(ibdl_geometry_s* g, int prec, const double* q, double* y,
                        cudaStream_t st) {
+  if (prec == IBDL_FP64_DF && (g->eta > 0 || g->grid.spectral))
+    return fail(IBDL_ERR_UNSUPPORTED, "double-float transforms: finite-difference, plain "
+                                      "system only");
   if (g->eta <= 0) return matvec_prec(g, prec, q, y, st);
   if (prec == IBDL_FP32_REFINED) {
     IBDL_TRY(ensure32(g, st));
@@ -506,7 +539,10 @@ ibdl_status build_rhs(ibdl_geometry_s* g, const double* bdata, const double* ggr
     SpreadSrc src;
     src.f_grid = ggrid;
     src.coef_grid = 1.0;
-    IBDL_TRY((field_solve<double, double>(g, src, g->ws64.grid, st, true)));
+    if (resid_prec(g) == IBDL_FP64_DF)
+      IBDL_TRY((field_solve<dd, double>(g, src, g->ws64.grid, st, true)));
+    else
+      IBDL_TRY((field_solve<double, double>(g, src, g->ws64.grid, st, true)));
     IBDL_CU(launch_interp<double>(g->grid, g->pd, g->ws64.grid, bdata, 1.0, b, st));
     return IBDL_OK;
   }
@@ -517,7 +553,10 @@ ibdl_status build_rhs(ibdl_geometry_s* g, const double* bdata, const double* ggr
     src.f_grid = ggrid;
     src.coef_grid = 1.0;
   }
-  IBDL_TRY((field_solve<double, double>(g, src, g->ws64.grid, st, true)));
+  if (resid_prec(g) == IBDL_FP64_DF)
+    IBDL_TRY((field_solve<dd, double>(g, src, g->ws64.grid, st, true)));
+  else
+    IBDL_TRY((field_solve<double, double>(g, src, g->ws64.grid, st, true)));
   IBDL_CU(launch_interp<double>(g->grid, g->pd, g->ws64.grid, nullptr, 0.0, b, st));
   return IBDL_OK;
 }
@@ -618,6 +657,8 @@ SolveInst make_inst(ibdl_geometry_s* g, const ibdl_solve_opts& o, int batch_size
   I.b = g->bins;
   I.w64 = g->ws64;
   I.w32 = g->ws32;
+  I.wdd = g->wsdd;
+  I.dd64 = resid_prec(g) == IBDL_FP64_DF && batch_size <= kDdMaxBatch;
   I.V = g->kry.V;
   I.ld = g->kry.ld;
   I.restart = o.restart;
@@ -979,6 +1020,15 @@ ibdl_status ibdl_create_geometry(const ibdl_geometry_desc* d, void* stream, ibdl
     if (e) return cleanup(cuda_fail(e, "configure kernels"));
   }
   if ((s = alloc_spectral<double>(g, g->ws64, st))) return cleanup(s);
+  {
+    // the double-float view shares the float64 spectrum (same 16-byte
+    // complex) and grid; it has its own twiddle and sin^2 tables
+    SpectralWs<dd>& w = g->wsdd;
+    w.spec = reinterpret_cast<cdd*>(g->ws64.spec);
+    w.grid = reinterpret_cast<dd*>(g->ws64.grid);
+    w.acc = reinterpret_cast<cdd*>(g->ws64.acc);
+    if ((s = fft_tables<dd>(n, &w.tw, &w.s2))) return cleanup(s);
+  }
   if (d->precision == IBDL_FP32_REFINED) {
     if ((s = ensure32(g, st))) return cleanup(s);
   }
@@ -1052,7 +1102,7 @@ ibdl_status ibdl_apply_precision(ibdl_geometry g, const double* q, double* y, in
   g_err.clear();
   IBDL_TRY(check_handle(g));
   if (!q || !y) return fail(IBDL_ERR_INVALID_ARG, "NULL q or y");
-  if (precision != IBDL_FP64 && precision != IBDL_FP32_REFINED)
+  if (precision != IBDL_FP64 && precision != IBDL_FP32_REFINED && precision != IBDL_FP64_DF)
     return fail(IBDL_ERR_INVALID_ARG, "unknown precision");
   cudaStream_t st = (cudaStream_t)stream;
   const double* qd;
@@ -1160,7 +1210,7 @@ ibdl_status ibdl_solve(ibdl_geometry g, const double* bdata, const double* g_gri
     if (x_zero) {
       IBDL_CU(cudaMemcpyAsync(g->vr, g->vb, sizeof(double) * ns, cudaMemcpyDeviceToDevice, st));
     } else {
-      IBDL_TRY(sys_matvec(g, IBDL_FP64, g->vx, g->vt, st));
+      IBDL_TRY(sys_matvec(g, resid_prec(g), g->vx, g->vt, st));
       run.matvecs++;
       IBDL_CU(launch_axpby(ns, 1.0, g->vb, -1.0, g->vt, g->vr, st));
     }
@@ -1198,7 +1248,7 @@ ibdl_status ibdl_solve(ibdl_geometry g, const double* bdata, const double* g_gri
         break;
       }
       IBDL_CU(launch_axpby(ns, 1.0, g->vx, 1.0, g->vd, g->vx, st));
-      IBDL_TRY(sys_matvec(g, IBDL_FP64, g->vx, g->vt, st));
+      IBDL_TRY(sys_matvec(g, resid_prec(g), g->vx, g->vt, st));
       run.matvecs++;
       IBDL_CU(launch_axpby(ns, 1.0, g->vb, -1.0, g->vt, g->vr, st));
       IBDL_TRY(vec_norm(g, g->vr, &rnorm, st));

@@ -10,6 +10,8 @@
 // persistent kernel an SM's L1 may hold a line from an earlier phase.
 #pragma once
 
+#include <type_traits>
+
 #include "ibdl_internal.cuh"
 
 namespace ibdl {
@@ -20,6 +22,41 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
+// ---- double-float arithmetic (the type dd, ibdl_internal.cuh) --------------
+// These rely on every float operation being rounded on its own: no term
+// below is a product added to something, so nothing is contracted into a
+// fused multiply-add except where fmaf is written out.
+__device__ __forceinline__ dd operator+(dd a, dd b) {
+  const float s = a.hi + b.hi;  // two-sum of the high parts
+  const float bb = s - a.hi;
+  float e = (a.hi - (s - bb)) + (b.hi - bb);
+  e += a.lo + b.lo;
+  const float h = s + e;        // fast two-sum: renormalise
+  return dd(h, e - (h - s));
+}
+__device__ __forceinline__ dd operator-(dd a) { return dd(-a.hi, -a.lo); }
+__device__ __forceinline__ dd operator-(dd a, dd b) { return a + (-b); }
+__device__ __forceinline__ dd operator*(dd a, dd b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);  // exact error of the high product
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  const float h = p + e;
+  return dd(h, e - (h - p));
+}
+__device__ __forceinline__ dd& operator+=(dd& a, dd b) { return a = a + b; }
+__device__ __forceinline__ dd& operator-=(dd& a, dd b) { return a = a - b; }
+__device__ __forceinline__ dd& operator*=(dd& a, dd b) { return a = a * b; }
+__device__ __forceinline__ bool operator>(dd a, dd b) {
+  return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo);
+}
+__device__ __forceinline__ cdd cmul(cdd a, cdd b) {
+  cdd r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+
 template <typename C> __device__ __forceinline__ C cadd(C a, C b) {
   C r;
   r.x = a.x + b.x;
@@ -304,6 +341,17 @@ __device__ __forceinline__ cx_t<T>* fft_run(cx_t<T>* src, cx_t<T>* dst, int lg, 
   }
 }
 
+template <typename V>
+__device__ __forceinline__ void copy_to_shared(V* dst, const V* __restrict__ src, int count);
+// double-float tables move as their float vectors
+__device__ __forceinline__ void copy_to_shared(cdd* dst, const cdd* __restrict__ src,
+                                               int count) {
+  copy_to_shared(reinterpret_cast<float4*>(dst), reinterpret_cast<const float4*>(src), count);
+}
+__device__ __forceinline__ void copy_to_shared(dd* dst, const dd* __restrict__ src, int count) {
+  copy_to_shared(reinterpret_cast<float2*>(dst), reinterpret_cast<const float2*>(src), count);
+}
+
 // Copies `count` values from global (around L1) to shared memory.
 template <typename V>
 __device__ __forceinline__ void copy_to_shared(V* dst, const V* __restrict__ src, int count) {
@@ -330,6 +378,13 @@ __device__ __forceinline__ void copy_to_shared(V* dst, const V* __restrict__ src
 template <typename T> __device__ __forceinline__ T recip_symbol(T x);
 template <> __device__ __forceinline__ float recip_symbol<float>(float x) {
   return __frcp_rn(x);
+}
+template <> __device__ __forceinline__ dd recip_symbol<dd>(dd x) {
+  // Newton from the float reciprocal of the high part, two steps in
+  // double-float (24 -> 48 bits)
+  dd r(__frcp_rn(x.hi), 0.0f);
+  r = r + r * (dd(1) - x * r);
+  return r + r * (dd(1) - x * r);
 }
 template <> __device__ __forceinline__ double recip_symbol<double>(double x) {
   double r = (double)__frcp_rn((float)x);
@@ -364,6 +419,27 @@ template <> struct Pair<double> {
     p[1] = b;
   }
 };
+
+template <> struct Pair<dd> {
+  cdd a, b;
+  __device__ __forceinline__ void load(const cdd* p) {
+    const float4 u = __ldcg(reinterpret_cast<const float4*>(p));
+    const float4 v = __ldcg(reinterpret_cast<const float4*>(p + 1));
+    a.x = dd(u.x, u.y);
+    a.y = dd(u.z, u.w);
+    b.x = dd(v.x, v.y);
+    b.y = dd(v.z, v.w);
+  }
+  __device__ __forceinline__ void store(cdd* p) const {
+    reinterpret_cast<float4*>(p)[0] = make_float4(a.x.hi, a.x.lo, a.y.hi, a.y.lo);
+    reinterpret_cast<float4*>(p)[1] = make_float4(b.x.hi, b.x.lo, b.y.hi, b.y.lo);
+  }
+};
+
+// The precision of the spread (shared-memory atomics) for transforms in T:
+// double-float transforms take a float64 spread, converted once per tile.
+template <typename T> struct SpreadType { using type = T; };
+template <> struct SpreadType<dd> { using type = double; };
 
 template <typename T> __device__ __forceinline__ T wload(const PointData& p, int c, int t, int i);
 template <> __device__ __forceinline__ double wload<double>(const PointData& p, int c, int t,
@@ -426,12 +502,13 @@ __device__ __forceinline__ void phase_rows_fwd(const GridDesc& g, const PointDat
                                const cx_t<T>* __restrict__ tw, double* write_grid, int tile,
                                unsigned char* smem) {
   using C = cx_t<T>;
+  using S = typename SpreadType<T>::type;  // the spread's precision
   const int n = g.n, lg = g.log2n, mask = n - 1, R = b.rows, npen = R >> 1;
   const int PS = pen_stride(n);
   C* bufA = reinterpret_cast<C*>(smem);
   C* bufB = bufA + (size_t)npen * PS;
   C* tws = bufB + (size_t)npen * PS;
-  T* rows = reinterpret_cast<T*>(bufA);  // row r, column x at [((r>>1)*PS + padi(x))*2 + (r&1)]
+  S* rows = reinterpret_cast<S*>(bufA);  // row r, column x at [((r>>1)*PS + padi(x))*2 + (r&1)]
   const int ngroups = n / R;
   const int z = (D == 3) ? tile / ngroups : 0;
   const int y0 = (tile % ngroups) * R;
@@ -463,8 +540,8 @@ __device__ __forceinline__ void phase_rows_fwd(const GridDesc& g, const PointDat
 
   for (int e = tid; e < R * n; e += nt) {
     const int r = e >> lg, x = e & mask;
-    T v = 0;
-    if (src.f_grid) v = (T)(src.coef_grid * src.f_grid[row0 + (size_t)r * n + x]);
+    S v = 0;
+    if (src.f_grid) v = (S)(src.coef_grid * src.f_grid[row0 + (size_t)r * n + x]);
     rows[((r >> 1) * PS + padi(x)) * 2 + (r & 1)] = v;
   }
   if (!write_grid) copy_to_shared(tws, tw, fft_tw_count(n));
@@ -479,12 +556,12 @@ __device__ __forceinline__ void phase_rows_fwd(const GridDesc& g, const PointDat
   //   cA = q w/h^d (ny dW_y[bb] W_z[c-1] + nz W_y[bb-1] dW_z[c]) + v w/h^d W_y[bb-1] W_z[c-1]
   //   cB = q w/h^d nx W_y[bb-1] W_z[c-1] / (2h),
   // staged as  cA = P dW_y[bb] + Q W_y[bb-1],  cB = X W_y[bb-1].
-  const T inv2h = (T)g.inv2h;
+  const S inv2h = (S)g.inv2h;
   constexpr int kWords = 11;  // wx[4], wy[4], P, Q, X
-  const int per_pt = kWords * (int)sizeof(T) + 2 * (int)sizeof(int);
+  const int per_pt = kWords * (int)sizeof(S) + 2 * (int)sizeof(int);
   int KP = (int)((size_t)npen * PS * sizeof(C) / per_pt);
   if (KP > 256) KP = 256;
-  T* sv = reinterpret_cast<T*>(bufB);         // [kWords][KP]
+  S* sv = reinterpret_cast<S*>(bufB);         // [kWords][KP]
   int* sxb = reinterpret_cast<int*>(sv + kWords * KP);
   int* syb = sxb + KP;
   for (int c0 = lo; c0 < hi; c0 += KP) {
@@ -492,33 +569,33 @@ __device__ __forceinline__ void phase_rows_fwd(const GridDesc& g, const PointDat
     for (int t = tid; t < np; t += nt) {
       const int i = __ldg(b.pts + c0 + t);
       int ok = 1;
-      T wz = (T)1, dz = (T)0;
+      S wz = (S)1, dz = (S)0;
       if (D == 3) {
         const int cz = (z - (__ldg(p.base[2] + i) - 1)) & mask;
         ok = cz < kBoxSide;
-        wz = wload<T>(p, 2, cz - 1, i);
-        dz = (wload<T>(p, 2, cz, i) - wload<T>(p, 2, cz - 2, i)) * inv2h;
+        wz = wload<S>(p, 2, cz - 1, i);
+        dz = (wload<S>(p, 2, cz, i) - wload<S>(p, 2, cz - 2, i)) * inv2h;
       }
-      T P = 0, Q = 0, X = 0;
+      S P = 0, Q = 0, X = 0;
       // float32: one conversion (q) per staged point; the normals and
       // weights have float copies (float64 work is slow on GB300)
-      const T wi = pt_w<T>(p, i);
+      const S wi = pt_w<S>(p, i);
       if (src.q_div) {
-        const T amp = (T)src.coef_div * (T)__ldcg(src.q_div + i) * wi;
-        P = amp * pt_nrm<T>(p, 1, i) * wz;
-        if (D == 3) Q = amp * pt_nrm<T>(p, 2, i) * dz;
-        X = amp * pt_nrm<T>(p, 0, i) * wz * inv2h;
+        const S amp = (S)src.coef_div * (S)__ldcg(src.q_div + i) * wi;
+        P = amp * pt_nrm<S>(p, 1, i) * wz;
+        if (D == 3) Q = amp * pt_nrm<S>(p, 2, i) * dz;
+        X = amp * pt_nrm<S>(p, 0, i) * wz * inv2h;
       }
       if (src.v_plain) {
-        T v = (T)src.coef_plain * (T)__ldcg(src.v_plain + i) * wi * wz;
-        if (src.plain_nrm >= 0) v *= pt_nrm<T>(p, src.plain_nrm, i);
+        S v = (S)src.coef_plain * (S)__ldcg(src.v_plain + i) * wi * wz;
+        if (src.plain_nrm >= 0) v *= pt_nrm<S>(p, src.plain_nrm, i);
         Q += v;
       }
       if (!ok) P = Q = X = 0;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        sv[u * KP + t] = wload<T>(p, 0, u, i);
-        sv[(4 + u) * KP + t] = wload<T>(p, 1, u, i);
+        sv[u * KP + t] = wload<S>(p, 0, u, i);
+        sv[(4 + u) * KP + t] = wload<S>(p, 1, u, i);
       }
       sv[8 * KP + t] = P;
       sv[9 * KP + t] = Q;
@@ -531,28 +608,28 @@ __device__ __forceinline__ void phase_rows_fwd(const GridDesc& g, const PointDat
       const int t = e / kBoxSide, bb = e - t * kBoxSide;
       const int ry = ((syb[t] + bb) & mask) - y0;
       if ((unsigned)ry >= (unsigned)R) continue;
-      const T P = sv[8 * KP + t], Q = sv[9 * KP + t], X = sv[10 * KP + t];
-      const T wyb = (bb >= 1 && bb <= 4) ? sv[(4 + bb - 1) * KP + t] : (T)0;
-      const T wy0 = bb <= 3 ? sv[(4 + bb) * KP + t] : (T)0;
-      const T wy2 = bb >= 2 ? sv[(4 + bb - 2) * KP + t] : (T)0;
-      const T cA = P * (wy0 - wy2) * inv2h + Q * wyb;
-      const T cB = X * wyb;
-      if (cA == (T)0 && cB == (T)0) continue;
-      T wx[6];
+      const S P = sv[8 * KP + t], Q = sv[9 * KP + t], X = sv[10 * KP + t];
+      const S wyb = (bb >= 1 && bb <= 4) ? sv[(4 + bb - 1) * KP + t] : (S)0;
+      const S wy0 = bb <= 3 ? sv[(4 + bb) * KP + t] : (S)0;
+      const S wy2 = bb >= 2 ? sv[(4 + bb - 2) * KP + t] : (S)0;
+      const S cA = P * (wy0 - wy2) * inv2h + Q * wyb;
+      const S cB = X * wyb;
+      if (cA == (S)0 && cB == (S)0) continue;
+      S wx[6];
       wx[0] = 0;
       wx[5] = 0;
 #pragma unroll
       for (int u = 0; u < 4; ++u) wx[u + 1] = sv[u * KP + t];  // wx[k] = W_x[k-1]
-      T* rowp = rows + (size_t)(ry >> 1) * PS * 2 + (ry & 1);
+      S* rowp = rows + (size_t)(ry >> 1) * PS * 2 + (ry & 1);
       const int xb = sxb[t];
 #pragma unroll
       for (int a = 0; a < kBoxSide; ++a) {
         // W_x[a] - W_x[a-2] = wx[a+1] - wx[a-1]
-        const T wa1 = wx[a];
-        const T wa = (a + 1 < 6) ? wx[a + 1] : (T)0;
-        const T wam2 = (a >= 1) ? wx[a - 1] : (T)0;
-        const T val = wa1 * cA + (wa - wam2) * cB;
-        if (val != (T)0) atomicAdd(rowp + (size_t)padi((xb + a) & mask) * 2, val);
+        const S wa1 = wx[a];
+        const S wa = (a + 1 < 6) ? wx[a + 1] : (S)0;
+        const S wam2 = (a >= 1) ? wx[a - 1] : (S)0;
+        const S val = wa1 * cA + (wa - wam2) * cB;
+        if (val != (S)0) atomicAdd(rowp + (size_t)padi((xb + a) & mask) * 2, val);
       }
     }
     __syncthreads();
@@ -567,6 +644,12 @@ __device__ __forceinline__ void phase_rows_fwd(const GridDesc& g, const PointDat
     return;
   }
 
+  if (!std::is_same<S, T>::value) {
+    // float64 spread -> double-float, in place (each thread its own slots)
+    T* rt = reinterpret_cast<T*>(bufA);
+    for (int e = tid; e < npen * PS * 2; e += nt) rt[e] = T(rows[e]);
+    __syncthreads();
+  }
   C* res = fft_run<T, false>(bufA, bufB, lg, npen, tws);
 
   for (int e = tid; e < (half + 1) * npen; e += nt) {

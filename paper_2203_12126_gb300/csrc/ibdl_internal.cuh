@@ -27,6 +27,26 @@ template <> struct Cx<double> { using type = double2; };
 template <> struct Cx<float> { using type = float2; };
 template <typename T> using cx_t = typename Cx<T>::type;
 
+// Double-float: the unevaluated sum hi + lo of two floats (|lo| <= ulp(hi)/2),
+// about 48 significant bits.  The float64-grade transforms of the refined
+// solver's residual and right-hand side run in it: GB300 issues float32
+// arithmetic at some sixty times its float64 rate.  Arithmetic (device,
+// ibdl_device.cuh): Knuth's two-sum for sums, the fused-multiply-add form of
+// Dekker's two-product for products, each renormalised by Dekker's fast
+// two-sum.
+struct __align__(8) dd {
+  float hi, lo;
+  dd() = default;
+  __host__ __device__ constexpr dd(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ dd(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+  __host__ __device__ constexpr dd(int v) : hi((float)v), lo(0.0f) {}
+  __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+struct __align__(16) cdd {
+  dd x, y;
+};
+template <> struct Cx<dd> { using type = cdd; };
+
 // Row tile height of the fused spread + x-FFT and x-iFFT kernels.
 constexpr int kBoxSide = 6;   // nodes per axis touched by the centred
                               // difference of a 4-point delta

@@ -9,6 +9,11 @@ constexpr int kSolverThreads = 256;  // threads per block; also the vector chunk
 constexpr int kMaxBatch = 512;       // instances per persistent launch
 constexpr int kSingleMax = 4096;     // points up to which one block does the vector work
 constexpr int kSingleMinBatch = 8;   // ... when at least this many instances share a launch
+// Largest launch whose float64-grade matvecs transform in double-float: in a
+// few-instance launch they sit on the critical path and the float64 pipe's
+// latency dominates; a saturated batch is bound by issue slots, where
+// double-float's extra float32 instructions cost more than they save.
+constexpr int kDdMaxBatch = 16;
 // Scheduler words per instance in the solver's barrier buffer (4 + this many
 // per instance, 32-bit words): claim counter, done counter, phase descriptor.
 constexpr int kSchedWords = 12;
@@ -29,6 +34,8 @@ struct SolveInst {
   Bins b;
   SpectralWs<double> w64;
   SpectralWs<float> w32;
+  SpectralWs<dd> wdd;  // double-float view of w64's buffers
+  int dd64;            // 1: the float64-grade matvecs transform in double-float
   double* V;        // (restart + 1) x ld
   int ld;
   int restart;

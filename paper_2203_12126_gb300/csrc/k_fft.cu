@@ -68,6 +68,11 @@ static int pencil_threads(int n, int c) {
 
 static int rows_threads(int n, int npen) { return clamp_threads(npen * n / 8); }
 
+// launch-profile label by element type: float, double, double-float
+template <typename T> static const char* tag3(const char* f32, const char* f64, const char* d2) {
+  return std::is_same<T, dd>::value ? d2 : (sizeof(T) == 8 ? f64 : f32);
+}
+
 template <typename T>
 cudaError_t launch_rows_fwd(const GridDesc& g, const PointData& p, const Bins& b,
                             const SpreadSrc& src, SpectralWs<T>& ws, double* write_grid,
@@ -80,7 +85,7 @@ cudaError_t launch_rows_fwd(const GridDesc& g, const PointData& p, const Bins& b
     k_rows_fwd<T, 2><<<b.ntiles, thr, smem, st>>>(g, p, b, src, ws.spec, ws.tw, write_grid);
   else
     k_rows_fwd<T, 3><<<b.ntiles, thr, smem, st>>>(g, p, b, src, ws.spec, ws.tw, write_grid);
-  count_launch(sizeof(T) == 8 ? "rows_fwd_f64" : "rows_fwd_f32", st);
+  count_launch(tag3<T>("rows_fwd_f32", "rows_fwd_f64", "rows_fwd_dd"), st);
   return check_launch();
 }
 
@@ -95,7 +100,7 @@ cudaError_t launch_rows_inv(const GridDesc& g, const Bins& b, SpectralWs<T>& ws,
     k_rows_inv<T, 2, OutT><<<b.ntiles, thr, smem, st>>>(g, b, ws.spec, ws.tw, out, band_only);
   else
     k_rows_inv<T, 3, OutT><<<b.ntiles, thr, smem, st>>>(g, b, ws.spec, ws.tw, out, band_only);
-  count_launch(sizeof(T) == 8 ? "rows_inv_f64" : "rows_inv_f32", st);
+  count_launch(tag3<T>("rows_inv_f32", "rows_inv_f64", "rows_inv_dd"), st);
   return check_launch();
 }
 
@@ -111,9 +116,10 @@ static cudaError_t run_pencils(const GridDesc& g, const PencilLayout& L, Spectra
   prof_begin(st);
   k_pencils<T, MODE><<<blocks, thr, smem, st>>>(g, L, ws.spec, ws.tw, ws.s2, cfac, scale0,
                                                  zskip, ngroups, zempty);
-  static const char* names[2][3] = {{"pencils_fwd_f32", "pencils_inv_f32", "pencils_solve_f32"},
-                                    {"pencils_fwd_f64", "pencils_inv_f64", "pencils_solve_f64"}};
-  count_launch(names[sizeof(T) == 8 ? 1 : 0][MODE], st);
+  static const char* names[3][3] = {{"pencils_fwd_f32", "pencils_inv_f32", "pencils_solve_f32"},
+                                    {"pencils_fwd_f64", "pencils_inv_f64", "pencils_solve_f64"},
+                                    {"pencils_fwd_dd", "pencils_inv_dd", "pencils_solve_dd"}};
+  count_launch(names[std::is_same<T, dd>::value ? 2 : (sizeof(T) == 8 ? 1 : 0)][MODE], st);
   return check_launch();
 }
 
@@ -262,6 +268,13 @@ cudaError_t configure_fft_kernels(int, int) {
   raise_smem(k_pencils<float, 0>);
   raise_smem(k_pencils<float, 1>);
   raise_smem(k_pencils<float, 2>);
+  raise_smem(k_rows_fwd<dd, 2>);
+  raise_smem(k_rows_fwd<dd, 3>);
+  raise_smem(k_rows_inv<dd, 2, double>);
+  raise_smem(k_rows_inv<dd, 3, double>);
+  raise_smem(k_pencils<dd, 0>);
+  raise_smem(k_pencils<dd, 1>);
+  raise_smem(k_pencils<dd, 2>);
   done = true;
   return cudaGetLastError();
 }
@@ -283,6 +296,13 @@ template cudaError_t launch_rows_inv<float, double>(const GridDesc&, const Bins&
                                                     bool);
 template cudaError_t launch_spectral_solve<double>(const GridDesc&, SpectralWs<double>&,
                                                    cudaStream_t, const Bins*, bool);
+template cudaError_t launch_rows_fwd<dd>(const GridDesc&, const PointData&, const Bins&,
+                                         const SpreadSrc&, SpectralWs<dd>&, double*,
+                                         cudaStream_t);
+template cudaError_t launch_rows_inv<dd, double>(const GridDesc&, const Bins&, SpectralWs<dd>&,
+                                                 double*, cudaStream_t, bool);
+template cudaError_t launch_spectral_solve<dd>(const GridDesc&, SpectralWs<dd>&, cudaStream_t,
+                                               const Bins*, bool);
 template cudaError_t launch_spectral_solve<float>(const GridDesc&, SpectralWs<float>&,
                                                   cudaStream_t, const Bins*, bool);
 template int fft_kernels_per_solve<double>(int);

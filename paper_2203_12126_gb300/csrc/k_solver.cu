@@ -148,6 +148,10 @@ template <>
 __device__ __forceinline__ SpectralWs<float> ws_of<float>(const SolveInst& I) {
   return I.w32;
 }
+template <>
+__device__ __forceinline__ SpectralWs<dd> ws_of<dd>(const SolveInst& I) {
+  return I.wdd;
+}
 
 __device__ __forceinline__ bool is_mv(int a) {
   return a == ACT_MV_ARNOLDI || a == ACT_MV_RESIDUAL || a == ACT_RHS;
@@ -194,7 +198,10 @@ __device__ __noinline__ void solver_rows_fwd(const SolveInst& I, const double* q
 template <typename T, int D>
 __device__ __noinline__ void solver_rows_inv(const SolveInst& I, int item, unsigned char* smem) {
   const SpectralWs<T> ws = ws_of<T>(I);
-  phase_rows_inv<T, D, T>(I.g, I.b, ws.spec, ws.tw, ws.grid, item, smem, true);
+  if constexpr (std::is_same<T, dd>::value)  // double-float writes the float64 grid
+    phase_rows_inv<T, D, double>(I.g, I.b, ws.spec, ws.tw, I.w64.grid, item, smem, true);
+  else
+    phase_rows_inv<T, D, T>(I.g, I.b, ws.spec, ws.tw, ws.grid, item, smem, true);
 }
 
 template <typename T, int MODE>
@@ -852,6 +859,8 @@ __device__ void run_item(const SolveInst& I, SolveState* S, const PhaseDesc& d, 
   if (d.phase < 5) {
     if (v.prec)
       mv_item<float>(I, v, d.phase, item, smem);
+    else if (I.dd64)
+      mv_item<dd>(I, v, d.phase, item, smem);
     else
       mv_item<double>(I, v, d.phase, item, smem);
   } else if (d.phase == kPhaseD) {

@@ -7,6 +7,9 @@ Tolerances (relative, 2-norm unless stated):
   so 1e-12 leaves three orders of margin while any indexing or sign error
   shows up at O(1).
 * float32 operators: 1e-5 (the raw float32 matvec bound).
+* double-float transforms (IBDL_FP64_DF, the refined solver's residual
+  operator): 1e-12 as for float64 (about 2^-48 per operation on either side
+  of the transforms, float64 spread and interpolation).
 * float64 solves at tol 1e-12 vs the dense-LU density: 1e-10.
 * float32-refined solves at tol 1e-10 vs the dense-LU density: 1e-8.
 """
@@ -157,7 +160,7 @@ def test_interp_parity(name, prec, tol):
 
 @pytest.mark.parametrize("name", list(ALL))
 @pytest.mark.parametrize("bc", [configs.DIRICHLET, configs.NEUMANN])
-@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-5)])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-5), (2, 1e-12)])
 def test_matvec_parity(name, bc, prec, tol):
     g = ALL[name]()
     G = make(g, bc=bc)
@@ -205,10 +208,10 @@ def test_matvec_parity_full_c2(bc):
     g = p.geom
     q = density(g, 6)
     ref = O.Operator(g, bc).apply(q)
-    for prec, tol in ((0, 1e-12), (1, 1e-5)):
-        G = make(g, bc=bc, precision=prec)
+    for prec, tol in ((0, 1e-12), (1, 1e-5), (2, 1e-12)):
+        G = make(g, bc=bc, precision=min(prec, 1))
         y = torch.empty(g.m, dtype=torch.float64, device=DEV)
-        G.apply(gpu(q), y)
+        G.apply(gpu(q), y, precision=prec)
         assert rel(host(y), ref) <= tol
         G.close()
 
@@ -220,10 +223,10 @@ def test_matvec_parity_full_c3_sampled():
     g = p.geom
     q = density(g, 9)
     ref = O.Operator(g, configs.NEUMANN).apply(q)
-    for prec, tol in ((0, 1e-12), (1, 1e-5)):
-        G = make(g, bc=configs.NEUMANN, precision=prec)
+    for prec, tol in ((0, 1e-12), (1, 1e-5), (2, 1e-12)):
+        G = make(g, bc=configs.NEUMANN, precision=min(prec, 1))
         y = torch.empty(g.m, dtype=torch.float64, device=DEV)
-        G.apply(gpu(q), y)
+        G.apply(gpu(q), y, precision=prec)
         assert rel(host(y), ref) <= tol
         G.close()
 
