@@ -6,7 +6,7 @@
 
 ``matvec`` applies the boundary operator of the 3D sphere (c3: N=256^3,
 M=38039) or the 2D star (c2: N=1024^2, M=3525) ``reps`` times (default 5)
-in float32 (f32) or float64 (f64); ``solve`` runs ``reps`` (default 2)
+in float32 (f32), float64 (f64) or with double-float transforms (dd); ``solve`` runs ``reps`` (default 2)
 float32-refined Dirichlet solves of c2 at tolerance 1e-8 through the
 persistent solver; ``pair`` runs ``reps`` (default 2) batched launches of the
 benchmark's step, the c2 Dirichlet + Neumann pair in one persistent launch.
@@ -34,15 +34,16 @@ def main(argv):
     prob = configs.c3() if case == "c3" else configs.c2()
     dev = torch.device("cuda:0")
     if what == "matvec":
-        prec = 1 if (len(argv) < 3 or argv[2] == "f32") else 0
+        tag = argv[2] if len(argv) > 2 else "f32"
+        prec = {"f32": 1, "f64": 0, "dd": 2}[tag]
         reps = int(argv[3]) if len(argv) > 3 else 5
-        g = pkg.Geometry.from_workload(prob.geom, bc=prob.bc, precision=prec)
+        g = pkg.Geometry.from_workload(prob.geom, bc=prob.bc, precision=min(prec, 1))
         q = torch.tensor(np.random.default_rng(0).standard_normal(prob.geom.m), device=dev)
         y = torch.empty_like(q)
         for _ in range(reps):
             g.apply(q, y, precision=prec)
         torch.cuda.synchronize()
-        print(f"matvec {case} {'f32' if prec else 'f64'} x{reps}: |y| = {float(y.norm()):.6e}")
+        print(f"matvec {case} {tag} x{reps}: |y| = {float(y.norm()):.6e}")
     elif what == "solve":
         reps = int(argv[2]) if len(argv) > 2 else 2
         g = pkg.Geometry.from_workload(prob.geom, bc=prob.bc, precision=pkg.FP32_REFINED)
