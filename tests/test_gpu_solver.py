@@ -235,3 +235,38 @@ def test_scheduler_stress_many_tiny_instances():
     batch.close()
     for G in geoms:
         G.close()
+
+
+def test_double_float_and_float64_residuals_agree():
+    """Float32-refined launches of at most 16 instances take double-float
+    residuals and right-hand sides, larger ones float64: the same refined
+    problems solved both ways meet the dense-LU solution to 1e-8 (tol 1e-10)."""
+    probs = [configs.table1(64, 1.0), configs.c1()]
+    geoms, bs, refs = [], [], []
+    for p in probs:
+        for bc in (configs.DIRICHLET, configs.NEUMANN):
+            g = p.geom
+            b = np.cos(2 * np.arange(g.m) * 2 * np.pi / g.m) + 0.3
+            refs.append(O.solve_dense(g, bc, b))
+            geoms.append(pkg.Geometry.from_workload(g, bc=bc, precision=ibdl.FP32_REFINED))
+            bs.append(gpu(b))
+    small = ibdl.Batch(4)
+    q_small = [torch.zeros(g.m, dtype=torch.float64, device=DEV) for g in geoms]
+    infos = small.solve(geoms, bs, q_small, tol=1e-10)
+    assert all(f["status"] == 0 for f in infos)
+    # 20 entries: the same four problems on fresh handles, five times over
+    many = [pkg.Geometry.from_workload(probs[k // 2 % 2].geom,
+                                      bc=(configs.DIRICHLET, configs.NEUMANN)[k % 2],
+                                      precision=ibdl.FP32_REFINED) for k in range(20)]
+    big = ibdl.Batch(20)
+    q_big = [torch.zeros(g.m, dtype=torch.float64, device=DEV) for g in many]
+    infos = big.solve(many, [bs[k % 4] for k in range(20)], q_big, tol=1e-10)
+    assert all(f["status"] == 0 for f in infos)
+    for k in range(4):
+        assert rel(q_small[k].cpu().numpy(), refs[k]) <= 1e-8
+    for k in range(20):
+        assert rel(q_big[k].cpu().numpy(), refs[k % 4]) <= 1e-8
+    small.close()
+    big.close()
+    for g in geoms + many:
+        g.close()
