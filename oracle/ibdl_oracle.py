@@ -25,7 +25,9 @@ Layer method" (arXiv:2203.12126):
 * interior indicator      App. D: Delta u + S~ 1 = 0, mean-zero solve, shift by
                           the box-corner value, threshold at 1/2
 * near-boundary values    Sec. 5.5, App. A (2D): linear interpolation between
-                          the chord point x_A and a point x_B m2 h inside
+                          the chord point x_A and a point x_B m2 h inside; its
+                          3D generalisation (Sec. 6.7) on the triangle of the
+                          three nearest points
 * Fourier-spectral        Sec. 5.1-5.2, Sec. 6.2.1, Sec. 6.7: spectral Laplacian
   discretisation          and (matching it, Sec. 5.2) spectral divergence in S~
 
@@ -646,6 +648,92 @@ def near_boundary_values(geom, u, ub, inside, m1, m2, nodes=None):
         LAB = np.linalg.norm(xB - xA)
         out[iy, ix] = uA * np.linalg.norm(xB - p) / LAB + uB * dA / LAB
     return out
+
+
+def near_boundary_values_3d(geom, u, ub, inside, m1, m2, nodes=None):
+    """The 3D near-boundary step of Sec. 6.7 ("a direct generalization" of
+    App. A), read as: for a node x_p of Omega whose nearest boundary point is
+    closer than m1 h,
+      1. x_1, x_2, x_3 = its three nearest boundary points (ties: lower index);
+      2. x_A = the orthogonal foot of x_p on their plane, with barycentric
+         coordinates (l_1, l_2, l_3) clamped to >= 0 and renormalised to sum 1
+         (the point of the triangle, or of its edges, nearest in that sense);
+         a degenerate triangle (zero area) takes x_A = x_1;
+      3. u(x_A) = sum l_k U_b(x_k);
+      4. x_B = x_A + m2 h (x_p - x_A) / |x_p - x_A|;
+      5. u(x_B) = the trilinear interpolation of u on the cell holding x_B;
+      6. u(x_p) = u(x_A)|x_B - x_p| / |x_B - x_A| + u(x_B)|x_A - x_p| / |x_B - x_A|.
+    A node at x_A takes u(x_A).  u, inside: grids (n, n, n) indexed [z, y, x]."""
+    box = Box.of(geom)
+    assert box.d == 3
+    n, h = box.n, box.h
+    X = np.asarray(geom.X, dtype=np.float64)
+    ub = np.asarray(ub, dtype=np.float64)
+    uin = np.asarray(u, dtype=np.float64).reshape(n, n, n)
+    out = uin.copy()
+    ins = np.asarray(inside).reshape(n, n, n)
+    thresh = (m1 * h) * (m1 * h)
+    ox, oy, oz = float(box.o[0]), float(box.o[1]), float(box.o[2])
+    todo = range(n ** 3) if nodes is None else sorted(int(j) for j in nodes)
+    for j in todo:
+        iz, r = divmod(j, n * n)
+        iy, ix = divmod(r, n)
+        if not ins[iz, iy, ix]:
+            continue
+        px, py, pz = ox + ix * h, oy + iy * h, oz + iz * h
+        dx, dy, dz = px - X[:, 0], py - X[:, 1], pz - X[:, 2]
+        d2 = dx * dx + dy * dy + dz * dz
+        order = np.argsort(d2, kind="stable")
+        if not d2[order[0]] < thresh:
+            continue
+        i1, i2, i3 = (int(k) for k in order[:3])
+        p = np.array([px, py, pz])
+        lam = _barycentric_clamped(p, X[i1], X[i2], X[i3])
+        if lam is None:
+            xA, uA = X[i1].copy(), ub[i1]
+        else:
+            xA = lam[0] * X[i1] + lam[1] * X[i2] + lam[2] * X[i3]
+            uA = lam[0] * ub[i1] + lam[1] * ub[i2] + lam[2] * ub[i3]
+        dA = np.linalg.norm(p - xA)
+        if dA == 0.0:
+            out[iz, iy, ix] = uA
+            continue
+        xB = xA + (p - xA) / dA * (m2 * h)
+        rr = [(xB[0] - ox) / h, (xB[1] - oy) / h, (xB[2] - oz) / h]
+        jj = [math.floor(v) for v in rr]
+        ff = [rr[c] - jj[c] for c in range(3)]
+        uB = 0.0
+        for cz in (0, 1):
+            for cy in (0, 1):
+                for cx in (0, 1):
+                    wgt = ((ff[0] if cx else 1.0 - ff[0]) * (ff[1] if cy else 1.0 - ff[1])
+                           * (ff[2] if cz else 1.0 - ff[2]))
+                    uB += wgt * uin[(jj[2] + cz) % n, (jj[1] + cy) % n, (jj[0] + cx) % n]
+        LAB = np.linalg.norm(xB - xA)
+        out[iz, iy, ix] = uA * np.linalg.norm(xB - p) / LAB + uB * dA / LAB
+    return out
+
+
+def _barycentric_clamped(p, a, b, c):
+    """Barycentric coordinates of the orthogonal foot of p on the plane of
+    the triangle (a, b, c), clamped to >= 0 and renormalised; None for a
+    degenerate triangle."""
+    e1, e2, w = b - a, c - a, p - a
+    d11, d12, d22 = _dot3(e1, e1), _dot3(e1, e2), _dot3(e2, e2)
+    w1, w2 = _dot3(w, e1), _dot3(w, e2)
+    det = d11 * d22 - d12 * d12
+    if not det > 0.0:
+        return None
+    l2 = (d22 * w1 - d12 * w2) / det
+    l3 = (d11 * w2 - d12 * w1) / det
+    lam = [max(1.0 - l2 - l3, 0.0), max(l2, 0.0), max(l3, 0.0)]
+    sm = lam[0] + lam[1] + lam[2]
+    return [lam[0] / sm, lam[1] / sm, lam[2] / sm]
+
+
+def _dot3(u, v):
+    """u . v summed left to right (so every rounding is fixed)."""
+    return float(u[0] * v[0] + u[1] * v[1] + u[2] * v[2])
 
 
 def _chord_t(p, x1, x2):

@@ -596,3 +596,48 @@ def test_spectral_first_order_convergence_in_l1():
         l1.append(np.mean(np.abs(u.reshape(-1)[mask] - p.exact(P)[mask])))
     r = [math.log2(l1[i] / l1[i + 1]) for i in range(2)]
     assert all(0.85 < x < 1.2 for x in r), (l1, r)
+
+
+def test_near_boundary_3d_exact_for_linear_fields():
+    """Sec. 6.7's 3D generalisation of App. A: every step (barycentric on the
+    triangle of the three nearest points, trilinear, the line A-p-B) is
+    linear, so a linear field with U_b = u on Gamma is reproduced; offsetting
+    the grid field changes exactly the inside nodes nearer than m1 h."""
+    g = geometry.sphere(32, 0.3, kappa=1e-2)
+    P = configs.grid_nodes(g)
+    lin = lambda Z: 0.3 + 1.7 * Z[:, 0] - 0.9 * Z[:, 1] + 0.4 * Z[:, 2]
+    u = lin(P).reshape(32, 32, 32)
+    rho = np.linalg.norm(P - np.array(g.center), axis=1)
+    inside = (rho < 0.3).astype(np.uint8).reshape(32, 32, 32)
+    band = np.nonzero(np.abs(rho - 0.3) < 5 * g.h)[0]
+    out = O.near_boundary_values_3d(g, u, lin(g.X), inside, 3, 5.0, nodes=band)
+    assert np.max(np.abs(out - u)) < 1e-13
+    off = O.near_boundary_values_3d(g, u + 1.0, lin(g.X), inside, 3, 5.0, nodes=band)
+    d2 = ((P[band, None, :] - g.X[None, :, :]) ** 2).sum(-1).min(axis=1)
+    near = np.zeros(32 ** 3, bool)
+    near[band] = (np.sqrt(d2) < 3 * g.h) & (inside.reshape(-1)[band] == 1)
+    changed = off.reshape(-1) != (u + 1.0).reshape(-1)
+    assert np.array_equal(changed, near)
+
+
+def test_near_boundary_3d_restores_pointwise_convergence():
+    """Laplace inside a sphere with U_b = x^2 - y^2: the max error over Omega
+    does not converge without the near-boundary step and does with it."""
+    raw, cor = [], []
+    for n in (32, 64):
+        g = geometry.sphere(n, 0.3, kappa=np.inf)
+        Xc = g.X - np.array(g.center)
+        ub = Xc[:, 0] ** 2 - Xc[:, 1] ** 2
+        res = O.solve(g, configs.DIRICHLET, ub, tol=1e-10)
+        u = res.op.evaluate(res.x).reshape(n, n, n)
+        Pc = configs.grid_nodes(g) - np.array(g.center)
+        ex = (Pc[:, 0] ** 2 - Pc[:, 1] ** 2).reshape(n, n, n)
+        rho = np.linalg.norm(Pc, axis=1)
+        ins = (rho < 0.3).astype(np.uint8).reshape(n, n, n)
+        band = np.nonzero((np.abs(rho - 0.3) < 7 * g.h) & (rho < 0.3))[0]
+        c = O.near_boundary_values_3d(g, u, ub, ins, 4, 6.0, nodes=band)
+        m = ins == 1
+        raw.append(np.max(np.abs(u - ex)[m]))
+        cor.append(np.max(np.abs(c - ex)[m]))
+    assert min(raw) > 0.05, raw
+    assert cor[0] < 0.015 and cor[1] < cor[0] / 2, cor
