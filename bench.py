@@ -269,6 +269,25 @@ def run_method_rows(pkg, peaks, reps=10):
                                "note": "m1 = 6, m2 = 8; the three nearest boundary points "
                                        "of each node from a cell list (3 x 3 cells of 8 h)"}
     G.close()
+    # the same two steps on the C3 sphere (N = 256^3, M = 38039)
+    c3 = configs.c3()
+    G3n = pkg.Geometry.from_workload(c3.geom)
+    n3 = c3.geom.n ** 3
+    chi3 = torch.empty(n3, dtype=torch.uint8, device=dev)
+    ind3_ms = _event_ms(lambda: G3n.indicator(None, chi3), 3, flush)
+    P3 = configs.grid_nodes(c3.geom)
+    u3in = torch.tensor(np.sin(3 * P3[:, 0]) * np.cos(2 * P3[:, 1]) * np.cos(P3[:, 2]),
+                        dtype=torch.float64, device=dev)
+    ub3n = torch.tensor(c3.bdata, dtype=torch.float64, device=dev)
+    u3out = torch.empty_like(u3in)
+    near3_ms = _event_ms(lambda: G3n.near_boundary(u3in, ub3n, chi3, 6, 8.0, u3out), 3, flush)
+    fixed3 = int((u3out != u3in).sum().item())
+    out["indicator_c3"] = {"us": ind3_ms * 1e3, "inside_nodes": int(chi3.sum().item())}
+    out["near_boundary_c3"] = {"us": near3_ms * 1e3, "replaced_nodes": fixed3,
+                               "ns_per_replaced_node": near3_ms * 1e6 / max(fixed3, 1),
+                               "note": "3D generalisation (Sec. 6.7), m1 = 6, m2 = 8"}
+    G3n.close()
+    del u3in, u3out, chi3
     gp = dataclasses.replace(g, kappa=float("inf"))
     Gp = pkg.Geometry.from_workload(gp, bc=configs.DIRICHLET, precision=ibdl.FP32_REFINED)
     q = torch.zeros(g.m, dtype=torch.float64, device=dev)

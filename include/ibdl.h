@@ -369,22 +369,27 @@ ibdl_status ibdl_interp(ibdl_geometry g, const double* u, double* y_out,
 ibdl_status ibdl_indicator(ibdl_geometry g, double* chi_h_out, uint8_t* chi_out,
                            void* stream);
 
-/* Near-boundary values (Sec. 5.5, App. A), 2D, float64.  u_out = u_in,
- * except at the nodes x_p with inside = 1 whose nearest boundary point is
- * closer than m1 h.  Those take the linear interpolation between
- *   x_A: the orthogonal foot of x_p on the chord of its two nearest
+/* Near-boundary values (Sec. 5.5, App. A; in 3D the generalisation of
+ * Sec. 6.7), float64.  u_out = u_in, except at the nodes x_p with inside = 1
+ * whose nearest boundary point is closer than m1 h.  Those take the linear
+ * interpolation between
+ *   x_A: 2D: the orthogonal foot of x_p on the chord of its two nearest
  *        boundary points (the two of the three nearest that lie farthest
  *        apart when the foot falls outside the chord, clamped to it), with
  *        the value interpolated from ub at those two points;
- *   x_B = x_A + m2 h (x_p - x_A) / |x_p - x_A|, with the bilinear
- *        interpolation of u_in in its grid cell.
+ *        3D: the orthogonal foot of x_p on the plane of its three nearest
+ *        boundary points, barycentric coordinates clamped to >= 0 and
+ *        renormalised (the first point for a degenerate triangle), with the
+ *        barycentric interpolation of ub;
+ *   x_B = x_A + m2 h (x_p - x_A) / |x_p - x_A|, with the bilinear (2D) or
+ *        trilinear (3D) interpolation of u_in in its grid cell.
  * Ties in distance go to the lower point index.  ub: the boundary values
- * (U_b for Dirichlet, the solved U for Neumann), length m.  inside: n^2
+ * (U_b for Dirichlet, the solved U for Neumann), length m.  inside: n^d
  * bytes, 1 = node of Omega (e.g. ibdl_indicator's chi, or 1 - chi for an
- * exterior domain).  u_in, u_out: n^2 doubles, must not overlap.  All
- * host or device.  m1 in 1..n/2 (the paper uses 6), m2 > 0 (the paper uses
- * m1 + 2).  Errors: IBDL_ERR_UNSUPPORTED (3D), IBDL_ERR_INVALID_ARG (m < 3,
- * m1 or m2 out of range, NULL or overlapping arrays), IBDL_ERR_CUDA. */
+ * exterior domain).  u_in, u_out: n^d doubles (x fastest), must not
+ * overlap.  All host or device.  m1 in 1..n/2 (the paper uses 6), m2 > 0
+ * (the paper uses m1 + 2).  Errors: IBDL_ERR_INVALID_ARG (m < 3, m1 or m2
+ * out of range, NULL or overlapping arrays), IBDL_ERR_CUDA. */
 ibdl_status ibdl_near_boundary(ibdl_geometry g, const double* u_in, const double* ub,
                                const uint8_t* inside, int32_t m1, double m2, double* u_out,
                                void* stream);

@@ -1469,7 +1469,6 @@ ibdl_status ibdl_near_boundary(ibdl_geometry g, const double* u_in, const double
   g_err.clear();
   IBDL_TRY(check_handle(g));
   if (!u_in || !ub || !inside || !u_out) return fail(IBDL_ERR_INVALID_ARG, "NULL argument");
-  if (g->grid.dim != 2) return fail(IBDL_ERR_UNSUPPORTED, "near-boundary values are 2D");
   if (g->m < 3) return fail(IBDL_ERR_INVALID_ARG, "at least three boundary points are needed");
   if (m1 < 1 || m1 > g->grid.n / 2) return fail(IBDL_ERR_INVALID_ARG, "m1 in 1 .. n/2");
   if (!(m2 > 0) || !isfinite(m2)) return fail(IBDL_ERR_INVALID_ARG, "m2 must be > 0");
@@ -1485,7 +1484,7 @@ ibdl_status ibdl_near_boundary(ibdl_geometry g, const double* u_in, const double
   double* uoutd = udev ? u_out : g->ws64.grid;
   const bool idev = is_device_ptr(inside);
   // scratch: the kernels' buffers, then a copy of a host mask
-  const size_t kb = (near_scratch_bytes(g->grid.n, g->m, m1) + 15) / 16 * 16;
+  const size_t kb = (near_scratch_bytes(g->grid.dim, g->grid.n, g->m, m1) + 15) / 16 * 16;
   const size_t bytes = kb + (idev ? 0 : (size_t)nn);
   cudaMemPool_t pool;
   IBDL_CU(workspace_pool(&pool));

@@ -237,9 +237,10 @@ cudaError_t launch_fill(int64_t n, double* x, double v, cudaStream_t st);
 cudaError_t launch_indicator(int64_t n, const double* u, double* chi_h, unsigned char* chi,
                              cudaStream_t st);
 
-// Near-boundary values, 2D (k_near.cu); scratch: near_scratch_bytes, 16-byte aligned.
-int64_t near_list_capacity(int n, int m, int m1);
-size_t near_scratch_bytes(int n, int m, int m1);
+// Near-boundary values, 2D and 3D (k_near.cu); scratch: near_scratch_bytes,
+// 16-byte aligned.
+int64_t near_list_capacity(int dim, int n, int m, int m1);
+size_t near_scratch_bytes(int dim, int n, int m, int m1);
 cudaError_t launch_near_boundary(const GridDesc& g, const PointData& p, const double* ub,
                                  const double* uin, const unsigned char* inside, int m1,
                                  double m2, double* uout, void* scratch, cudaStream_t st);

@@ -1,22 +1,24 @@
-// Near-boundary values (Sec. 5.5, App. A), 2D, float64.
+// Near-boundary values (Sec. 5.5, App. A in 2D; its 3D generalisation of
+// Sec. 6.7), float64.
 //
 // Grid nodes of Omega (inside = 1) whose nearest boundary point is closer
-// than m1 h get a value interpolated along the line from the chord point
-// x_A (on the segment of the two nearest boundary points, carrying the
-// boundary values) to x_B, m2 h further into Omega (bilinear in the grid
-// field):
-//   1. mark: each boundary point flags the nodes of the (2 m1 + 2)^2 box
+// than m1 h get a value interpolated along the line from a point x_A on the
+// discretised boundary (carrying the boundary values) to x_B, m2 h further
+// into Omega (bilinear / trilinear in the grid field).  2D: x_A on the chord
+// of the two nearest boundary points.  3D: x_A the foot of x_p on the plane
+// of the three nearest, barycentric coordinates clamped to the triangle.
+//   1. mark: each boundary point flags the nodes of the (2 m1 + 2)^d box
 //      around it (a superset of the nodes within m1 h);
 //   2. compact: flagged nodes with inside = 1 are appended to a list;
-//   3. cells: the points are counting-sorted into square cells of side
+//   3. cells: the points are counting-sorted into cubic cells of side
 //      s = max(m1 + 2, 8) h;
 //   4. fix: one thread per listed node finds the three nearest points (ordered
-//      by squared distance, then index) among the 3 x 3 cells around it.
+//      by squared distance, then index) among the 3^d cells around it.
 //      Every point outside those cells is at least s away (0.999 s, a margin
 //      for the rounding of the cell assignment), and s > m1 h: a node whose
 //      nearest found point is not within m1 h is not near, and the three
 //      found are the three nearest overall whenever the third is within
-//      0.999 s; otherwise the warp scans all points.  Then the steps of
+//      0.999 s; otherwise the thread scans all points.  Then the steps of
 //      App. A, and u_out.
 // u_out starts as a copy of u_in, and the fix reads only u_in, so the result
 // does not depend on the order in which nodes are corrected.
@@ -35,25 +37,31 @@ namespace {
 
 constexpr int kT = 256;
 
-__global__ void __launch_bounds__(kT) k_near_mark(int m, const double* __restrict__ X,
-                                                  const double* __restrict__ Y, double ox,
-                                                  double oy, double h, int n, int m1,
+struct Pts {
+  const double* X[3];
+  double o[3];
+};
+
+template <int D>
+__global__ void __launch_bounds__(kT) k_near_mark(int m, Pts P, double h, int n, int m1,
                                                   unsigned char* __restrict__ flag) {
-  __shared__ int cell[2];
+  __shared__ int cell[3];
   const int w = 2 * m1 + 2;
+  const int wd = D == 3 ? w * w * w : w * w;
   for (int i = blockIdx.x; i < m; i += gridDim.x) {
     if (threadIdx.x == 0) {  // one thread does the (slow) float64 divisions
-      double rx = (X[i] - ox) / h, ry = (Y[i] - oy) / h;
-      rx = fmin(fmax(rx, -1073741824.0), 1073741824.0);
-      ry = fmin(fmax(ry, -1073741824.0), 1073741824.0);
-      cell[0] = (int)floor(rx);
-      cell[1] = (int)floor(ry);
+      for (int c = 0; c < D; ++c) {
+        double r = (P.X[c][i] - P.o[c]) / h;
+        r = fmin(fmax(r, -1073741824.0), 1073741824.0);
+        cell[c] = (int)floor(r);
+      }
     }
     __syncthreads();
-    const int cx = cell[0], cy = cell[1];
-    for (int e = threadIdx.x; e < w * w; e += kT) {
-      const int ix = cx - m1 + e % w, iy = cy - m1 + e / w;
-      if (ix >= 0 && ix < n && iy >= 0 && iy < n) flag[(size_t)iy * n + ix] = 1;
+    for (int e = threadIdx.x; e < wd; e += kT) {
+      const int ix = cell[0] - m1 + e % w, iy = cell[1] - m1 + (e / w) % w;
+      const int iz = D == 3 ? cell[2] - m1 + e / (w * w) : 0;
+      if (ix >= 0 && ix < n && iy >= 0 && iy < n && iz >= 0 && iz < n)
+        flag[((size_t)iz * n + iy) * n + ix] = 1;
     }
     __syncthreads();
   }
@@ -108,15 +116,16 @@ struct Top3 {
   }
 };
 
-__global__ void __launch_bounds__(kT) k_cell_count(int m, const double* __restrict__ X,
-                                                   const double* __restrict__ Y, double ox,
-                                                   double oy, double s, int nc,
+template <int D>
+__global__ void __launch_bounds__(kT) k_cell_count(int m, Pts P, double s, int nc,
                                                    int* __restrict__ cell_of,
                                                    int* __restrict__ counts) {
   for (int i = blockIdx.x * kT + threadIdx.x; i < m; i += gridDim.x * kT) {
-    const double rx = fmin(fmax(floor((X[i] - ox) / s), 0.0), (double)(nc - 1));
-    const double ry = fmin(fmax(floor((Y[i] - oy) / s), 0.0), (double)(nc - 1));
-    const int c = (int)ry * nc + (int)rx;
+    int c = 0;
+    for (int a = D - 1; a >= 0; --a) {
+      const double r = fmin(fmax(floor((P.X[a][i] - P.o[a]) / s), 0.0), (double)(nc - 1));
+      c = c * nc + (int)r;
+    }
     cell_of[i] = c;
     atomicAdd(counts + c, 1);
   }
@@ -175,49 +184,120 @@ __global__ void __launch_bounds__(kT) k_cell_fill(int m, const int* __restrict__
 // lane repeats another's arithmetic).
 constexpr int kFixT = 64;  // small blocks spread the few thousand nodes over all SMs
 
+template <int D>
+__device__ __forceinline__ double sqdist(const double* p, const Pts& P, int i) {
+  const double dx = p[0] - __ldg(P.X[0] + i), dy = p[1] - __ldg(P.X[1] + i);
+  if (D == 2) return dx * dx + dy * dy;
+  const double dz = p[2] - __ldg(P.X[2] + i);
+  return dx * dx + dy * dy + dz * dz;
+}
+
+__device__ __forceinline__ double norm3(double a, double b, double c) {
+  return sqrt(a * a + b * b + c * c);
+}
+
+template <int D>
 __global__ void __launch_bounds__(kFixT) k_near_fix(const int* __restrict__ list, const int* count,
-                                                 int cap, int n, double ox, double oy, double h,
-                                                 int m, const double* __restrict__ X,
-                                                 const double* __restrict__ Y,
-                                                 const double* __restrict__ ub,
-                                                 const double* __restrict__ uin, double thresh,
-                                                 double m2h, int cw, int nc,
-                                                 const int* __restrict__ cstart,
-                                                 const int* __restrict__ sorted,
-                                                 double guard2, double* __restrict__ uout) {
+                                                    int cap, int n, Pts P, double h, int m,
+                                                    const double* __restrict__ ub,
+                                                    const double* __restrict__ uin,
+                                                    double thresh, double m2h, int cw, int nc,
+                                                    const int* __restrict__ cstart,
+                                                    const int* __restrict__ sorted,
+                                                    double guard2, double* __restrict__ uout) {
   const int cnt = min(*count, cap);
+  const double* X = P.X[0];
+  const double* Y = P.X[1];
+  const double* Z = P.X[2];
+  const double ox = P.o[0], oy = P.o[1], oz = P.o[2];
   for (int k = blockIdx.x * kFixT + threadIdx.x; k < cnt; k += gridDim.x * kFixT) {
     const int j = list[k];
-    const int ix = j % n, iy = j / n;
-    const double px = ox + (double)ix * h, py = oy + (double)iy * h;
+    const int ix = j % n, iy = (j / n) % n, iz = D == 3 ? j / (n * n) : 0;
+    double p[3];
+    p[0] = ox + (double)ix * h;
+    p[1] = oy + (double)iy * h;
+    p[2] = D == 3 ? oz + (double)iz * h : 0.0;
     Top3 t3;
     const int cx = min(ix / cw, nc - 1), cy = min(iy / cw, nc - 1);
-    for (int by = max(cy - 1, 0); by <= min(cy + 1, nc - 1); ++by)
-      for (int bx = max(cx - 1, 0); bx <= min(cx + 1, nc - 1); ++bx) {
-        const int c = by * nc + bx;
-        for (int t = cstart[c]; t < cstart[c + 1]; ++t) {
-          const int i = sorted[t];
-          const double dx = px - __ldg(X + i), dy = py - __ldg(Y + i);
-          t3.add(dx * dx + dy * dy, i);
+    const int cz = D == 3 ? min(iz / cw, nc - 1) : 0;
+    for (int bz = (D == 3 ? max(cz - 1, 0) : 0); bz <= (D == 3 ? min(cz + 1, nc - 1) : 0); ++bz)
+      for (int by = max(cy - 1, 0); by <= min(cy + 1, nc - 1); ++by)
+        for (int bx = max(cx - 1, 0); bx <= min(cx + 1, nc - 1); ++bx) {
+          const int c = (bz * nc + by) * nc + bx;
+          for (int t = cstart[c]; t < cstart[c + 1]; ++t) {
+            const int i = sorted[t];
+            t3.add(sqdist<D>(p, P, i), i);
+          }
         }
-      }
     // every point closer than the guard (> m1 h) was searched: a node whose
     // nearest found point is not within m1 h has none
     if (!(t3.d0 < thresh)) continue;
     if (!(t3.d2 < guard2)) {
       // the third nearest may lie outside the searched cells: scan all points
       t3 = Top3();
-      for (int i = 0; i < m; ++i) {
-        const double dx = px - __ldg(X + i), dy = py - __ldg(Y + i);
-        t3.add(dx * dx + dy * dy, i);
-      }
+      for (int i = 0; i < m; ++i) t3.add(sqdist<D>(p, P, i), i);
     }
-    const double dd[3] = {t3.d0, t3.d1, t3.d2};
-    const int ii[3] = {t3.i0, t3.i1, t3.i2};
-    const double d0 = dd[0];
-    const int i0 = ii[0], i1 = ii[1], i2 = ii[2];
+    const int i0 = t3.i0, i1 = t3.i1, i2 = t3.i2;
     // i1, i2 stay -1 only if squared distances overflow (points near 1e154)
-    if (!(d0 < thresh) || i1 < 0 || i2 < 0) continue;
+    if (!(t3.d0 < thresh) || i1 < 0 || i2 < 0) continue;
+    const double px = p[0], py = p[1], pz = p[2];
+    if (D == 3) {
+      // x_A: the foot on the plane of the three nearest points, barycentric
+      // coordinates clamped to the triangle and renormalised
+      double xa = X[i0], ya = Y[i0], za = Z[i0], uA = ub[i0];
+      const double e1x = X[i1] - X[i0], e1y = Y[i1] - Y[i0], e1z = Z[i1] - Z[i0];
+      const double e2x = X[i2] - X[i0], e2y = Y[i2] - Y[i0], e2z = Z[i2] - Z[i0];
+      const double wx = px - X[i0], wy = py - Y[i0], wz = pz - Z[i0];
+      const double d11 = e1x * e1x + e1y * e1y + e1z * e1z;
+      const double d12 = e1x * e2x + e1y * e2y + e1z * e2z;
+      const double d22 = e2x * e2x + e2y * e2y + e2z * e2z;
+      const double w1 = wx * e1x + wy * e1y + wz * e1z;
+      const double w2 = wx * e2x + wy * e2y + wz * e2z;
+      const double det = d11 * d22 - d12 * d12;
+      if (det > 0.0) {
+        const double l2 = (d22 * w1 - d12 * w2) / det;
+        const double l3 = (d11 * w2 - d12 * w1) / det;
+        double a0 = fmax(1.0 - l2 - l3, 0.0), a1 = fmax(l2, 0.0), a2 = fmax(l3, 0.0);
+        const double sm = a0 + a1 + a2;
+        a0 = a0 / sm;
+        a1 = a1 / sm;
+        a2 = a2 / sm;
+        xa = a0 * X[i0] + a1 * X[i1] + a2 * X[i2];
+        ya = a0 * Y[i0] + a1 * Y[i1] + a2 * Y[i2];
+        za = a0 * Z[i0] + a1 * Z[i1] + a2 * Z[i2];
+        uA = a0 * ub[i0] + a1 * ub[i1] + a2 * ub[i2];
+      }
+      const double dA = norm3(px - xa, py - ya, pz - za);
+      if (dA == 0.0) {
+        uout[j] = uA;
+        continue;
+      }
+      const double xb = xa + (px - xa) / dA * m2h, yb = ya + (py - ya) / dA * m2h;
+      const double zb = za + (pz - za) / dA * m2h;
+      const double rr[3] = {(xb - ox) / h, (yb - oy) / h, (zb - oz) / h};
+      int q0[3];
+      double ff[3];
+      for (int c = 0; c < 3; ++c) {
+        const double fj = floor(rr[c]);
+        ff[c] = rr[c] - fj;
+        constexpr double kBig = 4503599627370496.0;  // 2^52: keeps the casts defined
+        const long long jj = (long long)fmin(fmax(fj, -kBig), kBig);
+        q0[c] = (int)(((jj % n) + n) % n);
+      }
+      double uB = 0.0;
+      for (int dz = 0; dz < 2; ++dz)
+        for (int dy = 0; dy < 2; ++dy)
+          for (int dx = 0; dx < 2; ++dx) {
+            const double wgt = ((dx ? ff[0] : 1.0 - ff[0]) * (dy ? ff[1] : 1.0 - ff[1])) *
+                               (dz ? ff[2] : 1.0 - ff[2]);
+            const size_t at = ((size_t)((q0[2] + dz) % n) * n + (q0[1] + dy) % n) * n +
+                              (q0[0] + dx) % n;
+            uB = uB + wgt * uin[at];
+          }
+      const double LAB = norm3(xb - xa, yb - ya, zb - za);
+      uout[j] = uA * norm3(xb - px, yb - py, zb - pz) / LAB + uB * dA / LAB;
+      continue;
+    }
     int a = i0, b = i1;
     double t = chord_t(px, py, X[a], Y[a], X[b], Y[b]);
     if (!(t >= 0.0 && t <= 1.0)) {
@@ -267,9 +347,10 @@ int blocks_for(int64_t n) {
 
 }  // namespace
 
-int64_t near_list_capacity(int n, int m, int m1) {
+int64_t near_list_capacity(int dim, int n, int m, int m1) {
   const int64_t w = 2 * (int64_t)m1 + 2;
-  const int64_t a = (int64_t)n * n, b = (int64_t)m * w * w;
+  const int64_t a = dim == 3 ? (int64_t)n * n * n : (int64_t)n * n;
+  const int64_t b = (int64_t)m * w * w * (dim == 3 ? w : 1);
   return a < b ? a : b;
 }
 
@@ -280,22 +361,26 @@ static int near_cells(int n, int m1) {
   const int cw = near_cell_width(m1);
   return (n + cw - 1) / cw;
 }
-
-size_t near_scratch_bytes(int n, int m, int m1) {
+static int64_t near_cell_count(int dim, int n, int m1) {
   const int64_t nc = near_cells(n, m1);
-  const size_t flag = ((size_t)n * n + 15) / 16 * 16;
-  return flag + sizeof(int) * (4 + (size_t)near_list_capacity(n, m, m1) + 3 * (nc * nc + 1) +
-                               2 * (size_t)m);
+  return dim == 3 ? nc * nc * nc : nc * nc;
+}
+
+size_t near_scratch_bytes(int dim, int n, int m, int m1) {
+  const int64_t nn = dim == 3 ? (int64_t)n * n * n : (int64_t)n * n;
+  const size_t flag = ((size_t)nn + 15) / 16 * 16;
+  return flag + sizeof(int) * (4 + (size_t)near_list_capacity(dim, n, m, m1) +
+                               3 * ((size_t)near_cell_count(dim, n, m1) + 1) + 2 * (size_t)m);
 }
 
 cudaError_t launch_near_boundary(const GridDesc& g, const PointData& p, const double* ub,
                                  const double* uin, const unsigned char* inside, int m1,
                                  double m2, double* uout, void* scratch, cudaStream_t st) {
-  const int n = g.n;
-  const int64_t nn = (int64_t)n * n;
-  const int cap = (int)near_list_capacity(n, p.m, m1);
+  const int n = g.n, D = g.dim;
+  const int64_t nn = D == 3 ? (int64_t)n * n * n : (int64_t)n * n;
+  const int cap = (int)near_list_capacity(D, n, p.m, m1);
   const int nc = near_cells(n, m1);
-  const int ncell = nc * nc;
+  const int ncell = (int)near_cell_count(D, n, m1);
   unsigned char* flag = static_cast<unsigned char*>(scratch);
   int* count = reinterpret_cast<int*>(flag + ((size_t)nn + 15) / 16 * 16);
   int* list = count + 4;
@@ -304,6 +389,11 @@ cudaError_t launch_near_boundary(const GridDesc& g, const PointData& p, const do
   int* cursor = cstart + ncell + 1;
   int* cell_of = cursor + ncell + 1;
   int* sorted = cell_of + p.m;
+  Pts P;
+  for (int c = 0; c < 3; ++c) {
+    P.X[c] = p.X[c];
+    P.o[c] = g.origin[c];
+  }
   cudaError_t e;
   if ((e = cudaMemsetAsync(flag, 0, (size_t)nn, st))) return e;
   if ((e = cudaMemsetAsync(count, 0, sizeof(int), st))) return e;
@@ -313,8 +403,10 @@ cudaError_t launch_near_boundary(const GridDesc& g, const PointData& p, const do
   const int cw = near_cell_width(m1);
   const double s = (double)cw * g.h;
   prof_begin(st);
-  k_cell_count<<<blocks_for(p.m), kT, 0, st>>>(p.m, p.X[0], p.X[1], g.origin[0], g.origin[1], s,
-                                               nc, cell_of, counts);
+  if (D == 3)
+    k_cell_count<3><<<blocks_for(p.m), kT, 0, st>>>(p.m, P, s, nc, cell_of, counts);
+  else
+    k_cell_count<2><<<blocks_for(p.m), kT, 0, st>>>(p.m, P, s, nc, cell_of, counts);
   count_launch("near_cells", st);
   if ((e = check_launch())) return e;
   prof_begin(st);
@@ -325,9 +417,12 @@ cudaError_t launch_near_boundary(const GridDesc& g, const PointData& p, const do
   k_cell_fill<<<blocks_for(p.m), kT, 0, st>>>(p.m, cell_of, cursor, sorted);
   count_launch("near_cell_fill", st);
   if ((e = check_launch())) return e;
+  const int mb = p.m < 8 * 152 ? p.m : 8 * 152;
   prof_begin(st);
-  k_near_mark<<<p.m < 8 * 152 ? p.m : 8 * 152, kT, 0, st>>>(p.m, p.X[0], p.X[1], g.origin[0],
-                                                           g.origin[1], g.h, n, m1, flag);
+  if (D == 3)
+    k_near_mark<3><<<mb, kT, 0, st>>>(p.m, P, g.h, n, m1, flag);
+  else
+    k_near_mark<2><<<mb, kT, 0, st>>>(p.m, P, g.h, n, m1, flag);
   count_launch("near_mark", st);
   if ((e = check_launch())) return e;
   prof_begin(st);
@@ -336,11 +431,15 @@ cudaError_t launch_near_boundary(const GridDesc& g, const PointData& p, const do
   if ((e = check_launch())) return e;
   const double mh = (double)m1 * g.h;
   const double guard = 0.999 * s;
-  prof_begin(st);
   const int64_t fb = (cap + kFixT - 1) / kFixT;
-  k_near_fix<<<(int)(fb < 32 * 152 ? fb : 32 * 152), kFixT, 0, st>>>(
-      list, count, cap, n, g.origin[0], g.origin[1], g.h, p.m, p.X[0], p.X[1], ub, uin, mh * mh,
-      m2 * g.h, cw, nc, cstart, sorted, guard * guard, uout);
+  const int nfb = (int)(fb < 32 * 152 ? fb : 32 * 152);
+  prof_begin(st);
+  if (D == 3)
+    k_near_fix<3><<<nfb, kFixT, 0, st>>>(list, count, cap, n, P, g.h, p.m, ub, uin, mh * mh,
+                                         m2 * g.h, cw, nc, cstart, sorted, guard * guard, uout);
+  else
+    k_near_fix<2><<<nfb, kFixT, 0, st>>>(list, count, cap, n, P, g.h, p.m, ub, uin, mh * mh,
+                                         m2 * g.h, cw, nc, cstart, sorted, guard * guard, uout);
   count_launch("near_fix", st);
   return check_launch();
 }

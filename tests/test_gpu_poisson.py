@@ -296,13 +296,40 @@ def test_near_boundary_edge_cases():
             G.near_boundary(uin, gpu(ub), none, m1, m2, out)
         assert e.value.status == 1
     G.close()
-    s3 = geometry.sphere(32, 0.3, kappa=1e-2)
-    G3 = pkg.Geometry.from_workload(s3)
-    n3 = s3.n ** 3
-    with pytest.raises(ibdl.IbdlError) as e:
-        G3.near_boundary(torch.zeros(n3, dtype=torch.float64, device=DEV),
-                         torch.zeros(s3.m, dtype=torch.float64, device=DEV),
-                         torch.zeros(n3, dtype=torch.uint8, device=DEV), 2, 4.0,
-                         torch.zeros(n3, dtype=torch.float64, device=DEV))
-    assert e.value.status == 8
-    G3.close()
+
+
+def _sphere_band(g, r, m1):
+    """Nodes whose distance to the sphere is below (m1 + 1) h: a superset of
+    the nodes within m1 h of a boundary point."""
+    rho = np.linalg.norm(configs.grid_nodes(g) - np.array(g.center), axis=1)
+    return np.nonzero(np.abs(rho - r) < (m1 + 1) * g.h)[0], rho
+
+
+@pytest.mark.parametrize("n,r,m1,m2,center", [(32, 0.3, 3, 5.0, (0.5, 0.5, 0.5)),
+                                              (64, 0.27, 6, 8.0, (0.47, 0.52, 0.5)),
+                                              (64, 0.3, 1, 3.0, (0.5, 0.5, 0.5))])
+def test_near_boundary_3d_parity(n, r, m1, m2, center):
+    """Sec. 6.7's 3D near-boundary step against the oracle, every node (the
+    oracle visits a band that holds every near node; the others must be
+    untouched on both sides)."""
+    g = geometry.sphere(n, r, center=center, kappa=1e-2)
+    band, rho = _sphere_band(g, r, m1)
+    inside = (rho < r).astype(np.uint8)
+    P = configs.grid_nodes(g)
+    rr = np.random.default_rng(3)
+    u = (np.sin(3 * P[:, 0] + 1) * np.cos(2 * P[:, 1]) * np.cos(P[:, 2])
+         + 0.01 * rr.standard_normal(len(P)))
+    ub = rr.standard_normal(g.m)
+    ref = O.near_boundary_values_3d(g, u.reshape(n, n, n), ub, inside.reshape(n, n, n), m1, m2,
+                                    nodes=band).reshape(-1)
+    G = pkg.Geometry.from_workload(g)
+    out = torch.empty(n ** 3, dtype=torch.float64, device=DEV)
+    G.near_boundary(gpu(u), gpu(ub), gpu(inside, torch.uint8), m1, m2, out)
+    o = host(out)
+    assert np.max(np.abs(o - ref)) <= 1e-12 * np.max(np.abs(u))
+    assert np.array_equal(o != u, ref != u)
+    assert (ref != u).sum() > 0
+    ho = np.empty(n ** 3)
+    G.near_boundary(u, ub, inside, m1, m2, ho)
+    assert np.array_equal(ho, o)
+    G.close()
