@@ -168,6 +168,7 @@ struct ibdl_geometry_s {
   int nsys = 0;
   double eta = 0;
   double* cpart = nullptr;  // kRedBlocks + 1 reduction partials
+  double xmax = 0;          // max |coordinate| over the points
   Bins bins;
   PointData pd;
   SpectralWs<double> ws64;
@@ -969,8 +970,10 @@ ibdl_status ibdl_create_geometry(const ibdl_geometry_desc* d, void* stream, ibdl
                           cudaMemcpyDeviceToHost, st);
       if (!e) e = cudaStreamSynchronize(st);
       if (e) return cleanup(cuda_fail(e, "read points"));
-      for (int i = 0; i < m; ++i)
+      for (int i = 0; i < m; ++i) {
         if (!isfinite(hx[i])) return cleanup(fail(IBDL_ERR_INVALID_ARG, "non-finite point"));
+        g->xmax = fmax(g->xmax, fabs(hx[i]));
+      }
     }
     e = cudaMemcpyAsync(pts + (size_t)6 * m, hw.data(), sizeof(double) * m,
                         cudaMemcpyHostToDevice, st);
@@ -1496,7 +1499,11 @@ ibdl_status ibdl_near_boundary(ibdl_geometry g, const double* u_in, const double
     e = cudaMemcpyAsync(scratch + kb, inside, (size_t)nn, cudaMemcpyHostToDevice, st);
     insd = scratch + kb;
   }
-  if (!e) e = launch_near_boundary(g->grid, g->pd, ubd, uind, insd, m1, m2, uoutd, scratch, st);
+  double cmax = g->xmax;  // bounds every point and node coordinate
+  for (int c = 0; c < g->grid.dim; ++c)
+    cmax = fmax(cmax, fabs(g->grid.origin[c]) + g->grid.h * g->grid.n);
+  if (!e)
+    e = launch_near_boundary(g->grid, g->pd, ubd, uind, insd, m1, m2, cmax, uoutd, scratch, st);
   if (!e && !udev)
     e = cudaMemcpyAsync(u_out, uoutd, sizeof(double) * nn, cudaMemcpyDeviceToHost, st);
   cudaFreeAsync(scratch, st);

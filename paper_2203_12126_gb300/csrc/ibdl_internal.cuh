@@ -241,8 +241,11 @@ cudaError_t launch_indicator(int64_t n, const double* u, double* chi_h, unsigned
 // 16-byte aligned.
 int64_t near_list_capacity(int dim, int n, int m, int m1);
 size_t near_scratch_bytes(int dim, int n, int m, int m1);
+// cmax: a bound on |coordinate| of every point and grid node (the float32
+// distance filter's error bound scales with it)
 cudaError_t launch_near_boundary(const GridDesc& g, const PointData& p, const double* ub,
                                  const double* uin, const unsigned char* inside, int m1,
-                                 double m2, double* uout, void* scratch, cudaStream_t st);
+                                 double m2, double cmax, double* uout, void* scratch,
+                                 cudaStream_t st);
 
 }  // namespace ibdl

@@ -28,6 +28,7 @@
 // decisions (near or not, which points, which branch) are those of a plain
 // IEEE evaluation of the same expressions.
 #include <math.h>
+#include <stdint.h>
 
 #include "ibdl_internal.cuh"
 
@@ -172,16 +173,21 @@ __global__ void __launch_bounds__(1024) k_cell_scan(const int* __restrict__ coun
   if (tid == 0) start[ncell] = base;
 }
 
-__global__ void __launch_bounds__(kT) k_cell_fill(int m, const int* __restrict__ cell_of,
+// Points in cell order: the index, and float copies of the coordinates for
+// the distance filter of the fix.
+template <int D>
+__global__ void __launch_bounds__(kT) k_cell_fill(int m, Pts P, const int* __restrict__ cell_of,
                                                   int* __restrict__ cursor,
-                                                  int* __restrict__ sorted) {
-  for (int i = blockIdx.x * kT + threadIdx.x; i < m; i += gridDim.x * kT)
-    sorted[atomicAdd(cursor + cell_of[i], 1)] = i;
+                                                  int* __restrict__ sorted,
+                                                  float4* __restrict__ pts4) {
+  for (int i = blockIdx.x * kT + threadIdx.x; i < m; i += gridDim.x * kT) {
+    const int t = atomicAdd(cursor + cell_of[i], 1);
+    sorted[t] = i;
+    pts4[t] = make_float4((float)P.X[0][i], (float)P.X[1][i], D == 3 ? (float)P.X[2][i] : 0.0f,
+                          0.0f);
+  }
 }
 
-// One thread per listed node (the work per node is a few dozen points and
-// a few dozen float64 operations; GB300's float64 pipe is narrow, so no
-// lane repeats another's arithmetic).
 constexpr int kFixT = 64;  // small blocks spread the few thousand nodes over all SMs
 
 template <int D>
@@ -204,7 +210,9 @@ __global__ void __launch_bounds__(kFixT) k_near_fix(const int* __restrict__ list
                                                     double thresh, double m2h, int cw, int nc,
                                                     const int* __restrict__ cstart,
                                                     const int* __restrict__ sorted,
-                                                    double guard2, double* __restrict__ uout) {
+                                                    const float4* __restrict__ pts4,
+                                                    float ferr, double guard2,
+                                                    double* __restrict__ uout) {
   const int cnt = min(*count, cap);
   const double* X = P.X[0];
   const double* Y = P.X[1];
@@ -220,13 +228,23 @@ __global__ void __launch_bounds__(kFixT) k_near_fix(const int* __restrict__ list
     Top3 t3;
     const int cx = min(ix / cw, nc - 1), cy = min(iy / cw, nc - 1);
     const int cz = D == 3 ? min(iz / cw, nc - 1) : 0;
+    // float32 filter: |d2f - d2| <= ferr for every point of these cells, so
+    // a point with d2f > (third best, rounded up) + ferr cannot enter the
+    // three nearest; the others are ranked by their float64 distance
+    const float pxf = (float)p[0], pyf = (float)p[1], pzf = (float)p[2];
+    float third = INFINITY;
     for (int bz = (D == 3 ? max(cz - 1, 0) : 0); bz <= (D == 3 ? min(cz + 1, nc - 1) : 0); ++bz)
       for (int by = max(cy - 1, 0); by <= min(cy + 1, nc - 1); ++by)
         for (int bx = max(cx - 1, 0); bx <= min(cx + 1, nc - 1); ++bx) {
           const int c = (bz * nc + by) * nc + bx;
           for (int t = cstart[c]; t < cstart[c + 1]; ++t) {
+            const float4 q = __ldg(pts4 + t);
+            const float fx = pxf - q.x, fy = pyf - q.y, fz = pzf - q.z;
+            const float d2f = D == 3 ? fx * fx + fy * fy + fz * fz : fx * fx + fy * fy;
+            if (d2f > third + ferr) continue;
             const int i = sorted[t];
             t3.add(sqdist<D>(p, P, i), i);
+            third = __double2float_ru(t3.d2);
           }
         }
     // every point closer than the guard (> m1 h) was searched: a node whose
@@ -370,12 +388,14 @@ size_t near_scratch_bytes(int dim, int n, int m, int m1) {
   const int64_t nn = dim == 3 ? (int64_t)n * n * n : (int64_t)n * n;
   const size_t flag = ((size_t)nn + 15) / 16 * 16;
   return flag + sizeof(int) * (4 + (size_t)near_list_capacity(dim, n, m, m1) +
-                               3 * ((size_t)near_cell_count(dim, n, m1) + 1) + 2 * (size_t)m);
+                               3 * ((size_t)near_cell_count(dim, n, m1) + 1) + 2 * (size_t)m) +
+         16 + sizeof(float4) * (size_t)m;
 }
 
 cudaError_t launch_near_boundary(const GridDesc& g, const PointData& p, const double* ub,
                                  const double* uin, const unsigned char* inside, int m1,
-                                 double m2, double* uout, void* scratch, cudaStream_t st) {
+                                 double m2, double cmax, double* uout, void* scratch,
+                                 cudaStream_t st) {
   const int n = g.n, D = g.dim;
   const int64_t nn = D == 3 ? (int64_t)n * n * n : (int64_t)n * n;
   const int cap = (int)near_list_capacity(D, n, p.m, m1);
@@ -389,6 +409,8 @@ cudaError_t launch_near_boundary(const GridDesc& g, const PointData& p, const do
   int* cursor = cstart + ncell + 1;
   int* cell_of = cursor + ncell + 1;
   int* sorted = cell_of + p.m;
+  float4* pts4 = reinterpret_cast<float4*>(
+      (reinterpret_cast<uintptr_t>(sorted + p.m) + 15) / 16 * 16);
   Pts P;
   for (int c = 0; c < 3; ++c) {
     P.X[c] = p.X[c];
@@ -414,7 +436,10 @@ cudaError_t launch_near_boundary(const GridDesc& g, const PointData& p, const do
   count_launch("near_cell_scan", st);
   if ((e = check_launch())) return e;
   prof_begin(st);
-  k_cell_fill<<<blocks_for(p.m), kT, 0, st>>>(p.m, cell_of, cursor, sorted);
+  if (D == 3)
+    k_cell_fill<3><<<blocks_for(p.m), kT, 0, st>>>(p.m, P, cell_of, cursor, sorted, pts4);
+  else
+    k_cell_fill<2><<<blocks_for(p.m), kT, 0, st>>>(p.m, P, cell_of, cursor, sorted, pts4);
   count_launch("near_cell_fill", st);
   if ((e = check_launch())) return e;
   const int mb = p.m < 8 * 152 ? p.m : 8 * 152;
@@ -431,15 +456,26 @@ cudaError_t launch_near_boundary(const GridDesc& g, const PointData& p, const do
   if ((e = check_launch())) return e;
   const double mh = (double)m1 * g.h;
   const double guard = 0.999 * s;
+  // Error of d2 in float32 for a point of the 3^d cells (|dx_c| <= 2s):
+  // rounding the coordinates (|.| <= cmax) and the difference gives
+  // |dxf - dx| <= 4 u cmax =: e, so the squares sum to within e (2 sum|dx| + d e)
+  // of d2, and rounding the squares and sums adds 4 u d2; twice that.
+  const double u = 5.9604644775390625e-8;  // 2^-24
+  const double ec = 4.0 * u * cmax, rmax = 2.0 * s;
+  const double ferr_d = 2.0 * (ec * (2.0 * D * rmax + D * ec) + 4.0 * u * D * rmax * rmax);
+  float ferr = (float)ferr_d;  // rounded up
+  if ((double)ferr < ferr_d) ferr = nextafterf(ferr, INFINITY);
   const int64_t fb = (cap + kFixT - 1) / kFixT;
   const int nfb = (int)(fb < 32 * 152 ? fb : 32 * 152);
   prof_begin(st);
   if (D == 3)
     k_near_fix<3><<<nfb, kFixT, 0, st>>>(list, count, cap, n, P, g.h, p.m, ub, uin, mh * mh,
-                                         m2 * g.h, cw, nc, cstart, sorted, guard * guard, uout);
+                                         m2 * g.h, cw, nc, cstart, sorted, pts4, ferr,
+                                         guard * guard, uout);
   else
     k_near_fix<2><<<nfb, kFixT, 0, st>>>(list, count, cap, n, P, g.h, p.m, ub, uin, mh * mh,
-                                         m2 * g.h, cw, nc, cstart, sorted, guard * guard, uout);
+                                         m2 * g.h, cw, nc, cstart, sorted, pts4, ferr,
+                                         guard * guard, uout);
   count_launch("near_fix", st);
   return check_launch();
 }
