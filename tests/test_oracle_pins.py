@@ -641,3 +641,37 @@ def test_near_boundary_3d_restores_pointwise_convergence():
         cor.append(np.max(np.abs(c - ex)[m]))
     assert min(raw) > 0.05, raw
     assert cor[0] < 0.015 and cor[1] < cor[0] / 2, cor
+
+
+def test_forcing_converges_on_the_sec62_linear_problem():
+    """Sec. 6.2: Delta u - u = -(x + y) inside r = 0.25, u = x + y on Gamma,
+    with g extended smoothly outside (g_e = g's formula, as Sec. 2 allows):
+    the forced solve and field converge to u = x + y away from Gamma (a
+    dropped or mis-signed forcing term leaves an O(1) error)."""
+    errs = []
+    for n in (64, 128, 256):
+        g = geometry.circle(n, 0.25, spacing=0.75, center=(0.0, 0.0), origin=(-0.5, -0.5),
+                            kappa=1.0)
+        P = configs.grid_nodes(g)
+        gt = (-(P[:, 0] + P[:, 1])).reshape(n, n)
+        res = O.solve(g, configs.DIRICHLET, g.X[:, 0] + g.X[:, 1], tol=1e-10, g_grid=gt)
+        u = res.op.evaluate(res.x, g_grid=gt).reshape(-1)
+        m = np.linalg.norm(P, axis=1) < 0.25 - 6 * g.h
+        errs.append(np.mean(np.abs(u[m] - (P[m, 0] + P[m, 1]))))
+    assert errs[0] < 5e-3 and errs[1] < errs[0] / 1.4 and errs[2] < errs[1] / 1.4, errs
+
+
+def test_neumann_field_converges():
+    """The Neumann field u = kappa L'^{-1}(S~ U + S V_b) (eq. (ib neumann 1))
+    converges to e^{k d.x} away from Gamma at first order."""
+    errs = []
+    for n in (64, 128, 256):
+        g = geometry.circle(n, 0.25, spacing=0.75, center=(0.0, 0.0), origin=(-0.5, -0.5),
+                            kappa=1.0)
+        p = configs.exp_problem(g, configs.NEUMANN, (0.6, 0.8))
+        res = O.solve(g, p.bc, p.bdata, tol=1e-10)
+        u = res.op.evaluate(res.x, vb=p.bdata).reshape(-1)
+        P = configs.grid_nodes(g)
+        m = np.linalg.norm(P, axis=1) < 0.25 - 6 * g.h
+        errs.append(np.mean(np.abs(u[m] - p.exact(P)[m])))
+    assert errs[0] < 0.08 and errs[1] < errs[0] / 1.7 and errs[2] < errs[1] / 1.7, errs
