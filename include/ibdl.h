@@ -189,13 +189,18 @@ void ibdl_destroy_geometry(ibdl_geometry g);
 
 /* y = A q, one application of the boundary operator (A_D or A_N by the
  * geometry's bc), the GMRES matrix-vector product of Sec. 5.3.  q and y have
- * length m.  Computed in float64 for IBDL_FP64 geometries and in float32
+ * length m (m + 1 for a completed geometry: the operator of App. C on
+ * (Q, u_bar)).  Computed in float64 for IBDL_FP64 geometries and in float32
  * (spread, FFT solve, interpolation; the +-q/2 jump in float64) for
  * IBDL_FP32_REFINED geometries.  q and y may alias. */
 ibdl_status ibdl_apply(ibdl_geometry g, const double* q, double* y, void* stream);
 
 /* Same as ibdl_apply with the precision chosen per call:
- * ibdl_precision value 0 = float64 operator, 1 = float32 operator. */
+ * ibdl_precision value 0 = float64 operator, 1 = float32 operator,
+ * 2 = IBDL_FP64_DF (float64 spread and interpolation, double-float
+ * transforms; finite-difference, non-completed geometries, else
+ * IBDL_ERR_UNSUPPORTED).  For a completed geometry (eta > 0) q and y have
+ * length m + 1. */
 ibdl_status ibdl_apply_precision(ibdl_geometry g, const double* q, double* y,
                                  int32_t precision, void* stream);
 
