@@ -399,6 +399,14 @@ ibdl_status ibdl_near_boundary(ibdl_geometry g, const double* u_in, const double
                                const uint8_t* inside, int32_t m1, double m2, double* u_out,
                                void* stream);
 
+/* Self-test of the bounded device waits that the persistent solver uses
+ * between its blocks.  One block joins a barrier of two parties, so its
+ * wait cannot complete; it gives up after spin_limit polls (1 .. 2^24; the
+ * solver's own limit is 2^27), raises the error word and returns.  Returns
+ * IBDL_ERR_TIMEOUT when the wait gave up as designed (the context stays
+ * usable), IBDL_OK if it did not, IBDL_ERR_INVALID_ARG, IBDL_ERR_CUDA. */
+ibdl_status ibdl_selftest_bounded_wait(uint32_t spin_limit, void* stream);
+
 /* Read-only facts about a handle. */
 typedef struct {
   int32_t dim, n;

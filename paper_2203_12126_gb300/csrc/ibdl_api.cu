@@ -1512,6 +1512,26 @@ ibdl_status ibdl_near_boundary(ibdl_geometry g, const double* u_in, const double
   return IBDL_OK;
 }
 
+ibdl_status ibdl_selftest_bounded_wait(uint32_t spin_limit, void* stream) {
+  g_err.clear();
+  if (spin_limit < 1 || spin_limit > (1u << 24))
+    return fail(IBDL_ERR_INVALID_ARG, "spin_limit in 1 .. 2^24");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaMemPool_t pool;
+  IBDL_CU(workspace_pool(&pool));
+  unsigned* bar = nullptr;
+  IBDL_CU(cudaMallocFromPoolAsync((void**)&bar, 4 * sizeof(unsigned), pool, st));
+  unsigned flag = 0;
+  cudaError_t e = cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), st);
+  if (!e) e = launch_barrier_selftest(bar, spin_limit, st);
+  if (!e) e = cudaMemcpyAsync(&flag, bar + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(bar, st);
+  if (!e) e = cudaStreamSynchronize(st);
+  if (e) return cuda_fail(e, "bounded-wait self-test");
+  if (flag) return fail(IBDL_ERR_TIMEOUT, "the self-test wait gave up, as designed");
+  return IBDL_OK;
+}
+
 ibdl_status ibdl_get_geometry_info(ibdl_geometry g, ibdl_geometry_info* info) {
   IBDL_TRY(check_handle(g));
   if (!info) return fail(IBDL_ERR_INVALID_ARG, "NULL info");

@@ -71,6 +71,9 @@ struct SolveState {
 };
 
 int solver_smem_bytes(const GridDesc& g, int rows, int need32);
+// One block joins a two-party barrier: its bounded wait gives up after
+// `limit` polls and sets bar[2] (bar: 4 zeroed words).
+cudaError_t launch_barrier_selftest(unsigned* bar, unsigned limit, cudaStream_t st);
 // max_rounds > 0 stops the launch after that many rounds (states persist for
 // the next launch); reserve_sms SMs are left without solver blocks.
 cudaError_t launch_persistent_solve(const SolveInst* d_insts, SolveState* d_states, int ninst,

@@ -35,9 +35,10 @@ namespace ibdl {
 constexpr unsigned kSpinLimit = 1u << 27;  // x >= 20 ns sleeps: a few seconds
 
 // Counting barrier among `parties` blocks on ctr[0] (arrivals) and ctr[1]
-// (generation).  The spin is bounded: on timeout it raises *err, which every
-// later barrier sees, and all blocks leave the kernel.
-__device__ bool counted_barrier(unsigned* ctr, unsigned parties, unsigned* err) {
+// (generation).  The spin is bounded (`limit` polls): on timeout it raises
+// *err, which every later barrier sees, and all blocks leave the kernel.
+__device__ bool counted_barrier(unsigned* ctr, unsigned parties, unsigned* err,
+                                unsigned limit = kSpinLimit) {
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned* vgen = ctr + 1;
@@ -51,7 +52,7 @@ __device__ bool counted_barrier(unsigned* ctr, unsigned parties, unsigned* err) 
     } else {
       unsigned spins = 0;
       while (*vgen == gen) {
-        if (++spins > kSpinLimit) {
+        if (++spins > limit) {
           atomicExch(err, 1u);
           break;
         }
@@ -63,6 +64,18 @@ __device__ bool counted_barrier(unsigned* ctr, unsigned parties, unsigned* err) 
   }
   __syncthreads();
   return *(volatile unsigned*)err == 0u;
+}
+
+// Self-test of the bounded wait: a barrier of two parties that only this
+// one block joins, so its wait must give up after `limit` polls and raise
+// bar[2].
+__global__ void k_barrier_selftest(unsigned* bar, unsigned limit) {
+  counted_barrier(bar, 2u, bar + 2, limit);
+}
+
+cudaError_t launch_barrier_selftest(unsigned* bar, unsigned limit, cudaStream_t st) {
+  k_barrier_selftest<<<1, 32, 0, st>>>(bar, limit);
+  return cudaGetLastError();
 }
 
 // bar[0..1]: the start-up grid barrier, bar[2]: error flag, bar[3]: count of

@@ -39,6 +39,7 @@ EXPORTS = [
     "ibdl_server_config_default", "ibdl_server_create", "ibdl_server_destroy",
     "ibdl_server_clock", "ibdl_server_submit", "ibdl_server_step", "ibdl_server_take",
     "ibdl_server_get_stats", "ibdl_tuning_enable", "ibdl_indicator", "ibdl_near_boundary",
+    "ibdl_selftest_bounded_wait",
 ]
 
 
@@ -169,6 +170,7 @@ def load(path: str = LIB_PATH):
         "ibdl_tuning_enable": (None, [i32]),
         "ibdl_indicator": (C.c_int, [vp, vp, vp, vp]),
         "ibdl_near_boundary": (C.c_int, [vp, vp, vp, vp, i32, C.c_double, vp, vp]),
+        "ibdl_selftest_bounded_wait": (C.c_int, [C.c_uint32, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -241,6 +243,11 @@ def profile_read(reset: bool = True) -> dict:
     k = lib.ibdl_profile_read(arr, k, 1 if reset else 0)
     return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms))
             for i in range(k)}
+
+
+def selftest_bounded_wait(spin_limit=1 << 16, stream=None) -> int:
+    """Run the bounded-wait self-test; returns the status (TIMEOUT expected)."""
+    return int(load().ibdl_selftest_bounded_wait(int(spin_limit), _stream(stream)))
 
 
 def helmholtz_2d_noalloc(n, box_len, kappa, f, v_out, stream=None):

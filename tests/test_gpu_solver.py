@@ -270,3 +270,18 @@ def test_double_float_and_float64_residuals_agree():
     big.close()
     for g in geoms + many:
         g.close()
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable():
+    """The solver's inter-block waits are bounded: a two-party barrier that
+    only one block joins gives up after its poll limit and reports
+    IBDL_ERR_TIMEOUT (no fault, no hang); a solve right after succeeds."""
+    import time
+    t0 = time.time()
+    assert ibdl.selftest_bounded_wait(1 << 14) == ibdl.ERR_TIMEOUT
+    assert time.time() - t0 < 30
+    p = configs.c1()
+    G = pkg.Geometry.from_workload(p.geom, bc=p.bc)
+    q = torch.zeros(p.geom.m, dtype=torch.float64, device=DEV)
+    assert G.solve(gpu(p.bdata), q, tol=1e-10)["status"] == 0
+    G.close()
