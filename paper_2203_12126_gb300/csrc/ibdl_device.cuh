@@ -371,13 +371,17 @@ __device__ __forceinline__ void copy_to_shared(V* dst, const V* __restrict__ src
   }
 }
 
-// 1/x for the Helmholtz symbol (x >= 1).  float: the correctly rounded
-// reciprocal.  double: Newton-Raphson for 1/x, r <- r + r (1 - x r), from a
+// 1/x for the symbol (x > 0).  float: the hardware approximate reciprocal.
+// double: Newton-Raphson for 1/x, r <- r + r (1 - x r), from a
 // float first guess; each step doubles the number of correct bits (24 ->
 // 48 -> beyond 53), at four FMAs instead of a full double division.
 template <typename T> __device__ __forceinline__ T recip_symbol(T x);
 template <> __device__ __forceinline__ float recip_symbol<float>(float x) {
-  return __frcp_rn(x);
+  // the hardware approximate reciprocal (one MUFU instruction, within about
+  // an ulp): ample for the float32 operator, and once per spectral element
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
 }
 template <> __device__ __forceinline__ dd recip_symbol<dd>(dd x) {
   // Newton from the float reciprocal of the high part, two steps in
