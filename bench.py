@@ -181,7 +181,7 @@ def run_c3_solve(pkg, reps=3):
             "fp64_solve_ms": fp64_ms, "fp64_iters": i64["iters"], "rows_per_tile": rows}
 
 
-def run_batched_c4(pkg, count=256, reps=3):
+def run_batched_c4(pkg, count=256, reps=5):
     """C4: `count` uneven 2D star instances (N in {128,256,512}^2, kappa
     log-uniform [1e-4,1e-1], seed 2) solved in ONE persistent launch,
     float32-refined to 1e-8; event-timed, L2 flushed between launches."""
