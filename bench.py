@@ -822,7 +822,9 @@ def main():
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64" if prec == ibdl.FP32_REFINED else "f64",
+            # float32 inner operator; float64 spread, interpolation and Krylov
+            # work; double-float transforms for the residuals of the pair
+            "dtype": "f32+f64+dd" if prec == ibdl.FP32_REFINED else "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": n, "m": m, "kappa": 1e-3,
                        "tol": args.tol, "precision": args.precision,
