@@ -260,11 +260,57 @@ template <int LR, bool INV, typename C> __device__ __forceinline__ void dft_reg(
   if (LR == 4) dft16<INV>(a);
 }
 
-template <typename T, int LG, int S, bool INV>
+// 1/x for the symbol (x > 0).  float: the hardware approximate reciprocal.
+// double: Newton-Raphson for 1/x, r <- r + r (1 - x r), from a
+// float first guess; each step doubles the number of correct bits (24 ->
+// 48 -> beyond 53), at four FMAs instead of a full double division.
+template <typename T> __device__ __forceinline__ T recip_symbol(T x);
+template <> __device__ __forceinline__ float recip_symbol<float>(float x) {
+  // the hardware approximate reciprocal (one MUFU instruction, within about
+  // an ulp): ample for the float32 operator, and once per spectral element
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+template <> __device__ __forceinline__ dd recip_symbol<dd>(dd x) {
+  // Newton from the float reciprocal of the high part, two steps in
+  // double-float (24 -> 48 bits)
+  dd r(__frcp_rn(x.hi), 0.0f);
+  r = r + r * (dd(1) - x * r);
+  return r + r * (dd(1) - x * r);
+}
+template <> __device__ __forceinline__ double recip_symbol<double>(double x) {
+  double r = (double)__frcp_rn((float)x);
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+
+// Two consecutive complex values as one 16-byte access (float) or two
+// (double).  Even element indices keep the float pair 16-byte aligned.
+// The Helmholtz symbol multiply (Sec. 6.2) applied as the last forward pass
+// stores its outputs: element t of pencil pen is scaled by
+// scale0 / (c0 + cfac (pre + s2s[pbase + pen] + s2s[t])), or zeroed where
+// that denominator is 0 (the Poisson limit's k = 0 mode).  Pencils at or
+// beyond npl hold no data of the item and are left as they are.  Off for
+// double-float, whose reciprocal would be unrolled into every butterfly
+// output; there the multiply stays a sweep of its own.
+template <typename T> struct SymbolEpi {
+  const T* s2s;
+  T pre, c0, cfac, scale0;
+  int pbase, npl;
+};
+template <typename T> struct FoldsSymbol { static constexpr bool value = true; };
+template <> struct FoldsSymbol<dd> { static constexpr bool value = false; };
+
+template <typename T, int LG, int S, bool INV, bool LAST = false>
 __device__ __forceinline__ void fft_pass(const cx_t<T>* __restrict__ src,
                                          cx_t<T>* __restrict__ dst, int npen,
-                                         const cx_t<T>* __restrict__ tws) {
+                                         const cx_t<T>* __restrict__ tws,
+                                         const SymbolEpi<T>& epi = SymbolEpi<T>{}) {
   using C = cx_t<T>;
+  constexpr bool kEpi = LAST && !INV && FoldsSymbol<T>::value;
   constexpr int LR = plan_lr(LG, S), LGNS = plan_lgns(LG, S), OFF = plan_off(LG, S);
   constexpr int R = 1 << LR, LGNB = LG - LR, NB = 1 << LGNB, NS = 1 << LGNS;
   constexpr int PS = pen_stride(1 << LG);
@@ -295,6 +341,17 @@ __device__ __forceinline__ void fft_pass(const cx_t<T>* __restrict__ src,
     dft_reg<LR, INV>(a);
     C* y = dst + pen * PS;
     const int o = ((j - k) << LR) + k;
+    if (kEpi && pen < epi.npl) {
+      // the last pass writes frequency o + p NS of pencil pen
+      const T pt = epi.pre + epi.s2s[epi.pbase + pen];
+#pragma unroll
+      for (int p = 0; p < R; ++p) {
+        const T den = epi.c0 + epi.cfac * (pt + epi.s2s[o + p * NS]);
+        const T f = den > (T)0 ? epi.scale0 * recip_symbol<T>(den) : (T)0;
+        a[p].x *= f;
+        a[p].y *= f;
+      }
+    }
     C* yb = y + padi(o);
     if (NS % 16 == 0) {
       // padi(o + p NS) = padi(o) + p (NS + NS/16)
@@ -322,6 +379,21 @@ __device__ __noinline__ cx_t<T>* fft_run_lg(cx_t<T>* src, cx_t<T>* dst, int npen
   return dst;
 }
 
+// The forward transform with the symbol multiply on its last pass.
+template <typename T, int LG>
+__device__ __noinline__ cx_t<T>* fft_symbol_lg(cx_t<T>* src, cx_t<T>* dst, int npen,
+                                               const cx_t<T>* __restrict__ tws,
+                                               const SymbolEpi<T> epi) {
+  constexpr int NP = plan_npass(LG);
+  static_assert(NP <= 3, "n <= 4096");
+  fft_pass<T, LG, 0, false, NP == 1>(src, dst, npen, tws, epi);
+  if (NP == 1) return dst;
+  fft_pass<T, LG, (NP > 1 ? 1 : 0), false, NP == 2>(dst, src, npen, tws, epi);
+  if (NP == 2) return src;
+  fft_pass<T, LG, (NP > 2 ? 2 : 0), false, true>(src, dst, npen, tws, epi);
+  return dst;
+}
+
 // Transforms npen pencils held in src (shared, padded layout); tws is the
 // concatenated twiddle table in shared memory.  The caller synchronises
 // before the call.  Returns the buffer (src or dst) holding the result.
@@ -338,6 +410,26 @@ __device__ __forceinline__ cx_t<T>* fft_run(cx_t<T>* src, cx_t<T>* dst, int lg, 
     case 10: return fft_run_lg<T, 10, INV>(src, dst, npen, tws);
     case 11: return fft_run_lg<T, 11, INV>(src, dst, npen, tws);
     default: return fft_run_lg<T, 12, INV>(src, dst, npen, tws);
+  }
+}
+
+// Forward transform of npen pencils, each output scaled by the symbol as the
+// last pass stores it (float and double only).
+template <typename T>
+__device__ __forceinline__ cx_t<T>* fft_symbol(cx_t<T>* src, cx_t<T>* dst, int lg, int npen,
+                                               const cx_t<T>* __restrict__ tws,
+                                               const SymbolEpi<T>& epi) {
+  static_assert(FoldsSymbol<T>::value, "double-float multiplies in a sweep of its own");
+  switch (lg) {
+    case 4: return fft_symbol_lg<T, 4>(src, dst, npen, tws, epi);
+    case 5: return fft_symbol_lg<T, 5>(src, dst, npen, tws, epi);
+    case 6: return fft_symbol_lg<T, 6>(src, dst, npen, tws, epi);
+    case 7: return fft_symbol_lg<T, 7>(src, dst, npen, tws, epi);
+    case 8: return fft_symbol_lg<T, 8>(src, dst, npen, tws, epi);
+    case 9: return fft_symbol_lg<T, 9>(src, dst, npen, tws, epi);
+    case 10: return fft_symbol_lg<T, 10>(src, dst, npen, tws, epi);
+    case 11: return fft_symbol_lg<T, 11>(src, dst, npen, tws, epi);
+    default: return fft_symbol_lg<T, 12>(src, dst, npen, tws, epi);
   }
 }
 
@@ -371,35 +463,6 @@ __device__ __forceinline__ void copy_to_shared(V* dst, const V* __restrict__ src
   }
 }
 
-// 1/x for the symbol (x > 0).  float: the hardware approximate reciprocal.
-// double: Newton-Raphson for 1/x, r <- r + r (1 - x r), from a
-// float first guess; each step doubles the number of correct bits (24 ->
-// 48 -> beyond 53), at four FMAs instead of a full double division.
-template <typename T> __device__ __forceinline__ T recip_symbol(T x);
-template <> __device__ __forceinline__ float recip_symbol<float>(float x) {
-  // the hardware approximate reciprocal (one MUFU instruction, within about
-  // an ulp): ample for the float32 operator, and once per spectral element
-  float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
-template <> __device__ __forceinline__ dd recip_symbol<dd>(dd x) {
-  // Newton from the float reciprocal of the high part, two steps in
-  // double-float (24 -> 48 bits)
-  dd r(__frcp_rn(x.hi), 0.0f);
-  r = r + r * (dd(1) - x * r);
-  return r + r * (dd(1) - x * r);
-}
-template <> __device__ __forceinline__ double recip_symbol<double>(double x) {
-  double r = (double)__frcp_rn((float)x);
-  double e = fma(-x, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-x, r, 1.0);
-  return fma(r, e, r);
-}
-
-// Two consecutive complex values as one 16-byte access (float) or two
-// (double).  Even element indices keep the float pair 16-byte aligned.
 template <typename T> struct Pair;
 template <> struct Pair<float> {
   float2 a, b;
@@ -813,23 +876,38 @@ __device__ __forceinline__ void phase_pencils(const GridDesc& g, const PencilLay
   if (MODE == 2) copy_to_shared(s2s, s2, n);
   __syncthreads();
 
-  C* res = fft_run<T, MODE == 1>(bufA, bufB, lg, c, tws);
+  C* res;
   if (MODE == 2) {
     // 2D: pencil kx = p0 + pl, position ky = t; 3D: kx = gi0, ky = q0 + pl, kz = t
-    const T sfix = g.dim == 3 ? s2s[gi0] : (T)0;
     const T c0 = g.poisson ? (T)0 : (T)1;
-    for (int e = tid; e < (npl << lg); e += nt) {
-      const int pl = e >> lg, t = e & (n - 1);
-      const T ssum = g.dim == 3 ? sfix + s2s[q0 + pl] + s2s[t] : s2s[p0 + pl] + s2s[t];
-      const T den = c0 + cfac * ssum;
-      const T f = den > (T)0 ? scale0 * recip_symbol<T>(den) : (T)0;
-      C& v = res[pl * PS + padi(t)];
-      v.x *= f;
-      v.y *= f;
+    if constexpr (FoldsSymbol<T>::value) {
+      SymbolEpi<T> epi;
+      epi.s2s = s2s;
+      epi.pre = g.dim == 3 ? s2s[gi0] : (T)0;
+      epi.c0 = c0;
+      epi.cfac = cfac;
+      epi.scale0 = scale0;
+      epi.pbase = g.dim == 3 ? q0 : p0;
+      epi.npl = npl;
+      res = fft_symbol<T>(bufA, bufB, lg, c, tws, epi);
+    } else {
+      res = fft_run<T, false>(bufA, bufB, lg, c, tws);
+      const T sfix = g.dim == 3 ? s2s[gi0] : (T)0;
+      for (int e = tid; e < (npl << lg); e += nt) {
+        const int pl = e >> lg, t = e & (n - 1);
+        const T ssum = g.dim == 3 ? sfix + s2s[q0 + pl] + s2s[t] : s2s[p0 + pl] + s2s[t];
+        const T den = c0 + cfac * ssum;
+        const T f = den > (T)0 ? scale0 * recip_symbol<T>(den) : (T)0;
+        C& v = res[pl * PS + padi(t)];
+        v.x *= f;
+        v.y *= f;
+      }
+      __syncthreads();
     }
-    __syncthreads();
     C* other = (res == bufA) ? bufB : bufA;
     res = fft_run<T, true>(res, other, lg, c, tws);
+  } else {
+    res = fft_run<T, MODE == 1>(bufA, bufB, lg, c, tws);
   }
 
   for (int k = tid; k < npairs; k += nt) {
