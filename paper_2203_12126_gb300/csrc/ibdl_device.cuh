@@ -304,23 +304,37 @@ template <typename T> struct SymbolEpi {
 template <typename T> struct FoldsSymbol { static constexpr bool value = true; };
 template <> struct FoldsSymbol<dd> { static constexpr bool value = false; };
 
-template <typename T, int LG, int S, bool INV, bool LAST = false>
+// GIN: the pass reads its inputs from global memory, pencil pen at
+// gio + pen 2^LG in natural order, instead of from src; GOUT: it writes its
+// outputs there instead of to dst.  Either way only pencils below npl are
+// touched: the others hold no data of the item.  A first pass reads
+// elements j + q NB and a last pass writes j + p NS (NS = NB there), so a
+// warp's consecutive j make both accesses coalesced.
+template <typename T, int LG, int S, bool INV, bool LAST = false, bool GIN = false,
+          bool GOUT = false>
 __device__ __forceinline__ void fft_pass(const cx_t<T>* __restrict__ src,
                                          cx_t<T>* __restrict__ dst, int npen,
                                          const cx_t<T>* __restrict__ tws,
-                                         const SymbolEpi<T>& epi = SymbolEpi<T>{}) {
+                                         const SymbolEpi<T>& epi = SymbolEpi<T>{},
+                                         cx_t<T>* gio = nullptr, int npl = 0) {
   using C = cx_t<T>;
   constexpr bool kEpi = LAST && !INV && FoldsSymbol<T>::value;
   constexpr int LR = plan_lr(LG, S), LGNS = plan_lgns(LG, S), OFF = plan_off(LG, S);
   constexpr int R = 1 << LR, LGNB = LG - LR, NB = 1 << LGNB, NS = 1 << LGNS;
   constexpr int PS = pen_stride(1 << LG);
+  static_assert(!GIN || S == 0, "global inputs feed the first pass");
   const int total = npen << LGNB;
   for (int e = threadIdx.x; e < total; e += blockDim.x) {
     const int pen = e >> LGNB, j = e & (NB - 1);
+    if ((GIN || GOUT) && pen >= npl) continue;
     const int k = j & (NS - 1);
     const C* x = src + pen * PS;
     C a[R];
-    if (NB % 16 == 0) {
+    if constexpr (GIN) {
+      const C* xg = gio + ((size_t)pen << LG) + j;
+#pragma unroll
+      for (int q = 0; q < R; ++q) a[q] = __ldcg(xg + q * NB);
+    } else if (NB % 16 == 0) {
       // padi(j + q NB) = padi(j) + q (NB + NB/16)
       const C* xb = x + padi(j);
 #pragma unroll
@@ -339,7 +353,6 @@ __device__ __forceinline__ void fft_pass(const cx_t<T>* __restrict__ src,
       }
     }
     dft_reg<LR, INV>(a);
-    C* y = dst + pen * PS;
     const int o = ((j - k) << LR) + k;
     if (kEpi && pen < epi.npl) {
       // the last pass writes frequency o + p NS of pencil pen
@@ -352,7 +365,13 @@ __device__ __forceinline__ void fft_pass(const cx_t<T>* __restrict__ src,
         a[p].y *= f;
       }
     }
-    C* yb = y + padi(o);
+    if constexpr (GOUT) {
+      C* yg = gio + ((size_t)pen << LG) + o;
+#pragma unroll
+      for (int p = 0; p < R; ++p) yg[p * NS] = a[p];
+      continue;
+    }
+    C* yb = dst + pen * PS + padi(o);
     if (NS % 16 == 0) {
       // padi(o + p NS) = padi(o) + p (NS + NS/16)
 #pragma unroll
@@ -392,6 +411,58 @@ __device__ __noinline__ cx_t<T>* fft_symbol_lg(cx_t<T>* src, cx_t<T>* dst, int n
   if (NP == 2) return src;
   fft_pass<T, LG, (NP > 2 ? 2 : 0), false, true>(src, dst, npen, tws, epi);
   return dst;
+}
+
+// One Helmholtz solve of npl contiguous pencils at gio (global, natural
+// order, overwritten with the result): forward transform with the first
+// pass reading global memory, symbol multiply on the last forward pass,
+// inverse transform with the last pass writing global memory.  bufA/bufB
+// are the shared pencil buffers of npen pencils.
+template <typename T, int LG>
+__device__ __noinline__ void fft_solve_global_lg(cx_t<T>* gio, int npl, cx_t<T>* bufA,
+                                                 cx_t<T>* bufB, int npen,
+                                                 const cx_t<T>* __restrict__ tws,
+                                                 const SymbolEpi<T> epi) {
+  constexpr int NP = plan_npass(LG);
+  static_assert(NP <= 3, "n <= 4096");
+  constexpr int S1 = NP > 1 ? 1 : 0, S2 = NP > 2 ? 2 : 0;
+  // forward: bufB after pass 0, then alternate
+  fft_pass<T, LG, 0, false, NP == 1, true>(bufA, bufB, npen, tws, epi, gio, npl);
+  if (NP > 1) fft_pass<T, LG, S1, false, NP == 2>(bufB, bufA, npen, tws, epi);
+  if (NP > 2) fft_pass<T, LG, S2, false, true>(bufA, bufB, npen, tws, epi);
+  // the forward result is in bufB (NP odd) or bufA (NP even)
+  cx_t<T>* r = (NP % 2) ? bufB : bufA;
+  cx_t<T>* o = (NP % 2) ? bufA : bufB;
+  if (NP == 1) {
+    fft_pass<T, LG, 0, true, false, false, true>(r, o, npen, tws, epi, gio, npl);
+    return;
+  }
+  fft_pass<T, LG, 0, true>(r, o, npen, tws);
+  if (NP == 2) {
+    fft_pass<T, LG, S1, true, false, false, true>(o, r, npen, tws, epi, gio, npl);
+    return;
+  }
+  fft_pass<T, LG, S1, true>(o, r, npen, tws);
+  fft_pass<T, LG, S2, true, false, false, true>(r, o, npen, tws, epi, gio, npl);
+}
+
+template <typename T>
+__device__ __forceinline__ void fft_solve_global(cx_t<T>* gio, int npl, cx_t<T>* bufA,
+                                                 cx_t<T>* bufB, int lg, int npen,
+                                                 const cx_t<T>* __restrict__ tws,
+                                                 const SymbolEpi<T>& epi) {
+  static_assert(FoldsSymbol<T>::value, "double-float multiplies in a sweep of its own");
+  switch (lg) {
+    case 4: return fft_solve_global_lg<T, 4>(gio, npl, bufA, bufB, npen, tws, epi);
+    case 5: return fft_solve_global_lg<T, 5>(gio, npl, bufA, bufB, npen, tws, epi);
+    case 6: return fft_solve_global_lg<T, 6>(gio, npl, bufA, bufB, npen, tws, epi);
+    case 7: return fft_solve_global_lg<T, 7>(gio, npl, bufA, bufB, npen, tws, epi);
+    case 8: return fft_solve_global_lg<T, 8>(gio, npl, bufA, bufB, npen, tws, epi);
+    case 9: return fft_solve_global_lg<T, 9>(gio, npl, bufA, bufB, npen, tws, epi);
+    case 10: return fft_solve_global_lg<T, 10>(gio, npl, bufA, bufB, npen, tws, epi);
+    case 11: return fft_solve_global_lg<T, 11>(gio, npl, bufA, bufB, npen, tws, epi);
+    default: return fft_solve_global_lg<T, 12>(gio, npl, bufA, bufB, npen, tws, epi);
+  }
 }
 
 // Transforms npen pencils held in src (shared, padded layout); tws is the
@@ -831,6 +902,30 @@ __device__ __forceinline__ void phase_pencils(const GridDesc& g, const PencilLay
   // the interpolation, which reads planes that hold points
   if (zskip && zskip[(q0 + npl) * ngroups] == zskip[q0 * ngroups]) return;
 
+  // 2D: pencil kx = p0 + pl, position ky = t; 3D: kx = gi0, ky = q0 + pl, kz = t
+  auto symbol_epi = [&]() {
+    SymbolEpi<T> epi;
+    epi.s2s = s2s;
+    epi.pre = g.dim == 3 ? s2s[gi0] : (T)0;
+    epi.c0 = g.poisson ? (T)0 : (T)1;
+    epi.cfac = cfac;
+    epi.scale0 = scale0;
+    epi.pbase = g.dim == 3 ? q0 : p0;
+    epi.npl = npl;
+    return epi;
+  };
+  if constexpr (MODE == 2 && FoldsSymbol<T>::value) {
+    if (tfast) {
+      // contiguous pencils: the transforms read and write global memory
+      // directly in their first and last passes
+      copy_to_shared(tws, tw, ntw);
+      copy_to_shared(s2s, s2, n);
+      __syncthreads();
+      fft_solve_global<T>(base, npl, bufA, bufB, lg, c, tws, symbol_epi());
+      return;  // the last pass ends with a block barrier
+    }
+  }
+
   // pair k: contiguous -> elements 2k, 2k+1 of the item (one pencil, t even);
   // strided -> pencils pl, pl+1 (pl even) at position t.  npl is even or 1
   // in the strided case (c | pg, pg a power of two), so pairs never straddle.
@@ -878,18 +973,9 @@ __device__ __forceinline__ void phase_pencils(const GridDesc& g, const PencilLay
 
   C* res;
   if (MODE == 2) {
-    // 2D: pencil kx = p0 + pl, position ky = t; 3D: kx = gi0, ky = q0 + pl, kz = t
     const T c0 = g.poisson ? (T)0 : (T)1;
     if constexpr (FoldsSymbol<T>::value) {
-      SymbolEpi<T> epi;
-      epi.s2s = s2s;
-      epi.pre = g.dim == 3 ? s2s[gi0] : (T)0;
-      epi.c0 = c0;
-      epi.cfac = cfac;
-      epi.scale0 = scale0;
-      epi.pbase = g.dim == 3 ? q0 : p0;
-      epi.npl = npl;
-      res = fft_symbol<T>(bufA, bufB, lg, c, tws, epi);
+      res = fft_symbol<T>(bufA, bufB, lg, c, tws, symbol_epi());
     } else {
       res = fft_run<T, false>(bufA, bufB, lg, c, tws);
       const T sfix = g.dim == 3 ? s2s[gi0] : (T)0;
