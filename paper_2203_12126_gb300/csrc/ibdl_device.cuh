@@ -287,61 +287,100 @@ template <> __device__ __forceinline__ double recip_symbol<double>(double x) {
   return fma(r, e, r);
 }
 
-// Two consecutive complex values as one 16-byte access (float) or two
-// (double).  Even element indices keep the float pair 16-byte aligned.
 // The Helmholtz symbol multiply (Sec. 6.2) applied as the last forward pass
 // stores its outputs: element t of pencil pen is scaled by
 // scale0 / (c0 + cfac (pre + s2s[pbase + pen] + s2s[t])), or zeroed where
 // that denominator is 0 (the Poisson limit's k = 0 mode).  Pencils at or
-// beyond npl hold no data of the item and are left as they are.  Off for
-// double-float, whose reciprocal would be unrolled into every butterfly
-// output; there the multiply stays a sweep of its own.
+// beyond npl hold no data of the item and are left as they are.
 template <typename T> struct SymbolEpi {
   const T* s2s;
   T pre, c0, cfac, scale0;
   int pbase, npl;
 };
-template <typename T> struct FoldsSymbol { static constexpr bool value = true; };
-template <> struct FoldsSymbol<dd> { static constexpr bool value = false; };
 
-// GIN: the pass reads its inputs from global memory, pencil pen at
-// gio + pen 2^LG in natural order, instead of from src; GOUT: it writes its
-// outputs there instead of to dst.  Either way only pencils below npl are
-// touched: the others hold no data of the item.  A first pass reads
-// elements j + q NB and a last pass writes j + p NS (NS = NB there), so a
-// warp's consecutive j make both accesses coalesced.
-template <typename T, int LG, int S, bool INV, bool LAST = false, bool GIN = false,
-          bool GOUT = false>
+// Pencils of an item in global memory: pencil pen, element t at
+// p + pen n + t (contiguous) or p + t n + pen (strided: the 3D z pencils,
+// whose planes flagged in zempty hold no point and read as zeros).
+template <typename T> struct GlobalPencils {
+  cx_t<T>* p;
+  int npl;                     // pencils of the item (the rest are idle)
+  int lgc;                     // log2 of the item's pencil count (strided)
+  const unsigned char* zempty; // strided only; may be null
+};
+
+// Float and double transforms of the solver's pencil passes read their
+// first inputs from and write their last outputs to global memory, and
+// fold the symbol multiply into the last forward pass.  Double-float keeps
+// the staged copies and a multiply sweep of its own: the reciprocal and the
+// global accesses unrolled into every butterfly would grow its code, whose
+// size already limits it.
+template <typename T> struct DirectPencils { static constexpr bool value = true; };
+template <> struct DirectPencils<dd> { static constexpr bool value = false; };
+
+// One radix pass (see above).  SYM: scale the outputs by the symbol (a last
+// forward pass).  GIN: read the inputs from global memory (a first pass)
+// instead of src; GOUT: write the outputs to global memory (a last pass)
+// instead of dst; only pencils below gio.npl are touched then.  A first
+// pass reads elements j + q NB and a last pass writes j + p NS (NS = NB
+// there); the thread of butterfly e takes j fastest for contiguous pencils
+// and the pencil fastest for strided ones (STR), so a warp's accesses are
+// coalesced either way.
+template <typename T, int LG, int S, bool INV, bool SYM = false, bool GIN = false,
+          bool GOUT = false, bool STR = false>
 __device__ __forceinline__ void fft_pass(const cx_t<T>* __restrict__ src,
                                          cx_t<T>* __restrict__ dst, int npen,
                                          const cx_t<T>* __restrict__ tws,
                                          const SymbolEpi<T>& epi = SymbolEpi<T>{},
-                                         cx_t<T>* gio = nullptr, int npl = 0) {
+                                         const GlobalPencils<T>& gio = GlobalPencils<T>{}) {
   using C = cx_t<T>;
-  constexpr bool kEpi = LAST && !INV && FoldsSymbol<T>::value;
+  constexpr bool kSym = SYM && !INV && DirectPencils<T>::value;
+  constexpr bool kGlobal = GIN || GOUT;
+  constexpr int N = 1 << LG;
   constexpr int LR = plan_lr(LG, S), LGNS = plan_lgns(LG, S), OFF = plan_off(LG, S);
   constexpr int R = 1 << LR, LGNB = LG - LR, NB = 1 << LGNB, NS = 1 << LGNS;
-  constexpr int PS = pen_stride(1 << LG);
+  constexpr int PS = pen_stride(N);
   static_assert(!GIN || S == 0, "global inputs feed the first pass");
+  static_assert(!STR || kGlobal, "the strided order is for global accesses");
   const int total = npen << LGNB;
   for (int e = threadIdx.x; e < total; e += blockDim.x) {
-    const int pen = e >> LGNB, j = e & (NB - 1);
-    if ((GIN || GOUT) && pen >= npl) continue;
+    int pen, j;
+    if constexpr (STR) {
+      pen = e & ((1 << gio.lgc) - 1);
+      j = e >> gio.lgc;
+    } else {
+      pen = e >> LGNB;
+      j = e & (NB - 1);
+    }
+    if (kGlobal && pen >= gio.npl) continue;
     const int k = j & (NS - 1);
-    const C* x = src + pen * PS;
     C a[R];
     if constexpr (GIN) {
-      const C* xg = gio + ((size_t)pen << LG) + j;
+      if constexpr (STR) {
+        const C* xg = gio.p + (size_t)j * N + pen;
 #pragma unroll
-      for (int q = 0; q < R; ++q) a[q] = __ldcg(xg + q * NB);
-    } else if (NB % 16 == 0) {
-      // padi(j + q NB) = padi(j) + q (NB + NB/16)
-      const C* xb = x + padi(j);
+        for (int q = 0; q < R; ++q) {
+          if (gio.zempty && gio.zempty[j + q * NB]) {
+            a[q].x = a[q].y = 0;
+          } else {
+            a[q] = __ldcg(xg + (size_t)q * NB * N);
+          }
+        }
+      } else {
+        const C* xg = gio.p + (size_t)pen * N + j;
 #pragma unroll
-      for (int q = 0; q < R; ++q) a[q] = xb[q * (NB + NB / 16)];
+        for (int q = 0; q < R; ++q) a[q] = __ldcg(xg + q * NB);
+      }
     } else {
+      const C* x = src + pen * PS;
+      if (NB % 16 == 0) {
+        // padi(j + q NB) = padi(j) + q (NB + NB/16)
+        const C* xb = x + padi(j);
 #pragma unroll
-      for (int q = 0; q < R; ++q) a[q] = x[padi(j + q * NB)];
+        for (int q = 0; q < R; ++q) a[q] = xb[q * (NB + NB / 16)];
+      } else {
+#pragma unroll
+        for (int q = 0; q < R; ++q) a[q] = x[padi(j + q * NB)];
+      }
     }
     if (NS > 1) {
       const C* tw = tws + OFF + k;
@@ -354,7 +393,7 @@ __device__ __forceinline__ void fft_pass(const cx_t<T>* __restrict__ src,
     }
     dft_reg<LR, INV>(a);
     const int o = ((j - k) << LR) + k;
-    if (kEpi && pen < epi.npl) {
+    if (kSym && pen < epi.npl) {
       // the last pass writes frequency o + p NS of pencil pen
       const T pt = epi.pre + epi.s2s[epi.pbase + pen];
 #pragma unroll
@@ -366,102 +405,95 @@ __device__ __forceinline__ void fft_pass(const cx_t<T>* __restrict__ src,
       }
     }
     if constexpr (GOUT) {
-      C* yg = gio + ((size_t)pen << LG) + o;
+      if constexpr (STR) {
+        // planes without points are never read by the y inverse pass
+        C* yg = gio.p + (size_t)o * N + pen;
 #pragma unroll
-      for (int p = 0; p < R; ++p) yg[p * NS] = a[p];
-      continue;
-    }
-    C* yb = dst + pen * PS + padi(o);
-    if (NS % 16 == 0) {
-      // padi(o + p NS) = padi(o) + p (NS + NS/16)
+        for (int p = 0; p < R; ++p)
+          if (!(gio.zempty && gio.zempty[o + p * NS])) yg[(size_t)p * NS * N] = a[p];
+      } else {
+        C* yg = gio.p + (size_t)pen * N + o;
 #pragma unroll
-      for (int p = 0; p < R; ++p) yb[p * (NS + NS / 16)] = a[p];
+        for (int p = 0; p < R; ++p) yg[p * NS] = a[p];
+      }
     } else {
-      // NS == 1: o = R j, and o mod 16 + p < 16, so padi(o + p) = padi(o) + p
+      C* yb = dst + pen * PS + padi(o);
+      if (NS % 16 == 0) {
+        // padi(o + p NS) = padi(o) + p (NS + NS/16)
 #pragma unroll
-      for (int p = 0; p < R; ++p) yb[p] = a[p];
+        for (int p = 0; p < R; ++p) yb[p * (NS + NS / 16)] = a[p];
+      } else {
+        // NS == 1: o = R j, and o mod 16 + p < 16, so padi(o + p) = padi(o) + p
+#pragma unroll
+        for (int p = 0; p < R; ++p) yb[p] = a[p];
+      }
     }
   }
   __syncthreads();
 }
 
-template <typename T, int LG, bool INV>
-__device__ __noinline__ cx_t<T>* fft_run_lg(cx_t<T>* src, cx_t<T>* dst, int npen,
-                                            const cx_t<T>* __restrict__ tws) {
-  constexpr int NP = plan_npass(LG);
-  static_assert(NP <= 3, "n <= 4096");
-  fft_pass<T, LG, 0, INV>(src, dst, npen, tws);
-  if (NP == 1) return dst;
-  fft_pass<T, LG, (NP > 1 ? 1 : 0), INV>(dst, src, npen, tws);
-  if (NP == 2) return src;
-  fft_pass<T, LG, (NP > 2 ? 2 : 0), INV>(src, dst, npen, tws);
-  return dst;
-}
-
-// The forward transform with the symbol multiply on its last pass.
-template <typename T, int LG>
-__device__ __noinline__ cx_t<T>* fft_symbol_lg(cx_t<T>* src, cx_t<T>* dst, int npen,
+// All passes of one transform direction.  Pass s reads buffer s mod 2 and
+// writes buffer (s + 1) mod 2 of (a, b); returns the buffer of the result
+// (meaningless when GOUT).
+template <typename T, int LG, bool INV, bool SYM, bool GIN, bool GOUT, bool STR>
+__device__ __forceinline__ cx_t<T>* fft_passes(cx_t<T>* a, cx_t<T>* b, int npen,
                                                const cx_t<T>* __restrict__ tws,
-                                               const SymbolEpi<T> epi) {
-  constexpr int NP = plan_npass(LG);
-  static_assert(NP <= 3, "n <= 4096");
-  fft_pass<T, LG, 0, false, NP == 1>(src, dst, npen, tws, epi);
-  if (NP == 1) return dst;
-  fft_pass<T, LG, (NP > 1 ? 1 : 0), false, NP == 2>(dst, src, npen, tws, epi);
-  if (NP == 2) return src;
-  fft_pass<T, LG, (NP > 2 ? 2 : 0), false, true>(src, dst, npen, tws, epi);
-  return dst;
-}
-
-// One Helmholtz solve of npl contiguous pencils at gio (global, natural
-// order, overwritten with the result): forward transform with the first
-// pass reading global memory, symbol multiply on the last forward pass,
-// inverse transform with the last pass writing global memory.  bufA/bufB
-// are the shared pencil buffers of npen pencils.
-template <typename T, int LG>
-__device__ __noinline__ void fft_solve_global_lg(cx_t<T>* gio, int npl, cx_t<T>* bufA,
-                                                 cx_t<T>* bufB, int npen,
-                                                 const cx_t<T>* __restrict__ tws,
-                                                 const SymbolEpi<T> epi) {
+                                               const SymbolEpi<T>& epi,
+                                               const GlobalPencils<T>& gio) {
   constexpr int NP = plan_npass(LG);
   static_assert(NP <= 3, "n <= 4096");
   constexpr int S1 = NP > 1 ? 1 : 0, S2 = NP > 2 ? 2 : 0;
-  // forward: bufB after pass 0, then alternate
-  fft_pass<T, LG, 0, false, NP == 1, true>(bufA, bufB, npen, tws, epi, gio, npl);
-  if (NP > 1) fft_pass<T, LG, S1, false, NP == 2>(bufB, bufA, npen, tws, epi);
-  if (NP > 2) fft_pass<T, LG, S2, false, true>(bufA, bufB, npen, tws, epi);
-  // the forward result is in bufB (NP odd) or bufA (NP even)
-  cx_t<T>* r = (NP % 2) ? bufB : bufA;
-  cx_t<T>* o = (NP % 2) ? bufA : bufB;
-  if (NP == 1) {
-    fft_pass<T, LG, 0, true, false, false, true>(r, o, npen, tws, epi, gio, npl);
-    return;
-  }
-  fft_pass<T, LG, 0, true>(r, o, npen, tws);
-  if (NP == 2) {
-    fft_pass<T, LG, S1, true, false, false, true>(o, r, npen, tws, epi, gio, npl);
-    return;
-  }
-  fft_pass<T, LG, S1, true>(o, r, npen, tws);
-  fft_pass<T, LG, S2, true, false, false, true>(r, o, npen, tws, epi, gio, npl);
+  // the strided order only where a pass touches global memory
+  constexpr bool ST0 = STR && (GIN || (GOUT && NP == 1));
+  constexpr bool ST1 = STR && GOUT && NP == 2, ST2 = STR && GOUT && NP == 3;
+  fft_pass<T, LG, 0, INV, SYM && NP == 1, GIN, GOUT && NP == 1, ST0>(a, b, npen, tws, epi, gio);
+  if (NP == 1) return b;
+  fft_pass<T, LG, S1, INV, SYM && NP == 2, false, GOUT && NP == 2, ST1>(b, a, npen, tws, epi,
+                                                                         gio);
+  if (NP == 2) return a;
+  fft_pass<T, LG, S2, INV, SYM, false, GOUT, ST2>(a, b, npen, tws, epi, gio);
+  return b;
 }
 
-template <typename T>
-__device__ __forceinline__ void fft_solve_global(cx_t<T>* gio, int npl, cx_t<T>* bufA,
-                                                 cx_t<T>* bufB, int lg, int npen,
-                                                 const cx_t<T>* __restrict__ tws,
-                                                 const SymbolEpi<T>& epi) {
-  static_assert(FoldsSymbol<T>::value, "double-float multiplies in a sweep of its own");
+template <typename T, int LG, bool INV>
+__device__ __noinline__ cx_t<T>* fft_run_lg(cx_t<T>* src, cx_t<T>* dst, int npen,
+                                            const cx_t<T>* __restrict__ tws) {
+  return fft_passes<T, LG, INV, false, false, false, false>(src, dst, npen, tws, SymbolEpi<T>{},
+                                                            GlobalPencils<T>{});
+}
+
+// The pencil transforms of one item straight from and back to global
+// memory (gio): MODE 0 forward, 1 inverse, 2 forward with the symbol
+// multiply on its last pass, then inverse.  bufA/bufB are the shared pencil
+// buffers of npen pencils.
+template <typename T, int LG, int MODE, bool STR>
+__device__ __noinline__ void fft_global_lg(cx_t<T>* bufA, cx_t<T>* bufB, int npen,
+                                           const cx_t<T>* __restrict__ tws,
+                                           const SymbolEpi<T> epi, const GlobalPencils<T> gio) {
+  if constexpr (MODE == 2) {
+    cx_t<T>* r = fft_passes<T, LG, false, true, true, false, STR>(bufA, bufB, npen, tws, epi, gio);
+    cx_t<T>* o = (r == bufA) ? bufB : bufA;
+    fft_passes<T, LG, true, false, false, true, STR>(r, o, npen, tws, epi, gio);
+  } else {
+    fft_passes<T, LG, MODE == 1, false, true, true, STR>(bufA, bufB, npen, tws, epi, gio);
+  }
+}
+
+template <typename T, int MODE, bool STR>
+__device__ __forceinline__ void fft_global(cx_t<T>* bufA, cx_t<T>* bufB, int lg, int npen,
+                                           const cx_t<T>* __restrict__ tws,
+                                           const SymbolEpi<T>& epi, const GlobalPencils<T>& gio) {
+  static_assert(DirectPencils<T>::value, "double-float stages its pencils");
   switch (lg) {
-    case 4: return fft_solve_global_lg<T, 4>(gio, npl, bufA, bufB, npen, tws, epi);
-    case 5: return fft_solve_global_lg<T, 5>(gio, npl, bufA, bufB, npen, tws, epi);
-    case 6: return fft_solve_global_lg<T, 6>(gio, npl, bufA, bufB, npen, tws, epi);
-    case 7: return fft_solve_global_lg<T, 7>(gio, npl, bufA, bufB, npen, tws, epi);
-    case 8: return fft_solve_global_lg<T, 8>(gio, npl, bufA, bufB, npen, tws, epi);
-    case 9: return fft_solve_global_lg<T, 9>(gio, npl, bufA, bufB, npen, tws, epi);
-    case 10: return fft_solve_global_lg<T, 10>(gio, npl, bufA, bufB, npen, tws, epi);
-    case 11: return fft_solve_global_lg<T, 11>(gio, npl, bufA, bufB, npen, tws, epi);
-    default: return fft_solve_global_lg<T, 12>(gio, npl, bufA, bufB, npen, tws, epi);
+    case 4: return fft_global_lg<T, 4, MODE, STR>(bufA, bufB, npen, tws, epi, gio);
+    case 5: return fft_global_lg<T, 5, MODE, STR>(bufA, bufB, npen, tws, epi, gio);
+    case 6: return fft_global_lg<T, 6, MODE, STR>(bufA, bufB, npen, tws, epi, gio);
+    case 7: return fft_global_lg<T, 7, MODE, STR>(bufA, bufB, npen, tws, epi, gio);
+    case 8: return fft_global_lg<T, 8, MODE, STR>(bufA, bufB, npen, tws, epi, gio);
+    case 9: return fft_global_lg<T, 9, MODE, STR>(bufA, bufB, npen, tws, epi, gio);
+    case 10: return fft_global_lg<T, 10, MODE, STR>(bufA, bufB, npen, tws, epi, gio);
+    case 11: return fft_global_lg<T, 11, MODE, STR>(bufA, bufB, npen, tws, epi, gio);
+    default: return fft_global_lg<T, 12, MODE, STR>(bufA, bufB, npen, tws, epi, gio);
   }
 }
 
@@ -481,26 +513,6 @@ __device__ __forceinline__ cx_t<T>* fft_run(cx_t<T>* src, cx_t<T>* dst, int lg, 
     case 10: return fft_run_lg<T, 10, INV>(src, dst, npen, tws);
     case 11: return fft_run_lg<T, 11, INV>(src, dst, npen, tws);
     default: return fft_run_lg<T, 12, INV>(src, dst, npen, tws);
-  }
-}
-
-// Forward transform of npen pencils, each output scaled by the symbol as the
-// last pass stores it (float and double only).
-template <typename T>
-__device__ __forceinline__ cx_t<T>* fft_symbol(cx_t<T>* src, cx_t<T>* dst, int lg, int npen,
-                                               const cx_t<T>* __restrict__ tws,
-                                               const SymbolEpi<T>& epi) {
-  static_assert(FoldsSymbol<T>::value, "double-float multiplies in a sweep of its own");
-  switch (lg) {
-    case 4: return fft_symbol_lg<T, 4>(src, dst, npen, tws, epi);
-    case 5: return fft_symbol_lg<T, 5>(src, dst, npen, tws, epi);
-    case 6: return fft_symbol_lg<T, 6>(src, dst, npen, tws, epi);
-    case 7: return fft_symbol_lg<T, 7>(src, dst, npen, tws, epi);
-    case 8: return fft_symbol_lg<T, 8>(src, dst, npen, tws, epi);
-    case 9: return fft_symbol_lg<T, 9>(src, dst, npen, tws, epi);
-    case 10: return fft_symbol_lg<T, 10>(src, dst, npen, tws, epi);
-    case 11: return fft_symbol_lg<T, 11>(src, dst, npen, tws, epi);
-    default: return fft_symbol_lg<T, 12>(src, dst, npen, tws, epi);
   }
 }
 
@@ -534,6 +546,8 @@ __device__ __forceinline__ void copy_to_shared(V* dst, const V* __restrict__ src
   }
 }
 
+// Two consecutive complex values as one 16-byte access (float) or two
+// (double).  Even element indices keep the float pair 16-byte aligned.
 template <typename T> struct Pair;
 template <> struct Pair<float> {
   float2 a, b;
@@ -874,7 +888,10 @@ __host__ __device__ inline size_t pencil_smem_bytes(const PencilLayout& L, int n
 // An item's pencils are either contiguous (pencil p at data + p n: the 2D
 // kx slabs and the 3D y pencils) or strided (3D z pencils: the item's c
 // pencils are c consecutive y of one kx slab, element t at t n + pl), so one
-// base pointer per item addresses everything; elements move in pairs.
+// base pointer per item addresses everything.  Float and double items read
+// and write the pencils in their first and last radix passes; double-float
+// items (and the strided forward or inverse-only transforms) stage them
+// through shared memory, elements moving in pairs.
 template <typename T, int MODE>
 __device__ __forceinline__ void phase_pencils(const GridDesc& g, const PencilLayout& L,
                                               cx_t<T>* data, const cx_t<T>* __restrict__ tw,
@@ -902,26 +919,34 @@ __device__ __forceinline__ void phase_pencils(const GridDesc& g, const PencilLay
   // the interpolation, which reads planes that hold points
   if (zskip && zskip[(q0 + npl) * ngroups] == zskip[q0 * ngroups]) return;
 
-  // 2D: pencil kx = p0 + pl, position ky = t; 3D: kx = gi0, ky = q0 + pl, kz = t
-  auto symbol_epi = [&]() {
-    SymbolEpi<T> epi;
-    epi.s2s = s2s;
-    epi.pre = g.dim == 3 ? s2s[gi0] : (T)0;
-    epi.c0 = g.poisson ? (T)0 : (T)1;
-    epi.cfac = cfac;
-    epi.scale0 = scale0;
-    epi.pbase = g.dim == 3 ? q0 : p0;
-    epi.npl = npl;
-    return epi;
-  };
-  if constexpr (MODE == 2 && FoldsSymbol<T>::value) {
-    if (tfast) {
-      // contiguous pencils: the transforms read and write global memory
-      // directly in their first and last passes
+  if constexpr (DirectPencils<T>::value) {
+    if (MODE == 2 || tfast) {
+      // the transforms read and write global memory in their first and
+      // last passes (the strided forward and inverse-only transforms of
+      // the spectral discretisation stage their pencils below)
       copy_to_shared(tws, tw, ntw);
-      copy_to_shared(s2s, s2, n);
+      if (MODE == 2) copy_to_shared(s2s, s2, n);
       __syncthreads();
-      fft_solve_global<T>(base, npl, bufA, bufB, lg, c, tws, symbol_epi());
+      // 2D: pencil kx = p0 + pl, position ky = t; 3D: kx = gi0, ky = q0 + pl, kz = t
+      SymbolEpi<T> epi{};
+      if (MODE == 2) {
+        epi.s2s = s2s;
+        epi.pre = g.dim == 3 ? s2s[gi0] : (T)0;
+        epi.c0 = g.poisson ? (T)0 : (T)1;
+        epi.cfac = cfac;
+        epi.scale0 = scale0;
+        epi.pbase = g.dim == 3 ? q0 : p0;
+        epi.npl = npl;
+      }
+      GlobalPencils<T> gio;
+      gio.p = base;
+      gio.npl = npl;
+      gio.lgc = lgc;
+      gio.zempty = zempty;
+      if (tfast)
+        fft_global<T, MODE, false>(bufA, bufB, lg, c, tws, epi, gio);
+      else if constexpr (MODE == 2)
+        fft_global<T, MODE, true>(bufA, bufB, lg, c, tws, epi, gio);
       return;  // the last pass ends with a block barrier
     }
   }
@@ -971,29 +996,23 @@ __device__ __forceinline__ void phase_pencils(const GridDesc& g, const PencilLay
   if (MODE == 2) copy_to_shared(s2s, s2, n);
   __syncthreads();
 
-  C* res;
+  C* res = fft_run<T, MODE == 1>(bufA, bufB, lg, c, tws);
   if (MODE == 2) {
+    // double-float: the symbol multiply as a sweep of its own
     const T c0 = g.poisson ? (T)0 : (T)1;
-    if constexpr (FoldsSymbol<T>::value) {
-      res = fft_symbol<T>(bufA, bufB, lg, c, tws, symbol_epi());
-    } else {
-      res = fft_run<T, false>(bufA, bufB, lg, c, tws);
-      const T sfix = g.dim == 3 ? s2s[gi0] : (T)0;
-      for (int e = tid; e < (npl << lg); e += nt) {
-        const int pl = e >> lg, t = e & (n - 1);
-        const T ssum = g.dim == 3 ? sfix + s2s[q0 + pl] + s2s[t] : s2s[p0 + pl] + s2s[t];
-        const T den = c0 + cfac * ssum;
-        const T f = den > (T)0 ? scale0 * recip_symbol<T>(den) : (T)0;
-        C& v = res[pl * PS + padi(t)];
-        v.x *= f;
-        v.y *= f;
-      }
-      __syncthreads();
+    const T sfix = g.dim == 3 ? s2s[gi0] : (T)0;
+    for (int e = tid; e < (npl << lg); e += nt) {
+      const int pl = e >> lg, t = e & (n - 1);
+      const T ssum = g.dim == 3 ? sfix + s2s[q0 + pl] + s2s[t] : s2s[p0 + pl] + s2s[t];
+      const T den = c0 + cfac * ssum;
+      const T f = den > (T)0 ? scale0 * recip_symbol<T>(den) : (T)0;
+      C& v = res[pl * PS + padi(t)];
+      v.x *= f;
+      v.y *= f;
     }
+    __syncthreads();
     C* other = (res == bufA) ? bufB : bufA;
     res = fft_run<T, true>(res, other, lg, c, tws);
-  } else {
-    res = fft_run<T, MODE == 1>(bufA, bufB, lg, c, tws);
   }
 
   for (int k = tid; k < npairs; k += nt) {
