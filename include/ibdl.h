@@ -430,6 +430,17 @@ ibdl_status ibdl_get_geometry_info(ibdl_geometry g, ibdl_geometry_info* info);
  * tilings agree to rounding. */
 void ibdl_tuning_enable(int32_t on);
 
+/* Pins the x-pass tiling of one (current device, dim, n, precision): later
+ * geometries of that kind use `rows` grid rows per tile, as if the tuner
+ * had chosen it (while tuning is on; off, the fixed rule applies).  rows = 0
+ * drops the entry, so the next geometry of the kind tunes again.  For
+ * reproducible launches (a deployment that fixes its configuration, or a
+ * profiler run, under which timing candidates would be distorted).
+ * IBDL_ERR_INVALID_ARG unless dim is 2 or 3, n a power of two in
+ * [16, 4096], precision a geometry's (IBDL_FP64 or IBDL_FP32_REFINED),
+ * and rows 0 or an admissible tiling (as above); IBDL_ERR_CUDA if the current device cannot be read. */
+ibdl_status ibdl_tuning_set(int32_t dim, int32_t n, int32_t precision, int32_t rows);
+
 /* Number of this library's kernels launched so far in this process
  * (all handles, all streams). */
 int64_t ibdl_kernel_launch_count(void);

@@ -753,6 +753,12 @@ cudaError_t build_tiles(ibdl_geometry_s* g, int rows, int* start, int* cursor, i
 // rule rows_per_tile applies.
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int>, int> g_tuned;
+
+// the tilings the tuner times (and ibdl_tuning_set accepts)
+bool tiling_admissible(int n, int R) {
+  return R >= 2 && R <= 32 && (R & (R - 1)) == 0 && n / R >= 4 && R <= n - 5 &&
+         rows_smem_bytes<double>(n, R) <= 100 * 1024;
+}
 std::atomic<int> g_tuning_on{1};
 // set while the server builds a request's geometry: it takes a cached
 // tiling or the rule, never times candidates beside a running slice
@@ -776,8 +782,7 @@ ibdl_status tuned_rows(ibdl_geometry_s* g, int* rows_out, cudaStream_t st) {
   if (tl_no_tune || g->grid.spectral) return IBDL_OK;
   std::vector<int> cand;
   for (int R = 2; R <= 32; R *= 2)
-    if (n / R >= 4 && R <= n - 5 && rows_smem_bytes<double>(n, R) <= 100 * 1024)
-      cand.push_back(R);
+    if (tiling_admissible(n, R)) cand.push_back(R);
   if (cand.size() < 2) return IBDL_OK;
   cudaMemPool_t pool;
   IBDL_CU(workspace_pool(&pool));
@@ -1664,6 +1669,22 @@ ibdl_status ibdl_solve_batched(ibdl_batch b, int32_t count, const ibdl_geometry*
 int64_t ibdl_kernel_launch_count(void) { return (int64_t)g_launches.load(); }
 
 void ibdl_tuning_enable(int32_t on) { g_tuning_on.store(on != 0); }
+
+ibdl_status ibdl_tuning_set(int32_t dim, int32_t n, int32_t precision, int32_t rows) {
+  if ((dim != 2 && dim != 3) || n < 16 || n > 4096 || (n & (n - 1)) ||
+      precision < IBDL_FP64 || precision > IBDL_FP32_REFINED || rows < 0)
+    return IBDL_ERR_INVALID_ARG;
+  if (rows && !tiling_admissible(n, rows)) return IBDL_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return IBDL_ERR_CUDA;
+  const auto key = std::make_tuple(dev, (int)dim, (int)n, (int)precision);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (rows)
+    g_tuned[key] = rows;
+  else
+    g_tuned.erase(key);
+  return IBDL_OK;
+}
 
 void ibdl_profile_enable(int32_t on) {
   if (on && !g_phase_buf) {

@@ -38,8 +38,8 @@ EXPORTS = [
     "ibdl_batch_create", "ibdl_batch_destroy", "ibdl_solve_batched",
     "ibdl_server_config_default", "ibdl_server_create", "ibdl_server_destroy",
     "ibdl_server_clock", "ibdl_server_submit", "ibdl_server_step", "ibdl_server_take",
-    "ibdl_server_get_stats", "ibdl_tuning_enable", "ibdl_indicator", "ibdl_near_boundary",
-    "ibdl_selftest_bounded_wait",
+    "ibdl_server_get_stats", "ibdl_tuning_enable", "ibdl_tuning_set", "ibdl_indicator",
+    "ibdl_near_boundary", "ibdl_selftest_bounded_wait",
 ]
 
 
@@ -168,6 +168,7 @@ def load(path: str = LIB_PATH):
         "ibdl_server_take": (C.c_int, [vp, i64, vp, C.POINTER(RequestResult)]),
         "ibdl_server_get_stats": (C.c_int, [vp, C.POINTER(ServerStats)]),
         "ibdl_tuning_enable": (None, [i32]),
+        "ibdl_tuning_set": (i32, [i32, i32, i32, i32]),
         "ibdl_indicator": (C.c_int, [vp, vp, vp, vp]),
         "ibdl_near_boundary": (C.c_int, [vp, vp, vp, vp, i32, C.c_double, vp, vp]),
         "ibdl_selftest_bounded_wait": (C.c_int, [C.c_uint32, vp]),
@@ -261,6 +262,12 @@ def helmholtz_2d_noalloc(n, box_len, kappa, f, v_out, stream=None):
 
 def tuning_enable(on: bool = True) -> None:
     load().ibdl_tuning_enable(1 if on else 0)
+
+
+def tuning_set(dim: int, n: int, precision: int, rows: int) -> None:
+    """Pin the x-pass tiling of (current device, dim, n, precision); rows = 0
+    drops the pin."""
+    _check(load().ibdl_tuning_set(int(dim), int(n), int(precision), int(rows)))
 
 
 def version() -> int:

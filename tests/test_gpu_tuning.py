@@ -43,3 +43,36 @@ def test_tuned_tiling_matches_fixed_rule(which, prec, tol):
     finally:
         ibdl.tuning_enable(True)
     assert rel(out[True], out[False]) <= tol
+
+
+def test_pinned_tiling_is_used_and_checked():
+    """ibdl_tuning_set pins the tiling of a kind; the operator stays the
+    fixed rule's to rounding, and inadmissible pins are refused."""
+    g2 = geometry.circle(64, 0.3, kappa=1e-2)
+    g3 = geometry.sphere(32, 0.25, m=400, center=(0, 0, 0), origin=(-0.5,) * 3, kappa=1.0)
+    try:
+        for g, dim, pin in ((g2, 2, 8), (g3, 3, 4)):
+            q = torch.tensor(np.random.default_rng(9).standard_normal(g.m), device=DEV)
+            out = {}
+            for pinned in (False, True):
+                ibdl.tuning_enable(pinned)
+                if pinned:
+                    ibdl.tuning_set(dim, g.n, ibdl.FP64, pin)
+                G = pkg.Geometry.from_workload(g, bc=configs.DIRICHLET, precision=ibdl.FP64)
+                if pinned:
+                    assert G.info()["rows_per_tile"] == pin
+                y = torch.empty_like(q)
+                G.apply(q, y)
+                out[pinned] = y.cpu().numpy()
+                G.close()
+            assert rel(out[True], out[False]) <= 1e-12
+        bad = [(4, 64, 0, 8), (2, 100, 0, 8), (2, 64, 2, 8), (2, 64, 0, 6), (2, 64, 0, 32),
+               (2, 64, 0, -2), (3, 32, 0, 16)]
+        for args in bad:
+            with pytest.raises(ibdl.IbdlError) as e:
+                ibdl.tuning_set(*args)
+            assert e.value.status == 1, args
+    finally:
+        ibdl.tuning_set(2, 64, ibdl.FP64, 0)
+        ibdl.tuning_set(3, 32, ibdl.FP64, 0)
+        ibdl.tuning_enable(True)
