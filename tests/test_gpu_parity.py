@@ -231,6 +231,23 @@ def test_matvec_parity_full_c3_sampled():
         G.close()
 
 
+def test_matvec_parity_512_cube():
+    """3D at N=512^3 (M=3000): the smallest 3D grid whose pencil transforms
+    take three radix passes, so the strided z solve and the y passes run
+    their global-memory first and last passes in the three-pass plan.  The
+    oracle runs the full 512^3 FFTs once (about half a minute)."""
+    g = geometry.sphere(512, 0.3, m=3000, center=(0.0, 0.0, 0.0), origin=(-0.5,) * 3,
+                        kappa=1e-3)
+    q = density(g, 10)
+    ref = O.Operator(g, configs.NEUMANN).apply(q)
+    for prec, tol in ((0, 1e-12), (1, 1e-5), (2, 1e-12)):
+        G = make(g, bc=configs.NEUMANN, precision=min(prec, 1))
+        y = torch.empty(g.m, dtype=torch.float64, device=DEV)
+        G.apply(gpu(q), y, precision=prec)
+        assert rel(host(y), ref) <= tol, prec
+        G.close()
+
+
 # ---- solves ----------------------------------------------------------------------
 
 @pytest.mark.parametrize("name", ["c1", "wrap", "tiny", "cos4", "sphere_wrap16"])
