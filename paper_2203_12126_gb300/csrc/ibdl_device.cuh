@@ -324,14 +324,17 @@ template <> struct DirectPencils<dd> { static constexpr bool value = false; };
 // pass reads elements j + q NB and a last pass writes j + p NS (NS = NB
 // there); the thread of butterfly e takes j fastest for contiguous pencils
 // and the pencil fastest for strided ones (STR), so a warp's accesses are
-// coalesced either way.
+// coalesced either way.  With a row type RO, GOUT instead writes pencil pen
+// as two real rows, its real parts to rows[2 pen n + t] and its imaginary
+// parts to rows[(2 pen + 1) n + t] (the x inverse pass).
 template <typename T, int LG, int S, bool INV, bool SYM = false, bool GIN = false,
-          bool GOUT = false, bool STR = false>
+          bool GOUT = false, bool STR = false, typename RO = void>
 __device__ __forceinline__ void fft_pass(const cx_t<T>* __restrict__ src,
                                          cx_t<T>* __restrict__ dst, int npen,
                                          const cx_t<T>* __restrict__ tws,
                                          const SymbolEpi<T>& epi = SymbolEpi<T>{},
-                                         const GlobalPencils<T>& gio = GlobalPencils<T>{}) {
+                                         const GlobalPencils<T>& gio = GlobalPencils<T>{},
+                                         RO* rows = nullptr) {
   using C = cx_t<T>;
   constexpr bool kSym = SYM && !INV && DirectPencils<T>::value;
   constexpr bool kGlobal = GIN || GOUT;
@@ -404,7 +407,14 @@ __device__ __forceinline__ void fft_pass(const cx_t<T>* __restrict__ src,
         a[p].y *= f;
       }
     }
-    if constexpr (GOUT) {
+    if constexpr (GOUT && !std::is_void<RO>::value) {
+      RO* yr = rows + (size_t)(2 * pen) * N + o;
+#pragma unroll
+      for (int p = 0; p < R; ++p) {
+        yr[p * NS] = (RO)a[p].x;
+        yr[N + p * NS] = (RO)a[p].y;
+      }
+    } else if constexpr (GOUT) {
       if constexpr (STR) {
         // planes without points are never read by the y inverse pass
         C* yg = gio.p + (size_t)o * N + pen;
@@ -435,23 +445,26 @@ __device__ __forceinline__ void fft_pass(const cx_t<T>* __restrict__ src,
 // All passes of one transform direction.  Pass s reads buffer s mod 2 and
 // writes buffer (s + 1) mod 2 of (a, b); returns the buffer of the result
 // (meaningless when GOUT).
-template <typename T, int LG, bool INV, bool SYM, bool GIN, bool GOUT, bool STR>
+template <typename T, int LG, bool INV, bool SYM, bool GIN, bool GOUT, bool STR,
+          typename RO = void>
 __device__ __forceinline__ cx_t<T>* fft_passes(cx_t<T>* a, cx_t<T>* b, int npen,
                                                const cx_t<T>* __restrict__ tws,
                                                const SymbolEpi<T>& epi,
-                                               const GlobalPencils<T>& gio) {
+                                               const GlobalPencils<T>& gio,
+                                               RO* rows = nullptr) {
   constexpr int NP = plan_npass(LG);
   static_assert(NP <= 3, "n <= 4096");
   constexpr int S1 = NP > 1 ? 1 : 0, S2 = NP > 2 ? 2 : 0;
   // the strided order only where a pass touches global memory
   constexpr bool ST0 = STR && (GIN || (GOUT && NP == 1));
   constexpr bool ST1 = STR && GOUT && NP == 2, ST2 = STR && GOUT && NP == 3;
-  fft_pass<T, LG, 0, INV, SYM && NP == 1, GIN, GOUT && NP == 1, ST0>(a, b, npen, tws, epi, gio);
+  fft_pass<T, LG, 0, INV, SYM && NP == 1, GIN, GOUT && NP == 1, ST0, RO>(a, b, npen, tws, epi,
+                                                                         gio, rows);
   if (NP == 1) return b;
-  fft_pass<T, LG, S1, INV, SYM && NP == 2, false, GOUT && NP == 2, ST1>(b, a, npen, tws, epi,
-                                                                         gio);
+  fft_pass<T, LG, S1, INV, SYM && NP == 2, false, GOUT && NP == 2, ST1, RO>(b, a, npen, tws, epi,
+                                                                             gio, rows);
   if (NP == 2) return a;
-  fft_pass<T, LG, S2, INV, SYM, false, GOUT, ST2>(a, b, npen, tws, epi, gio);
+  fft_pass<T, LG, S2, INV, SYM, false, GOUT, ST2, RO>(a, b, npen, tws, epi, gio, rows);
   return b;
 }
 
@@ -494,6 +507,34 @@ __device__ __forceinline__ void fft_global(cx_t<T>* bufA, cx_t<T>* bufB, int lg,
     case 10: return fft_global_lg<T, 10, MODE, STR>(bufA, bufB, npen, tws, epi, gio);
     case 11: return fft_global_lg<T, 11, MODE, STR>(bufA, bufB, npen, tws, epi, gio);
     default: return fft_global_lg<T, 12, MODE, STR>(bufA, bufB, npen, tws, epi, gio);
+  }
+}
+
+// Inverse transform of the npen pencils in bufA (shared), the last pass
+// writing each pencil as two real rows of `rows` (global, n apart).
+template <typename T, int LG, typename OutT>
+__device__ __noinline__ void fft_inverse_rows_lg(cx_t<T>* bufA, cx_t<T>* bufB, int npen,
+                                                 const cx_t<T>* __restrict__ tws, OutT* rows) {
+  GlobalPencils<T> gio{};
+  gio.npl = npen;
+  fft_passes<T, LG, true, false, false, true, false, OutT>(bufA, bufB, npen, tws,
+                                                           SymbolEpi<T>{}, gio, rows);
+}
+
+template <typename T, typename OutT>
+__device__ __forceinline__ void fft_inverse_rows(cx_t<T>* bufA, cx_t<T>* bufB, int lg, int npen,
+                                                 const cx_t<T>* __restrict__ tws, OutT* rows) {
+  static_assert(DirectPencils<T>::value, "double-float stages its rows");
+  switch (lg) {
+    case 4: return fft_inverse_rows_lg<T, 4>(bufA, bufB, npen, tws, rows);
+    case 5: return fft_inverse_rows_lg<T, 5>(bufA, bufB, npen, tws, rows);
+    case 6: return fft_inverse_rows_lg<T, 6>(bufA, bufB, npen, tws, rows);
+    case 7: return fft_inverse_rows_lg<T, 7>(bufA, bufB, npen, tws, rows);
+    case 8: return fft_inverse_rows_lg<T, 8>(bufA, bufB, npen, tws, rows);
+    case 9: return fft_inverse_rows_lg<T, 9>(bufA, bufB, npen, tws, rows);
+    case 10: return fft_inverse_rows_lg<T, 10>(bufA, bufB, npen, tws, rows);
+    case 11: return fft_inverse_rows_lg<T, 11>(bufA, bufB, npen, tws, rows);
+    default: return fft_inverse_rows_lg<T, 12>(bufA, bufB, npen, tws, rows);
   }
 }
 
@@ -1098,8 +1139,13 @@ __device__ __forceinline__ void phase_rows_inv(const GridDesc& g, const Bins& b,
   }
   copy_to_shared(tws, tw, fft_tw_count(n));
   __syncthreads();
-  C* res = fft_run<T, true>(bufA, bufB, lg, npen, tws);
   const size_t row0 = ((size_t)z * n + y0) * n;
+  if constexpr (DirectPencils<T>::value) {
+    // the last radix pass writes the rows (it ends with a block barrier)
+    fft_inverse_rows<T, OutT>(bufA, bufB, lg, npen, tws, out + row0);
+    return;
+  }
+  C* res = fft_run<T, true>(bufA, bufB, lg, npen, tws);
   for (int e = tid; e < R * n; e += nt) {
     const int r = e >> lg, x = e & (n - 1);
     const C v = res[(r >> 1) * PS + padi(x)];
