@@ -725,6 +725,8 @@ cudaError_t build_tiles(ibdl_geometry_s* g, int rows, int* start, int* cursor, i
                         int* pts, unsigned char* dz, Bins* out, cudaStream_t st) {
   const GridDesc& gd = g->grid;
   const int n = gd.n;
+  // the x passes index a tile's pencils with shifts
+  if (rows < 2 || (rows & (rows - 1))) return cudaErrorInvalidValue;
   const int ntiles = (n / rows) * (gd.dim == 3 ? n : 1);
   cudaError_t e = launch_bins(gd, g->pd, rows, ntiles, start, cursor, counts, pts, st);
   if (e) return e;

@@ -697,6 +697,7 @@ __device__ __forceinline__ void phase_rows_fwd(const GridDesc& g, const PointDat
   using C = cx_t<T>;
   using S = typename SpreadType<T>::type;  // the spread's precision
   const int n = g.n, lg = g.log2n, mask = n - 1, R = b.rows, npen = R >> 1;
+  const int lgnp = __ffs(npen) - 1;  // R is a power of two (checked when the tiles are built)
   const int PS = pen_stride(n);
   C* bufA = reinterpret_cast<C*>(smem);
   C* bufB = bufA + (size_t)npen * PS;
@@ -724,7 +725,7 @@ __device__ __forceinline__ void phase_rows_fwd(const GridDesc& g, const PointDat
       zero.x = 0;
       zero.y = 0;
       for (int e = tid; e < (half + 1) * R; e += nt) {
-        const int k = e / R, a = e - k * R;
+        const int k = e >> (lgnp + 1), a = e & (R - 1);
         spec[(size_t)k * slab + pos0 + a] = zero;
       }
     }
@@ -846,7 +847,7 @@ __device__ __forceinline__ void phase_rows_fwd(const GridDesc& g, const PointDat
   C* res = fft_run<T, false>(bufA, bufB, lg, npen, tws);
 
   for (int e = tid; e < (half + 1) * npen; e += nt) {
-    const int k = e / npen, a = e - k * npen;
+    const int k = e >> lgnp, a = e & (npen - 1);
     const C zk = res[a * PS + padi(k)];
     const C zm = res[a * PS + padi((n - k) & mask)];
     C A, B;
@@ -1088,6 +1089,7 @@ __device__ __forceinline__ void phase_rows_inv(const GridDesc& g, const Bins& b,
   if (band_only && b.start[tile] == b.start[tile + 1]) return;
   using C = cx_t<T>;
   const int n = g.n, lg = g.log2n, R = b.rows, npen = R >> 1;
+  const int lgnp = __ffs(npen) - 1;  // R is a power of two (checked when the tiles are built)
   const int PS = pen_stride(n);
   C* bufA = reinterpret_cast<C*>(smem);
   C* bufB = bufA + (size_t)npen * PS;
@@ -1108,7 +1110,7 @@ __device__ __forceinline__ void phase_rows_inv(const GridDesc& g, const Bins& b,
     for (int u = 0; u < U; ++u) {
       const int e = e0 + u * nt;
       if (e < total) {
-        const int k = e / npen, a = e - k * npen;
+        const int k = e >> lgnp, a = e & (npen - 1);
         Pair<T> pr;
         pr.load(spec + (size_t)k * slab + pos0 + 2 * a);
         A[u] = pr.a;
@@ -1119,7 +1121,7 @@ __device__ __forceinline__ void phase_rows_inv(const GridDesc& g, const Bins& b,
     for (int u = 0; u < U; ++u) {
       const int e = e0 + u * nt;
       if (e < total) {
-        const int k = e / npen, a = e - k * npen;
+        const int k = e >> lgnp, a = e & (npen - 1);
         C Au = A[u], Bu = B[u];
         if (k == 0 || k == half) {
           Au.y = 0;
