@@ -511,7 +511,7 @@ FP64_PEAK_TFLOPS = 1.25
 
 # DRAM bytes (read + write) of one batched-pair launch of the persistent
 # solver, from one ncu capture of that launch (profiles/c2_persistent_solve.md)
-PAIR_LAUNCH_DRAM_BYTES = (42.406144 + 186.939136) * 1e6
+PAIR_LAUNCH_DRAM_BYTES = (59.424 + 178.529536) * 1e6
 
 
 # ---------------------------------------------------------------------------
