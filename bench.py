@@ -450,7 +450,7 @@ def matvec_bytes(n, m, prec):
                for k in ("rows_fwd", "solve", "rows_inv", "interp"))
 
 
-def survey_matvec_bytes(dim, n, m, p):
+def model_matvec_bytes(dim, n, m, p):
     """Algorithmic bytes of one matvec, the fixed model
     B = 9 p N^d + p M (4^d + 2d + 4): one grid write by the spread, two
     read+write passes per transform, the taps and point I/O."""
@@ -484,7 +484,7 @@ def run_matvec_roofline(pkg, peaks, reps=30):
                 ev.append((a, c))
             torch.cuda.synchronize()
             us = float(np.median([a.elapsed_time(c) for a, c in ev])) * 1e3
-            B = survey_matvec_bytes(prob.geom.dim, prob.geom.n, prob.geom.m, p)
+            B = model_matvec_bytes(prob.geom.dim, prob.geom.n, prob.geom.m, p)
             gbs = B / (us * 1e-6) / 1e9
             out[f"{name}-{tag}"] = {"us_median": us, "algorithmic_bytes": B,
                                     "achieved_gbs": gbs, "peak_gbs": peaks["hbm_gbs"],

@@ -65,7 +65,7 @@ typedef enum {
   IBDL_ERR_BREAKDOWN = 5,     /* Arnoldi produced a zero or non-finite norm */
   IBDL_ERR_NONFINITE = 6,     /* NaN/Inf in inputs or in the residual */
   IBDL_ERR_TIMEOUT = 7,       /* a bounded device wait gave up */
-  IBDL_ERR_UNSUPPORTED = 8    /* valid request this build does not support */
+  IBDL_ERR_UNSUPPORTED = 8    /* valid request the library does not support */
 } ibdl_status;
 
 typedef enum { IBDL_DIRICHLET = 0, IBDL_NEUMANN = 1 } ibdl_bc;
