@@ -73,3 +73,17 @@ def test_missing_3d_arrays_rejected(lib):
         ibdl.Geometry(**_desc_args(dim=3, n=32))
     assert e.value.status == ibdl.ERR_INVALID_ARG
     assert "NULL" in str(e.value)
+
+
+@pytest.mark.parametrize("args", [
+    (4, 64, 0, 8), (1, 64, 0, 8), (2, 100, 0, 8), (2, 8, 0, 2), (2, 8192, 0, 2),
+    (2, 64, 2, 8), (2, 64, -1, 8), (2, 64, 0, 6), (2, 64, 0, 32), (2, 64, 0, -2),
+    (2, 64, 0, 1), (2, 1024, 1, 8), (3, 32, 0, 16), (3, 256, 0, 64),
+])
+def test_inadmissible_tiling_pins_are_rejected(lib, args):
+    """ibdl_tuning_set checks dim, n, precision and the tiling (an even power
+    of two R with n/R >= 4, R <= n - 5, float64 row tiles within 100 KB)
+    before it reads the device."""
+    with pytest.raises(ibdl.IbdlError) as e:
+        ibdl.tuning_set(*args)
+    assert e.value.status == ibdl.ERR_INVALID_ARG
