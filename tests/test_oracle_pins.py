@@ -488,6 +488,34 @@ def test_chord_projection_is_the_orthogonal_foot():
     assert abs(O._chord_t(p, x1, x2) - 0.3) < 1e-15
 
 
+def test_triangle_foot_barycentrics():
+    """The 3D x_A: barycentric coordinates of the orthogonal foot of p on the
+    plane of the triangle, clamped to >= 0 and renormalised.  Checked
+    against the foot from a least-squares solve on the edge vectors (a
+    swapped Gram entry or sign would move it) and by orthogonality of p
+    minus the foot when it lies inside; a degenerate triangle gives None."""
+    rng = np.random.default_rng(21)
+    inside = outside = 0
+    for _ in range(400):
+        a, b, c = rng.standard_normal((3, 3))
+        p = rng.standard_normal(3)
+        lam = O._barycentric_clamped(p, a, b, c)
+        (l2, l3), *_ = np.linalg.lstsq(np.stack([b - a, c - a], axis=1), p - a, rcond=None)
+        exact = np.array([1.0 - l2 - l3, l2, l3])
+        clamped = np.maximum(exact, 0.0)
+        assert np.allclose(lam, clamped / clamped.sum(), atol=1e-9)
+        assert abs(sum(lam) - 1.0) < 1e-14 and min(lam) >= 0.0
+        if exact.min() > 0:
+            inside += 1
+            foot = lam[0] * a + lam[1] * b + lam[2] * c
+            assert abs(np.dot(p - foot, b - a)) < 1e-9 and abs(np.dot(p - foot, c - a)) < 1e-9
+        else:
+            outside += 1
+    assert inside > 20 and outside > 20
+    a = np.array([0.1, 0.2, 0.3])
+    assert O._barycentric_clamped(a + 1.0, a, a + 0.5, a + 2.0) is None  # collinear
+
+
 def _nearest_dist(g):
     P = configs.grid_nodes(g)
     d2 = ((P[:, None, :] - g.X[None, :, :]) ** 2).sum(-1)
