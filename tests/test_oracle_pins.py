@@ -588,6 +588,39 @@ def test_spectral_derivative_of_the_nyquist_mode_is_zero():
     assert np.max(np.abs(O.spectral_derivative(box, g, 0))) == 0.0
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_spectral_spread_div_against_the_analytic_gradient(dim):
+    """S~ with the spectral divergence is minus the adjoint of the gradient:
+    for a grid Fourier mode phi, h^d sum_j (S~Q)_j phi_j
+    = -sum_i Q_i w_i n_i . (S* grad phi)_i with grad phi sampled from the
+    analytic derivative (the spectral derivative is exact on the mode and
+    skew; S and S* are adjoint).  A wrong sign, 2 pi / L scale or axis of
+    the derivative fails it."""
+    rng = np.random.default_rng(31 + dim)
+    n, L = (32 if dim == 2 else 16), 1.7
+    origin = rng.uniform(-1, 1, dim)
+    box = O.Box(dim, n, L, origin)
+    M = 30
+    X = origin + rng.uniform(0, L, (M, dim))
+    nrm = rng.standard_normal((M, dim))
+    nrm /= np.linalg.norm(nrm, axis=1)[:, None]
+    w = rng.uniform(0.5, 2, M)
+    Q = rng.standard_normal(M)
+    # node coordinates, x fastest (numpy axis d - 1 - c holds direction c)
+    idx = np.indices(box.shape)
+    xs = [origin[c] + box.h * idx[box.axis(c)] for c in range(dim)]
+    f = O.spread_div_spectral(box, X, nrm, w, Q)
+    for kvec, theta in (((3, -5, 2)[:dim], 0.4), ((-7, 1, 6)[:dim], -1.1)):
+        arg = sum(2 * np.pi * kvec[c] * (xs[c] - origin[c]) / L for c in range(dim)) + theta
+        phi = np.cos(arg)
+        lhs = np.sum(f * phi) * box.h ** dim
+        rhs = 0.0
+        for c in range(dim):
+            dphi = -(2 * np.pi * kvec[c] / L) * np.sin(arg)
+            rhs -= np.sum(Q * w * nrm[:, c] * O.interp(box, X, dphi))
+        assert abs(lhs - rhs) <= 1e-11 * (abs(lhs) + 1.0), (lhs, rhs)
+
+
 @pytest.mark.parametrize("kappa", [1e-2, np.inf])
 def test_spectral_solve_closed_form(kappa):
     """kappa L'^{-1} of a Fourier mode: kappa / (1 + kappa |2 pi k / L|^2)
