@@ -46,8 +46,6 @@ def parse():
     ap.add_argument("--impl", default="ibdl", choices=["ibdl", "reference"])
     ap.add_argument("--precision", default="fp32-refined", choices=["fp32-refined", "fp64"])
     ap.add_argument("--tol", type=float, default=1e-8)
-    ap.add_argument("--cpu-seconds", type=float, default=12.0,
-                    help="CPU work budget of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="batched", choices=["batched", "solo"],
                     help="batched: each step solves the Dirichlet + Neumann pair in one "
@@ -58,8 +56,22 @@ def parse():
                     help="skip the matvec HBM-roofline measurement")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 256-instance batched measurement")
-    ap.add_argument("--serve-requests", type=int, default=200,
-                    help="requests of the mixed serving stream (0: skip it)")
+    ap.add_argument("--serve-requests", type=int, default=2000,
+                    help="requests of the mixed serving stream per offered rate (0: skip it)")
+    ap.add_argument("--no-c1", action="store_true", help="skip the C1 latency row")
+    ap.add_argument("--profile-case", default=None,
+                    choices=["matvec-c2-f32", "matvec-c2-f64", "matvec-c2-dd",
+                             "matvec-c3-f32", "matvec-c3-f64", "matvec-c3-dd",
+                             "solve-c2", "pair-c2"],
+                    help="run one small fixed workload for a profiler (ncu) and exit: "
+                         "matvecs of the 2D star (c2) or the 3D sphere (c3) in float32, "
+                         "float64 or with double-float transforms, float32-refined c2 "
+                         "solves, or the benchmark's batched c2 pair")
+    ap.add_argument("--reps", type=int, default=None,
+                    help="--profile-case: repetitions (matvec 5, solve/pair 2)")
+    ap.add_argument("--rows", type=int, default=None,
+                    help="--profile-case: pin the x-pass tiling (rows per tile); the "
+                         "autotuner's timings are distorted under a profiler")
     return ap.parse_args()
 
 
@@ -76,31 +88,31 @@ def combine_ranks(local_ms, local_solves, dist=None, device=None):
     return float(t.item()), int(s.item())
 
 
-def run_serving(pkg, nreq, seed=3, rate=2000.0, budget=120 << 30):
-    """Replay the seeded mixed serving stream (Poisson arrivals) in real time
+def run_serving(pkg, reqs, rate, precision, base_rate=2000.0, budget=120 << 30):
+    """Replay the seeded mixed serving stream (Poisson arrivals generated at
+    `base_rate`, their times scaled to the offered `rate`) in real time
     through the continuous-batching server; latency = arrival -> result."""
     import torch
-    from paper_2203_12126_gb300 import ibdl
-    reqs = configs.c5_requests(nreq, seed=seed, rate=rate)
     free, _ = torch.cuda.mem_get_info()
     budget = int(min(budget, 0.8 * free))
     srv = pkg.Server(memory_budget=budget, max_active=64, rounds_per_step=4, reserve_sms=8,
                      tol=1e-8)
+    scale = base_rate / rate
     t0 = srv.clock() + 0.02
     nxt = 0
     outstanding = {}
     recs = []
     while nxt < len(reqs) or outstanding:
         now = srv.clock()
-        while nxt < len(reqs) and t0 + reqs[nxt].t <= now:
+        while nxt < len(reqs) and t0 + reqs[nxt].t * scale <= now:
             r = reqs[nxt]
             rid = srv.submit(r.problem.geom, r.problem.bdata, bc=r.problem.bc,
-                             precision=ibdl.FP32_REFINED, t_arrival=t0 + r.t)
+                             precision=precision, t_arrival=t0 + r.t * scale)
             outstanding[rid] = r
             nxt += 1
         st = srv.stats()
         if st["active"] == 0 and st["queued"] == 0 and nxt < len(reqs):
-            time.sleep(max(0.0, t0 + reqs[nxt].t - srv.clock()))
+            time.sleep(max(0.0, t0 + reqs[nxt].t * scale - srv.clock()))
             continue
         for rid in srv.step():
             r = outstanding.pop(rid)
@@ -110,33 +122,58 @@ def run_serving(pkg, nreq, seed=3, rate=2000.0, budget=120 << 30):
     stats = srv.stats()
     srv.close()
     lat = np.array([(x["t_done"] - x["t_arrival"]) * 1e3 for x in recs])
+    qwait = np.array([(x["t_admit"] - x["t_arrival"]) * 1e3 for x in recs])
+    insvc = np.array([(x["t_done"] - x["t_admit"]) * 1e3 for x in recs])
     span = max(x["t_done"] for x in recs) - t0
     ok = [x for x in recs if x["status"] == 0]
     kinds = {}
     for x in recs:
         k = x["kind"].rsplit("-", 1)[0]
         kinds.setdefault(k, []).append((x["t_done"] - x["t_arrival"]) * 1e3)
+    pct = (lambda a: {"p50": float(np.percentile(a, 50)), "p99": float(np.percentile(a, 99))})
     return {
-        "workload": f"mixed stream, {nreq} requests, Poisson {rate:g}/s (seed {seed}): 80% 2D "
-                    "stars N in {256,512,1024}^2, 20% 3D spheres/ellipsoids N in "
-                    "{64,128,256}^3, kappa log-U[1e-4,1e-1], Dirichlet/Neumann 50/50, "
-                    "float32-refined, tol 1e-8",
-        "requests": nreq, "completed_ok": len(ok),
+        "offered_rate_per_s": rate, "requests": len(reqs), "completed_ok": len(ok),
         "solves_per_s": len(ok) / span,
-        "latency_ms": {"p50": float(np.percentile(lat, 50)),
-                       "p99": float(np.percentile(lat, 99)),
-                       "max": float(lat.max())},
+        "latency_ms": {**pct(lat), "max": float(lat.max())},
+        "queue_wait_ms": pct(qwait), "in_service_ms": pct(insvc),
         "latency_p50_ms_by_kind": {k: float(np.median(v)) for k, v in sorted(kinds.items())},
         "max_rel_residual": float(max(x["rel_residual"] for x in ok)) if ok else None,
         "memory_budget_bytes": budget, "peak_device_bytes": int(stats["peak_bytes"]),
         "slices": int(stats["launches"]),
         "host_admit_s": float(stats["admit_seconds"]),
         "host_wait_for_gpu_s": float(stats["wait_seconds"]),
-        "queue_wait_ms_p50": float(np.median([(x["t_admit"] - x["t_arrival"]) * 1e3
-                                              for x in recs])),
-        "in_service_ms_p50": float(np.median([(x["t_done"] - x["t_admit"]) * 1e3
-                                              for x in recs])),
-        "offered_span_s": float(reqs[-1].t), "makespan_s": float(span),
+        "offered_span_s": float(reqs[-1].t * scale), "makespan_s": float(span),
+    }
+
+
+def run_serving_sweep(pkg, nreq, seed=3, base_rate=2000.0):
+    """The C5 stream (`nreq` requests, seed 3) offered at the specified
+    2000/s (above one GPU's capacity: a saturated queue, which measures the
+    capacity), then at 80% and 50% of the capacity that run measured (the
+    steady states), float32-refined; and the same stream offered at 2000/s
+    to plain float64 solves (the same tolerance), for the refined-vs-float64
+    serving comparison."""
+    from paper_2203_12126_gb300 import ibdl
+    t = time.perf_counter()
+    reqs = configs.c5_requests(nreq, seed=seed, rate=base_rate)
+    gen_s = time.perf_counter() - t
+    sat = run_serving(pkg, reqs, base_rate, ibdl.FP32_REFINED, base_rate)
+    cap = sat["solves_per_s"]
+    rows = {"saturated_2000_per_s": sat}
+    for frac in (0.8, 0.5):
+        rows[f"steady_{int(frac * 100)}pct_of_capacity"] = run_serving(
+            pkg, reqs, frac * cap, ibdl.FP32_REFINED, base_rate)
+    f64 = run_serving(pkg, reqs, base_rate, ibdl.FP64, base_rate)
+    return {
+        "workload": f"mixed stream, {nreq} requests, Poisson arrivals (seed {seed}): 80% 2D "
+                    "stars N in {256,512,1024}^2, 20% 3D spheres/ellipsoids N in "
+                    "{64,128,256}^3, kappa log-U[1e-4,1e-1], Dirichlet/Neumann 50/50, "
+                    "tol 1e-8; the same requests at every offered rate",
+        "capacity_solves_per_s": cap,
+        "float32_refined": rows,
+        "float64_saturated_2000_per_s": f64,
+        "refined_over_float64_capacity": cap / f64["solves_per_s"],
+        "request_generation_s": gen_s,
     }
 
 
@@ -179,6 +216,71 @@ def run_c3_solve(pkg, reps=3):
             "refine_steps": info["refine_steps"], "rel_residual": info["rel_residual"],
             "rel_err_vs_fp64_1e-12": float(torch.linalg.norm(q - q64) / torch.linalg.norm(q64)),
             "fp64_solve_ms": fp64_ms, "fp64_iters": i64["iters"], "rows_per_tile": rows}
+
+
+def run_c1(pkg, solos=200, count=64, reps=5):
+    """C1: the plain float64 Dirichlet solve of the Sec. 6.1 circle shape
+    (N=128^2, r=0.3, M=242, cosine delta, kappa=1e-2, modified-Bessel data)
+    at tol 1e-10: single-solve latency over `solos` event-timed solves
+    (one persistent launch each, L2 flushed between), and throughput of
+    `count` copies solved in one batched launch; error against the dense-LU
+    density of the oracle."""
+    import torch
+    from oracle import ibdl_oracle as O
+    from paper_2203_12126_gb300 import ibdl
+    dev = torch.device("cuda", torch.cuda.current_device())
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    p = configs.c1()
+    g = pkg.Geometry.from_workload(p.geom, bc=p.bc, precision=ibdl.FP64)
+    b = torch.tensor(p.bdata, dtype=torch.float64, device=dev)
+    q = torch.zeros_like(b)
+    info = {}
+
+    def one():
+        info.update(g.solve(b, q, tol=1e-10))
+    for _ in range(5):
+        one()
+    lat = []
+    for _ in range(solos):
+        flush.fill_(5.0)
+        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        one()
+        c.record()
+        torch.cuda.synchronize()
+        lat.append(a.elapsed_time(c))
+    qstar = O.solve_dense(p.geom, p.bc, p.bdata)
+    err = float(np.linalg.norm(q.cpu().numpy() - qstar) / np.linalg.norm(qstar))
+    gs = [pkg.Geometry.from_workload(p.geom, bc=p.bc, precision=ibdl.FP64) for _ in range(count)]
+    bs = [b] * count
+    qs = [torch.zeros_like(b) for _ in range(count)]
+    batch = ibdl.Batch(count)
+    batch.solve(gs, bs, qs, tol=1e-10)
+    ms = []
+    for _ in range(reps):
+        flush.fill_(6.0)
+        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        infos = batch.solve(gs, bs, qs, tol=1e-10)
+        c.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(c))
+    berr = max(float(np.linalg.norm(x.cpu().numpy() - qstar) / np.linalg.norm(qstar)) for x in qs)
+    batch.close()
+    for gg in gs:
+        gg.close()
+    g.close()
+    med = float(np.median(ms))
+    return {"workload": "circle r=0.3, N=128^2, M=242, cos4 delta, kappa=1e-2, Dirichlet "
+                        "I_2 data, float64, tol 1e-10",
+            "solo": {"solves": solos, "solves_per_s": solos / (sum(lat) / 1e3),
+                     "latency_ms": {"p50": float(np.percentile(lat, 50)),
+                                    "p99": float(np.percentile(lat, 99))},
+                     "iters": info["iters"], "rel_err_vs_dense_lu": err},
+            "batched": {"instances": count, "launch_ms": med,
+                        "solves_per_s": count / (med / 1e3),
+                        "all_ok": all(f["status"] == 0 for f in infos),
+                        "max_rel_err_vs_dense_lu": berr}}
 
 
 def run_batched_c4(pkg, count=256, reps=5):
@@ -357,6 +459,60 @@ def problems():
     return [configs.c2(bc=configs.DIRICHLET), configs.c2(bc=configs.NEUMANN)]
 
 
+def run_profile_case(args):
+    """One small fixed workload for a profiler, then exit (no timing, no JSON
+    line): ``matvec-<c2|c3>-<f32|f64|dd>`` applies the boundary operator of
+    the 2D star (N=1024^2, M=3525) or the 3D sphere (N=256^3, M=38039)
+    ``--reps`` times (default 5); ``solve-c2`` runs float32-refined Dirichlet
+    solves of the star at tol 1e-8 (default 2); ``pair-c2`` runs the
+    benchmark's step, the Dirichlet + Neumann pair in one batched launch
+    (default 2).  ``--rows`` pins the x-pass tiling."""
+    import torch
+    import paper_2203_12126_gb300 as pkg
+    from paper_2203_12126_gb300 import ibdl
+    pkg.load()
+    dev = torch.device("cuda:0")
+    what = args.profile_case
+    if what.startswith("matvec"):
+        _, case, tag = what.split("-")
+        prob = configs.c3() if case == "c3" else configs.c2()
+        prec = {"f32": ibdl.FP32_REFINED, "f64": ibdl.FP64, "dd": 2}[tag]
+        reps = args.reps or 5
+        if args.rows:
+            ibdl.tuning_set(prob.geom.dim, prob.geom.n, min(prec, 1), args.rows)
+        g = pkg.Geometry.from_workload(prob.geom, bc=prob.bc, precision=min(prec, 1))
+        q = torch.tensor(np.random.default_rng(0).standard_normal(prob.geom.m), device=dev)
+        y = torch.empty_like(q)
+        for _ in range(reps):
+            g.apply(q, y, precision=prec)
+        torch.cuda.synchronize()
+        print(f"{what} x{reps}: |y| = {float(y.norm()):.6e}")
+        g.close()
+        return 0
+    reps = args.reps or 2
+    probs = [configs.c2(bc=configs.DIRICHLET)] if what == "solve-c2" else problems()
+    if args.rows:
+        ibdl.tuning_set(2, probs[0].geom.n, ibdl.FP32_REFINED, args.rows)
+    gs = [pkg.Geometry.from_workload(p.geom, bc=p.bc, precision=ibdl.FP32_REFINED)
+          for p in probs]
+    bs = [torch.tensor(p.bdata, device=dev) for p in probs]
+    qs = [torch.empty_like(b) for b in bs]
+    if what == "solve-c2":
+        for _ in range(reps):
+            info = gs[0].solve(bs[0], qs[0], tol=1e-8)
+        print(f"{what} x{reps}: iters {info['iters']} rel_res {info['rel_residual']:.2e}")
+    else:
+        batch = ibdl.Batch(len(gs))
+        for _ in range(reps):
+            infos = batch.solve(gs, bs, qs, tol=1e-8)
+        print(f"{what} x{reps}: iters {[f['iters'] for f in infos]}")
+        batch.close()
+    torch.cuda.synchronize()
+    for g in gs:
+        g.close()
+    return 0
+
+
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
@@ -439,17 +595,6 @@ def kernel_model(name, n, m):
     return None
 
 
-def matvec_flops(n, m, prec):
-    sfx = "_f64" if prec == 64 else "_f32"
-    return sum(kernel_model(k + sfx, n, m)["flops"] for k in ("rows_fwd", "solve", "rows_inv"))
-
-
-def matvec_bytes(n, m, prec):
-    sfx = "_f64" if prec == 64 else "_f32"
-    return sum(kernel_model(k + sfx, n, m)["bytes"]
-               for k in ("rows_fwd", "solve", "rows_inv", "interp"))
-
-
 def model_matvec_bytes(dim, n, m, p):
     """Algorithmic bytes of one matvec, the fixed model
     B = 9 p N^d + p M (4^d + 2d + 4): one grid write by the spread, two
@@ -458,9 +603,12 @@ def model_matvec_bytes(dim, n, m, p):
 
 
 def run_matvec_roofline(pkg, peaks, reps=30):
-    """Event-timed matvecs (float32 and float64) on the 3D 256^3 sphere (the
-    HBM-bound case) and the 2D 1024^2 star, L2 flushed between launches."""
+    """Event-timed matvecs (float32, float64, and float64 with double-float
+    transforms) on the 3D 256^3 sphere (the HBM-bound case) and the 2D
+    1024^2 star, L2 flushed between launches; then one profiled pass that
+    splits each matvec into its kernels (library event pairs)."""
     import torch
+    from paper_2203_12126_gb300 import ibdl
     dev = torch.device("cuda", torch.cuda.current_device())
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     out = {}
@@ -470,7 +618,7 @@ def run_matvec_roofline(pkg, peaks, reps=30):
         q = torch.tensor(np.random.default_rng(0).standard_normal(prob.geom.m),
                          dtype=torch.float64, device=dev)
         y = torch.empty_like(q)
-        for prec, tag, p in ((1, "f32", 4), (0, "f64", 8)):
+        for prec, tag, p in ((1, "f32", 4), (0, "f64", 8), (2, "dd", 8)):
             for _ in range(3):
                 g.apply(q, y, precision=prec)
             ev = []
@@ -486,10 +634,22 @@ def run_matvec_roofline(pkg, peaks, reps=30):
             us = float(np.median([a.elapsed_time(c) for a, c in ev])) * 1e3
             B = model_matvec_bytes(prob.geom.dim, prob.geom.n, prob.geom.m, p)
             gbs = B / (us * 1e-6) / 1e9
+            # per-kernel split of the same matvec (event pairs around each
+            # launch; a few microseconds of event overhead per launch)
+            ibdl.profile_enable(True)
+            ibdl.profile_read(reset=True)
+            for _ in range(5):
+                flush.fill_(2.0)
+                g.apply(q, y, precision=prec)
+            st = ibdl.profile_read(reset=True)
+            ibdl.profile_enable(False)
+            split = {k: v[1] / v[0] * 1e3 for k, v in sorted(st.items())
+                     if not k.startswith("phase:")}
             out[f"{name}-{tag}"] = {"us_median": us, "algorithmic_bytes": B,
                                     "achieved_gbs": gbs, "peak_gbs": peaks["hbm_gbs"],
                                     "frac_of_hbm": gbs / peaks["hbm_gbs"],
                                     "peak_src": peaks["src"],
+                                    "kernel_us": split,
                                     "rows_per_tile": g.info()["rows_per_tile"]}
         g.close()
     return out
@@ -505,13 +665,13 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "src": "fallback"}
 
 
-# Nominal GB300 FP64 rate (the recipe's figure); the FP64 FFT passes are
-# bound by it, not by HBM.
-FP64_PEAK_TFLOPS = 1.25
-
 # DRAM bytes (read + write) of one batched-pair launch of the persistent
-# solver, from one ncu capture of that launch (profiles/c2_persistent_solve.md)
-PAIR_LAUNCH_DRAM_BYTES = (59.424 + 178.529536) * 1e6
+# solver, from one ncu capture of that launch, or None when the solver kernel
+# has changed since the capture
+PAIR_LAUNCH_DRAM_BYTES = None
+PAIR_LAUNCH_DRAM_SRC = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one pair launch "
+                        "(profiles/c2_persistent_solve.md); null: the kernel changed since "
+                        "the last capture")
 
 
 # ---------------------------------------------------------------------------
@@ -534,6 +694,73 @@ def oracle_sample(probs, tol, budget_s):
             break
     el = time.perf_counter() - t0
     return done, el, iters, sols
+
+
+def _oracle_worker(args):
+    """One spawned worker of the all-cores baseline: `rounds` rounds of one
+    Dirichlet + one Neumann oracle solve; returns the seconds of each round."""
+    tol, rounds = args
+    probs = problems()
+    from oracle import ibdl_oracle as O
+    out = []
+    for _ in range(rounds):
+        t = time.perf_counter()
+        for p in probs:
+            O.solve(p.geom, p.bc, p.bdata, tol=tol)
+        out.append(time.perf_counter() - t)
+    return out
+
+
+def cpu_baseline(probs, tol, samples=5):
+    """The oracle as it stands on this host's cores: single thread (median
+    of `samples` rounds of one Dirichlet + one Neumann solve, plus the
+    per-matvec time) and all cores (one spawned process per core, each
+    solving pairs; throughput = solves of a round / its slowest worker,
+    median of `samples` rounds after a warm-up round)."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    from oracle import ibdl_oracle as O
+    t_all = time.perf_counter()
+    pair_s, x0 = [], None
+    for _ in range(samples):
+        t = time.perf_counter()
+        for k, p in enumerate(probs):
+            r = O.solve(p.geom, p.bc, p.bdata, tol=tol)
+            if k == 0:
+                x0 = r.x
+        pair_s.append(time.perf_counter() - t)
+    op = O.Operator(probs[0].geom, probs[0].bc)
+    qv = np.random.default_rng(0).standard_normal(probs[0].geom.m)
+    mv_s = []
+    for _ in range(samples):
+        t = time.perf_counter()
+        op.apply(qv)
+        mv_s.append(time.perf_counter() - t)
+    one = {"solves_per_s": len(probs) / statistics.median(pair_s),
+           "matvecs_per_s": 1.0 / statistics.median(mv_s),
+           "matvec_ms": statistics.median(mv_s) * 1e3, "cores": 1}
+    cores = os.cpu_count() or 1
+    env_keep = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",
+                                               "MKL_NUM_THREADS")}
+    for k in env_keep:
+        os.environ[k] = "1"      # one thread per worker process
+    try:
+        with ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as ex:
+            res = list(ex.map(_oracle_worker, [(tol, samples + 1)] * cores))
+    finally:
+        for k, v in env_keep.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    rounds = [max(r[i] for r in res) for i in range(1, samples + 1)]  # skip the warm-up
+    allc = {"solves_per_s": cores * len(probs) / statistics.median(rounds), "cores": cores}
+    return {"value": allc["solves_per_s"], "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"all {cores} host cores: one spawned process per core, each solving "
+                      f"{samples} + 1 Dirichlet+Neumann pairs (tol {tol:g}); value = median "
+                      f"round throughput; single thread: median of {samples} pairs",
+            "single_thread": one, "all_cores": allc, "nproc": cores,
+            "wall_s": time.perf_counter() - t_all, "_x0": x0}
 
 
 def run_reference(args, rank, world):
@@ -582,6 +809,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.profile_case:
+        return run_profile_case(args)
 
     import torch
     import paper_2203_12126_gb300 as pkg
@@ -730,43 +959,37 @@ def main():
         name, (cnt, ms) = dom
         avg_s = ms / cnt / 1e3
         if name == "persistent_solve":
-            # one launch = whole solves (per_launch of them): its binding
-            # resource is the FP64 pipe of the float64 FFT passes
+            # one launch = whole solves (per_launch of them).  The matvec
+            # byte model B = 9 p N^d + p M (4^d + 2d + 4) per field solve:
+            # p = 4 for the float32 Arnoldi matvecs, p = 8 for the
+            # float64-grade ones (the residuals and the Neumann right-hand
+            # side, transformed in double-float)
             mv = float(np.mean([f["matvecs"] for f in pinfos])) * per_launch
             it = float(np.mean([f["iters"] for f in pinfos])) * per_launch
             mv64 = (mv - it) if prec == ibdl.FP32_REFINED else mv
             mv32 = it if prec == ibdl.FP32_REFINED else 0.0
             # the Neumann right-hand side is one more float64-grade field solve
             mv64 += per_launch * sum(p.bc == configs.NEUMANN for p in probs) / len(probs)
-            fl = mv64 * matvec_flops(n, m, 64)
-            ach = fl / avg_s / 1e12
-            roofline = {"kernel": name, "bound": "alu", "achieved": ach,
-                        "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                        "frac": ach / FP64_PEAK_TFLOPS,
+            B = (mv64 * model_matvec_bytes(2, n, m, 8) + mv32 * model_matvec_bytes(2, n, m, 4))
+            ach = B / avg_s / 1e9
+            roofline = {"kernel": name, "bound": "hbm", "achieved": ach,
+                        "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": ach / peaks["hbm_gbs"],
+                        "peak_src": peaks["src"] + " (STREAM-style copy, MEASURED_PEAKS.json)",
                         "traffic": PAIR_LAUNCH_DRAM_BYTES if args.mode == "batched" else None,
-                        "traffic_src": "ncu dram__bytes_read.sum + dram__bytes_write.sum of "
-                                       "one pair launch (profiles/c2_persistent_solve.md)",
-                        "peak_src": "nominal GB300 FP64 rate (measured FMA probe: 1.19); "
-                                    "in the float32-refined launch the float64-grade "
-                                    "transforms run in double-float on the float32 pipes, "
-                                    "so `achieved` is an FP64-equivalent rate",
-                        "algorithmic_flops_per_launch": fl,
+                        "traffic_src": PAIR_LAUNCH_DRAM_SRC,
+                        "algorithmic_bytes_per_launch": B,
+                        "byte_model": "9 p N^d + p M (4^d + 2d + 4) per field solve, "
+                                      "p = 4 (float32 matvec) or 8 (float64-grade)",
                         "float64_grade_field_solves_per_launch": mv64,
                         "float32_matvecs_per_launch": mv32,
-                        "algorithmic_bytes_per_launch":
-                            mv64 * matvec_bytes(n, m, 64) + mv32 * matvec_bytes(n, m, 32),
-                        "avg_launch_us": avg_s * 1e6}
+                        "avg_launch_us": avg_s * 1e6,
+                        "l2_resident": "the working set of the pair (about 40 MB) fits the "
+                                       "129 MB L2; L2 is flushed between launches, so the "
+                                       "first touch of each buffer per launch comes from HBM"}
         else:
             model = kernel_model(name, n, m)
-            if model is not None and name.endswith("f64"):
-                ach = model["flops"] / avg_s / 1e12
-                roofline = {"kernel": name, "bound": "alu", "achieved": ach,
-                            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                            "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                            "peak_src": "nominal GB300 FP64 rate",
-                            "algorithmic_flops": model["flops"],
-                            "avg_launch_us": avg_s * 1e6}
-            elif model is not None:
+            if model is not None:
                 ach = model["bytes"] / avg_s / 1e9
                 roofline = {"kernel": name, "bound": "hbm", "achieved": ach,
                             "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -778,43 +1001,49 @@ def main():
     hb = [torch.tensor(p.bdata, dtype=torch.float64).pin_memory() for p in probs]
     hq = [torch.zeros(p.geom.m, dtype=torch.float64).pin_memory() for p in probs]
     e2e_steps = max(3, args.steps // 2)
-    t0 = time.perf_counter()
+    e2e_s = 0.0
     for _ in range(e2e_steps):
+        # the same L2 state as the device-timed steps: flushed before each
+        # step, outside the host timer
+        flush.fill_(7.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         if args.mode == "batched":
             batch.solve(geoms, hb, hq, tol=args.tol)
         else:
             for i in range(len(probs)):
                 solve(i, hb[i], hq[i])
-    e2e_s = time.perf_counter() - t0
+        e2e_s += time.perf_counter() - t0
     e2e = {"value": e2e_steps * len(probs) * world / e2e_s, "unit": "solves/s",
            "h2d_bytes_per_step": int(sum(8 * p.geom.m for p in probs)),
            "d2h_bytes_per_step": int(sum(8 * p.geom.m for p in probs)),
            "note": ("ibdl_solve_batched" if args.mode == "batched" else "ibdl_solve") +
                    " with pinned host U_b/V_b in and host Q/U out; copies inside the "
-                   "call; host wall clock"}
+                   "call; host wall clock per step, L2 flushed before each step outside "
+                   "the clock"}
 
     matvec = run_matvec_roofline(pkg, peaks) if not args.no_matvec else None
+    if matvec and roofline:
+        # the single-matvec fractions of the same byte model, per precision
+        roofline["matvec_frac_of_hbm"] = {k: v["frac_of_hbm"] for k, v in matvec.items()}
 
     batched_c4 = run_batched_c4(pkg) if not args.no_batched else None
+    c1 = run_c1(pkg) if not args.no_c1 else None
     c3_solve = run_c3_solve(pkg) if not args.no_matvec else None
     method_rows = run_method_rows(pkg, peaks) if not args.no_matvec else None
 
     serving = None
     if args.serve_requests > 0:
-        serving = run_serving(pkg, args.serve_requests)
+        serving = run_serving_sweep(pkg, args.serve_requests)
 
     out = None
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
-            done, el, citers, sols = oracle_sample(probs, args.tol, args.cpu_seconds)
-            cpu = {"value": done / el, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                   "sample": f"{done} oracle solves (Dirichlet/Neumann alternating, tol "
-                             f"{args.tol:g}) in {el:.1f} s, numpy single thread",
-                   "oracle_iters": citers[:2]}
+            cpu = cpu_baseline(probs, args.tol)
             qd = qs[0].cpu().numpy()
-            cpu["gpu_vs_oracle_rel_diff"] = float(
-                np.linalg.norm(qd - sols[probs[0].name]) / np.linalg.norm(sols[probs[0].name]))
+            ref = cpu.pop("_x0")
+            cpu["gpu_vs_oracle_rel_diff"] = float(np.linalg.norm(qd - ref) / np.linalg.norm(ref))
         iters = [f["iters"] for f in infos]
         mv = [f["matvecs"] for f in infos]
         out = {
@@ -849,6 +1078,7 @@ def main():
             "e2e": e2e,
             "matvec": matvec,
             "batched_c4": batched_c4,
+            "c1": c1,
             "c3_solve": c3_solve,
             "method_rows": method_rows,
             "serving": serving,

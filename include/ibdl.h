@@ -102,8 +102,9 @@ typedef struct ibdl_geometry_s* ibdl_geometry; /* opaque, library-owned */
 /* Geometry of one IBDL problem (Sec. 5.1-5.2).  Copied at creation. */
 typedef struct {
   int32_t dim;          /* 2 or 3 */
-  int32_t n;            /* grid nodes per axis: a power of two, 16..4096 in 2D,
-                           16..512 in 3D */
+  int32_t n;            /* grid nodes per axis: a power of two, 16..2048 in 2D,
+                           16..512 in 3D (larger grids need more shared memory
+                           per float64 FFT item than a block can have) */
   double box_len;       /* L > 0; h = L / n */
   double origin[3];     /* lower box corner; nodes at origin + j h */
   int64_t m;            /* number of boundary points, 1..16776960 */
@@ -426,7 +427,7 @@ ibdl_status ibdl_get_geometry_info(ibdl_geometry g, ibdl_geometry_info* info);
  * used by every later geometry of that kind in the process (a few matvecs
  * once, inside that first ibdl_create_geometry).  Geometries built by the
  * server use a tiling already chosen, else the fixed rule (4 rows in 2D, 2
- * for n = 4096; 8 in 3D).  Off: the fixed rule always.  Results of the two
+ * for n = 2048; 8 in 3D).  Off: the fixed rule always.  Results of the two
  * tilings agree to rounding. */
 void ibdl_tuning_enable(int32_t on);
 
@@ -437,9 +438,28 @@ void ibdl_tuning_enable(int32_t on);
  * reproducible launches (a deployment that fixes its configuration, or a
  * profiler run, under which timing candidates would be distorted).
  * IBDL_ERR_INVALID_ARG unless dim is 2 or 3, n a power of two in
- * [16, 4096], precision a geometry's (IBDL_FP64 or IBDL_FP32_REFINED),
+ * [16, 2048] (2D) / [16, 512] (3D), precision a geometry's (IBDL_FP64 or IBDL_FP32_REFINED),
  * and rows 0 or an admissible tiling (as above); IBDL_ERR_CUDA if the current device cannot be read. */
 ibdl_status ibdl_tuning_set(int32_t dim, int32_t n, int32_t precision, int32_t rows);
+
+/* Shared-memory bookkeeping of the persistent solver's work items (host
+ * only: touches no GPU, so it runs without one).  For a grid (dim, n), an
+ * x-pass tiling of `rows` grid rows per tile (a power of two in [2, n]) and
+ * an element type elem (0 float64, 1 float32, 2 double-float), with n a
+ * power of two in [16, 2048] (2D) / [16, 512] (3D), need_out[0]
+ * receives the dynamic shared memory of one x-pass row tile, need_out[1] of
+ * one item of the solve pencil pass (2D: y pencils; 3D: z pencils) and
+ * need_out[2] of one item of the 3D y pencil passes (0 in 2D); budget_out
+ * the dynamic shared memory a solver launch over such a geometry reserves
+ * (the largest need over the element types the solve can run), and
+ * twiddles_out the entries of the FFT's twiddle table.  Any output may be
+ * NULL.  A launch checks the same figures for every instance before it
+ * starts and returns IBDL_ERR_INVALID_ARG instead of launching when an item
+ * would not fit.  IBDL_ERR_INVALID_ARG for unsupported sizes.  No passage of
+ * the paper: this is the library's own resource accounting. */
+ibdl_status ibdl_solver_smem_query(int32_t dim, int32_t n, int32_t rows, int32_t elem,
+                                   int64_t need_out[3], int64_t* budget_out,
+                                   int32_t* twiddles_out);
 
 /* Number of this library's kernels launched so far in this process
  * (all handles, all streams). */
@@ -464,27 +484,32 @@ typedef struct {
 int32_t ibdl_profile_read(ibdl_kernel_stat* out, int32_t max_out, int32_t reset);
 
 /* Allocation-free variant of ibdl_helmholtz for callers that cannot
- * allocate device memory (for example code running inside a host callback
- * or a plugin whose host application owns all device allocations, where a
- * cudaMalloc is forbidden or would deadlock).  The paper has no counterpart:
- * it is a deployment variant of the periodic solve of Sec. 5.1.
+ * allocate device memory: code running inside a host callback or a stream
+ * callback, or a plugin whose host application owns every device
+ * allocation, where a cudaMalloc is forbidden, would deadlock or would grow
+ * a footprint that must stay fixed after start-up.  The paper has no
+ * counterpart.
  *
  * Computes v_out = kappa L'^{-1} f on an n x n periodic grid of spacing
  * h = box_len / n (L' = I - kappa Delta_h, 5-point stencil), float64, exactly
  * as ibdl_helmholtz does, without a geometry handle.  f and v_out are n*n
  * float64 values in DEVICE memory (x fastest) and may alias.  n must be a
- * power of two in [16, 512]; larger n returns IBDL_ERR_INVALID_ARG.
+ * power of two in [16, 512]; larger n returns IBDL_ERR_INVALID_ARG with a
+ * message naming the limit.
  *
  * Scratch: one file-scope __device__ array of about 2.1 MB (a 512 x 512
  * half spectrum, twiddle and symbol tables) that every GPU loading the
- * library holds until the process exits.  The call allocates nothing and
- * calls no allocating routine.  The first call on a device looks up the
- * array's device address with cudaGetSymbolAddress (with that device
- * current); make that first call before any stream capture.  Every call
- * shares the array and rewrites the parts it reads (tables, tile lists,
- * spectrum), so calls that overlap on the GPU -- on different streams or
- * from different host threads -- race and must be serialised by the caller.
- * Asynchronous on `stream`. */
+ * library holds until the process exits.  After the first call on a device
+ * the call allocates nothing and calls no allocating routine.  The FIRST
+ * call on each device is set-up: it looks up the array's device address with
+ * cudaGetSymbolAddress (with that device current), and under CUDA's lazy
+ * module loading it is also the call that loads this part of the library,
+ * which places the static array and the kernels in device memory.  Make that
+ * first call at start-up, where allocation is allowed, and before any stream
+ * capture.  Every call shares the array and rewrites the parts it reads
+ * (tables, tile lists, spectrum), so calls that overlap on the GPU -- on
+ * different streams or from different host threads -- race and must be
+ * serialised by the caller.  Asynchronous on `stream`. */
 ibdl_status ibdl_helmholtz_2d_noalloc(int32_t n, double box_len, double kappa,
                                       const double* f, double* v_out, void* stream);
 

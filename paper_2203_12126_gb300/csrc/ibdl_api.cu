@@ -280,6 +280,7 @@ ibdl_status fft_tables(int n, const typename Cx<T>::type** tw_out, const T** s2_
   auto it = g_tabs.find(key);
   if (it == g_tabs.end()) {
     const int ntw = fft_tw_count(n);
+    if (ntw < 0) return fail(IBDL_ERR_INVALID_ARG, "FFT tables: unsupported n");
     std::vector<typename Cx<T>::type> htw(ntw);
     std::vector<T> hs2(n);
     for (int j = 0; j < ntw; ++j) {
@@ -888,8 +889,8 @@ ibdl_status ibdl_create_geometry(const ibdl_geometry_desc* d, void* stream, ibdl
   cudaStream_t st = (cudaStream_t)stream;
   const int dim = d->dim, n = d->n;
   if (dim != 2 && dim != 3) return fail(IBDL_ERR_INVALID_ARG, "dim must be 2 or 3");
-  if (n < 16 || (n & (n - 1)) != 0 || n > (dim == 2 ? 4096 : 512))
-    return fail(IBDL_ERR_INVALID_ARG, "n must be a power of two in [16, 4096] (2D) / [16, 512] (3D)");
+  if (n < 16 || (n & (n - 1)) != 0 || n > (dim == 2 ? kMaxN2 : kMaxN3))
+    return fail(IBDL_ERR_INVALID_ARG, "n must be a power of two in [16, 2048] (2D) / [16, 512] (3D)");
   if (d->m < 1 || d->m > kMaxPoints)
     return fail(IBDL_ERR_INVALID_ARG, "m out of range (1 .. 16776960)");
   if (!(d->box_len > 0) || !isfinite(d->box_len))
@@ -1093,6 +1094,7 @@ ibdl_status ibdl_create_geometry(const ibdl_geometry_desc* d, void* stream, ibdl
   if ((s = g->alloc(&g->d_bar, (size_t)(4 + kSchedWords)))) return cleanup(s);
 
   g->solver_smem = solver_smem_bytes(gd, g->bins.rows, 1);
+  if (g->solver_smem < 0) return cleanup(fail(IBDL_ERR_INVALID_ARG, "solver shared memory"));
   {
     cudaError_t e = cudaStreamSynchronize(st);
     if (e) return cleanup(cuda_fail(e, "create sync"));
@@ -1178,6 +1180,11 @@ ibdl_status ibdl_solve(ibdl_geometry g, const double* bdata, const double* g_gri
     IBDL_CU(cudaMemcpyAsync(g->d_inst, g->h_inst, sizeof(SolveInst), cudaMemcpyHostToDevice, st));
     IBDL_CU(cudaMemcpyAsync(g->d_state, g->h_state, sizeof(SolveState), cudaMemcpyHostToDevice,
                             st));
+    {
+      char why[256];
+      if (!solver_smem_fits(g->h_inst, 1, g->solver_smem, why, sizeof(why)))
+        return fail(IBDL_ERR_INVALID_ARG, why);
+    }
     IBDL_CU(launch_persistent_solve(g->d_inst, g->d_state, 1, g->d_bar, g->solver_smem, st));
     IBDL_CU(cudaMemcpyAsync(g->h_state, g->d_state, sizeof(SolveState), cudaMemcpyDeviceToHost,
                             st));
@@ -1643,6 +1650,11 @@ ibdl_status ibdl_solve_batched(ibdl_batch b, int32_t count, const ibdl_geometry*
                           cudaMemcpyHostToDevice, st));
   IBDL_CU(cudaMemcpyAsync(b->d_state, b->h_state, sizeof(SolveState) * count,
                           cudaMemcpyHostToDevice, st));
+  {
+    char why[256];
+    if (!solver_smem_fits(b->h_inst, count, smem, why, sizeof(why)))
+      return fail(IBDL_ERR_INVALID_ARG, why);
+  }
   IBDL_CU(launch_persistent_solve(b->d_inst, b->d_state, count, b->d_bar, smem, st));
   IBDL_CU(cudaMemcpyAsync(b->h_state, b->d_state, sizeof(SolveState) * count,
                           cudaMemcpyDeviceToHost, st));
@@ -1670,10 +1682,31 @@ ibdl_status ibdl_solve_batched(ibdl_batch b, int32_t count, const ibdl_geometry*
 
 int64_t ibdl_kernel_launch_count(void) { return (int64_t)g_launches.load(); }
 
+ibdl_status ibdl_solver_smem_query(int32_t dim, int32_t n, int32_t rows, int32_t elem,
+                                   int64_t* need_out, int64_t* budget_out, int32_t* twiddles_out) {
+  g_err.clear();
+  if ((dim != 2 && dim != 3) || n < 16 || (n & (n - 1)) != 0 || n > (dim == 2 ? kMaxN2 : kMaxN3))
+    return fail(IBDL_ERR_INVALID_ARG, "n must be a power of two in [16, 2048] (2D) / [16, 512] (3D)");
+  if (rows < 2 || rows > n || (rows & (rows - 1)) != 0)
+    return fail(IBDL_ERR_INVALID_ARG, "rows: a power of two in [2, n]");
+  if (elem < 0 || elem > 2) return fail(IBDL_ERR_INVALID_ARG, "elem: 0, 1 or 2");
+  GridDesc g;
+  g.dim = dim;
+  g.n = n;
+  g.log2n = ilog2(n);
+  size_t need[3];
+  solver_item_smem(g, rows, elem, need);
+  if (need_out)
+    for (int k = 0; k < 3; ++k) need_out[k] = (int64_t)need[k];
+  if (budget_out) *budget_out = solver_smem_bytes(g, rows, 1);
+  if (twiddles_out) *twiddles_out = fft_tw_count(n);
+  return IBDL_OK;
+}
+
 void ibdl_tuning_enable(int32_t on) { g_tuning_on.store(on != 0); }
 
 ibdl_status ibdl_tuning_set(int32_t dim, int32_t n, int32_t precision, int32_t rows) {
-  if ((dim != 2 && dim != 3) || n < 16 || n > 4096 || (n & (n - 1)) ||
+  if ((dim != 2 && dim != 3) || n < 16 || n > (dim == 2 ? kMaxN2 : kMaxN3) || (n & (n - 1)) ||
       precision < IBDL_FP64 || precision > IBDL_FP32_REFINED || rows < 0)
     return IBDL_ERR_INVALID_ARG;
   if (rows && !tiling_admissible(n, rows)) return IBDL_ERR_INVALID_ARG;
@@ -2045,9 +2078,9 @@ ibdl_status ibdl_server_submit(ibdl_server s, const ibdl_geometry_desc* d, const
   g_err.clear();
   if (!s || !d || !bdata) return fail(IBDL_ERR_INVALID_ARG, "NULL server, desc or bdata");
   if (d->dim != 2 && d->dim != 3) return fail(IBDL_ERR_INVALID_ARG, "dim must be 2 or 3");
-  if (d->n < 16 || (d->n & (d->n - 1)) != 0 || d->n > (d->dim == 2 ? 4096 : 512))
+  if (d->n < 16 || (d->n & (d->n - 1)) != 0 || d->n > (d->dim == 2 ? kMaxN2 : kMaxN3))
     return fail(IBDL_ERR_INVALID_ARG,
-                "n must be a power of two in [16, 4096] (2D) / [16, 512] (3D)");
+                "n must be a power of two in [16, 2048] (2D) / [16, 512] (3D)");
   if (d->m < 1 || d->m > kMaxPoints)
     return fail(IBDL_ERR_INVALID_ARG, "m out of range (1 .. 16776960)");
   if (!d->x || !d->y || !d->nx || !d->ny || !d->w || (d->dim == 3 && (!d->z || !d->nz)))
@@ -2115,6 +2148,15 @@ ibdl_status ibdl_server_step(ibdl_server s, int64_t* done_ids, int32_t max_ids,
   ibdl_status slice_err = IBDL_OK;
   bool launched = false;
   if (hi >= 0) {
+    // every item of every active slot must fit the slice's shared memory
+    char why[256];
+    for (int k = 0; k <= hi && slice_err == IBDL_OK; ++k)
+      if (s->slot[k] && !solver_smem_fits(s->h_inst + k, 1, smem, why, sizeof(why)))
+        slice_err = fail(IBDL_ERR_INVALID_ARG, why);
+    if (slice_err != IBDL_OK)
+      for (int k = 0; k <= hi; ++k) s->fresh[k] = 0;  // retire them all below
+  }
+  if (hi >= 0 && slice_err == IBDL_OK) {
     cudaError_t e = cudaSuccess;
     for (int k = 0; k <= hi && !e; ++k) {
       if (!s->fresh[k]) continue;

@@ -126,6 +126,10 @@ __host__ __device__ inline int ilog2(int n) {
   return lg;
 }
 
+// Twiddle-table entries of an n-point FFT (the passes' tables concatenated),
+// n = 2^lg with 4 <= lg <= 12 (16 ... 4096 points, the sizes the library
+// accepts); -1 for any other n, so a caller sizing a buffer from it fails
+// instead of silently taking another size's table.
 __host__ __device__ inline int fft_tw_count(int n) {
   switch (ilog2(n)) {
     case 4: return plan_tw_total(4);
@@ -136,7 +140,8 @@ __host__ __device__ inline int fft_tw_count(int n) {
     case 9: return plan_tw_total(9);
     case 10: return plan_tw_total(10);
     case 11: return plan_tw_total(11);
-    default: return plan_tw_total(12);
+    case 12: return plan_tw_total(12);
+    default: return -1;
   }
 }
 
@@ -660,18 +665,21 @@ template <> __device__ __forceinline__ float pt_w<float>(const PointData& p, int
   return p.w32[i];
 }
 
-// Rows per tile of the x passes: 2D keeps 4 (2 for n = 4096) so that even a
+// Rows per tile of the x passes: 2D keeps 4 (2 for n = 2048) so that even a
 // 1024^2 grid has 256 tiles; 3D takes 8, so each kx of a tile is a 64-byte
 // (float) or 128-byte (double) segment of the transposed spectrum.
 __host__ __device__ inline int rows_per_tile(int dim, int n) {
   if (dim == 3) return 8;
-  return n >= 4096 ? 2 : 4;
+  return n >= 2048 ? 2 : 4;
 }
 
 // Shared memory of a row tile: two pencil buffers and the twiddle table.
+// (n outside the supported sizes: the largest size_t, which no budget meets)
 template <typename T>
 __host__ __device__ __forceinline__ size_t rows_smem_bytes(int n, int rows) {
-  return (2 * (size_t)(rows / 2) * pen_stride(n) + fft_tw_count(n)) * sizeof(cx_t<T>);
+  const int ntw = fft_tw_count(n);
+  if (ntw < 0) return ~(size_t)0;
+  return (2 * (size_t)(rows / 2) * pen_stride(n) + (size_t)ntw) * sizeof(cx_t<T>);
 }
 
 // ---- fused spread + forward x pass ------------------------------------------
@@ -879,7 +887,9 @@ struct PencilLayout {
 // pencils has >= 256 items when it can.
 template <typename T>
 __host__ __device__ inline size_t pencil_smem_for(int n, int c) {
-  return (2 * (size_t)c * pen_stride(n) + fft_tw_count(n)) * sizeof(cx_t<T>) +
+  const int ntw = fft_tw_count(n);
+  if (ntw < 0) return ~(size_t)0;
+  return (2 * (size_t)c * pen_stride(n) + (size_t)ntw) * sizeof(cx_t<T>) +
          (size_t)n * sizeof(T);
 }
 

@@ -22,6 +22,13 @@
 
 namespace ibdl {
 
+// Device ordinals with per-device state (kernel attributes, symbol addresses)
+constexpr int kMaxDevices = 64;
+// Largest grid per axis: 2D 2048 (a float64 pencil item of 4096 points would
+// need more than the 227 KB of shared memory a block can have), 3D 512.
+constexpr int kMaxN2 = 2048;
+constexpr int kMaxN3 = 512;
+
 template <typename T> struct Cx;
 template <> struct Cx<double> { using type = double2; };
 template <> struct Cx<float> { using type = float2; };

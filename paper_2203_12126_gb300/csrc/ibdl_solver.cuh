@@ -71,6 +71,12 @@ struct SolveState {
 };
 
 int solver_smem_bytes(const GridDesc& g, int rows, int need32);
+// Dynamic shared memory of one matvec work item per kind (row tile, pencil
+// layouts) for element type elem (0 float64, 1 float32, 2 double-float).
+void solver_item_smem(const GridDesc& g, int rows, int elem, size_t out[3]);
+// True when every item of every instance fits in `smem` bytes; else a
+// message in why.
+bool solver_smem_fits(const SolveInst* h_insts, int ninst, int smem, char* why, size_t why_len);
 // One block joins a two-party barrier: its bounded wait gives up after
 // `limit` polls and sets bar[2] (bar: 4 zeroed words).
 cudaError_t launch_barrier_selftest(unsigned* bar, unsigned limit, cudaStream_t st);

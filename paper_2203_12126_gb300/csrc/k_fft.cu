@@ -1,7 +1,6 @@
 // Periodic Helmholtz solve v = kappa L'^{-1} f, L' = I - kappa Delta_h, by
-// diagonalising the 5-point (2D) / 7-point (3D) stencil with the FFT
-// (Sec. 5.1: a periodic box "to make use of efficient ... methods").  The
-// eigenvalue of L' on exp(2 pi i k.j / n) is
+// diagonalising the 5-point (2D) / 7-point (3D) stencil with the FFT on the
+// periodic box of Sec. 5.1.  The eigenvalue of L' on exp(2 pi i k.j / n) is
 //     sigma(k) = 1 + (4 kappa / h^2) sum_c sin^2(pi k_c / n),
 // so v = IFFT( FFT(f) * kappa / sigma ) with the 1/n^d of the inverse folded
 // into the same multiplier.
@@ -12,11 +11,14 @@
 // 3D adds a y FFT pass before and an inverse y pass after the z pass, which
 // carries the multiplier.
 //
-// FFTs are shared-memory Stockham transforms (radix 4, one radix-2 stage for
-// odd log2 n), ping-ponging between two shared buffers; twiddles come from a
-// table exp(-2 pi i j / n) in global memory.  Two real rows are packed into
-// one complex row (real part / imaginary part) and separated after the FFT
-// with Z_k and conj(Z_{n-k}).
+// FFTs are shared-memory Stockham transforms (ibdl_device.cuh): a first pass
+// of radix 16, then the remaining bits of log2 n split as evenly as possible
+// into passes of radix <= 16 (1024 = 16 * 8 * 8, 256 = 16 * 16), ping-ponging
+// between two shared buffers, with per-pass twiddle tables.  Two real rows
+// are packed into one complex row (real part / imaginary part) and separated
+// after the FFT with Z_k and conj(Z_{n-k}).
+#include <mutex>
+
 #include "ibdl_device.cuh"
 
 namespace ibdl {
@@ -249,9 +251,17 @@ static void raise_smem(F* f) {
                        227 * 1024);
 }
 
+// Raises the dynamic shared-memory limit of every FFT kernel, once per
+// device (the attribute is per device), with that device current.
 cudaError_t configure_fft_kernels(int, int) {
-  static bool done = false;
-  if (done) return cudaSuccess;
+  static std::mutex mu;
+  static bool done[kMaxDevices] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev]) return cudaSuccess;
   raise_smem(k_rows_fwd<double, 2>);
   raise_smem(k_rows_fwd<double, 3>);
   raise_smem(k_rows_fwd<float, 2>);
@@ -275,8 +285,9 @@ cudaError_t configure_fft_kernels(int, int) {
   raise_smem(k_pencils<dd, 0>);
   raise_smem(k_pencils<dd, 1>);
   raise_smem(k_pencils<dd, 2>);
-  done = true;
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (e == cudaSuccess) done[dev] = true;
+  return e;
 }
 
 template cudaError_t launch_rows_fwd<double>(const GridDesc&, const PointData&, const Bins&,

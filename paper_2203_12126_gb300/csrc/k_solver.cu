@@ -26,6 +26,10 @@
 // in lock step.  Every wait is bounded; on timeout an error flag is raised
 // and every block leaves the kernel.
 #include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <mutex>
 
 #include "ibdl_device.cuh"
 #include "ibdl_solver.cuh"
@@ -818,7 +822,10 @@ __device__ int next_phase(const SolveInst& I, int phase) {
 }
 
 __device__ int items_of(const SolveInst& I, const PhaseDesc& d) {
-  if (d.phase < 5) return d.prec ? mv_items<float>(I, d.phase) : mv_items<double>(I, d.phase);
+  // each element type's own pencil layout (run_item dispatches the same way)
+  if (d.phase < 5)
+    return d.prec ? mv_items<float>(I, d.phase)
+                  : (I.dd64 ? mv_items<dd>(I, d.phase) : mv_items<double>(I, d.phase));
   if (d.phase == kPhaseSingle) return 1;
   return I.nchunk;
 }
@@ -1026,39 +1033,93 @@ __global__ void __launch_bounds__(kSolverThreads, 2)
   }
 }
 
+// Dynamic shared memory of one matvec work item of element type T: the row
+// tiles of the x passes and the pencil items of each pencil layout (2D: the
+// y solve; 3D: the z solve and the y passes).  out[0] row tile, out[1..2]
+// the pencil layouts (out[2] = 0 in 2D).
+template <typename T>
+static void item_smem(const GridDesc& g, int rows, size_t out[3]) {
+  out[0] = rows_smem_bytes<T>(g.n, rows);
+  out[1] = pencil_smem_bytes<T>(solve_layout<T>(g.dim, g.n, 1), g.n);
+  out[2] = g.dim == 3 ? pencil_smem_bytes<T>(solve_layout<T>(g.dim, g.n, 0), g.n) : 0;
+}
+
+void solver_item_smem(const GridDesc& g, int rows, int elem, size_t out[3]) {
+  if (elem == 1)
+    item_smem<float>(g, rows, out);
+  else if (elem == 2)
+    item_smem<dd>(g, rows, out);
+  else
+    item_smem<double>(g, rows, out);
+}
+
+// The launch reserves the largest need of every element type a solve of this
+// geometry may run: float64 (plain solves, and the float64-grade matvecs of
+// large batches), double-float (those of small refined launches) and float32
+// (the refined inner operator) -- each from its own plan and layout.
 int solver_smem_bytes(const GridDesc& g, int rows, int need32) {
-  size_t s = rows_smem_bytes<double>(g.n, rows);
-  const int nl = g.dim == 2 ? 1 : 2;
-  for (int w = 0; w < nl; ++w) {
-    const PencilLayout L = solve_layout<double>(g.dim, g.n, w == 0 ? 1 : 0);
-    const size_t ps = pencil_smem_bytes<double>(L, g.n);
-    if (ps > s) s = ps;
-    if (need32) {
-      const PencilLayout L32 = solve_layout<float>(g.dim, g.n, w == 0 ? 1 : 0);
-      const size_t p32 = pencil_smem_bytes<float>(L32, g.n);
-      if (p32 > s) s = p32;
+  size_t s = 0;
+  for (int elem = 0; elem < 3; ++elem) {
+    if (elem == 1 && !need32) continue;
+    size_t need[3];
+    solver_item_smem(g, rows, elem, need);
+    for (int k = 0; k < 3; ++k)
+      if (need[k] > s) s = need[k];
+  }
+  return s > (size_t)INT32_MAX ? -1 : (int)s;
+}
+
+// Before a cooperative launch: every item the instances can run fits in the
+// dynamic shared memory the launch reserves.  A shortfall would let an item
+// address past its block's shared window, so the launch is refused instead.
+bool solver_smem_fits(const SolveInst* h_insts, int ninst, int smem, char* why, size_t why_len) {
+  for (int k = 0; k < ninst; ++k) {
+    const SolveInst& I = h_insts[k];
+    const int elems[2] = {I.dd64 ? 2 : 0, I.refined ? 1 : -1};
+    for (int e : elems) {
+      if (e < 0) continue;
+      size_t need[3];
+      solver_item_smem(I.g, I.b.rows, e, need);
+      for (int c = 0; c < 3; ++c)
+        if (need[c] > (size_t)(smem < 0 ? 0 : smem)) {
+          snprintf(why, why_len,
+                   "persistent solver: instance %d (dim %d, n %d, element type %d, item kind %d) "
+                   "needs %zu bytes of shared memory, the launch reserves %d",
+                   k, I.g.dim, I.g.n, e, c, need[c], smem);
+          return false;
+        }
     }
   }
-  return (int)s;
+  return true;
 }
 
 cudaError_t launch_persistent_solve(const SolveInst* d_insts, SolveState* d_states, int ninst,
                                     unsigned* d_bar, int smem, cudaStream_t st, int max_rounds,
                                     int reserve_sms) {
   unsigned long long* ptimes = prof_phase_buffer();
-  static int sm_count = 0;
-  static int configured_smem = -1;
+  // per device: SM count and the shared-memory limit already raised
+  static std::mutex mu;
+  static int sm_counts[kMaxDevices] = {};
+  static int configured_smem[kMaxDevices] = {};
   cudaError_t e;
   int dev = 0;
   if ((e = cudaGetDevice(&dev))) return e;
-  if (!sm_count) {
-    if ((e = cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev))) return e;
-  }
-  if (smem > configured_smem) {
-    if ((e = cudaFuncSetAttribute((const void*)k_persistent_solve,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
-      return e;
-    configured_smem = smem;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  if (smem < 0) return cudaErrorInvalidValue;
+  int sm_count = 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!sm_counts[dev]) {
+      if ((e = cudaDeviceGetAttribute(&sm_counts[dev], cudaDevAttrMultiProcessorCount, dev)))
+        return e;
+    }
+    sm_count = sm_counts[dev];
+    if (smem > configured_smem[dev]) {
+      if ((e = cudaFuncSetAttribute((const void*)k_persistent_solve,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
+        return e;
+      configured_smem[dev] = smem;
+    }
   }
   int per_sm = 0;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent_solve,

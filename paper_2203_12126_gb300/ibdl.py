@@ -39,7 +39,7 @@ EXPORTS = [
     "ibdl_server_config_default", "ibdl_server_create", "ibdl_server_destroy",
     "ibdl_server_clock", "ibdl_server_submit", "ibdl_server_step", "ibdl_server_take",
     "ibdl_server_get_stats", "ibdl_tuning_enable", "ibdl_tuning_set", "ibdl_indicator",
-    "ibdl_near_boundary", "ibdl_selftest_bounded_wait",
+    "ibdl_near_boundary", "ibdl_selftest_bounded_wait", "ibdl_solver_smem_query",
 ]
 
 
@@ -172,6 +172,8 @@ def load(path: str = LIB_PATH):
         "ibdl_indicator": (C.c_int, [vp, vp, vp, vp]),
         "ibdl_near_boundary": (C.c_int, [vp, vp, vp, vp, i32, C.c_double, vp, vp]),
         "ibdl_selftest_bounded_wait": (C.c_int, [C.c_uint32, vp]),
+        "ibdl_solver_smem_query": (C.c_int, [i32, i32, i32, i32, C.POINTER(i64),
+                                             C.POINTER(i64), C.POINTER(i32)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -258,6 +260,18 @@ def helmholtz_2d_noalloc(n, box_len, kappa, f, v_out, stream=None):
     _check(load().ibdl_helmholtz_2d_noalloc(int(n), float(box_len), float(kappa), _ptr(f),
                                             _ptr(v_out), _stream(stream)))
     return v_out
+
+
+def solver_smem_query(dim: int, n: int, rows: int, elem: int) -> dict:
+    """Shared memory of one solver work item per kind for element type elem
+    (0 float64, 1 float32, 2 double-float), the launch's reservation and the
+    twiddle-table length (host only; see ibdl.h)."""
+    need = (C.c_int64 * 3)()
+    budget, ntw = C.c_int64(), C.c_int32()
+    _check(load().ibdl_solver_smem_query(int(dim), int(n), int(rows), int(elem), need,
+                                         C.byref(budget), C.byref(ntw)))
+    return {"need": [int(v) for v in need], "budget": int(budget.value),
+            "twiddles": int(ntw.value)}
 
 
 def tuning_enable(on: bool = True) -> None:

@@ -15,6 +15,7 @@ Tolerances (relative, 2-norm unless stated):
 """
 import numpy as np
 import pytest
+from parity_util import assert_parity
 
 torch = pytest.importorskip("torch")
 
@@ -111,7 +112,7 @@ def test_spread_div_parity(name, prec, tol):
     f = torch.empty((g.n,) * g.dim, dtype=torch.float64, device=DEV)
     G.spread_div(gpu(q), f, precision=prec)
     ref = O.spread_div(O.Box.of(g), g.X, g.normals, g.weights, q, g.delta)
-    assert rel(host(f), ref) <= tol
+    assert_parity(host(f), ref, tol)
     G.close()
 
 
@@ -123,7 +124,7 @@ def test_spread_parity(name):
     f = torch.empty((g.n,) * g.dim, dtype=torch.float64, device=DEV)
     G.spread(gpu(v), f)
     ref = O.spread(O.Box.of(g), g.X, v, g.weights, g.delta)
-    assert rel(host(f), ref) <= 1e-12
+    assert_parity(host(f), ref, 1e-12)
     G.close()
 
 
@@ -138,7 +139,7 @@ def test_helmholtz_parity(name, prec, tol):
     G.helmholtz(gpu(f), v, precision=prec)
     box = O.Box.of(g)
     ref = g.kappa * O.helmholtz_solve(box, g.kappa, f)
-    assert rel(host(v), ref) <= tol
+    assert_parity(host(v), ref, tol)
     G.close()
 
 
@@ -152,7 +153,7 @@ def test_interp_parity(name, prec, tol):
     y = torch.empty(g.m, dtype=torch.float64, device=DEV)
     G.interp(gpu(u), y, precision=prec)
     ref = O.interp(O.Box.of(g), g.X, u, g.delta)
-    assert rel(host(y), ref) <= tol
+    assert_parity(host(y), ref, tol)
     G.close()
 
 
@@ -168,7 +169,7 @@ def test_matvec_parity(name, bc, prec, tol):
     y = torch.empty(g.m, dtype=torch.float64, device=DEV)
     G.apply(gpu(q), y, precision=prec)
     ref = O.Operator(g, bc).apply(q)
-    assert rel(host(y), ref) <= tol
+    assert_parity(host(y), ref, tol)
     G.close()
 
 
@@ -183,11 +184,11 @@ def test_matvec_host_pointers_match_device_pointers():
     torch.cuda.synchronize()
     # the spread accumulates with shared-memory atomics, so two applications
     # agree to rounding, not bit for bit
-    assert rel(y_host, host(y_dev)) <= 1e-14
+    assert_parity(y_host, host(y_dev), 1e-14)
     pinned = torch.tensor(q).pin_memory()
     y_pin = torch.zeros(g.m, dtype=torch.float64).pin_memory()
     G.apply(pinned, y_pin)
-    assert rel(y_pin.numpy(), y_host) <= 1e-14
+    assert_parity(y_pin.numpy(), y_host, 1e-14)
     G.close()
 
 
@@ -197,7 +198,7 @@ def test_matvec_in_place_alias():
     q = density(g, 5)
     t = gpu(q)
     G.apply(t, t)
-    assert rel(host(t), O.Operator(g, configs.DIRICHLET).apply(q)) <= 1e-12
+    assert_parity(host(t), O.Operator(g, configs.DIRICHLET).apply(q), 1e-12)
     G.close()
 
 
@@ -212,7 +213,7 @@ def test_matvec_parity_full_c2(bc):
         G = make(g, bc=bc, precision=min(prec, 1))
         y = torch.empty(g.m, dtype=torch.float64, device=DEV)
         G.apply(gpu(q), y, precision=prec)
-        assert rel(host(y), ref) <= tol
+        assert_parity(host(y), ref, tol)
         G.close()
 
 
@@ -227,7 +228,7 @@ def test_matvec_parity_full_c3_sampled():
         G = make(g, bc=configs.NEUMANN, precision=min(prec, 1))
         y = torch.empty(g.m, dtype=torch.float64, device=DEV)
         G.apply(gpu(q), y, precision=prec)
-        assert rel(host(y), ref) <= tol
+        assert_parity(host(y), ref, tol)
         G.close()
 
 
@@ -244,7 +245,7 @@ def test_matvec_parity_512_cube():
         G = make(g, bc=configs.NEUMANN, precision=min(prec, 1))
         y = torch.empty(g.m, dtype=torch.float64, device=DEV)
         G.apply(gpu(q), y, precision=prec)
-        assert rel(host(y), ref) <= tol, prec
+        assert_parity(host(y), ref, tol, str(prec))
         G.close()
 
 
@@ -259,7 +260,7 @@ def test_fp64_solve_matches_dense_lu(name, bc):
     G = make(g, bc=bc)
     q = torch.empty(g.m, dtype=torch.float64, device=DEV)
     info = G.solve(gpu(b), q, tol=1e-12)
-    assert rel(host(q), q_star) <= 1e-10, info
+    assert_parity(host(q), q_star, 1e-10, str(info))
     assert info["rel_residual"] <= 1e-12
     G.close()
 
@@ -274,7 +275,7 @@ def test_fp32_refined_solve_reaches_1e8(name, bc):
     q = torch.empty(g.m, dtype=torch.float64, device=DEV)
     info = G.solve(gpu(b), q, tol=1e-10)
     assert info["refine_steps"] >= 1
-    assert rel(host(q), ref.x) <= 1e-8, info
+    assert_parity(host(q), ref.x, 1e-8, str(info))
     G.close()
 
 
@@ -308,10 +309,10 @@ def test_solve_with_forcing_and_evaluate():
     G = make(g)
     q = torch.empty(g.m, dtype=torch.float64, device=DEV)
     G.solve(gpu(b), q, g_grid=gpu(gg), tol=1e-12)
-    assert rel(host(q), q_ref) <= 1e-10
+    assert_parity(host(q), q_ref, 1e-10)
     u = torch.empty((g.n,) * 2, dtype=torch.float64, device=DEV)
     G.evaluate(q, u, g_grid=gpu(gg))
-    assert rel(host(u), op.evaluate(host(q), g_grid=gg)) <= 1e-12
+    assert_parity(host(u), op.evaluate(host(q), g_grid=gg), 1e-12)
     G.close()
 
 
@@ -323,10 +324,10 @@ def test_neumann_evaluate_with_vb():
     G.solve(gpu(vb), U, tol=1e-12)
     op = O.Operator(g, configs.NEUMANN)
     ref = O.gmres(op, op.rhs(vb), tol=1e-13).x
-    assert rel(host(U), ref) <= 1e-10
+    assert_parity(host(U), ref, 1e-10)
     u = torch.empty((g.n,) * 3, dtype=torch.float64, device=DEV)
     G.evaluate(U, u, vb=gpu(vb))
-    assert rel(host(u), op.evaluate(host(U), vb=vb)) <= 1e-12
+    assert_parity(host(u), op.evaluate(host(U), vb=vb), 1e-12)
     G.close()
 
 
@@ -404,4 +405,4 @@ def test_c3_refined_solve_matches_fp64_solve():
         assert info["rel_residual"] <= tol, info
         out[prec] = host(q)
         G.close()
-    assert rel(out[1], out[0]) <= 1e-8
+    assert_parity(out[1], out[0], 1e-8)

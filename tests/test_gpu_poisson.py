@@ -16,6 +16,7 @@ Tolerances:
 """
 import numpy as np
 import pytest
+from parity_util import assert_parity
 
 torch = pytest.importorskip("torch")
 
@@ -68,7 +69,7 @@ def test_poisson_matvec_parity(make, prec, tol):
     G = pkg.Geometry.from_workload(g, bc=configs.DIRICHLET, precision=prec)
     y = torch.empty(g.m, dtype=torch.float64, device=DEV)
     G.apply(gpu(q), y, precision=prec)
-    assert rel(host(y), ref) <= tol
+    assert_parity(host(y), ref, tol)
     G.close()
 
 
@@ -82,12 +83,12 @@ def test_poisson_solve_matches_dense_lu(engine):
     q = torch.zeros(g.m, dtype=torch.float64, device=DEV)
     info = G.solve(gpu(ub), q, tol=1e-12, engine=engine)
     assert info["status"] == 0
-    assert rel(host(q), qstar) <= 1e-10
+    assert_parity(host(q), qstar, 1e-10)
     # the field away from Gamma is the harmonic polynomial (Sec. 5.4, first order)
     u = torch.empty(g.n * g.n, dtype=torch.float64, device=DEV)
     G.evaluate(q, u)
     uo = O.Operator(g, configs.DIRICHLET).evaluate(host(q)).reshape(-1)
-    assert rel(host(u), uo) <= 1e-12
+    assert_parity(host(u), uo, 1e-12)
     G.close()
 
 
@@ -102,7 +103,7 @@ def test_poisson_forcing_and_refined_solve():
     q = torch.zeros(g.m, dtype=torch.float64, device=DEV)
     info = G.solve(gpu(ub), q, g_grid=gpu(gt), tol=1e-10)
     assert info["status"] == 0
-    assert rel(host(q), qstar) <= 1e-8
+    assert_parity(host(q), qstar, 1e-8)
     G.close()
 
 
@@ -125,11 +126,11 @@ def test_completed_apply_parity(n, L):
     assert G.nsys == g.m + 1
     y = torch.empty(g.m + 1, dtype=torch.float64, device=DEV)
     G.apply(gpu(z), y)
-    assert rel(host(y), ref) <= 1e-12
+    assert_parity(host(y), ref, 1e-12)
     # in place: q and y alias
     zz = gpu(z)
     G.apply(zz, zz)
-    assert rel(host(zz), ref) <= 1e-12
+    assert_parity(host(zz), ref, 1e-12)
     G.close()
 
 
@@ -153,10 +154,10 @@ def test_completed_solve_matches_dense_lu(prec, tol, rtol):
     z = torch.zeros(g.m + 1, dtype=torch.float64, device=DEV)
     info = G.solve(gpu(ub), z, g_grid=gpu(gt), tol=tol)
     assert info["status"] == 0
-    assert rel(host(z), zstar) <= rtol
+    assert_parity(host(z), zstar, rtol)
     u = torch.empty(g.n * g.n, dtype=torch.float64, device=DEV)
     G.evaluate(gpu(zstar), u, g_grid=gpu(gt))
-    assert rel(host(u), op.evaluate(zstar, gt).reshape(-1)) <= 1e-12
+    assert_parity(host(u), op.evaluate(zstar, gt).reshape(-1), 1e-12)
     G.close()
 
 

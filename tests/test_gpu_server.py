@@ -4,6 +4,7 @@ every result equals the same problem solved alone (and the float64 oracle)
 within the float32-refined path's tolerance."""
 import numpy as np
 import pytest
+from parity_util import assert_parity
 
 torch = pytest.importorskip("torch")
 
@@ -82,9 +83,9 @@ def test_mixed_stream_matches_alone_and_oracle():
         q_alone = q.cpu().numpy()
         G.close()
         ref = O.solve(p.geom, p.bc, p.bdata, tol=1e-13).x
-        assert rel(q_mix, q_alone) <= STATED, (k, rel(q_mix, q_alone))
-        assert rel(q_mix, ref) <= STATED, (k, rel(q_mix, ref))
-        assert rel(q_alone, ref) <= STATED, (k, rel(q_alone, ref))
+        assert_parity(q_mix, q_alone, STATED, str((k, rel(q_mix, q_alone))))
+        assert_parity(q_mix, ref, STATED, str((k, rel(q_mix, ref))))
+        assert_parity(q_alone, ref, STATED, str((k, rel(q_alone, ref))))
     srv.close()
 
 

@@ -2,6 +2,7 @@
 solver against the host-driven loop, individual solves and the oracle."""
 import numpy as np
 import pytest
+from parity_util import assert_parity
 
 torch = pytest.importorskip("torch")
 
@@ -58,10 +59,10 @@ def test_persistent_engine_matches_host_loop(bc, prec):
     i0 = G.solve(gpu(b), q0, tol=1e-10, engine=0)
     i1 = G.solve(gpu(b), q1, tol=1e-10, engine=1)
     assert abs(i0["iters"] - i1["iters"]) <= 1
-    assert rel(q0.cpu(), q1.cpu()) <= 1e-8
+    assert_parity(q0.cpu(), q1.cpu(), 1e-8)
     assert i0["rel_residual"] <= 1e-10
     ref = O.solve(g, bc, b, tol=1e-13).x
-    assert rel(q0.cpu(), ref) <= 1e-8
+    assert_parity(q0.cpu(), ref, 1e-8)
     G.close()
 
 
@@ -71,7 +72,7 @@ def test_persistent_solve_c1_tight():
     G = pkg.Geometry.from_workload(p.geom, bc=p.bc)
     q = torch.empty(p.geom.m, dtype=torch.float64, device=DEV)
     info = G.solve(gpu(p.bdata), q, tol=1e-12)
-    assert rel(q.cpu(), q_star) <= 1e-10
+    assert_parity(q.cpu(), q_star, 1e-10)
     assert 4 <= info["iters"] <= 8 and info["matvecs"] >= info["iters"]
     assert len(info["history"]) == info["iters"]
     G.close()
@@ -84,7 +85,7 @@ def test_persistent_restarts_and_max_iters():
     q = torch.empty(g.m, dtype=torch.float64, device=DEV)
     info = G.solve(gpu(b), q, tol=1e-12, restart=2)       # many short cycles
     ref = O.solve(g, configs.DIRICHLET, b, tol=1e-13).x
-    assert rel(q.cpu(), ref) <= 1e-10
+    assert_parity(q.cpu(), ref, 1e-10)
     info = G.solve(gpu(b), q, tol=1e-14, max_iters=3, raise_on_error=False)
     assert info["status"] == ibdl.ERR_NOT_CONVERGED and info["iters"] == 3
     G.close()
@@ -116,9 +117,9 @@ def test_batched_matches_individual_and_oracle():
         # the spread's shared-memory atomics make rounding order vary between
         # launches, so the two runs agree to the solve tolerance, not bitwise
         assert abs(infos[k]["iters"] - ia["iters"]) <= 1
-        assert rel(qs[k].cpu(), alone.cpu()) <= (1e-8 if prec else 1e-10)
+        assert_parity(qs[k].cpu(), alone.cpu(), (1e-8 if prec else 1e-10))
         ref = O.solve(g, bc, b, tol=1e-13).x
-        assert rel(qs[k].cpu(), ref) <= (1e-8 if prec else 1e-9), (k, infos[k])
+        assert_parity(qs[k].cpu(), ref, (1e-8 if prec else 1e-9), str((k, infos[k])))
     batch.close()
     for G in geoms:
         G.close()
@@ -151,7 +152,7 @@ def test_c4_style_batch_of_64():
         ref = torch.empty_like(qs[k])
         geoms[k].solve(bs[k], ref, tol=1e-12)
         assert infos[k]["rel_residual"] <= 1e-8
-        assert rel(qs[k].cpu(), ref.cpu()) <= 1e-7
+        assert_parity(qs[k].cpu(), ref.cpu(), 1e-7)
     batch.close()
     for G in geoms:
         G.close()
@@ -167,7 +168,7 @@ def test_multiblock_vector_path_3d_large_m(prec):
     q = torch.empty(g.m, dtype=torch.float64, device=DEV)
     info = G.solve(gpu(b), q, tol=1e-10)
     ref = O.solve(g, configs.NEUMANN, b, tol=1e-13).x
-    assert rel(q.cpu(), ref) <= (1e-8 if prec else 1e-9), info
+    assert_parity(q.cpu(), ref, (1e-8 if prec else 1e-9), str(info))
     G.close()
 
 
@@ -203,7 +204,7 @@ print(json.dumps(out))
     b = np.random.default_rng(6).standard_normal(g.m)
     ref = O.solve(g, configs.NEUMANN, b, tol=1e-13).x
     for prec, (q, iters) in zip((0, 1), forced):
-        assert rel(q, ref) <= (1e-8 if prec else 1e-9)
+        assert_parity(q, ref, (1e-8 if prec else 1e-9))
 
 
 def test_scheduler_stress_many_tiny_instances():
@@ -231,7 +232,7 @@ def test_scheduler_stress_many_tiny_instances():
         infos = batch.solve(geoms, bs, qs, tol=1e-10)
         for k, info in enumerate(infos):
             assert info["status"] == 0 and info["rel_residual"] <= 1e-10, (k, info)
-            assert rel(qs[k].cpu(), solo[k]) <= 1e-8, k
+            assert_parity(qs[k].cpu(), solo[k], 1e-8, str(k))
     batch.close()
     for G in geoms:
         G.close()
@@ -263,9 +264,9 @@ def test_double_float_and_float64_residuals_agree():
     infos = big.solve(many, [bs[k % 4] for k in range(20)], q_big, tol=1e-10)
     assert all(f["status"] == 0 for f in infos)
     for k in range(4):
-        assert rel(q_small[k].cpu().numpy(), refs[k]) <= 1e-8
+        assert_parity(q_small[k].cpu().numpy(), refs[k], 1e-8)
     for k in range(20):
-        assert rel(q_big[k].cpu().numpy(), refs[k % 4]) <= 1e-8
+        assert_parity(q_big[k].cpu().numpy(), refs[k % 4], 1e-8)
     small.close()
     big.close()
     for g in geoms + many:

@@ -4,6 +4,7 @@ finite-difference operators: float64 1e-12 relative, float32 1e-5, solves
 at tol 1e-12 against dense LU 1e-10."""
 import numpy as np
 import pytest
+from parity_util import assert_parity
 
 torch = pytest.importorskip("torch")
 
@@ -54,7 +55,7 @@ def test_spectral_matvec_parity(name, prec, tol):
         G = pkg.Geometry.from_workload(g, bc=bc, precision=prec, disc="spectral")
         y = torch.empty(g.m, dtype=torch.float64, device=DEV)
         G.apply(gpu(q), y, precision=prec)
-        assert rel(host(y), ref) <= tol, bc
+        assert_parity(host(y), ref, tol, str(bc))
         G.close()
 
 
@@ -68,7 +69,7 @@ def test_spectral_solve_matches_dense_lu(bc):
     q = torch.zeros(g.m, dtype=torch.float64, device=DEV)
     info = G.solve(gpu(ub), q, tol=1e-12)
     assert info["status"] == 0
-    assert rel(host(q), qstar) <= 1e-10
+    assert_parity(host(q), qstar, 1e-10)
     G.close()
 
 
@@ -84,7 +85,7 @@ def test_spectral_refined_solve_and_table3_count():
     q = torch.zeros(g.m, dtype=torch.float64, device=DEV)
     info = G.solve(gpu(ub), q, tol=1e-10)
     assert info["status"] == 0
-    assert rel(host(q), qstar) <= 1e-8
+    assert_parity(host(q), qstar, 1e-8)
     G.close()
     G = pkg.Geometry.from_workload(g, disc="spectral")
     info = G.solve(gpu(ub), q, tol=1e-8)
@@ -102,12 +103,12 @@ def test_spectral_evaluate_with_forcing_and_neumann_vb():
         G = pkg.Geometry.from_workload(g, bc=bc, disc="spectral")
         u = torch.empty(128 * 128, dtype=torch.float64, device=DEV)
         G.evaluate(gpu(q), u, vb=None if v is None else gpu(v), g_grid=gpu(gt))
-        assert rel(host(u), ref) <= 1e-12
+        assert_parity(host(u), ref, 1e-12)
         # the right-hand side with forcing goes through the same spectral path
         qs = torch.zeros(g.m, dtype=torch.float64, device=DEV)
         G.solve(gpu(q), qs, g_grid=gpu(gt), tol=1e-12)
         qd = O.solve_dense(g, bc, q, g_grid=gt, disc="spectral")
-        assert rel(host(qs), qd) <= 1e-10
+        assert_parity(host(qs), qd, 1e-10)
         G.close()
 
 

@@ -2,6 +2,7 @@
 the fixed rule's to rounding (float64 1e-12, float32 1e-6 relative)."""
 import numpy as np
 import pytest
+from parity_util import assert_parity
 
 torch = pytest.importorskip("torch")
 
@@ -42,7 +43,7 @@ def test_tuned_tiling_matches_fixed_rule(which, prec, tol):
             G.close()
     finally:
         ibdl.tuning_enable(True)
-    assert rel(out[True], out[False]) <= tol
+    assert_parity(out[True], out[False], tol)
 
 
 def test_pinned_tiling_is_used_and_checked():
@@ -65,7 +66,7 @@ def test_pinned_tiling_is_used_and_checked():
                 G.apply(q, y)
                 out[pinned] = y.cpu().numpy()
                 G.close()
-            assert rel(out[True], out[False]) <= 1e-12
+            assert_parity(out[True], out[False], 1e-12)
         bad = [(4, 64, 0, 8), (2, 100, 0, 8), (2, 64, 2, 8), (2, 64, 0, 6), (2, 64, 0, 32),
                (2, 64, 0, -2), (3, 32, 0, 16)]
         for args in bad:

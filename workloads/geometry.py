@@ -88,8 +88,14 @@ class StarCurve:
         # of the speed decay geometrically well before that
         keep = max(8, int(np.max(np.nonzero(np.abs(c[: n_modes // 2]) > 1e-15 * abs(c[0]))[0])) + 1)
         self._c0 = c[0].real
-        self._cm = c[1:keep]
-        self._mm = np.arange(1, keep)
+        mm = np.arange(1, keep)
+        # the speed depends on theta only through lobes*theta, so only the
+        # harmonics that are multiples of `lobes` are non-zero; the others
+        # hold FFT rounding noise and are dropped
+        if self.lobes > 1 and self.amp != 0.0:
+            mm = mm[mm % self.lobes == 0]
+        self._cm = c[mm]
+        self._mm = mm
 
     def radius(self, t):
         return self.r0 * (1.0 + self.amp * np.cos(self.lobes * t))
