@@ -417,15 +417,25 @@ typedef struct {
   int64_t device_bytes;      /* device memory the handle owns */
   int32_t fft_passes;        /* kernels per Helmholtz solve */
   int32_t rows_per_tile;     /* grid rows per x-pass tile (spread bin size) */
+  int32_t pencils_per_item[2]; /* pencils per work item of the solve pass (2D y,
+                                  3D z) and of the 3D y passes (0 in 2D), in
+                                  the geometry's inner precision */
 } ibdl_geometry_info;
 ibdl_status ibdl_get_geometry_info(ibdl_geometry g, ibdl_geometry_info* info);
 
-/* Autotuner of the x-pass tiling (on by default).  The first geometry of
- * each (device, dim, n, precision) times one matvec for every admissible
- * number of grid rows per tile -- an even R with n/R >= 4, R <= n - 5 and
- * float64 row buffers within 100 KB of shared memory -- and the fastest is
- * used by every later geometry of that kind in the process (a few matvecs
- * once, inside that first ibdl_create_geometry).  Geometries built by the
+/* Autotuner of the x-pass tiling and of the pencil items (on by default).
+ * The first geometry of each (device, dim, n, precision) times one matvec
+ * for every admissible number of grid rows per tile -- an even R with
+ * n/R >= 4, R <= n - 5 and float64 row buffers within 100 KB of shared
+ * memory -- then, with that tiling, for every admissible number of pencils
+ * per work item of each pencil pass (a power of two <= 16 whose item fits
+ * 100 KB; strided z items at least 2), in the geometry's inner precision; the
+ * fastest choices are used by every later geometry of that kind in the
+ * process (a few matvecs once, inside that first ibdl_create_geometry).
+ * The pencil choice applies to the launch-based passes (ibdl_apply,
+ * ibdl_evaluate, ibdl_helmholtz, the host-loop engine); the persistent
+ * solver keeps the fixed rule, under which its instances share the GPU
+ * better.  Geometries built by the
  * server use a tiling already chosen, else the fixed rule (4 rows in 2D, 2
  * for n = 2048; 8 in 3D).  Off: the fixed rule always.  Results of the two
  * tilings agree to rounding. */
@@ -441,6 +451,20 @@ void ibdl_tuning_enable(int32_t on);
  * [16, 2048] (2D) / [16, 512] (3D), precision a geometry's (IBDL_FP64 or IBDL_FP32_REFINED),
  * and rows 0 or an admissible tiling (as above); IBDL_ERR_CUDA if the current device cannot be read. */
 ibdl_status ibdl_tuning_set(int32_t dim, int32_t n, int32_t precision, int32_t rows);
+
+/* Pins the pencils per work item of one (current device, dim, n,
+ * precision) kind, as if the autotuner had chosen them: c_solve for the solve
+ * pass (2D y pencils, 3D z pencils), c_y for the 3D y passes (0 in 2D); 0 for
+ * one of them keeps the fixed rule for that pass, and both 0 drops the entry
+ * (the next geometry of the kind tunes again).  The precision's own element
+ * type is pinned (float32 for IBDL_FP32_REFINED, float64 for IBDL_FP64); a
+ * value must be admissible: a power of two <= 16 whose item fits 100 KB of
+ * shared memory, at least 2 and at most n for strided z pencils.  Later
+ * geometries of the kind use the pin; results agree with the fixed rule's to
+ * rounding.  IBDL_ERR_INVALID_ARG otherwise; IBDL_ERR_CUDA if the current
+ * device cannot be read.  No passage of the paper: a resource choice. */
+ibdl_status ibdl_tuning_set_pencils(int32_t dim, int32_t n, int32_t precision, int32_t c_solve,
+                                    int32_t c_y);
 
 /* Shared-memory bookkeeping of the persistent solver's work items (host
  * only: touches no GPU, so it runs without one).  For a grid (dim, n), an

@@ -14,6 +14,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <chrono>
 #include <deque>
@@ -175,6 +176,8 @@ struct ibdl_geometry_s {
   SpectralWs<float> ws32;
   SpectralWs<dd> wsdd;  // double-float view of the float64 buffers (own tables)
   bool have32 = false;
+  TmaDesc zmap32;            // 3D: tensor map of ws32.spec for the staged z pass
+  unsigned* d_err = nullptr;  // raised by a bounded wait inside a transform
   KrylovWs kry;
   double *vb = nullptr, *vx = nullptr, *vr = nullptr, *vt = nullptr, *vd = nullptr;
   double *stage_a = nullptr, *stage_b = nullptr;
@@ -330,6 +333,13 @@ ibdl_status alloc_spectral(ibdl_geometry_s* g, SpectralWs<T>& ws, cudaStream_t) 
 ibdl_status ensure32(ibdl_geometry_s* g, cudaStream_t st) {
   if (g->have32) return IBDL_OK;
   IBDL_TRY(alloc_spectral<float>(g, g->ws32, st));
+  g->ws32.err = g->d_err;
+  // 3D: the z pass stages its pencils with bulk tensor copies when the
+  // driver can encode the tensor map (otherwise the plain pass runs)
+  if (g->grid.dim == 3 && !g->grid.spectral &&
+      make_zsolve_map<float>(g->grid, g->ws32.spec, &g->zmap32) == cudaSuccess)
+    g->ws32.zmap = &g->zmap32;
+  cudaGetLastError();
   g->have32 = true;
   return IBDL_OK;
 }
@@ -723,18 +733,19 @@ ibdl_status vec_norm(ibdl_geometry_s* g, const double* v, double* out, cudaStrea
 // Tile lists of `rows` rows per tile into `out` (3D: with the empty-plane
 // flags in dz), from caller-provided buffers; asynchronous on st.
 cudaError_t build_tiles(ibdl_geometry_s* g, int rows, int* start, int* cursor, int* counts,
-                        int* pts, unsigned char* dz, Bins* out, cudaStream_t st) {
+                        int* pts, int* spts, unsigned char* dz, Bins* out, cudaStream_t st) {
   const GridDesc& gd = g->grid;
   const int n = gd.n;
   // the x passes index a tile's pencils with shifts
   if (rows < 2 || (rows & (rows - 1))) return cudaErrorInvalidValue;
   const int ntiles = (n / rows) * (gd.dim == 3 ? n : 1);
-  cudaError_t e = launch_bins(gd, g->pd, rows, ntiles, start, cursor, counts, pts, st);
+  cudaError_t e = launch_bins(gd, g->pd, rows, ntiles, start, cursor, counts, pts, spts, st);
   if (e) return e;
   out->rows = rows;
   out->ntiles = ntiles;
   out->start = start;
   out->pts = pts;
+  out->spts = spts;
   out->zempty = nullptr;
   if (gd.dim == 3) {
     // planes no point touches: their spectrum stays zero through the x and
@@ -815,7 +826,7 @@ ibdl_status tuned_rows(ibdl_geometry_s* g, int* rows_out, cudaStream_t st) {
   for (int R : cand) {
     const int ntiles = (n / R) * (dim == 3 ? n : 1);
     void* buf = nullptr;
-    const size_t ni = 3 * ((size_t)ntiles + 1) + (size_t)bins_capacity(dim, R, m);
+    const size_t ni = 3 * ((size_t)ntiles + 1) + 2 * (size_t)bins_capacity(dim, R, m);
     cudaError_t e = cudaMallocFromPoolAsync(&buf, ni * sizeof(int) + n, pool, st);
     if (e) {
       status = cuda_fail(e, "autotuner buffers");
@@ -825,8 +836,9 @@ ibdl_status tuned_rows(ibdl_geometry_s* g, int* rows_out, cudaStream_t st) {
     int* cursor = start + ntiles + 1;
     int* counts = cursor + ntiles + 1;
     int* pts = counts + ntiles + 1;
-    unsigned char* dz = reinterpret_cast<unsigned char*>(pts + bins_capacity(dim, R, m));
-    e = build_tiles(g, R, start, cursor, counts, pts, dz, &g->bins, st);
+    int* spts = pts + bins_capacity(dim, R, m);
+    unsigned char* dz = reinterpret_cast<unsigned char*>(spts + bins_capacity(dim, R, m));
+    e = build_tiles(g, R, start, cursor, counts, pts, spts, dz, &g->bins, st);
     float ms = 0;
     for (int rep = 0; rep < 4 && !e && status == IBDL_OK; ++rep) {
       if (rep == 1) e = cudaEventRecord(e0, st);
@@ -856,6 +868,100 @@ ibdl_status tuned_rows(ibdl_geometry_s* g, int* rows_out, cudaStream_t st) {
     g_tuned[key] = best;
   }
   *rows_out = best;
+  return IBDL_OK;
+}
+
+// Pencils per work item of the pencil passes, per (device, dim, n,
+// precision): after the tiling, the first geometry of a kind times a matvec
+// of its inner precision (float32 for a refined geometry, float64 else) for
+// every admissible c of each pencil layout in turn (3D: the solve pass, then
+// the y passes; c a power of two <= 16 whose item fits 100 KB of shared
+// memory, strided items at least 2), keeping the fastest.  The other
+// precision class keeps the fixed rule.
+std::map<std::tuple<int, int, int, int>, std::array<int, 2>> g_tuned_pc;
+
+// The tensor map of the staged z pass encodes its box (c pencils): encode
+// again whenever the float32 solve layout changes.
+ibdl_status refresh_maps(ibdl_geometry_s* g) {
+  if (!g->ws32.zmap) return IBDL_OK;
+  IBDL_CU(make_zsolve_map<float>(g->grid, g->ws32.spec, &g->zmap32));
+  return IBDL_OK;
+}
+
+ibdl_status tuned_pencils(ibdl_geometry_s* g, cudaStream_t st) {
+  GridDesc& gd = g->grid;
+  const int n = gd.n, dim = gd.dim, cls = g->precision == IBDL_FP32_REFINED ? 0 : 1;
+  if (!g_tuning_on.load() || gd.spectral || g->eta > 0) return IBDL_OK;
+  int dev = 0;
+  IBDL_CU(cudaGetDevice(&dev));
+  const auto key = std::make_tuple(dev, dim, n, g->precision);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned_pc.find(key);
+    if (it != g_tuned_pc.end()) {
+      gd.pcap[cls][0] = it->second[0];
+      gd.pcap[cls][1] = it->second[1];
+      return refresh_maps(g);
+    }
+  }
+  if (tl_no_tune) return IBDL_OK;
+  cudaMemPool_t pool;
+  IBDL_CU(workspace_pool(&pool));
+  const int m = g->m;
+  double *q = nullptr, *y = nullptr;
+  IBDL_CU(cudaMallocFromPoolAsync((void**)&q, sizeof(double) * m, pool, st));
+  IBDL_CU(cudaMallocFromPoolAsync((void**)&y, sizeof(double) * m, pool, st));
+  IBDL_CU(cudaMemsetAsync(q, 0, sizeof(double) * m, st));
+  IBDL_CU(launch_fill(m, q, 1.0, st));
+  cudaEvent_t e0, e1;
+  IBDL_CU(cudaEventCreate(&e0));
+  IBDL_CU(cudaEventCreate(&e1));
+  ibdl_status status = IBDL_OK;
+  const int passes[2] = {1, 0};
+  for (int w = 0; w < (dim == 3 ? 2 : 1) && status == IBDL_OK; ++w) {
+    const int which = passes[w];
+    const PencilLayout base = cls == 0 ? solve_layout<float>(dim, n, which)
+                                       : solve_layout<double>(dim, n, which);
+    std::vector<int> cand;
+    for (int c = 1; c <= 16; c *= 2) {
+      const bool ok = cls == 0 ? pencils_admissible<float>(n, base.estride, base.pg, c)
+                               : pencils_admissible<double>(n, base.estride, base.pg, c);
+      if (ok) cand.push_back(c);
+    }
+    if (cand.size() < 2) continue;
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int c : cand) {
+      gd.pcap[cls][which] = c;
+      if ((status = refresh_maps(g)) != IBDL_OK) break;
+      cudaError_t e = cudaSuccess;
+      float ms = 0;
+      for (int rep = 0; rep < 4 && !e && status == IBDL_OK; ++rep) {
+        if (rep == 1) e = cudaEventRecord(e0, st);
+        if (e) break;
+        status = matvec_prec(g, g->precision, q, y, st);
+      }
+      if (!e && status == IBDL_OK) e = cudaEventRecord(e1, st);
+      if (!e && status == IBDL_OK) e = cudaEventSynchronize(e1);
+      if (!e && status == IBDL_OK) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e) status = cuda_fail(e, "autotuner timing");
+      if (status != IBDL_OK) break;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = c;
+      }
+    }
+    gd.pcap[cls][which] = best;
+  }
+  cudaFreeAsync(q, st);
+  cudaFreeAsync(y, st);
+  cudaStreamSynchronize(st);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (status == IBDL_OK) status = refresh_maps(g);
+  if (status != IBDL_OK) return status;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned_pc[key] = {gd.pcap[cls][0], gd.pcap[cls][1]};
   return IBDL_OK;
 }
 
@@ -1030,7 +1136,13 @@ ibdl_status ibdl_create_geometry(const ibdl_geometry_desc* d, void* stream, ibdl
     cudaError_t e = configure_fft_kernels(n, 0);
     if (e) return cleanup(cuda_fail(e, "configure kernels"));
   }
+  if ((s = g->alloc(&g->d_err, (size_t)1))) return cleanup(s);
+  {
+    cudaError_t e = cudaMemsetAsync(g->d_err, 0, sizeof(unsigned), st);
+    if (e) return cleanup(cuda_fail(e, "clear error word"));
+  }
   if ((s = alloc_spectral<double>(g, g->ws64, st))) return cleanup(s);
+  g->ws64.err = g->d_err;
   {
     // the double-float view shares the float64 spectrum (same 16-byte
     // complex) and grid; it has its own twiddle and sin^2 tables
@@ -1049,16 +1161,19 @@ ibdl_status ibdl_create_geometry(const ibdl_geometry_desc* d, void* stream, ibdl
   if ((s = tuned_rows(g, &rows, st))) return cleanup(s);
   {
     const int ntiles = (n / rows) * (dim == 3 ? n : 1);
-    int *start, *cursor, *counts, *bpts;
+    int *start, *cursor, *counts, *bpts, *spts;
     unsigned char* dz = nullptr;
     if ((s = g->alloc(&start, (size_t)ntiles + 1))) return cleanup(s);
     if ((s = g->alloc(&cursor, (size_t)ntiles + 1))) return cleanup(s);
     if ((s = g->alloc(&counts, (size_t)ntiles + 1))) return cleanup(s);
     if ((s = g->alloc(&bpts, (size_t)bins_capacity(dim, rows, m)))) return cleanup(s);
+    if ((s = g->alloc(&spts, (size_t)bins_capacity(dim, rows, m)))) return cleanup(s);
     if (dim == 3 && (s = g->alloc(&dz, (size_t)n))) return cleanup(s);
-    cudaError_t e = build_tiles(g, rows, start, cursor, counts, bpts, dz, &g->bins, st);
+    cudaError_t e = build_tiles(g, rows, start, cursor, counts, bpts, spts, dz, &g->bins, st);
     if (e) return cleanup(cuda_fail(e, "binning"));
   }
+  // pencils per item of the pencil passes, with the autotuner
+  if ((s = tuned_pencils(g, st))) return cleanup(s);
 
   // Krylov workspace (float64, restart up to 64)
   KrylovWs& k = g->kry;
@@ -1274,7 +1389,14 @@ ibdl_status ibdl_solve(ibdl_geometry g, const double* bdata, const double* g_gri
     }
   }
   IBDL_CU(cudaMemcpyAsync(q_out, g->vx, sizeof(double) * ns, cudaMemcpyDefault, st));
+  unsigned* herr = reinterpret_cast<unsigned*>(g->host_scal + 12);
+  IBDL_CU(cudaMemcpyAsync(herr, g->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
   IBDL_CU(cudaStreamSynchronize(st));
+  if (*herr) {
+    // a bounded wait inside a transform gave up: the result is not valid
+    cudaMemsetAsync(g->d_err, 0, sizeof(unsigned), st);
+    status = fail(IBDL_ERR_TIMEOUT, "a bounded wait for a staged copy timed out");
+  }
   if (info) {
     memset(info, 0, sizeof(*info));
     info->iters = run.iters;
@@ -1561,6 +1683,14 @@ ibdl_status ibdl_get_geometry_info(ibdl_geometry g, ibdl_geometry_info* info) {
   info->device_bytes = g->bytes;
   info->fft_passes = fft_kernels_per_solve<double>(g->grid.dim);
   info->rows_per_tile = g->bins.rows;
+  // the pencils per item the passes of the geometry's inner precision use
+  if (g->precision == IBDL_FP32_REFINED) {
+    info->pencils_per_item[0] = solve_layout<float>(g->grid, 1).c;
+    info->pencils_per_item[1] = g->grid.dim == 3 ? solve_layout<float>(g->grid, 0).c : 0;
+  } else {
+    info->pencils_per_item[0] = solve_layout<double>(g->grid, 1).c;
+    info->pencils_per_item[1] = g->grid.dim == 3 ? solve_layout<double>(g->grid, 0).c : 0;
+  }
   return IBDL_OK;
 }
 
@@ -1705,6 +1835,36 @@ ibdl_status ibdl_solver_smem_query(int32_t dim, int32_t n, int32_t rows, int32_t
 
 void ibdl_tuning_enable(int32_t on) { g_tuning_on.store(on != 0); }
 
+ibdl_status ibdl_tuning_set_pencils(int32_t dim, int32_t n, int32_t precision, int32_t c_solve,
+                                    int32_t c_y) {
+  g_err.clear();
+  if ((dim != 2 && dim != 3) || n < 16 || n > (dim == 2 ? kMaxN2 : kMaxN3) || (n & (n - 1)) ||
+      precision < IBDL_FP64 || precision > IBDL_FP32_REFINED)
+    return fail(IBDL_ERR_INVALID_ARG, "dim, n or precision");
+  if (dim == 2 && c_y != 0) return fail(IBDL_ERR_INVALID_ARG, "2D has no y passes: c_y = 0");
+  const int cs[2] = {c_y, c_solve};
+  for (int which = 0; which < 2; ++which) {
+    const int c = cs[which];
+    if (c == 0 || (dim == 2 && which == 0)) continue;
+    const PencilLayout base = precision == IBDL_FP32_REFINED
+                                  ? solve_layout<float>(dim, n, which)
+                                  : solve_layout<double>(dim, n, which);
+    const bool ok = precision == IBDL_FP32_REFINED
+                        ? pencils_admissible<float>(n, base.estride, base.pg, c)
+                        : pencils_admissible<double>(n, base.estride, base.pg, c);
+    if (!ok) return fail(IBDL_ERR_INVALID_ARG, "pencils per item: not admissible");
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return fail(IBDL_ERR_CUDA, "cudaGetDevice");
+  const auto key = std::make_tuple(dev, (int)dim, (int)n, (int)precision);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (c_solve == 0 && c_y == 0)
+    g_tuned_pc.erase(key);
+  else
+    g_tuned_pc[key] = {c_y, c_solve};
+  return IBDL_OK;
+}
+
 ibdl_status ibdl_tuning_set(int32_t dim, int32_t n, int32_t precision, int32_t rows) {
   if ((dim != 2 && dim != 3) || n < 16 || n > (dim == 2 ? kMaxN2 : kMaxN3) || (n & (n - 1)) ||
       precision < IBDL_FP64 || precision > IBDL_FP32_REFINED || rows < 0)
@@ -1825,7 +1985,8 @@ int64_t estimate_request_bytes(const ibdl_geometry_desc& d) {
   const int64_t ntiles = (n / rows) * (d.dim == 3 ? n : 1);
   const int64_t ld = (m + 31) / 32 * 32;
   int64_t b = 7 * m * 8 + 3 * m * 4 + 12 * m * 8 + 12 * m * 4;      // points, delta weights
-  b += 2 * (ntiles + 1) * 4 + (d.dim == 3 ? 18 : 3) * m * 4;        // tile lists
+  b += 3 * (ntiles + 1) * 4 + 2 * (d.dim == 3 ? 18 : 3) * m * 4;    // tile lists (two orders)
+  b += 4;                                                            // error word
   b += spec * 16 + ncells * 8 + ntw * 16 + n * 8;                   // float64 spectral
   if (d.precision == IBDL_FP32_REFINED) b += spec * 8 + ncells * 4 + ntw * 8 + n * 4;
   b += (65 * ld + 65 * 64 + 3 * 64 + 65 + 8 + 7 * ld) * 8;          // Krylov, vectors

@@ -311,7 +311,47 @@ template <typename T> struct GlobalPencils {
   int npl;                     // pencils of the item (the rest are idle)
   int lgc;                     // log2 of the item's pencil count (strided)
   const unsigned char* zempty; // strided only; may be null
+  // shared input (SIN): the item's strided pencils as a dense box in shared
+  // memory, element t of pencil pen at sin[t * ld + pen] (a bulk tensor copy)
+  const cx_t<T>* sin;
+  int ld;
+  // SIN: once the first pass has read the box, thread 0 starts the copy of
+  // item tma_next (>= 0) into it
+  const struct TmaItem* tma;
+  int tma_next;
 };
+
+// The bulk tensor copy of one staged z-pass item (k_tma.cu): the tensor map,
+// the mbarrier the copy completes on, the box in shared memory and the
+// item geometry (c pencils per item, n points, zb z rows per copy).
+struct TmaItem {
+  const void* map;
+  uint64_t* bar;
+  void* box;
+  int c, n, lgn, zb, words, row_bytes;
+  unsigned bytes;
+};
+
+// Starts the copy of item k's box (thread 0 only): c pencils of slab kx from
+// y0, all n z rows, in copies of at most zb rows.  The box was last read with
+// ordinary loads, so the async proxy is fenced first.
+__device__ __forceinline__ void tma_issue_item(const TmaItem& t, int k) {
+  const int p0 = k * t.c, kx = p0 >> t.lgn, y0 = p0 & (t.n - 1);
+  const uint32_t bar = (uint32_t)__cvta_generic_to_shared(t.bar);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+               "r"(t.bytes)
+               : "memory");
+  for (int z0 = 0; z0 < t.n; z0 += t.zb) {
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(
+        reinterpret_cast<unsigned char*>(t.box) + (size_t)z0 * t.row_bytes);
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(t.map)), "r"(y0 * t.words), "r"(z0), "r"(kx), "r"(bar)
+        : "memory");
+  }
+}
 
 // Float and double transforms of the solver's pencil passes read their
 // first inputs from and write their last outputs to global memory, and
@@ -333,7 +373,7 @@ template <> struct DirectPencils<dd> { static constexpr bool value = false; };
 // as two real rows, its real parts to rows[2 pen n + t] and its imaginary
 // parts to rows[(2 pen + 1) n + t] (the x inverse pass).
 template <typename T, int LG, int S, bool INV, bool SYM = false, bool GIN = false,
-          bool GOUT = false, bool STR = false, typename RO = void>
+          bool GOUT = false, bool STR = false, typename RO = void, bool SIN = false>
 __device__ __forceinline__ void fft_pass(const cx_t<T>* __restrict__ src,
                                          cx_t<T>* __restrict__ dst, int npen,
                                          const cx_t<T>* __restrict__ tws,
@@ -362,7 +402,18 @@ __device__ __forceinline__ void fft_pass(const cx_t<T>* __restrict__ src,
     if (kGlobal && pen >= gio.npl) continue;
     const int k = j & (NS - 1);
     C a[R];
-    if constexpr (GIN) {
+    if constexpr (GIN && SIN) {
+      // the strided pencils staged as a dense box in shared memory
+      const C* xs = gio.sin + j * gio.ld + pen;
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        if (gio.zempty && gio.zempty[j + q * NB]) {
+          a[q].x = a[q].y = 0;
+        } else {
+          a[q] = xs[q * NB * gio.ld];
+        }
+      }
+    } else if constexpr (GIN) {
       if constexpr (STR) {
         const C* xg = gio.p + (size_t)j * N + pen;
 #pragma unroll
@@ -450,8 +501,12 @@ __device__ __forceinline__ void fft_pass(const cx_t<T>* __restrict__ src,
 // All passes of one transform direction.  Pass s reads buffer s mod 2 and
 // writes buffer (s + 1) mod 2 of (a, b); returns the buffer of the result
 // (meaningless when GOUT).
+// SIN: the first pass reads the staged box (gio.sin).  HOOK: before the last
+// pass (after the barrier that ends the pass before it), thread 0 starts the
+// bulk copy of the next item (gio.tma_next >= 0) into the staging box, which
+// the passes before have finished with.
 template <typename T, int LG, bool INV, bool SYM, bool GIN, bool GOUT, bool STR,
-          typename RO = void>
+          typename RO = void, bool SIN = false, bool HOOK = false>
 __device__ __forceinline__ cx_t<T>* fft_passes(cx_t<T>* a, cx_t<T>* b, int npen,
                                                const cx_t<T>* __restrict__ tws,
                                                const SymbolEpi<T>& epi,
@@ -463,12 +518,21 @@ __device__ __forceinline__ cx_t<T>* fft_passes(cx_t<T>* a, cx_t<T>* b, int npen,
   // the strided order only where a pass touches global memory
   constexpr bool ST0 = STR && (GIN || (GOUT && NP == 1));
   constexpr bool ST1 = STR && GOUT && NP == 2, ST2 = STR && GOUT && NP == 3;
-  fft_pass<T, LG, 0, INV, SYM && NP == 1, GIN, GOUT && NP == 1, ST0, RO>(a, b, npen, tws, epi,
-                                                                         gio, rows);
+  if constexpr (HOOK && NP == 1) {
+    if (threadIdx.x == 0 && gio.tma_next >= 0) tma_issue_item(*gio.tma, gio.tma_next);
+  }
+  fft_pass<T, LG, 0, INV, SYM && NP == 1, GIN, GOUT && NP == 1, ST0, RO, SIN && GIN>(
+      a, b, npen, tws, epi, gio, rows);
   if (NP == 1) return b;
+  if constexpr (HOOK && NP == 2) {
+    if (threadIdx.x == 0 && gio.tma_next >= 0) tma_issue_item(*gio.tma, gio.tma_next);
+  }
   fft_pass<T, LG, S1, INV, SYM && NP == 2, false, GOUT && NP == 2, ST1, RO>(b, a, npen, tws, epi,
                                                                              gio, rows);
   if (NP == 2) return a;
+  if constexpr (HOOK && NP == 3) {
+    if (threadIdx.x == 0 && gio.tma_next >= 0) tma_issue_item(*gio.tma, gio.tma_next);
+  }
   fft_pass<T, LG, S2, INV, SYM, false, GOUT, ST2, RO>(a, b, npen, tws, epi, gio, rows);
   return b;
 }
@@ -484,34 +548,37 @@ __device__ __noinline__ cx_t<T>* fft_run_lg(cx_t<T>* src, cx_t<T>* dst, int npen
 // memory (gio): MODE 0 forward, 1 inverse, 2 forward with the symbol
 // multiply on its last pass, then inverse.  bufA/bufB are the shared pencil
 // buffers of npen pencils.
-template <typename T, int LG, int MODE, bool STR>
+template <typename T, int LG, int MODE, bool STR, bool SIN = false>
 __device__ __noinline__ void fft_global_lg(cx_t<T>* bufA, cx_t<T>* bufB, int npen,
                                            const cx_t<T>* __restrict__ tws,
                                            const SymbolEpi<T> epi, const GlobalPencils<T> gio) {
   if constexpr (MODE == 2) {
-    cx_t<T>* r = fft_passes<T, LG, false, true, true, false, STR>(bufA, bufB, npen, tws, epi, gio);
+    // SIN: bufA is the staging box (sized for a padded buffer), reused as a
+    // ping-pong buffer once the first pass has read it
+    cx_t<T>* r = fft_passes<T, LG, false, true, true, false, STR, void, SIN>(bufA, bufB, npen,
+                                                                              tws, epi, gio);
     cx_t<T>* o = (r == bufA) ? bufB : bufA;
-    fft_passes<T, LG, true, false, false, true, STR>(r, o, npen, tws, epi, gio);
+    fft_passes<T, LG, true, false, false, true, STR, void, false, SIN>(r, o, npen, tws, epi, gio);
   } else {
     fft_passes<T, LG, MODE == 1, false, true, true, STR>(bufA, bufB, npen, tws, epi, gio);
   }
 }
 
-template <typename T, int MODE, bool STR>
+template <typename T, int MODE, bool STR, bool SIN = false>
 __device__ __forceinline__ void fft_global(cx_t<T>* bufA, cx_t<T>* bufB, int lg, int npen,
                                            const cx_t<T>* __restrict__ tws,
                                            const SymbolEpi<T>& epi, const GlobalPencils<T>& gio) {
   static_assert(DirectPencils<T>::value, "double-float stages its pencils");
   switch (lg) {
-    case 4: return fft_global_lg<T, 4, MODE, STR>(bufA, bufB, npen, tws, epi, gio);
-    case 5: return fft_global_lg<T, 5, MODE, STR>(bufA, bufB, npen, tws, epi, gio);
-    case 6: return fft_global_lg<T, 6, MODE, STR>(bufA, bufB, npen, tws, epi, gio);
-    case 7: return fft_global_lg<T, 7, MODE, STR>(bufA, bufB, npen, tws, epi, gio);
-    case 8: return fft_global_lg<T, 8, MODE, STR>(bufA, bufB, npen, tws, epi, gio);
-    case 9: return fft_global_lg<T, 9, MODE, STR>(bufA, bufB, npen, tws, epi, gio);
-    case 10: return fft_global_lg<T, 10, MODE, STR>(bufA, bufB, npen, tws, epi, gio);
-    case 11: return fft_global_lg<T, 11, MODE, STR>(bufA, bufB, npen, tws, epi, gio);
-    default: return fft_global_lg<T, 12, MODE, STR>(bufA, bufB, npen, tws, epi, gio);
+    case 4: return fft_global_lg<T, 4, MODE, STR, SIN>(bufA, bufB, npen, tws, epi, gio);
+    case 5: return fft_global_lg<T, 5, MODE, STR, SIN>(bufA, bufB, npen, tws, epi, gio);
+    case 6: return fft_global_lg<T, 6, MODE, STR, SIN>(bufA, bufB, npen, tws, epi, gio);
+    case 7: return fft_global_lg<T, 7, MODE, STR, SIN>(bufA, bufB, npen, tws, epi, gio);
+    case 8: return fft_global_lg<T, 8, MODE, STR, SIN>(bufA, bufB, npen, tws, epi, gio);
+    case 9: return fft_global_lg<T, 9, MODE, STR, SIN>(bufA, bufB, npen, tws, epi, gio);
+    case 10: return fft_global_lg<T, 10, MODE, STR, SIN>(bufA, bufB, npen, tws, epi, gio);
+    case 11: return fft_global_lg<T, 11, MODE, STR, SIN>(bufA, bufB, npen, tws, epi, gio);
+    default: return fft_global_lg<T, 12, MODE, STR, SIN>(bufA, bufB, npen, tws, epi, gio);
   }
 }
 
@@ -592,6 +659,57 @@ __device__ __forceinline__ void copy_to_shared(V* dst, const V* __restrict__ src
   }
 }
 
+// Shared-memory tables: the twiddles (ntw complex) and the sin^2 table (ns
+// reals, ns = 0 for none), copied with all of a thread's loads of a batch in
+// flight before its first store, so that tables of up to KB * blockDim
+// entries cost one L2 round trip (a batch per KB * blockDim entries).  The
+// loads are issued first, the stores come when `stage_tables_store` runs, so
+// a caller can overlap other global loads with them.
+template <typename V> struct TabVec { using type = V; };
+template <> struct TabVec<cdd> { using type = float4; };
+template <> struct TabVec<dd> { using type = float2; };
+
+template <typename T, int KB> struct TableStage {
+  using C = cx_t<T>;
+  using VC = typename TabVec<C>::type;
+  using VT = typename TabVec<T>::type;
+  VC a[KB];
+  VT b[KB];
+  __device__ __forceinline__ void load(const C* __restrict__ tw, int ntw, const T* __restrict__ s2,
+                                       int ns, int base) {
+    const VC* tv = reinterpret_cast<const VC*>(tw);
+    const VT* sv = reinterpret_cast<const VT*>(s2);
+#pragma unroll
+    for (int u = 0; u < KB; ++u) {
+      const int e = base + threadIdx.x + u * blockDim.x;
+      if (e < ntw) a[u] = __ldcg(tv + e);
+      if (e < ns) b[u] = __ldcg(sv + e);
+    }
+  }
+  __device__ __forceinline__ void store(C* tws, int ntw, T* s2s, int ns, int base) const {
+    VC* tv = reinterpret_cast<VC*>(tws);
+    VT* sv = reinterpret_cast<VT*>(s2s);
+#pragma unroll
+    for (int u = 0; u < KB; ++u) {
+      const int e = base + threadIdx.x + u * blockDim.x;
+      if (e < ntw) tv[e] = a[u];
+      if (e < ns) sv[e] = b[u];
+    }
+  }
+  // everything past the first batch (large n or few threads), copied at once
+  __device__ __forceinline__ void rest(const C* __restrict__ tw, C* tws, int ntw,
+                                       const T* __restrict__ s2, T* s2s, int ns) {
+    for (int base = KB * blockDim.x; base < ntw || base < ns; base += KB * blockDim.x) {
+      load(tw, ntw, s2, ns, base);
+      store(tws, ntw, s2s, ns, base);
+    }
+  }
+};
+
+// Entries per thread of a table batch: twiddles of an n <= 1024 FFT
+// (1168 entries) in one batch of 256 threads.
+constexpr int kTabBatch = 5;
+
 // Two consecutive complex values as one 16-byte access (float) or two
 // (double).  Even element indices keep the float pair 16-byte aligned.
 template <typename T> struct Pair;
@@ -634,11 +752,8 @@ template <> struct Pair<dd> {
   }
 };
 
-// The precision of the spread (shared-memory atomics) for transforms in T:
-// double-float transforms take a float64 spread, converted once per tile.
-template <typename T> struct SpreadType { using type = T; };
-template <> struct SpreadType<dd> { using type = double; };
-
+// The spread runs in the transforms' own arithmetic: float, float64, or
+// double-float (the spread gathers without atomics, so any type works).
 template <typename T> __device__ __forceinline__ T wload(const PointData& p, int c, int t, int i);
 template <> __device__ __forceinline__ double wload<double>(const PointData& p, int c, int t,
                                                             int i) {
@@ -647,6 +762,9 @@ template <> __device__ __forceinline__ double wload<double>(const PointData& p, 
 template <> __device__ __forceinline__ float wload<float>(const PointData& p, int c, int t,
                                                           int i) {
   return (t >= 0 && t < 4) ? p.W32[c][t * p.m + i] : 0.0f;
+}
+template <> __device__ __forceinline__ dd wload<dd>(const PointData& p, int c, int t, int i) {
+  return (t >= 0 && t < 4) ? dd(p.W64[c][t * p.m + i]) : dd(0);
 }
 
 // Point normal component c and weight / h^d in the spread's precision.
@@ -657,12 +775,33 @@ template <> __device__ __forceinline__ double pt_nrm<double>(const PointData& p,
 template <> __device__ __forceinline__ float pt_nrm<float>(const PointData& p, int c, int i) {
   return p.nrm32[c][i];
 }
+template <> __device__ __forceinline__ dd pt_nrm<dd>(const PointData& p, int c, int i) {
+  return dd(p.nrm[c][i]);
+}
 template <typename T> __device__ __forceinline__ T pt_w(const PointData& p, int i);
 template <> __device__ __forceinline__ double pt_w<double>(const PointData& p, int i) {
   return p.w[i];
 }
 template <> __device__ __forceinline__ float pt_w<float>(const PointData& p, int i) {
   return p.w32[i];
+}
+template <> __device__ __forceinline__ dd pt_w<dd>(const PointData& p, int i) {
+  return dd(p.w[i]);
+}
+
+template <typename T> __device__ __forceinline__ bool is_zero(T v) { return v == (T)0; }
+template <> __device__ __forceinline__ bool is_zero<dd>(dd v) { return v.hi == 0.0f; }
+
+// First index in [p, np) whose sorted key sx[] is >= v (np if none), found by
+// the 32 lanes of a warp together; every lane returns the same index.
+__device__ __forceinline__ int warp_lower_bound(const int* sx, int p, int np, int v) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    const int idx = p + lane;
+    const unsigned lt = __ballot_sync(0xffffffffu, idx < np && sx[idx] < v);
+    if (lt != 0xffffffffu) return p + __popc(lt);  // keys are sorted: a prefix
+    p += 32;
+  }
 }
 
 // Rows per tile of the x passes: 2D keeps 4 (2 for n = 2048) so that even a
@@ -682,78 +821,160 @@ __host__ __device__ __forceinline__ size_t rows_smem_bytes(int n, int rows) {
   return (2 * (size_t)(rows / 2) * pen_stride(n) + (size_t)ntw) * sizeof(cx_t<T>);
 }
 
-// ---- fused spread + forward x pass ------------------------------------------
-//
-// Tile = R rows y0..y0+R-1 at plane z.  The rows are zeroed (or seeded with
-// coef_grid * f) in shared memory, then every (point, box node) pair of the
-// tile's bin adds its share with a shared-memory atomic:
-//
-//   S~q at node (bx-1+a, by-1+b, bz-1+c) (Sec. 5.2, the centred difference of
-//   the spread of q n, fused):  q w/h^d [ nx dW_x[a] W_y[b-1] W_z[c-1]
-//        + ny W_x[a-1] dW_y[b] W_z[c-1] + nz W_x[a-1] W_y[b-1] dW_z[c] ],
-//   dW[a] = (W[a] - W[a-2]) / (2h),  W[t] = 0 outside t = 0..3;
-//   S v at the same node:  v w/h^d W_x[a-1] W_y[b-1] W_z[c-1].
-//
-// Then two real rows are packed as one complex row, FFT'd along x, separated
-// (A_k = (Z_k + conj Z_{n-k})/2, B_k = (Z_k - conj Z_{n-k})/(2i)) and written
-// to the transposed half spectrum spec[k][z][y], k = 0..n/2.
-template <typename T, int D>
-__device__ __forceinline__ void phase_rows_fwd(const GridDesc& g, const PointData& p, const Bins& b,
-                               const SpreadSrc& src, cx_t<T>* spec,
-                               const cx_t<T>* __restrict__ tw, double* write_grid, int tile,
-                               unsigned char* smem) {
-  using C = cx_t<T>;
-  using S = typename SpreadType<T>::type;  // the spread's precision
-  const int n = g.n, lg = g.log2n, mask = n - 1, R = b.rows, npen = R >> 1;
-  const int lgnp = __ffs(npen) - 1;  // R is a power of two (checked when the tiles are built)
+// Gather spread of one tile (double-float).  rows holds the tile's R rows in
+// the interleaved pencil layout; sbuf (bytes) is the staging space for the
+// chunks' point records.  A tile's bin is sorted by the point's first
+// support column xs (then by index), so the points that reach a run of
+// columns are a contiguous run of the bin.  The 32 lanes of a warp own 32
+// nodes -- R rows of 32/R neighbouring columns -- and walk that run
+// together, each lane adding the shares that fall on its node in a register;
+// a node has exactly one owner, so no atomics are needed and the sum's order
+// is fixed (the spread is bitwise reproducible).  Warps take the column
+// groups in turn.  The sorted lists are b.spts.
+template <typename S, int D>
+__device__ __forceinline__ void spread_gather(const GridDesc& g, const PointData& p, const Bins& b,
+                                           const SpreadSrc& src, S* rows, unsigned char* sbuf,
+                                           size_t sbytes, int z, int y0, int lo, int hi) {
+  const int n = g.n, mask = n - 1, R = b.rows, lgR = __ffs(R) - 1;
   const int PS = pen_stride(n);
-  C* bufA = reinterpret_cast<C*>(smem);
-  C* bufB = bufA + (size_t)npen * PS;
-  C* tws = bufB + (size_t)npen * PS;
-  S* rows = reinterpret_cast<S*>(bufA);  // row r, column x at [((r>>1)*PS + padi(x))*2 + (r&1)]
-  const int ngroups = n / R;
-  const int z = (D == 3) ? tile / ngroups : 0;
-  const int y0 = (tile % ngroups) * R;
   const int tid = threadIdx.x, nt = blockDim.x;
-  const size_t row0 = ((size_t)z * n + y0) * n;
-  const int lo = b.start[tile], hi = b.start[tile + 1];
-  const int half = n >> 1;
-  const size_t slab = (D == 3) ? (size_t)n * n : (size_t)n;
-  const size_t pos0 = (size_t)z * n + y0;
-
-  if (D == 3 && src.skip_empty_planes && !src.f_grid && !write_grid && b.zempty &&
-      b.zempty[z])
-    return;  // a plane without points: zero, and read as zero by the z pass
-  if (lo == hi && !src.f_grid) {
-    // no source touches the tile: its rows, and so their spectrum, are zero
-    if (write_grid) {
-      for (int e = tid; e < R * n; e += nt) write_grid[row0 + e] = 0.0;
-    } else {
-      C zero;
-      zero.x = 0;
-      zero.y = 0;
-      for (int e = tid; e < (half + 1) * R; e += nt) {
-        const int k = e >> (lgnp + 1), a = e & (R - 1);
-        spec[(size_t)k * slab + pos0 + a] = zero;
+  // The tile's points are taken in chunks of KP (contiguous runs of the
+  // sorted bin).  Stage A (one thread per point) gathers each point's data
+  // with independent loads and stages, in bufB (unused until the FFT), its
+  // first column xs, first row yb and the node factors of its 6 x 6 box:
+  //   node (xs + a, yb + bb):  U[a] cA[bb] + V[a] cB[bb],
+  //   U[a] = W_x[a-1],  V[a] = W_x[a] - W_x[a-2],
+  //   cA[bb] = P dW_y[bb] + Q W_y[bb-1],  cB[bb] = X W_y[bb-1],
+  // P = q w/h^d ny W_z[c-1], Q = q w/h^d nz dW_z[c] + v w/h^d W_z[c-1],
+  // X = q w/h^d nx W_z[c-1] / (2h), c the plane offset (3D), W[t] = 0
+  // outside t = 0..3.  Stage B gathers (see above).
+  const S inv2h = (S)g.inv2h;
+  constexpr int kRec = 24;  // U[6], V[6], cA[6], cB[6]
+  const int per_pt = kRec * (int)sizeof(S) + 2 * (int)sizeof(int);
+  int KP = (int)(sbytes / per_pt);
+  if (KP > 512) KP = 512;
+  S* sv = reinterpret_cast<S*>(sbuf);  // [KP][kRec]
+  int* sxs = reinterpret_cast<int*>(sv + (size_t)kRec * KP);
+  int* syb = sxs + KP;
+  const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
+  const int cpg = 32 >> lgR;          // columns per lane group (R <= 32)
+  const int lr = lane & (R - 1);      // this lane's row of the tile
+  const int lc = lane >> lgR;         // this lane's column within the group
+  const int ncg = n / cpg;            // column groups
+  for (int c0 = lo; c0 < hi; c0 += KP) {
+    const int np = min(KP, hi - c0);
+    for (int t = tid; t < np; t += nt) {
+      const int i = __ldg(b.spts + c0 + t);
+      int ok = 1;
+      S wz = (S)1, dz = (S)0;
+      if (D == 3) {
+        const int cz = (z - (__ldg(p.base[2] + i) - 1)) & mask;
+        ok = cz < kBoxSide;
+        wz = wload<S>(p, 2, cz - 1, i);
+        dz = (wload<S>(p, 2, cz, i) - wload<S>(p, 2, cz - 2, i)) * inv2h;
       }
+      S P = 0, Q = 0, X = 0;
+      const S wi = pt_w<S>(p, i);
+      if (src.q_div) {
+        const S amp = (S)src.coef_div * (S)__ldcg(src.q_div + i) * wi;
+        P = amp * pt_nrm<S>(p, 1, i) * wz;
+        if (D == 3) Q = amp * pt_nrm<S>(p, 2, i) * dz;
+        X = amp * pt_nrm<S>(p, 0, i) * wz * inv2h;
+      }
+      if (src.v_plain) {
+        S v = (S)src.coef_plain * (S)__ldcg(src.v_plain + i) * wi * wz;
+        if (src.plain_nrm >= 0) v *= pt_nrm<S>(p, src.plain_nrm, i);
+        Q += v;
+      }
+      if (!ok) P = Q = X = 0;
+      S wx[4], wy[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        wx[u] = wload<S>(p, 0, u, i);
+        wy[u] = wload<S>(p, 1, u, i);
+      }
+      S* rec = sv + (size_t)t * kRec;
+#pragma unroll
+      for (int a = 0; a < kBoxSide; ++a) {
+        const S w1 = (a >= 1 && a <= 4) ? wx[a - 1] : (S)0;
+        const S w0 = a <= 3 ? wx[a] : (S)0;
+        const S w2 = (a >= 2) ? wx[a - 2] : (S)0;
+        rec[a] = w1;
+        rec[6 + a] = w0 - w2;
+        const S y1 = (a >= 1 && a <= 4) ? wy[a - 1] : (S)0;
+        const S y0v = a <= 3 ? wy[a] : (S)0;
+        const S y2 = (a >= 2) ? wy[a - 2] : (S)0;
+        rec[12 + a] = P * (y0v - y2) * inv2h + Q * y1;
+        rec[18 + a] = X * y1;
+      }
+      sxs[t] = (__ldg(p.base[0] + i) - 1) & mask;
+      syb[t] = __ldg(p.base[1] + i) - 1;
     }
-    return;
+    __syncthreads();
+    // Stage B: warp `warp` takes column groups warp, warp + nwarps, ...; the
+    // candidates of group g (first column x0) have xs in [x0 - 5, x0 + cpg - 1]
+    // (mod n).  plo / phi advance with g (the groups rise with x).
+    int plo = 0, phi = 0;
+    const bool all = cpg + kBoxSide - 1 >= n;  // the window covers every column
+    for (int gi = warp; gi < ncg; gi += nwarps) {
+      const int x0 = gi * cpg, x = x0 + lc;
+      int e0, e1, w0 = np, w1 = np;  // [e0, e1): main run; [w0, w1): wrapped run
+      if (all) {
+        e0 = 0;
+        e1 = np;
+      } else {
+        const int wl = x0 - (kBoxSide - 1);
+        plo = warp_lower_bound(sxs, plo, np, wl < 0 ? 0 : wl);
+        phi = warp_lower_bound(sxs, phi > plo ? phi : plo, np, x0 + cpg);
+        e0 = plo;
+        e1 = phi;
+        if (wl < 0) w0 = warp_lower_bound(sxs, phi, np, n + wl);  // points near x = n
+        if (e0 == e1 && w0 == w1) {
+          // no candidate: skip to the next group of this warp that can have one
+          if (plo >= np) break;
+          const int first = sxs[plo];  // the next candidate's column
+          const int gneed = (first - cpg + 1) / cpg;  // groups before it cannot reach it
+          if (gneed > gi + nwarps) gi += ((gneed - gi) / nwarps) * nwarps - nwarps;
+          continue;
+        }
+      }
+      S acc = 0;
+      const int yrow = y0 + lr;
+      for (int pass = 0; pass < 2; ++pass) {
+        const int ea = pass ? w0 : e0, eb = pass ? w1 : e1;
+        for (int e = ea; e < eb; ++e) {
+          const int a = (x - sxs[e]) & mask;
+          const int bb = (yrow - syb[e]) & mask;
+          if (a < kBoxSide && bb < kBoxSide) {
+            const S* rec = sv + (size_t)e * kRec;
+            acc += rec[a] * rec[12 + bb] + rec[6 + a] * rec[18 + bb];
+          }
+        }
+      }
+      if (!is_zero(acc)) rows[((lr >> 1) * PS + padi(x)) * 2 + (lr & 1)] += acc;
+    }
+    __syncthreads();
   }
 
-  for (int e = tid; e < R * n; e += nt) {
-    const int r = e >> lg, x = e & mask;
-    S v = 0;
-    if (src.f_grid) v = (S)(src.coef_grid * src.f_grid[row0 + (size_t)r * n + x]);
-    rows[((r >> 1) * PS + padi(x)) * 2 + (r & 1)] = v;
-  }
-  if (!write_grid) copy_to_shared(tws, tw, fft_tw_count(n));
-  __syncthreads();
+}
 
-  // The tile's points are taken in chunks of KP.  Stage A (one thread per
-  // point) gathers each point's data with independent loads and folds it
-  // into per-point coefficients, staged in bufB (unused until the FFT);
-  // stage B (one thread per (point, support row bb)) adds the 6 x nodes of
-  // that row.  With c = the plane offset (3D) and W[t] = 0 outside t = 0..3:
+// Scatter spread of one tile (float, float64): one thread per (point, support
+// row) adds the 6 nodes of that row with shared-memory atomics (native for
+// both types), so the sum's order varies with the atomics' order (rounding
+// only).  The bin is in fill order (about the points' index order), so the
+// threads of stage A load neighbouring points' data from neighbouring
+// addresses.
+template <typename S, int D>
+__device__ __forceinline__ void spread_scatter(const GridDesc& g, const PointData& p, const Bins& b,
+                                            const SpreadSrc& src, S* rows, unsigned char* sbuf,
+                                            size_t sbytes, int z, int y0, int lo, int hi) {
+  const int n = g.n, mask = n - 1, R = b.rows;
+  const int PS = pen_stride(n);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  // Stage A (one thread per point) gathers each point's data with
+  // independent loads and folds it into per-point coefficients; stage B (one
+  // thread per (point, support row bb)) adds the 6 x nodes of that row.
+  // With c = the plane offset (3D) and W[t] = 0 outside t = 0..3:
   //   node a: W_x[a-1] * cA + (W_x[a] - W_x[a-2]) * cB,
   //   cA = q w/h^d (ny dW_y[bb] W_z[c-1] + nz W_y[bb-1] dW_z[c]) + v w/h^d W_y[bb-1] W_z[c-1]
   //   cB = q w/h^d nx W_y[bb-1] W_z[c-1] / (2h),
@@ -761,9 +982,9 @@ __device__ __forceinline__ void phase_rows_fwd(const GridDesc& g, const PointDat
   const S inv2h = (S)g.inv2h;
   constexpr int kWords = 11;  // wx[4], wy[4], P, Q, X
   const int per_pt = kWords * (int)sizeof(S) + 2 * (int)sizeof(int);
-  int KP = (int)((size_t)npen * PS * sizeof(C) / per_pt);
+  int KP = (int)(sbytes / per_pt);
   if (KP > 256) KP = 256;
-  S* sv = reinterpret_cast<S*>(bufB);         // [kWords][KP]
+  S* sv = reinterpret_cast<S*>(sbuf);  // [kWords][KP]
   int* sxb = reinterpret_cast<int*>(sv + kWords * KP);
   int* syb = sxb + KP;
   for (int c0 = lo; c0 < hi; c0 += KP) {
@@ -836,6 +1057,94 @@ __device__ __forceinline__ void phase_rows_fwd(const GridDesc& g, const PointDat
     }
     __syncthreads();
   }
+}
+
+// The spread of a tile gathers (no atomics) in double-float, which has no
+// atomic add and whose float64 alternative runs on GB300's slow float64
+// pipe; float and float64 scatter with native shared-memory atomics, which
+// measured faster for them (a gather walks every candidate point of a
+// column group with all 32 lanes).
+template <typename T> struct SpreadGathers { static constexpr bool value = false; };
+template <> struct SpreadGathers<dd> { static constexpr bool value = true; };
+
+// ---- fused spread + forward x pass ------------------------------------------
+//
+// Tile = R rows y0..y0+R-1 at plane z.  The rows are zeroed (or seeded with
+// coef_grid * f) in shared memory, then every node of the tile gathers the
+// shares of the points in the tile's bin:
+//
+//   S~q at node (bx-1+a, by-1+b, bz-1+c) (Sec. 5.2, the centred difference of
+//   the spread of q n, fused):  q w/h^d [ nx dW_x[a] W_y[b-1] W_z[c-1]
+//        + ny W_x[a-1] dW_y[b] W_z[c-1] + nz W_x[a-1] W_y[b-1] dW_z[c] ],
+//   dW[a] = (W[a] - W[a-2]) / (2h),  W[t] = 0 outside t = 0..3;
+//   S v at the same node:  v w/h^d W_x[a-1] W_y[b-1] W_z[c-1].
+//
+// Then two real rows are packed as one complex row, FFT'd along x, separated
+// (A_k = (Z_k + conj Z_{n-k})/2, B_k = (Z_k - conj Z_{n-k})/(2i)) and written
+// to the transposed half spectrum spec[k][z][y], k = 0..n/2.  The spread
+// runs in the transforms' arithmetic T: scattered with atomics (float,
+// float64) or gathered (double-float), see SpreadGathers.
+template <typename T, int D>
+__device__ __forceinline__ void phase_rows_fwd(const GridDesc& g, const PointData& p, const Bins& b,
+                               const SpreadSrc& src, cx_t<T>* spec,
+                               const cx_t<T>* __restrict__ tw, double* write_grid, int tile,
+                               unsigned char* smem) {
+  using C = cx_t<T>;
+  using S = T;  // the spread's arithmetic
+  const int n = g.n, lg = g.log2n, mask = n - 1, R = b.rows, npen = R >> 1;
+  const int lgnp = __ffs(npen) - 1;  // R is a power of two (checked when the tiles are built)
+  const int PS = pen_stride(n);
+  C* bufA = reinterpret_cast<C*>(smem);
+  C* bufB = bufA + (size_t)npen * PS;
+  C* tws = bufB + (size_t)npen * PS;
+  S* rows = reinterpret_cast<S*>(bufA);  // row r, column x at [((r>>1)*PS + padi(x))*2 + (r&1)]
+  const int ngroups = n / R;
+  const int z = (D == 3) ? tile / ngroups : 0;
+  const int y0 = (tile % ngroups) * R;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const size_t row0 = ((size_t)z * n + y0) * n;
+  const int lo = b.start[tile], hi = b.start[tile + 1];
+  const int half = n >> 1;
+  const size_t slab = (D == 3) ? (size_t)n * n : (size_t)n;
+  const size_t pos0 = (size_t)z * n + y0;
+
+  if (D == 3 && src.skip_empty_planes && !src.f_grid && !write_grid && b.zempty &&
+      b.zempty[z])
+    return;  // a plane without points: zero, and read as zero by the z pass
+  if (lo == hi && !src.f_grid) {
+    // no source touches the tile: its rows, and so their spectrum, are zero
+    if (write_grid) {
+      for (int e = tid; e < R * n; e += nt) write_grid[row0 + e] = 0.0;
+    } else {
+      C zero;
+      zero.x = 0;
+      zero.y = 0;
+      for (int e = tid; e < (half + 1) * R; e += nt) {
+        const int k = e >> (lgnp + 1), a = e & (R - 1);
+        spec[(size_t)k * slab + pos0 + a] = zero;
+      }
+    }
+    return;
+  }
+
+  for (int e = tid; e < R * n; e += nt) {
+    const int r = e >> lg, x = e & mask;
+    S v = 0;
+    if (src.f_grid) v = (S)(src.coef_grid * src.f_grid[row0 + (size_t)r * n + x]);
+    rows[((r >> 1) * PS + padi(x)) * 2 + (r & 1)] = v;
+  }
+  if (!write_grid) copy_to_shared(tws, tw, fft_tw_count(n));
+  __syncthreads();
+
+  const size_t sbytes = (size_t)npen * PS * sizeof(C);  // bufB, unused until the FFT
+  if (lo < hi) {
+    if constexpr (SpreadGathers<T>::value)
+      spread_gather<S, D>(g, p, b, src, rows, reinterpret_cast<unsigned char*>(bufB), sbytes, z,
+                          y0, lo, hi);
+    else
+      spread_scatter<S, D>(g, p, b, src, rows, reinterpret_cast<unsigned char*>(bufB), sbytes,
+                           z, y0, lo, hi);
+  }
 
   if (write_grid) {
     for (int e = tid; e < R * n; e += nt) {
@@ -846,12 +1155,6 @@ __device__ __forceinline__ void phase_rows_fwd(const GridDesc& g, const PointDat
     return;
   }
 
-  if (!std::is_same<S, T>::value) {
-    // float64 spread -> double-float, in place (each thread its own slots)
-    T* rt = reinterpret_cast<T*>(bufA);
-    for (int e = tid; e < npen * PS * 2; e += nt) rt[e] = T(rows[e]);
-    __syncthreads();
-  }
   C* res = fft_run<T, false>(bufA, bufB, lg, npen, tws);
 
   for (int e = tid; e < (half + 1) * npen; e += nt) {
@@ -883,8 +1186,9 @@ struct PencilLayout {
 // c: pencils per work item (a power of two <= 16): at most pg when the
 // pencils are strided, shared memory (pencil buffers + tables) within 100 KB
 // so that two blocks of the persistent solver fit on an SM (with its ~7 KB
-// of static shared memory), and small enough that a pass over contiguous
-// pencils has >= 256 items when it can.
+// of static shared memory), and -- by the fixed rule -- small enough that a
+// pass over contiguous pencils has >= 256 items when it can.  want > 0 (the
+// autotuner's choice) replaces the rule when it is admissible.
 template <typename T>
 __host__ __device__ inline size_t pencil_smem_for(int n, int c) {
   const int ntw = fft_tw_count(n);
@@ -894,8 +1198,16 @@ __host__ __device__ inline size_t pencil_smem_for(int n, int c) {
 }
 
 template <typename T>
+__host__ __device__ inline bool pencils_admissible(int n, int64_t estride, int pg, int c) {
+  if (c < 1 || c > 16 || (c & (c - 1))) return false;
+  if (estride != 1 && (c < 2 || c > pg)) return false;
+  return pencil_smem_for<T>(n, c) <= 100 * 1024;
+}
+
+template <typename T>
 __host__ __device__ inline PencilLayout pencil_layout(int n, int64_t gstride, int64_t bstride,
-                                                      int64_t estride, int pg, int npencils) {
+                                                      int64_t estride, int pg, int npencils,
+                                                      int want = 0) {
   PencilLayout L;
   L.gstride = gstride;
   L.bstride = bstride;
@@ -907,6 +1219,7 @@ __host__ __device__ inline PencilLayout pencil_layout(int n, int64_t gstride, in
   while (c > 1 && pencil_smem_for<T>(n, c) > 100 * 1024) c >>= 1;
   while (c > 1 && npencils / c < 256 && estride == 1) c >>= 1;
   if (estride != 1 && c < 2) c = 2;  // strided items move pencils in pairs
+  if (want > 0 && pencils_admissible<T>(n, estride, pg, want)) c = want;
   L.c = c;
   L.lgc = 0;
   while ((1 << L.lgc) < c) ++L.lgc;
@@ -919,12 +1232,20 @@ __host__ __device__ inline PencilLayout pencil_layout(int n, int64_t gstride, in
 // forward + multiply + inverse); 3D has three: y forward on (kx, z),
 // z forward + multiply + inverse on (kx, y), y inverse on (kx, z).
 template <typename T>
-__host__ __device__ inline PencilLayout solve_layout(int dim, int n, int which) {
+__host__ __device__ inline PencilLayout solve_layout(int dim, int n, int which, int want = 0) {
   const int half = n / 2;
-  if (dim == 2) return pencil_layout<T>(n, n, 0, 1, 1, half + 1);
+  if (dim == 2) return pencil_layout<T>(n, n, 0, 1, 1, half + 1, want);
   const int64_t n2 = (int64_t)n * n;
-  if (which == 1) return pencil_layout<T>(n, n2, 1, n, n, (half + 1) * n);
-  return pencil_layout<T>(n, n2, n, 1, n, (half + 1) * n);
+  if (which == 1) return pencil_layout<T>(n, n2, 1, n, n, (half + 1) * n, want);
+  return pencil_layout<T>(n, n2, n, 1, n, (half + 1) * n, want);
+}
+
+// The layout of a geometry's pencil pass `which` (1: the solve pass) in
+// element type T, with the autotuner's pencils per item.
+template <typename T>
+__host__ __device__ inline PencilLayout solve_layout(const GridDesc& g, int which) {
+  const int cls = sizeof(T) == 4 ? 0 : 1;
+  return solve_layout<T>(g.dim, g.n, which, g.pcap[cls][g.dim == 2 ? 1 : which]);
 }
 
 // pencil buffers, twiddles, sin^2 table
@@ -932,6 +1253,21 @@ template <typename T>
 __host__ __device__ inline size_t pencil_smem_bytes(const PencilLayout& L, int n) {
   return pencil_smem_for<T>(n, L.c);
 }
+
+// Threads per block of the launch-based pencil passes: one per butterfly of
+// the FFT pass with the most butterflies (n over the smallest radix of the
+// plan, per pencil) -- more would idle in the FFT passes and thin the
+// per-thread work over which an item's fixed cost is spread.  Row tiles take
+// n/8 per pencil: their spread stage wants the extra threads.
+inline int clamp_threads(int t) { return t < 64 ? 64 : (t > 512 ? 512 : t); }
+inline int pencil_threads(int n, int c) {
+  const int lg = ilog2(n);
+  int min_lr = 4;
+  for (int s = 0; s < plan_npass(lg); ++s)
+    if (plan_lr(lg, s) < min_lr) min_lr = plan_lr(lg, s);
+  return clamp_threads(c * (n >> min_lr));
+}
+
 
 // MODE 0: forward, 1: inverse, 2: forward, multiply by
 // scale0 / (c0 + cfac * sum_c sin^2(pi k_c / n)) (c0 = 1; c0 = 0 and the
@@ -976,8 +1312,13 @@ __device__ __forceinline__ void phase_pencils(const GridDesc& g, const PencilLay
       // the transforms read and write global memory in their first and
       // last passes (the strided forward and inverse-only transforms of
       // the spectral discretisation stage their pencils below)
-      copy_to_shared(tws, tw, ntw);
-      if (MODE == 2) copy_to_shared(s2s, s2, n);
+      {
+        TableStage<T, kTabBatch> ts;
+        const int ns = MODE == 2 ? n : 0;
+        ts.load(tw, ntw, s2, ns, 0);
+        ts.store(tws, ntw, s2s, ns, 0);
+        ts.rest(tw, tws, ntw, s2, s2s, ns);
+      }
       __syncthreads();
       // 2D: pencil kx = p0 + pl, position ky = t; 3D: kx = gi0, ky = q0 + pl, kz = t
       SymbolEpi<T> epi{};
@@ -990,7 +1331,7 @@ __device__ __forceinline__ void phase_pencils(const GridDesc& g, const PencilLay
         epi.pbase = g.dim == 3 ? q0 : p0;
         epi.npl = npl;
       }
-      GlobalPencils<T> gio;
+      GlobalPencils<T> gio{};
       gio.p = base;
       gio.npl = npl;
       gio.lgc = lgc;
@@ -1006,7 +1347,12 @@ __device__ __forceinline__ void phase_pencils(const GridDesc& g, const PencilLay
   // pair k: contiguous -> elements 2k, 2k+1 of the item (one pencil, t even);
   // strided -> pencils pl, pl+1 (pl even) at position t.  npl is even or 1
   // in the strided case (c | pg, pg a power of two), so pairs never straddle.
-  constexpr int U = sizeof(T) == 4 ? 4 : 2;
+  // The first batch of pairs and the tables are loaded together (one L2
+  // round trip), then stored.
+  constexpr int U = 4;
+  TableStage<T, kTabBatch> ts;
+  const int ns = MODE == 2 ? n : 0;
+  ts.load(tw, ntw, s2, ns, 0);
   for (int k0 = tid; k0 < npairs; k0 += U * nt) {
     Pair<T> v[U];
 #pragma unroll
@@ -1044,8 +1390,8 @@ __device__ __forceinline__ void phase_pencils(const GridDesc& g, const PencilLay
       }
     }
   }
-  copy_to_shared(tws, tw, ntw);
-  if (MODE == 2) copy_to_shared(s2s, s2, n);
+  ts.store(tws, ntw, s2s, ns, 0);
+  ts.rest(tw, tws, ntw, s2, s2s, ns);
   __syncthreads();
 
   C* res = fft_run<T, MODE == 1>(bufA, bufB, lg, c, tws);
@@ -1114,6 +1460,10 @@ __device__ __forceinline__ void phase_rows_inv(const GridDesc& g, const Bins& b,
 
   constexpr int U = sizeof(T) == 4 ? 4 : 2;
   const int total = (half + 1) * npen;
+  // the twiddles load together with the first batch of the spectrum
+  const int ntw = fft_tw_count(n);
+  TableStage<T, kTabBatch> ts;
+  ts.load(tw, ntw, nullptr, 0, 0);
   for (int e0 = tid; e0 < total; e0 += U * nt) {
     C A[U], B[U];
 #pragma unroll
@@ -1149,7 +1499,8 @@ __device__ __forceinline__ void phase_rows_inv(const GridDesc& g, const Bins& b,
       }
     }
   }
-  copy_to_shared(tws, tw, fft_tw_count(n));
+  ts.store(tws, ntw, nullptr, 0, 0);
+  ts.rest(tw, tws, ntw, nullptr, nullptr, 0);
   __syncthreads();
   const size_t row0 = ((size_t)z * n + y0) * n;
   if constexpr (DirectPencils<T>::value) {
@@ -1174,6 +1525,12 @@ template <> __device__ __forceinline__ const double* wtab<double>(const PointDat
 }
 template <> __device__ __forceinline__ const float* wtab<float>(const PointData& p, int c) {
   return p.W32[c];
+}
+
+// Weight t of axis c of point i in T (W[c][t * m + i]).
+template <typename T>
+__device__ __forceinline__ T interp_w(const PointData& p, int c, int t, int i, int m) {
+  return wtab<T>(p, c)[t * m + i];
 }
 
 // Grid load of the interpolation: around L1 (ld.global.cg) where another

@@ -74,7 +74,9 @@ struct Bins {
   int rows = 4;              // R: y rows per tile (even)
   int ntiles = 0;            // n^(d-2) * (n / R)
   const int* start = nullptr;  // ntiles + 1
-  const int* pts = nullptr;
+  const int* pts = nullptr;    // per tile: points in fill order (about index order)
+  const int* spts = nullptr;   // the same lists sorted by first support column, then
+                               // index (the gather spread's order)
   const unsigned char* zempty = nullptr;  // 3D: 1 for z planes no point touches
 };
 
@@ -94,6 +96,10 @@ struct GridDesc {
   // 1: the Fourier-spectral discretisation (Sec. 5.1, Sec. 6.2.1): spectral
   // Laplacian in the solve, spectral divergence in S~ (Sec. 5.2)
   int spectral = 0;
+  // pencils per work item of the pencil passes, chosen by the autotuner:
+  // [0] float32 layouts, [1] float64 and double-float layouts; [.][0] the 3D
+  // y passes, [.][1] the solve pass (2D y, 3D z).  0: the fixed rule.
+  int pcap[2][2] = {{0, 0}, {0, 0}};
 };
 
 // Host constants of the symbol multiply: the solve scales mode k by
@@ -108,6 +114,12 @@ __host__ __device__ inline double symbol_scale0(const GridDesc& g) {
   return (g.poisson ? 1.0 : g.kappa) / nd;
 }
 
+// Storage of a CUDA tensor map (the 128-byte CUtensorMap of the driver API),
+// kept opaque outside the translation unit that encodes and uses it.
+struct alignas(64) TmaDesc {
+  unsigned char bytes[128];
+};
+
 template <typename T>
 struct SpectralWs {
   typename Cx<T>::type* spec = nullptr;  // (n/2+1) * n^(d-1) complex
@@ -115,6 +127,10 @@ struct SpectralWs {
   const typename Cx<T>::type* tw = nullptr;  // tw[j] = exp(-2 pi i j / n)
   const T* s2 = nullptr;                  // sin^2(pi k / n), k < n
   typename Cx<T>::type* acc = nullptr;    // spectral discretisation: source accumulator
+  // 3D float32: tensor map of spec for the bulk-copy staged z pass (k_tma.cu),
+  // or null; err: device word raised when a bounded wait there gives up
+  const TmaDesc* zmap = nullptr;
+  unsigned* err = nullptr;
 };
 
 // Sources of the fused spread kernel: out = coef_div * S~ q_div
@@ -149,10 +165,12 @@ ibdl_status set_last_error(ibdl_status s, const char* msg);
 cudaError_t launch_point_prep(const GridDesc& g, int m, const double* const X[3],
                               int* const base[3], double* const W64[3],
                               float* const W32[3], cudaStream_t st);
-// Bin building: counts, scan, fill (asynchronous).  counts: ntiles + 1
-// ints of scratch; pts: bins_capacity(dim, rows, m) ints.
+// Bin building: counts, scan, fill into pts, then each tile's list sorted by
+// first support column and point index into spts (asynchronous).  counts:
+// ntiles + 1 ints of scratch; pts, spts: bins_capacity(dim, rows, m) ints.
 cudaError_t launch_bins(const GridDesc& g, const PointData& p, int rows, int ntiles,
-                        int* start, int* cursor, int* counts, int* pts, cudaStream_t st);
+                        int* start, int* cursor, int* counts, int* pts, int* spts,
+                        cudaStream_t st);
 int64_t bins_capacity(int dim, int rows, int64_t m);
 // 3D: zempty[z] = 1 for planes whose tiles list no point.
 cudaError_t launch_plane_flags(const int* start, int ngroups, int n, unsigned char* zempty,
@@ -187,6 +205,19 @@ cudaError_t launch_rows_inv(const GridDesc& g, const Bins& b, SpectralWs<T>& ws,
 template <typename T>
 int fft_kernels_per_solve(int dim);
 cudaError_t configure_fft_kernels(int n, int rows);
+
+// ---- bulk-copy staged z pass (k_tma.cu, 3D float32) --------------------------
+// Shared memory of one block of the staged z pass with c pencils per item.
+template <typename T>
+size_t zsolve_smem(int n, int c);
+// Encodes the tensor map of a (n/2+1) x n x n transposed half spectrum.
+template <typename T>
+cudaError_t make_zsolve_map(const GridDesc& g, const typename Cx<T>::type* spec, TmaDesc* out);
+// Forward z FFT, symbol, inverse z FFT of the 3D solve, in place on ws.spec
+// (ws.zmap set); zempty: planes without points (read as zero, not stored).
+template <typename T>
+cudaError_t launch_zsolve_tma(const GridDesc& g, SpectralWs<T>& ws, const unsigned char* zempty,
+                              cudaStream_t st);
 
 // ---- Krylov kernels (k_krylov.cu) -----------------------------------------
 struct KrylovWs {

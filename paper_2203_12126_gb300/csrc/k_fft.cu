@@ -58,16 +58,6 @@ __global__ void __launch_bounds__(512) k_rows_inv(GridDesc g, Bins b, const cx_t
 // -- more would idle in the FFT passes and thin the per-thread work over
 // which an item's fixed cost is spread.  Row tiles take n/8 per pencil:
 // their spread stage wants the extra threads.
-static int clamp_threads(int t) { return t < 64 ? 64 : (t > 512 ? 512 : t); }
-
-static int pencil_threads(int n, int c) {
-  const int lg = ilog2(n);
-  int min_lr = 4;
-  for (int s = 0; s < plan_npass(lg); ++s)
-    if (plan_lr(lg, s) < min_lr) min_lr = plan_lr(lg, s);
-  return clamp_threads(c * (n >> min_lr));
-}
-
 static int rows_threads(int n, int npen) { return clamp_threads(npen * n / 8); }
 
 // launch-profile label by element type: float, double, double-float
@@ -129,33 +119,39 @@ template <typename T>
 cudaError_t launch_spectral_solve(const GridDesc& g, SpectralWs<T>& ws, cudaStream_t st,
                                   const Bins* skip, bool skip_fwd) {
   cudaError_t e;
-  if (g.dim == 2) return run_pencils<T, 2>(g, solve_layout<T>(2, g.n, 1), ws, st);
-  PencilLayout Ly = solve_layout<T>(3, g.n, 0);   // (kx, z) -> y
-  PencilLayout Lz = solve_layout<T>(3, g.n, 1);   // (kx, y) -> z
+  if (g.dim == 2) return run_pencils<T, 2>(g, solve_layout<T>(g, 1), ws, st);
+  PencilLayout Ly = solve_layout<T>(g, 0);   // (kx, z) -> y
+  PencilLayout Lz = solve_layout<T>(g, 1);   // (kx, y) -> z
   const int ngroups = g.n / (skip ? skip->rows : 1);
   if ((e = run_pencils<T, 0>(g, Ly, ws, st, (skip && skip_fwd) ? skip->start : nullptr,
                              ngroups)))
     return e;
-  if ((e = run_pencils<T, 2>(g, Lz, ws, st, nullptr, 0,
-                             (skip && skip_fwd) ? skip->zempty : nullptr)))
-    return e;
+  const unsigned char* zfw = (skip && skip_fwd) ? skip->zempty : nullptr;
+  if constexpr (std::is_same<T, float>::value) {
+    // float32: the z pass with its pencils staged by bulk tensor copies
+    if (ws.zmap) {
+      if ((e = launch_zsolve_tma<T>(g, ws, zfw, st))) return e;
+      return run_pencils<T, 1>(g, Ly, ws, st, skip ? skip->start : nullptr, ngroups);
+    }
+  }
+  if ((e = run_pencils<T, 2>(g, Lz, ws, st, nullptr, 0, zfw))) return e;
   return run_pencils<T, 1>(g, Ly, ws, st, skip ? skip->start : nullptr, ngroups);
 }
 
 template <typename T>
 cudaError_t launch_pencils_forward(const GridDesc& g, SpectralWs<T>& ws, cudaStream_t st) {
-  if (g.dim == 2) return run_pencils<T, 0>(g, solve_layout<T>(2, g.n, 1), ws, st);
-  cudaError_t e = run_pencils<T, 0>(g, solve_layout<T>(3, g.n, 0), ws, st);
+  if (g.dim == 2) return run_pencils<T, 0>(g, solve_layout<T>(g, 1), ws, st);
+  cudaError_t e = run_pencils<T, 0>(g, solve_layout<T>(g, 0), ws, st);
   if (e) return e;
-  return run_pencils<T, 0>(g, solve_layout<T>(3, g.n, 1), ws, st);
+  return run_pencils<T, 0>(g, solve_layout<T>(g, 1), ws, st);
 }
 
 template <typename T>
 cudaError_t launch_pencils_inverse(const GridDesc& g, SpectralWs<T>& ws, cudaStream_t st) {
-  if (g.dim == 2) return run_pencils<T, 1>(g, solve_layout<T>(2, g.n, 1), ws, st);
-  cudaError_t e = run_pencils<T, 1>(g, solve_layout<T>(3, g.n, 1), ws, st);
+  if (g.dim == 2) return run_pencils<T, 1>(g, solve_layout<T>(g, 1), ws, st);
+  cudaError_t e = run_pencils<T, 1>(g, solve_layout<T>(g, 1), ws, st);
   if (e) return e;
-  return run_pencils<T, 1>(g, solve_layout<T>(3, g.n, 0), ws, st);
+  return run_pencils<T, 1>(g, solve_layout<T>(g, 0), ws, st);
 }
 
 // Combination of spectral source terms on the transposed half spectrum

@@ -115,13 +115,92 @@ __global__ void k_scan(const int* counts, int* start, int* cursor, int ntiles) {
   }
 }
 
-// Tile lists: count, scan, fill.  The order of points inside a tile is the
-// order of the fill's atomics; it does not matter, since the spread adds a
-// tile's contributions with shared-memory atomics anyway (the sum is the
-// same up to rounding in any order).  pts has room for the largest possible
-// count (bins_capacity), so no host round trip sizes it.
+// Writes each tile's list, ordered by the point's first support column
+// xs = (base_x - 1) mod n and then by point index, to spts: a counting sort
+// over the n columns (histogram, scan, scatter), then each column's bucket
+// sorted by index in place by one thread.  The gather spread finds a node's
+// sources in the sorted list (a contiguous run of columns), and the fixed
+// order makes that spread bitwise reproducible.  Dynamic shared memory:
+// 2 (n + 1) ints.
+__global__ void __launch_bounds__(256) k_sort_bins(GridDesc g, const int* __restrict__ base0,
+                                                   const int* __restrict__ start,
+                                                   const int* __restrict__ pts, int* spts,
+                                                   int ntiles) {
+  extern __shared__ int sh[];
+  const int n = g.n, mask = n - 1, tid = threadIdx.x, nt = blockDim.x;
+  int* cnt = sh;          // n + 1: counts, then running ends
+  int* beg = sh + n + 1;  // n + 1: bucket starts
+  __shared__ int part[32];
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int lo = start[t], hi = start[t + 1];
+    if (hi - lo < 2) {
+      if (hi > lo && tid == 0) spts[lo] = pts[lo];
+      continue;
+    }
+    for (int x = tid; x <= n; x += nt) cnt[x] = 0;
+    __syncthreads();
+    for (int e = lo + tid; e < hi; e += nt) atomicAdd(&cnt[(base0[pts[e]] - 1) & mask], 1);
+    __syncthreads();
+    // exclusive scan of cnt[0..n) into beg: per-thread runs, then the warp
+    // sums of the run totals
+    const int per = (n + nt - 1) / nt, x0 = min(n, tid * per), x1 = min(n, x0 + per);
+    int run = 0;
+    for (int x = x0; x < x1; ++x) run += cnt[x];
+    int incl = run;
+    const int lane = tid & 31, wid = tid >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (lane == 31) part[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      int w = lane < (nt >> 5) ? part[lane] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += v;
+      }
+      if (lane < (nt >> 5)) part[lane] = w;  // inclusive warp totals
+    }
+    __syncthreads();
+    int acc = incl - run + (wid > 0 ? part[wid - 1] : 0);
+    for (int x = x0; x < x1; ++x) {
+      const int c = cnt[x];
+      beg[x] = acc;
+      cnt[x] = acc;  // running end of bucket x
+      acc += c;
+    }
+    __syncthreads();
+    for (int e = lo + tid; e < hi; e += nt) {
+      const int i = pts[e];
+      const int pos = atomicAdd(&cnt[(base0[i] - 1) & mask], 1);
+      spts[lo + pos] = i;
+    }
+    __syncthreads();
+    // each bucket by point index (buckets hold the few points of a column)
+    for (int x = tid; x < n; x += nt) {
+      const int b0 = lo + beg[x], b1 = lo + cnt[x];
+      for (int a = b0 + 1; a < b1; ++a) {
+        const int v = spts[a];
+        int b = a;
+        while (b > b0 && spts[b - 1] > v) {
+          spts[b] = spts[b - 1];
+          --b;
+        }
+        spts[b] = v;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Tile lists: count, scan, fill (pts: fill order), then each tile's list
+// ordered by first support column and point index into spts (k_sort_bins).
+// pts and spts have room for the largest possible count (bins_capacity), so
+// no host round trip sizes them.
 cudaError_t launch_bins(const GridDesc& g, const PointData& p, int rows, int ntiles,
-                        int* start, int* cursor, int* counts, int* pts, cudaStream_t st) {
+                        int* start, int* cursor, int* counts, int* pts, int* spts,
+                        cudaStream_t st) {
   cudaError_t e;
   const int bs = 256;
   const int gb = (p.m + bs - 1) / bs;
@@ -140,6 +219,12 @@ cudaError_t launch_bins(const GridDesc& g, const PointData& p, int rows, int nti
   prof_begin(st);
   k_bins<true><<<gb, bs, 0, st>>>(g, p, rows, cursor, pts);
   count_launch("bins", st);
+  if ((e = check_launch())) return e;
+  prof_begin(st);
+  const int sb = ntiles < 2048 ? ntiles : 2048;
+  k_sort_bins<<<sb, 256, 2 * (g.n + 1) * sizeof(int), st>>>(g, p.base[0], start, pts, spts,
+                                                              ntiles);
+  count_launch("sort_bins", st);
   return check_launch();
 }
 
@@ -165,23 +250,62 @@ cudaError_t launch_plane_flags(const int* start, int ngroups, int n, unsigned ch
 
 // ---- interpolation ------------------------------------------------------------
 
-// y_i = S* grid at X_i (+ jump * jvec_i).
+// y_i = S* grid at X_i (+ jump * jvec_i).  Four threads share a point, one
+// per tap plane (3D: z = bz + t) or tap row (2D: y = by + t), so a warp keeps
+// four times as many independent grid loads in flight; the four partial sums
+// are combined by a fixed butterfly of shuffles (a deterministic order).
 template <typename T, int D>
 __global__ void __launch_bounds__(128) k_interp(GridDesc g, PointData p, const T* grid,
                                                 const double* jvec, double jump, double* y) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= p.m) return;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = gt >> 2, sub = gt & 3;
+  const bool live = i < p.m;
+  const int ii = live ? i : 0;
+  const int n = g.n, mask = n - 1, m = p.m;
   // the grid comes from an earlier launch: cached loads are coherent here
-  double out = (double)interp_point<T, D, true>(g, p, grid, i);
-  if (jvec) out += jump * jvec[i];
-  y[i] = out;
+  T wx[4];
+  int col[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) wx[t] = interp_w<T>(p, 0, t, ii, m);
+  const int bx = p.base[0][ii], by = p.base[1][ii];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) col[t] = (bx + t) & mask;
+  T acc = 0;
+  if (D == 2) {
+    const T* row = grid + (size_t)((by + sub) & mask) * n;
+    T r = 0;
+#pragma unroll
+    for (int tx = 0; tx < 4; ++tx) r += __ldg(row + col[tx]) * wx[tx];
+    acc = r * interp_w<T>(p, 1, sub, ii, m);
+  } else {
+    T wy[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) wy[t] = interp_w<T>(p, 1, t, ii, m);
+    const T* plane = grid + (size_t)((p.base[2][ii] + sub) & mask) * n * n;
+#pragma unroll
+    for (int ty = 0; ty < 4; ++ty) {
+      const T* row = plane + (size_t)((by + ty) & mask) * n;
+      T r = 0;
+#pragma unroll
+      for (int tx = 0; tx < 4; ++tx) r += __ldg(row + col[tx]) * wx[tx];
+      acc += r * wy[ty];
+    }
+    acc *= interp_w<T>(p, 2, sub, ii, m);
+  }
+  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+  if (live && sub == 0) {
+    double out = (double)acc;
+    if (jvec) out += jump * jvec[i];
+    y[i] = out;
+  }
 }
 
 template <typename T>
 cudaError_t launch_interp(const GridDesc& g, const PointData& p, const T* grid,
                           const double* jvec, double jump, double* y, cudaStream_t st) {
   const int bs = 128;
-  const int gb = (p.m + bs - 1) / bs;
+  const int gb = (int)((4 * (int64_t)p.m + bs - 1) / bs);
   prof_begin(st);
   if (g.dim == 2)
     k_interp<T, 2><<<gb, bs, 0, st>>>(g, p, grid, jvec, jump, y);

@@ -40,6 +40,7 @@ EXPORTS = [
     "ibdl_server_clock", "ibdl_server_submit", "ibdl_server_step", "ibdl_server_take",
     "ibdl_server_get_stats", "ibdl_tuning_enable", "ibdl_tuning_set", "ibdl_indicator",
     "ibdl_near_boundary", "ibdl_selftest_bounded_wait", "ibdl_solver_smem_query",
+    "ibdl_tuning_set_pencils",
 ]
 
 
@@ -82,6 +83,7 @@ class GeometryInfo(C.Structure):
         ("kappa", C.c_double), ("bc", C.c_int32), ("delta", C.c_int32),
         ("precision", C.c_int32), ("device_bytes", C.c_int64),
         ("fft_passes", C.c_int32), ("rows_per_tile", C.c_int32),
+        ("pencils_per_item", C.c_int32 * 2),
     ]
 
 
@@ -174,6 +176,7 @@ def load(path: str = LIB_PATH):
         "ibdl_selftest_bounded_wait": (C.c_int, [C.c_uint32, vp]),
         "ibdl_solver_smem_query": (C.c_int, [i32, i32, i32, i32, C.POINTER(i64),
                                              C.POINTER(i64), C.POINTER(i32)]),
+        "ibdl_tuning_set_pencils": (C.c_int, [i32, i32, i32, i32, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -282,6 +285,13 @@ def tuning_set(dim: int, n: int, precision: int, rows: int) -> None:
     """Pin the x-pass tiling of (current device, dim, n, precision); rows = 0
     drops the pin."""
     _check(load().ibdl_tuning_set(int(dim), int(n), int(precision), int(rows)))
+
+
+def tuning_set_pencils(dim: int, n: int, precision: int, c_solve: int, c_y: int = 0) -> None:
+    """Pin the pencils per work item of (current device, dim, n, precision);
+    both 0 drops the pin."""
+    _check(load().ibdl_tuning_set_pencils(int(dim), int(n), int(precision), int(c_solve),
+                                          int(c_y)))
 
 
 def version() -> int:
@@ -447,7 +457,11 @@ class Geometry:
     def info(self):
         gi = GeometryInfo()
         _check(load().ibdl_get_geometry_info(self._h, C.byref(gi)))
-        return {f: getattr(gi, f) for f, _ in GeometryInfo._fields_ if f != "reserved"}
+        out = {}
+        for f, _ in GeometryInfo._fields_:
+            v = getattr(gi, f)
+            out[f] = list(v) if isinstance(v, C.Array) else v
+        return out
 
     def apply(self, q, y, precision=None, stream=None):
         lib = load()

@@ -1,11 +1,15 @@
-"""The x-pass tiling autotuner: whatever tiling it picks, the operator is
-the fixed rule's to rounding (float64 1e-12, float32 1e-6 relative)."""
+"""The autotuner of the x-pass tiling and of the pencil items: whatever it
+picks, the operator is the fixed rule's to rounding (float64 1e-12, float32
+1e-6 relative), and every admissible pencils-per-item choice matches the
+float64 oracle element-wise at the matvec tolerances (float64 1e-12, float32
+1e-5)."""
 import numpy as np
 import pytest
 from parity_util import assert_parity
 
 torch = pytest.importorskip("torch")
 
+from oracle import ibdl_oracle as O  # noqa: E402
 from workloads import configs, geometry  # noqa: E402
 
 pytestmark = pytest.mark.gpu
@@ -77,3 +81,41 @@ def test_pinned_tiling_is_used_and_checked():
         ibdl.tuning_set(2, 64, ibdl.FP64, 0)
         ibdl.tuning_set(3, 32, ibdl.FP64, 0)
         ibdl.tuning_enable(True)
+
+
+PENCIL_CASES = [
+    # (geometry, pinned precision, matvec precisions and tolerances, c_solve, c_y)
+    ("star256", 0, ((0, 1e-12), (2, 1e-12)),
+     (1, 2, 4), (0,)),
+    ("star256", 1, ((1, 1e-5),), (1, 2, 4, 8), (0,)),
+    ("sphere64", 1, ((1, 1e-5),), (2, 4, 8, 16), (1, 4, 16)),
+    ("sphere64", 0, ((0, 1e-12),), (2, 4, 8), (2, 8)),
+]
+
+
+@pytest.mark.parametrize("name,prec,checks,csolve,cy", PENCIL_CASES)
+def test_every_pencil_choice_matches_oracle(name, prec, checks, csolve, cy):
+    if name == "star256":
+        g = geometry.star(256, 0.3, 0.2, 5, kappa=1e-3)
+    else:
+        g = geometry.sphere(64, 0.3, kappa=1e-2)
+    q = np.random.default_rng(17).standard_normal(g.m)
+    ref = O.Operator(g, configs.DIRICHLET).apply(q)
+    try:
+        for c in csolve:
+            for y in cy:
+                ibdl.tuning_set_pencils(g.dim, g.n, prec, c, y)
+                G = pkg.Geometry.from_workload(g, bc=configs.DIRICHLET, precision=prec)
+                info = G.info()
+                assert info["pencils_per_item"][0] == c, info
+                if g.dim == 3 and y:
+                    assert info["pencils_per_item"][1] == y, info
+                for mp, tol in checks:
+                    out = torch.empty(g.m, dtype=torch.float64, device=DEV)
+                    G.apply(torch.tensor(q, device=DEV), out, precision=mp)
+                    assert_parity(out.cpu().numpy(), ref, tol, f"{name} c={c} y={y} prec={mp}")
+                G.close()
+        with pytest.raises(ibdl.IbdlError):
+            ibdl.tuning_set_pencils(g.dim, g.n, prec, 3, 0)
+    finally:
+        ibdl.tuning_set_pencils(g.dim, g.n, prec, 0, 0)
