@@ -44,7 +44,7 @@ struct SolveInst {
   double* sn;
   double* gv;       // restart + 1
   double* ysol;     // restart
-  double* part;     // 3 sections x nchunk x pstride
+  double* part;     // partial sums: sections of nchunk x pstride
   int nchunk;
   int pstride;
   double* bvec;         // right-hand side (written by ACT_RHS)

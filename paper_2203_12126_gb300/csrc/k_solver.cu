@@ -9,11 +9,14 @@
 //   B   pencils    y (and z) FFT passes with the symbol            (matvec)
 //   C   rows_inv   x inverse FFT to the real grid                  (matvec)
 //   D   interp     w = S* grid +- input/2, then the first-pass dot products
-//   E   reduce, w -= V h (CGS pass 1), second-pass dots / residual norm
-//   F   reduce, w -= V h (CGS pass 2), norm partial / x update
-//   G   normalise w; Givens rotation; control (next action)
+//   E   reduce, w1 = w - V h1 (CGS pass 1), second-pass dots h2 and ||w1||^2
+//   F   reduce, w2 = w1 - V h2 (CGS pass 2), ||w2|| = sqrt(||w1||^2 - |h2|^2)
+//       (Pythagoras: V is orthonormal), normalise; Givens rotation; control
 //
-// (small instances in large batches do D..G as one item on one block).
+// An Arnoldi step is D, E, F; a residual round D, E (E normalises r and runs
+// control); FINISH D, E (back substitution, x += V y, control); the Neumann
+// right-hand side D alone.  (Small instances in large batches do the vector
+// work of a round as one item on one block.)
 // Actions: RHS (Neumann right-hand side), RESID_ZERO (r = b at x = 0),
 // MV_RESIDUAL (r = b - A64 x), MV_ARNOLDI (Arnoldi step j with the float64
 // or float32 operator), FINISH (back substitution, x += V y), DONE.  The
@@ -94,6 +97,10 @@ struct RoundView {
 };
 
 constexpr int kMaxCols = 66;  // restart (<= 64) + 2
+
+struct BlockRed;
+__device__ void control(const SolveInst& I, SolveState* S, const RoundView& v, double hn,
+                        double beta, double bnorm2, BlockRed& R);
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -270,7 +277,8 @@ __device__ void mv_item(const SolveInst& I, const RoundView& v, int phase, int i
 // ---- vector phases ------------------------------------------------------------
 
 template <int D>
-__device__ void phase_D(const SolveInst& I, const RoundView& v, int chunk, BlockRed& R) {
+__device__ void phase_D(const SolveInst& I, SolveState* S, const RoundView& v, int chunk,
+                        BlockRed& R) {
   const int i = chunk * blockDim.x + threadIdx.x;
   const bool valid = i < I.p.m;
   double* part1 = I.part;
@@ -288,8 +296,10 @@ __device__ void phase_D(const SolveInst& I, const RoundView& v, int chunk, Block
     return;
   }
   if (v.action == ACT_RHS) {
-    // b = S* grid, grid = -kappa L'^{-1} S V_b (the Neumann right-hand side)
+    // b = S* grid, grid = -kappa L'^{-1} S V_b (the Neumann right-hand side);
+    // the round ends here, so chunk 0 also picks the next action
     if (valid) I.bvec[i] = interp_point<double, D>(I.g, I.p, I.w64.grid, i);
+    if (chunk == 0 && threadIdx.x == 0) control(I, S, v, 0, 0, 0, R);
     return;
   }
   const double jump = I.bc == IBDL_DIRICHLET ? 0.5 : -0.5;
@@ -333,17 +343,17 @@ __device__ void phase_D(const SolveInst& I, const RoundView& v, int chunk, Block
   __syncthreads();
 }
 
-// CGS pass: h = sum of partials (section `in`), Hcol (+)= h (chunk 0),
-// w -= V h; then dots of w with V (pass 1) or ||w||^2 (pass 2) into `out`.
+// First CGS pass of an Arnoldi step: h1 = sum of the partials (section
+// `in`), H[:, j] = h1 (chunk 0), w1 = w - V h1; then the dots of w1 with V
+// and ||w1||^2 (column j + 1) into `out`, for phase F.
 __device__ void cgs_pass(const SolveInst& I, const RoundView& v, int chunk, BlockRed& R,
-                         const double* in, double* out, bool first) {
+                         const double* in, double* out) {
   const int ncols = v.j + 1;
   const int ldh = I.restart + 1;
   reduce_parts(in, I.nchunk, I.pstride, 0, ncols, R.h);
   if (chunk == 0) {
     double* Hcol = I.H + (size_t)v.j * ldh;
-    for (int c = threadIdx.x; c < ncols; c += blockDim.x)
-      Hcol[c] = first ? R.h[c] : __ldcg(Hcol + c) + R.h[c];
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) Hcol[c] = R.h[c];
   }
   const int i = chunk * blockDim.x + threadIdx.x;
   const bool valid = i < I.p.m;
@@ -354,30 +364,17 @@ __device__ void cgs_pass(const SolveInst& I, const RoundView& v, int chunk, Bloc
     wp[i] = w;
   }
   __syncthreads();
-  if (first) {
-    chunk_dots(I, w, valid, i, ncols, false, out, chunk, R);
-  } else {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const double s = warp_sum(valid ? w * w : 0.0);
-    if (lane == 0) R.red[0][wid] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0;
-      for (int k = 0; k < nw; ++k) t += R.red[0][k];
-      out[(size_t)chunk * I.pstride] = t;
-    }
-    __syncthreads();
-  }
+  chunk_dots(I, w, valid, i, ncols, true, out, chunk, R);
 }
 
-__device__ void phase_E(const SolveInst& I, const RoundView& v, int chunk, BlockRed& R) {
+__device__ void phase_E(const SolveInst& I, SolveState* S, const RoundView& v, int chunk,
+                        BlockRed& R) {
   double* part1 = I.part;
   double* part2 = I.part + (size_t)I.nchunk * I.pstride;
   if (v.action == ACT_MV_ARNOLDI) {
-    cgs_pass(I, v, chunk, R, part1, part2, true);
+    cgs_pass(I, v, chunk, R, part1, part2);
     return;
   }
-  if (v.action == ACT_RHS) return;
   const int i = chunk * blockDim.x + threadIdx.x;
   const bool valid = i < I.p.m;
   if (v.action == ACT_FINISH) {
@@ -386,21 +383,19 @@ __device__ void phase_E(const SolveInst& I, const RoundView& v, int chunk, Block
     __syncthreads();
     if (valid) I.x[i] = sub_projection(I, __ldcg(I.x + i), i, v.kdim, R.h);
     __syncthreads();
+    if (chunk == 0 && threadIdx.x == 0) control(I, S, v, 0, 0, 0, R);
+    __syncthreads();
     return;
   }
-  // residual actions: V0 = r / ||r||
-  reduce_parts(part1, I.nchunk, I.pstride, 0, 1, R.h);
+  // residual actions: V0 = r / ||r||, and the round's control step
+  reduce_parts(part1, I.nchunk, I.pstride, 0, 2, R.h);
   const double beta = sqrt(R.h[0]);
+  const double b2 = R.h[1];
   const double inv = (beta > 0 && isfinite(beta)) ? 1.0 / beta : 0.0;
   if (valid) I.V[i] = __ldcg(I.r + i) * inv;
   __syncthreads();
-}
-
-__device__ void phase_F(const SolveInst& I, const RoundView& v, int chunk, BlockRed& R) {
-  if (v.action != ACT_MV_ARNOLDI) return;
-  double* part2 = I.part + (size_t)I.nchunk * I.pstride;
-  double* part3 = I.part + 2 * (size_t)I.nchunk * I.pstride;
-  cgs_pass(I, v, chunk, R, part2, part3, false);
+  if (chunk == 0 && threadIdx.x == 0) control(I, S, v, 0, beta, b2, R);
+  __syncthreads();
 }
 
 // Control of one instance (one thread).  hn: new subdiagonal, beta: residual
@@ -508,43 +503,42 @@ __device__ void control(const SolveInst& I, SolveState* S, const RoundView& v, d
   __threadfence();
 }
 
-__device__ void phase_G(const SolveInst& I, SolveState* S, const RoundView& v, int chunk,
+// Second CGS pass of an Arnoldi step, normalisation and control: h2 and
+// ||w1||^2 come from phase E's partials; ||w2||^2 = ||w1||^2 - |h2|^2 since
+// w2 = w1 - V h2 with V orthonormal and h2 = V^T w1 (the second pass's
+// correction is small, so the difference does not cancel).
+__device__ void phase_F(const SolveInst& I, SolveState* S, const RoundView& v, int chunk,
                         BlockRed& R) {
-  if (v.action == ACT_MV_ARNOLDI) {
-    double* part3 = I.part + 2 * (size_t)I.nchunk * I.pstride;
-    reduce_parts(part3, I.nchunk, I.pstride, 0, 1, R.h);
-    const double hn = sqrt(R.h[0]);
-    const double inv = (hn > 0 && isfinite(hn)) ? 1.0 / hn : 0.0;
-    const int i = chunk * blockDim.x + threadIdx.x;
-    if (i < I.p.m && inv != 0.0) {
-      double* wp = I.V + (size_t)(v.j + 1) * I.ld;
-      wp[i] = __ldcg(wp + i) * inv;
-    }
-    if (chunk == 0) {
-      const int j = v.j, ldh = I.restart + 1;
-      __syncthreads();
-      for (int r = threadIdx.x; r <= j; r += blockDim.x) {
-        R.col[r] = __ldcg(I.H + (size_t)j * ldh + r);
-        if (r < j) {
-          R.cs[r] = __ldcg(I.cs + r);
-          R.sn[r] = __ldcg(I.sn + r);
-        }
+  const int j = v.j, ncols = j + 1, ldh = I.restart + 1;
+  double* part2 = I.part + (size_t)I.nchunk * I.pstride;
+  reduce_parts(part2, I.nchunk, I.pstride, 0, ncols + 1, R.h);
+  double ss = 0;
+  for (int c = 0; c < ncols; ++c) ss += R.h[c] * R.h[c];
+  const double d2 = R.h[ncols] - ss;
+  const double hn = sqrt(d2 > 0.0 ? d2 : 0.0);
+  const double inv = (hn > 0 && isfinite(hn)) ? 1.0 / hn : 0.0;
+  const int i = chunk * blockDim.x + threadIdx.x;
+  if (i < I.p.m) {
+    double* wp = I.V + (size_t)(j + 1) * I.ld;
+    const double w = sub_projection(I, __ldcg(wp + i), i, ncols, R.h);
+    wp[i] = inv != 0.0 ? w * inv : w;
+  }
+  if (chunk == 0) {
+    // stage the Hessenberg column (h1 from phase E plus h2), the earlier
+    // rotations and g_j for the control step
+    for (int r = threadIdx.x; r <= j; r += blockDim.x) {
+      R.col[r] = __ldcg(I.H + (size_t)j * ldh + r) + R.h[r];
+      if (r < j) {
+        R.cs[r] = __ldcg(I.cs + r);
+        R.sn[r] = __ldcg(I.sn + r);
       }
-      if (threadIdx.x == 0) R.h[0] = __ldcg(I.gv + j);
-      __syncthreads();
-      if (threadIdx.x == 0) control(I, S, v, hn, 0, 0, R);
     }
     __syncthreads();
-    return;
+    if (threadIdx.x == 0) {
+      R.h[0] = __ldcg(I.gv + j);
+      control(I, S, v, hn, 0, 0, R);
+    }
   }
-  if (chunk != 0) return;
-  double beta = 0, b2 = 0;
-  if (v.action != ACT_FINISH && v.action != ACT_RHS) {
-    reduce_parts(I.part, I.nchunk, I.pstride, 0, 2, R.h);
-    beta = sqrt(R.h[0]);
-    b2 = R.h[1];
-  }
-  if (threadIdx.x == 0) control(I, S, v, 0, beta, b2, R);
   __syncthreads();
 }
 
@@ -758,7 +752,7 @@ struct PhaseDesc {
   int action, prec, j, kdim;
 };
 
-constexpr int kPhaseD = 5, kPhaseE = 6, kPhaseF = 7, kPhaseG = 8, kPhaseSingle = 9;
+constexpr int kPhaseD = 5, kPhaseE = 6, kPhaseF = 7, kPhaseSingle = 9;
 
 // claim word: bits 63..48 the phase epoch (mod 2^16), 47..32 the phase's
 // item count, 31..0 the next item index.  A claim is valid exactly when the
@@ -811,8 +805,8 @@ __device__ int first_phase(const SolveInst& I, int action) {
   return I.single ? kPhaseSingle : kPhaseD;
 }
 
-// -1: the round ends after `phase`
-__device__ int next_phase(const SolveInst& I, int phase) {
+// -1: the round ends after `phase` (of a round doing `action`)
+__device__ int next_phase(const SolveInst& I, int phase, int action) {
   const bool d3 = I.g.dim == 3;
   switch (phase) {
     case 0: return d3 ? 1 : 2;
@@ -820,9 +814,8 @@ __device__ int next_phase(const SolveInst& I, int phase) {
     case 2: return d3 ? 3 : 4;
     case 3: return 4;
     case 4: return I.single ? kPhaseSingle : kPhaseD;
-    case kPhaseD: return kPhaseE;
-    case kPhaseE: return kPhaseF;
-    case kPhaseF: return kPhaseG;
+    case kPhaseD: return action == ACT_RHS ? -1 : kPhaseE;
+    case kPhaseE: return action == ACT_MV_ARNOLDI ? kPhaseF : -1;
     default: return -1;
   }
 }
@@ -851,7 +844,7 @@ __device__ bool view_from_state(const SolveState* S, PhaseDesc& d) {
 __device__ void advance(const SolveInst& I, const SolveState* S, unsigned* bar, int k,
                         int max_rounds) {
   PhaseDesc d = load_desc(desc_of(bar, k));
-  int np = next_phase(I, d.phase);
+  int np = next_phase(I, d.phase, d.action);
   if (np < 0) {
     d.round++;
     const bool active = view_from_state(S, d);
@@ -891,15 +884,13 @@ __device__ void run_item(const SolveInst& I, SolveState* S, const PhaseDesc& d, 
       mv_item<double>(I, v, d.phase, item, smem);
   } else if (d.phase == kPhaseD) {
     if (I.g.dim == 2)
-      phase_D<2>(I, v, item, R);
+      phase_D<2>(I, S, v, item, R);
     else
-      phase_D<3>(I, v, item, R);
+      phase_D<3>(I, S, v, item, R);
   } else if (d.phase == kPhaseE) {
-    phase_E(I, v, item, R);
+    phase_E(I, S, v, item, R);
   } else if (d.phase == kPhaseF) {
-    phase_F(I, v, item, R);
-  } else if (d.phase == kPhaseG) {
-    phase_G(I, S, v, item, R);
+    phase_F(I, S, v, item, R);
   } else {
     vec_single(I, S, v, R);
   }
