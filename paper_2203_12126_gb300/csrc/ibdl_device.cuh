@@ -1127,13 +1127,17 @@ __device__ __forceinline__ void phase_rows_fwd(const GridDesc& g, const PointDat
     return;
   }
 
+  // the twiddles load now and land in shared memory after the spread, so
+  // their L2 round trip overlaps the zero fill and the spread's own loads
+  const int ntw = fft_tw_count(n);
+  TableStage<T, kTabBatch> ts;
+  if (!write_grid) ts.load(tw, ntw, nullptr, 0, 0);
   for (int e = tid; e < R * n; e += nt) {
     const int r = e >> lg, x = e & mask;
     S v = 0;
     if (src.f_grid) v = (S)(src.coef_grid * src.f_grid[row0 + (size_t)r * n + x]);
     rows[((r >> 1) * PS + padi(x)) * 2 + (r & 1)] = v;
   }
-  if (!write_grid) copy_to_shared(tws, tw, fft_tw_count(n));
   __syncthreads();
 
   const size_t sbytes = (size_t)npen * PS * sizeof(C);  // bufB, unused until the FFT
@@ -1154,6 +1158,9 @@ __device__ __forceinline__ void phase_rows_fwd(const GridDesc& g, const PointDat
     __syncthreads();
     return;
   }
+  ts.store(tws, ntw, nullptr, 0, 0);
+  ts.rest(tw, tws, ntw, nullptr, nullptr, 0);
+  __syncthreads();
 
   C* res = fft_run<T, false>(bufA, bufB, lg, npen, tws);
 
