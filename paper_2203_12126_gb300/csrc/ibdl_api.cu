@@ -1900,7 +1900,7 @@ int32_t ibdl_profile_read(ibdl_kernel_stat* out, int32_t max_out, int32_t reset)
     static const char* names[15] = {
         "phase:rows_fwd_f64", "phase:y_fwd_f64", "phase:solve_f64", "phase:y_inv_f64",
         "phase:rows_inv_f64", "phase:rows_fwd_f32", "phase:y_fwd_f32", "phase:solve_f32",
-        "phase:y_inv_f32", "phase:rows_inv_f32", "phase:vector_D_to_G", "phase:unused11",
+        "phase:y_inv_f32", "phase:rows_inv_f32", "phase:vector_phases", "phase:unused11",
         "phase:unused12", "phase:unused13", "phase:idle_blocks"};
     unsigned long long h[2 * kPhaseSlots];
     if (cudaMemcpy(h, g_phase_buf, sizeof(h), cudaMemcpyDeviceToHost) == cudaSuccess) {

@@ -841,9 +841,11 @@ __device__ bool view_from_state(const SolveState* S, PhaseDesc& d) {
 
 // Publishes instance k's next phase (one thread).  `finished` counts
 // instances that are done or have used their rounds for this launch.
+// `cur` is the descriptor of the phase whose last item the caller finished:
+// the stored one, which nobody else can change now.
 __device__ void advance(const SolveInst& I, const SolveState* S, unsigned* bar, int k,
-                        int max_rounds) {
-  PhaseDesc d = load_desc(desc_of(bar, k));
+                        int max_rounds, const PhaseDesc& cur) {
+  PhaseDesc d = cur;
   int np = next_phase(I, d.phase, d.action);
   if (np < 0) {
     d.round++;
@@ -1024,7 +1026,7 @@ __global__ void __launch_bounds__(kSolverThreads, 2)
         // every item of the phase is done: see their writes (the state of
         // the control step included) before choosing the next phase
         __threadfence();
-        advance(insts[k], states + k, bar, k, max_rounds);
+        advance(insts[k], states + k, bar, k, max_rounds, d);
       }
     }
   }

@@ -12,7 +12,8 @@
 // ping-pong buffer of the transforms, and before the last inverse pass --
 // when nothing reads the box any more -- the block's thread 0 starts the
 // copy of its next item there; the copy overlaps that pass and its stores.
-// One staging box doubles as a pencil buffer, so three blocks share an SM.  Every wait on the mbarrier is bounded: on timeout the block
+// One staging box doubles as a pencil buffer, so three blocks share an SM.
+// Every wait on the mbarrier is bounded: on timeout the block
 // raises an error word, waits (bounded) for its copy in flight and leaves.
 //
 // Only the GPU's own memory is addressed (no multicast, no clusters).
