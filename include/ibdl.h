@@ -466,6 +466,21 @@ ibdl_status ibdl_tuning_set(int32_t dim, int32_t n, int32_t precision, int32_t r
 ibdl_status ibdl_tuning_set_pencils(int32_t dim, int32_t n, int32_t precision, int32_t c_solve,
                                     int32_t c_y);
 
+/* Pencils per work item of the persistent solver's solve pass (2D y
+ * pencils, 3D z pencils) for this geometry's solves, per element type:
+ * c_f64 float64, c_f32 float32 (the refined inner operator), c_dd
+ * double-float (the residuals of small refined launches); 0 keeps the fixed
+ * rule (every y or z pencil group of about 256 items).  Fewer, larger items
+ * let the instances of one batched launch run side by side; more, smaller
+ * ones shorten a lone solve's phases.  Each value must be admissible (a
+ * power of two <= 16 whose item fits 100 KB of shared memory; strided z
+ * items at least 2), and the solver's items must fit one block's shared
+ * memory.  Results agree with the fixed rule's to rounding.
+ * IBDL_ERR_INVALID_ARG otherwise (the geometry is left as it was).  No
+ * passage of the paper: a resource choice. */
+ibdl_status ibdl_geometry_set_solver_pencils(ibdl_geometry g, int32_t c_f64, int32_t c_f32,
+                                             int32_t c_dd);
+
 /* Shared-memory bookkeeping of the persistent solver's work items (host
  * only: touches no GPU, so it runs without one).  For a grid (dim, n), an
  * x-pass tiling of `rows` grid rows per tile (a power of two in [2, n]) and
@@ -506,6 +521,24 @@ typedef struct {
  * NULL).  Returns the number of kernel families recorded; reset != 0 clears
  * the totals afterwards. */
 int32_t ibdl_profile_read(ibdl_kernel_stat* out, int32_t max_out, int32_t reset);
+
+/* Work-item trace of the persistent solver (diagnostics; needs profiling
+ * on).  On clears the trace; while on, each block of a persistent launch
+ * writes one record per work item it runs and one per phase hand-off, into
+ * its own share of 65536 records (later records of a block whose share is
+ * full are dropped).  IBDL_ERR_INVALID_ARG if profiling is off. */
+ibdl_status ibdl_profile_trace(int32_t on);
+
+/* Synchronises the device, copies up to max_records trace records (three
+ * uint64 words each: start and end on the GPU's global nanosecond timer, then
+ * block << 40 | instance << 24 | phase << 20 | precision << 18 | item, where
+ * phase 0..4 are the matvec phases (x forward, 3D y forward, solve, 3D y
+ * inverse, x inverse), 5..9 the vector phases and the one-block step, 15 a
+ * hand-off whose item field is the next phase (15: the instance stopped), and
+ * precision 1 float32 items) to out (may be NULL), then clears the trace.
+ * Returns the number of records written since the trace was last cleared,
+ * or -1 on a CUDA error. */
+int64_t ibdl_profile_trace_read(uint64_t* out, int64_t max_records);
 
 /* Allocation-free variant of ibdl_helmholtz for callers that cannot
  * allocate device memory: code running inside a host callback or a stream

@@ -694,6 +694,7 @@ SolveInst make_inst(ibdl_geometry_s* g, const ibdl_solve_opts& o, int batch_size
   I.hist = g->d_hist;
   I.hist_cap = kHistCap;
   I.single = g->m <= kSingleMax && batch_size >= kSingleMinBatch && !g_force_multi;
+  solver_fill_items(I);
   return I;
 }
 
@@ -1865,6 +1866,32 @@ ibdl_status ibdl_tuning_set_pencils(int32_t dim, int32_t n, int32_t precision, i
   return IBDL_OK;
 }
 
+ibdl_status ibdl_geometry_set_solver_pencils(ibdl_geometry g, int32_t c_f64, int32_t c_f32,
+                                             int32_t c_dd) {
+  g_err.clear();
+  IBDL_TRY(check_handle(g));
+  GridDesc gd = g->grid;
+  const int cs[3] = {c_f64, c_f32, c_dd};
+  for (int e = 0; e < 3; ++e) {
+    const int c = cs[e];
+    if (c == 0) continue;
+    const PencilLayout base = solve_layout<double>(gd.dim, gd.n, 1);
+    const bool ok = e == 1 ? pencils_admissible<float>(gd.n, base.estride, base.pg, c)
+                  : e == 2 ? pencils_admissible<dd>(gd.n, base.estride, base.pg, c)
+                           : pencils_admissible<double>(gd.n, base.estride, base.pg, c);
+    if (!ok) return fail(IBDL_ERR_INVALID_ARG, "solver pencils per item: not admissible");
+    gd.scap[e] = c;
+  }
+  for (int e = 0; e < 3; ++e)
+    if (cs[e] == 0) gd.scap[e] = 0;
+  const int smem = solver_smem_bytes(gd, g->bins.rows, 1);
+  if (smem < 0 || smem > 227 * 1024)
+    return fail(IBDL_ERR_INVALID_ARG, "solver pencils per item: items exceed shared memory");
+  g->grid = gd;
+  g->solver_smem = smem;
+  return IBDL_OK;
+}
+
 ibdl_status ibdl_tuning_set(int32_t dim, int32_t n, int32_t precision, int32_t rows) {
   if ((dim != 2 && dim != 3) || n < 16 || n > (dim == 2 ? kMaxN2 : kMaxN3) || (n & (n - 1)) ||
       precision < IBDL_FP64 || precision > IBDL_FP32_REFINED || rows < 0)
@@ -1884,13 +1911,47 @@ ibdl_status ibdl_tuning_set(int32_t dim, int32_t n, int32_t precision, int32_t r
 void ibdl_profile_enable(int32_t on) {
   if (on && !g_phase_buf) {
     // allocated when profiling is switched on, never on the solve path
-    if (cudaMalloc((void**)&g_phase_buf, 2 * kPhaseSlots * sizeof(unsigned long long)) ==
+    if (cudaMalloc((void**)&g_phase_buf, kProfWords * sizeof(unsigned long long)) ==
         cudaSuccess)
-      cudaMemset(g_phase_buf, 0, 2 * kPhaseSlots * sizeof(unsigned long long));
+      cudaMemset(g_phase_buf, 0, kProfWords * sizeof(unsigned long long));
     else
       g_phase_buf = nullptr;
   }
   g_prof.store(on != 0);
+}
+
+ibdl_status ibdl_profile_trace(int32_t on) {
+  g_err.clear();
+  if (!g_phase_buf) return fail(IBDL_ERR_INVALID_ARG, "profiling is off (ibdl_profile_enable)");
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  const unsigned long long h[2] = {on ? 1ull : 0ull, 0ull};
+  IBDL_CU(cudaDeviceSynchronize());
+  IBDL_CU(cudaMemset(g_phase_buf + kTraceFlag + 2, 0,
+                     3 * (size_t)kTraceCap * sizeof(unsigned long long)));
+  IBDL_CU(cudaMemcpy(g_phase_buf + kTraceFlag, h, sizeof(h), cudaMemcpyHostToDevice));
+  return IBDL_OK;
+}
+
+int64_t ibdl_profile_trace_read(uint64_t* out, int64_t max_records) {
+  if (!g_phase_buf) return 0;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  std::vector<uint64_t> h(3 * (size_t)kTraceCap);
+  if (cudaMemcpy(h.data(), g_phase_buf + kTraceFlag + 2, h.size() * sizeof(uint64_t),
+                 cudaMemcpyDeviceToHost) ||
+      cudaMemset(g_phase_buf + kTraceFlag + 2, 0, h.size() * sizeof(uint64_t)))
+    return -1;
+  int64_t k = 0;
+  for (size_t r = 0; r < (size_t)kTraceCap; ++r) {
+    if (h[3 * r] == 0) continue;
+    if (out && k < max_records)
+      for (int w = 0; w < 3; ++w) out[3 * k + w] = h[3 * r + w];
+    ++k;
+  }
+  return k;
 }
 
 int32_t ibdl_profile_read(ibdl_kernel_stat* out, int32_t max_out, int32_t reset) {

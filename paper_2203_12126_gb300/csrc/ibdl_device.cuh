@@ -258,6 +258,51 @@ template <bool INV, typename C> __device__ __forceinline__ void dft16(C* a) {
   t = a[11]; a[11] = a[14]; a[14] = t;
 }
 
+// cos and sin of 2 pi e / 16 (no recursion: used only in constant
+// expressions, below as template arguments' constants)
+__host__ __device__ constexpr double cos16(int e) {
+  return ((e & 15) < 8 ? 1.0 : -1.0) *
+         ((e & 7) == 0 ? 1.0 : (e & 7) == 1 ? kC8 : (e & 7) == 2 ? kR2 : (e & 7) == 3 ? kS8
+          : (e & 7) == 4 ? 0.0 : (e & 7) == 5 ? -kS8 : (e & 7) == 6 ? -kR2 : -kC8);
+}
+__host__ __device__ constexpr double sin16(int e) { return cos16(e + 12); }
+
+// a * w16^E0 (h false) or a * w16^E1 (h true), w16 = exp(-+2 pi i / 16) for
+// the forward (inverse) direction: both constants fold at compile time and
+// each thread selects one
+template <bool INV, int E0, int E1, typename C>
+__device__ __forceinline__ C cmul_w16_sel(C a, bool h) {
+  using T = decltype(a.x);
+  constexpr double sg = INV ? 1.0 : -1.0;
+  constexpr double c0 = cos16(E0), s0 = sg * sin16(E0);
+  constexpr double c1 = cos16(E1), s1 = sg * sin16(E1);
+  const T r0 = (T)c0, i0 = (T)s0, r1 = (T)c1, i1 = (T)s1;
+  const T wr = h ? r1 : r0, wi = h ? i1 : i0;
+  C r;
+  r.x = a.x * wr - a.y * wi;
+  r.y = a.x * wi + a.y * wr;
+  return r;
+}
+
+template <typename C> __device__ __forceinline__ C cneg_if(C a, bool neg) {
+  C r;
+  r.x = neg ? -a.x : a.x;
+  r.y = neg ? -a.y : a.y;
+  return r;
+}
+
+// value of lane ^ 16 (all 32 lanes of the warp take part)
+template <typename C> __device__ __forceinline__ C shfl_xor16(C v) {
+  static_assert(sizeof(C) % 4 == 0, "whole words");
+  constexpr int W = sizeof(C) / 4;
+  unsigned u[W];
+  memcpy(u, &v, sizeof(C));
+#pragma unroll
+  for (int i = 0; i < W; ++i) u[i] = __shfl_xor_sync(0xffffffffu, u[i], 16);
+  memcpy(&v, u, sizeof(C));
+  return v;
+}
+
 template <int LR, bool INV, typename C> __device__ __forceinline__ void dft_reg(C* a) {
   if (LR == 1) dft2<INV>(a);
   if (LR == 2) dft4<INV>(a);
@@ -362,6 +407,101 @@ __device__ __forceinline__ void tma_issue_item(const TmaItem& t, int k) {
 template <typename T> struct DirectPencils { static constexpr bool value = true; };
 template <> struct DirectPencils<dd> { static constexpr bool value = false; };
 
+// The radix-16 first pass (Ns = 1: no pass twiddles) with each butterfly
+// split over two threads, for passes with at most half as many butterflies
+// as the block has threads: the unsplit pass would leave half the threads
+// idle while each of the others runs the whole 16-point DFT.
+//
+// 16 = 4 x 4 as in dft16 (input q = q2 + 4 q1, output p = p1 + 4 p2).  Half
+// h of a butterfly takes the inputs with q2 in {2h, 2h + 1}; its DFT-4s over
+// q1 are taken with the odd-q1 inputs negated when h = 1, which rotates
+// their outputs by two (register r holds p1 = (r + 2h) mod 4), so that
+// registers r = 2, 3 always hold the values the other half needs.  After
+// the w16^(p1 q2) twiddles the halves swap those four values (lanes l and
+// l ^ 16 hold the two halves of one butterfly) and each does the DFT-4s
+// over q2 for its p1 = 2h + r.  For h = 1 the swapped-in values are the
+// inputs q2 = 0, 1 and its own q2 = 2, 3, a cyclic shift by two, so outputs
+// with odd p2 come out negated and are negated back.  Inputs as in
+// fft_pass (global, staged box or shared); the outputs go to shared memory.
+template <typename T, int LG, bool INV, bool GIN, bool STR, bool SIN>
+__device__ __forceinline__ void fft_pass16_split(const cx_t<T>* __restrict__ src,
+                                                 cx_t<T>* __restrict__ dst, int npen,
+                                                 const GlobalPencils<T>& gio) {
+  using C = cx_t<T>;
+  constexpr int N = 1 << LG, LGNB = LG - 4, NB = 1 << LGNB, PS = pen_stride(N);
+  const int e = threadIdx.x;
+  // the caller checked 2 total <= blockDim and total % 16 == 0, so the
+  // threads below 2 total are whole warps
+  if (e < (npen << LGNB) * 2) {
+    const bool h = (e >> 4) & 1;
+    const int b = ((e >> 5) << 4) | (e & 15);
+    int pen, j;
+    if constexpr (STR) {
+      pen = b & ((1 << gio.lgc) - 1);
+      j = b >> gio.lgc;
+    } else {
+      pen = b >> LGNB;
+      j = b & (NB - 1);
+    }
+    const bool live = !GIN || pen < gio.npl;
+    auto in = [&](int q) -> C {
+      C v;
+      v.x = v.y = 0;
+      if (!live) return v;
+      const int t = j + q * NB;
+      if constexpr (GIN && SIN) {
+        if (!(gio.zempty && gio.zempty[t])) v = gio.sin[t * gio.ld + pen];
+      } else if constexpr (GIN && STR) {
+        if (!(gio.zempty && gio.zempty[t])) v = __ldcg(gio.p + (size_t)t * N + pen);
+      } else if constexpr (GIN) {
+        v = __ldcg(gio.p + (size_t)pen * N + t);
+      } else {
+        v = src[pen * PS + padi(t)];
+      }
+      return v;
+    };
+    C x[2][4];
+#pragma unroll
+    for (int q2l = 0; q2l < 2; ++q2l)
+#pragma unroll
+      for (int q1 = 0; q1 < 4; ++q1) x[q2l][q1] = in(2 * h + q2l + 4 * q1);
+#pragma unroll
+    for (int q2l = 0; q2l < 2; ++q2l) {
+      x[q2l][1] = cneg_if(x[q2l][1], h);
+      x[q2l][3] = cneg_if(x[q2l][3], h);
+      dft4<INV>(x[q2l][0], x[q2l][1], x[q2l][2], x[q2l][3]);
+    }
+    // register (q2l, r): exponent p1 q2 = r q2l (h = 0), ((r + 2) mod 4)(2 + q2l) (h = 1)
+    x[0][0] = cmul_w16_sel<INV, 0, 4>(x[0][0], h);
+    x[0][1] = cmul_w16_sel<INV, 0, 6>(x[0][1], h);
+    x[0][3] = cmul_w16_sel<INV, 0, 2>(x[0][3], h);
+    x[1][0] = cmul_w16_sel<INV, 0, 6>(x[1][0], h);
+    x[1][1] = cmul_w16_sel<INV, 1, 9>(x[1][1], h);
+    x[1][2] = cmul_w16_sel<INV, 2, 0>(x[1][2], h);
+    x[1][3] = cmul_w16_sel<INV, 3, 3>(x[1][3], h);
+    C y[2][4];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      y[r][0] = x[0][r];
+      y[r][1] = x[1][r];
+      y[r][2] = shfl_xor16(x[0][r + 2]);
+      y[r][3] = shfl_xor16(x[1][r + 2]);
+      dft4<INV>(y[r][0], y[r][1], y[r][2], y[r][3]);
+      y[r][1] = cneg_if(y[r][1], h);
+      y[r][3] = cneg_if(y[r][3], h);
+    }
+    if (live) {
+      // outputs p = p1 + 4 p2 of butterfly j at padi(16 j + p) = padi(16 j) + p
+      C* yb = dst + pen * PS + padi(j << 4) + 2 * h;
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int p2 = 0; p2 < 4; ++p2) yb[r + 4 * p2] = y[r][p2];
+    }
+  }
+  __syncthreads();
+}
+
 // One radix pass (see above).  SYM: scale the outputs by the symbol (a last
 // forward pass).  GIN: read the inputs from global memory (a first pass)
 // instead of src; GOUT: write the outputs to global memory (a last pass)
@@ -390,6 +530,18 @@ __device__ __forceinline__ void fft_pass(const cx_t<T>* __restrict__ src,
   static_assert(!GIN || S == 0, "global inputs feed the first pass");
   static_assert(!STR || kGlobal, "the strided order is for global accesses");
   const int total = npen << LGNB;
+  if constexpr (std::is_same<T, dd>::value && S == 0 && LR == 4 && LG > 4 && !SYM && !GOUT) {
+    // a first pass that is not also the last (fft_passes also instantiates
+    // unreached passes with S = 0, which keep the plain loop).  Only the
+    // double-float butterflies are split: the split costs six more twiddle
+    // multiplies per butterfly and the exchange, which pays where the
+    // arithmetic of a butterfly is long, not for float or float64 items
+    // (measured: float32 solve items 9.4 -> 10.6 us split)
+    if (2 * total <= (int)blockDim.x && (total & 15) == 0) {
+      fft_pass16_split<T, LG, INV, GIN, STR, SIN>(src, dst, npen, gio);
+      return;
+    }
+  }
   for (int e = threadIdx.x; e < total; e += blockDim.x) {
     int pen, j;
     if constexpr (STR) {
@@ -1253,6 +1405,20 @@ template <typename T>
 __host__ __device__ inline PencilLayout solve_layout(const GridDesc& g, int which) {
   const int cls = sizeof(T) == 4 ? 0 : 1;
   return solve_layout<T>(g.dim, g.n, which, g.pcap[cls][g.dim == 2 ? 1 : which]);
+}
+
+// Element type code of the solver's per-type choices: 0 float64, 1 float32,
+// 2 double-float.
+template <typename T> struct ElemCode;
+template <> struct ElemCode<double> { static constexpr int value = 0; };
+template <> struct ElemCode<float> { static constexpr int value = 1; };
+template <> struct ElemCode<dd> { static constexpr int value = 2; };
+
+// The persistent solver's layout of pencil pass `which`: the solve pass
+// takes the geometry's solver choice (g.scap), the 3D y passes the rule.
+template <typename T>
+__host__ __device__ inline PencilLayout solver_layout(const GridDesc& g, int which) {
+  return solve_layout<T>(g.dim, g.n, which, which == 1 ? g.scap[ElemCode<T>::value] : 0);
 }
 
 // pencil buffers, twiddles, sin^2 table

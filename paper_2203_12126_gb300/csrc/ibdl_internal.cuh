@@ -100,6 +100,10 @@ struct GridDesc {
   // [0] float32 layouts, [1] float64 and double-float layouts; [.][0] the 3D
   // y passes, [.][1] the solve pass (2D y, 3D z).  0: the fixed rule.
   int pcap[2][2] = {{0, 0}, {0, 0}};
+  // pencils per work item of the persistent solver's solve pass (2D y, 3D
+  // z), per element type [0] float64, [1] float32, [2] double-float; 0: the
+  // fixed rule
+  int scap[3] = {0, 0, 0};
 };
 
 // Host constants of the symbol multiply: the solve scales mode k by
@@ -157,6 +161,17 @@ cudaError_t check_launch();
 // Device buffer of per-phase times of the persistent solver while profiling
 // is on (nullptr otherwise); kPhaseSlots (id) pairs of (ns, count).
 constexpr int kPhaseSlots = 16;
+// The same buffer holds the solver's item trace after the phase times: word
+// kTraceFlag switches it on (nonzero) for the launches that follow, word
+// kTraceFlag + 1 is spare, then kTraceCap records of three words (start ns,
+// end ns, and block << 40 | instance << 24 | phase << 20 | prec << 18 |
+// item), each block of a launch writing its own kTraceCap / blocks of them
+// (start 0: unused).  Phase 15 marks a hand-off: the finishing block
+// choosing and publishing the next phase (item = that phase, or 15 when the
+// instance stops).
+constexpr int kTraceFlag = 2 * kPhaseSlots;
+constexpr int kTraceCap = 1 << 16;
+constexpr size_t kProfWords = 2 * kPhaseSlots + 2 + 3 * (size_t)kTraceCap;
 unsigned long long* prof_phase_buffer();
 // Sets the per-thread message of ibdl_last_error_message and returns s.
 ibdl_status set_last_error(ibdl_status s, const char* msg);

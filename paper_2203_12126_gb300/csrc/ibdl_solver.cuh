@@ -60,6 +60,10 @@ struct SolveInst {
   double* hist;
   int hist_cap;
   int single;       // 1: all vector work of a round on one block (m <= kSingleMax)
+  // work items of matvec phase 0..4 in the float64-grade (float64 or
+  // double-float, [.][0]) and float32 ([.][1]) operator; filled on the host
+  // (solver_fill_items), so that a phase hand-off reads them
+  int mv_nitems[5][2];
 };
 
 // Mutable; written by the instance's control thread.
@@ -71,6 +75,8 @@ struct SolveState {
 };
 
 int solver_smem_bytes(const GridDesc& g, int rows, int need32);
+// Fills I.mv_nitems from the instance's grid, tiling and element types.
+void solver_fill_items(SolveInst& I);
 // Dynamic shared memory of one matvec work item per kind (row tile, pencil
 // layouts) for element type elem (0 float64, 1 float32, 2 double-float).
 void solver_item_smem(const GridDesc& g, int rows, int elem, size_t out[3]);

@@ -41,6 +41,15 @@ namespace ibdl {
 
 constexpr unsigned kSpinLimit = 1u << 27;  // x >= 20 ns sleeps: a few seconds
 
+// Acquire-release fence at GPU scope: orders this thread's earlier memory
+// operations (and, after a block barrier, its block's) before its later
+// ones for every observer on the GPU.  The scheduler's message passing (data,
+// then a counter or claim word; a counter or claim word, then data) needs no
+// more than that, and it is cheaper than a sequentially consistent fence.
+__device__ __forceinline__ void fence_acq_rel() {
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
+
 // Counting barrier among `parties` blocks on ctr[0] (arrivals) and ctr[1]
 // (generation).  The spin is bounded (`limit` polls): on timeout it raises
 // *err, which every later barrier sees, and all blocks leave the kernel.
@@ -187,15 +196,15 @@ __device__ __forceinline__ const double* mv_input(const SolveInst& I, const Roun
 }
 
 template <typename T>
-__device__ int mv_items(const SolveInst& I, int phase) {
+__host__ __device__ int mv_items(const SolveInst& I, int phase) {
   const int d = I.g.dim, n = I.g.n;
   if (phase == 0 || phase == 4) return I.b.ntiles;
   PencilLayout L;
   if (d == 2) {
     if (phase != 2) return 0;
-    L = solve_layout<T>(2, n, 1);
+    L = solver_layout<T>(I.g, 1);
   } else {
-    L = solve_layout<T>(3, n, phase == 2 ? 1 : 0);
+    L = solver_layout<T>(I.g, phase == 2 ? 1 : 0);
   }
   return (L.npencils + L.c - 1) / L.c;
 }
@@ -244,7 +253,7 @@ __device__ __noinline__ void solver_pencils(const SolveInst& I, int which, int i
   // the matvec's grid feeds only the interpolation and has no grid source:
   // 3D y-pass items of planes without points are skipped (both directions)
   const int* zskip = (g.dim == 3 && MODE != 2) ? I.b.start : nullptr;
-  phase_pencils<T, MODE>(g, solve_layout<T>(g.dim, g.n, which), ws.spec, ws.tw, ws.s2, cfac,
+  phase_pencils<T, MODE>(g, solver_layout<T>(g, which), ws.spec, ws.tw, ws.s2, cfac,
                          scale0, item, smem, zskip, g.n / I.b.rows,
                          (g.dim == 3 && MODE == 2) ? I.b.zempty : nullptr);
 }
@@ -821,12 +830,17 @@ __device__ int next_phase(const SolveInst& I, int phase, int action) {
 }
 
 __device__ int items_of(const SolveInst& I, const PhaseDesc& d) {
-  // each element type's own pencil layout (run_item dispatches the same way)
-  if (d.phase < 5)
-    return d.prec ? mv_items<float>(I, d.phase)
-                  : (I.dd64 ? mv_items<dd>(I, d.phase) : mv_items<double>(I, d.phase));
+  if (d.phase < 5) return I.mv_nitems[d.phase][d.prec ? 1 : 0];
   if (d.phase == kPhaseSingle) return 1;
   return I.nchunk;
+}
+
+// each element type's own pencil layout (run_item dispatches the same way)
+void solver_fill_items(SolveInst& I) {
+  for (int ph = 0; ph < 5; ++ph) {
+    I.mv_nitems[ph][0] = I.dd64 ? mv_items<dd>(I, ph) : mv_items<double>(I, ph);
+    I.mv_nitems[ph][1] = mv_items<float>(I, ph);
+  }
 }
 
 // The round view of the state; `active` is false when the instance is done.
@@ -843,8 +857,12 @@ __device__ bool view_from_state(const SolveState* S, PhaseDesc& d) {
 // instances that are done or have used their rounds for this launch.
 // `cur` is the descriptor of the phase whose last item the caller finished:
 // the stored one, which nobody else can change now.
-__device__ void advance(const SolveInst& I, const SolveState* S, unsigned* bar, int k,
-                        int max_rounds, const PhaseDesc& cur) {
+// With take_first the caller keeps item 0 of the new phase for itself (the
+// claim word is published with item 1 next): returns true and the new
+// descriptor in *out when there is such an item.
+__device__ bool advance(const SolveInst& I, const SolveState* S, unsigned* bar, int k,
+                        int max_rounds, const PhaseDesc& cur, bool take_first,
+                        PhaseDesc* out) {
   PhaseDesc d = cur;
   int np = next_phase(I, d.phase, d.action);
   if (np < 0) {
@@ -854,10 +872,10 @@ __device__ void advance(const SolveInst& I, const SolveState* S, unsigned* bar, 
       d.nitems = 0;
       d.epoch++;
       store_desc(desc_of(bar, k), d);
-      __threadfence();
+      fence_acq_rel();
       atomicExch(claim_word(bar, k), claim_value(d.epoch, 0));
       atomicAdd(bar + 3, 1u);
-      return;
+      return false;
     }
     np = first_phase(I, d.action);
   }
@@ -866,8 +884,11 @@ __device__ void advance(const SolveInst& I, const SolveState* S, unsigned* bar, 
   d.epoch++;
   store_desc(desc_of(bar, k), d);
   *(volatile unsigned*)done_word(bar, k) = 0u;
-  __threadfence();
-  atomicExch(claim_word(bar, k), claim_value(d.epoch, d.nitems));
+  fence_acq_rel();
+  const bool take = take_first && d.nitems > 0;
+  atomicExch(claim_word(bar, k), claim_value(d.epoch, d.nitems) + (take ? 1ull : 0ull));
+  *out = d;
+  return take;
 }
 
 __device__ void run_item(const SolveInst& I, SolveState* S, const PhaseDesc& d, int item,
@@ -907,6 +928,23 @@ __device__ __forceinline__ void add_time(unsigned long long* ptimes, int id,
                                          unsigned long long dt) {
   atomicAdd(ptimes + 2 * id, dt);
   atomicAdd(ptimes + 2 * id + 1, 1ull);
+}
+
+// One record of the item trace (thread 0, while the trace is on): block b
+// owns records [b * per_block, (b + 1) * per_block) of the trace and counts
+// its own in *n, so a record costs three stores and no atomic.
+__device__ __forceinline__ void trace_item(unsigned long long* ptimes, int* n,
+                                           unsigned long long t0, unsigned long long t1, int k,
+                                           int phase, int prec, int item) {
+  const int per_block = kTraceCap / (int)gridDim.x;
+  if (*n >= per_block) return;
+  const size_t r = (size_t)blockIdx.x * per_block + (*n)++;
+  unsigned long long* rec = ptimes + kTraceFlag + 2 + 3 * r;
+  rec[0] = t0;
+  rec[1] = t1;
+  rec[2] = ((unsigned long long)blockIdx.x << 40) | ((unsigned long long)(k & 0xffff) << 24) |
+           ((unsigned long long)(phase & 15) << 20) | ((unsigned long long)(prec & 3) << 18) |
+           (unsigned long long)(item & 0x3ffff);
 }
 
 struct ItemSlot {
@@ -949,12 +987,28 @@ __global__ void __launch_bounds__(kSolverThreads, 2)
   unsigned long long idle0 = 0;
   int rot = bid % (ninst > 0 ? ninst : 1);
   const int lane = threadIdx.x & 31;
+  // thread 0: the slot already holds an item this block claimed when it
+  // finished its last one (the next item of the same phase, or item 0 of the
+  // phase it handed off to)
+  int preclaimed = 0;
+  // the item trace: switched on for the whole launch, or not at all
+  const bool tracing =
+      ptimes && threadIdx.x == 0 && *(volatile unsigned long long*)(ptimes + kTraceFlag) != 0ull;
+  int ntrace = 0;
   for (;;) {
     // warp 0 looks for an item: its lanes probe 32 instances at a time (the
     // descriptor's epoch and item count and the claim word, read around L1)
     if (threadIdx.x < 32) {
+      // a block with an item in hand runs it; one without first checks the
+      // error word (set when a wait gave up: then every block leaves)
       int have = 0;
-      if (lane == 0 && *(volatile unsigned*)(bar + 2) != 0u) have = -1;  // error: leave
+      if (lane == 0) {
+        if (preclaimed)
+          have = 1;
+        else if (*(volatile unsigned*)(bar + 2) != 0u)
+          have = -1;
+      }
+      preclaimed = 0;
       have = __shfl_sync(0xffffffffu, have, 0);
       for (int base = 0; base < ninst && have == 0; base += 32) {
         const int t = base + lane;
@@ -969,7 +1023,7 @@ __global__ void __launch_bounds__(kSolverThreads, 2)
           if (lane == 0) {
             const unsigned long long w = atomicAdd(claim_word(bar, kk), 1ull);
             if (claim_open(w)) {
-              __threadfence();
+              fence_acq_rel();
               slot.k = kk;
               slot.item = (int)(w & 0xffffffffu);
               slot.d = load_desc(desc_of(bar, kk));
@@ -1019,14 +1073,47 @@ __global__ void __launch_bounds__(kSolverThreads, 2)
     run_item(insts[k], states + k, d, item, smem, R);
     __syncthreads();
     if (threadIdx.x == 0) {
-      if (ptimes) add_time(ptimes, d.phase < 5 ? d.phase + 5 * d.prec : 10, global_ns() - ta);
-      __threadfence();
+      unsigned long long tb = 0;
+      if (ptimes) {
+        tb = global_ns();
+        add_time(ptimes, d.phase < 5 ? d.phase + 5 * d.prec : 10, tb - ta);
+        if (tracing) trace_item(ptimes, &ntrace, ta, tb, k, d.phase, d.prec, item);
+      }
+      fence_acq_rel();  // the item's writes before its done count
+      // the next item of the same phase is claimed together with the done
+      // count (both atomics in flight at once): a block that stays on one
+      // phase needs no scan and no descriptor read between its items
+      const unsigned long long w = atomicAdd(claim_word(bar, k), 1ull);
       const unsigned prior = atomicAdd(done_word(bar, k), 1u);
+      if (claim_open(w)) {
+        slot.k = k;
+        slot.item = (int)(w & 0xffffffffu);
+        if ((unsigned)(w >> 48) == ((unsigned)d.epoch & 0xffffu)) {
+          slot.d = d;
+        } else {
+          // another block advanced the phase between the two atomics
+          fence_acq_rel();
+          slot.d = load_desc(desc_of(bar, k));
+        }
+        preclaimed = 1;
+      }
       if ((int)prior == d.nitems - 1) {
         // every item of the phase is done: see their writes (the state of
-        // the control step included) before choosing the next phase
-        __threadfence();
-        advance(insts[k], states + k, bar, k, max_rounds, d);
+        // the control step included) before choosing the next phase; the
+        // claim above found the phase exhausted, so this block takes item 0
+        // of the next one
+        fence_acq_rel();
+        PhaseDesc nd = d;
+        const bool took = advance(insts[k], states + k, bar, k, max_rounds, d,
+                                  !preclaimed, &nd);
+        if (took) {
+          slot.k = k;
+          slot.item = 0;
+          slot.d = nd;
+          preclaimed = 1;
+        }
+        if (tracing)
+          trace_item(ptimes, &ntrace, tb, global_ns(), k, 15, nd.prec, took ? nd.phase : 15);
       }
     }
   }
@@ -1039,8 +1126,8 @@ __global__ void __launch_bounds__(kSolverThreads, 2)
 template <typename T>
 static void item_smem(const GridDesc& g, int rows, size_t out[3]) {
   out[0] = rows_smem_bytes<T>(g.n, rows);
-  out[1] = pencil_smem_bytes<T>(solve_layout<T>(g.dim, g.n, 1), g.n);
-  out[2] = g.dim == 3 ? pencil_smem_bytes<T>(solve_layout<T>(g.dim, g.n, 0), g.n) : 0;
+  out[1] = pencil_smem_bytes<T>(solver_layout<T>(g, 1), g.n);
+  out[2] = g.dim == 3 ? pencil_smem_bytes<T>(solver_layout<T>(g, 0), g.n) : 0;
 }
 
 void solver_item_smem(const GridDesc& g, int rows, int elem, size_t out[3]) {

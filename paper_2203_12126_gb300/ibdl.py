@@ -40,7 +40,8 @@ EXPORTS = [
     "ibdl_server_clock", "ibdl_server_submit", "ibdl_server_step", "ibdl_server_take",
     "ibdl_server_get_stats", "ibdl_tuning_enable", "ibdl_tuning_set", "ibdl_indicator",
     "ibdl_near_boundary", "ibdl_selftest_bounded_wait", "ibdl_solver_smem_query",
-    "ibdl_tuning_set_pencils",
+    "ibdl_tuning_set_pencils", "ibdl_profile_trace", "ibdl_profile_trace_read",
+    "ibdl_geometry_set_solver_pencils",
 ]
 
 
@@ -177,6 +178,9 @@ def load(path: str = LIB_PATH):
         "ibdl_solver_smem_query": (C.c_int, [i32, i32, i32, i32, C.POINTER(i64),
                                              C.POINTER(i64), C.POINTER(i32)]),
         "ibdl_tuning_set_pencils": (C.c_int, [i32, i32, i32, i32, i32]),
+        "ibdl_profile_trace": (C.c_int, [i32]),
+        "ibdl_profile_trace_read": (i64, [vp, i64]),
+        "ibdl_geometry_set_solver_pencils": (C.c_int, [vp, i32, i32, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -249,6 +253,26 @@ def profile_read(reset: bool = True) -> dict:
     k = lib.ibdl_profile_read(arr, k, 1 if reset else 0)
     return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms))
             for i in range(k)}
+
+
+def profile_trace(on: bool = True) -> None:
+    """Switch the persistent solver's work-item trace on or off (profiling
+    must be on)."""
+    _check(load().ibdl_profile_trace(1 if on else 0))
+
+
+TRACE_CAP = 1 << 16
+
+
+def profile_trace_read():
+    """(records, count): the trace records as a (k, 3) uint64 array (start
+    ns, end ns, packed ids; see ibdl.h) and their number; clears the trace."""
+    import numpy as np
+    out = np.zeros((TRACE_CAP, 3), dtype=np.uint64)
+    k = int(load().ibdl_profile_trace_read(out.ctypes.data, TRACE_CAP))
+    if k < 0:
+        raise IbdlError(ERR_CUDA, "trace read failed")
+    return out[:k].copy(), k
 
 
 def selftest_bounded_wait(spin_limit=1 << 16, stream=None) -> int:
@@ -462,6 +486,12 @@ class Geometry:
             v = getattr(gi, f)
             out[f] = list(v) if isinstance(v, C.Array) else v
         return out
+
+    def set_solver_pencils(self, c_f64=0, c_f32=0, c_dd=0):
+        """Pencils per work item of the persistent solver's solve pass, per
+        element type (0: the fixed rule)."""
+        _check(load().ibdl_geometry_set_solver_pencils(self._h, int(c_f64), int(c_f32),
+                                                       int(c_dd)))
 
     def apply(self, q, y, precision=None, stream=None):
         lib = load()

@@ -165,3 +165,87 @@ def test_row_writes_of_the_x_inverse_pass(lg, rows):
     imag = (2 * pen + 1) * n + t
     count = np.bincount(np.concatenate([real.ravel(), imag.ravel()]), minlength=rows * n)
     assert count.size == rows * n and np.all(count == 1)
+
+
+# ---- the radix-16 first pass split over two threads (fft_pass16_split) ----
+
+# exponent of w16 for register (q2l, r) of half h: the table in the kernel
+SPLIT_TW = {(0, 0): (0, 4), (0, 1): (0, 6), (0, 2): (0, 0), (0, 3): (0, 2),
+            (1, 0): (0, 6), (1, 1): (1, 9), (1, 2): (2, 0), (1, 3): (3, 3)}
+
+
+def dft4(v, sign):
+    w = np.exp(sign * 2j * np.pi * np.outer(np.arange(4), np.arange(4)) / 4)
+    return v @ w
+
+
+def split_radix16(x, inverse):
+    """Both halves of one split butterfly, step by step as the kernel takes
+    them: returns the 16 outputs each half stores, by output index."""
+    sign = 1.0 if inverse else -1.0
+    w16 = lambda e: np.exp(sign * 2j * np.pi * e / 16)
+    regs = {}
+    for h in (0, 1):
+        reg = np.zeros((2, 4), complex)
+        for q2l in range(2):
+            v = np.array([x[2 * h + q2l + 4 * q1] for q1 in range(4)])
+            if h:
+                v[1::2] = -v[1::2]          # rotates the DFT-4 outputs by two
+            reg[q2l] = dft4(v, sign)
+            for r in range(4):
+                reg[q2l, r] *= w16(SPLIT_TW[(q2l, r)][h])
+        regs[h] = reg
+    out = {}
+    for h in (0, 1):
+        own, other = regs[h], regs[1 - h]
+        for r in range(2):
+            y = dft4(np.array([own[0, r], own[1, r], other[0, r + 2], other[1, r + 2]]), sign)
+            if h:
+                y[1::2] = -y[1::2]
+            for p2 in range(4):
+                p = 2 * h + r + 4 * p2
+                assert p not in out
+                out[p] = y[p2]
+    return np.array([out[p] for p in range(16)])
+
+
+@pytest.mark.parametrize("inverse", [False, True])
+def test_split_radix16_butterfly_is_the_16_point_dft(inverse):
+    rng = np.random.default_rng(16 + inverse)
+    for _ in range(4):
+        x = rng.standard_normal(16) + 1j * rng.standard_normal(16)
+        ref = 16 * np.fft.ifft(x) if inverse else np.fft.fft(x)
+        assert np.allclose(split_radix16(x, inverse), ref, rtol=0, atol=1e-12)
+
+
+def test_split_twiddle_table_is_p1_times_q2():
+    # register (q2l, r) of half h holds p1 = (r + 2h) mod 4 of q2 = 2h + q2l
+    for (q2l, r), (e0, e1) in SPLIT_TW.items():
+        for h, e in ((0, e0), (1, e1)):
+            assert e % 16 == (((r + 2 * h) % 4) * (2 * h + q2l)) % 16
+
+
+@pytest.mark.parametrize("lg", [5, 6, 8, 10, 11])
+@pytest.mark.parametrize("npen", [1, 2, 4, 16])
+@pytest.mark.parametrize("strided", [False, True])
+def test_split_first_pass_threads_cover_each_butterfly_half_once(lg, npen, strided):
+    """Thread e < 2 total takes half h = (e >> 4) & 1 of butterfly
+    b = ((e >> 5) << 4) | (e & 15); lanes l and l ^ 16 hold the two halves
+    of one butterfly, and every (pencil, j, h) is taken once."""
+    nb = 1 << (lg - 4)
+    total = npen * nb
+    if total % 16:
+        pytest.skip("the kernel keeps the plain pass unless total % 16 == 0")
+    lgc = npen.bit_length() - 1
+    seen = set()
+    for e in range(2 * total):
+        h = (e >> 4) & 1
+        b = ((e >> 5) << 4) | (e & 15)
+        assert b < total
+        pen, j = ((b & (npen - 1), b >> lgc) if strided else (b >> (lg - 4), b & (nb - 1)))
+        assert (pen, j, h) not in seen
+        seen.add((pen, j, h))
+        partner = e ^ 16
+        assert partner < 2 * total and partner >> 5 == e >> 5
+        assert ((partner >> 5) << 4) | (partner & 15) == b and (partner >> 4) & 1 != h
+    assert len(seen) == 2 * total
