@@ -694,6 +694,20 @@ SolveInst make_inst(ibdl_geometry_s* g, const ibdl_solve_opts& o, int batch_size
   I.hist = g->d_hist;
   I.hist_cap = kHistCap;
   I.single = g->m <= kSingleMax && batch_size >= kSingleMinBatch && !g_force_multi;
+  // A few 2D instances in one launch share the blocks: float32 solve items
+  // of 4 pencils (about 129 per instance) let them run side by side (the C2
+  // pair: 1.268 -> 1.251 ms against the rule's 2 pencils), where the item
+  // fits the geometry's reservation and no choice was set on the geometry.
+  if (I.g.dim == 2 && batch_size >= 2 && batch_size <= kDdMaxBatch && I.g.scap[1] == 0) {
+    const PencilLayout base = solve_layout<float>(2, I.g.n, 1);
+    GridDesc gd = I.g;
+    gd.scap[1] = 4;
+    size_t need[3];
+    solver_item_smem(gd, I.b.rows, 1, need);
+    if (pencils_admissible<float>(I.g.n, base.estride, base.pg, 4) &&
+        need[1] <= (size_t)g->solver_smem)
+      I.g.scap[1] = 4;
+  }
   solver_fill_items(I);
   return I;
 }

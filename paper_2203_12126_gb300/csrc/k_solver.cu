@@ -109,7 +109,30 @@ constexpr int kMaxCols = 66;  // restart (<= 64) + 2
 
 struct BlockRed;
 __device__ void control(const SolveInst& I, SolveState* S, const RoundView& v, double hn,
-                        double beta, double bnorm2, BlockRed& R);
+                        double beta, double bnorm2, BlockRed& R,
+                        const SolveState* pre = nullptr);
+
+// The instance state as the control step reads it: written by other blocks
+// in earlier rounds, so read around L1.
+__device__ __forceinline__ SolveState load_state(const SolveState* S) {
+  SolveState s;
+  volatile const SolveState* vs = S;
+  s.action = vs->action;
+  s.prec = vs->prec;
+  s.j = vs->j;
+  s.kdim = vs->kdim;
+  s.iters = vs->iters;
+  s.outer = vs->outer;
+  s.status = vs->status;
+  s.matvecs = vs->matvecs;
+  s.nhist = vs->nhist;
+  s.xinit = vs->xinit;
+  s.beta = vs->beta;
+  s.bnorm = vs->bnorm;
+  s.tol_abs = vs->tol_abs;
+  s.rel = vs->rel;
+  return s;
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -142,13 +165,25 @@ __device__ void reduce_parts(const double* part, int nchunk, int pstride, int c0
 
 // Writes, for c < ncols, the block sum of x_i * V_c[i] over this chunk, and
 // optionally the sum of x_i^2 as column ncols, to part[chunk][.].
+// Basis columns are read kColBatch at a time, all loads of a batch in
+// flight together (one L2 round trip per batch, not per column).
+constexpr int kColBatch = 8;
+
 __device__ void chunk_dots(const SolveInst& I, double xi, bool valid, int i, int ncols,
                            bool with_norm, double* part, int chunk, BlockRed& R) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int c = 0; c < ncols; ++c) {
-    const double v = valid ? xi * __ldcg(I.V + (size_t)c * I.ld + i) : 0.0;
-    const double s = warp_sum(v);
-    if (lane == 0) R.red[c][wid] = s;
+  for (int c0 = 0; c0 < ncols; c0 += kColBatch) {
+    double vc[kColBatch];
+#pragma unroll
+    for (int u = 0; u < kColBatch; ++u)
+      vc[u] = (valid && c0 + u < ncols) ? __ldcg(I.V + (size_t)(c0 + u) * I.ld + i) : 0.0;
+#pragma unroll
+    for (int u = 0; u < kColBatch; ++u) {
+      if (c0 + u < ncols) {
+        const double sm = warp_sum(xi * vc[u]);
+        if (lane == 0) R.red[c0 + u][wid] = sm;
+      }
+    }
   }
   if (with_norm) {
     const double s = warp_sum(valid ? xi * xi : 0.0);
@@ -167,7 +202,15 @@ __device__ void chunk_dots(const SolveInst& I, double xi, bool valid, int i, int
 // w - sum_{c < ncols} h[c] V_c[i]
 __device__ __forceinline__ double sub_projection(const SolveInst& I, double w, int i, int ncols,
                                                  const double* h) {
-  for (int c = 0; c < ncols; ++c) w -= h[c] * __ldcg(I.V + (size_t)c * I.ld + i);
+  for (int c0 = 0; c0 < ncols; c0 += kColBatch) {
+    double vc[kColBatch];
+#pragma unroll
+    for (int u = 0; u < kColBatch; ++u)
+      vc[u] = c0 + u < ncols ? __ldcg(I.V + (size_t)(c0 + u) * I.ld + i) : 0.0;
+#pragma unroll
+    for (int u = 0; u < kColBatch; ++u)
+      if (c0 + u < ncols) w -= h[c0 + u] * vc[u];
+  }
   return w;
 }
 
@@ -292,15 +335,38 @@ __device__ void phase_D(const SolveInst& I, SolveState* S, const RoundView& v, i
   const bool valid = i < I.p.m;
   double* part1 = I.part;
   if (v.action == ACT_FINISH) {
-    if (chunk == 0 && threadIdx.x == 0) {
+    if (chunk == 0) {
+      // back substitution R y = g (R: the rotated Hessenberg's k x k upper
+      // triangle, column l at H + l ldh).  The block stages R and g in shared
+      // memory in one round of loads (up to kMaxCols (kSolverThreads / 32)
+      // entries; larger k read them as they go), then one thread solves.
       const int k = v.kdim, ldh = I.restart + 1;
-      for (int r = k - 1; r >= 0; --r) {
-        double s = __ldcg(I.gv + r);
-        for (int l = r + 1; l < k; ++l) s -= __ldcg(I.H + (size_t)l * ldh + r) * I.ysol[l];
-        const double dgn = __ldcg(I.H + (size_t)r * ldh + r);
-        I.ysol[r] = dgn != 0.0 ? s / dgn : 0.0;
+      const bool staged = k * (k + 1) / 2 <= kMaxCols * (kSolverThreads / 32);
+      double* tri = &R.red[0][0];  // entry (r, l), r <= l, at l (l + 1) / 2 + r
+      if (staged) {
+        for (int e = threadIdx.x; e < k * (k + 1) / 2; e += blockDim.x) {
+          int l = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
+          while (l * (l + 1) / 2 > e) --l;
+          while ((l + 1) * (l + 2) / 2 <= e) ++l;
+          const int r = e - l * (l + 1) / 2;
+          tri[e] = __ldcg(I.H + (size_t)l * ldh + r);
+        }
+        for (int r = threadIdx.x; r < k; r += blockDim.x) R.h[r] = __ldcg(I.gv + r);
       }
-      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        for (int r = k - 1; r >= 0; --r) {
+          double sacc = staged ? R.h[r] : __ldcg(I.gv + r);
+          for (int l = r + 1; l < k; ++l)
+            sacc -= (staged ? tri[l * (l + 1) / 2 + r] : __ldcg(I.H + (size_t)l * ldh + r)) *
+                    R.col[l];
+          const double dgn = staged ? tri[r * (r + 1) / 2 + r] : __ldcg(I.H + (size_t)r * ldh + r);
+          R.col[r] = dgn != 0.0 ? sacc / dgn : 0.0;
+        }
+      }
+      __syncthreads();
+      // read in the next phase: released with the item's done count
+      for (int r = threadIdx.x; r < k; r += blockDim.x) I.ysol[r] = R.col[r];
     }
     return;
   }
@@ -384,6 +450,21 @@ __device__ void phase_E(const SolveInst& I, SolveState* S, const RoundView& v, i
     cgs_pass(I, v, chunk, R, part1, part2);
     return;
   }
+  // item nchunk runs the round's control step beside the vector work of
+  // items 0 .. nchunk - 1 (it reads the same reduced sums and nothing they
+  // write), so the step's serial float64 work is off the phase's longest item
+  if (chunk == I.nchunk) {
+    SolveState st;
+    if (threadIdx.x == 0) st = load_state(S);
+    if (v.action == ACT_FINISH) {
+      if (threadIdx.x == 0) control(I, S, v, 0, 0, 0, R, &st);
+    } else {
+      reduce_parts(part1, I.nchunk, I.pstride, 0, 2, R.h);
+      if (threadIdx.x == 0) control(I, S, v, 0, sqrt(R.h[0]), R.h[1], R, &st);
+    }
+    __syncthreads();
+    return;
+  }
   const int i = chunk * blockDim.x + threadIdx.x;
   const bool valid = i < I.p.m;
   if (v.action == ACT_FINISH) {
@@ -392,28 +473,29 @@ __device__ void phase_E(const SolveInst& I, SolveState* S, const RoundView& v, i
     __syncthreads();
     if (valid) I.x[i] = sub_projection(I, __ldcg(I.x + i), i, v.kdim, R.h);
     __syncthreads();
-    if (chunk == 0 && threadIdx.x == 0) control(I, S, v, 0, 0, 0, R);
-    __syncthreads();
     return;
   }
-  // residual actions: V0 = r / ||r||, and the round's control step
+  // residual actions: V0 = r / ||r||
+  const double ri = valid ? __ldcg(I.r + i) : 0.0;
   reduce_parts(part1, I.nchunk, I.pstride, 0, 2, R.h);
   const double beta = sqrt(R.h[0]);
-  const double b2 = R.h[1];
   const double inv = (beta > 0 && isfinite(beta)) ? 1.0 / beta : 0.0;
-  if (valid) I.V[i] = __ldcg(I.r + i) * inv;
-  __syncthreads();
-  if (chunk == 0 && threadIdx.x == 0) control(I, S, v, 0, beta, b2, R);
+  if (valid) I.V[i] = ri * inv;
   __syncthreads();
 }
 
 // Control of one instance (one thread).  hn: new subdiagonal, beta: residual
-// norm of a residual action, bnorm2: ||b||^2 partial sum.
+// norm of a residual action, bnorm2: ||b||^2 partial sum; pre: the state,
+// when the caller loaded it ahead (it cannot change during the phase).  Its
+// writes reach the other blocks through the block's release of its done
+// count at the end of the item.
 __device__ void control(const SolveInst& I, SolveState* S, const RoundView& v, double hn,
-                        double beta, double bnorm2, BlockRed& R) {
+                        double beta, double bnorm2, BlockRed& R, const SolveState* pre) {
   const int ldh = I.restart + 1;
   SolveState s;
-  {
+  if (pre) {
+    s = *pre;
+  } else {
     // written by other blocks in earlier rounds: read around L1
     volatile const SolveState* vs = S;
     s.action = vs->action;
@@ -442,12 +524,17 @@ __device__ void control(const SolveInst& I, SolveState* S, const RoundView& v, d
       cj[r + 1] = -sr * cj[r] + cr * cj[r + 1];
       cj[r] = t;
     }
+    // the rotation zeroing b against a; the Hessenberg entries of this
+    // second-kind operator are O(1), far from where the plain
+    // sqrt(a^2 + b^2) could overflow, and one reciprocal serves both ratios
+    // (float64 is slow on this part, and this sits on every step's path)
     const double a = cj[j], b = cj[j + 1];
-    const double den = hypot(a, b);
+    const double den = sqrt(fma(a, a, b * b));
     double c = 1.0, sn = 0.0;
     if (den > 0) {
-      c = a / den;
-      sn = b / den;
+      const double inv = 1.0 / den;
+      c = a * inv;
+      sn = b * inv;
     }
     cj[j] = den;
     cj[j + 1] = 0.0;
@@ -509,7 +596,6 @@ __device__ void control(const SolveInst& I, SolveState* S, const RoundView& v, d
     }
   }
   *S = s;
-  __threadfence();
 }
 
 // Second CGS pass of an Arnoldi step, normalisation and control: h2 and
@@ -520,33 +606,52 @@ __device__ void phase_F(const SolveInst& I, SolveState* S, const RoundView& v, i
                         BlockRed& R) {
   const int j = v.j, ncols = j + 1, ldh = I.restart + 1;
   double* part2 = I.part + (size_t)I.nchunk * I.pstride;
+  // item nchunk runs the control step beside the normalisation of items
+  // 0 .. nchunk - 1; its inputs (the state, the Hessenberg column's first
+  // pass, the earlier rotations, g_j) go out beside the partial sums' loads
+  const bool ctl_item = chunk == I.nchunk;
+  double hcol = 0, csr = 0, snr = 0, gj = 0;
+  SolveState st;
+  if (ctl_item) {
+    const int r = threadIdx.x;
+    if (r <= j) hcol = __ldcg(I.H + (size_t)j * ldh + r);
+    if (r < j) {
+      csr = __ldcg(I.cs + r);
+      snr = __ldcg(I.sn + r);
+    }
+    if (r == 0) {
+      gj = __ldcg(I.gv + j);
+      st = load_state(S);
+    }
+  }
   reduce_parts(part2, I.nchunk, I.pstride, 0, ncols + 1, R.h);
   double ss = 0;
   for (int c = 0; c < ncols; ++c) ss += R.h[c] * R.h[c];
   const double d2 = R.h[ncols] - ss;
   const double hn = sqrt(d2 > 0.0 ? d2 : 0.0);
+  if (ctl_item) {
+    // stage the Hessenberg column (h1 from phase E plus h2), the earlier
+    // rotations and g_j for the control step (j < restart <= blockDim)
+    const int r = threadIdx.x;
+    if (r <= j) R.col[r] = hcol + R.h[r];
+    if (r < j) {
+      R.cs[r] = csr;
+      R.sn[r] = snr;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      R.h[0] = gj;
+      control(I, S, v, hn, 0, 0, R, &st);
+    }
+    __syncthreads();
+    return;
+  }
   const double inv = (hn > 0 && isfinite(hn)) ? 1.0 / hn : 0.0;
   const int i = chunk * blockDim.x + threadIdx.x;
   if (i < I.p.m) {
     double* wp = I.V + (size_t)(j + 1) * I.ld;
     const double w = sub_projection(I, __ldcg(wp + i), i, ncols, R.h);
     wp[i] = inv != 0.0 ? w * inv : w;
-  }
-  if (chunk == 0) {
-    // stage the Hessenberg column (h1 from phase E plus h2), the earlier
-    // rotations and g_j for the control step
-    for (int r = threadIdx.x; r <= j; r += blockDim.x) {
-      R.col[r] = __ldcg(I.H + (size_t)j * ldh + r) + R.h[r];
-      if (r < j) {
-        R.cs[r] = __ldcg(I.cs + r);
-        R.sn[r] = __ldcg(I.sn + r);
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      R.h[0] = __ldcg(I.gv + j);
-      control(I, S, v, hn, 0, 0, R);
-    }
   }
   __syncthreads();
 }
@@ -832,6 +937,10 @@ __device__ int next_phase(const SolveInst& I, int phase, int action) {
 __device__ int items_of(const SolveInst& I, const PhaseDesc& d) {
   if (d.phase < 5) return I.mv_nitems[d.phase][d.prec ? 1 : 0];
   if (d.phase == kPhaseSingle) return 1;
+  // the control step is an item of its own in F, and in E when the round
+  // ends there (phase_E, phase_F)
+  if (d.phase == kPhaseF || (d.phase == kPhaseE && d.action != ACT_MV_ARNOLDI))
+    return I.nchunk + 1;
   return I.nchunk;
 }
 
