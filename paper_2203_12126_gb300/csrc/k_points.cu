@@ -250,11 +250,67 @@ cudaError_t launch_plane_flags(const int* start, int ngroups, int n, unsigned ch
 
 // ---- interpolation ------------------------------------------------------------
 
+// The four x taps grid[x0 .. x0 + 3] (mod n) of one grid row: away from the
+// row's end, from the aligned 16-byte vectors that cover them (one or two
+// loads instead of four), else one load per tap with the periodic wrap.  The
+// row starts a multiple of n >= 16 elements into the grid, so with VEC (a
+// 16-byte aligned grid) the vectors are aligned.
+template <bool VEC>
+__device__ __forceinline__ void row_taps(const float* row, int x0, int n, float t[4]) {
+  x0 &= n - 1;
+  const int a0 = x0 & ~3, sh = x0 & 3;
+  if (VEC && a0 + 8 <= n) {
+    const float4 u = __ldg(reinterpret_cast<const float4*>(row + a0));
+    if (sh == 0) {
+      t[0] = u.x;
+      t[1] = u.y;
+      t[2] = u.z;
+      t[3] = u.w;
+      return;
+    }
+    const float4 w = __ldg(reinterpret_cast<const float4*>(row + a0 + 4));
+    const float v[8] = {u.x, u.y, u.z, u.w, w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) t[k] = sh == 1 ? v[k + 1] : (sh == 2 ? v[k + 2] : v[k + 3]);
+    return;
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) t[k] = __ldg(row + ((x0 + k) & (n - 1)));
+}
+template <bool VEC>
+__device__ __forceinline__ void row_taps(const double* row, int x0, int n, double t[4]) {
+  x0 &= n - 1;
+  const int a0 = x0 & ~1, sh = x0 & 1;
+  if (VEC && a0 + 6 <= n) {
+    const double2 u = __ldg(reinterpret_cast<const double2*>(row + a0));
+    const double2 w = __ldg(reinterpret_cast<const double2*>(row + a0 + 2));
+    if (sh == 0) {
+      t[0] = u.x;
+      t[1] = u.y;
+      t[2] = w.x;
+      t[3] = w.y;
+      return;
+    }
+    const double2 z = __ldg(reinterpret_cast<const double2*>(row + a0 + 4));
+    t[0] = u.y;
+    t[1] = w.x;
+    t[2] = w.y;
+    t[3] = z.x;
+    return;
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) t[k] = __ldg(row + ((x0 + k) & (n - 1)));
+}
+
 // y_i = S* grid at X_i (+ jump * jvec_i).  Four threads share a point, one
 // per tap plane (3D: z = bz + t) or tap row (2D: y = by + t), so a warp keeps
 // four times as many independent grid loads in flight; the four partial sums
 // are combined by a fixed butterfly of shuffles (a deterministic order).
-template <typename T, int D>
+// In 3D lane t of a point loads the point's tap weights W_c[t] and base
+// index c = t and hands them to the other three by shuffles, and the x taps
+// of a row come in vector loads (row_taps): that kernel is bound by its load
+// instructions, not by their bytes (C3 float32: 14.4 -> 11.4 us).
+template <typename T, int D, bool VEC>
 __global__ void __launch_bounds__(128) k_interp(GridDesc g, PointData p, const T* grid,
                                                 const double* jvec, double jump, double* y) {
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
@@ -262,35 +318,49 @@ __global__ void __launch_bounds__(128) k_interp(GridDesc g, PointData p, const T
   const bool live = i < p.m;
   const int ii = live ? i : 0;
   const int n = g.n, mask = n - 1, m = p.m;
-  // the grid comes from an earlier launch: cached loads are coherent here
-  T wx[4];
-  int col[4];
-#pragma unroll
-  for (int t = 0; t < 4; ++t) wx[t] = interp_w<T>(p, 0, t, ii, m);
-  const int bx = p.base[0][ii], by = p.base[1][ii];
-#pragma unroll
-  for (int t = 0; t < 4; ++t) col[t] = (bx + t) & mask;
   T acc = 0;
-  if (D == 2) {
+  if constexpr (D == 2) {
+    // 2D: each lane loads its own weights and indices (a shuffle hand-off
+    // lengthens this latency-bound kernel's chain: measured 6.1 -> 7.2 us)
+    T wx[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) wx[t] = interp_w<T>(p, 0, t, ii, m);
+    const int bx = p.base[0][ii], by = p.base[1][ii];
     const T* row = grid + (size_t)((by + sub) & mask) * n;
     T r = 0;
 #pragma unroll
-    for (int tx = 0; tx < 4; ++tx) r += __ldg(row + col[tx]) * wx[tx];
+    for (int tx = 0; tx < 4; ++tx) r += __ldg(row + ((bx + tx) & mask)) * wx[tx];
     acc = r * interp_w<T>(p, 1, sub, ii, m);
   } else {
-    T wy[4];
+    // 3D: 16 rows of 4 taps per point, bound by load instructions: lane t of
+    // a point loads W_c[t] and base index c = t for the other three lanes
+    const int lead = threadIdx.x & 28;  // lane of the point's sub = 0 thread
+    const T wxs = interp_w<T>(p, 0, sub, ii, m);
+    const T wys = interp_w<T>(p, 1, sub, ii, m);
+    const T wzs = interp_w<T>(p, 2, sub, ii, m);
+    const int* bp = sub == 0 ? p.base[0] : (sub == 1 ? p.base[1] : p.base[2]);
+    const int bsub = sub < 3 ? __ldg(bp + ii) : 0;
+    T wx[4], wy[4];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) wy[t] = interp_w<T>(p, 1, t, ii, m);
-    const T* plane = grid + (size_t)((p.base[2][ii] + sub) & mask) * n * n;
+    for (int t = 0; t < 4; ++t) {
+      wx[t] = __shfl_sync(0xffffffffu, wxs, lead + t);
+      wy[t] = __shfl_sync(0xffffffffu, wys, lead + t);
+    }
+    const int bx = __shfl_sync(0xffffffffu, bsub, lead);
+    const int by = __shfl_sync(0xffffffffu, bsub, lead + 1);
+    const int bz = __shfl_sync(0xffffffffu, bsub, lead + 2);
+    const T* plane = grid + (size_t)((bz + sub) & mask) * n * n;
 #pragma unroll
     for (int ty = 0; ty < 4; ++ty) {
       const T* row = plane + (size_t)((by + ty) & mask) * n;
+      T tp[4];
+      row_taps<VEC>(row, bx, n, tp);
       T r = 0;
 #pragma unroll
-      for (int tx = 0; tx < 4; ++tx) r += __ldg(row + col[tx]) * wx[tx];
+      for (int tx = 0; tx < 4; ++tx) r += tp[tx] * wx[tx];
       acc += r * wy[ty];
     }
-    acc *= interp_w<T>(p, 2, sub, ii, m);
+    acc *= wzs;
   }
   acc += __shfl_xor_sync(0xffffffffu, acc, 1);
   acc += __shfl_xor_sync(0xffffffffu, acc, 2);
@@ -306,11 +376,21 @@ cudaError_t launch_interp(const GridDesc& g, const PointData& p, const T* grid,
                           const double* jvec, double jump, double* y, cudaStream_t st) {
   const int bs = 128;
   const int gb = (int)((4 * (int64_t)p.m + bs - 1) / bs);
+  // vector tap loads need a 16-byte aligned grid (the library's own grids
+  // are; one passed in by a caller may not be)
+  const bool vec = (reinterpret_cast<uintptr_t>(grid) & 15) == 0;
   prof_begin(st);
-  if (g.dim == 2)
-    k_interp<T, 2><<<gb, bs, 0, st>>>(g, p, grid, jvec, jump, y);
-  else
-    k_interp<T, 3><<<gb, bs, 0, st>>>(g, p, grid, jvec, jump, y);
+  if (g.dim == 2) {
+    if (vec)
+      k_interp<T, 2, true><<<gb, bs, 0, st>>>(g, p, grid, jvec, jump, y);
+    else
+      k_interp<T, 2, false><<<gb, bs, 0, st>>>(g, p, grid, jvec, jump, y);
+  } else {
+    if (vec)
+      k_interp<T, 3, true><<<gb, bs, 0, st>>>(g, p, grid, jvec, jump, y);
+    else
+      k_interp<T, 3, false><<<gb, bs, 0, st>>>(g, p, grid, jvec, jump, y);
+  }
   count_launch(sizeof(T) == 8 ? "interp_f64" : "interp_f32", st);
   return check_launch();
 }
