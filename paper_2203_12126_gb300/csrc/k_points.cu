@@ -318,6 +318,7 @@ __global__ void __launch_bounds__(128) k_interp(GridDesc g, PointData p, const T
   const bool live = i < p.m;
   const int ii = live ? i : 0;
   const int n = g.n, mask = n - 1, m = p.m;
+  // the grid comes from an earlier launch: cached loads are coherent here
   T acc = 0;
   if constexpr (D == 2) {
     // 2D: each lane loads its own weights and indices (a shuffle hand-off
