@@ -69,6 +69,10 @@ def parse():
                          "solves, or the benchmark's batched c2 pair")
     ap.add_argument("--reps", type=int, default=None,
                     help="--profile-case: repetitions (matvec 5, solve/pair 2)")
+    ap.add_argument("--trace", action="store_true",
+                    help="--profile-case pair-c2: after the repetitions, trace one more "
+                         "launch's work items and print a summary (phase hand-offs, "
+                         "starts, busy share) as one JSON line")
     ap.add_argument("--rows", type=int, default=None,
                     help="--profile-case: pin the x-pass tiling (rows per tile); the "
                          "autotuner's timings are distorted under a profiler")
@@ -515,11 +519,63 @@ def run_profile_case(args):
         for _ in range(reps):
             infos = batch.solve(gs, bs, qs, tol=1e-8)
         print(f"{what} x{reps}: iters {[f['iters'] for f in infos]}")
+        if args.trace:
+            ibdl.profile_enable(True)
+            ibdl.profile_trace(True)
+            batch.solve(gs, bs, qs, tol=1e-8)
+            rec, _ = ibdl.profile_trace_read()
+            ibdl.profile_trace(False)
+            ibdl.profile_enable(False)
+            print(json.dumps(trace_summary(rec)))
         batch.close()
     torch.cuda.synchronize()
     for g in gs:
         g.close()
     return 0
+
+
+TRACE_PHASES = {0: "x_fwd", 1: "y_fwd", 2: "solve", 3: "y_inv", 4: "x_inv", 5: "D", 6: "E",
+                7: "F", 9: "single"}
+
+
+def trace_summary(rec):
+    """Per instance: phases, the phase hand-offs (last item done -> next phase
+    published) and the start gaps (publication -> first item of the phase);
+    per phase kind and precision: count, median span and median item; the
+    busy share of blocks x launch."""
+    r = rec.astype(np.int64)
+    t0 = int(r[:, 0].min())
+    s, e, meta = r[:, 0] - t0, r[:, 1] - t0, r[:, 2]
+    blk, inst = meta >> 40, (meta >> 24) & 0xFFFF
+    ph, prec = (meta >> 20) & 15, (meta >> 18) & 3
+    span = int(e.max())
+    nblk = int(blk.max()) + 1
+    out = {"span_us": span / 1e3, "blocks": nblk,
+           "busy_share": float((e - s)[ph != 15].sum() / (span * nblk)), "instances": {}}
+    for k in np.unique(inst):
+        m = inst == k
+        ho = np.sort(e[m & (ph == 15)])
+        hod = (e - s)[m & (ph == 15)]
+        items = m & (ph != 15)
+        grp = np.searchsorted(ho, s[items])
+        kinds = {}
+        gaps = []
+        for g in np.unique(grp):
+            sel = grp == g
+            ss, ee = s[items][sel], e[items][sel]
+            kind = f"{TRACE_PHASES.get(int(ph[items][sel][0]), '?')}_{'f32' if prec[items][sel][0] else 'f64'}"
+            kinds.setdefault(kind, []).append(((ee.max() - ss.min()) / 1e3,
+                                               float(np.median(ee - ss)) / 1e3))
+            if g > 0:
+                gaps.append((ss.min() - ho[g - 1]) / 1e3)
+        out["instances"][int(k)] = {
+            "phases": int(len(np.unique(grp))),
+            "handoff_us_median": float(np.median(hod)) / 1e3 if len(hod) else None,
+            "start_gap_us_median": float(np.median(gaps)) if gaps else None,
+            "by_kind": {kk: {"phases": len(v), "span_us_median": float(np.median([a for a, _ in v])),
+                             "item_us_median": float(np.median([b for _, b in v]))}
+                        for kk, v in sorted(kinds.items())}}
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -675,9 +731,9 @@ def load_peaks():
 
 
 # DRAM bytes (read + write) of one batched-pair launch of the persistent
-# solver, from one ncu capture of that launch (81.0 MB read + 219.0 MB
+# solver, from one ncu capture of that launch (80.4 MB read + 210.0 MB
 # write); None whenever the solver kernel changes, until it is captured again
-PAIR_LAUNCH_DRAM_BYTES = (81.009920 + 219.019520) * 1e6
+PAIR_LAUNCH_DRAM_BYTES = (80.412416 + 209.988096) * 1e6
 PAIR_LAUNCH_DRAM_SRC = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one pair launch "
                         "(profiles/c2_persistent_solve.md)")
 
