@@ -191,6 +191,7 @@ struct ibdl_geometry_s {
   double* ppart = nullptr;
   double* d_hist = nullptr;
   int nchunk = 0;
+  int nsec = 0;
   int solver_smem = 0;
   SolveInst* h_inst = nullptr;    // pinned
   SolveState* h_state = nullptr;  // pinned
@@ -681,6 +682,7 @@ SolveInst make_inst(ibdl_geometry_s* g, const ibdl_solve_opts& o, int batch_size
   I.ysol = g->kry.ysol;
   I.part = g->ppart;
   I.nchunk = g->nchunk;
+  I.nsec = g->nsec;
   I.pstride = g->kry.restart + 2;
   I.bvec = g->vb;
   I.x = g->vx;
@@ -694,6 +696,17 @@ SolveInst make_inst(ibdl_geometry_s* g, const ibdl_solve_opts& o, int batch_size
   I.hist = g->d_hist;
   I.hist_cap = kHistCap;
   I.single = g->m <= kSingleMax && batch_size >= kSingleMinBatch && !g_force_multi;
+  // 2D solves alone in their launch: the Arnoldi steps interpolate in their
+  // x-inverse tiles, one phase fewer per step on the instance's chain (C2
+  // solve 0.993 -> 0.957 ms, C1 0.726 -> 0.711 ms).  Instances that share a
+  // launch keep phase D: the fused x-inverse items do more work in all (a
+  // point's share in up to two tiles' bins, a dot-product row per tile), and
+  // sharing the blocks that costs more than the phase saves (the C2 pair
+  // 1.261 -> 1.281 ms).  Float64 steps only for small instances: their
+  // float64 interpolation lengthens the x-inverse items (the C2 float64 pair
+  // 2.99 -> 3.30 ms when fused).
+  if (batch_size == 1 && g->grid.dim == 2 && !I.single && g->nsec >= g->bins.ntiles)
+    I.fuse_interp = g->m <= 1024 ? 2 : 1;
   // A few 2D instances in one launch share the blocks: float32 solve items
   // of 4 pencils (about 129 per instance) let them run side by side (the C2
   // pair: 1.268 -> 1.251 ms against the rule's 2 pencils), where the item
@@ -1217,7 +1230,10 @@ ibdl_status ibdl_create_geometry(const ibdl_geometry_desc* d, void* stream, ibdl
   if ((s = g->alloc(&g->d_flag, (size_t)4))) return cleanup(s);
   if ((s = g->alloc(&g->cpart, (size_t)kRedBlocks + 1))) return cleanup(s);
   g->nchunk = (m + kSolverThreads - 1) / kSolverThreads;
-  if ((s = g->alloc(&g->ppart, (size_t)3 * g->nchunk * (k.restart + 2)))) return cleanup(s);
+  // a section holds one row per vector chunk, or per x tile in 2D (the
+  // Arnoldi steps' first dot products come from the x-inverse tiles)
+  g->nsec = g->nchunk > (dim == 2 ? g->bins.ntiles : 0) ? g->nchunk : g->bins.ntiles;
+  if ((s = g->alloc(&g->ppart, (size_t)3 * g->nsec * (k.restart + 2)))) return cleanup(s);
   if ((s = g->alloc(&g->d_hist, (size_t)kHistCap))) return cleanup(s);
   if ((s = g->alloc(&g->d_inst, (size_t)1))) return cleanup(s);
   if ((s = g->alloc(&g->d_state, (size_t)1))) return cleanup(s);

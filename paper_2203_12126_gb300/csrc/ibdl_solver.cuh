@@ -44,9 +44,14 @@ struct SolveInst {
   double* sn;
   double* gv;       // restart + 1
   double* ysol;     // restart
-  double* part;     // partial sums: sections of nchunk x pstride
+  double* part;     // partial sums: three sections of nsec x pstride
   int nchunk;
   int pstride;
+  int nsec;         // rows per section: max(nchunk, the 2D x tiles)
+  // 2D Arnoldi steps that interpolate in their x-inverse tiles (no phase D;
+  // their first dot products come as per-tile partial sums): 0 none, 1 the
+  // float32 steps, 2 all steps
+  int fuse_interp;
   double* bvec;         // right-hand side (written by ACT_RHS)
   const double* vdata;  // V_b for ACT_RHS
   double* x;

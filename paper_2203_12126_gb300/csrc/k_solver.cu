@@ -277,13 +277,99 @@ __device__ __noinline__ void solver_rows_fwd(const SolveInst& I, const double* q
   phase_rows_fwd<T, D>(I.g, I.p, I.b, src, ws.spec, ws.tw, nullptr, item, smem);
 }
 
+// 2D Arnoldi step, after x-inverse tile `tile` has written its R grid rows:
+// the tile's share of w = S* grid + jump v_j (Sec. 5.2, eq. (ibdl 2)), for
+// every point of its bin whose 4-row stencil meets the tile, added to
+// w = V[j+1] (zeroed by the phase before; a stencil meets at most two
+// tiles), the jump term by the tile holding the stencil's first row; and
+// the tile's share of the first CGS dot products V_c . w, c <= j, as the
+// tile's row of partial sums (linear in the shares).  Replaces phase D of
+// the step.  The grid rows were written by this block: read them plainly.
+template <typename G>
+__device__ void fused_interp_tile(const SolveInst& I, const RoundView& v, const G* grid,
+                                  int tile, unsigned char* smem) {
+  const GridDesc& g = I.g;
+  const PointData& p = I.p;
+  const int n = g.n, mask = n - 1, R = I.b.rows, y0 = tile * R, m = p.m;
+  const int lo = I.b.start[tile], hi = I.b.start[tile + 1];
+  const double jump = I.bc == IBDL_DIRICHLET ? 0.5 : -0.5;
+  const int ncols = v.j + 1;
+  double* w = I.V + (size_t)(v.j + 1) * I.ld;
+  const double* vin = I.V + (size_t)v.j * I.ld;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double* red = reinterpret_cast<double*>(smem);  // [ncols][nw], the FFT is done with smem
+  for (int c = threadIdx.x; c < ncols * nw; c += blockDim.x) red[c] = 0.0;
+  __syncthreads();
+  for (int e0 = lo; e0 < hi; e0 += blockDim.x) {
+    const int e = e0 + threadIdx.x;
+    double contrib = 0.0;
+    int i = 0;
+    bool any = false;
+    if (e < hi) {
+      i = __ldg(I.b.pts + e);
+      const int bx = p.base[0][i], by = p.base[1][i];
+      G acc = 0;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int row = (by + t) & mask;
+        if ((unsigned)(row - y0) < (unsigned)R) {
+          const G* rp = grid + (size_t)row * n;
+          G r = 0;
+#pragma unroll
+          for (int tx = 0; tx < 4; ++tx) r += rp[(bx + tx) & mask] * interp_w<G>(p, 0, tx, i, m);
+          acc += r * interp_w<G>(p, 1, t, i, m);
+          any = true;
+        }
+      }
+      contrib = (double)acc;
+      if ((unsigned)((by & mask) - y0) < (unsigned)R) {
+        contrib += jump * __ldcg(vin + i);
+        any = true;
+      }
+      if (any) atomicAdd(w + i, contrib);
+    }
+    for (int c0 = 0; c0 < ncols; c0 += kColBatch) {
+      double vc[kColBatch];
+#pragma unroll
+      for (int u = 0; u < kColBatch; ++u)
+        vc[u] = (any && c0 + u < ncols) ? __ldcg(I.V + (size_t)(c0 + u) * I.ld + i) : 0.0;
+#pragma unroll
+      for (int u = 0; u < kColBatch; ++u) {
+        if (c0 + u < ncols) {
+          const double sm = warp_sum(contrib * vc[u]);
+          if (lane == 0) red[(c0 + u) * nw + wid] += sm;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
+    double sm = 0;
+    for (int q = 0; q < nw; ++q) sm += red[c * nw + q];
+    I.part[(size_t)tile * I.pstride + c] = sm;
+  }
+  __syncthreads();
+}
+
+// Whether an Arnoldi step of this precision interpolates in its x-inverse
+// tiles (I.fuse_interp: 1 float32 steps, 2 all steps).
+__device__ __forceinline__ bool fused_step(const SolveInst& I, int action, int prec) {
+  return action == ACT_MV_ARNOLDI && (I.fuse_interp == 2 || (I.fuse_interp == 1 && prec == 1));
+}
+
 template <typename T, int D>
-__device__ __noinline__ void solver_rows_inv(const SolveInst& I, int item, unsigned char* smem) {
+__device__ __noinline__ void solver_rows_inv(const SolveInst& I, const RoundView& v, int item,
+                                             unsigned char* smem) {
   const SpectralWs<T> ws = ws_of<T>(I);
-  if constexpr (std::is_same<T, dd>::value)  // double-float writes the float64 grid
+  if constexpr (std::is_same<T, dd>::value) {  // double-float writes the float64 grid
     phase_rows_inv<T, D, double>(I.g, I.b, ws.spec, ws.tw, I.w64.grid, item, smem, true);
-  else
+    if (D == 2 && fused_step(I, v.action, v.prec))
+      fused_interp_tile<double>(I, v, I.w64.grid, item, smem);
+  } else {
     phase_rows_inv<T, D, T>(I.g, I.b, ws.spec, ws.tw, ws.grid, item, smem, true);
+    if (D == 2 && fused_step(I, v.action, v.prec))
+      fused_interp_tile<T>(I, v, ws.grid, item, smem);
+  }
 }
 
 template <typename T, int MODE>
@@ -313,9 +399,9 @@ __device__ void mv_item(const SolveInst& I, const RoundView& v, int phase, int i
       solver_rows_fwd<T, 3>(I, mv_input(I, v), item, smem);
   } else if (phase == 4) {
     if (d == 2)
-      solver_rows_inv<T, 2>(I, item, smem);
+      solver_rows_inv<T, 2>(I, v, item, smem);
     else
-      solver_rows_inv<T, 3>(I, item, smem);
+      solver_rows_inv<T, 3>(I, v, item, smem);
   } else if (d == 2 || phase == 2) {
     solver_pencils<T, 2>(I, 1, item, smem);
   } else if (phase == 1) {
@@ -425,7 +511,10 @@ __device__ void cgs_pass(const SolveInst& I, const RoundView& v, int chunk, Bloc
                          const double* in, double* out) {
   const int ncols = v.j + 1;
   const int ldh = I.restart + 1;
-  reduce_parts(in, I.nchunk, I.pstride, 0, ncols, R.h);
+  // the first pass's partial sums: one row per x tile when the x-inverse
+  // tiles interpolated (2D), else one per vector chunk (phase D)
+  reduce_parts(in, fused_step(I, v.action, v.prec) ? I.b.ntiles : I.nchunk, I.pstride, 0, ncols,
+               R.h);
   if (chunk == 0) {
     double* Hcol = I.H + (size_t)v.j * ldh;
     for (int c = threadIdx.x; c < ncols; c += blockDim.x) Hcol[c] = R.h[c];
@@ -445,7 +534,7 @@ __device__ void cgs_pass(const SolveInst& I, const RoundView& v, int chunk, Bloc
 __device__ void phase_E(const SolveInst& I, SolveState* S, const RoundView& v, int chunk,
                         BlockRed& R) {
   double* part1 = I.part;
-  double* part2 = I.part + (size_t)I.nchunk * I.pstride;
+  double* part2 = I.part + (size_t)I.nsec * I.pstride;
   if (v.action == ACT_MV_ARNOLDI) {
     cgs_pass(I, v, chunk, R, part1, part2);
     return;
@@ -475,12 +564,16 @@ __device__ void phase_E(const SolveInst& I, SolveState* S, const RoundView& v, i
     __syncthreads();
     return;
   }
-  // residual actions: V0 = r / ||r||
+  // residual actions: V0 = r / ||r|| (and V1 cleared for the x-inverse
+  // tiles' interpolation of the first Arnoldi step)
   const double ri = valid ? __ldcg(I.r + i) : 0.0;
   reduce_parts(part1, I.nchunk, I.pstride, 0, 2, R.h);
   const double beta = sqrt(R.h[0]);
   const double inv = (beta > 0 && isfinite(beta)) ? 1.0 / beta : 0.0;
-  if (valid) I.V[i] = ri * inv;
+  if (valid) {
+    I.V[i] = ri * inv;
+    if (I.fuse_interp && I.restart >= 1) I.V[(size_t)I.ld + i] = 0.0;
+  }
   __syncthreads();
 }
 
@@ -605,7 +698,7 @@ __device__ void control(const SolveInst& I, SolveState* S, const RoundView& v, d
 __device__ void phase_F(const SolveInst& I, SolveState* S, const RoundView& v, int chunk,
                         BlockRed& R) {
   const int j = v.j, ncols = j + 1, ldh = I.restart + 1;
-  double* part2 = I.part + (size_t)I.nchunk * I.pstride;
+  double* part2 = I.part + (size_t)I.nsec * I.pstride;
   // item nchunk runs the control step beside the normalisation of items
   // 0 .. nchunk - 1; its inputs (the state, the Hessenberg column's first
   // pass, the earlier rotations, g_j) go out beside the partial sums' loads
@@ -652,6 +745,8 @@ __device__ void phase_F(const SolveInst& I, SolveState* S, const RoundView& v, i
     double* wp = I.V + (size_t)(j + 1) * I.ld;
     const double w = sub_projection(I, __ldcg(wp + i), i, ncols, R.h);
     wp[i] = inv != 0.0 ? w * inv : w;
+    // the next step's w, accumulated by its x-inverse tiles
+    if (I.fuse_interp && j + 2 <= I.restart) wp[I.ld + i] = 0.0;
   }
   __syncthreads();
 }
@@ -920,14 +1015,16 @@ __device__ int first_phase(const SolveInst& I, int action) {
 }
 
 // -1: the round ends after `phase` (of a round doing `action`)
-__device__ int next_phase(const SolveInst& I, int phase, int action) {
+__device__ int next_phase(const SolveInst& I, int phase, int action, int prec) {
   const bool d3 = I.g.dim == 3;
   switch (phase) {
     case 0: return d3 ? 1 : 2;
     case 1: return 2;
     case 2: return d3 ? 3 : 4;
     case 3: return 4;
-    case 4: return I.single ? kPhaseSingle : kPhaseD;
+    case 4:
+      if (I.single) return kPhaseSingle;
+      return fused_step(I, action, prec) ? kPhaseE : kPhaseD;
     case kPhaseD: return action == ACT_RHS ? -1 : kPhaseE;
     case kPhaseE: return action == ACT_MV_ARNOLDI ? kPhaseF : -1;
     default: return -1;
@@ -973,7 +1070,7 @@ __device__ bool advance(const SolveInst& I, const SolveState* S, unsigned* bar, 
                         int max_rounds, const PhaseDesc& cur, bool take_first,
                         PhaseDesc* out) {
   PhaseDesc d = cur;
-  int np = next_phase(I, d.phase, d.action);
+  int np = next_phase(I, d.phase, d.action, d.prec);
   if (np < 0) {
     d.round++;
     const bool active = view_from_state(S, d);
