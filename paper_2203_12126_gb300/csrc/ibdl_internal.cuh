@@ -152,6 +152,43 @@ struct SpreadSrc {
   bool skip_empty_planes = false;
 };
 
+// ---- dependent launches ----------------------------------------------------
+// The kernels of a matvec chain (x forward, pencil passes, x inverse,
+// interpolation) are launched with programmatic stream serialisation: the
+// next kernel of the stream may be launched before this one has finished,
+// its blocks taking the SMs this one's blocks leave.  Every such kernel
+// starts with pdl_wait() -- it returns once the grids it depends on have
+// completed and their memory operations are visible -- before touching any
+// memory, and lets its own successor launch when a block has done its work
+// (pdl_release at the end: released at the start, the successor's waiting
+// blocks sat beside the running ones and slowed the double-float chain).
+// Without a programmatic predecessor both are no-ops.
+__device__ __forceinline__ void pdl_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_release() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Launches kernel<<<grid, block, smem, st>>>(args...) as a programmatic
+// dependent of the stream's previous kernel (the kernel must begin with
+// pdl_wait()).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block,
+                                    size_t smem, cudaStream_t st, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
+}
+
 // ---- launch bookkeeping -------------------------------------------------
 // prof_begin records a start event when profiling is on; count_launch counts
 // the launch and records its end event (name must be a string literal).

@@ -29,7 +29,9 @@ __global__ void __launch_bounds__(512) k_rows_fwd(GridDesc g, PointData p, Bins 
                                                    const cx_t<T>* __restrict__ tw,
                                                    double* write_grid) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_wait();
   phase_rows_fwd<T, D>(g, p, b, src, spec, tw, write_grid, blockIdx.x, smem_raw);
+  pdl_release();
 }
 
 template <typename T, int MODE>
@@ -39,8 +41,10 @@ __global__ void __launch_bounds__(512) k_pencils(GridDesc g, PencilLayout L, cx_
                                                  const int* zskip, int ngroups,
                                                  const unsigned char* zempty) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_wait();
   phase_pencils<T, MODE>(g, L, data, tw, s2, cfac, scale0, blockIdx.x, smem_raw, zskip,
                          ngroups, zempty);
+  pdl_release();
 }
 
 template <typename T, int D, typename OutT>
@@ -48,7 +52,9 @@ __global__ void __launch_bounds__(512) k_rows_inv(GridDesc g, Bins b, const cx_t
                                                    const cx_t<T>* __restrict__ tw,
                                                    OutT* out, bool band_only) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_wait();
   phase_rows_inv<T, D, OutT>(g, b, spec, tw, out, blockIdx.x, smem_raw, band_only);
+  pdl_release();
 }
 
 // ---- launchers ----------------------------------------------------------------
@@ -74,9 +80,11 @@ cudaError_t launch_rows_fwd(const GridDesc& g, const PointData& p, const Bins& b
   const int thr = rows_threads(g.n, npen);
   prof_begin(st);
   if (g.dim == 2)
-    k_rows_fwd<T, 2><<<b.ntiles, thr, smem, st>>>(g, p, b, src, ws.spec, ws.tw, write_grid);
+    launch_dependent(k_rows_fwd<T, 2>, b.ntiles, thr, smem, st, g, p, b, src, ws.spec,
+                     (const cx_t<T>*)ws.tw, write_grid);
   else
-    k_rows_fwd<T, 3><<<b.ntiles, thr, smem, st>>>(g, p, b, src, ws.spec, ws.tw, write_grid);
+    launch_dependent(k_rows_fwd<T, 3>, b.ntiles, thr, smem, st, g, p, b, src, ws.spec,
+                     (const cx_t<T>*)ws.tw, write_grid);
   count_launch(tag3<T>("rows_fwd_f32", "rows_fwd_f64", "rows_fwd_dd"), st);
   return check_launch();
 }
@@ -93,9 +101,11 @@ cudaError_t launch_rows_inv(const GridDesc& g, const Bins& b, SpectralWs<T>& ws,
                                                 : rows_threads(g.n, npen);
   prof_begin(st);
   if (g.dim == 2)
-    k_rows_inv<T, 2, OutT><<<b.ntiles, thr, smem, st>>>(g, b, ws.spec, ws.tw, out, band_only);
+    launch_dependent(k_rows_inv<T, 2, OutT>, b.ntiles, thr, smem, st, g, b,
+                     (const cx_t<T>*)ws.spec, (const cx_t<T>*)ws.tw, out, band_only);
   else
-    k_rows_inv<T, 3, OutT><<<b.ntiles, thr, smem, st>>>(g, b, ws.spec, ws.tw, out, band_only);
+    launch_dependent(k_rows_inv<T, 3, OutT>, b.ntiles, thr, smem, st, g, b,
+                     (const cx_t<T>*)ws.spec, (const cx_t<T>*)ws.tw, out, band_only);
   count_launch(tag3<T>("rows_inv_f32", "rows_inv_f64", "rows_inv_dd"), st);
   return check_launch();
 }
@@ -110,8 +120,8 @@ static cudaError_t run_pencils(const GridDesc& g, const PencilLayout& L, Spectra
   const T cfac = (T)symbol_cfac(g);
   const T scale0 = (T)symbol_scale0(g);
   prof_begin(st);
-  k_pencils<T, MODE><<<blocks, thr, smem, st>>>(g, L, ws.spec, ws.tw, ws.s2, cfac, scale0,
-                                                 zskip, ngroups, zempty);
+  launch_dependent(k_pencils<T, MODE>, blocks, thr, smem, st, g, L, ws.spec,
+                   (const cx_t<T>*)ws.tw, (const T*)ws.s2, cfac, scale0, zskip, ngroups, zempty);
   static const char* names[3][3] = {{"pencils_fwd_f32", "pencils_inv_f32", "pencils_solve_f32"},
                                     {"pencils_fwd_f64", "pencils_inv_f64", "pencils_solve_f64"},
                                     {"pencils_fwd_dd", "pencils_inv_dd", "pencils_solve_dd"}};

@@ -313,6 +313,7 @@ __device__ __forceinline__ void row_taps(const double* row, int x0, int n, doubl
 template <typename T, int D, bool VEC>
 __global__ void __launch_bounds__(128) k_interp(GridDesc g, PointData p, const T* grid,
                                                 const double* jvec, double jump, double* y) {
+  pdl_wait();
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = gt >> 2, sub = gt & 3;
   const bool live = i < p.m;
@@ -370,6 +371,7 @@ __global__ void __launch_bounds__(128) k_interp(GridDesc g, PointData p, const T
     if (jvec) out += jump * jvec[i];
     y[i] = out;
   }
+  pdl_release();
 }
 
 template <typename T>
@@ -383,14 +385,14 @@ cudaError_t launch_interp(const GridDesc& g, const PointData& p, const T* grid,
   prof_begin(st);
   if (g.dim == 2) {
     if (vec)
-      k_interp<T, 2, true><<<gb, bs, 0, st>>>(g, p, grid, jvec, jump, y);
+      launch_dependent(k_interp<T, 2, true>, gb, bs, 0, st, g, p, grid, jvec, jump, y);
     else
-      k_interp<T, 2, false><<<gb, bs, 0, st>>>(g, p, grid, jvec, jump, y);
+      launch_dependent(k_interp<T, 2, false>, gb, bs, 0, st, g, p, grid, jvec, jump, y);
   } else {
     if (vec)
-      k_interp<T, 3, true><<<gb, bs, 0, st>>>(g, p, grid, jvec, jump, y);
+      launch_dependent(k_interp<T, 3, true>, gb, bs, 0, st, g, p, grid, jvec, jump, y);
     else
-      k_interp<T, 3, false><<<gb, bs, 0, st>>>(g, p, grid, jvec, jump, y);
+      launch_dependent(k_interp<T, 3, false>, gb, bs, 0, st, g, p, grid, jvec, jump, y);
   }
   count_launch(sizeof(T) == 8 ? "interp_f64" : "interp_f32", st);
   return check_launch();

@@ -106,6 +106,10 @@ __global__ void __launch_bounds__(512) k_zsolve_tma(GridDesc g, int c, int lgc, 
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     bad = 0;
   }
+  // the tables and the barrier do not depend on the previous kernel: they
+  // are staged before its spectrum is waited for (a dependent launch)
+  pdl_wait();
+  if (tid == 0) asm volatile("fence.proxy.async.global;" ::: "memory");
   __syncthreads();
   int k = blockIdx.x;
   if (tid == 0 && k < nitems) tma_issue_item(ti, k);
@@ -145,6 +149,7 @@ __global__ void __launch_bounds__(512) k_zsolve_tma(GridDesc g, int c, int lgc, 
       mbar_wait(&bar, parity, kTmaSpin);
     }
   }
+  pdl_release();
 }
 
 namespace {
@@ -258,8 +263,8 @@ cudaError_t launch_zsolve_tma(const GridDesc& g, SpectralWs<T>& ws, const unsign
   const T cfac = (T)symbol_cfac(g);
   const T scale0 = (T)symbol_scale0(g);
   prof_begin(st);
-  k_zsolve_tma<T><<<blocks, thr, smem, st>>>(g, c, lgc, nitems, ws.spec, map, ws.tw, ws.s2, cfac,
-                                              scale0, zempty, ws.err);
+  launch_dependent(k_zsolve_tma<T>, blocks, thr, smem, st, g, c, lgc, nitems, ws.spec, map,
+                   (const cx_t<T>*)ws.tw, (const T*)ws.s2, cfac, scale0, zempty, ws.err);
   count_launch(sizeof(T) == 4 ? "zsolve_tma_f32" : "zsolve_tma_f64", st);
   return check_launch();
 }
