@@ -731,9 +731,9 @@ def load_peaks():
 
 
 # DRAM bytes (read + write) of one batched-pair launch of the persistent
-# solver, from one ncu capture of that launch (80.4 MB read + 210.0 MB
-# write); None whenever the solver kernel changes, until it is captured again
-PAIR_LAUNCH_DRAM_BYTES = (80.412416 + 209.988096) * 1e6
+# solver, from one ncu capture of that launch; None whenever the solver
+# kernel changes, until it is captured again
+PAIR_LAUNCH_DRAM_BYTES = None
 PAIR_LAUNCH_DRAM_SRC = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one pair launch "
                         "(profiles/c2_persistent_solve.md)")
 
@@ -1025,15 +1025,21 @@ def main():
         if name == "persistent_solve":
             # one launch = whole solves (per_launch of them).  The matvec
             # byte model B = 9 p N^d + p M (4^d + 2d + 4) per field solve:
-            # p = 4 for the float32 Arnoldi matvecs, p = 8 for the
-            # float64-grade ones (the residuals and the Neumann right-hand
-            # side, transformed in double-float)
+            # p = 4 for the float32 Arnoldi matvecs (and a refined launch's
+            # Neumann right-hand side), p = 8 for the float64-grade ones (the
+            # residuals, transformed in double-float)
             mv = float(np.mean([f["matvecs"] for f in pinfos])) * per_launch
             it = float(np.mean([f["iters"] for f in pinfos])) * per_launch
             mv64 = (mv - it) if prec == ibdl.FP32_REFINED else mv
             mv32 = it if prec == ibdl.FP32_REFINED else 0.0
-            # the Neumann right-hand side is one more float64-grade field solve
-            mv64 += per_launch * sum(p.bc == configs.NEUMANN for p in probs) / len(probs)
+            # the Neumann right-hand side is one more field solve: float32 in
+            # a refined launch (its residuals carry the S V_b term), float64
+            # else
+            nneu = per_launch * sum(p.bc == configs.NEUMANN for p in probs) / len(probs)
+            if prec == ibdl.FP32_REFINED:
+                mv32 += nneu
+            else:
+                mv64 += nneu
             B = (mv64 * model_matvec_bytes(2, n, m, 8) + mv32 * model_matvec_bytes(2, n, m, 4))
             ach = B / avg_s / 1e9
             roofline = {"kernel": name, "bound": "hbm", "achieved": ach,

@@ -726,12 +726,20 @@ SolveInst make_inst(ibdl_geometry_s* g, const ibdl_solve_opts& o, int batch_size
 }
 
 // rhs_in_kernel: the Neumann right-hand side is built by the solver's first
-// action (ACT_RHS) from V_b in inst.vdata.
-SolveState initial_state(bool x_zero, bool rhs_in_kernel = false) {
+// action (ACT_RHS) from V_b in inst.vdata.  A float32-refined instance then
+// builds it in float32 (it only starts the first inner solve) and adds
+// S V_b to every float64-grade residual's spread instead (I.rhs_resid):
+// r = b - A x = -kappa S* L'^{-1} (S~ x + S V_b) + x / 2 in one Helmholtz
+// solve, so a solve needs one float64-grade field solve fewer.
+SolveState initial_state(SolveInst& I, bool x_zero, bool rhs_in_kernel = false) {
   SolveState s;
   memset(&s, 0, sizeof(s));
   s.action = x_zero ? ACT_RESID_ZERO : ACT_MV_RESIDUAL;
-  if (rhs_in_kernel) s.action = ACT_RHS;
+  I.rhs_resid = rhs_in_kernel && I.refined ? 1 : 0;
+  if (rhs_in_kernel) {
+    s.action = ACT_RHS;
+    s.prec = I.rhs_resid;
+  }
   s.xinit = x_zero ? 0 : 1;
   s.status = IBDL_ERR_NOT_CONVERGED;
   s.bnorm = -1.0;
@@ -806,6 +814,33 @@ std::atomic<int> g_tuning_on{1};
 // tiling or the rule, never times candidates beside a running slice
 thread_local bool tl_no_tune = false;
 
+// Per-matvec time of a candidate: one warm-up matvec, three timed ones,
+// and, when those took under a millisecond (small grids, where a few
+// launches are all noise), as many more as fill about a millisecond (at
+// most 64), which are the ones timed.
+ibdl_status time_matvecs(ibdl_geometry_s* g, const double* q, double* y, cudaEvent_t e0,
+                         cudaEvent_t e1, cudaStream_t st, float* per_ms) {
+  ibdl_status status = matvec_prec(g, g->precision, q, y, st);
+  int reps = 3;
+  for (int round = 0; round < 2 && status == IBDL_OK; ++round) {
+    cudaError_t e = cudaEventRecord(e0, st);
+    for (int rep = 0; rep < reps && !e && status == IBDL_OK; ++rep)
+      status = matvec_prec(g, g->precision, q, y, st);
+    float ms = 0;
+    if (!e && status == IBDL_OK) e = cudaEventRecord(e1, st);
+    if (!e && status == IBDL_OK) e = cudaEventSynchronize(e1);
+    if (!e && status == IBDL_OK) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e) return cuda_fail(e, "autotuner timing");
+    if (status != IBDL_OK) break;
+    *per_ms = ms / reps;
+    if (ms >= 1.0f) break;
+    const float t = ms / reps > 1e-4f ? ms / reps : 1e-4f;
+    reps = (int)(1.0f / t) + 1;
+    if (reps > 64) reps = 64;
+  }
+  return status;
+}
+
 ibdl_status tuned_rows(ibdl_geometry_s* g, int* rows_out, cudaStream_t st) {
   const GridDesc& gd = g->grid;
   const int n = gd.n, dim = gd.dim;
@@ -847,9 +882,7 @@ ibdl_status tuned_rows(ibdl_geometry_s* g, int* rows_out, cudaStream_t st) {
   IBDL_CU(cudaEventCreate(&e0));
   IBDL_CU(cudaEventCreate(&e1));
   const Bins saved = g->bins;
-  const int prec = g->precision;
-  int best = cand[0];
-  float best_ms = 1e30f;
+  std::vector<float> times;
   ibdl_status status = IBDL_OK;
   for (int R : cand) {
     const int ntiles = (n / R) * (dim == 3 ? n : 1);
@@ -868,21 +901,23 @@ ibdl_status tuned_rows(ibdl_geometry_s* g, int* rows_out, cudaStream_t st) {
     unsigned char* dz = reinterpret_cast<unsigned char*>(spts + bins_capacity(dim, R, m));
     e = build_tiles(g, R, start, cursor, counts, pts, spts, dz, &g->bins, st);
     float ms = 0;
-    for (int rep = 0; rep < 4 && !e && status == IBDL_OK; ++rep) {
-      if (rep == 1) e = cudaEventRecord(e0, st);
-      if (e) break;
-      status = matvec_prec(g, prec, q, y, st);
-    }
-    if (!e && status == IBDL_OK) e = cudaEventRecord(e1, st);
-    if (!e && status == IBDL_OK) e = cudaEventSynchronize(e1);
-    if (!e && status == IBDL_OK) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e) status = cuda_fail(e, "autotuner tiles");
+    if (status == IBDL_OK) status = time_matvecs(g, q, y, e0, e1, st, &ms);
     cudaFreeAsync(buf, st);
-    if (e) status = cuda_fail(e, "autotuner timing");
     if (status != IBDL_OK) break;
-    if (ms < best_ms) {
-      best_ms = ms;
-      best = R;
-    }
+    times.push_back(ms);
+  }
+  // the largest tiling within 5% of the fastest: fewer, larger tiles cost
+  // a lone matvec next to nothing on a small grid, but they shorten the
+  // persistent solver's phases when many instances share its blocks (256
+  // C4 stars: 39.2 ms per launch with the 2-row tiles a 3-matvec timing
+  // picked at 128^2 and 256^2, 30.2 ms with 32 and 16 rows)
+  int best = cand[0];
+  if (status == IBDL_OK && !times.empty()) {
+    float tmin = times[0];
+    for (float t : times) tmin = t < tmin ? t : tmin;
+    for (size_t k = 0; k < times.size(); ++k)
+      if (times[k] <= 1.05f * tmin) best = cand[k];
   }
   g->bins = saved;
   cudaFreeAsync(q, st);
@@ -962,18 +997,8 @@ ibdl_status tuned_pencils(ibdl_geometry_s* g, cudaStream_t st) {
     for (int c : cand) {
       gd.pcap[cls][which] = c;
       if ((status = refresh_maps(g)) != IBDL_OK) break;
-      cudaError_t e = cudaSuccess;
       float ms = 0;
-      for (int rep = 0; rep < 4 && !e && status == IBDL_OK; ++rep) {
-        if (rep == 1) e = cudaEventRecord(e0, st);
-        if (e) break;
-        status = matvec_prec(g, g->precision, q, y, st);
-      }
-      if (!e && status == IBDL_OK) e = cudaEventRecord(e1, st);
-      if (!e && status == IBDL_OK) e = cudaEventSynchronize(e1);
-      if (!e && status == IBDL_OK) e = cudaEventElapsedTime(&ms, e0, e1);
-      if (e) status = cuda_fail(e, "autotuner timing");
-      if (status != IBDL_OK) break;
+      if ((status = time_matvecs(g, q, y, e0, e1, st, &ms)) != IBDL_OK) break;
       if (ms < best_ms) {
         best_ms = ms;
         best = c;
@@ -1322,7 +1347,7 @@ ibdl_status ibdl_solve(ibdl_geometry g, const double* bdata, const double* g_gri
     // one persistent launch runs the whole solve; the host waits once
     *g->h_inst = make_inst(g, o, 1);
     g->h_inst->vdata = g->stage_a;
-    *g->h_state = initial_state(x_zero, rhs_in_kernel);
+    *g->h_state = initial_state(*g->h_inst, x_zero, rhs_in_kernel);
     IBDL_CU(cudaMemcpyAsync(g->d_inst, g->h_inst, sizeof(SolveInst), cudaMemcpyHostToDevice, st));
     IBDL_CU(cudaMemcpyAsync(g->d_state, g->h_state, sizeof(SolveState), cudaMemcpyHostToDevice,
                             st));
@@ -1804,7 +1829,7 @@ ibdl_status ibdl_solve_batched(ibdl_batch b, int32_t count, const ibdl_geometry*
     IBDL_CU(cudaMemsetAsync(g->vx, 0, sizeof(double) * g->m, st));
     b->h_inst[k] = make_inst(g, o, count);
     b->h_inst[k].vdata = g->stage_a;
-    b->h_state[k] = initial_state(true, rhs_in_kernel);
+    b->h_state[k] = initial_state(b->h_inst[k], true, rhs_in_kernel);
     if (g->solver_smem > smem) smem = g->solver_smem;
   }
   IBDL_CU(cudaMemcpyAsync(b->d_inst, b->h_inst, sizeof(SolveInst) * count,
@@ -2189,7 +2214,7 @@ ibdl_status admit_one(ibdl_server_s* s, SrvReq* r, int k) {
   r->t_admit = server_now();
   s->h_inst[k] = make_inst(g, s->cfg.opts, s->cap);
   s->h_inst[k].vdata = g->stage_a;
-  s->h_state_in[k] = initial_state(true, g->bc == IBDL_NEUMANN);
+  s->h_state_in[k] = initial_state(s->h_inst[k], true, g->bc == IBDL_NEUMANN);
   s->slot[k] = r;
   s->fresh[k] = 1;
   s->bytes += r->held;

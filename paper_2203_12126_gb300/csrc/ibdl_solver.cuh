@@ -54,6 +54,12 @@ struct SolveInst {
   int fuse_interp;
   double* bvec;         // right-hand side (written by ACT_RHS)
   const double* vdata;  // V_b for ACT_RHS
+  // 1 (float32-refined Neumann solves whose right-hand side the solver
+  // builds): ACT_RHS runs in float32 and gives only the inner solves' first
+  // right-hand side; every float64-grade residual spreads S~ x + S V_b into
+  // one Helmholtz solve, r = -(S* kappa L'^{-1} (S~ x + S V_b) - x / 2)
+  // = b - A x, so b itself is never needed to float64 accuracy
+  int rhs_resid;
   double* x;
   double* r;
   int bc;

@@ -262,13 +262,19 @@ __host__ __device__ int mv_items(const SolveInst& I, int phase) {
 // phase gets its own register allocation inside this one large kernel.  The
 // wrappers take the instance by reference to its global-memory descriptor.
 template <typename T, int D>
-__device__ __noinline__ void solver_rows_fwd(const SolveInst& I, const double* q, int item,
-                                             unsigned char* smem) {
+__device__ __noinline__ void solver_rows_fwd(const SolveInst& I, const double* q, bool with_rhs,
+                                             int item, unsigned char* smem) {
   SpreadSrc src;
   src.skip_empty_planes = true;  // the grid feeds only the interpolation
   if (q) {
     src.q_div = q;
     src.coef_div = 1.0;
+    if (with_rhs) {
+      // residual of a solve whose b is not stored: the spread of S V_b
+      // joins S~ x (linearity of the Helmholtz solve and of S*)
+      src.v_plain = I.vdata;
+      src.coef_plain = 1.0;
+    }
   } else {
     src.v_plain = I.vdata;  // right-hand side: -S V_b
     src.coef_plain = -1.0;
@@ -393,10 +399,11 @@ __device__ void mv_item(const SolveInst& I, const RoundView& v, int phase, int i
                         unsigned char* smem) {
   const int d = I.g.dim;
   if (phase == 0) {
+    const bool with_rhs = v.action == ACT_MV_RESIDUAL && I.rhs_resid;
     if (d == 2)
-      solver_rows_fwd<T, 2>(I, mv_input(I, v), item, smem);
+      solver_rows_fwd<T, 2>(I, mv_input(I, v), with_rhs, item, smem);
     else
-      solver_rows_fwd<T, 3>(I, mv_input(I, v), item, smem);
+      solver_rows_fwd<T, 3>(I, mv_input(I, v), with_rhs, item, smem);
   } else if (phase == 4) {
     if (d == 2)
       solver_rows_inv<T, 2>(I, v, item, smem);
@@ -457,9 +464,12 @@ __device__ void phase_D(const SolveInst& I, SolveState* S, const RoundView& v, i
     return;
   }
   if (v.action == ACT_RHS) {
-    // b = S* grid, grid = -kappa L'^{-1} S V_b (the Neumann right-hand side);
-    // the round ends here, so chunk 0 also picks the next action
-    if (valid) I.bvec[i] = interp_point<double, D>(I.g, I.p, I.w64.grid, i);
+    // b = S* grid, grid = -kappa L'^{-1} S V_b (the Neumann right-hand side;
+    // in float32 when the residuals carry the S V_b term); the round ends
+    // here, so chunk 0 also picks the next action
+    if (valid)
+      I.bvec[i] = v.prec ? (double)interp_point<float, D>(I.g, I.p, I.w32.grid, i)
+                         : interp_point<double, D>(I.g, I.p, I.w64.grid, i);
     if (chunk == 0 && threadIdx.x == 0) control(I, S, v, 0, 0, 0, R);
     return;
   }
@@ -482,7 +492,7 @@ __device__ void phase_D(const SolveInst& I, SolveState* S, const RoundView& v, i
     bi = __ldcg(I.bvec + i);
     if (v.action == ACT_MV_RESIDUAL) {
       const double t = interp_point<double, D>(I.g, I.p, I.w64.grid, i) + jump * __ldcg(I.x + i);
-      r = bi - t;
+      r = I.rhs_resid ? -t : bi - t;  // rhs_resid: t = A x - b
     } else {
       r = bi;
     }
@@ -788,9 +798,7 @@ __device__ void vec_single(const SolveInst& I, SolveState* S, const RoundView& v
 #pragma unroll
     for (int k = 0; k < kSingleK; ++k) {
       const int i = tid + k * nt;
-      if (i < m)
-        I.bvec[i] = d3 ? interp_point<double, 3>(I.g, I.p, I.w64.grid, i)
-                       : interp_point<double, 2>(I.g, I.p, I.w64.grid, i);
+      if (i < m) I.bvec[i] = d3 ? interp_any<3>(I, v.prec, i) : interp_any<2>(I, v.prec, i);
     }
     __syncthreads();
     if (tid == 0) control(I, S, v, 0, 0, 0, R);
@@ -911,7 +919,8 @@ __device__ void vec_single(const SolveInst& I, SolveState* S, const RoundView& v
       if (v.action == ACT_MV_RESIDUAL) {
         const double acc = d3 ? interp_point<double, 3>(I.g, I.p, I.w64.grid, i)
                               : interp_point<double, 2>(I.g, I.p, I.w64.grid, i);
-        r = bi - (acc + jump * __ldcg(I.x + i));
+        const double t = acc + jump * __ldcg(I.x + i);
+        r = I.rhs_resid ? -t : bi - t;  // rhs_resid: t = A x - b
       }
       I.r[i] = r;
       rk[k] = r;

@@ -122,3 +122,47 @@ def test_c3_field_matches_oracle_and_closed_form(c3_oracle):
     e256r, u256r = _c3_field_error(256, 1)
     e2, einf = parity_errors(u256r, uref)
     assert e2 <= 1e-8 and einf <= 1e-8, (e2, einf)
+
+
+def _true_rel_residual(p, x):
+    """||b - A x|| / ||b|| with the oracle's A and its float64 b (Sec. 4.2:
+    the Neumann b = -kappa S* L'^{-1} S V_b)."""
+    op = O.Operator(p.geom, p.bc)
+    b = op.rhs(p.bdata)
+    return float(np.linalg.norm(b - op.apply(x)) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("batched", [False, True])
+def test_refined_neumann_reports_the_true_residual(batched):
+    """A float32-refined Neumann solve builds its right-hand side in float32
+    only to start the first inner solve; its float64-grade residuals spread
+    S~ x + S V_b into one Helmholtz solve, which is b - A x by linearity.
+    The residual it reports must then be the true one: the oracle's
+    ||b - A x|| / ||b|| of the returned density agrees with the reported
+    value and is below the tolerance, and the density matches the oracle's
+    solve -- alone in a launch and beside a Dirichlet instance."""
+    pn = configs.c2(bc=configs.NEUMANN)
+    pd = configs.c2(bc=configs.DIRICHLET)
+    probs = [pn, pd] if batched else [pn]
+    gs = [pkg.Geometry.from_workload(p.geom, bc=p.bc, precision=ibdl.FP32_REFINED)
+          for p in probs]
+    qs = [torch.zeros(p.geom.m, dtype=torch.float64, device=DEV) for p in probs]
+    try:
+        if batched:
+            batch = ibdl.Batch(len(probs))
+            infos = batch.solve(gs, [gpu(p.bdata) for p in probs], qs, tol=1e-8)
+            batch.close()
+        else:
+            infos = [gs[0].solve(gpu(pn.bdata), qs[0], tol=1e-8)]
+    finally:
+        for g in gs:
+            g.close()
+    info, x = infos[0], host(qs[0])
+    true_rel = _true_rel_residual(pn, x)
+    assert info["status"] == ibdl.OK and info["rel_residual"] <= 1e-8, info
+    assert true_rel <= 1e-8, true_rel
+    # the reported residual is computed in double-float (about 1e-13 of
+    # ||b||) and normed by the float32 b (relative error about 1e-6)
+    assert abs(info["rel_residual"] - true_rel) <= 1e-6 * true_rel + 1e-12, (info, true_rel)
+    ref = O.solve(pn.geom, pn.bc, pn.bdata, tol=1e-13).x
+    assert_parity(x, ref, 1e-8, f"C2 Neumann refined, batched={batched}")
