@@ -1026,12 +1026,14 @@ def main():
             # one launch = whole solves (per_launch of them).  The matvec
             # byte model B = 9 p N^d + p M (4^d + 2d + 4) per field solve:
             # p = 4 for the float32 Arnoldi matvecs (and a refined launch's
-            # Neumann right-hand side), p = 8 for the float64-grade ones (the
-            # residuals, transformed in double-float)
+            # Neumann right-hand side and residual updates), p = 8 for the
+            # float64-grade ones (the residuals, transformed in double-float)
             mv = float(np.mean([f["matvecs"] for f in pinfos])) * per_launch
             it = float(np.mean([f["iters"] for f in pinfos])) * per_launch
-            mv64 = (mv - it) if prec == ibdl.FP32_REFINED else mv
-            mv32 = it if prec == ibdl.FP32_REFINED else 0.0
+            # residuals updated by a float32 matvec of the correction
+            up = float(np.mean([f.get("residual_updates", 0) for f in pinfos])) * per_launch
+            mv64 = (mv - it - up) if prec == ibdl.FP32_REFINED else mv
+            mv32 = (it + up) if prec == ibdl.FP32_REFINED else 0.0
             # the Neumann right-hand side is one more field solve: float32 in
             # a refined launch (its residuals carry the S V_b term), float64
             # else
@@ -1139,6 +1141,13 @@ def main():
             "solo": solo,
             "fp64": fp64,
             "iters_per_solve": {"min": min(iters), "max": max(iters)},
+            # per solve: float64-grade residuals and float32 residual updates
+            "residuals_per_solve": {
+                "float64_grade": float(np.mean([f["matvecs"] - f["iters"]
+                                                - f.get("residual_updates", 0)
+                                                for f in infos])),
+                "float32_updates": float(np.mean([f.get("residual_updates", 0)
+                                                  for f in infos]))},
             "matvecs_per_s": float(sum(mv)) * world / (total_ms / 1e3),
             "rel_err_vs_fp64_1e-12": max(errs),
             "roofline": roofline,

@@ -164,8 +164,15 @@ typedef struct {
   int32_t refine_steps;      /* outer refinement steps taken (0 for FP64) */
   int32_t matvecs;           /* operator applications, all precisions */
   int32_t n_history;         /* entries used in residual_history */
-  double rel_residual;       /* final ||b - A x|| / ||b|| (float64 operator) */
+  double rel_residual;       /* final ||b - A x|| / ||b||: from a float64-grade
+                                residual, or (FP32_REFINED) from a residual
+                                updated after a small correction d as
+                                r - A32 d, within 1e-5 ||d|| of the true
+                                one, a bound the stopping test adds to it */
   double residual_history[256]; /* relative residual after each iteration */
+  int32_t residual_updates;  /* FP32_REFINED: residuals updated by a float32
+                                matvec of the last correction instead of
+                                recomputed (counted in matvecs) */
 } ibdl_solve_info;
 
 /* Sets every field of *opts to its default. */

@@ -687,6 +687,8 @@ SolveInst make_inst(ibdl_geometry_s* g, const ibdl_solve_opts& o, int batch_size
   I.bvec = g->vb;
   I.x = g->vx;
   I.r = g->vr;
+  I.dvec = g->vt;  // free in the persistent engine (the host loop's scratch)
+  I.upd_resid = g->precision == IBDL_FP32_REFINED;
   I.bc = g->bc;
   I.refined = g->precision == IBDL_FP32_REFINED;
   I.maxit = o.max_iters;
@@ -752,6 +754,7 @@ void info_from_state(const SolveState& st, const double* hist, ibdl_solve_info* 
   info->iters = st.iters;
   info->refine_steps = st.outer;
   info->matvecs = st.matvecs;
+  info->residual_updates = st.nupd;
   info->rel_residual = st.rel;
   const int nh = st.nhist < 256 ? st.nhist : 256;
   info->n_history = nh;

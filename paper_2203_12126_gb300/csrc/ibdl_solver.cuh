@@ -24,8 +24,16 @@ enum SolveAction {
   ACT_MV_RESIDUAL = 2,  // r = b - A64 x
   ACT_MV_ARNOLDI = 3,   // Arnoldi step j
   ACT_FINISH = 4,       // back substitution, x += V y
-  ACT_RHS = 5           // Neumann right-hand side b = -kappa S* L'^{-1} S V_b (float64)
+  ACT_RHS = 5,          // Neumann right-hand side b = -kappa S* L'^{-1} S V_b
+  ACT_MV_UPDATE = 6     // r -= A32 d, d = V y the last correction (refined solves)
 };
+
+// Bound on the float32 operator's error relative to its argument,
+// ||A32 v - A v|| <= kF32OpErr ||v||, used to bound the error of a residual
+// updated by a float32 matvec of the last correction (ACT_MV_UPDATE).  The
+// parity tests hold every float32 matvec within 1e-5 of the float64 oracle
+// (2-norm and element-wise); measured on GB300: 0.6e-8 - 6e-8 (C1, C2, C3).
+constexpr double kF32OpErr = 1e-5;
 
 // Read-only during a launch.
 struct SolveInst {
@@ -60,6 +68,13 @@ struct SolveInst {
   // one Helmholtz solve, r = -(S* kappa L'^{-1} (S~ x + S V_b) - x / 2)
   // = b - A x, so b itself is never needed to float64 accuracy
   int rhs_resid;
+  // 1 (float32-refined solves): after an inner solve whose correction d is
+  // small, the residual is updated, r <- r - A32 d (ACT_MV_UPDATE), instead
+  // of recomputed with a float64-grade matvec; its error grows by at most
+  // kF32OpErr ||d|| (SolveState::rerr), which is allowed up to a tenth of
+  // the tolerance and counted against it
+  int upd_resid;
+  double* dvec;         // the last inner solve's correction d = V y
   double* x;
   double* r;
   int bc;
@@ -82,7 +97,12 @@ struct SolveState {
   int action, prec, j, kdim;
   int iters, outer, status, matvecs;
   int nhist, xinit;  // xinit: the solve starts from a caller-given x
+  int nupd;          // residuals updated by a float32 matvec (ACT_MV_UPDATE)
   double beta, bnorm, tol_abs, rel;
+  // bound on ||r - (b - A x)|| of the stored residual r: 0 after a
+  // float64-grade residual, + kF32OpErr ||d|| per update, infinite while r
+  // is a right-hand side built in float32
+  double rerr;
 };
 
 int solver_smem_bytes(const GridDesc& g, int rows, int need32);

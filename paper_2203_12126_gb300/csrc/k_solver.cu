@@ -127,10 +127,12 @@ __device__ __forceinline__ SolveState load_state(const SolveState* S) {
   s.matvecs = vs->matvecs;
   s.nhist = vs->nhist;
   s.xinit = vs->xinit;
+  s.nupd = vs->nupd;
   s.beta = vs->beta;
   s.bnorm = vs->bnorm;
   s.tol_abs = vs->tol_abs;
   s.rel = vs->rel;
+  s.rerr = vs->rerr;
   return s;
 }
 
@@ -230,11 +232,12 @@ __device__ __forceinline__ SpectralWs<dd> ws_of<dd>(const SolveInst& I) {
 }
 
 __device__ __forceinline__ bool is_mv(int a) {
-  return a == ACT_MV_ARNOLDI || a == ACT_MV_RESIDUAL || a == ACT_RHS;
+  return a == ACT_MV_ARNOLDI || a == ACT_MV_RESIDUAL || a == ACT_RHS || a == ACT_MV_UPDATE;
 }
 
 __device__ __forceinline__ const double* mv_input(const SolveInst& I, const RoundView& v) {
   if (v.action == ACT_RHS) return nullptr;
+  if (v.action == ACT_MV_UPDATE) return I.dvec;
   return v.action == ACT_MV_ARNOLDI ? I.V + (size_t)v.j * I.ld : I.x;
 }
 
@@ -493,6 +496,11 @@ __device__ void phase_D(const SolveInst& I, SolveState* S, const RoundView& v, i
     if (v.action == ACT_MV_RESIDUAL) {
       const double t = interp_point<double, D>(I.g, I.p, I.w64.grid, i) + jump * __ldcg(I.x + i);
       r = I.rhs_resid ? -t : bi - t;  // rhs_resid: t = A x - b
+    } else if (v.action == ACT_MV_UPDATE) {
+      // r <- r - A32 d: x moved by d since r was formed
+      const double t =
+          (double)interp_point<float, D>(I.g, I.p, I.w32.grid, i) + jump * __ldcg(I.dvec + i);
+      r = __ldcg(I.r + i) - t;
     } else {
       r = bi;
     }
@@ -556,7 +564,16 @@ __device__ void phase_E(const SolveInst& I, SolveState* S, const RoundView& v, i
     SolveState st;
     if (threadIdx.x == 0) st = load_state(S);
     if (v.action == ACT_FINISH) {
-      if (threadIdx.x == 0) control(I, S, v, 0, 0, 0, R, &st);
+      if (threadIdx.x == 0) {
+        // ||d|| = ||V y|| = ||y|| (V orthonormal): the update residual's bound
+        double yy = 0;
+        if (I.upd_resid)
+          for (int c = 0; c < v.kdim; ++c) {
+            const double yc = __ldcg(I.ysol + c);
+            yy += yc * yc;
+          }
+        control(I, S, v, 0, sqrt(yy), 0, R, &st);
+      }
     } else {
       reduce_parts(part1, I.nchunk, I.pstride, 0, 2, R.h);
       if (threadIdx.x == 0) control(I, S, v, 0, sqrt(R.h[0]), R.h[1], R, &st);
@@ -570,7 +587,17 @@ __device__ void phase_E(const SolveInst& I, SolveState* S, const RoundView& v, i
     // x += V y: stage -y in shared memory, then one batched pass over V
     for (int c = threadIdx.x; c < v.kdim; c += blockDim.x) R.h[c] = -__ldcg(I.ysol + c);
     __syncthreads();
-    if (valid) I.x[i] = sub_projection(I, __ldcg(I.x + i), i, v.kdim, R.h);
+    if (valid) {
+      if (I.upd_resid) {
+        // the correction d = V y (R.h holds -y) is kept for an update of
+        // the residual
+        const double d = sub_projection(I, 0.0, i, v.kdim, R.h);
+        I.dvec[i] = d;
+        I.x[i] = __ldcg(I.x + i) + d;
+      } else {
+        I.x[i] = sub_projection(I, __ldcg(I.x + i), i, v.kdim, R.h);
+      }
+    }
     __syncthreads();
     return;
   }
@@ -611,10 +638,12 @@ __device__ void control(const SolveInst& I, SolveState* S, const RoundView& v, d
     s.matvecs = vs->matvecs;
     s.nhist = vs->nhist;
     s.xinit = vs->xinit;
+    s.nupd = vs->nupd;
     s.beta = vs->beta;
     s.bnorm = vs->bnorm;
     s.tol_abs = vs->tol_abs;
     s.rel = vs->rel;
+    s.rerr = vs->rerr;
   }
   if (v.action == ACT_MV_ARNOLDI) {
     const int j = v.j;
@@ -661,13 +690,30 @@ __device__ void control(const SolveInst& I, SolveState* S, const RoundView& v, d
       s.j = j + 1;
     }
   } else if (v.action == ACT_FINISH) {
-    s.action = ACT_MV_RESIDUAL;
-    s.prec = 0;
+    // beta carries ||d||, the norm of this inner solve's correction.  A small
+    // correction updates the residual with a float32 matvec, r -= A32 d,
+    // whose error is at most kF32OpErr ||d|| (x_new = x + d, so
+    // b - A x_new = r - A d); the errors of the updates since the last
+    // float64-grade residual may add up to a tenth of the tolerance
+    const double bound = kF32OpErr * beta;
+    if (I.upd_resid && s.bnorm > 0 && s.rerr + bound <= 0.1 * I.tol * s.bnorm) {
+      s.rerr += bound;
+      s.nupd++;
+      s.action = ACT_MV_UPDATE;
+      s.prec = 1;
+    } else {
+      s.action = ACT_MV_RESIDUAL;
+      s.prec = 0;
+    }
   } else if (v.action == ACT_RHS) {
     s.action = s.xinit ? ACT_MV_RESIDUAL : ACT_RESID_ZERO;
     s.prec = 0;
   } else {
-    if (v.action == ACT_MV_RESIDUAL) s.matvecs++;
+    if (v.action == ACT_MV_RESIDUAL || v.action == ACT_MV_UPDATE) s.matvecs++;
+    // the stored residual's error bound (the update added its own share
+    // when it was chosen); r = b32 is no float64-grade residual at all
+    if (v.action == ACT_MV_RESIDUAL) s.rerr = 0.0;
+    if (v.action == ACT_RESID_ZERO) s.rerr = I.rhs_resid ? __longlong_as_double(0x7ff0000000000000LL) : 0.0;
     if (s.bnorm < 0) s.bnorm = sqrt(bnorm2);
     s.beta = beta;
     s.rel = s.bnorm > 0 ? beta / s.bnorm : 0.0;
@@ -677,7 +723,7 @@ __device__ void control(const SolveInst& I, SolveState* S, const RoundView& v, d
     } else if (!isfinite(beta)) {
       s.status = IBDL_ERR_NONFINITE;
       s.action = ACT_DONE;
-    } else if (s.rel <= I.tol) {
+    } else if ((beta + s.rerr) / s.bnorm <= I.tol) {
       s.status = IBDL_OK;
       s.action = ACT_DONE;
     } else if (s.iters >= I.maxit || (I.refined && s.outer >= I.max_refine)) {
@@ -816,11 +862,14 @@ __device__ void vec_single(const SolveInst& I, SolveState* S, const RoundView& v
       }
     }
     __syncthreads();
+    // x += V y; with upd_resid the correction d = V y is summed on its own
+    // and kept for an update of the residual
+    const bool upd = I.upd_resid;
     double xk[kSingleK];
 #pragma unroll
     for (int k = 0; k < kSingleK; ++k) {
       const int i = tid + k * nt;
-      xk[k] = i < m ? __ldcg(I.x + i) : 0.0;
+      xk[k] = (i < m && !upd) ? __ldcg(I.x + i) : 0.0;
     }
     for (int c = 0; c < v.kdim; ++c) {
       const double yc = R.h[c];
@@ -834,10 +883,22 @@ __device__ void vec_single(const SolveInst& I, SolveState* S, const RoundView& v
 #pragma unroll
     for (int k = 0; k < kSingleK; ++k) {
       const int i = tid + k * nt;
-      if (i < m) I.x[i] = xk[k];
+      if (i < m) {
+        if (upd) {
+          I.dvec[i] = xk[k];
+          I.x[i] = __ldcg(I.x + i) + xk[k];
+        } else {
+          I.x[i] = xk[k];
+        }
+      }
     }
     __syncthreads();
-    if (tid == 0) control(I, S, v, 0, 0, 0, R);
+    if (tid == 0) {
+      double yy = 0;  // ||d|| = ||y|| (V orthonormal)
+      if (upd)
+        for (int c = 0; c < v.kdim; ++c) yy += R.h[c] * R.h[c];
+      control(I, S, v, 0, sqrt(yy), 0, R);
+    }
     __syncthreads();
     return;
   }
@@ -921,6 +982,10 @@ __device__ void vec_single(const SolveInst& I, SolveState* S, const RoundView& v
                               : interp_point<double, 2>(I.g, I.p, I.w64.grid, i);
         const double t = acc + jump * __ldcg(I.x + i);
         r = I.rhs_resid ? -t : bi - t;  // rhs_resid: t = A x - b
+      } else if (v.action == ACT_MV_UPDATE) {
+        const double t = (d3 ? interp_any<3>(I, 1, i) : interp_any<2>(I, 1, i)) +
+                         jump * __ldcg(I.dvec + i);
+        r = __ldcg(I.r + i) - t;
       }
       I.r[i] = r;
       rk[k] = r;

@@ -69,12 +69,13 @@ class SolveInfo(C.Structure):
     _fields_ = [
         ("iters", C.c_int32), ("refine_steps", C.c_int32), ("matvecs", C.c_int32),
         ("n_history", C.c_int32), ("rel_residual", C.c_double),
-        ("residual_history", C.c_double * 256),
+        ("residual_history", C.c_double * 256), ("residual_updates", C.c_int32),
     ]
 
     def as_dict(self):
         return {"iters": self.iters, "refine_steps": self.refine_steps,
                 "matvecs": self.matvecs, "rel_residual": self.rel_residual,
+                "residual_updates": self.residual_updates,
                 "history": list(self.residual_history[: self.n_history])}
 
 

@@ -132,37 +132,42 @@ def _true_rel_residual(p, x):
     return float(np.linalg.norm(b - op.apply(x)) / np.linalg.norm(b))
 
 
+@pytest.mark.parametrize("bc", ["neumann", "dirichlet"])
 @pytest.mark.parametrize("batched", [False, True])
-def test_refined_neumann_reports_the_true_residual(batched):
-    """A float32-refined Neumann solve builds its right-hand side in float32
-    only to start the first inner solve; its float64-grade residuals spread
-    S~ x + S V_b into one Helmholtz solve, which is b - A x by linearity.
-    The residual it reports must then be the true one: the oracle's
-    ||b - A x|| / ||b|| of the returned density agrees with the reported
-    value and is below the tolerance, and the density matches the oracle's
-    solve -- alone in a launch and beside a Dirichlet instance."""
-    pn = configs.c2(bc=configs.NEUMANN)
-    pd = configs.c2(bc=configs.DIRICHLET)
-    probs = [pn, pd] if batched else [pn]
+def test_refined_solve_reports_the_true_residual(bc, batched):
+    """The residual a float32-refined solve reports is the true one.
+
+    Two shortcuts feed it: a Neumann solve builds its right-hand side in
+    float32 only to start the first inner solve, its float64-grade residuals
+    spreading S~ x + S V_b into one Helmholtz solve (b - A x by linearity);
+    and after an inner solve with a small correction d the residual is
+    updated, r <- r - A32 d, with an error of at most 1e-5 ||d|| that the
+    stopping test counts against the tolerance.  So the oracle's
+    ||b - A x|| / ||b|| of the returned density must be below the tolerance
+    and agree with the reported value to a tenth of it, and the density must
+    match the oracle's solve -- alone in a launch and beside an instance of
+    the other boundary condition."""
+    p0 = configs.c2(bc=configs.NEUMANN if bc == "neumann" else configs.DIRICHLET)
+    p1 = configs.c2(bc=configs.DIRICHLET if bc == "neumann" else configs.NEUMANN)
+    probs = [p0, p1] if batched else [p0]
+    tol = 1e-8
     gs = [pkg.Geometry.from_workload(p.geom, bc=p.bc, precision=ibdl.FP32_REFINED)
           for p in probs]
     qs = [torch.zeros(p.geom.m, dtype=torch.float64, device=DEV) for p in probs]
     try:
         if batched:
             batch = ibdl.Batch(len(probs))
-            infos = batch.solve(gs, [gpu(p.bdata) for p in probs], qs, tol=1e-8)
+            infos = batch.solve(gs, [gpu(p.bdata) for p in probs], qs, tol=tol)
             batch.close()
         else:
-            infos = [gs[0].solve(gpu(pn.bdata), qs[0], tol=1e-8)]
+            infos = [gs[0].solve(gpu(p0.bdata), qs[0], tol=tol)]
     finally:
         for g in gs:
             g.close()
     info, x = infos[0], host(qs[0])
-    true_rel = _true_rel_residual(pn, x)
-    assert info["status"] == ibdl.OK and info["rel_residual"] <= 1e-8, info
-    assert true_rel <= 1e-8, true_rel
-    # the reported residual is computed in double-float (about 1e-13 of
-    # ||b||) and normed by the float32 b (relative error about 1e-6)
-    assert abs(info["rel_residual"] - true_rel) <= 1e-6 * true_rel + 1e-12, (info, true_rel)
-    ref = O.solve(pn.geom, pn.bc, pn.bdata, tol=1e-13).x
-    assert_parity(x, ref, 1e-8, f"C2 Neumann refined, batched={batched}")
+    true_rel = _true_rel_residual(p0, x)
+    assert info["status"] == ibdl.OK and info["rel_residual"] <= tol, info
+    assert true_rel <= tol, true_rel
+    assert abs(info["rel_residual"] - true_rel) <= 0.1 * tol, (info, true_rel)
+    ref = O.solve(p0.geom, p0.bc, p0.bdata, tol=1e-13).x
+    assert_parity(x, ref, 1e-8, f"C2 {bc} refined, batched={batched}")
