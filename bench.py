@@ -79,6 +79,9 @@ def parse():
     ap.add_argument("--pencils", default=None,
                     help="--profile-case: pin the pencils per item of the solve pass and "
                          "of the 3D y passes, as 'c_solve,c_y' (c_y 0 in 2D)")
+    ap.add_argument("--plan", type=int, default=None,
+                    help="--profile-case: pin the float32 FFT plan variant of 2D "
+                         "float32-refined kinds (0 or 1)")
     return ap.parse_args()
 
 
@@ -490,6 +493,8 @@ def run_profile_case(args):
         if args.pencils:
             cs, cy = (int(v) for v in args.pencils.split(","))
             ibdl.tuning_set_pencils(prob.geom.dim, prob.geom.n, min(prec, 1), cs, cy)
+        if args.plan is not None and prob.geom.dim == 2:
+            ibdl.tuning_set_plan(2, prob.geom.n, ibdl.FP32_REFINED, args.plan)
         g = pkg.Geometry.from_workload(prob.geom, bc=prob.bc, precision=min(prec, 1))
         q = torch.tensor(np.random.default_rng(0).standard_normal(prob.geom.m), device=dev)
         y = torch.empty_like(q)
@@ -506,6 +511,8 @@ def run_profile_case(args):
     if args.pencils:
         cs, cy = (int(v) for v in args.pencils.split(","))
         ibdl.tuning_set_pencils(2, probs[0].geom.n, ibdl.FP32_REFINED, cs, cy)
+    if args.plan is not None:
+        ibdl.tuning_set_plan(2, probs[0].geom.n, ibdl.FP32_REFINED, args.plan)
     gs = [pkg.Geometry.from_workload(p.geom, bc=p.bc, precision=ibdl.FP32_REFINED)
           for p in probs]
     bs = [torch.tensor(p.bdata, device=dev) for p in probs]
@@ -715,7 +722,9 @@ def run_matvec_roofline(pkg, peaks, reps=30):
                                     "frac_of_hbm": gbs / peaks["hbm_gbs"],
                                     "peak_src": peaks["src"],
                                     "kernel_us": split,
-                                    "rows_per_tile": g.info()["rows_per_tile"]}
+                                    "rows_per_tile": g.info()["rows_per_tile"],
+                                    "pencils_per_item": g.info()["pencils_per_item"],
+                                    "fft_plan": g.info()["fft_plan"]}
         g.close()
     return out
 
@@ -1140,6 +1149,9 @@ def main():
                                   else "step (two solves in sequence)"},
             "solo": solo,
             "fp64": fp64,
+            # the autotuner's picks for the benchmark's geometry kind
+            "tuner_picks": {k: geoms[0].info()[k]
+                            for k in ("rows_per_tile", "pencils_per_item", "fft_plan")},
             "iters_per_solve": {"min": min(iters), "max": max(iters)},
             # per solve: float64-grade residuals and float32 residual updates
             "residuals_per_solve": {

@@ -427,6 +427,10 @@ typedef struct {
   int32_t pencils_per_item[2]; /* pencils per work item of the solve pass (2D y,
                                   3D z) and of the 3D y passes (0 in 2D), in
                                   the geometry's inner precision */
+  int32_t fft_plan;          /* FFT plan variant of the float32 transforms:
+                                0 radices as even as possible after a first
+                                radix-16 pass (1024 = 16*8*8), 1 radix-16
+                                passes first (1024 = 16*16*4; n = 512, 1024) */
 } ibdl_geometry_info;
 ibdl_status ibdl_get_geometry_info(ibdl_geometry g, ibdl_geometry_info* info);
 
@@ -472,6 +476,21 @@ ibdl_status ibdl_tuning_set(int32_t dim, int32_t n, int32_t precision, int32_t r
  * device cannot be read.  No passage of the paper: a resource choice. */
 ibdl_status ibdl_tuning_set_pencils(int32_t dim, int32_t n, int32_t precision, int32_t c_solve,
                                     int32_t c_y);
+
+/* Pins the FFT plan variant of the float32 transforms of one (current
+ * device, dim = 2, n, IBDL_FP32_REFINED) kind, as if the autotuner had
+ * chosen it:
+ * plan 0 = a first pass of radix 16, then the remaining bits split as evenly
+ * as possible (1024 = 16 * 8 * 8, 512 = 16 * 8 * 4); plan 1 = radix-16
+ * passes first, the remainder last (1024 = 16 * 16 * 4, 512 = 16 * 16 * 2),
+ * offered for n = 512 and 1024 only (the other sizes have one plan); plan -1
+ * drops the pin (the next geometry of the kind tunes again; 3D geometries
+ * always use plan 0).  Later geometries of the
+ * kind transform in that plan everywhere in float32, the persistent solver
+ * included; results agree with plan 0's to rounding.  IBDL_ERR_INVALID_ARG
+ * for another precision, size or plan; IBDL_ERR_CUDA if the current device
+ * cannot be read.  No passage of the paper: a resource choice. */
+ibdl_status ibdl_tuning_set_plan(int32_t dim, int32_t n, int32_t precision, int32_t plan);
 
 /* Pencils per work item of the persistent solver's solve pass (2D y
  * pencils, 3D z pencils) for this geometry's solves, per element type:

@@ -274,22 +274,25 @@ void cis_2pi(int64_t num, int64_t den, double* c, double* s) {
 std::mutex g_tab_mu;
 std::map<std::tuple<int, int, int>, std::pair<const void*, const void*>> g_tabs;
 
+// v: the plan variant of the twiddle table (float32 only; see plan_lr).
 template <typename T>
-ibdl_status fft_tables(int n, const typename Cx<T>::type** tw_out, const T** s2_out) {
+ibdl_status fft_tables(int n, const typename Cx<T>::type** tw_out, const T** s2_out, int v = 0) {
   int dev = 0;
   IBDL_CU(cudaGetDevice(&dev));
+  if (v != 0 && !std::is_same<T, float>::value)
+    return fail(IBDL_ERR_INVALID_ARG, "FFT tables: only float32 tables have plan variants");
   std::lock_guard<std::mutex> lk(g_tab_mu);
-  const int tag = std::is_same<T, dd>::value ? 2 : (sizeof(T) == 8 ? 1 : 0);
+  const int tag = (std::is_same<T, dd>::value ? 2 : (sizeof(T) == 8 ? 1 : 0)) + 3 * v;
   const auto key = std::make_tuple(dev, n, tag);
   auto it = g_tabs.find(key);
   if (it == g_tabs.end()) {
-    const int ntw = fft_tw_count(n);
-    if (ntw < 0) return fail(IBDL_ERR_INVALID_ARG, "FFT tables: unsupported n");
+    const int ntw = fft_tw_count(n, v);
+    if (ntw < 0) return fail(IBDL_ERR_INVALID_ARG, "FFT tables: unsupported n or plan");
     std::vector<typename Cx<T>::type> htw(ntw);
     std::vector<T> hs2(n);
     for (int j = 0; j < ntw; ++j) {
       int num, den;
-      fft_tw_angle(n, j, &num, &den);
+      fft_tw_angle(n, j, &num, &den, v);
       double c, s;
       cis_2pi(num, den, &c, &s);
       htw[j].x = (T)c;
@@ -322,12 +325,29 @@ ibdl_status alloc_spectral(ibdl_geometry_s* g, SpectralWs<T>& ws, cudaStream_t) 
   const T* s2;
   IBDL_TRY(g->alloc(&spec, (size_t)spec_count));
   IBDL_TRY(g->alloc(&grid, (size_t)g->ncells));
-  IBDL_TRY(fft_tables<T>(n, &tw, &s2));
+  IBDL_TRY(fft_tables<T>(n, &tw, &s2, plan_variant_of<T>(g->grid)));
   if (g->grid.spectral) IBDL_TRY(g->alloc(&ws.acc, (size_t)spec_count));
   ws.spec = spec;
   ws.grid = grid;
   ws.tw = tw;
   ws.s2 = s2;
+  return IBDL_OK;
+}
+
+// Switches the geometry's float32 transforms to plan variant v: its float32
+// twiddle table is replaced by that variant's (the buffers and budgets are
+// sized for either, fft_tw_capacity).  No-op before the float32 workspace
+// exists; ensure32 then takes the table of g->grid.fplan.
+ibdl_status set_float_plan(ibdl_geometry_s* g, int v) {
+  if (v < 0 || v >= kPlanVariants || !plan_offered(g->grid.log2n, v))
+    return fail(IBDL_ERR_INVALID_ARG, "plan variant not offered for this size");
+  if (g->have32) {
+    const cx_t<float>* tw;
+    const float* s2;
+    IBDL_TRY(fft_tables<float>(g->grid.n, &tw, &s2, v));
+    g->ws32.tw = tw;
+  }
+  g->grid.fplan = v;
   return IBDL_OK;
 }
 
@@ -1021,6 +1041,60 @@ ibdl_status tuned_pencils(ibdl_geometry_s* g, cudaStream_t st) {
   return IBDL_OK;
 }
 
+// FFT plan variant of the float32 transforms, per (device, dim, n,
+// precision): a float32-refined 2D geometry of a size with two plans
+// (n = 512, 1024: radices as even as possible, or radix-16 passes first,
+// plan_lr) times its float32 matvec in each, after the tiling and the
+// pencils per item, and keeps the radix-16-first plan only when it is at
+// least 2% faster.  3D geometries and float64 precision keep the balanced
+// plan (the double-float and float64 transforms have one plan each).
+std::map<std::tuple<int, int, int, int>, int> g_tuned_plan;
+
+ibdl_status tuned_plan(ibdl_geometry_s* g, cudaStream_t st) {
+  GridDesc& gd = g->grid;
+  const int n = gd.n, dim = gd.dim;
+  if (!g_tuning_on.load() || gd.spectral || g->eta > 0) return IBDL_OK;
+  if (g->precision != IBDL_FP32_REFINED || !plan_offered(gd.log2n, 1)) return IBDL_OK;
+  int dev = 0;
+  IBDL_CU(cudaGetDevice(&dev));
+  const auto key = std::make_tuple(dev, dim, n, g->precision);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned_plan.find(key);
+    if (it != g_tuned_plan.end()) return dim == 2 ? set_float_plan(g, it->second) : IBDL_OK;
+  }
+  if (tl_no_tune || dim != 2) return IBDL_OK;
+  cudaMemPool_t pool;
+  IBDL_CU(workspace_pool(&pool));
+  const int m = g->m;
+  double *q = nullptr, *y = nullptr;
+  IBDL_CU(cudaMallocFromPoolAsync((void**)&q, sizeof(double) * m, pool, st));
+  IBDL_CU(cudaMallocFromPoolAsync((void**)&y, sizeof(double) * m, pool, st));
+  IBDL_CU(cudaMemsetAsync(q, 0, sizeof(double) * m, st));
+  IBDL_CU(launch_fill(m, q, 1.0, st));
+  cudaEvent_t e0, e1;
+  IBDL_CU(cudaEventCreate(&e0));
+  IBDL_CU(cudaEventCreate(&e1));
+  float ms[kPlanVariants] = {0, 0};
+  ibdl_status status = IBDL_OK;
+  for (int v = 0; v < kPlanVariants && status == IBDL_OK; ++v) {
+    if ((status = set_float_plan(g, v)) != IBDL_OK) break;
+    status = time_matvecs(g, q, y, e0, e1, st, &ms[v]);
+  }
+  const int best = (status == IBDL_OK && ms[1] < 0.98f * ms[0]) ? 1 : 0;
+  cudaFreeAsync(q, st);
+  cudaFreeAsync(y, st);
+  cudaStreamSynchronize(st);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const ibdl_status s2 = set_float_plan(g, best);
+  if (status != IBDL_OK) return status;
+  if (s2 != IBDL_OK) return s2;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned_plan[key] = best;
+  return IBDL_OK;
+}
+
 ibdl_status check_handle(ibdl_geometry g) {
   if (!g) return fail(IBDL_ERR_INVALID_ARG, "NULL geometry handle");
   return IBDL_OK;
@@ -1228,8 +1302,10 @@ ibdl_status ibdl_create_geometry(const ibdl_geometry_desc* d, void* stream, ibdl
     cudaError_t e = build_tiles(g, rows, start, cursor, counts, bpts, spts, dz, &g->bins, st);
     if (e) return cleanup(cuda_fail(e, "binning"));
   }
-  // pencils per item of the pencil passes, with the autotuner
+  // pencils per item of the pencil passes, then the float32 FFT plan, with
+  // the autotuner
   if ((s = tuned_pencils(g, st))) return cleanup(s);
+  if ((s = tuned_plan(g, st))) return cleanup(s);
 
   // Krylov workspace (float64, restart up to 64)
   KrylovWs& k = g->kry;
@@ -1742,6 +1818,7 @@ ibdl_status ibdl_get_geometry_info(ibdl_geometry g, ibdl_geometry_info* info) {
   info->device_bytes = g->bytes;
   info->fft_passes = fft_kernels_per_solve<double>(g->grid.dim);
   info->rows_per_tile = g->bins.rows;
+  info->fft_plan = g->grid.fplan;
   // the pencils per item the passes of the geometry's inner precision use
   if (g->precision == IBDL_FP32_REFINED) {
     info->pencils_per_item[0] = solve_layout<float>(g->grid, 1).c;
@@ -1921,6 +1998,24 @@ ibdl_status ibdl_tuning_set_pencils(int32_t dim, int32_t n, int32_t precision, i
     g_tuned_pc.erase(key);
   else
     g_tuned_pc[key] = {c_y, c_solve};
+  return IBDL_OK;
+}
+
+ibdl_status ibdl_tuning_set_plan(int32_t dim, int32_t n, int32_t precision, int32_t plan) {
+  g_err.clear();
+  if (dim != 2 || n < 16 || n > kMaxN2 || (n & (n - 1)) || precision != IBDL_FP32_REFINED)
+    return fail(IBDL_ERR_INVALID_ARG,
+                "dim, n or precision (plan variants: 2D, float32-refined only)");
+  if (plan < -1 || plan >= kPlanVariants || (plan >= 0 && !plan_offered(ilog2(n), plan)))
+    return fail(IBDL_ERR_INVALID_ARG, "plan variant not offered for this size");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return fail(IBDL_ERR_CUDA, "cudaGetDevice");
+  const auto key = std::make_tuple(dev, (int)dim, (int)n, (int)precision);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (plan < 0)
+    g_tuned_plan.erase(key);
+  else
+    g_tuned_plan[key] = plan;
   return IBDL_OK;
 }
 

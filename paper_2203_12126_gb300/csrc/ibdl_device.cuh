@@ -102,23 +102,39 @@ template <typename C> __device__ __forceinline__ C cconj(C a) {
 __host__ __device__ constexpr int padi(int t) { return t + (t >> 4); }
 __host__ __device__ constexpr int pen_stride(int n) { return n + (n >> 4) + 1; }
 
-// Pass plan of an n = 2^lg point FFT: a first pass of radix 16 (or n when
-// n < 16), then the remaining bits split as evenly as possible into passes
-// of radix <= 16, larger radices first.  After the first pass Ns >= 16, so
-// the padded shared offsets of every later pass are compile-time constants.
-__host__ __device__ constexpr int plan_npass(int lg) { return lg <= 4 ? 1 : 1 + (lg - 1) / 4; }
-__host__ __device__ constexpr int plan_lr(int lg, int s) {
-  return s == 0 ? (lg < 4 ? lg : 4)
-                : (lg - 4) / (plan_npass(lg) - 1) +
-                      (s - 1 < (lg - 4) % (plan_npass(lg) - 1) ? 1 : 0);
+// Pass plan of an n = 2^lg point FFT, named by a plan code pl = lg + 16 v:
+// a first pass of radix 16 (or n when n < 16), then the remaining bits in
+// passes of radix <= 16, larger radices first -- split as evenly as
+// possible (variant v = 0: 1024 = 16 * 8 * 8, 512 = 16 * 8 * 4), or radix-16
+// passes first and the remainder last (v = 1: 1024 = 16 * 16 * 4,
+// 512 = 16 * 16 * 2).  The two differ only for lg = 9 and 10, the only
+// sizes where v = 1 is offered (the float32 transforms of 2D geometries,
+// chosen by the autotuner).  After the first pass Ns >= 16, so the padded
+// shared offsets of every later pass are compile-time constants.
+constexpr int kPlanVariants = 2;
+__host__ __device__ constexpr int plan_lg(int pl) { return pl & 15; }
+__host__ __device__ constexpr int plan_variant(int pl) { return pl >> 4; }
+__host__ __device__ constexpr int plan_npass(int pl) {
+  return plan_lg(pl) <= 4 ? 1 : 1 + (plan_lg(pl) - 1) / 4;
 }
-__host__ __device__ constexpr int plan_lgns(int lg, int s) {
-  return s == 0 ? 0 : plan_lgns(lg, s - 1) + plan_lr(lg, s - 1);
+__host__ __device__ constexpr int plan_lr(int pl, int s) {
+  return s == 0 ? (plan_lg(pl) < 4 ? plan_lg(pl) : 4)
+         : plan_variant(pl) == 1
+             ? (s < plan_npass(pl) - 1 ? 4 : plan_lg(pl) - 4 - 4 * (plan_npass(pl) - 2))
+             : (plan_lg(pl) - 4) / (plan_npass(pl) - 1) +
+                   (s - 1 < (plan_lg(pl) - 4) % (plan_npass(pl) - 1) ? 1 : 0);
 }
-__host__ __device__ constexpr int plan_off(int lg, int s) {
-  return s == 0 ? 0 : plan_off(lg, s - 1) + (1 << (plan_lgns(lg, s - 1) + plan_lr(lg, s - 1)));
+__host__ __device__ constexpr int plan_lgns(int pl, int s) {
+  return s == 0 ? 0 : plan_lgns(pl, s - 1) + plan_lr(pl, s - 1);
 }
-__host__ __device__ constexpr int plan_tw_total(int lg) { return plan_off(lg, plan_npass(lg)); }
+__host__ __device__ constexpr int plan_off(int pl, int s) {
+  return s == 0 ? 0 : plan_off(pl, s - 1) + (1 << (plan_lgns(pl, s - 1) + plan_lr(pl, s - 1)));
+}
+__host__ __device__ constexpr int plan_tw_total(int pl) { return plan_off(pl, plan_npass(pl)); }
+// the variants that exist for an lg (v = 1 only where it differs from v = 0)
+__host__ __device__ constexpr bool plan_offered(int lg, int v) {
+  return v == 0 || (v == 1 && (lg == 9 || lg == 10));
+}
 
 __host__ __device__ inline int ilog2(int n) {
   int lg = 0;
@@ -126,12 +142,15 @@ __host__ __device__ inline int ilog2(int n) {
   return lg;
 }
 
-// Twiddle-table entries of an n-point FFT (the passes' tables concatenated),
-// n = 2^lg with 4 <= lg <= 12 (16 ... 4096 points, the sizes the library
-// accepts); -1 for any other n, so a caller sizing a buffer from it fails
-// instead of silently taking another size's table.
-__host__ __device__ inline int fft_tw_count(int n) {
-  switch (ilog2(n)) {
+// Twiddle-table entries of an n-point FFT (the passes' tables concatenated)
+// in plan variant v, n = 2^lg with 4 <= lg <= 12 (16 ... 4096 points, the
+// sizes the library accepts); -1 for any other n or a variant not offered
+// for it, so a caller sizing a buffer from it fails instead of silently
+// taking another size's table.
+__host__ __device__ inline int fft_tw_count(int n, int v = 0) {
+  const int lg = ilog2(n);
+  if ((1 << lg) != n || v < 0 || v >= kPlanVariants || !plan_offered(lg, v)) return -1;
+  switch (lg + 16 * v) {
     case 4: return plan_tw_total(4);
     case 5: return plan_tw_total(5);
     case 6: return plan_tw_total(6);
@@ -141,18 +160,41 @@ __host__ __device__ inline int fft_tw_count(int n) {
     case 10: return plan_tw_total(10);
     case 11: return plan_tw_total(11);
     case 12: return plan_tw_total(12);
+    case 16 + 9: return plan_tw_total(16 + 9);
+    case 16 + 10: return plan_tw_total(16 + 10);
     default: return -1;
   }
 }
 
-// Table entry idx of an n-point FFT is exp(-2 pi i num / den) (the passes'
-// tables walked without recursion, for run-time n).
-__host__ __device__ inline void fft_tw_angle(int n, int idx, int* num, int* den) {
-  const int lg = ilog2(n), np = plan_npass(lg);
+// Entries a twiddle buffer of element type T holds: the float32 tables may
+// be of either variant (the autotuner's choice, per geometry), so their
+// buffers and shared-memory budgets take the larger; the others use v = 0.
+template <typename T>
+__host__ __device__ inline int fft_tw_capacity(int n) {
+  const int t0 = fft_tw_count(n, 0);
+  if (!std::is_same<T, float>::value || t0 < 0) return t0;
+  const int t1 = fft_tw_count(n, 1);
+  return t1 > t0 ? t1 : t0;
+}
+
+// Plan variant and plan code of a geometry's transforms of element type T
+// (only the float32 transforms have a tuned variant).
+template <typename T>
+__host__ __device__ inline int plan_variant_of(const GridDesc& g) {
+  return std::is_same<T, float>::value ? g.fplan : 0;
+}
+template <typename T>
+__host__ __device__ inline int plan_code_of(const GridDesc& g) {
+  return g.log2n + 16 * plan_variant_of<T>(g);
+}
+
+// Table entry idx of an n-point FFT in plan variant v is exp(-2 pi i num /
+// den) (the passes' tables walked without recursion, for run-time n).
+__host__ __device__ inline void fft_tw_angle(int n, int idx, int* num, int* den, int v = 0) {
+  const int pl = ilog2(n) + 16 * v, np = plan_npass(pl);
   int off = 0, lgns = 0;
   for (int s = 0; s < np; ++s) {
-    const int lr = s == 0 ? (lg < 4 ? lg : 4)
-                          : (lg - 4) / (np - 1) + (s - 1 < (lg - 4) % (np - 1) ? 1 : 0);
+    const int lr = plan_lr(pl, s);
     const int size = 1 << (lgns + lr);
     if (idx < off + size || s == np - 1) {
       const int local = idx - off;
@@ -428,6 +470,7 @@ __device__ __forceinline__ void fft_pass16_split(const cx_t<T>* __restrict__ src
                                                  cx_t<T>* __restrict__ dst, int npen,
                                                  const GlobalPencils<T>& gio) {
   using C = cx_t<T>;
+  static_assert(plan_variant(LG) == 0, "double-float transforms use the balanced plan");
   constexpr int N = 1 << LG, LGNB = LG - 4, NB = 1 << LGNB, PS = pen_stride(N);
   const int e = threadIdx.x;
   // the caller checked 2 total <= blockDim and total % 16 == 0, so the
@@ -523,14 +566,16 @@ __device__ __forceinline__ void fft_pass(const cx_t<T>* __restrict__ src,
   using C = cx_t<T>;
   constexpr bool kSym = SYM && !INV && DirectPencils<T>::value;
   constexpr bool kGlobal = GIN || GOUT;
-  constexpr int N = 1 << LG;
+  // LG is a plan code (plan_lg(LG) = log2 n, plan_variant(LG) the variant)
+  constexpr int N = 1 << plan_lg(LG);
   constexpr int LR = plan_lr(LG, S), LGNS = plan_lgns(LG, S), OFF = plan_off(LG, S);
-  constexpr int R = 1 << LR, LGNB = LG - LR, NB = 1 << LGNB, NS = 1 << LGNS;
+  constexpr int R = 1 << LR, LGNB = plan_lg(LG) - LR, NB = 1 << LGNB, NS = 1 << LGNS;
   constexpr int PS = pen_stride(N);
   static_assert(!GIN || S == 0, "global inputs feed the first pass");
   static_assert(!STR || kGlobal, "the strided order is for global accesses");
   const int total = npen << LGNB;
-  if constexpr (std::is_same<T, dd>::value && S == 0 && LR == 4 && LG > 4 && !SYM && !GOUT) {
+  if constexpr (std::is_same<T, dd>::value && S == 0 && LR == 4 && plan_lg(LG) > 4 && !SYM &&
+                !GOUT) {
     // a first pass that is not also the last (fft_passes also instantiates
     // unreached passes with S = 0, which keep the plain loop).  Only the
     // double-float butterflies are split: the split costs six more twiddle
@@ -717,11 +762,16 @@ __device__ __noinline__ void fft_global_lg(cx_t<T>* bufA, cx_t<T>* bufB, int npe
 }
 
 template <typename T, int MODE, bool STR, bool SIN = false>
-__device__ __forceinline__ void fft_global(cx_t<T>* bufA, cx_t<T>* bufB, int lg, int npen,
+__device__ __forceinline__ void fft_global(cx_t<T>* bufA, cx_t<T>* bufB, int pl, int npen,
                                            const cx_t<T>* __restrict__ tws,
                                            const SymbolEpi<T>& epi, const GlobalPencils<T>& gio) {
   static_assert(DirectPencils<T>::value, "double-float stages its pencils");
-  switch (lg) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (pl == 16 + 9) return fft_global_lg<T, 16 + 9, MODE, STR, SIN>(bufA, bufB, npen, tws, epi, gio);
+    if (pl == 16 + 10)
+      return fft_global_lg<T, 16 + 10, MODE, STR, SIN>(bufA, bufB, npen, tws, epi, gio);
+  }
+  switch (plan_lg(pl)) {
     case 4: return fft_global_lg<T, 4, MODE, STR, SIN>(bufA, bufB, npen, tws, epi, gio);
     case 5: return fft_global_lg<T, 5, MODE, STR, SIN>(bufA, bufB, npen, tws, epi, gio);
     case 6: return fft_global_lg<T, 6, MODE, STR, SIN>(bufA, bufB, npen, tws, epi, gio);
@@ -746,10 +796,14 @@ __device__ __noinline__ void fft_inverse_rows_lg(cx_t<T>* bufA, cx_t<T>* bufB, i
 }
 
 template <typename T, typename OutT>
-__device__ __forceinline__ void fft_inverse_rows(cx_t<T>* bufA, cx_t<T>* bufB, int lg, int npen,
+__device__ __forceinline__ void fft_inverse_rows(cx_t<T>* bufA, cx_t<T>* bufB, int pl, int npen,
                                                  const cx_t<T>* __restrict__ tws, OutT* rows) {
   static_assert(DirectPencils<T>::value, "double-float stages its rows");
-  switch (lg) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (pl == 16 + 9) return fft_inverse_rows_lg<T, 16 + 9>(bufA, bufB, npen, tws, rows);
+    if (pl == 16 + 10) return fft_inverse_rows_lg<T, 16 + 10>(bufA, bufB, npen, tws, rows);
+  }
+  switch (plan_lg(pl)) {
     case 4: return fft_inverse_rows_lg<T, 4>(bufA, bufB, npen, tws, rows);
     case 5: return fft_inverse_rows_lg<T, 5>(bufA, bufB, npen, tws, rows);
     case 6: return fft_inverse_rows_lg<T, 6>(bufA, bufB, npen, tws, rows);
@@ -763,12 +817,17 @@ __device__ __forceinline__ void fft_inverse_rows(cx_t<T>* bufA, cx_t<T>* bufB, i
 }
 
 // Transforms npen pencils held in src (shared, padded layout); tws is the
-// concatenated twiddle table in shared memory.  The caller synchronises
-// before the call.  Returns the buffer (src or dst) holding the result.
+// concatenated twiddle table in shared memory, of the plan pl (a plan code:
+// log2 n + 16 * variant).  The caller synchronises before the call.
+// Returns the buffer (src or dst) holding the result.
 template <typename T, bool INV>
-__device__ __forceinline__ cx_t<T>* fft_run(cx_t<T>* src, cx_t<T>* dst, int lg, int npen,
+__device__ __forceinline__ cx_t<T>* fft_run(cx_t<T>* src, cx_t<T>* dst, int pl, int npen,
                                             const cx_t<T>* __restrict__ tws) {
-  switch (lg) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (pl == 16 + 9) return fft_run_lg<T, 16 + 9, INV>(src, dst, npen, tws);
+    if (pl == 16 + 10) return fft_run_lg<T, 16 + 10, INV>(src, dst, npen, tws);
+  }
+  switch (plan_lg(pl)) {
     case 4: return fft_run_lg<T, 4, INV>(src, dst, npen, tws);
     case 5: return fft_run_lg<T, 5, INV>(src, dst, npen, tws);
     case 6: return fft_run_lg<T, 6, INV>(src, dst, npen, tws);
@@ -968,7 +1027,7 @@ __host__ __device__ inline int rows_per_tile(int dim, int n) {
 // (n outside the supported sizes: the largest size_t, which no budget meets)
 template <typename T>
 __host__ __device__ __forceinline__ size_t rows_smem_bytes(int n, int rows) {
-  const int ntw = fft_tw_count(n);
+  const int ntw = fft_tw_capacity<T>(n);
   if (ntw < 0) return ~(size_t)0;
   return (2 * (size_t)(rows / 2) * pen_stride(n) + (size_t)ntw) * sizeof(cx_t<T>);
 }
@@ -1281,7 +1340,7 @@ __device__ __forceinline__ void phase_rows_fwd(const GridDesc& g, const PointDat
 
   // the twiddles load now and land in shared memory after the spread, so
   // their L2 round trip overlaps the zero fill and the spread's own loads
-  const int ntw = fft_tw_count(n);
+  const int ntw = fft_tw_count(n, plan_variant_of<T>(g));
   TableStage<T, kTabBatch> ts;
   if (!write_grid) ts.load(tw, ntw, nullptr, 0, 0);
   for (int e = tid; e < R * n; e += nt) {
@@ -1314,7 +1373,7 @@ __device__ __forceinline__ void phase_rows_fwd(const GridDesc& g, const PointDat
   ts.rest(tw, tws, ntw, nullptr, nullptr, 0);
   __syncthreads();
 
-  C* res = fft_run<T, false>(bufA, bufB, lg, npen, tws);
+  C* res = fft_run<T, false>(bufA, bufB, plan_code_of<T>(g), npen, tws);
 
   for (int e = tid; e < (half + 1) * npen; e += nt) {
     const int k = e >> lgnp, a = e & (npen - 1);
@@ -1350,7 +1409,7 @@ struct PencilLayout {
 // autotuner's choice) replaces the rule when it is admissible.
 template <typename T>
 __host__ __device__ inline size_t pencil_smem_for(int n, int c) {
-  const int ntw = fft_tw_count(n);
+  const int ntw = fft_tw_capacity<T>(n);
   if (ntw < 0) return ~(size_t)0;
   return (2 * (size_t)c * pen_stride(n) + (size_t)ntw) * sizeof(cx_t<T>) +
          (size_t)n * sizeof(T);
@@ -1462,7 +1521,7 @@ __device__ __forceinline__ void phase_pencils(const GridDesc& g, const PencilLay
                                               const unsigned char* zempty = nullptr) {
   using C = cx_t<T>;
   const int n = g.n, lg = g.log2n, c = L.c, lgc = L.lgc, PS = pen_stride(n);
-  const int ntw = fft_tw_count(n);
+  const int ntw = fft_tw_count(n, plan_variant_of<T>(g));
   C* bufA = reinterpret_cast<C*>(smem);
   C* bufB = bufA + (size_t)c * PS;
   C* tws = bufB + (size_t)c * PS;
@@ -1510,9 +1569,9 @@ __device__ __forceinline__ void phase_pencils(const GridDesc& g, const PencilLay
       gio.lgc = lgc;
       gio.zempty = zempty;
       if (tfast)
-        fft_global<T, MODE, false>(bufA, bufB, lg, c, tws, epi, gio);
+        fft_global<T, MODE, false>(bufA, bufB, plan_code_of<T>(g), c, tws, epi, gio);
       else if constexpr (MODE == 2)
-        fft_global<T, MODE, true>(bufA, bufB, lg, c, tws, epi, gio);
+        fft_global<T, MODE, true>(bufA, bufB, plan_code_of<T>(g), c, tws, epi, gio);
       return;  // the last pass ends with a block barrier
     }
   }
@@ -1567,7 +1626,7 @@ __device__ __forceinline__ void phase_pencils(const GridDesc& g, const PencilLay
   ts.rest(tw, tws, ntw, s2, s2s, ns);
   __syncthreads();
 
-  C* res = fft_run<T, MODE == 1>(bufA, bufB, lg, c, tws);
+  C* res = fft_run<T, MODE == 1>(bufA, bufB, plan_code_of<T>(g), c, tws);
   if (MODE == 2) {
     // double-float: the symbol multiply as a sweep of its own
     const T c0 = g.poisson ? (T)0 : (T)1;
@@ -1583,7 +1642,7 @@ __device__ __forceinline__ void phase_pencils(const GridDesc& g, const PencilLay
     }
     __syncthreads();
     C* other = (res == bufA) ? bufB : bufA;
-    res = fft_run<T, true>(res, other, lg, c, tws);
+    res = fft_run<T, true>(res, other, plan_code_of<T>(g), c, tws);
   }
 
   for (int k = tid; k < npairs; k += nt) {
@@ -1634,7 +1693,7 @@ __device__ __forceinline__ void phase_rows_inv(const GridDesc& g, const Bins& b,
   constexpr int U = sizeof(T) == 4 ? 4 : 2;
   const int total = (half + 1) * npen;
   // the twiddles load together with the first batch of the spectrum
-  const int ntw = fft_tw_count(n);
+  const int ntw = fft_tw_count(n, plan_variant_of<T>(g));
   TableStage<T, kTabBatch> ts;
   ts.load(tw, ntw, nullptr, 0, 0);
   for (int e0 = tid; e0 < total; e0 += U * nt) {
@@ -1678,10 +1737,10 @@ __device__ __forceinline__ void phase_rows_inv(const GridDesc& g, const Bins& b,
   const size_t row0 = ((size_t)z * n + y0) * n;
   if constexpr (DirectPencils<T>::value) {
     // the last radix pass writes the rows (it ends with a block barrier)
-    fft_inverse_rows<T, OutT>(bufA, bufB, lg, npen, tws, out + row0);
+    fft_inverse_rows<T, OutT>(bufA, bufB, plan_code_of<T>(g), npen, tws, out + row0);
     return;
   }
-  C* res = fft_run<T, true>(bufA, bufB, lg, npen, tws);
+  C* res = fft_run<T, true>(bufA, bufB, plan_code_of<T>(g), npen, tws);
   for (int e = tid; e < R * n; e += nt) {
     const int r = e >> lg, x = e & (n - 1);
     const C v = res[(r >> 1) * PS + padi(x)];

@@ -104,6 +104,10 @@ struct GridDesc {
   // z), per element type [0] float64, [1] float32, [2] double-float; 0: the
   // fixed rule
   int scap[3] = {0, 0, 0};
+  // FFT plan variant of the float32 transforms (plan_lr: 0 radices as even
+  // as possible, 1 radix-16 passes first), chosen by the autotuner; the
+  // float32 twiddle table is of the same variant
+  int fplan = 0;
 };
 
 // Host constants of the symbol multiply: the solve scales mode k by

@@ -77,7 +77,8 @@ __global__ void __launch_bounds__(512) k_zsolve_tma(GridDesc g, int c, int lgc, 
   __shared__ __align__(8) uint64_t bar;
   __shared__ TmaItem ti;
   __shared__ int bad;
-  const int n = g.n, lg = g.log2n, PS = pen_stride(n), ntw = fft_tw_count(n);
+  const int n = g.n, lg = g.log2n, PS = pen_stride(n);
+  const int ntw = fft_tw_count(n, plan_variant_of<T>(g));
   const int tid = threadIdx.x;
   C* box = reinterpret_cast<C*>(smem);  // dense [n][c] when staged; padded pencils later
   C* bufB = box + (size_t)c * PS;
@@ -139,7 +140,7 @@ __global__ void __launch_bounds__(512) k_zsolve_tma(GridDesc g, int c, int lgc, 
     // next item into the box
     gio.tma = &ti;
     gio.tma_next = k + (int)gridDim.x < nitems ? k + (int)gridDim.x : -1;
-    fft_global<T, 2, true, true>(box, bufB, lg, c, tws, epi, gio);  // ends with a barrier
+    fft_global<T, 2, true, true>(box, bufB, plan_code_of<T>(g), c, tws, epi, gio);  // ends with a barrier
   }
   if (bad) {
     // the copy engine did not deliver within the bound: report it, then wait
@@ -177,7 +178,7 @@ EncodeTiled encoder() {
 
 template <typename T>
 size_t zsolve_smem(int n, int c) {
-  const int ntw = fft_tw_count(n);
+  const int ntw = fft_tw_capacity<T>(n);
   if (ntw < 0) return ~(size_t)0;
   // the staging box (dense n x c) lives in the first of the two padded
   // pencil buffers (c x pen_stride(n) >= n x c)

@@ -41,7 +41,7 @@ EXPORTS = [
     "ibdl_server_get_stats", "ibdl_tuning_enable", "ibdl_tuning_set", "ibdl_indicator",
     "ibdl_near_boundary", "ibdl_selftest_bounded_wait", "ibdl_solver_smem_query",
     "ibdl_tuning_set_pencils", "ibdl_profile_trace", "ibdl_profile_trace_read",
-    "ibdl_geometry_set_solver_pencils",
+    "ibdl_geometry_set_solver_pencils", "ibdl_tuning_set_plan",
 ]
 
 
@@ -85,7 +85,7 @@ class GeometryInfo(C.Structure):
         ("kappa", C.c_double), ("bc", C.c_int32), ("delta", C.c_int32),
         ("precision", C.c_int32), ("device_bytes", C.c_int64),
         ("fft_passes", C.c_int32), ("rows_per_tile", C.c_int32),
-        ("pencils_per_item", C.c_int32 * 2),
+        ("pencils_per_item", C.c_int32 * 2), ("fft_plan", C.c_int32),
     ]
 
 
@@ -179,6 +179,7 @@ def load(path: str = LIB_PATH):
         "ibdl_solver_smem_query": (C.c_int, [i32, i32, i32, i32, C.POINTER(i64),
                                              C.POINTER(i64), C.POINTER(i32)]),
         "ibdl_tuning_set_pencils": (C.c_int, [i32, i32, i32, i32, i32]),
+        "ibdl_tuning_set_plan": (C.c_int, [i32, i32, i32, i32]),
         "ibdl_profile_trace": (C.c_int, [i32]),
         "ibdl_profile_trace_read": (i64, [vp, i64]),
         "ibdl_geometry_set_solver_pencils": (C.c_int, [vp, i32, i32, i32]),
@@ -317,6 +318,12 @@ def tuning_set_pencils(dim: int, n: int, precision: int, c_solve: int, c_y: int 
     both 0 drops the pin."""
     _check(load().ibdl_tuning_set_pencils(int(dim), int(n), int(precision), int(c_solve),
                                           int(c_y)))
+
+
+def tuning_set_plan(dim: int, n: int, precision: int, plan: int) -> None:
+    """Pin the float32 FFT plan variant of (current device, dim, n,
+    precision); -1 drops the pin."""
+    _check(load().ibdl_tuning_set_plan(int(dim), int(n), int(precision), int(plan)))
 
 
 def version() -> int:

@@ -119,3 +119,56 @@ def test_every_pencil_choice_matches_oracle(name, prec, checks, csolve, cy):
             ibdl.tuning_set_pencils(g.dim, g.n, prec, 3, 0)
     finally:
         ibdl.tuning_set_pencils(g.dim, g.n, prec, 0, 0)
+
+
+@pytest.mark.parametrize("n", [512, 1024])
+@pytest.mark.parametrize("plan", [0, 1])
+def test_every_fft_plan_matches_the_oracle(n, plan):
+    """Both FFT plan variants of the float32 transforms (radices as even as
+    possible after a first radix-16 pass, or radix-16 passes first: 1024 =
+    16*8*8 or 16*16*4, 512 = 16*8*4 or 16*16*2), pinned for a 2D
+    float32-refined kind, give the float64 oracle's operator element-wise at
+    the float32 matvec tolerance, through the launch-based passes; the
+    geometry reports the plan it uses."""
+    g = geometry.star(n, 0.3, 0.2, 5, kappa=1e-3)
+    q = np.random.default_rng(40 + n + plan).standard_normal(g.m)
+    try:
+        ibdl.tuning_set_plan(2, n, ibdl.FP32_REFINED, plan)
+        G = pkg.Geometry.from_workload(g, bc=configs.DIRICHLET, precision=ibdl.FP32_REFINED)
+        assert G.info()["fft_plan"] == plan
+        y = torch.empty(g.m, dtype=torch.float64, device=DEV)
+        G.apply(torch.tensor(q, device=DEV), y, precision=ibdl.FP32_REFINED)
+        torch.cuda.synchronize()
+        G.close()
+    finally:
+        ibdl.tuning_set_plan(2, n, ibdl.FP32_REFINED, -1)
+    ref = O.Operator(g, configs.DIRICHLET).apply(q)
+    assert_parity(y.cpu().numpy(), ref, 1e-5, f"plan {plan} n={n}")
+
+
+def test_radix16_first_plan_in_the_persistent_solver():
+    """With the radix-16-first plan pinned for the C2 kind, the persistent
+    solver's float32 items transform in that plan too: the benchmark's
+    Dirichlet + Neumann pair, solved in one batched launch at tol 1e-8,
+    matches the oracle's solves (Sec. 5.3) to 1e-8."""
+    probs = [configs.c2(bc=configs.DIRICHLET), configs.c2(bc=configs.NEUMANN)]
+    try:
+        ibdl.tuning_set_plan(2, 1024, ibdl.FP32_REFINED, 1)
+        gs = [pkg.Geometry.from_workload(p.geom, bc=p.bc, precision=ibdl.FP32_REFINED)
+              for p in probs]
+    finally:
+        ibdl.tuning_set_plan(2, 1024, ibdl.FP32_REFINED, -1)
+    qs = [torch.zeros(p.geom.m, dtype=torch.float64, device=DEV) for p in probs]
+    batch = ibdl.Batch(2)
+    try:
+        assert all(G.info()["fft_plan"] == 1 for G in gs)
+        infos = batch.solve(gs, [torch.tensor(p.bdata, device=DEV) for p in probs], qs,
+                            tol=1e-8)
+    finally:
+        batch.close()
+        for G in gs:
+            G.close()
+    for p, q, info in zip(probs, qs, infos):
+        assert info["status"] == ibdl.OK and info["rel_residual"] <= 1e-8, info
+        ref = O.solve(p.geom, p.bc, p.bdata, tol=1e-13).x
+        assert_parity(q.cpu().numpy(), ref, 1e-8, f"{p.name} plan 1")

@@ -25,25 +25,37 @@ def lib():
     return pkg.load()
 
 
-def plan_radices(lg):
-    """Radix of each pass: 16 first (n itself below 16), the remaining bits
-    split as evenly as possible, larger radices first."""
+def plan_radices(lg, variant=0):
+    """Radix of each pass: 16 first (n itself below 16), then the remaining
+    bits split as evenly as possible, larger radices first (variant 0), or
+    radix-16 passes first and the remainder last (variant 1)."""
     if lg <= 4:
         return [1 << lg]
     rest = lg - 4
     npass = (rest + 3) // 4
     out = [16]
+    if variant == 1:
+        return out + [16] * (npass - 1) + [1 << (rest - 4 * (npass - 1))]
     for s in range(npass):
         out.append(1 << (rest // npass + (1 if s < rest % npass else 0)))
     return out
 
 
-def twiddle_count(lg):
+def twiddle_count(lg, variant=0):
     ns, tot = 1, 0
-    for r in plan_radices(lg):
+    for r in plan_radices(lg, variant):
         tot += ns * r
         ns *= r
     return tot
+
+
+def table_capacity(lg, elem):
+    """Entries a twiddle buffer holds: float32 tables (elem 1) may be of
+    either plan variant where two exist (lg 9, 10), so they are sized for
+    the larger."""
+    if elem == 1 and lg in (9, 10):
+        return max(twiddle_count(lg, 0), twiddle_count(lg, 1))
+    return twiddle_count(lg)
 
 
 def tilings(dim, n):
@@ -81,7 +93,8 @@ def test_every_item_fits_the_launch(lib, dim, n):
             # twiddle table, in the element type's complex size
             csize = 8 if elem == 1 else 16
             pen_stride = n + n // 16 + 1
-            assert q["need"][0] == (2 * (rows // 2) * pen_stride + twiddle_count(lg)) * csize
+            assert q["need"][0] == (2 * (rows // 2) * pen_stride
+                                    + table_capacity(lg, elem)) * csize
         assert len(budgets) == 1      # one reservation per geometry
         # the reservation fits an SM's shared memory (227 KB per block)
         assert budgets.pop() <= 227 * 1024
@@ -92,6 +105,31 @@ def test_plan_twiddle_counts_by_hand():
     assert plan_radices(10) == [16, 8, 8] and twiddle_count(10) == 16 + 128 + 1024
     assert plan_radices(8) == [16, 16] and twiddle_count(8) == 16 + 256
     assert plan_radices(12) == [16, 16, 16] and twiddle_count(12) == 16 + 256 + 4096
+    # the radix-16-first variant: 1024 = 16 * 16 * 4, 512 = 16 * 16 * 2
+    assert plan_radices(10, 1) == [16, 16, 4] and twiddle_count(10, 1) == 16 + 256 + 1024
+    assert plan_radices(9, 1) == [16, 16, 2] and twiddle_count(9, 1) == 16 + 256 + 512
+    # elsewhere the two variants coincide (only lg 9 and 10 offer variant 1)
+    for lg in (4, 5, 6, 7, 8, 11, 12):
+        assert plan_radices(lg, 1) == plan_radices(lg)
+
+
+@pytest.mark.parametrize("n,plan", [(1024, 1), (512, 1), (1024, 0), (2048, 0)])
+def test_plan_pins_are_checked_on_the_host(lib, n, plan):
+    # a float32-refined 2D kind accepts any plan offered for its size (the
+    # pin touches no GPU memory; without a device it reports the CUDA error)
+    try:
+        ibdl.tuning_set_plan(2, n, ibdl.FP32_REFINED, plan)
+        ibdl.tuning_set_plan(2, n, ibdl.FP32_REFINED, -1)
+    except ibdl.IbdlError as e:
+        assert e.status == ibdl.ERR_CUDA
+
+
+@pytest.mark.parametrize("dim,n,prec,plan", [(2, 256, 1, 1), (2, 2048, 1, 1), (3, 512, 1, 1),
+                                             (2, 1024, 0, 1), (2, 1024, 1, 2), (2, 1000, 1, 0)])
+def test_plan_pins_outside_the_offered_set_are_refused(lib, dim, n, prec, plan):
+    with pytest.raises(ibdl.IbdlError) as e:
+        ibdl.tuning_set_plan(dim, n, prec, plan)
+    assert e.value.status == ibdl.ERR_INVALID_ARG
 
 
 @pytest.mark.parametrize("dim,n,rows,elem", [(2, 8, 4, 0), (2, 4096, 2, 0), (3, 1024, 8, 0),
