@@ -709,6 +709,7 @@ SolveInst make_inst(ibdl_geometry_s* g, const ibdl_solve_opts& o, int batch_size
   I.r = g->vr;
   I.dvec = g->vt;  // free in the persistent engine (the host loop's scratch)
   I.upd_resid = g->precision == IBDL_FP32_REFINED;
+  I.cgs1 = g->precision == IBDL_FP32_REFINED;
   I.bc = g->bc;
   I.refined = g->precision == IBDL_FP32_REFINED;
   I.maxit = o.max_iters;

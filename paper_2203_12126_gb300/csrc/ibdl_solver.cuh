@@ -75,6 +75,10 @@ struct SolveInst {
   // the tolerance and counted against it
   int upd_resid;
   double* dvec;         // the last inner solve's correction d = V y
+  // 1: float32 Arnoldi steps that interpolate in phase D orthogonalise in
+  // one classical Gram-Schmidt pass, the new norm by Pythagoras from the
+  // same reduction (phases D and E; float64 steps keep two passes)
+  int cgs1;
   double* x;
   double* r;
   int bc;

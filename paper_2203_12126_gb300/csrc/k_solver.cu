@@ -366,6 +366,18 @@ __device__ __forceinline__ bool fused_step(const SolveInst& I, int action, int p
   return action == ACT_MV_ARNOLDI && (I.fuse_interp == 2 || (I.fuse_interp == 1 && prec == 1));
 }
 
+// A float32 Arnoldi step that interpolates in phase D (not in its x-inverse
+// tiles) may orthogonalise in one pass: phase D adds ||w||^2 to the dot
+// products V_c . w, and phase E takes h = V^T w, ||w - V h||^2 = ||w||^2 -
+// |h|^2 (V orthonormal), w <- (w - V h) / ||w - V h||, Givens and control --
+// one vector phase fewer per step.  Inner solves stop at a 1e-5 reduction
+// within a few steps, where one pass keeps V orthonormal to about 1e-13 and
+// the subtraction loses at most about eps64 ||w||^2 / ||w - V h||^2 of the
+// new norm; float64 steps (tolerances to 1e-12, longer cycles) keep two.
+__device__ __forceinline__ bool single_pass(const SolveInst& I, int action, int prec) {
+  return I.cgs1 && action == ACT_MV_ARNOLDI && prec == 1 && !fused_step(I, action, prec);
+}
+
 template <typename T, int D>
 __device__ __noinline__ void solver_rows_inv(const SolveInst& I, const RoundView& v, int item,
                                              unsigned char* smem) {
@@ -486,7 +498,7 @@ __device__ void phase_D(const SolveInst& I, SolveState* S, const RoundView& v, i
       w = acc + jump * __ldcg(vin + i);
       I.V[(size_t)(v.j + 1) * I.ld + i] = w;
     }
-    chunk_dots(I, w, valid, i, v.j + 1, false, part1, chunk, R);
+    chunk_dots(I, w, valid, i, v.j + 1, single_pass(I, v.action, v.prec), part1, chunk, R);
     return;
   }
   // residual actions: r = b - A x (or r = b), partial ||r||^2 and ||b||^2
@@ -549,12 +561,18 @@ __device__ void cgs_pass(const SolveInst& I, const RoundView& v, int chunk, Bloc
   chunk_dots(I, w, valid, i, ncols, true, out, chunk, R);
 }
 
+__device__ void phase_F(const SolveInst& I, SolveState* S, const RoundView& v, int chunk,
+                        BlockRed& R, bool single = false);
+
 __device__ void phase_E(const SolveInst& I, SolveState* S, const RoundView& v, int chunk,
                         BlockRed& R) {
   double* part1 = I.part;
   double* part2 = I.part + (size_t)I.nsec * I.pstride;
   if (v.action == ACT_MV_ARNOLDI) {
-    cgs_pass(I, v, chunk, R, part1, part2);
+    if (single_pass(I, v.action, v.prec))
+      phase_F(I, S, v, chunk, R, true);  // the one pass: F's work on D's sums
+    else
+      cgs_pass(I, v, chunk, R, part1, part2);
     return;
   }
   // item nchunk runs the round's control step beside the vector work of
@@ -751,10 +769,12 @@ __device__ void control(const SolveInst& I, SolveState* S, const RoundView& v, d
 // ||w1||^2 come from phase E's partials; ||w2||^2 = ||w1||^2 - |h2|^2 since
 // w2 = w1 - V h2 with V orthonormal and h2 = V^T w1 (the second pass's
 // correction is small, so the difference does not cancel).
+// single: a one-pass step (single_pass), run as phase E on phase D's sums
+// (h1 and ||w||^2; the Hessenberg column is h1 alone)
 __device__ void phase_F(const SolveInst& I, SolveState* S, const RoundView& v, int chunk,
-                        BlockRed& R) {
+                        BlockRed& R, bool single) {
   const int j = v.j, ncols = j + 1, ldh = I.restart + 1;
-  double* part2 = I.part + (size_t)I.nsec * I.pstride;
+  double* part2 = single ? I.part : I.part + (size_t)I.nsec * I.pstride;
   // item nchunk runs the control step beside the normalisation of items
   // 0 .. nchunk - 1; its inputs (the state, the Hessenberg column's first
   // pass, the earlier rotations, g_j) go out beside the partial sums' loads
@@ -763,7 +783,7 @@ __device__ void phase_F(const SolveInst& I, SolveState* S, const RoundView& v, i
   SolveState st;
   if (ctl_item) {
     const int r = threadIdx.x;
-    if (r <= j) hcol = __ldcg(I.H + (size_t)j * ldh + r);
+    if (r <= j && !single) hcol = __ldcg(I.H + (size_t)j * ldh + r);
     if (r < j) {
       csr = __ldcg(I.cs + r);
       snr = __ldcg(I.sn + r);
@@ -1100,7 +1120,8 @@ __device__ int next_phase(const SolveInst& I, int phase, int action, int prec) {
       if (I.single) return kPhaseSingle;
       return fused_step(I, action, prec) ? kPhaseE : kPhaseD;
     case kPhaseD: return action == ACT_RHS ? -1 : kPhaseE;
-    case kPhaseE: return action == ACT_MV_ARNOLDI ? kPhaseF : -1;
+    case kPhaseE:
+      return action == ACT_MV_ARNOLDI && !single_pass(I, action, prec) ? kPhaseF : -1;
     default: return -1;
   }
 }
@@ -1110,7 +1131,9 @@ __device__ int items_of(const SolveInst& I, const PhaseDesc& d) {
   if (d.phase == kPhaseSingle) return 1;
   // the control step is an item of its own in F, and in E when the round
   // ends there (phase_E, phase_F)
-  if (d.phase == kPhaseF || (d.phase == kPhaseE && d.action != ACT_MV_ARNOLDI))
+  if (d.phase == kPhaseF ||
+      (d.phase == kPhaseE &&
+       (d.action != ACT_MV_ARNOLDI || single_pass(I, d.action, d.prec))))
     return I.nchunk + 1;
   return I.nchunk;
 }
