@@ -149,6 +149,7 @@ struct BlockRed {
   double col[kMaxCols];  // staged H column / Givens vectors for the control step
   double cs[kMaxCols];
   double sn[kMaxCols];
+  int fin;  // k > 0: the control step just chose FINISH with k columns
 };
 
 // out[c] = sum over chunks of part[ch * pstride + c0 + c], c < ncols: one
@@ -436,6 +437,41 @@ __device__ void mv_item(const SolveInst& I, const RoundView& v, int phase, int i
 
 // ---- vector phases ------------------------------------------------------------
 
+// Back substitution R y = g (R: the rotated Hessenberg's k x k upper
+// triangle, column l at H + l ldh), by the whole block; y goes to I.ysol,
+// which the next phase reads (released with the item's done count).  The
+// block stages R and g in shared memory in one round of loads (up to
+// kMaxCols (kSolverThreads / 32) entries; larger k read them as they go),
+// then one thread solves.
+__device__ void back_substitute(const SolveInst& I, int k, BlockRed& R) {
+  const int ldh = I.restart + 1;
+  const bool staged = k * (k + 1) / 2 <= kMaxCols * (kSolverThreads / 32);
+  double* tri = &R.red[0][0];  // entry (r, l), r <= l, at l (l + 1) / 2 + r
+  if (staged) {
+    for (int e = threadIdx.x; e < k * (k + 1) / 2; e += blockDim.x) {
+      int l = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
+      while (l * (l + 1) / 2 > e) --l;
+      while ((l + 1) * (l + 2) / 2 <= e) ++l;
+      const int r = e - l * (l + 1) / 2;
+      tri[e] = __ldcg(I.H + (size_t)l * ldh + r);
+    }
+    for (int r = threadIdx.x; r < k; r += blockDim.x) R.h[r] = __ldcg(I.gv + r);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int r = k - 1; r >= 0; --r) {
+      double sacc = staged ? R.h[r] : __ldcg(I.gv + r);
+      for (int l = r + 1; l < k; ++l)
+        sacc -= (staged ? tri[l * (l + 1) / 2 + r] : __ldcg(I.H + (size_t)l * ldh + r)) *
+                R.col[l];
+      const double dgn = staged ? tri[r * (r + 1) / 2 + r] : __ldcg(I.H + (size_t)r * ldh + r);
+      R.col[r] = dgn != 0.0 ? sacc / dgn : 0.0;
+    }
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < k; r += blockDim.x) I.ysol[r] = R.col[r];
+}
+
 template <int D>
 __device__ void phase_D(const SolveInst& I, SolveState* S, const RoundView& v, int chunk,
                         BlockRed& R) {
@@ -443,39 +479,9 @@ __device__ void phase_D(const SolveInst& I, SolveState* S, const RoundView& v, i
   const bool valid = i < I.p.m;
   double* part1 = I.part;
   if (v.action == ACT_FINISH) {
-    if (chunk == 0) {
-      // back substitution R y = g (R: the rotated Hessenberg's k x k upper
-      // triangle, column l at H + l ldh).  The block stages R and g in shared
-      // memory in one round of loads (up to kMaxCols (kSolverThreads / 32)
-      // entries; larger k read them as they go), then one thread solves.
-      const int k = v.kdim, ldh = I.restart + 1;
-      const bool staged = k * (k + 1) / 2 <= kMaxCols * (kSolverThreads / 32);
-      double* tri = &R.red[0][0];  // entry (r, l), r <= l, at l (l + 1) / 2 + r
-      if (staged) {
-        for (int e = threadIdx.x; e < k * (k + 1) / 2; e += blockDim.x) {
-          int l = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
-          while (l * (l + 1) / 2 > e) --l;
-          while ((l + 1) * (l + 2) / 2 <= e) ++l;
-          const int r = e - l * (l + 1) / 2;
-          tri[e] = __ldcg(I.H + (size_t)l * ldh + r);
-        }
-        for (int r = threadIdx.x; r < k; r += blockDim.x) R.h[r] = __ldcg(I.gv + r);
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        for (int r = k - 1; r >= 0; --r) {
-          double sacc = staged ? R.h[r] : __ldcg(I.gv + r);
-          for (int l = r + 1; l < k; ++l)
-            sacc -= (staged ? tri[l * (l + 1) / 2 + r] : __ldcg(I.H + (size_t)l * ldh + r)) *
-                    R.col[l];
-          const double dgn = staged ? tri[r * (r + 1) / 2 + r] : __ldcg(I.H + (size_t)r * ldh + r);
-          R.col[r] = dgn != 0.0 ? sacc / dgn : 0.0;
-        }
-      }
-      __syncthreads();
-      // read in the next phase: released with the item's done count
-      for (int r = threadIdx.x; r < k; r += blockDim.x) I.ysol[r] = R.col[r];
-    }
+    // (the control step that chose FINISH solved for y already, phase_F;
+    // a round that starts here solves now)
+    if (chunk == 0) back_substitute(I, v.kdim, R);
     return;
   }
   if (v.action == ACT_RHS) {
@@ -811,8 +817,13 @@ __device__ void phase_F(const SolveInst& I, SolveState* S, const RoundView& v, i
     if (threadIdx.x == 0) {
       R.h[0] = gj;
       control(I, S, v, hn, 0, 0, R, &st);
+      // its own writes (state, H column, g): the FINISH round's back
+      // substitution runs here, so that round starts at phase E
+      const volatile SolveState* vs = S;
+      R.fin = vs->action == ACT_FINISH ? vs->kdim : 0;
     }
     __syncthreads();
+    if (R.fin > 0) back_substitute(I, R.fin, R);
     return;
   }
   const double inv = (hn > 0 && isfinite(hn)) ? 1.0 / hn : 0.0;
@@ -1105,7 +1116,9 @@ __device__ void store_desc(PhaseDesc* p, const PhaseDesc& d) {
 
 __device__ int first_phase(const SolveInst& I, int action) {
   if (is_mv(action)) return 0;
-  return I.single ? kPhaseSingle : kPhaseD;
+  if (I.single) return kPhaseSingle;
+  // y was solved for by the control step that chose FINISH (phase_F)
+  return action == ACT_FINISH ? kPhaseE : kPhaseD;
 }
 
 // -1: the round ends after `phase` (of a round doing `action`)
