@@ -740,9 +740,9 @@ def load_peaks():
 
 
 # DRAM bytes (read + write) of one batched-pair launch of the persistent
-# solver, from one ncu capture of that launch (53.9 MB read + 118.5 MB
+# solver, from one ncu capture of that launch (53.5 MB read + 119.5 MB
 # write); None whenever the solver kernel changes, until it is captured again
-PAIR_LAUNCH_DRAM_BYTES = (53.921536 + 118.509056) * 1e6
+PAIR_LAUNCH_DRAM_BYTES = (53.455872 + 119.521536) * 1e6
 PAIR_LAUNCH_DRAM_SRC = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one pair launch "
                         "(profiles/c2_persistent_solve.md)")
 

@@ -759,6 +759,7 @@ SolveState initial_state(SolveInst& I, bool x_zero, bool rhs_in_kernel = false) 
   memset(&s, 0, sizeof(s));
   s.action = x_zero ? ACT_RESID_ZERO : ACT_MV_RESIDUAL;
   I.rhs_resid = rhs_in_kernel && I.refined ? 1 : 0;
+  I.rhs_r0 = rhs_in_kernel && x_zero ? 1 : 0;
   if (rhs_in_kernel) {
     s.action = ACT_RHS;
     s.prec = I.rhs_resid;

@@ -68,6 +68,9 @@ struct SolveInst {
   // one Helmholtz solve, r = -(S* kappa L'^{-1} (S~ x + S V_b) - x / 2)
   // = b - A x, so b itself is never needed to float64 accuracy
   int rhs_resid;
+  // 1: ACT_RHS is followed by RESID_ZERO (x = 0); its phase D also writes
+  // r = b and the partial sums of ||r||^2, ||b||^2, and RESID_ZERO starts at E
+  int rhs_r0;
   // 1 (float32-refined solves): after an inner solve whose correction d is
   // small, the residual is updated, r <- r - A32 d (ACT_MV_UPDATE), instead
   // of recomputed with a float64-grade matvec; its error grows by at most

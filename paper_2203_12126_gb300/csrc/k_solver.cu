@@ -492,7 +492,10 @@ __device__ void phase_D(const SolveInst& I, SolveState* S, const RoundView& v, i
       I.bvec[i] = v.prec ? (double)interp_point<float, D>(I.g, I.p, I.w32.grid, i)
                          : interp_point<double, D>(I.g, I.p, I.w64.grid, i);
     if (chunk == 0 && threadIdx.x == 0) control(I, S, v, 0, 0, 0, R);
-    return;
+    if (!I.rhs_r0) return;
+    // the solve starts from x = 0 (RESID_ZERO next): this phase also does
+    // that round's phase D, r = b and its partial sums (below), so the round
+    // starts at phase E
   }
   const double jump = I.bc == IBDL_DIRICHLET ? 0.5 : -0.5;
   if (v.action == ACT_MV_ARNOLDI) {
@@ -1117,6 +1120,8 @@ __device__ void store_desc(PhaseDesc* p, const PhaseDesc& d) {
 __device__ int first_phase(const SolveInst& I, int action) {
   if (is_mv(action)) return 0;
   if (I.single) return kPhaseSingle;
+  // r = b and its partial sums came with the right-hand side's phase D
+  if (action == ACT_RESID_ZERO && I.rhs_r0) return kPhaseE;
   // y was solved for by the control step that chose FINISH (phase_F)
   return action == ACT_FINISH ? kPhaseE : kPhaseD;
 }
