@@ -303,6 +303,10 @@ def run_batched_c4(pkg, count=256, reps=5):
     insts = configs.c4_instances(count)
     geoms = [pkg.Geometry.from_workload(p.geom, bc=p.bc, precision=ibdl.FP32_REFINED)
              for p in insts]
+    # the autotuner's tiling per grid size (the batch's time depends on it)
+    picks = {}
+    for p, g in zip(insts, geoms):
+        picks.setdefault(str(p.geom.n), g.info()["rows_per_tile"])
     bs = [torch.tensor(p.bdata, dtype=torch.float64, device=dev) for p in insts]
     qs = [torch.zeros(p.geom.m, dtype=torch.float64, device=dev) for p in insts]
     batch = ibdl.Batch(count)
@@ -323,6 +327,7 @@ def run_batched_c4(pkg, count=256, reps=5):
     med = float(np.median(ms))
     return {"workload": f"{count} 2D star instances, N in {{128,256,512}}^2 (seed 2), "
                         "float32-refined, tol 1e-8, one persistent launch",
+            "rows_per_tile": picks,
             "solves_per_s": count / (med / 1e3), "launch_ms": med,
             "max_rel_residual": float(max(f["rel_residual"] for f in infos)),
             "all_ok": all(f["status"] == 0 for f in infos),
