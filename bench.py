@@ -679,6 +679,29 @@ def model_matvec_bytes(dim, n, m, p):
     return 9 * p * n ** dim + p * m * (4 ** dim + 2 * dim + 4)
 
 
+def launch_field_solves(infos, per_launch, refined, neumann, n, m, dim=2):
+    """Field solves of one persistent launch by precision, and its
+    algorithmic bytes by the matvec model: (float64-grade, float32, bytes).
+    infos: the solve infos of the launches timed (per_launch solves each,
+    in the order of `neumann`, a flag per problem).  A refined solve's
+    matvecs are its inner iterations and residual updates (float32) and its
+    float64-grade residuals; a Neumann solve adds one field solve for its
+    right-hand side (float32 when refined: its residuals carry the S V_b
+    term; float64 else)."""
+    mv = float(np.mean([f["matvecs"] for f in infos])) * per_launch
+    it = float(np.mean([f["iters"] for f in infos])) * per_launch
+    up = float(np.mean([f.get("residual_updates", 0) for f in infos])) * per_launch
+    mv64 = (mv - it - up) if refined else mv
+    mv32 = (it + up) if refined else 0.0
+    nneu = per_launch * sum(bool(x) for x in neumann) / len(neumann)
+    if refined:
+        mv32 += nneu
+    else:
+        mv64 += nneu
+    B = mv64 * model_matvec_bytes(dim, n, m, 8) + mv32 * model_matvec_bytes(dim, n, m, 4)
+    return mv64, mv32, B
+
+
 def run_matvec_roofline(pkg, peaks, reps=30):
     """Event-timed matvecs (float32, float64, and float64 with double-float
     transforms) on the 3D 256^3 sphere (the HBM-bound case) and the 2D
@@ -1042,21 +1065,9 @@ def main():
             # p = 4 for the float32 Arnoldi matvecs (and a refined launch's
             # Neumann right-hand side and residual updates), p = 8 for the
             # float64-grade ones (the residuals, transformed in double-float)
-            mv = float(np.mean([f["matvecs"] for f in pinfos])) * per_launch
-            it = float(np.mean([f["iters"] for f in pinfos])) * per_launch
-            # residuals updated by a float32 matvec of the correction
-            up = float(np.mean([f.get("residual_updates", 0) for f in pinfos])) * per_launch
-            mv64 = (mv - it - up) if prec == ibdl.FP32_REFINED else mv
-            mv32 = (it + up) if prec == ibdl.FP32_REFINED else 0.0
-            # the Neumann right-hand side is one more field solve: float32 in
-            # a refined launch (its residuals carry the S V_b term), float64
-            # else
-            nneu = per_launch * sum(p.bc == configs.NEUMANN for p in probs) / len(probs)
-            if prec == ibdl.FP32_REFINED:
-                mv32 += nneu
-            else:
-                mv64 += nneu
-            B = (mv64 * model_matvec_bytes(2, n, m, 8) + mv32 * model_matvec_bytes(2, n, m, 4))
+            mv64, mv32, B = launch_field_solves(
+                pinfos, per_launch, prec == ibdl.FP32_REFINED,
+                [p.bc == configs.NEUMANN for p in probs], n, m)
             ach = B / avg_s / 1e9
             roofline = {"kernel": name, "bound": "hbm", "achieved": ach,
                         "peak": peaks["hbm_gbs"], "unit": "GB/s",
